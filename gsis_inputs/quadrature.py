@@ -1,0 +1,94 @@
+"""Seeded/deterministic quadrature generators (inputs only, no method arithmetic).
+
+Velocity grids are returned as ``(xi, w)`` with ``xi`` of shape ``[n, vdim]`` and
+``w`` of shape ``[n]`` such that ``sum_i w_i phi(xi_i)`` approximates the integral
+of ``phi`` over the (reduced) velocity space.  Photon grids are ``(omega, w)``
+with unit directions ``omega`` of shape ``[n, 3]`` and ``sum w = 4*pi``.
+
+These rules are the inputs that the solver and the oracle both consume: the
+velocity grids of the paper's cases are uniform Cartesian grids in a reduced
+velocity space (Section 6) and the photon grids cover the unit sphere.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def gauss_hermite_1d(n: int):
+    """n-point Gauss-Hermite rule for the weight exp(-xi^2/2) on the real line.
+
+    The stored weights absorb exp(+xi^2/2), so ``sum w_i f(xi_i)`` approximates
+    ``int f dxi`` for Maxwellian-like ``f``.
+    """
+    x, wx = np.polynomial.hermite.hermgauss(n)      # weight exp(-x^2)
+    xi = np.sqrt(2.0) * x
+    w = np.sqrt(2.0) * wx * np.exp(x * x)
+    return xi.reshape(n, 1), w
+
+
+def newton_cotes_38_weights(n: int, half_width: float):
+    """Composite Simpson-3/8 rule with n points on [-L, L]; n-1 must be a multiple of 3."""
+    if (n - 1) % 3 != 0:
+        raise ValueError("composite 3/8 rule needs n = 3k + 1 points")
+    x = np.linspace(-half_width, half_width, n)
+    h = x[1] - x[0]
+    w = np.zeros(n)
+    for p in range((n - 1) // 3):
+        w[3 * p: 3 * p + 4] += np.array([1.0, 3.0, 3.0, 1.0]) * (3.0 * h / 8.0)
+    return x, w
+
+
+def trapezoid_weights(n: int, half_width: float):
+    """Uniform trapezoid rule with n points on [-L, L]."""
+    x = np.linspace(-half_width, half_width, n)
+    h = x[1] - x[0]
+    w = np.full(n, h)
+    w[0] = w[-1] = 0.5 * h
+    return x, w
+
+
+def tensor_grid(nodes_w_list):
+    """Tensor product of 1-D rules; the first axis varies slowest."""
+    xs = [nw[0] for nw in nodes_w_list]
+    ws = [nw[1] for nw in nodes_w_list]
+    mesh = np.meshgrid(*xs, indexing="ij")
+    wmesh = np.meshgrid(*ws, indexing="ij")
+    xi = np.stack([m.ravel() for m in mesh], axis=1)
+    w = np.ones(xi.shape[0])
+    for wm in wmesh:
+        w = w * wm.ravel()
+    return xi, w
+
+
+def newton_cotes_2d(n: int, half_width: float):
+    """n x n composite Newton-Cotes (3/8) product grid on [-L, L]^2."""
+    r = newton_cotes_38_weights(n, half_width)
+    return tensor_grid([r, r])
+
+
+def trapezoid_nd(n: int, half_width: float, dim: int):
+    r = trapezoid_weights(n, half_width)
+    return tensor_grid([r] * dim)
+
+
+def gauss_legendre_slab(n: int):
+    """Photon directions for a plane-parallel slab: Gauss-Legendre in mu = Omega_x.
+
+    Each node stands for the ring of directions with the same mu, so its weight
+    is 2*pi times the Gauss-Legendre weight; the direction stored for the ring is
+    (mu, sqrt(1-mu^2), 0).
+    """
+    mu, wmu = np.polynomial.legendre.leggauss(n)
+    om = np.stack([mu, np.sqrt(1.0 - mu * mu), np.zeros(n)], axis=1)
+    return om, 2.0 * np.pi * wmu
+
+
+def photon_product(n_polar: int, n_azim: int):
+    """Gauss-Legendre in cos(polar angle about z) x uniform azimuth in the x-y plane."""
+    mu, wmu = np.polynomial.legendre.leggauss(n_polar)
+    phi = (np.arange(n_azim) + 0.5) * (2.0 * np.pi / n_azim)
+    M, P = np.meshgrid(mu, phi, indexing="ij")
+    W = np.meshgrid(wmu, np.full(n_azim, 2.0 * np.pi / n_azim), indexing="ij")
+    s = np.sqrt(1.0 - M * M)
+    om = np.stack([(s * np.cos(P)).ravel(), (s * np.sin(P)).ravel(), M.ravel()], axis=1)
+    return om, (W[0] * W[1]).ravel()
