@@ -1,0 +1,321 @@
+"""Benchmark: DVM cell-velocity updates/s of the GSIS kinetic step on one GB300.
+
+A step is one outer iteration through the library's C ABI (gsis_step_async): per-cell
+reference-distribution coefficients, wall densities, the implicit second-order
+finite-volume sweep of the four gas planes and of the photon intensities with block
+Gauss-Seidel point relaxation, the velocity moments, the FP64 macroscopic fields and
+the convergence measure.  Workload: 2-D heated lid-driven cavity, 20 000 seeded
+triangles, 28 x 28 closed Newton-Cotes (trapezoid) velocity grid, 64 photon directions, FP32 f and I.
+
+``value``  device-timed, distributions resident in HBM (both f buffers exceed L2).
+``e2e``    same metric through the C ABI with host buffers: every step uploads f and I
+           from pinned host memory, iterates, and reads the fields back.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (the only other place this script runs the oracle).
+
+With ``--gpus N`` (torchrun, one rank per GPU) every rank runs its own replica; the
+timing is the maximum over ranks and value is the sum of all ranks' updates.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DVM cell-velocity updates/s"
+UNIT = "updates/s"
+
+
+def workload(args):
+    import gsis_inputs as gi
+    wl = gi.workloads.cavity(n_side=100, Kn=args.kn, Kn_p=args.kn_p)
+    return gi.workloads.with_solver(wl, precision=args.precision, order=args.order, relax_block=args.block)
+
+
+def config(args, wl):
+    return {"workload": "cavity 2-D, %d triangles, 28x28 closed Newton-Cotes (trapezoid) velocities (%d), %d photon directions"
+                        % (wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]),
+            "n_cells": wl.mesh.n_cells, "n_xi": int(wl.xi.shape[0]), "n_omega": int(wl.omega.shape[0]),
+            "order": args.order, "relax_block": args.block, "Kn": args.kn, "Kn_photon": args.kn_p,
+            "step": "one CIS outer iteration (kinetic sweep + moments + fields + epsilon)",
+            "l2": "inputs larger than L2 (f: 2 x %.0f MB)" % (wl.mesh.n_cells * 896 * 16 / 1e6),
+            "parallelism": "replicas" if args.gpus > 1 else "1 GPU"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 8 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 8 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples if len(s) > 8 for k in range(4)
+                          if s[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def create_ctx(wl, stream):
+    from paper_2601_03935_gb300 import gsis as G
+    m = wl.mesh
+    return G.gsis_create(m.dim, m.face_owner, m.face_nbr, m.face_normal, m.face_area, m.face_centroid,
+                         m.cell_volume, m.cell_centroid, m.patches, wl.xi, wl.w, wl.omega, wl.wo, wl.model,
+                         wl.solver, stream)
+
+
+def initial_state(wl):
+    """Uniform gas at rest, rho = T = 1 (the paper's cases start from a uniform state)."""
+    import gsis_inputs as gi
+    M = gi.fields.uniform_fields(wl.mesh.n_cells, rho=1.0, T=1.0)
+    return gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 2, wl.model.d_r, wl.model.d_v, wl.model.sigma_R,
+                                       seed=1, noise=0.0)
+
+
+def cpu_baseline(wl, seconds=12.0):
+    """FP64 oracle sweep of whole relaxation blocks, as many as fit in ~``seconds``."""
+    from oracle import kinetic as K
+    f, I = initial_state(wl)
+    geo = K.Geometry(wl.mesh)
+    B = wl.solver.relax_block
+    n_blocks = (wl.mesh.n_cells + B - 1) // B
+    rng = np.random.default_rng(5)
+    done_cells, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        b = int(rng.integers(n_blocks))
+        cells = np.arange(b * B, min(b * B + B, wl.mesh.n_cells))
+        K.kinetic_sweep(f, I, wl, geo=geo, cells=cells, relax_block=B)
+        done_cells += len(cells)
+    dt = time.perf_counter() - t0
+    return {"value": done_cells * wl.xi.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d cells (%d random whole relaxation blocks of %d) x %d velocities, FP64 NumPy, "
+                      "one thread, %.1f s" % (done_cells, done_cells // B, B, wl.xi.shape[0], dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = workload(args)
+    from oracle import kinetic as K
+    f, I = initial_state(wl)
+    geo = K.Geometry(wl.mesh)
+    B = wl.solver.relax_block
+    n_blocks = (wl.mesh.n_cells + B - 1) // B
+    rng = np.random.default_rng(7)
+
+    def step():
+        b = int(rng.integers(n_blocks))
+        cells = np.arange(b * B, min(b * B + B, wl.mesh.n_cells))
+        K.kinetic_sweep(f, I, wl, geo=geo, cells=cells, relax_block=B)
+        return len(cells)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    cells = sum(step() for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    value = cells * wl.xi.shape[0] / dt
+    sample = "%d steps x one random relaxation block of %d cells x %d velocities (FP64 NumPy oracle, one thread)" % (
+        args.steps, B, wl.xi.shape[0])
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_2601_03935_gb300 import build
+    from paper_2601_03935_gb300 import gsis as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    G.load()
+    wl = workload(args)
+    nc, V, NO = wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]
+    stream = torch.cuda.Stream()
+    ctx = create_ctx(wl, stream.cuda_stream)
+    f, I = initial_state(wl)
+    G.gsis_set_distributions(ctx, f, I)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident throughput
+    for _ in range(args.warmup):
+        G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+    G.gsis_last_eps(ctx)
+    G.gsis_profile_enable(ctx, True)
+    G.gsis_profile_reset(ctx)
+    launches0 = G.gsis_launch_count(ctx)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = G.gsis_launch_count(ctx) - launches0
+    prof = G.gsis_profile_read(ctx)
+    G.gsis_profile_enable(ctx, False)
+    eps = G.gsis_last_eps(ctx)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- end to end through the C ABI with host buffers
+    f32 = np.float32 if args.precision == "fp32" else np.float64
+    hf = torch.from_numpy(f.astype(f32)).pin_memory()
+    hI = torch.from_numpy(I.astype(f32)).pin_memory()
+    hout = torch.empty((nc, G.GSIS_NF), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+
+    def e2e_step():
+        G.gsis_upload_distributions(ctx, hf.data_ptr(), hI.data_ptr())
+        G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+        G.gsis_download_fields_async(ctx, hout.data_ptr(), nc)
+        stream.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    G.gsis_destroy(ctx)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    sweep_ms, sweep_n = prof["sweep_gas"]
+    avg_sweep = sweep_ms / max(sweep_n, 1)
+    rs = 4 if args.precision == "fp32" else 8
+    alg_bytes = nc * V * 4 * rs * 2                     # read and write the four planes once
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (avg_sweep * 1e-3) / 1e9
+    value = world * nc * V / (ms * 1e-3)
+    kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
+                   "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)} for k, v in prof.items() if v[1]}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded cavity mesh and near-equilibrium distributions)",
+        "config": config(args, wl),
+        "roofline": {"kernel": "sweep_gas", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": avg_sweep},
+        "e2e": {"value": world * nc * V / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": nc * (V * 4 + NO) * rs, "d2h_bytes_per_step": nc * G.GSIS_NF * 8},
+        "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "last_eps": eps,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--kn", type=float, default=0.01)
+    ap.add_argument("--kn-p", type=float, default=10.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

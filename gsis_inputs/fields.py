@@ -28,6 +28,32 @@ def random_macro_fields(n_cells: int, dim: int, seed: int, u_scale: float = 1.0,
     return M
 
 
+def smooth_random_fields(x, seed: int, u_scale: float = 0.3, q_scale: float = 0.05) -> np.ndarray:
+    """Per-cell states from a few seeded low-wavenumber Fourier modes of the cell
+    centroids x [n, dim]: rho in [0.6, 1.4], temperatures in [0.8, 2.2], |u| <= u_scale,
+    heat fluxes up to q_scale rho T^1.5."""
+    rng = np.random.default_rng(seed)
+    n, dim = x.shape
+
+    def field():
+        acc = np.zeros(n)
+        for _ in range(3):
+            k = rng.uniform(-2.0 * np.pi, 2.0 * np.pi, dim)
+            acc += np.sin(x @ k + rng.uniform(0.0, 2.0 * np.pi)) / 3.0
+        return acc                                    # in [-1, 1]
+
+    M = np.zeros((n, NF))
+    M[:, RHO] = 1.0 + 0.4 * field()
+    for a in range(dim):
+        M[:, UX + a] = u_scale * field()
+    for k in (TT, TR, TV, TRAD):
+        M[:, k] = 1.5 + 0.7 * field()
+    for base, T in ((QT, TT), (QR, TR), (QV, TV), (QRAD, TRAD)):
+        for a in range(dim):
+            M[:, base + a] = q_scale * M[:, RHO] * M[:, T] ** 1.5 * field()
+    return M
+
+
 def uniform_fields(n_cells: int, rho=1.0, u=(0.0, 0.0, 0.0), T=1.0, T_R=None) -> np.ndarray:
     M = np.zeros((n_cells, NF))
     M[:, RHO] = rho

@@ -106,8 +106,9 @@ def cavity_triangles(n_side: int, seed: int = 0, jitter: float = 0.2, flip_p: fl
     """Jittered, randomly split triangulation of the unit square: 2*n_side^2 cells.
 
     Interior vertices move by up to ``jitter*h`` in each direction, each square
-    is cut along a randomly chosen diagonal, cells come square by square in
-    row-major order.  Patches: 0 bottom, 1 right, 2 top (lid), 3 left.
+    is cut along a randomly chosen diagonal.  Cells are numbered square by square
+    along a Z-order (Morton) curve, so that any run of consecutive cells is a
+    compact patch.  Patches: 0 bottom, 1 right, 2 top (lid), 3 left.
     """
     rng = np.random.default_rng(seed)
     h = 1.0 / n_side
@@ -117,15 +118,22 @@ def cavity_triangles(n_side: int, seed: int = 0, jitter: float = 0.2, flip_p: fl
     inner = (verts[:, 0] > 0) & (verts[:, 0] < 1) & (verts[:, 1] > 0) & (verts[:, 1] < 1)
     verts[inner] += rng.uniform(-jitter * h, jitter * h, size=(int(inner.sum()), 2))
     diag = rng.random(n_side * n_side) < flip_p
+
+    def morton(i, j):
+        code = 0
+        for b in range(16):
+            code |= ((i >> b) & 1) << (2 * b) | ((j >> b) & 1) << (2 * b + 1)
+        return code
+
+    squares = sorted(((i, j) for j in range(n_side) for i in range(n_side)), key=lambda t: morton(*t))
     tris = []
-    for j in range(n_side):
-        for i in range(n_side):
-            a = j * (n_side + 1) + i
-            b, c, d = a + 1, a + n_side + 2, a + n_side + 1
-            if diag[j * n_side + i]:
-                tris += [(a, b, c), (a, c, d)]
-            else:
-                tris += [(a, b, d), (b, c, d)]
+    for i, j in squares:
+        a = j * (n_side + 1) + i
+        b, c, d = a + 1, a + n_side + 2, a + n_side + 1
+        if diag[j * n_side + i]:
+            tris += [(a, b, c), (a, c, d)]
+        else:
+            tris += [(a, b, d), (b, c, d)]
     tris = np.asarray(tris, np.int64)
 
     def side(p, q):

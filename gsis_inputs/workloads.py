@@ -33,6 +33,7 @@ class ModelParams:
 class SolverParams:
     precision: str = "fp32"              # "fp32" or "fp64" storage/arithmetic of f and I
     order: int = 2                       # 1 = first-order upwind, 2 = limited linear reconstruction
+    relax_block: int = 16                # Gauss-Seidel block of consecutive cells (1 = Jacobi)
     cfl_meso: float = 1e5
     cfl_macro: float = 1e3
     venkat_K: float = 5.0
@@ -73,14 +74,18 @@ def slab(n_cells: int = 64, n_xi: int = 32, n_mu: int = 16, Kn: float = 0.1,
 
 
 def cavity(n_side: int = 100, n_v: int = 28, n_polar: int = 8, n_azim: int = 8, Kn: float = 0.1,
-           Kn_p: float = 1.0, sigma_R: float = 0.005, u_lid: float = 0.18, T_lid: float = 3.0,
-           seed: int = 0) -> Workload:
-    """2-D lid-driven, heated cavity on a seeded triangle mesh (2*n_side^2 cells)."""
+           Kn_p: float = 10.0, sigma_R: float = 0.005, u_lid: float = 0.18, T_lid: float = 3.0,
+           seed: int = 0, rule: str = "trapezoid") -> Workload:
+    """2-D lid-driven, heated cavity on a seeded triangle mesh (2*n_side^2 cells).
+
+    The n_v x n_v uniform velocity grid spans +-(|u_lid| + 5 sqrt(T_lid)) with the
+    composite closed Newton-Cotes rule of degree one (trapezoid) by default; "nc38"
+    selects the composite 3/8 rule."""
     m = _mesh.cavity_triangles(n_side, seed=seed, patches=[
         _mesh.Patch(_mesh.WALL, T_t=1.0), _mesh.Patch(_mesh.WALL, T_t=1.0),
         _mesh.Patch(_mesh.WALL, u=(u_lid, 0.0, 0.0), T_t=T_lid), _mesh.Patch(_mesh.WALL, T_t=1.0)])
     L = abs(u_lid) + 5.0 * np.sqrt(max(T_lid, 1.0))
-    xi, w = _q.newton_cotes_2d(n_v, L)
+    xi, w = _q.trapezoid_nd(n_v, L, 2) if rule == "trapezoid" else _q.newton_cotes_2d(n_v, L)
     om, wo = _q.photon_product(n_polar, n_azim)
     return Workload("cavity%d" % (2 * n_side * n_side), m, xi, w, om, wo,
                     ModelParams(Kn=Kn, Kn_p=Kn_p, sigma_R=sigma_R))

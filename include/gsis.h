@@ -1,0 +1,210 @@
+/*
+ * gsis.h -- C ABI of the GB300 library for the general synthetic iterative scheme
+ * (GSIS) of "Accelerated simulation of multiscale gas-radiation coupling flows via a
+ * general synthetic iterative scheme".
+ *
+ * The library solves the steady kinetic model of Section 2.1 (Eq. kinetic_equation:
+ * three reduced gas distributions f0, f1, f2 and the gray radiative intensity I_R)
+ * with the unstructured finite-volume discrete velocity method of Section 5
+ * (Eq. dis_micro).  A problem is stated the way the paper states it: a mesh, a
+ * discrete velocity grid, a photon direction grid and the model parameters go in;
+ * macroscopic fields (Eq. getmoment) come out.
+ *
+ * Conventions
+ *  - Every entry point returns int: GSIS_OK (0) or a negative GSIS_ERR_* code.  No
+ *    C++ exception, abort or exit crosses this boundary.  gsis_strerror() names a
+ *    code; gsis_last_error() gives the context's last detailed message.
+ *  - All pointers passed in are HOST pointers owned by the caller.  gsis_create()
+ *    copies everything it needs; the caller may free its arrays afterwards.  The
+ *    library owns every byte of device memory it uses.
+ *  - Output buffers are caller-owned host memory; their length (in elements) is
+ *    passed and checked, GSIS_ERR_INVALID_ARG if too short.
+ *  - One context belongs to one host thread at a time.  All device work of a
+ *    context is issued on the CUDA stream given at creation (NULL: the legacy
+ *    default stream); calls that return host data synchronise that stream.
+ *  - Doubles at the boundary whatever the internal precision.
+ *
+ * Reduced velocity spaces: with dim in-plane velocity components (dim = spatial
+ * dimension) and m = 3 - dim hidden ones, the gas state is four planes per cell and
+ * discrete velocity, in the order
+ *      [F0, H0, f1, f2],  F0 = int f0 dxi_hidden,  H0 = int |xi_hidden|^2 f0 dxi_hidden,
+ * f1, f2 integrated over xi_hidden.  In 3-D the H0 plane is unused (zero).
+ */
+#ifndef GSIS_H
+#define GSIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define GSIS_OK                 0
+#define GSIS_ERR_INVALID_ARG   -1   /* bad pointer, size, parameter or buffer length   */
+#define GSIS_ERR_OUT_OF_MEMORY -2   /* device or host allocation failed                 */
+#define GSIS_ERR_CUDA          -3   /* a CUDA runtime call failed (see gsis_last_error) */
+#define GSIS_ERR_DIVERGED      -4   /* NaN/Inf or a negative density/temperature        */
+#define GSIS_ERR_NOT_CONVERGED -5   /* gsis_solve hit max_outer before tol_outer        */
+#define GSIS_ERR_TIMEOUT       -6   /* a bounded device wait ran out                    */
+#define GSIS_ERR_BAD_MESH      -7   /* inconsistent connectivity or geometry            */
+#define GSIS_ERR_UNSUPPORTED   -8   /* valid request that this build does not implement */
+
+/* ---- per-cell field record (doubles), used by gsis_init_fields / get_fields --
+ *  0 rho | 1..3 u | 4 T_t | 5 T_r | 6 T_v | 7 T_R | 8..10 q_t | 11..13 q_r |
+ *  14..16 q_v | 17..19 q_R | 20..25 sigma (xx, yy, zz, xy, xz, yz)            */
+#define GSIS_NF 26
+
+/* ---- boundary patches ------------------------------------------------------ */
+#define GSIS_PATCH_WALL     0  /* gas: diffuse, fully accommodating at (T_t, u);
+                                  photons: black at T_t                           */
+#define GSIS_PATCH_FARFIELD 1  /* incoming: equilibrium of (rho, u, T_t, T_r, T_v, T_R) */
+
+typedef struct {
+    int32_t kind;               /* GSIS_PATCH_*                                    */
+    double rho;                 /* far field only                                  */
+    double u[3];                /* wall velocity or far-field velocity             */
+    double T_t, T_r, T_v, T_R;  /* wall temperature is T_t                         */
+} gsis_patch;
+
+/* Unstructured finite-volume mesh (Section 5): faces with owner and neighbour.
+ * face_nbr[f] >= 0 is the neighbour cell; face_nbr[f] = -1 - p marks a boundary face
+ * of patch p.  face_normal is the unit normal from owner to neighbour (outward on the
+ * boundary), [n_faces][dim] row-major.  Areas are lengths in 2-D and 1 in 1-D.
+ * Cells are relaxed in blocks of consecutive indices: number them with locality. */
+typedef struct {
+    int32_t dim;                      /* 1 or 2 in this build (3: GSIS_ERR_UNSUPPORTED) */
+    int64_t n_cells, n_faces;
+    const int32_t *face_owner;        /* [n_faces]            */
+    const int32_t *face_nbr;          /* [n_faces]            */
+    const double *face_normal;        /* [n_faces][dim]       */
+    const double *face_area;          /* [n_faces]            */
+    const double *face_centroid;      /* [n_faces][dim]       */
+    const double *cell_volume;        /* [n_cells]            */
+    const double *cell_centroid;      /* [n_cells][dim]       */
+    int32_t n_patches;
+    const gsis_patch *patches;        /* [n_patches]          */
+} gsis_mesh;
+
+/* Discrete velocities xi [n][dim] and weights w [n]: sum_i w_i phi(xi_i) approximates
+ * the integral over the reduced velocity space (Section 6 uses uniform grids). */
+typedef struct { int32_t n; const double *xi; const double *w; } gsis_velocity_quad;
+
+/* Photon directions omega [n][3] (unit vectors) and weights w [n], sum w = 4 pi.
+ * Transport uses the first dim components of omega. */
+typedef struct { int32_t n; const double *omega; const double *w; } gsis_photon_quad;
+
+/* Model parameters of Section 2.1. */
+typedef struct {
+    double d_r, d_v;            /* rotational / vibrational degrees of freedom (d_v constant) */
+    double Z_r, Z_v;            /* collision numbers                                          */
+    double omega;               /* viscosity index: tau = sqrt(2/pi) T_t^(omega-1) Kn / rho   */
+    double Sc;                  /* Schmidt number in the Mason-Monchick matrix A              */
+    double Kn, Kn_p;            /* gas and photon Knudsen numbers                             */
+    double sigma_R;             /* dimensionless Stefan-Boltzmann constant                    */
+    int32_t k_eff_density_scaled; /* 0: k_eff = 1/Kn_p; 1: k_eff = rho/Kn_p                  */
+    const double *A;            /* 3x3 row-major relaxation-rate matrix, or NULL for the
+                                   Mason-Monchick form of Section 2.1                         */
+} gsis_model_params;
+
+#define GSIS_FP32 0             /* f and I stored and updated in FP32 */
+#define GSIS_FP64 1             /* plain FP64 everywhere              */
+
+/* Solver parameters (Section 5 and Section 6). */
+typedef struct {
+    int32_t precision;          /* GSIS_FP32 or GSIS_FP64                                   */
+    int32_t order;              /* 1: first-order upwind residual; 2: Venkatakrishnan-limited
+                                   linear reconstruction (Eq. deltaflux_micro)               */
+    int32_t relax_block;        /* point relaxation: forward + backward Gauss-Seidel inside
+                                   blocks of this many consecutive cells (1..64)            */
+    double cfl_meso, cfl_macro; /* pseudo time step dt = CFL dx / (|u| + c_s)              */
+    double venkat_K;            /* limiter constant, eps^2 = (K dx)^3                       */
+    int32_t n_cis_precond;      /* CIS iterations before GSIS starts                        */
+    int32_t max_outer, max_inner, macro_sweeps;
+    double tol_outer, tol_inner;
+} gsis_solver_params;
+
+typedef struct gsis_ctx gsis_ctx;
+
+/* Create a solver context: validates and copies the problem, builds the device
+ * geometry, allocates the distribution planes (two copies of [n_cells][V][4] and of
+ * [n_cells][n_omega] in the chosen precision) and sets f to the equilibrium of a
+ * uniform unit state.  cuda_stream is a cudaStream_t (may be NULL).
+ * Errors: INVALID_ARG, BAD_MESH, UNSUPPORTED, OUT_OF_MEMORY, CUDA. */
+int gsis_create(const gsis_mesh *mesh, const gsis_velocity_quad *vq, const gsis_photon_quad *pq,
+                const gsis_model_params *model, const gsis_solver_params *solver,
+                void *cuda_stream, gsis_ctx **out);
+
+/* Release every resource of the context (NULL is a no-op). */
+void gsis_destroy(gsis_ctx *ctx);
+
+/* Static description of a status code; never NULL. */
+const char *gsis_strerror(int code);
+
+/* Last detailed error message of the context ("" if none); valid until the next call. */
+const char *gsis_last_error(const gsis_ctx *ctx);
+
+/* Set f to the multi-temperature local equilibrium of per-cell states
+ * M [n_cells][GSIS_NF] (rho, u, T_t, T_r, T_v, T_R used; the moments of Eq. getmoment):
+ * F0 = rho f_eq(T_t), H0 = m T_t F0, f1 = (d_r/2) T_r F0, f2 = (d_v/2) T_v F0,
+ * I = sigma_R T_R^4 / pi.  Then the macroscopic fields are taken from the new f. */
+int gsis_init_fields(gsis_ctx *ctx, const double *M, int64_t len);
+
+/* Set the distributions from host FP64 arrays f [n_cells][n_xi][4] and I [n_cells][n_omega]
+ * (rounded to the storage precision), then take the macroscopic fields from them. */
+int gsis_set_distributions(gsis_ctx *ctx, const double *f, int64_t f_len, const double *I, int64_t I_len);
+
+/* Copy the current distributions to host FP64 arrays of the same layout. */
+int gsis_get_distributions(gsis_ctx *ctx, double *f, int64_t f_len, double *I, int64_t I_len);
+
+/* Same as gsis_set_distributions but from host buffers already in the storage
+ * precision (float for GSIS_FP32, double for GSIS_FP64), layout [n_cells][n_xi][4] and
+ * [n_cells][n_omega].  Pinned buffers make the copies asynchronous on the context
+ * stream; the call returns without synchronising. */
+int gsis_upload_distributions(gsis_ctx *ctx, const void *f, const void *I);
+
+/* Macroscopic fields of the current distributions, [n_cells][GSIS_NF] doubles. */
+int gsis_get_fields(gsis_ctx *ctx, double *out, int64_t len);
+
+/* Same, asynchronously into a caller buffer (pinned for true asynchrony) on the
+ * context stream; the caller synchronises the stream before reading it. */
+int gsis_download_fields_async(gsis_ctx *ctx, double *out, int64_t len);
+
+#define GSIS_MODE_CIS  0        /* conventional iteration: one kinetic step                */
+#define GSIS_MODE_GSIS 1        /* kinetic step + synthetic equations + synchronisation    */
+
+/* One outer iteration from the current distributions f^k (Section 3):
+ * CIS:  moments M^k -> reference distributions -> one implicit sweep (Eq. dis_micro)
+ *       for gas and photons -> f^{k+1} and M^{k+1}.
+ * *eps_out (may be NULL) receives the convergence measure of Section 6 between M^k
+ * and M^{k+1}.  This call synchronises the stream to read eps.
+ * Errors: DIVERGED (non-finite or non-positive density/temperature), CUDA, UNSUPPORTED. */
+int gsis_step(gsis_ctx *ctx, int32_t mode, double *eps_out);
+
+/* Same iteration without reading eps back: the device work is queued on the context
+ * stream and the call returns at once.  gsis_last_eps() synchronises and returns the
+ * measure of the most recent iteration. */
+int gsis_step_async(gsis_ctx *ctx, int32_t mode);
+int gsis_last_eps(gsis_ctx *ctx, double *eps_out);
+
+/* Kernel timing.  While enabled, the library brackets each of its kernel launches with
+ * CUDA events on the context stream and accumulates device time per kernel id.
+ * gsis_profile_read fills up to n entries of names/ms/launches (arrays of length n)
+ * and sets *n_out to the number of kernel ids. */
+int gsis_profile_enable(gsis_ctx *ctx, int32_t on);
+int gsis_profile_reset(gsis_ctx *ctx);
+int gsis_profile_read(gsis_ctx *ctx, int32_t n, const char **names, double *ms, int64_t *launches,
+                      int32_t *n_out);
+
+/* Total number of kernels the context has launched since creation. */
+int64_t gsis_launch_count(const gsis_ctx *ctx);
+
+/* Sizes chosen by the library: padded velocity count, padded photon count, number of
+ * velocity chunks per cell and the relaxation block size actually used. */
+int gsis_get_layout(const gsis_ctx *ctx, int32_t *v_pad, int32_t *o_pad, int32_t *n_chunks,
+                    int32_t *block);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSIS_H */

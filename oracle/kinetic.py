@@ -183,21 +183,33 @@ class Geometry:
         self.vol = mesh.cell_volume.astype(np.float64)
         self.xc = mesh.cell_centroid[:, :dim].astype(np.float64)
         self.dx = self.vol ** (1.0 / dim)
-        # Least squares: grad_i = sum_j C_ij (phi_j - phi_i) over interior neighbours,
-        # C_ij = (sum_k d_k d_k^T)^-1 d_j, d_j = x_j - x_i; zero gradient if fewer
-        # interior neighbours than dimensions.
+        # Least squares: grad_i = sum_j C_ij (phi_j - phi_i) over the stencil of cell i,
+        # C_ij = (sum_k d_k d_k^T)^-1 d_j, d_j = x_j - x_i.  The stencil is the face
+        # neighbours and their face neighbours: with face neighbours alone, the
+        # second-order upwind residual on triangles is not contracted by a first-order
+        # implicit operator (some eigenvalues of A1^-1 A2 have negative real part).
+        # A zero gradient is used where the normal matrix is singular.
+        self.face_nbrs = [[fc[0] for fc in self.cell_faces[i] if fc[0] >= 0] for i in range(self.nc)]
         self.lsq = []
         for i in range(self.nc):
-            nbrs = [fc[0] for fc in self.cell_faces[i] if fc[0] >= 0]
-            if len(nbrs) < dim:
-                self.lsq.append((nbrs, np.zeros((len(nbrs), dim))))
+            st = set(self.face_nbrs[i])
+            for j in self.face_nbrs[i]:
+                st.update(self.face_nbrs[j])
+            st.discard(i)
+            st = sorted(st)
+            if len(st) < dim:
+                self.lsq.append((st, np.zeros((len(st), dim))))
                 continue
-            D = self.xc[nbrs] - self.xc[i]
+            D = self.xc[st] - self.xc[i]
             G = D.T @ D
-            self.lsq.append((nbrs, D @ np.linalg.inv(G).T))
+            scale = np.trace(G) / dim
+            if np.linalg.det(G) <= 1e-10 * scale ** dim:
+                self.lsq.append((st, np.zeros((len(st), dim))))
+                continue
+            self.lsq.append((st, D @ np.linalg.inv(G).T))
 
     def interior_neighbours(self, i):
-        return self.lsq[i][0]
+        return self.face_nbrs[i]
 
 
 def venkatakrishnan(d1, d2, eps2):
@@ -207,16 +219,19 @@ def venkatakrishnan(d1, d2, eps2):
 
 def limited_slope(geo, i, q, K):
     """Venkatakrishnan-limited least-squares gradient of the cell values q[i] ([..]-shaped
-    per cell).  Returns (grad [dim, ...], phi [...])."""
-    nbrs, C = geo.lsq[i]
+    per cell).  The bounds Delta_max, Delta_min come from the face neighbours.
+    Returns (grad [dim, ...], phi [...])."""
+    stencil, C = geo.lsq[i]
     qi = q[i]
     grad = np.zeros((geo.dim,) + qi.shape)
+    for k, j in enumerate(stencil):
+        dq = q[j] - qi
+        for a in range(geo.dim):
+            grad[a] = grad[a] + C[k, a] * dq
+    nbrs = geo.face_nbrs[i]
     if len(nbrs) == 0:
         return grad, np.ones(qi.shape)
     dq = np.stack([q[j] - qi for j in nbrs])                      # [k, ...]
-    for k in range(len(nbrs)):
-        for a in range(geo.dim):
-            grad[a] = grad[a] + C[k, a] * dq[k]
     dmax = np.maximum(dq.max(axis=0), 0.0)
     dmin = np.minimum(dq.min(axis=0), 0.0)
     eps2 = (K * geo.dx[i]) ** 3
@@ -280,7 +295,42 @@ def relaxation_source(Fc, f, I, wl):
 
 
 # --------------------------------------------------------------------------- sweep
-def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
+def _relax_downwind(cells, res, dg, offdiag, geo, dirs, B, nc, which):
+    """Forward/backward Gauss-Seidel inside each block of B consecutive cells, with
+    the cells of a block visited, for each discrete velocity (or photon direction)
+    separately, in increasing order of (direction . centroid): the forward pass then
+    meets the upwind neighbours first.  Ties are broken by the cell index."""
+    pos = {int(c): k for k, c in enumerate(cells)}
+    out = np.zeros_like(res)
+    nv = res.shape[1]
+    for b in sorted(set(int(c) // B for c in cells)):
+        members = list(range(b * B, min((b + 1) * B, nc)))
+        proj = geo.xc[members] @ dirs.T                            # [m, nv]
+        order = np.lexsort((np.repeat(np.arange(len(members))[:, None], nv, 1), proj), axis=0)
+        rank = np.empty_like(order)
+        for v in range(nv):
+            rank[order[:, v], v] = np.arange(len(members))
+        local = {c: m for m, c in enumerate(members)}
+        for sweep in (0, 1):
+            seq = range(len(members)) if sweep == 0 else range(len(members) - 1, -1, -1)
+            for t in seq:
+                for v in range(nv):
+                    m = order[t, v]
+                    k = pos[members[m]]
+                    acc = res[k, v].copy() if sweep == 0 else out[k, v].copy()
+                    for j, a, aR in offdiag[k]:
+                        if j in local:
+                            rj = rank[local[j], v]
+                            coef = (a if which == 0 else aR)[v]
+                            if sweep == 0 and rj < t:
+                                acc -= coef * out[pos[j], v]
+                            elif sweep == 1 and rj > t:
+                                acc -= coef * out[pos[j], v] / dg[k, v]
+                    out[k, v] = acc / dg[k, v] if sweep == 0 else acc
+    return out
+
+
+def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None, ordering="natural"):
     """One implicit kinetic step (Eq. dis_micro) for the gas planes and photons.
 
     For every cell i and discrete velocity (photon direction):
@@ -300,8 +350,12 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
     geo = geo or Geometry(mesh)
     nc = mesh.n_cells
     cells = np.arange(nc) if cells is None else np.asarray(cells)
-    if relax_block != 1 and len(cells) != nc:
-        raise ValueError("block relaxation needs every cell")
+    if relax_block != 1:
+        blocks = sorted(set(int(c) // relax_block for c in cells))
+        want = np.concatenate([np.arange(b * relax_block, min((b + 1) * relax_block, nc)) for b in blocks])
+        if len(want) != len(cells) or np.any(np.sort(cells) != want):
+            raise ValueError("block relaxation needs whole blocks of consecutive cells")
+        cells = want
     order, K = solver.order, solver.venkat_K
 
     # cells whose moments are needed: targets and their neighbours (the neighbours'
@@ -363,21 +417,27 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
     if relax_block == 1:
         df = res / dg[..., None]
         dI = resR / dR
-    else:
+    elif ordering == "natural":
+        pos = {int(c): k for k, c in enumerate(cells)}
         df = np.zeros_like(res)
         dI = np.zeros_like(resR)
-        for b0 in range(0, nc, relax_block):
-            b1 = min(b0 + relax_block, nc)
+        for b in sorted(set(int(c) // relax_block for c in cells)):
+            b0, b1 = b * relax_block, min((b + 1) * relax_block, nc)
             for i in range(b0, b1):                               # forward
-                acc, accR = res[i].copy(), resR[i].copy()
-                for j, a, aR in offdiag[i]:
+                k = pos[i]
+                acc, accR = res[k].copy(), resR[k].copy()
+                for j, a, aR in offdiag[k]:
                     if b0 <= j < i:
-                        acc -= a[:, None] * df[j]
-                        accR -= aR * dI[j]
-                df[i], dI[i] = acc / dg[i][:, None], accR / dR[i]
+                        acc -= a[:, None] * df[pos[j]]
+                        accR -= aR * dI[pos[j]]
+                df[k], dI[k] = acc / dg[k][:, None], accR / dR[k]
             for i in range(b1 - 1, b0 - 1, -1):                   # backward
-                for j, a, aR in offdiag[i]:
+                k = pos[i]
+                for j, a, aR in offdiag[k]:
                     if i < j < b1:
-                        df[i] -= a[:, None] * df[j] / dg[i][:, None]
-                        dI[i] -= aR * dI[j] / dR[i]
+                        df[k] -= a[:, None] * df[pos[j]] / dg[k][:, None]
+                        dI[k] -= aR * dI[pos[j]] / dR[k]
+    else:
+        df = _relax_downwind(cells, res, dg, offdiag, geo, xi[:, :dim], relax_block, nc, 0)
+        dI = _relax_downwind(cells, resR[..., None], dR, offdiag, geo, om[:, :dim], relax_block, nc, 1)[..., 0]
     return f[cells] + df, I[cells] + dI

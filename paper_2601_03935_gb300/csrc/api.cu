@@ -1,0 +1,787 @@
+// Host side of the GSIS C ABI: validation, geometry preprocessing, device buffers and
+// the orchestration of one outer iteration (Section 3) on the context stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gsis.h"
+#include "gsis_impl.cuh"
+
+using namespace gsis;
+
+namespace {
+
+enum KernelId { K_COEF, K_WALL, K_SWEEP_GAS, K_SWEEP_PHOTON, K_FINISH, K_EPS, K_EQUIL, K_MOMENTS, K_COUNT };
+const char *kKernelNames[K_COUNT] = {"coefficients", "wall_density", "sweep_gas", "sweep_photon",
+                                     "finish",       "eps_reduce",   "equilibrium", "moments_only"};
+
+}  // namespace
+
+struct gsis_ctx {
+    int dim = 0, precision = 0, order = 2, block = 16;
+    int64_t nc = 0;
+    int V = 0, Vp = 0, NO = 0, Op = 0, nch = 0, och = 0, n_bf = 0;
+    size_t real_size = 4;
+    cudaStream_t stream = nullptr;
+    ModelDev model{};
+    gsis_solver_params solver{};
+
+    // device buffers; Real-typed ones are void* and cast by precision
+    void *f[2] = {nullptr, nullptr}, *I[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *coef = nullptr, *bcoef = nullptr, *partial = nullptr, *opartial = nullptr;
+    double *fields = nullptr, *fields_old = nullptr, *eps_terms = nullptr, *eps_sums = nullptr;
+    int *err = nullptr;
+    double *vol = nullptr, *cell_dx = nullptr;
+    int *g_nf = nullptr, *g_nbr = nullptr, *bf_cell = nullptr, *bf_patch = nullptr, *g_nst = nullptr,
+        *g_stn = nullptr;
+    signed char *g_local = nullptr;
+    void *g_nrm = nullptr, *g_sv = nullptr, *g_dxf = nullptr, *g_dxn = nullptr, *g_lsq = nullptr,
+         *g_eps2 = nullptr, *bf_nrm = nullptr;
+    void *vq_x = nullptr, *vq_w = nullptr, *oq_x = nullptr, *oq_w = nullptr;
+    double *patch_T = nullptr, *patch_u = nullptr;
+    int *patch_kind = nullptr;
+    double *h_pinned = nullptr;  // NEPS sums + error word
+
+    bool have_eps = false;
+    double last_eps = 0.0;
+    bool prof = false;
+    double prof_ms[K_COUNT] = {0};
+    int64_t prof_n[K_COUNT] = {0};
+    struct Pending { int id; cudaEvent_t e0, e1; };
+    std::vector<Pending> pending;          // recorded, not yet resolved
+    std::vector<cudaEvent_t> event_pool;   // free events
+    int64_t launches = 0;
+    std::vector<void *> allocations;
+    std::string last_error;
+};
+
+namespace {
+
+int fail(gsis_ctx *c, int code, const std::string &msg) {
+    if (c) c->last_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(c, expr)                                                                         \
+    do {                                                                                          \
+        cudaError_t _e = (expr);                                                                  \
+        if (_e != cudaSuccess)                                                                    \
+            return fail((c), GSIS_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+template <typename T>
+int dalloc(gsis_ctx *c, T **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+    if (e != cudaSuccess) return fail(c, GSIS_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->allocations.push_back(q);
+    *p = static_cast<T *>(q);
+    return GSIS_OK;
+}
+
+int dalloc_real(gsis_ctx *c, void **p, size_t n) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * c->real_size > 0 ? n * c->real_size : 16);
+    if (e != cudaSuccess) return fail(c, GSIS_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    c->allocations.push_back(q);
+    *p = q;
+    return GSIS_OK;
+}
+
+// upload a host double array as Real
+int upload_real(gsis_ctx *c, void *dst, const std::vector<double> &src) {
+    if (c->precision == GSIS_FP64) {
+        CUDA_TRY(c, cudaMemcpy(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> t(src.begin(), src.end());
+        CUDA_TRY(c, cudaMemcpy(dst, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return GSIS_OK;
+}
+
+template <typename T>
+int upload(gsis_ctx *c, T *dst, const std::vector<T> &src) {
+    CUDA_TRY(c, cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return GSIS_OK;
+}
+
+template <typename Real>
+Geom<Real> geom(const gsis_ctx *c) {
+    Geom<Real> g;
+    g.n_cells = (int)c->nc;
+    g.dim = c->dim;
+    g.block = c->block;
+    g.nf = c->g_nf;
+    g.nbr = c->g_nbr;
+    g.local = c->g_local;
+    g.nrm = (const Real *)c->g_nrm;
+    g.sv = (const Real *)c->g_sv;
+    g.dxf = (const Real *)c->g_dxf;
+    g.dxn = (const Real *)c->g_dxn;
+    g.nst = c->g_nst;
+    g.stn = c->g_stn;
+    g.lsq = (const Real *)c->g_lsq;
+    g.eps2 = (const Real *)c->g_eps2;
+    g.n_bf = c->n_bf;
+    g.bf_cell = c->bf_cell;
+    g.bf_patch = c->bf_patch;
+    g.bf_nrm = (const Real *)c->bf_nrm;
+    return g;
+}
+
+template <typename Real>
+Quad<Real> vquad(const gsis_ctx *c) {
+    return Quad<Real>{c->V, c->Vp, (const Real *)c->vq_x, (const Real *)c->vq_w};
+}
+template <typename Real>
+Quad<Real> oquad(const gsis_ctx *c) {
+    return Quad<Real>{c->NO, c->Op, (const Real *)c->oq_x, (const Real *)c->oq_w};
+}
+
+int take_event(gsis_ctx *c, cudaEvent_t *e) {
+    if (!c->event_pool.empty()) {
+        *e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return GSIS_OK;
+    }
+    CUDA_TRY(c, cudaEventCreate(e));
+    return GSIS_OK;
+}
+
+// Resolve recorded launch timings (synchronises on the last recorded event).
+int resolve_profile(gsis_ctx *c) {
+    for (auto &p : c->pending) {
+        CUDA_TRY(c, cudaEventSynchronize(p.e1));
+        float ms = 0.f;
+        CUDA_TRY(c, cudaEventElapsedTime(&ms, p.e0, p.e1));
+        c->prof_ms[p.id] += ms;
+        c->prof_n[p.id] += 1;
+        c->event_pool.push_back(p.e0);
+        c->event_pool.push_back(p.e1);
+    }
+    c->pending.clear();
+    return GSIS_OK;
+}
+
+// Launch bracket: counts launches and, when profiling, brackets the launch with two
+// events on the context stream (resolved later, so the stream never stalls).
+template <typename F>
+int launch(gsis_ctx *c, int id, F &&fn) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->prof) {
+        if (take_event(c, &e0) != GSIS_OK || take_event(c, &e1) != GSIS_OK) return GSIS_ERR_CUDA;
+        CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+    }
+    cudaError_t e = fn();
+    if (e != cudaSuccess)
+        return fail(c, GSIS_ERR_CUDA, std::string("launch of ") + kKernelNames[id] + ": " + cudaGetErrorString(e));
+    c->launches++;
+    if (c->prof) {
+        CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        c->pending.push_back({id, e0, e1});
+    }
+    return GSIS_OK;
+}
+
+#define TRY(expr)                 \
+    do {                          \
+        int _r = (expr);          \
+        if (_r != GSIS_OK) return _r; \
+    } while (0)
+
+// moments of the current distributions -> fields (FP64): a first pass about zero
+// velocity, a second about the velocity it found
+template <typename Real>
+int refresh_fields(gsis_ctx *c) {
+    const Geom<Real> g = geom<Real>(c);
+    CUDA_TRY(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    // the first pass takes moments about zero velocity, independent of earlier state
+    CUDA_TRY(c, cudaMemsetAsync(c->coef, 0, (size_t)c->nc * cf::NC * c->real_size, c->stream));
+    for (int pass = 0; pass < 2; ++pass) {
+        TRY(launch(c, K_MOMENTS, [&] {
+            return launch_moments_only<Real>(c->stream, c->dim, (int)c->nc, vquad<Real>(c), oquad<Real>(c),
+                                             (const Real *)c->coef, (const Real *)c->f[c->cur],
+                                             (const Real *)c->I[c->cur], (Real *)c->partial, (Real *)c->opartial);
+        }));
+        TRY(launch(c, K_FINISH, [&] {
+            return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
+                                       (const Real *)c->partial, (const Real *)c->opartial, c->vol, nullptr,
+                                       c->fields, c->eps_terms, c->err, 0);
+        }));
+        TRY(launch(c, K_COEF, [&] {
+            return launch_coefficients<Real>(c->stream, c->dim, g, c->model, c->fields, c->cell_dx, (Real *)c->coef);
+        }));
+    }
+    c->have_eps = false;
+    return GSIS_OK;
+}
+
+int refresh(gsis_ctx *c) { return c->precision == GSIS_FP64 ? refresh_fields<double>(c) : refresh_fields<float>(c); }
+
+// One CIS iteration: coefficients are current (built from the fields of f^k).
+template <typename Real>
+int cis_iteration(gsis_ctx *c) {
+    const Geom<Real> g = geom<Real>(c);
+    const int nxt = 1 - c->cur;
+    CUDA_TRY(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    TRY(launch(c, K_WALL, [&] {
+        return launch_wall_density<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_T, c->patch_u, c->patch_kind,
+                                         (const Real *)c->f[c->cur], (Real *)c->bcoef);
+    }));
+    TRY(launch(c, K_SWEEP_GAS, [&] {
+        return launch_sweep_gas<Real>(c->stream, c->dim, c->order, g, vquad<Real>(c), (const Real *)c->coef,
+                                      (const Real *)c->bcoef, (const Real *)c->f[c->cur], (Real *)c->f[nxt],
+                                      (Real *)c->partial);
+    }));
+    TRY(launch(c, K_SWEEP_PHOTON, [&] {
+        return launch_sweep_photon<Real>(c->stream, c->dim, c->order, g, oquad<Real>(c), (const Real *)c->coef,
+                                         (const Real *)c->bcoef, (const Real *)c->I[c->cur], (Real *)c->I[nxt],
+                                         (Real *)c->opartial);
+    }));
+    std::swap(c->fields, c->fields_old);
+    TRY(launch(c, K_FINISH, [&] {
+        return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
+                                   (const Real *)c->partial, (const Real *)c->opartial, c->vol, c->fields_old,
+                                   c->fields, c->eps_terms, c->err, 1);
+    }));
+    TRY(launch(c, K_EPS, [&] { return launch_eps_reduce(c->stream, (int)c->nc, c->eps_terms, c->eps_sums); }));
+    TRY(launch(c, K_COEF, [&] {
+        return launch_coefficients<Real>(c->stream, c->dim, g, c->model, c->fields, c->cell_dx, (Real *)c->coef);
+    }));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, c->eps_sums, NEPS * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned + NEPS, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    c->cur = nxt;
+    c->have_eps = true;
+    return GSIS_OK;
+}
+
+int read_eps(gsis_ctx *c, double *eps) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const double *s = c->h_pinned;
+    int errw = 0;
+    std::memcpy(&errw, c->h_pinned + NEPS, sizeof(int));
+    if (errw) return fail(c, GSIS_ERR_DIVERGED, "non-finite or non-positive density or temperature");
+    // Section 6: max over rho, u, T of the volume-weighted relative change; the
+    // velocity denominator is floored at 1% of the thermal-speed norm
+    const double e_rho = std::sqrt(s[0]) / std::sqrt(s[1]);
+    const double e_T = std::sqrt(s[4]) / std::sqrt(s[5]);
+    const double den_u = std::fmax(std::sqrt(s[3]), 0.01 * std::sqrt(s[6]));
+    const double e_u = std::sqrt(s[2]) / den_u;
+    double e = std::fmax(e_rho, std::fmax(e_T, e_u));
+    c->last_eps = e;
+    if (eps) *eps = e;
+    return GSIS_OK;
+}
+
+int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon_quad *pq,
+             const gsis_model_params *mp, const gsis_solver_params *sp, std::string &why) {
+    if (!m || !vq || !pq || !mp || !sp) return why = "null argument", GSIS_ERR_INVALID_ARG;
+    if (m->dim == 3) return why = "3-D meshes are not supported by this build", GSIS_ERR_UNSUPPORTED;
+    if (m->dim < 1 || m->dim > 2) return why = "dim must be 1 or 2", GSIS_ERR_INVALID_ARG;
+    if (m->n_cells <= 0 || m->n_faces <= 0 || m->n_cells > (1LL << 30)) return why = "bad mesh sizes", GSIS_ERR_INVALID_ARG;
+    if (!m->face_owner || !m->face_nbr || !m->face_normal || !m->face_area || !m->face_centroid || !m->cell_volume ||
+        !m->cell_centroid)
+        return why = "null mesh array", GSIS_ERR_INVALID_ARG;
+    if (m->n_patches < 0 || (m->n_patches > 0 && !m->patches)) return why = "bad patches", GSIS_ERR_INVALID_ARG;
+    if (vq->n <= 0 || !vq->xi || !vq->w) return why = "bad velocity quadrature", GSIS_ERR_INVALID_ARG;
+    if (pq->n <= 0 || !pq->omega || !pq->w) return why = "bad photon quadrature", GSIS_ERR_INVALID_ARG;
+    if (sp->precision != GSIS_FP32 && sp->precision != GSIS_FP64) return why = "bad precision", GSIS_ERR_INVALID_ARG;
+    if (sp->order != 1 && sp->order != 2) return why = "order must be 1 or 2", GSIS_ERR_INVALID_ARG;
+    if (sp->relax_block < 1 || sp->relax_block > MAXB) return why = "relax_block must be in 1..64", GSIS_ERR_INVALID_ARG;
+    {   // the gas sweep keeps block x VCH x 4 values in shared memory
+        const size_t rs = sp->precision == GSIS_FP64 ? 8 : 4;
+        if ((size_t)sp->relax_block * VCH * 4 * rs > 200 * 1024)
+            return why = "relax_block too large for the shared memory of one CTA (FP64: at most 50)",
+                   GSIS_ERR_INVALID_ARG;
+    }
+    if (!(sp->cfl_meso > 0) || !(sp->venkat_K > 0)) return why = "bad CFL or limiter constant", GSIS_ERR_INVALID_ARG;
+    if (!(mp->Kn > 0) || !(mp->Kn_p > 0) || !(mp->sigma_R >= 0) || !(mp->Z_r > 0) || !(mp->Z_v > 0) ||
+        !(mp->d_r >= 0) || !(mp->d_v > 0) || !(mp->d_r > 0))
+        return why = "bad model parameters", GSIS_ERR_INVALID_ARG;
+    if (!(mp->sigma_R > 0)) return why = "sigma_R must be positive (photons always on)", GSIS_ERR_INVALID_ARG;
+    for (int p = 0; p < m->n_patches; ++p) {
+        const gsis_patch &P = m->patches[p];
+        if (P.kind != GSIS_PATCH_WALL && P.kind != GSIS_PATCH_FARFIELD) return why = "bad patch kind", GSIS_ERR_INVALID_ARG;
+        if (!(P.T_t > 0) || (P.kind == GSIS_PATCH_FARFIELD && (!(P.rho > 0) || !(P.T_r > 0) || !(P.T_v > 0) || !(P.T_R >= 0))))
+            return why = "bad patch state", GSIS_ERR_INVALID_ARG;
+    }
+    return GSIS_OK;
+}
+
+void mason_monchick(const gsis_model_params *mp, double A[9]) {
+    const double dr = mp->d_r, dv = mp->d_v, Zr = mp->Z_r, Zv = mp->Z_v, Sc = mp->Sc;
+    for (int k = 0; k < 9; ++k) A[k] = 0.0;
+    A[0] = 2.0 / 3.0 + 5.0 / 6.0 * (dr / ((3 + dr) * Zr) + dv / ((3 + dv) * Zv));
+    A[1] = -5.0 / (2.0 * (3 + dr) * Zr);
+    A[2] = -5.0 / (2.0 * (3 + dv) * Zv);
+    A[3] = -dr / ((3 + dr) * Zr);
+    A[4] = Sc + 3.0 / (2.0 * (3 + dr) * Zr);
+    A[6] = -dv / ((3 + dv) * Zv);
+    A[8] = Sc + 3.0 / (2.0 * (3 + dv) * Zv);
+}
+
+template <typename Real>
+int init_uniform(gsis_ctx *c) {
+    std::vector<double> M((size_t)c->nc * NF, 0.0);
+    for (int64_t i = 0; i < c->nc; ++i) {
+        M[i * NF + 0] = 1.0;
+        for (int k = 4; k < 8; ++k) M[i * NF + k] = 1.0;
+    }
+    CUDA_TRY(c, cudaMemcpy(c->fields, M.data(), M.size() * sizeof(double), cudaMemcpyHostToDevice));
+    TRY(launch(c, K_EQUIL, [&] {
+        return launch_equilibrium<Real>(c->stream, c->dim, (int)c->nc, vquad<Real>(c), oquad<Real>(c), c->model,
+                                        c->fields, (Real *)c->f[c->cur], (Real *)c->I[c->cur]);
+    }));
+    return GSIS_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *gsis_strerror(int code) {
+    switch (code) {
+        case GSIS_OK: return "ok";
+        case GSIS_ERR_INVALID_ARG: return "invalid argument";
+        case GSIS_ERR_OUT_OF_MEMORY: return "out of memory";
+        case GSIS_ERR_CUDA: return "CUDA error";
+        case GSIS_ERR_DIVERGED: return "iteration diverged";
+        case GSIS_ERR_NOT_CONVERGED: return "not converged";
+        case GSIS_ERR_TIMEOUT: return "device wait timed out";
+        case GSIS_ERR_BAD_MESH: return "bad mesh";
+        case GSIS_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+const char *gsis_last_error(const gsis_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+void gsis_destroy(gsis_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &p : ctx->pending) {
+        cudaEventDestroy(p.e0);
+        cudaEventDestroy(p.e1);
+    }
+    for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    for (void *p : ctx->allocations) cudaFree(p);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+}
+
+int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon_quad *pq,
+                const gsis_model_params *mp, const gsis_solver_params *sp, void *cuda_stream, gsis_ctx **out) {
+    if (!out) return GSIS_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string why;
+    int rc = validate(m, vq, pq, mp, sp, why);
+    if (rc != GSIS_OK) return rc;
+    gsis_ctx *c = new (std::nothrow) gsis_ctx();
+    if (!c) return GSIS_ERR_OUT_OF_MEMORY;
+    auto bail = [&](int code) {
+        gsis_destroy(c);
+        return code;
+    };
+    const int dim = m->dim;
+    c->dim = dim;
+    c->precision = sp->precision;
+    c->real_size = sp->precision == GSIS_FP64 ? 8 : 4;
+    c->order = sp->order;
+    c->block = sp->relax_block;
+    c->solver = *sp;
+    c->nc = m->n_cells;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->V = vq->n;
+    c->Vp = (vq->n + VCH - 1) / VCH * VCH;
+    c->NO = pq->n;
+    c->Op = (pq->n + OCH - 1) / OCH * OCH;
+    c->nch = c->Vp / VCH;
+    c->och = c->Op / OCH;
+
+    ModelDev &md = c->model;
+    md.d_r = mp->d_r;
+    md.d_v = mp->d_v;
+    md.Z_r = mp->Z_r;
+    md.Z_v = mp->Z_v;
+    md.omega = mp->omega;
+    md.Sc = mp->Sc;
+    md.Kn = mp->Kn;
+    md.Kn_p = mp->Kn_p;
+    md.sigma_R = mp->sigma_R;
+    md.k_eff_density_scaled = mp->k_eff_density_scaled;
+    md.cfl_meso = sp->cfl_meso;
+    if (mp->A) std::memcpy(md.A, mp->A, 9 * sizeof(double));
+    else mason_monchick(mp, md.A);
+    {   // auxiliary heat-flux matrix of Section 2.1
+        const double Zi = 1.0 / (1.0 / mp->Z_r + 1.0 / mp->Z_v);
+        const double *A = md.A;
+        const double Mx[9] = {(2.0 - 3.0 * A[0]) * Zi + 1.0, -3.0 * A[1] * Zi, -3.0 * A[2] * Zi,
+                              -A[3] * Zi, 1.0 - A[4] * Zi, -A[5] * Zi,
+                              -A[6] * Zi, -A[7] * Zi, 1.0 - A[8] * Zi};
+        std::memcpy(md.Mix, Mx, sizeof(Mx));
+    }
+
+    // ---- connectivity: per cell up to MAXF faces (outward normal, neighbour)
+    const int64_t nc = m->n_cells, nfc = m->n_faces;
+    std::vector<int> nf(nc, 0), nbr(nc * MAXF, 0), bf_cell, bf_patch;
+    std::vector<double> nrm(nc * MAXF * 3, 0.0), sv(nc * MAXF, 0.0), dxf(nc * MAXF * 3, 0.0),
+        dxn(nc * MAXF * 3, 0.0), bfn;
+    std::vector<int64_t> face_of(nc * MAXF, -1);
+    for (int64_t f = 0; f < nfc; ++f) {
+        const int o = m->face_owner[f], nb = m->face_nbr[f];
+        if (o < 0 || o >= nc) return bail(GSIS_ERR_BAD_MESH);
+        if (nb >= nc || (nb < 0 && -1 - nb >= m->n_patches) || nb == o) return bail(GSIS_ERR_BAD_MESH);
+        const double S = m->face_area[f];
+        double nn = 0.0;
+        for (int a = 0; a < dim; ++a) nn += m->face_normal[f * dim + a] * m->face_normal[f * dim + a];
+        if (!(S > 0) || std::fabs(nn - 1.0) > 1e-6) return bail(GSIS_ERR_BAD_MESH);
+        const int sides[2] = {o, nb};
+        for (int s = 0; s < (nb >= 0 ? 2 : 1); ++s) {
+            const int cell = sides[s];
+            if (nf[cell] >= MAXF) return bail(GSIS_ERR_UNSUPPORTED);
+            const int k = nf[cell]++;
+            const double sg = s == 0 ? 1.0 : -1.0;
+            const double V = m->cell_volume[cell];
+            if (!(V > 0)) return bail(GSIS_ERR_BAD_MESH);
+            for (int a = 0; a < dim; ++a) {
+                nrm[(cell * MAXF + k) * 3 + a] = sg * m->face_normal[f * dim + a];
+                dxf[(cell * MAXF + k) * 3 + a] = m->face_centroid[f * dim + a] - m->cell_centroid[cell * dim + a];
+            }
+            sv[cell * MAXF + k] = S / V;
+            face_of[cell * MAXF + k] = f;
+            if (nb >= 0) {
+                const int other = sides[1 - s];
+                nbr[cell * MAXF + k] = other;
+                for (int a = 0; a < dim; ++a)
+                    dxn[(cell * MAXF + k) * 3 + a] = m->face_centroid[f * dim + a] - m->cell_centroid[other * dim + a];
+            } else {
+                const int b = (int)bf_cell.size();
+                nbr[cell * MAXF + k] = -1 - b;
+                bf_cell.push_back(o);
+                bf_patch.push_back(-1 - nb);
+                for (int a = 0; a < 3; ++a) bfn.push_back(a < dim ? m->face_normal[f * dim + a] : 0.0);
+            }
+        }
+    }
+    c->n_bf = (int)bf_cell.size();
+    // least-squares weights C_ij = (sum_k d_k d_k^T)^-1 d_j over the stencil of face
+    // neighbours and their face neighbours; a zero gradient where the normal matrix is
+    // singular (det <= 1e-10 (tr/dim)^dim)
+    std::vector<double> lsq(nc * MAXS * 3, 0.0), eps2(nc), cdx(nc), vol(nc);
+    std::vector<int> nst(nc, 0), stn(nc * MAXS, 0);
+    std::vector<signed char> local(nc * MAXF, -1);
+    for (int64_t i = 0; i < nc; ++i) {
+        vol[i] = m->cell_volume[i];
+        cdx[i] = std::pow(vol[i], 1.0 / dim);
+        const double Kdx = sp->venkat_K * cdx[i];
+        eps2[i] = Kdx * Kdx * Kdx;
+        std::vector<int> st;
+        for (int k = 0; k < nf[i]; ++k) {
+            const int j = nbr[i * MAXF + k];
+            if (j < 0) continue;
+            if (j / c->block == i / c->block) local[i * MAXF + k] = (signed char)(j - (i / c->block) * c->block);
+            st.push_back(j);
+            for (int k2 = 0; k2 < nf[j]; ++k2) {
+                const int j2 = nbr[j * MAXF + k2];
+                if (j2 >= 0 && j2 != i) st.push_back(j2);
+            }
+        }
+        std::sort(st.begin(), st.end());
+        st.erase(std::unique(st.begin(), st.end()), st.end());
+        if ((int)st.size() > MAXS) return bail(fail(c, GSIS_ERR_UNSUPPORTED, "least-squares stencil larger than 12"));
+        nst[i] = (int)st.size();
+        for (size_t k = 0; k < st.size(); ++k) stn[i * MAXS + k] = st[k];
+        if ((int)st.size() < dim) continue;
+        double G[2][2] = {{0, 0}, {0, 0}};
+        for (int j : st) {
+            double d[2] = {0, 0};
+            for (int a = 0; a < dim; ++a) d[a] = m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a];
+            for (int a = 0; a < dim; ++a)
+                for (int b = 0; b < dim; ++b) G[a][b] += d[a] * d[b];
+        }
+        double Gi[2][2] = {{0, 0}, {0, 0}};
+        if (dim == 1) {
+            if (!(G[0][0] > 0.0)) continue;
+            Gi[0][0] = 1.0 / G[0][0];
+        } else {
+            const double det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+            const double sc = 0.5 * (G[0][0] + G[1][1]);
+            if (!(det > 1e-10 * sc * sc)) continue;
+            Gi[0][0] = G[1][1] / det;
+            Gi[1][1] = G[0][0] / det;
+            Gi[0][1] = -G[0][1] / det;
+            Gi[1][0] = -G[1][0] / det;
+        }
+        for (size_t k = 0; k < st.size(); ++k) {
+            const int j = st[k];
+            double d[2] = {0, 0};
+            for (int a = 0; a < dim; ++a) d[a] = m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a];
+            for (int a = 0; a < dim; ++a) {
+                double s = 0.0;
+                for (int b = 0; b < dim; ++b) s += Gi[a][b] * d[b];
+                lsq[(i * MAXS + k) * 3 + a] = s;
+            }
+        }
+    }
+
+    // ---- quadratures, padded with zero-weight points at the origin
+    std::vector<double> vx(3 * (size_t)c->Vp, 0.0), vw(c->Vp, 0.0), ox(3 * (size_t)c->Op, 0.0), ow(c->Op, 0.0);
+    for (int v = 0; v < vq->n; ++v) {
+        for (int a = 0; a < dim; ++a) vx[a * (size_t)c->Vp + v] = vq->xi[v * dim + a];
+        vw[v] = vq->w[v];
+    }
+    for (int o = 0; o < pq->n; ++o) {
+        for (int a = 0; a < 3; ++a) ox[a * (size_t)c->Op + o] = pq->omega[o * 3 + a];
+        ow[o] = pq->w[o];
+    }
+
+    // ---- boundary records: constant parts (wall density is refreshed every step)
+    const int MH = 3 - dim;
+    std::vector<double> bco((size_t)std::max(c->n_bf, 1) * bc::NB, 0.0), pT(std::max(m->n_patches, 1)),
+        pu(3 * std::max(m->n_patches, 1)), tmp;
+    std::vector<int> pk(std::max(m->n_patches, 1), 0);
+    for (int p = 0; p < m->n_patches; ++p) {
+        pT[p] = m->patches[p].T_t;
+        pk[p] = m->patches[p].kind;
+        for (int a = 0; a < 3; ++a) pu[p * 3 + a] = m->patches[p].u[a];
+    }
+    for (int b = 0; b < c->n_bf; ++b) {
+        const gsis_patch &P = m->patches[bf_patch[b]];
+        double *B = &bco[(size_t)b * bc::NB];
+        const bool wall = P.kind == GSIS_PATCH_WALL;
+        const double T = P.T_t, Tr = wall ? P.T_t : P.T_r, Tv = wall ? P.T_t : P.T_v, TR = wall ? P.T_t : P.T_R;
+        B[bc::A] = (wall ? 1.0 : P.rho) * std::pow(2.0 * M_PI * T, -0.5 * dim);
+        B[bc::B] = 0.5 / T;
+        for (int a = 0; a < 3; ++a) B[bc::U + a] = P.u[a];
+        B[bc::M0] = 1.0;
+        B[bc::MH] = MH * T;
+        B[bc::M1] = 0.5 * mp->d_r * Tr;
+        B[bc::M2] = 0.5 * mp->d_v * Tv;
+        B[bc::IIN] = mp->sigma_R * TR * TR * TR * TR / M_PI;
+    }
+
+    // ---- device allocations
+    const size_t fsz = (size_t)nc * c->Vp * 4, isz = (size_t)nc * c->Op;
+    rc = GSIS_OK;
+#define A_(x) do { rc = (x); if (rc != GSIS_OK) { int _r = rc; if (!c->last_error.empty()) fprintf(stderr, "gsis: %s\n", c->last_error.c_str()); return bail(_r); } } while (0)
+    A_(dalloc_real(c, &c->f[0], fsz));
+    A_(dalloc_real(c, &c->f[1], fsz));
+    A_(dalloc_real(c, &c->I[0], isz));
+    A_(dalloc_real(c, &c->I[1], isz));
+    A_(dalloc_real(c, &c->coef, (size_t)nc * cf::NC));
+    A_(dalloc_real(c, &c->bcoef, bco.size()));
+    A_(dalloc_real(c, &c->partial, (size_t)nc * c->nch * NMP));
+    A_(dalloc_real(c, &c->opartial, (size_t)nc * c->och * NMO));
+    A_(dalloc(c, &c->fields, (size_t)nc * NF));
+    A_(dalloc(c, &c->fields_old, (size_t)nc * NF));
+    A_(dalloc(c, &c->eps_terms, (size_t)nc * NEPS));
+    A_(dalloc(c, &c->eps_sums, NEPS));
+    A_(dalloc(c, &c->err, 1));
+    A_(dalloc(c, &c->vol, nc));
+    A_(dalloc(c, &c->cell_dx, nc));
+    A_(dalloc(c, &c->g_nf, nc));
+    A_(dalloc(c, &c->g_nbr, nc * MAXF));
+    A_(dalloc(c, &c->g_local, nc * MAXF));
+    A_(dalloc(c, &c->bf_cell, std::max(c->n_bf, 1)));
+    A_(dalloc(c, &c->bf_patch, std::max(c->n_bf, 1)));
+    A_(dalloc_real(c, &c->g_nrm, nc * MAXF * 3));
+    A_(dalloc_real(c, &c->g_sv, nc * MAXF));
+    A_(dalloc_real(c, &c->g_dxf, nc * MAXF * 3));
+    A_(dalloc_real(c, &c->g_dxn, nc * MAXF * 3));
+    A_(dalloc_real(c, &c->g_lsq, nc * MAXS * 3));
+    A_(dalloc(c, &c->g_nst, nc));
+    A_(dalloc(c, &c->g_stn, nc * MAXS));
+    A_(dalloc_real(c, &c->g_eps2, nc));
+    A_(dalloc_real(c, &c->bf_nrm, 3 * std::max(c->n_bf, 1)));
+    A_(dalloc_real(c, &c->vq_x, vx.size()));
+    A_(dalloc_real(c, &c->vq_w, vw.size()));
+    A_(dalloc_real(c, &c->oq_x, ox.size()));
+    A_(dalloc_real(c, &c->oq_w, ow.size()));
+    A_(dalloc(c, &c->patch_T, pT.size()));
+    A_(dalloc(c, &c->patch_u, pu.size()));
+    A_(dalloc(c, &c->patch_kind, pk.size()));
+    if (cudaMallocHost(&c->h_pinned, (NEPS + 1) * sizeof(double)) != cudaSuccess) return bail(GSIS_ERR_OUT_OF_MEMORY);
+
+    if (bfn.empty()) bfn.assign(3, 0.0);
+    if (bf_cell.empty()) { bf_cell.push_back(0); bf_patch.push_back(0); }
+    A_(upload(c, c->vol, vol));
+    A_(upload(c, c->cell_dx, cdx));
+    A_(upload(c, c->g_nf, nf));
+    A_(upload(c, c->g_nbr, nbr));
+    A_(upload(c, c->g_local, local));
+    A_(upload(c, c->g_nst, nst));
+    A_(upload(c, c->g_stn, stn));
+    A_(upload(c, c->bf_cell, bf_cell));
+    A_(upload(c, c->bf_patch, bf_patch));
+    A_(upload_real(c, c->g_nrm, nrm));
+    A_(upload_real(c, c->g_sv, sv));
+    A_(upload_real(c, c->g_dxf, dxf));
+    A_(upload_real(c, c->g_dxn, dxn));
+    A_(upload_real(c, c->g_lsq, lsq));
+    A_(upload_real(c, c->g_eps2, eps2));
+    A_(upload_real(c, c->bf_nrm, bfn));
+    A_(upload_real(c, c->vq_x, vx));
+    A_(upload_real(c, c->vq_w, vw));
+    A_(upload_real(c, c->oq_x, ox));
+    A_(upload_real(c, c->oq_w, ow));
+    A_(upload_real(c, c->bcoef, bco));
+    A_(upload(c, c->patch_T, pT));
+    A_(upload(c, c->patch_u, pu));
+    A_(upload(c, c->patch_kind, pk));
+    if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) return bail(GSIS_ERR_CUDA);
+    if (cudaMemset(c->coef, 0, (size_t)nc * cf::NC * c->real_size) != cudaSuccess) return bail(GSIS_ERR_CUDA);
+    A_(c->precision == GSIS_FP64 ? init_uniform<double>(c) : init_uniform<float>(c));
+    A_(refresh(c));
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return bail(GSIS_ERR_CUDA);
+#undef A_
+    *out = c;
+    return GSIS_OK;
+}
+
+int gsis_init_fields(gsis_ctx *c, const double *M, int64_t len) {
+    if (!c || !M || len < c->nc * NF) return fail(c, GSIS_ERR_INVALID_ARG, "fields buffer too short");
+    CUDA_TRY(c, cudaMemcpyAsync(c->fields, M, (size_t)c->nc * NF * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    int rc = c->precision == GSIS_FP64
+                 ? launch(c, K_EQUIL, [&] {
+                       return launch_equilibrium<double>(c->stream, c->dim, (int)c->nc, vquad<double>(c),
+                                                         oquad<double>(c), c->model, c->fields, (double *)c->f[c->cur],
+                                                         (double *)c->I[c->cur]);
+                   })
+                 : launch(c, K_EQUIL, [&] {
+                       return launch_equilibrium<float>(c->stream, c->dim, (int)c->nc, vquad<float>(c),
+                                                        oquad<float>(c), c->model, c->fields, (float *)c->f[c->cur],
+                                                        (float *)c->I[c->cur]);
+                   });
+    TRY(rc);
+    TRY(refresh(c));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return GSIS_OK;
+}
+
+int gsis_upload_distributions(gsis_ctx *c, const void *f, const void *I) {
+    if (!c || !f || !I) return fail(c, GSIS_ERR_INVALID_ARG, "null buffer");
+    const size_t rs = c->real_size;
+    CUDA_TRY(c, cudaMemcpy2DAsync(c->f[c->cur], (size_t)c->Vp * 4 * rs, f, (size_t)c->V * 4 * rs, (size_t)c->V * 4 * rs,
+                                  (size_t)c->nc, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpy2DAsync(c->I[c->cur], (size_t)c->Op * rs, I, (size_t)c->NO * rs, (size_t)c->NO * rs,
+                                  (size_t)c->nc, cudaMemcpyHostToDevice, c->stream));
+    TRY(refresh(c));
+    return GSIS_OK;
+}
+
+int gsis_set_distributions(gsis_ctx *c, const double *f, int64_t f_len, const double *I, int64_t I_len) {
+    if (!c || !f || !I) return fail(c, GSIS_ERR_INVALID_ARG, "null buffer");
+    if (f_len < c->nc * c->V * 4 || I_len < c->nc * c->NO) return fail(c, GSIS_ERR_INVALID_ARG, "buffer too short");
+    // zero the padding so that padded velocities start from a defined state
+    CUDA_TRY(c, cudaMemsetAsync(c->f[c->cur], 0, (size_t)c->nc * c->Vp * 4 * c->real_size, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->I[c->cur], 0, (size_t)c->nc * c->Op * c->real_size, c->stream));
+    if (c->precision == GSIS_FP64) {
+        TRY(gsis_upload_distributions(c, f, I));
+    } else {
+        std::vector<float> ff(f, f + (size_t)c->nc * c->V * 4), fi(I, I + (size_t)c->nc * c->NO);
+        TRY(gsis_upload_distributions(c, ff.data(), fi.data()));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return GSIS_OK;
+}
+
+int gsis_get_distributions(gsis_ctx *c, double *f, int64_t f_len, double *I, int64_t I_len) {
+    if (!c || !f || !I) return fail(c, GSIS_ERR_INVALID_ARG, "null buffer");
+    if (f_len < c->nc * c->V * 4 || I_len < c->nc * c->NO) return fail(c, GSIS_ERR_INVALID_ARG, "buffer too short");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const size_t rs = c->real_size;
+    std::vector<unsigned char> hf((size_t)c->nc * c->V * 4 * rs), hi((size_t)c->nc * c->NO * rs);
+    CUDA_TRY(c, cudaMemcpy2D(hf.data(), (size_t)c->V * 4 * rs, c->f[c->cur], (size_t)c->Vp * 4 * rs, (size_t)c->V * 4 * rs,
+                             (size_t)c->nc, cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy2D(hi.data(), (size_t)c->NO * rs, c->I[c->cur], (size_t)c->Op * rs, (size_t)c->NO * rs,
+                             (size_t)c->nc, cudaMemcpyDeviceToHost));
+    const size_t nf = (size_t)c->nc * c->V * 4, ni = (size_t)c->nc * c->NO;
+    if (rs == 8) {
+        std::memcpy(f, hf.data(), nf * 8);
+        std::memcpy(I, hi.data(), ni * 8);
+    } else {
+        const float *a = reinterpret_cast<const float *>(hf.data()), *b = reinterpret_cast<const float *>(hi.data());
+        for (size_t k = 0; k < nf; ++k) f[k] = a[k];
+        for (size_t k = 0; k < ni; ++k) I[k] = b[k];
+    }
+    return GSIS_OK;
+}
+
+int gsis_get_fields(gsis_ctx *c, double *out, int64_t len) {
+    if (!c || !out || len < c->nc * NF) return fail(c, GSIS_ERR_INVALID_ARG, "fields buffer too short");
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->fields, (size_t)c->nc * NF * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return GSIS_OK;
+}
+
+int gsis_download_fields_async(gsis_ctx *c, double *out, int64_t len) {
+    if (!c || !out || len < c->nc * NF) return fail(c, GSIS_ERR_INVALID_ARG, "fields buffer too short");
+    CUDA_TRY(c, cudaMemcpyAsync(out, c->fields, (size_t)c->nc * NF * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    return GSIS_OK;
+}
+
+int gsis_step_async(gsis_ctx *c, int32_t mode) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (mode == GSIS_MODE_GSIS) return fail(c, GSIS_ERR_UNSUPPORTED, "GSIS mode is not built yet");
+    if (mode != GSIS_MODE_CIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
+    return c->precision == GSIS_FP64 ? cis_iteration<double>(c) : cis_iteration<float>(c);
+}
+
+int gsis_last_eps(gsis_ctx *c, double *eps_out) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (!c->have_eps) return fail(c, GSIS_ERR_INVALID_ARG, "no iteration since the distributions were set");
+    return read_eps(c, eps_out);
+}
+
+int gsis_step(gsis_ctx *c, int32_t mode, double *eps_out) {
+    TRY(gsis_step_async(c, mode));
+    return read_eps(c, eps_out);
+}
+
+int gsis_profile_enable(gsis_ctx *c, int32_t on) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    c->prof = on != 0;
+    return GSIS_OK;
+}
+
+int gsis_profile_reset(gsis_ctx *c) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    TRY(resolve_profile(c));
+    for (int k = 0; k < K_COUNT; ++k) {
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+    }
+    return GSIS_OK;
+}
+
+int gsis_profile_read(gsis_ctx *c, int32_t n, const char **names, double *ms, int64_t *launches, int32_t *n_out) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    TRY(resolve_profile(c));
+    for (int k = 0; k < K_COUNT && k < n; ++k) {
+        if (names) names[k] = kKernelNames[k];
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_n[k];
+    }
+    if (n_out) *n_out = K_COUNT;
+    return GSIS_OK;
+}
+
+int64_t gsis_launch_count(const gsis_ctx *c) { return c ? c->launches : 0; }
+
+int gsis_get_layout(const gsis_ctx *c, int32_t *v_pad, int32_t *o_pad, int32_t *n_chunks, int32_t *block) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (v_pad) *v_pad = c->Vp;
+    if (o_pad) *o_pad = c->Op;
+    if (n_chunks) *n_chunks = c->nch;
+    if (block) *block = c->block;
+    return GSIS_OK;
+}
+
+}  // extern "C"

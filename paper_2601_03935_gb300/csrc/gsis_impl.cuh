@@ -1,0 +1,109 @@
+// Internal declarations of the GSIS library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gsis {
+
+constexpr int MAXF = 4;        // faces per cell (segments, triangles, quads, tetrahedra)
+constexpr int MAXS = 12;       // least-squares stencil: face neighbours and their face neighbours
+constexpr int NF = 26;         // per-cell field record, see gsis.h
+constexpr int VCH = 128;       // discrete velocities per CTA of the gas sweep
+constexpr int OCH = 64;        // photon directions per CTA of the photon sweep
+constexpr int NMP = 20;        // stride of per-(cell, chunk) gas moment partials
+constexpr int NMO = 4;         // stride of per-(cell, chunk) photon moment partials
+constexpr int MAXB = 64;       // largest relaxation block
+constexpr int NEPS = 8;        // per-cell terms of the convergence measure
+
+// ---- per-cell coefficient record (Real), built from the FP64 fields each iteration
+// u[3] | per Maxwellian a in {t, tr, tv}: A, B, T, Q[3], K1, K2, R1[3], R2[3] (14) |
+// rate (1/tau) | inv_dt | sink | photon source g_R | photon rate k_eff
+namespace cf {
+constexpr int U = 0;
+constexpr int COMP = 3;        // first component block
+constexpr int CSZ = 14;        // size of one component block
+constexpr int A = 0, B = 1, T = 2, Q = 3, K1 = 6, K2 = 7, R1 = 8, R2 = 11;
+constexpr int RATE = COMP + 3 * CSZ;   // 45
+constexpr int INV_DT = RATE + 1;
+constexpr int SINK = RATE + 2;
+constexpr int GR = RATE + 3;
+constexpr int KEFF = RATE + 4;
+constexpr int NC = 52;         // padded record length
+}  // namespace cf
+
+// ---- per-boundary-face record (Real): incoming state
+namespace bc {
+constexpr int A = 0;           // density * (2 pi T)^(-dim/2)
+constexpr int B = 1;           // 1 / (2 T)
+constexpr int U = 2;           // velocity [3]
+constexpr int M0 = 5, MH = 6, M1 = 7, M2 = 8;  // plane multipliers (1, m T, d_r/2 T_r, d_v/2 T_v)
+constexpr int IIN = 9;         // incoming photon intensity
+constexpr int NB = 12;
+}  // namespace bc
+
+template <typename Real>
+struct Geom {
+    int n_cells, dim, block;
+    const int *nf;             // [nc]
+    const int *nbr;            // [nc][MAXF]: >= 0 cell, < 0: -1 - boundary face index
+    const signed char *local;  // [nc][MAXF]: neighbour's index inside the cell's block, or -1
+    const Real *nrm;           // [nc][MAXF][3] outward unit normal
+    const Real *sv;            // [nc][MAXF] face area / cell volume
+    const Real *dxf;           // [nc][MAXF][3] face centroid - cell centroid
+    const Real *dxn;           // [nc][MAXF][3] face centroid - neighbour centroid
+    const int *nst;            // [nc] stencil size
+    const int *stn;            // [nc][MAXS] stencil cells
+    const Real *lsq;           // [nc][MAXS][3] least-squares weights of the stencil cells
+    const Real *eps2;          // [nc] (K dx)^3
+    int n_bf;
+    const int *bf_cell;        // [n_bf]
+    const int *bf_patch;       // [n_bf]
+    const Real *bf_nrm;        // [n_bf][3] outward normal
+};
+
+template <typename Real>
+struct Quad {
+    int n, n_pad;
+    const Real *x;             // [3][n_pad] SoA (components beyond dim are zero)
+    const Real *w;             // [n_pad], zero on padding
+};
+
+struct ModelDev {
+    double d_r, d_v, Z_r, Z_v, omega, Sc, Kn, Kn_p, sigma_R;
+    int k_eff_density_scaled;
+    double A[9];
+    double Mix[9];             // (q0, q1, q2) = Mix (q_t, q_r, q_v)
+    double cfl_meso;
+};
+
+// ---- kernel launchers (kernels.cu); every launcher returns the launch status
+template <typename Real>
+cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, const ModelDev &m,
+                                const double *fields, const double *cell_dx, Real *coef);
+template <typename Real>
+cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
+                                const double *patch_T, const double *patch_u, const int *patch_kind,
+                                const Real *f, Real *bcoef);
+template <typename Real>
+cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
+                             const Real *coef, const Real *bcoef, const Real *f_in, Real *f_out,
+                             Real *partial);
+template <typename Real>
+cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
+                                const Real *coef, const Real *bcoef, const Real *I_in, Real *I_out,
+                                Real *partial);
+template <typename Real>
+cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const ModelDev &m,
+                          const Real *coef, const Real *partial, const Real *opartial, const double *vol,
+                          const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
+                          int have_old);
+cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_sums);
+template <typename Real>
+cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+                               const ModelDev &m, const double *fields, Real *f, Real *I);
+template <typename Real>
+cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+                                const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial);
+
+}  // namespace gsis

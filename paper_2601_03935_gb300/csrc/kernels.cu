@@ -1,0 +1,992 @@
+// Device kernels of the GSIS library.
+//
+//  coefficients   per-cell reference-distribution coefficients from the FP64 fields
+//                 (Section 2.1; Eq. reference_distribution)
+//  wall_density   density of diffusely re-emitted molecules at each wall face
+//  sweep_gas      implicit finite-volume kinetic step of Eq. (dis_micro) for the four
+//                 gas planes: upwind (order 1) or Venkatakrishnan-limited linear
+//                 (order 2, Eq. deltaflux_micro) residual, then forward/backward
+//                 Gauss-Seidel point relaxation inside a block of consecutive cells,
+//                 then the velocity moments of the new distribution (Eq. getmoment)
+//  sweep_photon   the same step for the gray intensity I_R
+//  finish         FP64 macroscopic fields from the moment partials, and the per-cell
+//                 terms of the convergence measure of Section 6
+//  eps_reduce     deterministic single-CTA reduction of those terms
+//  equilibrium    multi-temperature local equilibrium of given fields
+//  moments_only   velocity moments of the current distributions
+#include <cmath>
+#include <cstdio>
+
+#include "gsis_impl.cuh"
+
+namespace gsis {
+
+// ------------------------------------------------------------------ small vector type
+template <typename Real, int N>
+struct __align__(sizeof(Real) * N) Vec {
+    Real v[N];
+};
+
+template <typename Real, int N>
+__device__ __forceinline__ Vec<Real, N> vload(const Real *p) {
+    return *reinterpret_cast<const Vec<Real, N> *>(p);
+}
+template <typename Real, int N>
+__device__ __forceinline__ void vstore(Real *p, const Vec<Real, N> &x) {
+    *reinterpret_cast<Vec<Real, N> *>(p) = x;
+}
+
+__device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ double fexp(double x) { return exp(x); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+
+// ------------------------------------------------------------------ coefficients
+template <typename Real, int DIM>
+__global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restrict__ F,
+                               const double *__restrict__ cell_dx, Real *__restrict__ coef) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_cells) return;
+    const double *M = F + (size_t)i * NF;
+    const double rho = M[0], Tt = M[4], Tr = M[5], Tv = M[6], TR = M[7];
+    const double dr = m.d_r, dv = m.d_v;
+    const double Ttr = (3.0 * Tt + dr * Tr) / (3.0 + dr);
+    const double Ttv = (3.0 * Tt + dv * Tv) / (3.0 + dv);
+    const int MH = 3 - DIM;
+    double q[3][3];  // [mode t,r,v][component]
+    for (int a = 0; a < 3; ++a) {
+        q[0][a] = M[8 + a];
+        q[1][a] = M[11 + a];
+        q[2][a] = M[14 + a];
+    }
+    double qa[3][3];  // q0, q1, q2
+    for (int r = 0; r < 3; ++r)
+        for (int a = 0; a < 3; ++a) qa[r][a] = m.Mix[r * 3 + 0] * q[0][a] + m.Mix[r * 3 + 1] * q[1][a] + m.Mix[r * 3 + 2] * q[2][a];
+    const double alpha[3] = {1.0 - 1.0 / m.Z_r - 1.0 / m.Z_v, 1.0 / m.Z_r, 1.0 / m.Z_v};
+    const double Ta[3] = {Tt, Ttr, Ttv};
+    const double k1[3] = {0.5 * dr * Tr, 0.5 * dr * Ttr, 0.5 * dr * Tr};
+    const double k2[3] = {0.5 * dv * Tv, 0.5 * dv * Tv, 0.5 * dv * Ttv};
+    const double *qg0[3] = {q[0], qa[0], qa[0]};
+    const double *qg1[3] = {q[1], qa[1], qa[1]};
+    const double *qg2[3] = {q[2], qa[2], qa[2]};
+    Real *C = coef + (size_t)i * cf::NC;
+    for (int a = 0; a < 3; ++a) C[cf::U + a] = (Real)M[1 + a];
+    const double two_pi = 6.283185307179586;
+    for (int c = 0; c < 3; ++c) {
+        Real *Cc = C + cf::COMP + c * cf::CSZ;
+        const double T = Ta[c];
+        Cc[cf::A] = (Real)(alpha[c] * rho * pow(two_pi * T, -0.5 * DIM));
+        Cc[cf::B] = (Real)(0.5 / T);
+        Cc[cf::T] = (Real)T;
+        const double s = 2.0 / (15.0 * T * rho * T);
+        for (int a = 0; a < 3; ++a) {
+            Cc[cf::Q + a] = (Real)(s * qg0[c][a]);
+            Cc[cf::R1 + a] = (Real)(qg1[c][a] / (rho * T));
+            Cc[cf::R2 + a] = (Real)(qg2[c][a] / (rho * T));
+        }
+        Cc[cf::K1] = (Real)k1[c];
+        Cc[cf::K2] = (Real)k2[c];
+    }
+    (void)MH;
+    const double tau = sqrt(2.0 / 3.141592653589793) * pow(Tt, m.omega - 1.0) * m.Kn / rho;
+    const double keff = m.k_eff_density_scaled ? rho / m.Kn_p : 1.0 / m.Kn_p;
+    const double umag = sqrt(M[1] * M[1] + M[2] * M[2] + M[3] * M[3]);
+    const double eR = 4.0 * m.sigma_R * TR * TR * TR * TR;
+    C[cf::RATE] = (Real)(1.0 / tau);
+    C[cf::INV_DT] = (Real)((umag + sqrt(5.0 * Tt / 3.0)) / (m.cfl_meso * cell_dx[i]));
+    C[cf::SINK] = (Real)(-keff * (4.0 * m.sigma_R * Tv * Tv * Tv * Tv - eR) / rho);
+    C[cf::GR] = (Real)(m.sigma_R * Tv * Tv * Tv * Tv / 3.141592653589793);
+    C[cf::KEFF] = (Real)keff;
+}
+
+// ------------------------------------------------------------------ wall density
+// One warp per boundary face; far-field records are constant and left untouched.
+template <typename Real, int DIM>
+__global__ void k_wall_density(Geom<Real> g, Quad<Real> vq, const double *__restrict__ patch_T,
+                               const double *__restrict__ patch_u, const int *__restrict__ patch_kind,
+                               const Real *__restrict__ f, Real *__restrict__ bcoef) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= g.n_bf) return;
+    const int p = g.bf_patch[warp];
+    if (patch_kind[p] != 0) return;
+    const int cell = g.bf_cell[warp];
+    const double Tw = patch_T[p];
+    double n[3], uw[3];
+    for (int a = 0; a < 3; ++a) {
+        n[a] = (double)g.bf_nrm[warp * 3 + a];
+        uw[a] = patch_u[p * 3 + a];
+    }
+    const double norm = pow(6.283185307179586 * Tw, -0.5 * DIM);
+    double out = 0.0, inc = 0.0;
+    for (int v = lane; v < vq.n_pad; v += 32) {
+        double xn = 0.0, c2 = 0.0;
+        for (int a = 0; a < DIM; ++a) {
+            const double x = (double)vq.x[a * vq.n_pad + v];
+            xn += x * n[a];
+            c2 += (x - uw[a]) * (x - uw[a]);
+        }
+        const double w = (double)vq.w[v];
+        if (xn > 0.0) out += w * xn * (double)f[((size_t)cell * vq.n_pad + v) * 4];
+        else if (xn < 0.0) inc += w * xn * norm * exp(-c2 / (2.0 * Tw));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        out += __shfl_xor_sync(0xffffffffu, out, o);
+        inc += __shfl_xor_sync(0xffffffffu, inc, o);
+    }
+    if (lane == 0) {
+        const double rho_w = inc < 0.0 ? -out / inc : 0.0;
+        bcoef[(size_t)warp * bc::NB + bc::A] = (Real)(rho_w * norm);
+    }
+}
+
+// ------------------------------------------------------------------ sweep helpers
+template <typename Real, int N>
+struct V {
+    Real x[N];
+};
+
+template <typename Real, int N>
+__device__ __forceinline__ V<Real, N> ldv(const Real *base, size_t idx) {
+    V<Real, N> r;
+    if constexpr (N == 1) {
+        r.x[0] = base[idx];
+    } else {
+        Vec<Real, N> t = vload<Real, N>(base + idx * N);
+#pragma unroll
+        for (int p = 0; p < N; ++p) r.x[p] = t.v[p];
+    }
+    return r;
+}
+template <typename Real, int N>
+__device__ __forceinline__ void stv(Real *base, size_t idx, const V<Real, N> &a) {
+    if constexpr (N == 1) {
+        base[idx] = a.x[0];
+    } else {
+        Vec<Real, N> t;
+#pragma unroll
+        for (int p = 0; p < N; ++p) t.v[p] = a.x[p];
+        vstore<Real, N>(base + idx * N, t);
+    }
+}
+
+// Venkatakrishnan-limited least-squares slope of cell j at one discrete velocity:
+// grad = sum_s C_js (f_s - f_j) over the stencil (face neighbours and their face
+// neighbours); phi = min(1, min_faces phi_V(Delta_1, Delta_2)) per plane with the
+// bounds Delta_max/min taken over the face neighbours.  Returns the slope times phi.
+template <typename Real, int N, int DIM>
+__device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *__restrict__ f, int stride, int j,
+                                              int v, const V<Real, N> &fj, V<Real, N> (&slope)[DIM]) {
+    V<Real, N> dmax, dmin;
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        dmax.x[p] = Real(0);
+        dmin.x[p] = Real(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) slope[d].x[p] = Real(0);
+    }
+    const int ns = g.nst[j];
+    for (int k = 0; k < ns; ++k) {
+        const int s = g.stn[j * MAXS + k];
+        const V<Real, N> fs = ldv<Real, N>(f, (size_t)s * stride + v);
+        Real c[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) c[d] = g.lsq[(j * MAXS + k) * 3 + d];
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            const Real dq = fs.x[p] - fj.x[p];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) slope[d].x[p] = fma(c[d], dq, slope[d].x[p]);
+        }
+    }
+    const int nf = g.nf[j];
+    for (int k = 0; k < nf; ++k) {
+        const int nb = g.nbr[j * MAXF + k];
+        if (nb < 0) continue;
+        const V<Real, N> fk = ldv<Real, N>(f, (size_t)nb * stride + v);
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            const Real dq = fk.x[p] - fj.x[p];
+            dmax.x[p] = fmax(dmax.x[p], dq);
+            dmin.x[p] = fmin(dmin.x[p], dq);
+        }
+    }
+    const Real eps2 = g.eps2[j];
+    V<Real, N> phi;
+#pragma unroll
+    for (int p = 0; p < N; ++p) phi.x[p] = Real(1);
+    for (int k = 0; k < nf; ++k) {
+        if (g.nbr[j * MAXF + k] < 0) continue;
+        Real dx[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) dx[d] = g.dxf[(j * MAXF + k) * 3 + d];
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            Real d2 = Real(0);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) d2 = fma(slope[d].x[p], dx[d], d2);
+            const Real d1 = d2 > Real(0) ? dmax.x[p] : dmin.x[p];
+            const Real num = fma(d1, d1 + Real(2) * d2, eps2);
+            const Real den = fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2));
+            const Real pf = d2 != Real(0) ? fdiv(num, den) : Real(1);
+            phi.x[p] = fmin(phi.x[p], pf);
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+        for (int p = 0; p < N; ++p) slope[d].x[p] *= phi.x[p];
+}
+
+// Residual r = source - (1/V) sum_faces S (xi_n^+ f_L + xi_n^- f_R) of one (cell, velocity);
+// the source is passed in.  Also returns d = inv_dt + rate + (1/V) sum S xi_n^+.
+template <typename Real, int N, int DIM, int ORDER>
+__device__ __forceinline__ void transport_residual(const Geom<Real> &g, const Real *__restrict__ f, int stride,
+                                                   const Real *__restrict__ bcoef, int i, int v, const Real *xi,
+                                                   const V<Real, N> &fi, V<Real, N> &r, Real &d, bool photon) {
+    V<Real, N> slope_i[DIM];
+    if constexpr (ORDER == 2) limited_slope<Real, N, DIM>(g, f, stride, i, v, fi, slope_i);
+    const int nf = g.nf[i];
+    for (int k = 0; k < nf; ++k) {
+        const int fk = i * MAXF + k;
+        const int nb = g.nbr[fk];
+        Real xn = Real(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) xn = fma(xi[a], g.nrm[fk * 3 + a], xn);
+        const Real sv = g.sv[fk];
+        V<Real, N> face;
+        if (xn > Real(0)) {
+            d = fma(sv, xn, d);
+            face = fi;
+            if constexpr (ORDER == 2) {
+                if (nb >= 0) {
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        const Real dx = g.dxf[fk * 3 + a];
+#pragma unroll
+                        for (int p = 0; p < N; ++p) face.x[p] = fma(slope_i[a].x[p], dx, face.x[p]);
+                    }
+                }
+            }
+        } else if (xn < Real(0)) {
+            if (nb >= 0) {
+                face = ldv<Real, N>(f, (size_t)nb * stride + v);
+                if constexpr (ORDER == 2) {
+                    V<Real, N> slope_j[DIM];
+                    limited_slope<Real, N, DIM>(g, f, stride, nb, v, face, slope_j);
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        const Real dx = g.dxn[fk * 3 + a];
+#pragma unroll
+                        for (int p = 0; p < N; ++p) face.x[p] = fma(slope_j[a].x[p], dx, face.x[p]);
+                    }
+                }
+            } else {
+                const Real *B = bcoef + (size_t)(-1 - nb) * bc::NB;
+                if (photon) {
+                    face.x[0] = B[bc::IIN];
+                } else {
+                    Real c2 = Real(0);
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        const Real c = xi[a] - B[bc::U + a];
+                        c2 = fma(c, c, c2);
+                    }
+                    const Real E = B[bc::A] * fexp(-B[bc::B] * c2);
+                    if constexpr (N == 4) {
+                        face.x[0] = E * B[bc::M0];
+                        face.x[1] = E * B[bc::MH];
+                        face.x[2] = E * B[bc::M1];
+                        face.x[3] = E * B[bc::M2];
+                    } else {
+                        face.x[0] = E;
+                    }
+                }
+            }
+        } else {
+            continue;
+        }
+        const Real s = sv * xn;
+#pragma unroll
+        for (int p = 0; p < N; ++p) r.x[p] = fma(-s, face.x[p], r.x[p]);
+    }
+}
+
+// Reference distribution of the four gas planes at one (cell, velocity).
+template <typename Real, int DIM>
+__device__ __forceinline__ void reference(const Real *__restrict__ C, const Real *xi, Real (&gp)[4]) {
+    constexpr int MH = 3 - DIM;
+    Real c[DIM], c2 = Real(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        c[a] = xi[a] - C[cf::U + a];
+        c2 = fma(c[a], c[a], c2);
+    }
+    gp[0] = gp[1] = gp[2] = gp[3] = Real(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const Real *Ck = C + cf::COMP + k * cf::CSZ;
+        const Real Bk = Ck[cf::B], T = Ck[cf::T];
+        const Real E = Ck[cf::A] * fexp(-Bk * c2);
+        Real qc = Real(0), r1 = Real(0), r2 = Real(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            qc = fma(Ck[cf::Q + a], c[a], qc);
+            r1 = fma(Ck[cf::R1 + a], c[a], r1);
+            r2 = fma(Ck[cf::R2 + a], c[a], r2);
+        }
+        const Real p0 = fma(qc, fma(c2 + Real(MH) * T, Bk, Real(-2.5)), Real(1));
+        gp[0] = fma(E, p0, gp[0]);
+        if constexpr (MH > 0) {
+            const Real ph = fma(qc, fma(c2 + Real(MH + 2) * T, Bk, Real(-2.5)), Real(1));
+            gp[1] = fma(E * (Real(MH) * T), ph, gp[1]);
+        }
+        gp[2] = fma(E, fma(Ck[cf::K1], p0, r1), gp[2]);
+        gp[3] = fma(E, fma(Ck[cf::K2], p0, r2), gp[3]);
+    }
+}
+
+// Number of moments per gas chunk partial: F0: 1, c (DIM), cc (DIM(DIM+1)/2), c|c|^2 (DIM);
+// H0 (DIM < 3): 1, c; f1: 1, c; f2: 1, c.
+template <int DIM>
+constexpr int n_gas_moments() {
+    return 1 + DIM + DIM * (DIM + 1) / 2 + DIM + (DIM < 3 ? 3 : 2) * (1 + DIM);
+}
+
+// Accumulate the moments of one (cell, velocity) value into acc (shifted basis c = xi - u).
+template <typename Real, int DIM>
+__device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Real w, const Real (&fv)[4]) {
+    Real c2 = Real(0);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) c2 = fma(c[a], c[a], c2);
+    const Real w0 = w * fv[0];
+    int m = 0;
+    acc[m++] += w0;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) acc[m++] += w0 * c[a];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int b = a; b < DIM; ++b) acc[m++] += w0 * c[a] * c[b];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) acc[m++] += w0 * c[a] * c2;
+#pragma unroll
+    for (int p = (DIM < 3 ? 1 : 2); p < 4; ++p) {
+        const Real wp = w * fv[p];
+        acc[m++] += wp;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) acc[m++] += wp * c[a];
+    }
+}
+
+// ------------------------------------------------------------------ gas sweep
+// CTA = one block of consecutive cells x VCH discrete velocities; thread = velocity.
+template <typename Real, int DIM, int ORDER>
+__global__ void __launch_bounds__(VCH) k_sweep_gas(Geom<Real> g, Quad<Real> vq, const Real *__restrict__ coef,
+                                                    const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
+                                                    Real *__restrict__ f_out, Real *__restrict__ partial) {
+    extern __shared__ unsigned char smem_raw[];
+    Vec<Real, 4> *R = reinterpret_cast<Vec<Real, 4> *>(smem_raw);           // [block][VCH]
+    Real *sxi = reinterpret_cast<Real *>(R + g.block * VCH);                  // [DIM+1][VCH]
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * g.block;
+    const int nb = min(g.block, g.n_cells - c0);
+    const int chunk = blockIdx.y;
+    const int v = chunk * VCH + tid;
+    const int stride = vq.n_pad;
+    Real xi[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        xi[a] = vq.x[a * stride + v];
+        sxi[a * VCH + tid] = xi[a];
+    }
+    sxi[DIM * VCH + tid] = vq.w[v];
+
+    // residuals at f^k
+    for (int l = 0; l < nb; ++l) {
+        const int i = c0 + l;
+        const Real *C = coef + (size_t)i * cf::NC;
+        Real gp[4];
+        reference<Real, DIM>(C, xi, gp);
+        const V<Real, 4> fi = ldv<Real, 4>(f_in, (size_t)i * stride + v);
+        const Real rate = C[cf::RATE];
+        V<Real, 4> r;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) r.x[p] = (gp[p] - fi.x[p]) * rate;
+        r.x[3] = fma(C[cf::SINK], fi.x[0], r.x[3]);
+        Real d = Real(0);
+        transport_residual<Real, 4, DIM, ORDER>(g, f_in, stride, bcoef, i, v, xi, fi, r, d, false);
+        Vec<Real, 4> t;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) t.v[p] = r.x[p];
+        R[l * VCH + tid] = t;
+    }
+    // forward Gauss-Seidel inside the block
+    for (int l = 0; l < nb; ++l) {
+        const int i = c0 + l;
+        const Real *C = coef + (size_t)i * cf::NC;
+        Real d = C[cf::INV_DT] + C[cf::RATE];
+        Vec<Real, 4> acc = R[l * VCH + tid];
+        const int nf = g.nf[i];
+        for (int k = 0; k < nf; ++k) {
+            const int fk = i * MAXF + k;
+            Real xn = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) xn = fma(xi[a], g.nrm[fk * 3 + a], xn);
+            const Real sv = g.sv[fk];
+            if (xn > Real(0)) d = fma(sv, xn, d);
+            const int lj = g.local[fk];
+            if (lj >= 0 && lj < l && xn < Real(0)) {
+                const Vec<Real, 4> dj = R[lj * VCH + tid];
+                const Real a_ = sv * xn;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc.v[p] = fma(-a_, dj.v[p], acc.v[p]);
+            }
+        }
+        const Real inv = Real(1) / d;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc.v[p] *= inv;
+        R[l * VCH + tid] = acc;
+    }
+    // backward Gauss-Seidel
+    for (int l = nb - 1; l >= 0; --l) {
+        const int i = c0 + l;
+        const Real *C = coef + (size_t)i * cf::NC;
+        Real d = C[cf::INV_DT] + C[cf::RATE];
+        Vec<Real, 4> corr;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) corr.v[p] = Real(0);
+        const int nf = g.nf[i];
+        for (int k = 0; k < nf; ++k) {
+            const int fk = i * MAXF + k;
+            Real xn = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) xn = fma(xi[a], g.nrm[fk * 3 + a], xn);
+            const Real sv = g.sv[fk];
+            if (xn > Real(0)) d = fma(sv, xn, d);
+            const int lj = g.local[fk];
+            if (lj > l && xn < Real(0)) {
+                const Vec<Real, 4> dj = R[lj * VCH + tid];
+                const Real a_ = sv * xn;
+#pragma unroll
+                for (int p = 0; p < 4; ++p) corr.v[p] = fma(a_, dj.v[p], corr.v[p]);
+            }
+        }
+        Vec<Real, 4> acc = R[l * VCH + tid];
+        const Real inv = Real(1) / d;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) acc.v[p] = fma(-corr.v[p], inv, acc.v[p]);
+        R[l * VCH + tid] = acc;
+    }
+    // f^{k+1/2} = f^k + delta; stage it for the moments
+    for (int l = 0; l < nb; ++l) {
+        const size_t idx = (size_t)(c0 + l) * stride + v;
+        Vec<Real, 4> fo = vload<Real, 4>(f_in + idx * 4);
+        Vec<Real, 4> dl = R[l * VCH + tid];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) fo.v[p] += dl.v[p];
+        vstore<Real, 4>(f_out + idx * 4, fo);
+        R[l * VCH + tid] = fo;
+    }
+    __syncthreads();
+    // moments: 8 threads per cell, each over VCH/8 velocities, shuffle-reduced
+    constexpr int TPC = 8;
+    constexpr int NM = n_gas_moments<DIM>();
+    const int sub = tid % TPC;
+    for (int l = tid / TPC; l < nb; l += VCH / TPC) {
+        const int i = c0 + l;
+        const Real *C = coef + (size_t)i * cf::NC;
+        Real u[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) u[a] = C[cf::U + a];
+        Real acc[NMP];
+#pragma unroll
+        for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
+        for (int vl = sub; vl < VCH; vl += TPC) {
+            const Vec<Real, 4> fv4 = R[l * VCH + vl];
+            Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};
+            Real c[DIM];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) c[a] = sxi[a * VCH + vl] - u[a];
+            add_moments<Real, DIM>(acc, c, sxi[DIM * VCH + vl], fv);
+        }
+        // the TPC lanes of one cell share the loop trip count; exchange only among them
+        const unsigned gmask = 0xFFu << ((tid & 31) & ~(TPC - 1));
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+#pragma unroll
+            for (int o = 1; o < TPC; o <<= 1) acc[m] += __shfl_xor_sync(gmask, acc[m], o);
+        }
+        if (sub == 0) {
+            Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMP;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) P[m] = acc[m];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ photon sweep
+template <typename Real, int DIM, int ORDER>
+__global__ void __launch_bounds__(OCH) k_sweep_photon(Geom<Real> g, Quad<Real> oq, const Real *__restrict__ coef,
+                                                       const Real *__restrict__ bcoef, const Real *__restrict__ I_in,
+                                                       Real *__restrict__ I_out, Real *__restrict__ partial) {
+    extern __shared__ unsigned char smem_raw[];
+    Real *R = reinterpret_cast<Real *>(smem_raw);            // [block][OCH]
+    Real *som = R + g.block * OCH;                           // [DIM+1][OCH]
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * g.block;
+    const int nb = min(g.block, g.n_cells - c0);
+    const int chunk = blockIdx.y;
+    const int o = chunk * OCH + tid;
+    const int stride = oq.n_pad;
+    Real om[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        om[a] = oq.x[a * stride + o];
+        som[a * OCH + tid] = om[a];
+    }
+    som[DIM * OCH + tid] = oq.w[o];
+    for (int l = 0; l < nb; ++l) {
+        const int i = c0 + l;
+        const Real *C = coef + (size_t)i * cf::NC;
+        const V<Real, 1> Ii = ldv<Real, 1>(I_in, (size_t)i * stride + o);
+        V<Real, 1> r;
+        r.x[0] = C[cf::KEFF] * (C[cf::GR] - Ii.x[0]);
+        Real d = Real(0);
+        transport_residual<Real, 1, DIM, ORDER>(g, I_in, stride, bcoef, i, o, om, Ii, r, d, true);
+        R[l * OCH + tid] = r.x[0];
+    }
+    for (int l = 0; l < nb; ++l) {
+        const int i = c0 + l;
+        const Real *C = coef + (size_t)i * cf::NC;
+        Real d = C[cf::INV_DT] + C[cf::KEFF];
+        Real acc = R[l * OCH + tid];
+        const int nf = g.nf[i];
+        for (int k = 0; k < nf; ++k) {
+            const int fk = i * MAXF + k;
+            Real on = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) on = fma(om[a], g.nrm[fk * 3 + a], on);
+            const Real sv = g.sv[fk];
+            if (on > Real(0)) d = fma(sv, on, d);
+            const int lj = g.local[fk];
+            if (lj >= 0 && lj < l && on < Real(0)) acc = fma(-sv * on, R[lj * OCH + tid], acc);
+        }
+        R[l * OCH + tid] = acc / d;
+    }
+    for (int l = nb - 1; l >= 0; --l) {
+        const int i = c0 + l;
+        const Real *C = coef + (size_t)i * cf::NC;
+        Real d = C[cf::INV_DT] + C[cf::KEFF];
+        Real corr = Real(0);
+        const int nf = g.nf[i];
+        for (int k = 0; k < nf; ++k) {
+            const int fk = i * MAXF + k;
+            Real on = Real(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) on = fma(om[a], g.nrm[fk * 3 + a], on);
+            const Real sv = g.sv[fk];
+            if (on > Real(0)) d = fma(sv, on, d);
+            const int lj = g.local[fk];
+            if (lj > l && on < Real(0)) corr = fma(sv * on, R[lj * OCH + tid], corr);
+        }
+        R[l * OCH + tid] = R[l * OCH + tid] - corr / d;
+    }
+    for (int l = 0; l < nb; ++l) {
+        const size_t idx = (size_t)(c0 + l) * stride + o;
+        const Real In = I_in[idx] + R[l * OCH + tid];
+        I_out[idx] = In;
+        R[l * OCH + tid] = In;
+    }
+    __syncthreads();
+    constexpr int TPC = 8;
+    const int sub = tid % TPC;
+    for (int l = tid / TPC; l < nb; l += OCH / TPC) {
+        Real acc[1 + DIM];
+#pragma unroll
+        for (int m = 0; m <= DIM; ++m) acc[m] = Real(0);
+        for (int ol = sub; ol < OCH; ol += TPC) {
+            const Real wI = som[DIM * OCH + ol] * R[l * OCH + ol];
+            acc[0] += wI;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) acc[1 + a] += wI * som[a * OCH + ol];
+        }
+        const unsigned gmask = 0xFFu << ((tid & 31) & ~(TPC - 1));
+#pragma unroll
+        for (int m = 0; m <= DIM; ++m)
+#pragma unroll
+            for (int s = 1; s < TPC; s <<= 1) acc[m] += __shfl_xor_sync(gmask, acc[m], s);
+        if (sub == 0) {
+            Real *P = partial + ((size_t)(c0 + l) * gridDim.y + chunk) * NMO;
+#pragma unroll
+            for (int m = 0; m <= DIM; ++m) P[m] = acc[m];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ moments only
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(VCH) k_moments_gas(int n_cells, Quad<Real> vq, const Real *__restrict__ coef,
+                                                      const Real *__restrict__ f, Real *__restrict__ partial) {
+    // one warp per (cell, chunk); lanes stride the chunk's velocities
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (VCH / 32) + warp;
+    const int chunk = blockIdx.y;
+    if (i >= n_cells) return;
+    constexpr int NM = n_gas_moments<DIM>();
+    const Real *C = coef + (size_t)i * cf::NC;
+    Real acc[NMP];
+#pragma unroll
+    for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
+    for (int vl = lane; vl < VCH; vl += 32) {
+        const int v = chunk * VCH + vl;
+        const Vec<Real, 4> fv4 = vload<Real, 4>(f + ((size_t)i * vq.n_pad + v) * 4);
+        Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};
+        Real c[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) c[a] = vq.x[a * vq.n_pad + v] - C[cf::U + a];
+        add_moments<Real, DIM>(acc, c, vq.w[v], fv);
+    }
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+    if (lane == 0) {
+        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMP;
+#pragma unroll
+        for (int m = 0; m < NM; ++m) P[m] = acc[m];
+    }
+}
+
+template <typename Real, int DIM>
+__global__ void k_moments_photon(int n_cells, Quad<Real> oq, const Real *__restrict__ I, Real *__restrict__ partial) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x / 32) + warp;
+    const int chunk = blockIdx.y;
+    if (i >= n_cells) return;
+    Real acc[1 + DIM];
+#pragma unroll
+    for (int m = 0; m <= DIM; ++m) acc[m] = Real(0);
+    for (int ol = lane; ol < OCH; ol += 32) {
+        const int o = chunk * OCH + ol;
+        const Real wI = oq.w[o] * I[(size_t)i * oq.n_pad + o];
+        acc[0] += wI;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) acc[1 + a] += wI * oq.x[a * oq.n_pad + o];
+    }
+#pragma unroll
+    for (int m = 0; m <= DIM; ++m)
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], s);
+    if (lane == 0) {
+        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMO;
+#pragma unroll
+        for (int m = 0; m <= DIM; ++m) P[m] = acc[m];
+    }
+}
+
+// ------------------------------------------------------------------ finish (FP64)
+// Shifted moments S about the coefficient velocity u0 (the shift the sweep used):
+// with delta = S_c / rho the flow velocity is u0 + delta and every central moment
+// follows from the binomial shift by delta.
+template <typename Real, int DIM>
+__global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, const Real *__restrict__ coef,
+                         const Real *__restrict__ partial, const Real *__restrict__ opartial,
+                         const double *__restrict__ vol, const double *__restrict__ F_old, double *__restrict__ F_new,
+                         double *__restrict__ eps_terms, int *__restrict__ err, int have_old) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    constexpr int NM = n_gas_moments<DIM>();
+    constexpr int MH = 3 - DIM;
+    double S[NM];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) S[k] = 0.0;
+    for (int c = 0; c < n_chunks; ++c) {
+        const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
+#pragma unroll
+        for (int k = 0; k < NM; ++k) S[k] += (double)P[k];
+    }
+    double Ph[1 + DIM];
+#pragma unroll
+    for (int k = 0; k <= DIM; ++k) Ph[k] = 0.0;
+    for (int c = 0; c < o_chunks; ++c) {
+        const Real *P = opartial + ((size_t)i * o_chunks + c) * NMO;
+#pragma unroll
+        for (int k = 0; k <= DIM; ++k) Ph[k] += (double)P[k];
+    }
+    // unpack
+    int k = 0;
+    const double rho = S[k++];
+    double Sc[DIM], Scc[DIM][DIM], Sc3[DIM];
+    for (int a = 0; a < DIM; ++a) Sc[a] = S[k++];
+    for (int a = 0; a < DIM; ++a)
+        for (int b = a; b < DIM; ++b) {
+            Scc[a][b] = S[k];
+            Scc[b][a] = S[k];
+            ++k;
+        }
+    for (int a = 0; a < DIM; ++a) Sc3[a] = S[k++];
+    double H0 = 0.0, Hc[DIM];
+    for (int a = 0; a < DIM; ++a) Hc[a] = 0.0;
+    if (MH > 0) {
+        H0 = S[k++];
+        for (int a = 0; a < DIM; ++a) Hc[a] = S[k++];
+    }
+    const double G1 = S[k++];
+    double G1c[DIM];
+    for (int a = 0; a < DIM; ++a) G1c[a] = S[k++];
+    const double G2 = S[k++];
+    double G2c[DIM];
+    for (int a = 0; a < DIM; ++a) G2c[a] = S[k++];
+
+    double dl[DIM];
+    for (int a = 0; a < DIM; ++a) dl[a] = Sc[a] / rho;
+    // central second moments  P_ab = int (c-d)_a (c-d)_b F0 = Scc_ab - rho d_a d_b
+    double P[DIM][DIM], trP = 0.0;
+    for (int a = 0; a < DIM; ++a)
+        for (int b = 0; b < DIM; ++b) P[a][b] = Scc[a][b] - rho * dl[a] * dl[b];
+    for (int a = 0; a < DIM; ++a) trP += P[a][a];
+    const double int_c2 = trP + H0;                       // int c^2 f0 over all velocity components
+    double *Fn = F_new + (size_t)i * NF;
+    for (int q = 0; q < NF; ++q) Fn[q] = 0.0;
+    const Real *C = coef + (size_t)i * cf::NC;
+    Fn[0] = rho;
+    for (int a = 0; a < DIM; ++a) Fn[1 + a] = (double)C[cf::U + a] + dl[a];
+    const double Tt = int_c2 / (3.0 * rho);
+    Fn[4] = Tt;
+    Fn[5] = 2.0 * G1 / (m.d_r * rho);
+    Fn[6] = 2.0 * G2 / (m.d_v * rho);
+    const double eR = Ph[0];
+    Fn[7] = m.sigma_R > 0.0 ? pow(fmax(eR, 0.0) / (4.0 * m.sigma_R), 0.25) : 0.0;
+    // heat fluxes: q_t,a = 1/2 int (c-d)_a ((c-d)^2 F0 + H0)
+    //   int (c-d)_a |c-d|^2 F0 = Sc3_a - 2 sum_b d_b Scc_ab - d_a trScc + |d|^2 Sc_a
+    //                            + 2 d_a (d . Sc) - rho d_a |d|^2  (Sc = rho d)
+    double trS = 0.0, d2 = 0.0, dSc = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        trS += Scc[a][a];
+        d2 += dl[a] * dl[a];
+        dSc += dl[a] * Sc[a];
+    }
+    for (int a = 0; a < DIM; ++a) {
+        double t = Sc3[a] - dl[a] * trS + d2 * Sc[a] + 2.0 * dl[a] * dSc - rho * dl[a] * d2;
+        for (int b = 0; b < DIM; ++b) t -= 2.0 * dl[b] * Scc[a][b];
+        const double hflux = Hc[a] - dl[a] * H0;
+        Fn[8 + a] = 0.5 * (t + hflux);
+        Fn[11 + a] = G1c[a] - dl[a] * G1;
+        Fn[14 + a] = G2c[a] - dl[a] * G2;
+        Fn[17 + a] = Ph[1 + a];
+    }
+    // stress (xx, yy, zz, xy, xz, yz)
+    double sig[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < DIM; ++a)
+        for (int b = 0; b < DIM; ++b) sig[a][b] = P[a][b];
+    for (int a = DIM; a < 3; ++a) sig[a][a] = MH > 0 ? H0 / MH : 0.0;
+    for (int a = 0; a < 3; ++a) sig[a][a] -= int_c2 / 3.0;
+    Fn[20] = sig[0][0];
+    Fn[21] = sig[1][1];
+    Fn[22] = sig[2][2];
+    Fn[23] = sig[0][1];
+    Fn[24] = sig[0][2];
+    Fn[25] = sig[1][2];
+
+    const bool bad = !(rho > 0.0) || !(Tt > 0.0) || !(Fn[5] > 0.0) || !(Fn[6] > 0.0) || !isfinite(rho) ||
+                     !isfinite(Tt) || !isfinite(Fn[5]) || !isfinite(Fn[6]) || !isfinite(eR);
+    if (bad) atomicOr(err, 1);
+    // convergence terms: (drho^2, rho^2, |du|^2, |u|^2, dT^2, T^2, T) * V
+    const double V = vol[i];
+    const double Ttot = (3.0 * Tt + m.d_r * Fn[5] + m.d_v * Fn[6]) / (3.0 + m.d_r + m.d_v);
+    double *E = eps_terms + (size_t)i * NEPS;
+    if (have_old) {
+        const double *Fo = F_old + (size_t)i * NF;
+        const double To = (3.0 * Fo[4] + m.d_r * Fo[5] + m.d_v * Fo[6]) / (3.0 + m.d_r + m.d_v);
+        double du2 = 0.0, uo2 = 0.0;
+        for (int a = 0; a < DIM; ++a) {
+            du2 += (Fn[1 + a] - Fo[1 + a]) * (Fn[1 + a] - Fo[1 + a]);
+            uo2 += Fo[1 + a] * Fo[1 + a];
+        }
+        E[0] = (rho - Fo[0]) * (rho - Fo[0]) * V;
+        E[1] = Fo[0] * Fo[0] * V;
+        E[2] = du2 * V;
+        E[3] = uo2 * V;
+        E[4] = (Ttot - To) * (Ttot - To) * V;
+        E[5] = To * To * V;
+        E[6] = To * V;
+        E[7] = 0.0;
+    } else {
+        for (int q = 0; q < NEPS; ++q) E[q] = 0.0;
+    }
+}
+
+__global__ void k_eps_reduce(int n_cells, const double *__restrict__ terms, double *__restrict__ sums) {
+    __shared__ double sh[NEPS][256];
+    double acc[NEPS];
+    for (int q = 0; q < NEPS; ++q) acc[q] = 0.0;
+    for (int i = threadIdx.x; i < n_cells; i += blockDim.x)
+        for (int q = 0; q < NEPS; ++q) acc[q] += terms[(size_t)i * NEPS + q];
+    for (int q = 0; q < NEPS; ++q) sh[q][threadIdx.x] = acc[q];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int q = 0; q < NEPS; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int q = 0; q < NEPS; ++q) sums[q] = sh[q][0];
+}
+
+// ------------------------------------------------------------------ equilibrium
+template <typename Real, int DIM>
+__global__ void k_equilibrium(int n_cells, Quad<Real> vq, Quad<Real> oq, ModelDev m, const double *__restrict__ F,
+                              Real *__restrict__ f, Real *__restrict__ I) {
+    const int i = blockIdx.x;
+    const double *M = F + (size_t)i * NF;
+    const double rho = M[0], Tt = M[4];
+    const double norm = rho * pow(6.283185307179586 * Tt, -0.5 * DIM);
+    for (int v = threadIdx.x; v < vq.n_pad; v += blockDim.x) {
+        double c2 = 0.0;
+        for (int a = 0; a < DIM; ++a) {
+            const double c = (double)vq.x[a * vq.n_pad + v] - M[1 + a];
+            c2 += c * c;
+        }
+        const double F0 = norm * exp(-c2 / (2.0 * Tt));
+        Vec<Real, 4> t;
+        t.v[0] = (Real)F0;
+        t.v[1] = (Real)((3 - DIM) * Tt * F0);
+        t.v[2] = (Real)(0.5 * m.d_r * M[5] * F0);
+        t.v[3] = (Real)(0.5 * m.d_v * M[6] * F0);
+        vstore<Real, 4>(f + ((size_t)i * vq.n_pad + v) * 4, t);
+    }
+    const double B = m.sigma_R * M[7] * M[7] * M[7] * M[7] / 3.141592653589793;
+    for (int o = threadIdx.x; o < oq.n_pad; o += blockDim.x) I[(size_t)i * oq.n_pad + o] = (Real)B;
+}
+
+// ------------------------------------------------------------------ launchers
+#define GSIS_DISPATCH_DIM(dim, ...)                    \
+    switch (dim) {                                     \
+        case 1: { constexpr int DIM = 1; __VA_ARGS__; } break; \
+        case 2: { constexpr int DIM = 2; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;         \
+    }
+
+template <typename Real>
+cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, const ModelDev &m, const double *fields,
+                                const double *cell_dx, Real *coef) {
+    const int nt = 128, nbk = (g.n_cells + nt - 1) / nt;
+    GSIS_DISPATCH_DIM(dim, (k_coefficients<Real, DIM><<<nbk, nt, 0, s>>>(g, m, fields, cell_dx, coef)));
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
+                                const double *patch_T, const double *patch_u, const int *patch_kind, const Real *f,
+                                Real *bcoef) {
+    if (g.n_bf == 0) return cudaSuccess;
+    const int nt = 256, nbk = (g.n_bf * 32 + nt - 1) / nt;
+    GSIS_DISPATCH_DIM(dim, (k_wall_density<Real, DIM><<<nbk, nt, 0, s>>>(g, vq, patch_T, patch_u, patch_kind, f, bcoef)));
+    return cudaGetLastError();
+}
+
+template <typename Real, int DIM, int ORDER>
+static cudaError_t sweep_gas_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &vq, const Real *coef,
+                               const Real *bcoef, const Real *f_in, Real *f_out, Real *partial) {
+    const size_t smem = (size_t)g.block * VCH * sizeof(Vec<Real, 4>) + (DIM + 1) * VCH * sizeof(Real);
+    auto kern = k_sweep_gas<Real, DIM, ORDER>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.n_cells + g.block - 1) / g.block, vq.n_pad / VCH);
+    kern<<<grid, VCH, smem, s>>>(g, vq, coef, bcoef, f_in, f_out, partial);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
+                             const Real *coef, const Real *bcoef, const Real *f_in, Real *f_out, Real *partial) {
+    if (order == 1) {
+        GSIS_DISPATCH_DIM(dim, return (sweep_gas_t<Real, DIM, 1>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
+    } else {
+        GSIS_DISPATCH_DIM(dim, return (sweep_gas_t<Real, DIM, 2>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename Real, int DIM, int ORDER>
+static cudaError_t sweep_photon_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &oq, const Real *coef,
+                                  const Real *bcoef, const Real *I_in, Real *I_out, Real *partial) {
+    const size_t smem = (size_t)g.block * OCH * sizeof(Real) + (DIM + 1) * OCH * sizeof(Real);
+    auto kern = k_sweep_photon<Real, DIM, ORDER>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((g.n_cells + g.block - 1) / g.block, oq.n_pad / OCH);
+    kern<<<grid, OCH, smem, s>>>(g, oq, coef, bcoef, I_in, I_out, partial);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
+                                const Real *coef, const Real *bcoef, const Real *I_in, Real *I_out, Real *partial) {
+    if (order == 1) {
+        GSIS_DISPATCH_DIM(dim, return (sweep_photon_t<Real, DIM, 1>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
+    } else {
+        GSIS_DISPATCH_DIM(dim, return (sweep_photon_t<Real, DIM, 2>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename Real>
+cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const ModelDev &m,
+                          const Real *coef, const Real *partial, const Real *opartial, const double *vol,
+                          const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
+                          int have_old) {
+    const int nt = 128, nbk = (n_cells + nt - 1) / nt;
+    GSIS_DISPATCH_DIM(dim, (k_finish<Real, DIM><<<nbk, nt, 0, s>>>(n_cells, n_chunks, o_chunks, m, coef, partial,
+                                                                    opartial, vol, fields_old, fields_new, eps_terms,
+                                                                    err_flag, have_old)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_sums) {
+    k_eps_reduce<<<1, 256, 0, s>>>(n_cells, eps_terms, eps_sums);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+                               const ModelDev &m, const double *fields, Real *f, Real *I) {
+    GSIS_DISPATCH_DIM(dim, (k_equilibrium<Real, DIM><<<n_cells, 256, 0, s>>>(n_cells, vq, oq, m, fields, f, I)));
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+                                const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial) {
+    dim3 gg((n_cells + VCH / 32 - 1) / (VCH / 32), vq.n_pad / VCH);
+    dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
+    GSIS_DISPATCH_DIM(dim, (k_moments_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, coef, f, partial)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    GSIS_DISPATCH_DIM(dim, (k_moments_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, I, opartial)));
+    return cudaGetLastError();
+}
+
+#define GSIS_INSTANTIATE(Real)                                                                                     \
+    template cudaError_t launch_coefficients<Real>(cudaStream_t, int, const Geom<Real> &, const ModelDev &,        \
+                                                   const double *, const double *, Real *);                        \
+    template cudaError_t launch_wall_density<Real>(cudaStream_t, int, const Geom<Real> &, const Quad<Real> &,     \
+                                                   const double *, const double *, const int *, const Real *,      \
+                                                   Real *);                                                        \
+    template cudaError_t launch_sweep_gas<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,    \
+                                                const Real *, const Real *, const Real *, Real *, Real *);         \
+    template cudaError_t launch_sweep_photon<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &, \
+                                                   const Real *, const Real *, const Real *, Real *, Real *);      \
+    template cudaError_t launch_finish<Real>(cudaStream_t, int, int, int, int, const ModelDev &, const Real *,     \
+                                             const Real *, const Real *, const double *, const double *, double *, \
+                                             double *, int *, int);                                                \
+    template cudaError_t launch_equilibrium<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &,  \
+                                                  const ModelDev &, const double *, Real *, Real *);               \
+    template cudaError_t launch_moments_only<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &, \
+                                                   const Real *, const Real *, const Real *, Real *, Real *);
+
+GSIS_INSTANTIATE(float)
+GSIS_INSTANTIATE(double)
+
+}  // namespace gsis

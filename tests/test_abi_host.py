@@ -1,0 +1,78 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every entry
+point that include/gsis.h declares; argument validation runs before any device call."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import gsis_inputs as gi
+from paper_2601_03935_gb300 import build
+from paper_2601_03935_gb300 import gsis as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return G.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "gsis.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gsis_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    assert "gsis_create" in names and "gsis_step" in names and len(names) >= 15
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_strerror_names_codes(lib):
+    assert lib.gsis_strerror(0) == b"ok"
+    assert b"unsupported" in lib.gsis_strerror(G.GSIS_ERR_UNSUPPORTED)
+    assert lib.gsis_strerror(12345) == b"unknown status"
+
+
+def _args(wl):
+    m = wl.mesh
+    return (m.dim, m.face_owner, m.face_nbr, m.face_normal, m.face_area, m.face_centroid, m.cell_volume,
+            m.cell_centroid, m.patches, wl.xi[:, :m.dim], wl.w, wl.omega, wl.wo, wl.model, wl.solver)
+
+
+def test_validation_rejects_before_touching_the_device(lib):
+    wl = gi.workloads.slab(n_cells=8)
+    bad = gi.workloads.with_solver(wl, order=3)
+    with pytest.raises(G.GsisError) as e:
+        G.gsis_create(*_args(bad))
+    assert e.value.code == G.GSIS_ERR_INVALID_ARG
+    bad = gi.workloads.with_solver(wl, relax_block=65)
+    with pytest.raises(G.GsisError) as e:
+        G.gsis_create(*_args(bad))
+    assert e.value.code == G.GSIS_ERR_INVALID_ARG
+    bad = gi.workloads.with_model(wl, Kn=-1.0)
+    with pytest.raises(G.GsisError) as e:
+        G.gsis_create(*_args(bad))
+    assert e.value.code == G.GSIS_ERR_INVALID_ARG
+    args = list(_args(wl))
+    args[0] = 3
+    with pytest.raises(G.GsisError) as e:
+        G.gsis_create(*args)
+    assert e.value.code == G.GSIS_ERR_UNSUPPORTED
+    out = C.c_void_p()
+    assert lib.gsis_create(None, None, None, None, None, None, C.byref(out)) == G.GSIS_ERR_INVALID_ARG
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.gsis_step(None, 0, None) == G.GSIS_ERR_INVALID_ARG
+    assert lib.gsis_get_fields(None, None, 0) == G.GSIS_ERR_INVALID_ARG
+    assert lib.gsis_launch_count(None) == 0
+    lib.gsis_destroy(None)

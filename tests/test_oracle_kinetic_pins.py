@@ -174,7 +174,7 @@ def test_moments_of_maxwellian():
 def test_gas_photon_energy_exchange_balances():
     """int (f2 source) dxi + int (photon source) dOmega = 0 up to the gas relaxation,
     which conserves energy by itself (Eq. kinetic_equation, Eq. macroscopic_equation)."""
-    wl = gi.workloads.cavity(n_side=2, n_v=40)
+    wl = gi.workloads.cavity(n_side=2, n_v=40, Kn_p=1.0)
     wl.xi, wl.w = _fine_grid(2, n=64, L=12.0)
     M = gi.fields.random_macro_fields(wl.mesh.n_cells, 2, seed=15, u_scale=0.3)
     f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 2, 2.0, 1.16, wl.model.sigma_R, seed=16)
