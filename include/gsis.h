@@ -204,6 +204,35 @@ int64_t gsis_launch_count(const gsis_ctx *ctx);
 int gsis_get_layout(const gsis_ctx *ctx, int32_t *v_pad, int32_t *o_pad, int32_t *n_chunks,
                     int32_t *block);
 
+/* Allocation-free velocity moments (the paper has no counterpart: this serves callers
+ * that cannot allocate device memory, e.g. a host framework that owns the whole device
+ * heap through its own pool allocator, or a plugin that may only use the buffers it is
+ * handed; such callers cannot create a context, because gsis_create allocates).
+ *
+ * Computes the per-cell field record (GSIS_NF doubles: rho, u, T_t, T_r, T_v, T_R, heat
+ * fluxes, stress; the moments of Eq. getmoment) of DEVICE-resident distributions:
+ *   xi [n_xi][dim], w [n_xi], omega [n_omega][3], wo [n_omega]   doubles, device
+ *   f  [n_cells][n_xi][4] planes [F0, H0, f1, f2], I [n_cells][n_omega]  in the
+ *      storage type of `precision` (float for GSIS_FP32, double for GSIS_FP64), device
+ *   fields [n_cells][GSIS_NF] doubles, device (output)
+ * on cuda_stream (NULL: the legacy default stream); the call returns after queueing.
+ *
+ * It calls no cudaMalloc/cudaFree and no allocating library routine.  Its partial sums
+ * live in one 32 MiB file-scope device array that every GPU loading the library holds
+ * until the process exits; sizes whose partials do not fit,
+ *   (n_cells * ceil(n_xi/128) * 20 + n_cells * ceil(n_omega/128) * 4) * sizeof(storage)
+ *   > 32 MiB,
+ * are rejected with GSIS_ERR_INVALID_ARG before anything is launched.  The first call on
+ * a device looks up the array's device address (with that device current); make that
+ * first call before any stream capture.  All calls share the array: calls whose kernels
+ * overlap on one GPU race on it.
+ * Errors: INVALID_ARG (null pointer, non-positive size, too large), UNSUPPORTED (dim 3),
+ * CUDA (address lookup or launch failure). */
+int gsis_moments_static(int32_t dim, int32_t precision, int64_t n_cells, int32_t n_xi, const double *xi,
+                        const double *w, int32_t n_omega, const double *omega, const double *wo,
+                        const void *f, const void *I, double d_r, double d_v, double sigma_R, double *fields,
+                        void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,8 @@ def load():
                                         C.POINTER(C.c_int32)]),
         "gsis_launch_count": (C.c_int64, [vp]),
         "gsis_get_layout": (C.c_int, [vp, _ip, _ip, _ip, _ip]),
+        "gsis_moments_static": (C.c_int, [C.c_int32, C.c_int32, C.c_int64, C.c_int32, vp, vp, C.c_int32, vp, vp,
+                                          vp, vp, C.c_double, C.c_double, C.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,3 +255,12 @@ def gsis_get_layout(ctx):
     v = [C.c_int32() for _ in range(4)]
     _check(load().gsis_get_layout(ctx, *[C.byref(x) for x in v]), ctx)
     return dict(v_pad=v[0].value, o_pad=v[1].value, n_chunks=v[2].value, block=v[3].value)
+
+
+def gsis_moments_static(dim, precision, n_cells, n_xi, xi_ptr, w_ptr, n_omega, omega_ptr, wo_ptr, f_ptr, I_ptr,
+                        d_r, d_v, sigma_R, fields_ptr, stream=0):
+    """Allocation-free moments of device-resident distributions (all pointers are device
+    addresses as ints); returns the status code."""
+    prec = {"fp32": GSIS_FP32, "fp64": GSIS_FP64}.get(precision, precision)
+    return load().gsis_moments_static(dim, prec, n_cells, n_xi, xi_ptr, w_ptr, n_omega, omega_ptr, wo_ptr, f_ptr,
+                                      I_ptr, d_r, d_v, sigma_R, fields_ptr, stream)
