@@ -37,11 +37,10 @@ struct gsis_ctx {
     double *fields = nullptr, *fields_old = nullptr, *eps_terms = nullptr, *eps_sums = nullptr;
     int *err = nullptr;
     double *vol = nullptr, *cell_dx = nullptr;
-    int *g_nf = nullptr, *g_nbr = nullptr, *bf_cell = nullptr, *bf_patch = nullptr, *g_nst = nullptr,
-        *g_stn = nullptr;
-    signed char *g_local = nullptr;
-    void *g_nrm = nullptr, *g_sv = nullptr, *g_dxf = nullptr, *g_dxn = nullptr, *g_lsq = nullptr,
-         *g_eps2 = nullptr, *bf_nrm = nullptr;
+    int *bf_cell = nullptr, *bf_patch = nullptr, *g_stn = nullptr;
+    int4 *g_info = nullptr;
+    int2 *g_fnb = nullptr;
+    void *g_fgeo = nullptr, *g_lsq = nullptr, *g_eps2 = nullptr, *bf_nrm = nullptr;
     void *vq_x = nullptr, *vq_w = nullptr, *oq_x = nullptr, *oq_w = nullptr;
     double *patch_T = nullptr, *patch_u = nullptr;
     int *patch_kind = nullptr;
@@ -116,14 +115,9 @@ Geom<Real> geom(const gsis_ctx *c) {
     g.n_cells = (int)c->nc;
     g.dim = c->dim;
     g.block = c->block;
-    g.nf = c->g_nf;
-    g.nbr = c->g_nbr;
-    g.local = c->g_local;
-    g.nrm = (const Real *)c->g_nrm;
-    g.sv = (const Real *)c->g_sv;
-    g.dxf = (const Real *)c->g_dxf;
-    g.dxn = (const Real *)c->g_dxn;
-    g.nst = c->g_nst;
+    g.info = c->g_info;
+    g.fnb = c->g_fnb;
+    g.fgeo = (const Real *)c->g_fgeo;
     g.stn = c->g_stn;
     g.lsq = (const Real *)c->g_lsq;
     g.eps2 = (const Real *)c->g_eps2;
@@ -471,31 +465,45 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     }
     c->n_bf = (int)bf_cell.size();
     // least-squares weights C_ij = (sum_k d_k d_k^T)^-1 d_j over the stencil of face
-    // neighbours and their face neighbours; a zero gradient where the normal matrix is
-    // singular (det <= 1e-10 (tr/dim)^dim)
-    std::vector<double> lsq(nc * MAXS * 3, 0.0), eps2(nc), cdx(nc), vol(nc);
-    std::vector<int> nst(nc, 0), stn(nc * MAXS, 0);
-    std::vector<signed char> local(nc * MAXF, -1);
+    // neighbours and their face neighbours (interior face neighbours first); a zero
+    // gradient where the normal matrix is singular (det <= 1e-10 (tr/dim)^dim)
+    std::vector<double> lsq(nc * MAXS * 2, 0.0), eps2(nc), cdx(nc), vol(nc), fgeo(nc * MAXF * fr::SIZE, 0.0);
+    std::vector<int> stn(nc * MAXS, 0), info(nc * 4, 0), fnb(nc * MAXF * 2, -1);
     for (int64_t i = 0; i < nc; ++i) {
         vol[i] = m->cell_volume[i];
         cdx[i] = std::pow(vol[i], 1.0 / dim);
         const double Kdx = sp->venkat_K * cdx[i];
         eps2[i] = Kdx * Kdx * Kdx;
-        std::vector<int> st;
+        std::vector<int> first, rest;
         for (int k = 0; k < nf[i]; ++k) {
             const int j = nbr[i * MAXF + k];
+            double *F = &fgeo[((size_t)i * MAXF + k) * fr::SIZE];
+            F[fr::NX] = nrm[(i * MAXF + k) * 3 + 0];
+            F[fr::NY] = dim > 1 ? nrm[(i * MAXF + k) * 3 + 1] : 0.0;
+            F[fr::SV] = sv[i * MAXF + k];
+            F[fr::DFX] = dxf[(i * MAXF + k) * 3 + 0];
+            F[fr::DFY] = dim > 1 ? dxf[(i * MAXF + k) * 3 + 1] : 0.0;
+            fnb[(i * MAXF + k) * 2 + 0] = j;
             if (j < 0) continue;
-            if (j / c->block == i / c->block) local[i * MAXF + k] = (signed char)(j - (i / c->block) * c->block);
-            st.push_back(j);
+            F[fr::SVN] = m->face_area[face_of[i * MAXF + k]] / m->cell_volume[j];
+            F[fr::DNX] = dxn[(i * MAXF + k) * 3 + 0];
+            F[fr::DNY] = dim > 1 ? dxn[(i * MAXF + k) * 3 + 1] : 0.0;
+            if (j / c->block == i / c->block) fnb[(i * MAXF + k) * 2 + 1] = (int)(j - (i / c->block) * c->block);
+            if (std::find(first.begin(), first.end(), j) == first.end()) first.push_back(j);
+        }
+        for (int j : first)
             for (int k2 = 0; k2 < nf[j]; ++k2) {
                 const int j2 = nbr[j * MAXF + k2];
-                if (j2 >= 0 && j2 != i) st.push_back(j2);
+                if (j2 >= 0 && j2 != i && std::find(first.begin(), first.end(), j2) == first.end()) rest.push_back(j2);
             }
-        }
-        std::sort(st.begin(), st.end());
-        st.erase(std::unique(st.begin(), st.end()), st.end());
+        std::sort(rest.begin(), rest.end());
+        rest.erase(std::unique(rest.begin(), rest.end()), rest.end());
+        std::vector<int> st(first);
+        st.insert(st.end(), rest.begin(), rest.end());
         if ((int)st.size() > MAXS) return bail(fail(c, GSIS_ERR_UNSUPPORTED, "least-squares stencil larger than 12"));
-        nst[i] = (int)st.size();
+        info[i * 4 + 0] = nf[i];
+        info[i * 4 + 1] = (int)st.size();
+        info[i * 4 + 2] = (int)first.size();
         for (size_t k = 0; k < st.size(); ++k) stn[i * MAXS + k] = st[k];
         if ((int)st.size() < dim) continue;
         double G[2][2] = {{0, 0}, {0, 0}};
@@ -525,7 +533,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             for (int a = 0; a < dim; ++a) {
                 double s = 0.0;
                 for (int b = 0; b < dim; ++b) s += Gi[a][b] * d[b];
-                lsq[(i * MAXS + k) * 3 + a] = s;
+                lsq[(i * MAXS + k) * 2 + a] = s;
             }
         }
     }
@@ -585,17 +593,12 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc(c, &c->err, 1));
     A_(dalloc(c, &c->vol, nc));
     A_(dalloc(c, &c->cell_dx, nc));
-    A_(dalloc(c, &c->g_nf, nc));
-    A_(dalloc(c, &c->g_nbr, nc * MAXF));
-    A_(dalloc(c, &c->g_local, nc * MAXF));
+    A_(dalloc(c, &c->g_info, nc));
+    A_(dalloc(c, &c->g_fnb, nc * MAXF));
     A_(dalloc(c, &c->bf_cell, std::max(c->n_bf, 1)));
     A_(dalloc(c, &c->bf_patch, std::max(c->n_bf, 1)));
-    A_(dalloc_real(c, &c->g_nrm, nc * MAXF * 3));
-    A_(dalloc_real(c, &c->g_sv, nc * MAXF));
-    A_(dalloc_real(c, &c->g_dxf, nc * MAXF * 3));
-    A_(dalloc_real(c, &c->g_dxn, nc * MAXF * 3));
-    A_(dalloc_real(c, &c->g_lsq, nc * MAXS * 3));
-    A_(dalloc(c, &c->g_nst, nc));
+    A_(dalloc_real(c, &c->g_fgeo, nc * MAXF * fr::SIZE));
+    A_(dalloc_real(c, &c->g_lsq, nc * MAXS * 2));
     A_(dalloc(c, &c->g_stn, nc * MAXS));
     A_(dalloc_real(c, &c->g_eps2, nc));
     A_(dalloc_real(c, &c->bf_nrm, 3 * std::max(c->n_bf, 1)));
@@ -612,17 +615,12 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     if (bf_cell.empty()) { bf_cell.push_back(0); bf_patch.push_back(0); }
     A_(upload(c, c->vol, vol));
     A_(upload(c, c->cell_dx, cdx));
-    A_(upload(c, c->g_nf, nf));
-    A_(upload(c, c->g_nbr, nbr));
-    A_(upload(c, c->g_local, local));
-    A_(upload(c, c->g_nst, nst));
+    CUDA_TRY(c, cudaMemcpy(c->g_info, info.data(), info.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->g_fnb, fnb.data(), fnb.size() * sizeof(int), cudaMemcpyHostToDevice));
     A_(upload(c, c->g_stn, stn));
     A_(upload(c, c->bf_cell, bf_cell));
     A_(upload(c, c->bf_patch, bf_patch));
-    A_(upload_real(c, c->g_nrm, nrm));
-    A_(upload_real(c, c->g_sv, sv));
-    A_(upload_real(c, c->g_dxf, dxf));
-    A_(upload_real(c, c->g_dxn, dxn));
+    A_(upload_real(c, c->g_fgeo, fgeo));
     A_(upload_real(c, c->g_lsq, lsq));
     A_(upload_real(c, c->g_eps2, eps2));
     A_(upload_real(c, c->bf_nrm, bfn));

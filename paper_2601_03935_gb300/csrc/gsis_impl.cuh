@@ -16,20 +16,22 @@ constexpr int NMO = 4;         // stride of per-(cell, chunk) photon moment part
 constexpr int MAXB = 64;       // largest relaxation block
 constexpr int NEPS = 8;        // per-cell terms of the convergence measure
 
-// ---- per-cell coefficient record (Real), built from the FP64 fields each iteration
-// u[3] | per Maxwellian a in {t, tr, tv}: A, B, T, Q[3], K1, K2, R1[3], R2[3] (14) |
-// rate (1/tau) | inv_dt | sink | photon source g_R | photon rate k_eff
+// ---- per-cell coefficient record (Real), built from the FP64 fields each iteration,
+// laid out for 16-byte vector loads:
+// u[3], pad | per Maxwellian a in {t, tr, tv} (16 each): A, B, T, K1 | Q[3], K2 |
+// R1[3], pad | R2[3], pad | rate (1/tau), inv_dt, sink, photon source g_R |
+// photon rate k_eff, pad[3]
 namespace cf {
 constexpr int U = 0;
-constexpr int COMP = 3;        // first component block
-constexpr int CSZ = 14;        // size of one component block
-constexpr int A = 0, B = 1, T = 2, Q = 3, K1 = 6, K2 = 7, R1 = 8, R2 = 11;
-constexpr int RATE = COMP + 3 * CSZ;   // 45
+constexpr int COMP = 4;        // first component block
+constexpr int CSZ = 16;        // size of one component block
+constexpr int A = 0, B = 1, T = 2, K1 = 3, Q = 4, K2 = 7, R1 = 8, R2 = 12;
+constexpr int RATE = COMP + 3 * CSZ;   // 52
 constexpr int INV_DT = RATE + 1;
 constexpr int SINK = RATE + 2;
 constexpr int GR = RATE + 3;
 constexpr int KEFF = RATE + 4;
-constexpr int NC = 52;         // padded record length
+constexpr int NC = 60;         // record length (multiple of 4)
 }  // namespace cf
 
 // ---- per-boundary-face record (Real): incoming state
@@ -42,19 +44,21 @@ constexpr int IIN = 9;         // incoming photon intensity
 constexpr int NB = 12;
 }  // namespace bc
 
+// Per cell-face record (Real x 8): outward normal (x, y), S/V of this cell, S/V of the
+// neighbour (0 on the boundary), face centroid - cell centroid (x, y), face centroid -
+// neighbour centroid (x, y).  Up to two spatial dimensions.
+namespace fr {
+constexpr int NX = 0, NY = 1, SV = 2, SVN = 3, DFX = 4, DFY = 5, DNX = 6, DNY = 7, SIZE = 8;
+}
+
 template <typename Real>
 struct Geom {
     int n_cells, dim, block;
-    const int *nf;             // [nc]
-    const int *nbr;            // [nc][MAXF]: >= 0 cell, < 0: -1 - boundary face index
-    const signed char *local;  // [nc][MAXF]: neighbour's index inside the cell's block, or -1
-    const Real *nrm;           // [nc][MAXF][3] outward unit normal
-    const Real *sv;            // [nc][MAXF] face area / cell volume
-    const Real *dxf;           // [nc][MAXF][3] face centroid - cell centroid
-    const Real *dxn;           // [nc][MAXF][3] face centroid - neighbour centroid
-    const int *nst;            // [nc] stencil size
-    const int *stn;            // [nc][MAXS] stencil cells
-    const Real *lsq;           // [nc][MAXS][3] least-squares weights of the stencil cells
+    const int4 *info;          // [nc]: faces, stencil size, face neighbours leading the stencil, -
+    const int2 *fnb;           // [nc][MAXF]: neighbour (>= 0 cell, < 0: -1 - boundary face), in-block index or -1
+    const Real *fgeo;          // [nc][MAXF][fr::SIZE]
+    const int *stn;            // [nc][MAXS] stencil cells, interior face neighbours first
+    const Real *lsq;           // [nc][MAXS][2] least-squares weights of the stencil cells
     const Real *eps2;          // [nc] (K dx)^3
     int n_bf;
     const int *bf_cell;        // [n_bf]

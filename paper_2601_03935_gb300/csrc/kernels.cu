@@ -158,22 +158,33 @@ __device__ __forceinline__ V<Real, N> ldv(const Real *base, size_t idx) {
     }
     return r;
 }
-template <typename Real, int N>
-__device__ __forceinline__ void stv(Real *base, size_t idx, const V<Real, N> &a) {
-    if constexpr (N == 1) {
-        base[idx] = a.x[0];
-    } else {
-        Vec<Real, N> t;
-#pragma unroll
-        for (int p = 0; p < N; ++p) t.v[p] = a.x[p];
-        vstore<Real, N>(base + idx * N, t);
-    }
+
+template <typename Real>
+struct Face {
+    Real n[2], sv, svn, df[2], dn[2];
+};
+
+template <typename Real>
+__device__ __forceinline__ Face<Real> load_face(const Real *__restrict__ fgeo, int c, int k) {
+    const Real *p = fgeo + ((size_t)c * MAXF + k) * fr::SIZE;
+    const Vec<Real, 4> a = vload<Real, 4>(p), b = vload<Real, 4>(p + 4);
+    Face<Real> F;
+    F.n[0] = a.v[0];
+    F.n[1] = a.v[1];
+    F.sv = a.v[2];
+    F.svn = a.v[3];
+    F.df[0] = b.v[0];
+    F.df[1] = b.v[1];
+    F.dn[0] = b.v[2];
+    F.dn[1] = b.v[3];
+    return F;
 }
 
 // Venkatakrishnan-limited least-squares slope of cell j at one discrete velocity:
 // grad = sum_s C_js (f_s - f_j) over the stencil (face neighbours and their face
 // neighbours); phi = min(1, min_faces phi_V(Delta_1, Delta_2)) per plane with the
-// bounds Delta_max/min taken over the face neighbours.  Returns the slope times phi.
+// bounds Delta_max/min taken over the interior face neighbours (the first entries of
+// the stencil).  Returns the slope multiplied by phi.
 template <typename Real, int N, int DIM>
 __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *__restrict__ f, int stride, int j,
                                               int v, const V<Real, N> &fj, V<Real, N> (&slope)[DIM]) {
@@ -185,46 +196,38 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
 #pragma unroll
         for (int d = 0; d < DIM; ++d) slope[d].x[p] = Real(0);
     }
-    const int ns = g.nst[j];
+    const int4 info = g.info[j];
+    const int ns = info.y, nfn = info.z;
     for (int k = 0; k < ns; ++k) {
         const int s = g.stn[j * MAXS + k];
         const V<Real, N> fs = ldv<Real, N>(f, (size_t)s * stride + v);
-        Real c[DIM];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) c[d] = g.lsq[(j * MAXS + k) * 3 + d];
+        const Real *w = g.lsq + ((size_t)j * MAXS + k) * 2;
+        const Real c0 = w[0], c1 = DIM > 1 ? w[1] : Real(0);
+        const bool face_nbr = k < nfn;
 #pragma unroll
         for (int p = 0; p < N; ++p) {
             const Real dq = fs.x[p] - fj.x[p];
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) slope[d].x[p] = fma(c[d], dq, slope[d].x[p]);
-        }
-    }
-    const int nf = g.nf[j];
-    for (int k = 0; k < nf; ++k) {
-        const int nb = g.nbr[j * MAXF + k];
-        if (nb < 0) continue;
-        const V<Real, N> fk = ldv<Real, N>(f, (size_t)nb * stride + v);
-#pragma unroll
-        for (int p = 0; p < N; ++p) {
-            const Real dq = fk.x[p] - fj.x[p];
-            dmax.x[p] = fmax(dmax.x[p], dq);
-            dmin.x[p] = fmin(dmin.x[p], dq);
+            if (face_nbr) {
+                dmax.x[p] = fmax(dmax.x[p], dq);
+                dmin.x[p] = fmin(dmin.x[p], dq);
+            }
+            slope[0].x[p] = fma(c0, dq, slope[0].x[p]);
+            if constexpr (DIM > 1) slope[1].x[p] = fma(c1, dq, slope[1].x[p]);
         }
     }
     const Real eps2 = g.eps2[j];
     V<Real, N> phi;
 #pragma unroll
     for (int p = 0; p < N; ++p) phi.x[p] = Real(1);
+    const int nf = info.x;
     for (int k = 0; k < nf; ++k) {
-        if (g.nbr[j * MAXF + k] < 0) continue;
-        Real dx[DIM];
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) dx[d] = g.dxf[(j * MAXF + k) * 3 + d];
+        if (g.fnb[j * MAXF + k].x < 0) continue;
+        const Real *q = g.fgeo + ((size_t)j * MAXF + k) * fr::SIZE + fr::DFX;
+        const Real dx0 = q[0], dx1 = DIM > 1 ? q[1] : Real(0);
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-            Real d2 = Real(0);
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) d2 = fma(slope[d].x[p], dx[d], d2);
+            Real d2 = slope[0].x[p] * dx0;
+            if constexpr (DIM > 1) d2 = fma(slope[1].x[p], dx1, d2);
             const Real d1 = d2 > Real(0) ? dmax.x[p] : dmin.x[p];
             const Real num = fma(d1, d1 + Real(2) * d2, eps2);
             const Real den = fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2));
@@ -238,102 +241,31 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
         for (int p = 0; p < N; ++p) slope[d].x[p] *= phi.x[p];
 }
 
-// Residual r = source - (1/V) sum_faces S (xi_n^+ f_L + xi_n^- f_R) of one (cell, velocity);
-// the source is passed in.  Also returns d = inv_dt + rate + (1/V) sum S xi_n^+.
-template <typename Real, int N, int DIM, int ORDER>
-__device__ __forceinline__ void transport_residual(const Geom<Real> &g, const Real *__restrict__ f, int stride,
-                                                   const Real *__restrict__ bcoef, int i, int v, const Real *xi,
-                                                   const V<Real, N> &fi, V<Real, N> &r, Real &d, bool photon) {
-    V<Real, N> slope_i[DIM];
-    if constexpr (ORDER == 2) limited_slope<Real, N, DIM>(g, f, stride, i, v, fi, slope_i);
-    const int nf = g.nf[i];
-    for (int k = 0; k < nf; ++k) {
-        const int fk = i * MAXF + k;
-        const int nb = g.nbr[fk];
-        Real xn = Real(0);
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) xn = fma(xi[a], g.nrm[fk * 3 + a], xn);
-        const Real sv = g.sv[fk];
-        V<Real, N> face;
-        if (xn > Real(0)) {
-            d = fma(sv, xn, d);
-            face = fi;
-            if constexpr (ORDER == 2) {
-                if (nb >= 0) {
-#pragma unroll
-                    for (int a = 0; a < DIM; ++a) {
-                        const Real dx = g.dxf[fk * 3 + a];
-#pragma unroll
-                        for (int p = 0; p < N; ++p) face.x[p] = fma(slope_i[a].x[p], dx, face.x[p]);
-                    }
-                }
-            }
-        } else if (xn < Real(0)) {
-            if (nb >= 0) {
-                face = ldv<Real, N>(f, (size_t)nb * stride + v);
-                if constexpr (ORDER == 2) {
-                    V<Real, N> slope_j[DIM];
-                    limited_slope<Real, N, DIM>(g, f, stride, nb, v, face, slope_j);
-#pragma unroll
-                    for (int a = 0; a < DIM; ++a) {
-                        const Real dx = g.dxn[fk * 3 + a];
-#pragma unroll
-                        for (int p = 0; p < N; ++p) face.x[p] = fma(slope_j[a].x[p], dx, face.x[p]);
-                    }
-                }
-            } else {
-                const Real *B = bcoef + (size_t)(-1 - nb) * bc::NB;
-                if (photon) {
-                    face.x[0] = B[bc::IIN];
-                } else {
-                    Real c2 = Real(0);
-#pragma unroll
-                    for (int a = 0; a < DIM; ++a) {
-                        const Real c = xi[a] - B[bc::U + a];
-                        c2 = fma(c, c, c2);
-                    }
-                    const Real E = B[bc::A] * fexp(-B[bc::B] * c2);
-                    if constexpr (N == 4) {
-                        face.x[0] = E * B[bc::M0];
-                        face.x[1] = E * B[bc::MH];
-                        face.x[2] = E * B[bc::M1];
-                        face.x[3] = E * B[bc::M2];
-                    } else {
-                        face.x[0] = E;
-                    }
-                }
-            }
-        } else {
-            continue;
-        }
-        const Real s = sv * xn;
-#pragma unroll
-        for (int p = 0; p < N; ++p) r.x[p] = fma(-s, face.x[p], r.x[p]);
-    }
-}
-
 // Reference distribution of the four gas planes at one (cell, velocity).
 template <typename Real, int DIM>
 __device__ __forceinline__ void reference(const Real *__restrict__ C, const Real *xi, Real (&gp)[4]) {
     constexpr int MH = 3 - DIM;
+    const Vec<Real, 4> u4 = vload<Real, 4>(C + cf::U);
     Real c[DIM], c2 = Real(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        c[a] = xi[a] - C[cf::U + a];
+        c[a] = xi[a] - u4.v[a];
         c2 = fma(c[a], c[a], c2);
     }
     gp[0] = gp[1] = gp[2] = gp[3] = Real(0);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const Real *Ck = C + cf::COMP + k * cf::CSZ;
-        const Real Bk = Ck[cf::B], T = Ck[cf::T];
-        const Real E = Ck[cf::A] * fexp(-Bk * c2);
+        const Vec<Real, 4> a0 = vload<Real, 4>(Ck), a1 = vload<Real, 4>(Ck + 4), a2 = vload<Real, 4>(Ck + 8),
+                           a3 = vload<Real, 4>(Ck + 12);
+        const Real A = a0.v[0], Bk = a0.v[1], T = a0.v[2], K1 = a0.v[3], K2 = a1.v[3];
+        const Real E = A * fexp(-Bk * c2);
         Real qc = Real(0), r1 = Real(0), r2 = Real(0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            qc = fma(Ck[cf::Q + a], c[a], qc);
-            r1 = fma(Ck[cf::R1 + a], c[a], r1);
-            r2 = fma(Ck[cf::R2 + a], c[a], r2);
+            qc = fma(a1.v[a], c[a], qc);
+            r1 = fma(a2.v[a], c[a], r1);
+            r2 = fma(a3.v[a], c[a], r2);
         }
         const Real p0 = fma(qc, fma(c2 + Real(MH) * T, Bk, Real(-2.5)), Real(1));
         gp[0] = fma(E, p0, gp[0]);
@@ -341,8 +273,8 @@ __device__ __forceinline__ void reference(const Real *__restrict__ C, const Real
             const Real ph = fma(qc, fma(c2 + Real(MH + 2) * T, Bk, Real(-2.5)), Real(1));
             gp[1] = fma(E * (Real(MH) * T), ph, gp[1]);
         }
-        gp[2] = fma(E, fma(Ck[cf::K1], p0, r1), gp[2]);
-        gp[3] = fma(E, fma(Ck[cf::K2], p0, r2), gp[3]);
+        gp[2] = fma(E, fma(K1, p0, r1), gp[2]);
+        gp[3] = fma(E, fma(K2, p0, r2), gp[3]);
     }
 }
 
@@ -379,247 +311,265 @@ __device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Rea
     }
 }
 
-// ------------------------------------------------------------------ gas sweep
-// CTA = one block of consecutive cells x VCH discrete velocities; thread = velocity.
-template <typename Real, int DIM, int ORDER>
-__global__ void __launch_bounds__(VCH) k_sweep_gas(Geom<Real> g, Quad<Real> vq, const Real *__restrict__ coef,
-                                                    const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
-                                                    Real *__restrict__ f_out, Real *__restrict__ partial) {
+// ------------------------------------------------------------------ the sweep
+// One CTA = one block of consecutive cells x NT discrete velocities (N = 4 gas planes)
+// or photon directions (N = 1); thread = velocity.
+//  1. residuals at f^k, assembled face by face: each cell's limited slope is computed
+//     once; the flux leaving a cell through an outflow face is subtracted from its
+//     residual and added to the in-block neighbour's; inflow from outside the block
+//     (boundary states, or a halo cell reconstructed here) is added directly;
+//  2. forward and backward Gauss-Seidel inside the block (first-order operator);
+//  3. f^{k+1/2} = f^k + delta, and its velocity moments per (cell, chunk).
+template <typename Real, int N, int DIM, int ORDER, int NT>
+__global__ void __launch_bounds__(NT) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
+                                               const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
+                                               Real *__restrict__ f_out, Real *__restrict__ partial) {
+    constexpr bool PHOTON = (N == 1);
     extern __shared__ unsigned char smem_raw[];
-    Vec<Real, 4> *R = reinterpret_cast<Vec<Real, 4> *>(smem_raw);           // [block][VCH]
-    Real *sxi = reinterpret_cast<Real *>(R + g.block * VCH);                  // [DIM+1][VCH]
+    Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][NT]
+    Real *sxi = reinterpret_cast<Real *>(R + g.block * NT);              // [DIM+1][NT]
     const int tid = threadIdx.x;
     const int c0 = blockIdx.x * g.block;
     const int nb = min(g.block, g.n_cells - c0);
     const int chunk = blockIdx.y;
-    const int v = chunk * VCH + tid;
-    const int stride = vq.n_pad;
+    const int v = chunk * NT + tid;
+    const int stride = q.n_pad;
     Real xi[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
-        xi[a] = vq.x[a * stride + v];
-        sxi[a * VCH + tid] = xi[a];
+        xi[a] = q.x[a * stride + v];
+        sxi[a * NT + tid] = xi[a];
     }
-    sxi[DIM * VCH + tid] = vq.w[v];
+    sxi[DIM * NT + tid] = q.w[v];
 
-    // residuals at f^k
-    for (int l = 0; l < nb; ++l) {
-        const int i = c0 + l;
-        const Real *C = coef + (size_t)i * cf::NC;
-        Real gp[4];
-        reference<Real, DIM>(C, xi, gp);
-        const V<Real, 4> fi = ldv<Real, 4>(f_in, (size_t)i * stride + v);
-        const Real rate = C[cf::RATE];
-        V<Real, 4> r;
+    auto Rget = [&](int l) {
+        V<Real, N> r;
+        const Vec<Real, N> t = R[l * NT + tid];
 #pragma unroll
-        for (int p = 0; p < 4; ++p) r.x[p] = (gp[p] - fi.x[p]) * rate;
-        r.x[3] = fma(C[cf::SINK], fi.x[0], r.x[3]);
-        Real d = Real(0);
-        transport_residual<Real, 4, DIM, ORDER>(g, f_in, stride, bcoef, i, v, xi, fi, r, d, false);
-        Vec<Real, 4> t;
+        for (int p = 0; p < N; ++p) r.x[p] = t.v[p];
+        return r;
+    };
+    auto Rset = [&](int l, const V<Real, N> &r) {
+        Vec<Real, N> t;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) t.v[p] = r.x[p];
-        R[l * VCH + tid] = t;
+        for (int p = 0; p < N; ++p) t.v[p] = r.x[p];
+        R[l * NT + tid] = t;
+    };
+    {
+        V<Real, N> z;
+#pragma unroll
+        for (int p = 0; p < N; ++p) z.x[p] = Real(0);
+        for (int l = 0; l < nb; ++l) Rset(l, z);
     }
-    // forward Gauss-Seidel inside the block
+
+    // ---- 1. residuals
     for (int l = 0; l < nb; ++l) {
         const int i = c0 + l;
         const Real *C = coef + (size_t)i * cf::NC;
-        Real d = C[cf::INV_DT] + C[cf::RATE];
-        Vec<Real, 4> acc = R[l * VCH + tid];
-        const int nf = g.nf[i];
+        const V<Real, N> fi = ldv<Real, N>(f_in, (size_t)i * stride + v);
+        V<Real, N> r = Rget(l);
+        if constexpr (PHOTON) {
+            const Vec<Real, 4> cc = vload<Real, 4>(C + cf::RATE);
+            r.x[0] += vload<Real, 4>(C + cf::KEFF).v[0] * (cc.v[3] - fi.x[0]);
+        } else {
+            Real gp[4];
+            reference<Real, DIM>(C, xi, gp);
+            const Vec<Real, 4> cc = vload<Real, 4>(C + cf::RATE);
+            const Real rate = cc.v[0];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) r.x[p] = fma(gp[p] - fi.x[p], rate, r.x[p]);
+            r.x[3] = fma(cc.v[2], fi.x[0], r.x[3]);
+        }
+        V<Real, N> slope_i[DIM];
+        if constexpr (ORDER == 2) limited_slope<Real, N, DIM>(g, f_in, stride, i, v, fi, slope_i);
+        const int nf = g.info[i].x;
+#pragma unroll 1
         for (int k = 0; k < nf; ++k) {
-            const int fk = i * MAXF + k;
-            Real xn = Real(0);
+            const Face<Real> F = load_face(g.fgeo, i, k);
+            const int2 nl = g.fnb[i * MAXF + k];
+            Real xn = xi[0] * F.n[0];
+            if constexpr (DIM > 1) xn = fma(xi[1], F.n[1], xn);
+            if (xn > Real(0)) {
+                V<Real, N> fv = fi;
+                if constexpr (ORDER == 2) {
+                    if (nl.x >= 0) {
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) xn = fma(xi[a], g.nrm[fk * 3 + a], xn);
-            const Real sv = g.sv[fk];
-            if (xn > Real(0)) d = fma(sv, xn, d);
-            const int lj = g.local[fk];
+                        for (int p = 0; p < N; ++p) {
+                            fv.x[p] = fma(slope_i[0].x[p], F.df[0], fv.x[p]);
+                            if constexpr (DIM > 1) fv.x[p] = fma(slope_i[1].x[p], F.df[1], fv.x[p]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < N; ++p) r.x[p] = fma(-F.sv * xn, fv.x[p], r.x[p]);
+                if (nl.y >= 0) {
+                    V<Real, N> rn = Rget(nl.y);
+#pragma unroll
+                    for (int p = 0; p < N; ++p) rn.x[p] = fma(F.svn * xn, fv.x[p], rn.x[p]);
+                    Rset(nl.y, rn);
+                }
+            } else if (xn < Real(0) && nl.y < 0) {
+                V<Real, N> fv;
+                if (nl.x < 0) {
+                    const Real *B = bcoef + (size_t)(-1 - nl.x) * bc::NB;
+                    if constexpr (PHOTON) {
+                        fv.x[0] = B[bc::IIN];
+                    } else {
+                        Real c2 = Real(0);
+#pragma unroll
+                        for (int a = 0; a < DIM; ++a) {
+                            const Real c = xi[a] - B[bc::U + a];
+                            c2 = fma(c, c, c2);
+                        }
+                        const Real E = B[bc::A] * fexp(-B[bc::B] * c2);
+                        fv.x[0] = E * B[bc::M0];
+                        fv.x[1] = E * B[bc::MH];
+                        fv.x[2] = E * B[bc::M1];
+                        fv.x[3] = E * B[bc::M2];
+                    }
+                } else {
+                    fv = ldv<Real, N>(f_in, (size_t)nl.x * stride + v);
+                    if constexpr (ORDER == 2) {
+                        V<Real, N> slope_j[DIM];
+                        limited_slope<Real, N, DIM>(g, f_in, stride, nl.x, v, fv, slope_j);
+#pragma unroll
+                        for (int p = 0; p < N; ++p) {
+                            fv.x[p] = fma(slope_j[0].x[p], F.dn[0], fv.x[p]);
+                            if constexpr (DIM > 1) fv.x[p] = fma(slope_j[1].x[p], F.dn[1], fv.x[p]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < N; ++p) r.x[p] = fma(-F.sv * xn, fv.x[p], r.x[p]);
+            }
+        }
+        Rset(l, r);
+    }
+
+    // ---- 2. Gauss-Seidel inside the block with the first-order operator
+    //   d_i = 1/dt + rate + sum S/V xi_n^+ ;  off-diagonal S/V xi_n^- for in-block neighbours
+    auto diag = [&](int i, Real &d) {
+        const Vec<Real, 4> cc = vload<Real, 4>(coef + (size_t)i * cf::NC + cf::RATE);
+        d = cc.v[1] + (PHOTON ? vload<Real, 4>(coef + (size_t)i * cf::NC + cf::KEFF).v[0] : cc.v[0]);
+    };
+    for (int l = 0; l < nb; ++l) {
+        const int i = c0 + l;
+        Real d;
+        diag(i, d);
+        V<Real, N> acc = Rget(l);
+        const int nf = g.info[i].x;
+        for (int k = 0; k < nf; ++k) {
+            const Real *p4 = g.fgeo + ((size_t)i * MAXF + k) * fr::SIZE;
+            const Vec<Real, 4> a = vload<Real, 4>(p4);
+            Real xn = xi[0] * a.v[0];
+            if constexpr (DIM > 1) xn = fma(xi[1], a.v[1], xn);
+            if (xn > Real(0)) d = fma(a.v[2], xn, d);
+            const int lj = g.fnb[i * MAXF + k].y;
             if (lj >= 0 && lj < l && xn < Real(0)) {
-                const Vec<Real, 4> dj = R[lj * VCH + tid];
-                const Real a_ = sv * xn;
+                const V<Real, N> dj = Rget(lj);
 #pragma unroll
-                for (int p = 0; p < 4; ++p) acc.v[p] = fma(-a_, dj.v[p], acc.v[p]);
+                for (int p = 0; p < N; ++p) acc.x[p] = fma(-a.v[2] * xn, dj.x[p], acc.x[p]);
             }
         }
         const Real inv = Real(1) / d;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) acc.v[p] *= inv;
-        R[l * VCH + tid] = acc;
+        for (int p = 0; p < N; ++p) acc.x[p] *= inv;
+        Rset(l, acc);
     }
-    // backward Gauss-Seidel
     for (int l = nb - 1; l >= 0; --l) {
         const int i = c0 + l;
-        const Real *C = coef + (size_t)i * cf::NC;
-        Real d = C[cf::INV_DT] + C[cf::RATE];
-        Vec<Real, 4> corr;
+        Real d;
+        diag(i, d);
+        V<Real, N> corr;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) corr.v[p] = Real(0);
-        const int nf = g.nf[i];
+        for (int p = 0; p < N; ++p) corr.x[p] = Real(0);
+        const int nf = g.info[i].x;
         for (int k = 0; k < nf; ++k) {
-            const int fk = i * MAXF + k;
-            Real xn = Real(0);
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) xn = fma(xi[a], g.nrm[fk * 3 + a], xn);
-            const Real sv = g.sv[fk];
-            if (xn > Real(0)) d = fma(sv, xn, d);
-            const int lj = g.local[fk];
+            const Real *p4 = g.fgeo + ((size_t)i * MAXF + k) * fr::SIZE;
+            const Vec<Real, 4> a = vload<Real, 4>(p4);
+            Real xn = xi[0] * a.v[0];
+            if constexpr (DIM > 1) xn = fma(xi[1], a.v[1], xn);
+            if (xn > Real(0)) d = fma(a.v[2], xn, d);
+            const int lj = g.fnb[i * MAXF + k].y;
             if (lj > l && xn < Real(0)) {
-                const Vec<Real, 4> dj = R[lj * VCH + tid];
-                const Real a_ = sv * xn;
+                const V<Real, N> dj = Rget(lj);
 #pragma unroll
-                for (int p = 0; p < 4; ++p) corr.v[p] = fma(a_, dj.v[p], corr.v[p]);
+                for (int p = 0; p < N; ++p) corr.x[p] = fma(a.v[2] * xn, dj.x[p], corr.x[p]);
             }
         }
-        Vec<Real, 4> acc = R[l * VCH + tid];
+        V<Real, N> acc = Rget(l);
         const Real inv = Real(1) / d;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) acc.v[p] = fma(-corr.v[p], inv, acc.v[p]);
-        R[l * VCH + tid] = acc;
+        for (int p = 0; p < N; ++p) acc.x[p] = fma(-corr.x[p], inv, acc.x[p]);
+        Rset(l, acc);
     }
-    // f^{k+1/2} = f^k + delta; stage it for the moments
+
+    // ---- 3. f^{k+1/2} = f^k + delta, staged for the moments
     for (int l = 0; l < nb; ++l) {
         const size_t idx = (size_t)(c0 + l) * stride + v;
-        Vec<Real, 4> fo = vload<Real, 4>(f_in + idx * 4);
-        Vec<Real, 4> dl = R[l * VCH + tid];
+        V<Real, N> fo = ldv<Real, N>(f_in, idx);
+        const V<Real, N> dl = Rget(l);
 #pragma unroll
-        for (int p = 0; p < 4; ++p) fo.v[p] += dl.v[p];
-        vstore<Real, 4>(f_out + idx * 4, fo);
-        R[l * VCH + tid] = fo;
-    }
-    __syncthreads();
-    // moments: 8 threads per cell, each over VCH/8 velocities, shuffle-reduced
-    constexpr int TPC = 8;
-    constexpr int NM = n_gas_moments<DIM>();
-    const int sub = tid % TPC;
-    for (int l = tid / TPC; l < nb; l += VCH / TPC) {
-        const int i = c0 + l;
-        const Real *C = coef + (size_t)i * cf::NC;
-        Real u[DIM];
+        for (int p = 0; p < N; ++p) fo.x[p] += dl.x[p];
+        Rset(l, fo);
+        if constexpr (N == 1) {
+            f_out[idx] = fo.x[0];
+        } else {
+            Vec<Real, N> t;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) u[a] = C[cf::U + a];
-        Real acc[NMP];
-#pragma unroll
-        for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
-        for (int vl = sub; vl < VCH; vl += TPC) {
-            const Vec<Real, 4> fv4 = R[l * VCH + vl];
-            Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};
-            Real c[DIM];
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) c[a] = sxi[a * VCH + vl] - u[a];
-            add_moments<Real, DIM>(acc, c, sxi[DIM * VCH + vl], fv);
+            for (int p = 0; p < N; ++p) t.v[p] = fo.x[p];
+            vstore<Real, N>(f_out + idx * N, t);
         }
-        // the TPC lanes of one cell share the loop trip count; exchange only among them
-        const unsigned gmask = 0xFFu << ((tid & 31) & ~(TPC - 1));
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-#pragma unroll
-            for (int o = 1; o < TPC; o <<= 1) acc[m] += __shfl_xor_sync(gmask, acc[m], o);
-        }
-        if (sub == 0) {
-            Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMP;
-#pragma unroll
-            for (int m = 0; m < NM; ++m) P[m] = acc[m];
-        }
-    }
-}
-
-// ------------------------------------------------------------------ photon sweep
-template <typename Real, int DIM, int ORDER>
-__global__ void __launch_bounds__(OCH) k_sweep_photon(Geom<Real> g, Quad<Real> oq, const Real *__restrict__ coef,
-                                                       const Real *__restrict__ bcoef, const Real *__restrict__ I_in,
-                                                       Real *__restrict__ I_out, Real *__restrict__ partial) {
-    extern __shared__ unsigned char smem_raw[];
-    Real *R = reinterpret_cast<Real *>(smem_raw);            // [block][OCH]
-    Real *som = R + g.block * OCH;                           // [DIM+1][OCH]
-    const int tid = threadIdx.x;
-    const int c0 = blockIdx.x * g.block;
-    const int nb = min(g.block, g.n_cells - c0);
-    const int chunk = blockIdx.y;
-    const int o = chunk * OCH + tid;
-    const int stride = oq.n_pad;
-    Real om[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        om[a] = oq.x[a * stride + o];
-        som[a * OCH + tid] = om[a];
-    }
-    som[DIM * OCH + tid] = oq.w[o];
-    for (int l = 0; l < nb; ++l) {
-        const int i = c0 + l;
-        const Real *C = coef + (size_t)i * cf::NC;
-        const V<Real, 1> Ii = ldv<Real, 1>(I_in, (size_t)i * stride + o);
-        V<Real, 1> r;
-        r.x[0] = C[cf::KEFF] * (C[cf::GR] - Ii.x[0]);
-        Real d = Real(0);
-        transport_residual<Real, 1, DIM, ORDER>(g, I_in, stride, bcoef, i, o, om, Ii, r, d, true);
-        R[l * OCH + tid] = r.x[0];
-    }
-    for (int l = 0; l < nb; ++l) {
-        const int i = c0 + l;
-        const Real *C = coef + (size_t)i * cf::NC;
-        Real d = C[cf::INV_DT] + C[cf::KEFF];
-        Real acc = R[l * OCH + tid];
-        const int nf = g.nf[i];
-        for (int k = 0; k < nf; ++k) {
-            const int fk = i * MAXF + k;
-            Real on = Real(0);
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) on = fma(om[a], g.nrm[fk * 3 + a], on);
-            const Real sv = g.sv[fk];
-            if (on > Real(0)) d = fma(sv, on, d);
-            const int lj = g.local[fk];
-            if (lj >= 0 && lj < l && on < Real(0)) acc = fma(-sv * on, R[lj * OCH + tid], acc);
-        }
-        R[l * OCH + tid] = acc / d;
-    }
-    for (int l = nb - 1; l >= 0; --l) {
-        const int i = c0 + l;
-        const Real *C = coef + (size_t)i * cf::NC;
-        Real d = C[cf::INV_DT] + C[cf::KEFF];
-        Real corr = Real(0);
-        const int nf = g.nf[i];
-        for (int k = 0; k < nf; ++k) {
-            const int fk = i * MAXF + k;
-            Real on = Real(0);
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) on = fma(om[a], g.nrm[fk * 3 + a], on);
-            const Real sv = g.sv[fk];
-            if (on > Real(0)) d = fma(sv, on, d);
-            const int lj = g.local[fk];
-            if (lj > l && on < Real(0)) corr = fma(sv * on, R[lj * OCH + tid], corr);
-        }
-        R[l * OCH + tid] = R[l * OCH + tid] - corr / d;
-    }
-    for (int l = 0; l < nb; ++l) {
-        const size_t idx = (size_t)(c0 + l) * stride + o;
-        const Real In = I_in[idx] + R[l * OCH + tid];
-        I_out[idx] = In;
-        R[l * OCH + tid] = In;
     }
     __syncthreads();
     constexpr int TPC = 8;
     const int sub = tid % TPC;
-    for (int l = tid / TPC; l < nb; l += OCH / TPC) {
-        Real acc[1 + DIM];
+    const unsigned gmask = 0xFFu << ((tid & 31) & ~(TPC - 1));
+    if constexpr (PHOTON) {
+        for (int l = tid / TPC; l < nb; l += NT / TPC) {
+            Real acc[1 + DIM];
 #pragma unroll
-        for (int m = 0; m <= DIM; ++m) acc[m] = Real(0);
-        for (int ol = sub; ol < OCH; ol += TPC) {
-            const Real wI = som[DIM * OCH + ol] * R[l * OCH + ol];
-            acc[0] += wI;
+            for (int m = 0; m <= DIM; ++m) acc[m] = Real(0);
+            for (int ol = sub; ol < NT; ol += TPC) {
+                const Real wI = sxi[DIM * NT + ol] * R[l * NT + ol].v[0];
+                acc[0] += wI;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a) acc[1 + a] += wI * som[a * OCH + ol];
+                for (int a = 0; a < DIM; ++a) acc[1 + a] += wI * sxi[a * NT + ol];
+            }
+#pragma unroll
+            for (int m = 0; m <= DIM; ++m)
+#pragma unroll
+                for (int s = 1; s < TPC; s <<= 1) acc[m] += __shfl_xor_sync(gmask, acc[m], s);
+            if (sub == 0) {
+                Real *P = partial + ((size_t)(c0 + l) * gridDim.y + chunk) * NMO;
+#pragma unroll
+                for (int m = 0; m <= DIM; ++m) P[m] = acc[m];
+            }
         }
-        const unsigned gmask = 0xFFu << ((tid & 31) & ~(TPC - 1));
+    } else {
+        constexpr int NM = n_gas_moments<DIM>();
+        for (int l = tid / TPC; l < nb; l += NT / TPC) {
+            const Vec<Real, 4> u4 = vload<Real, 4>(coef + (size_t)(c0 + l) * cf::NC + cf::U);
+            Real acc[NMP];
 #pragma unroll
-        for (int m = 0; m <= DIM; ++m)
+            for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
+            for (int vl = sub; vl < NT; vl += TPC) {
+                const Vec<Real, N> fv4 = R[l * NT + vl];
+                Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};
+                Real c[DIM];
 #pragma unroll
-            for (int s = 1; s < TPC; s <<= 1) acc[m] += __shfl_xor_sync(gmask, acc[m], s);
-        if (sub == 0) {
-            Real *P = partial + ((size_t)(c0 + l) * gridDim.y + chunk) * NMO;
+                for (int a = 0; a < DIM; ++a) c[a] = sxi[a * NT + vl] - u4.v[a];
+                add_moments<Real, DIM>(acc, c, sxi[DIM * NT + vl], fv);
+            }
 #pragma unroll
-            for (int m = 0; m <= DIM; ++m) P[m] = acc[m];
+            for (int m = 0; m < NM; ++m)
+#pragma unroll
+                for (int o = 1; o < TPC; o <<= 1) acc[m] += __shfl_xor_sync(gmask, acc[m], o);
+            if (sub == 0) {
+                Real *P = partial + ((size_t)(c0 + l) * gridDim.y + chunk) * NMP;
+#pragma unroll
+                for (int m = 0; m < NM; ++m) P[m] = acc[m];
+            }
         }
     }
 }
@@ -886,15 +836,15 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
     return cudaGetLastError();
 }
 
-template <typename Real, int DIM, int ORDER>
-static cudaError_t sweep_gas_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &vq, const Real *coef,
-                               const Real *bcoef, const Real *f_in, Real *f_out, Real *partial) {
-    const size_t smem = (size_t)g.block * VCH * sizeof(Vec<Real, 4>) + (DIM + 1) * VCH * sizeof(Real);
-    auto kern = k_sweep_gas<Real, DIM, ORDER>;
+template <typename Real, int N, int DIM, int ORDER, int NT>
+static cudaError_t sweep_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *coef,
+                           const Real *bcoef, const Real *f_in, Real *f_out, Real *partial) {
+    const size_t smem = (size_t)g.block * NT * sizeof(Vec<Real, N>) + (DIM + 1) * NT * sizeof(Real);
+    auto kern = k_sweep<Real, N, DIM, ORDER, NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.n_cells + g.block - 1) / g.block, vq.n_pad / VCH);
-    kern<<<grid, VCH, smem, s>>>(g, vq, coef, bcoef, f_in, f_out, partial);
+    dim3 grid((g.n_cells + g.block - 1) / g.block, q.n_pad / NT);
+    kern<<<grid, NT, smem, s>>>(g, q, coef, bcoef, f_in, f_out, partial);
     return cudaGetLastError();
 }
 
@@ -902,32 +852,20 @@ template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
                              const Real *coef, const Real *bcoef, const Real *f_in, Real *f_out, Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_gas_t<Real, DIM, 1>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 1, VCH>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_gas_t<Real, DIM, 2>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 2, VCH>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
     }
     return cudaErrorInvalidValue;
-}
-
-template <typename Real, int DIM, int ORDER>
-static cudaError_t sweep_photon_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &oq, const Real *coef,
-                                  const Real *bcoef, const Real *I_in, Real *I_out, Real *partial) {
-    const size_t smem = (size_t)g.block * OCH * sizeof(Real) + (DIM + 1) * OCH * sizeof(Real);
-    auto kern = k_sweep_photon<Real, DIM, ORDER>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((g.n_cells + g.block - 1) / g.block, oq.n_pad / OCH);
-    kern<<<grid, OCH, smem, s>>>(g, oq, coef, bcoef, I_in, I_out, partial);
-    return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
                                 const Real *coef, const Real *bcoef, const Real *I_in, Real *I_out, Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_photon_t<Real, DIM, 1>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 1, OCH>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_photon_t<Real, DIM, 2>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 2, OCH>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
