@@ -43,6 +43,7 @@ class SolverParams:
     macro_sweeps: int = 6
     tol_outer: float = 1e-6
     tol_inner: float = 1e-7
+    sync_relax: float = 1.0              # weight of the equilibrium correction in the synchronisation
 
 
 @dataclass

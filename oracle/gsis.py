@@ -40,3 +40,56 @@ def cis_step(f, I, wl, geo):
     f_new, I_new = K.kinetic_sweep(f, I, wl, geo=geo, F=F_old)
     F_new = K.moments(f_new, I_new, wl.xi, wl.w, wl.omega, wl.wo, wl.dim, wl.model)
     return f_new, I_new, epsilon(F_new, F_old, geo.vol, wl.model, wl.dim), F_new
+
+
+def gsis_step(f, I, wl, geo, faces, F_old=None):
+    """One GSIS iteration (Section 3): kinetic step, high-order terms, synthetic
+    equations, then the synchronisation
+        f^{k+1} = f^{k+1/2} + w [f^eq(M^{k+1}) - f^eq(M^{k+1/2})]
+    with multi-temperature equilibria (photons: sigma_R T_R^4 / pi).  The paper's
+    step has w = 1; w = wl.solver.sync_relax.
+
+    In a closed domain (walls only) the total mass is not fixed by the steady equations,
+    and a synthetic solve stopped after a finite number of point-relaxation sweeps moves
+    it.  That drift would pass into f through the synchronisation every iteration, so
+    M^{k+1} is rescaled to the total mass of M^{k+1/2} there (a uniform factor on all
+    conservative variables: velocities and temperatures are unchanged)."""
+    from . import macro as MA
+    dim, model = wl.dim, wl.model
+    F_old = F_old if F_old is not None else K.moments(f, I, wl.xi, wl.w, wl.omega, wl.wo, dim, model)
+    fh, Ih = K.kinetic_sweep(f, I, wl, geo=geo, F=F_old, relax_block=wl.solver.relax_block)
+    Fh = K.moments(fh, Ih, wl.xi, wl.w, wl.omega, wl.wo, dim, model)
+    hot = MA.high_order_terms(faces, Fh, MA.kinetic_boundary_flux(faces, fh, Ih, wl), wl)
+    Wh = MA.conservative(Fh, dim, model)
+    W = MA.macro_solve(Wh, faces, hot, wl)
+    if all(p.kind == K.WALL for p in wl.mesh.patches):
+        W = W * (np.sum(F_old["rho"] * geo.vol) / np.sum(W[:, 0] * geo.vol))
+    Fn = MA.fields_from_W(W, dim, model)
+    om = wl.solver.sync_relax
+    f_new = fh + om * (K.equilibrium_planes(Fn, wl.xi, dim, model) - K.equilibrium_planes(Fh, wl.xi, dim, model))
+    I_new = Ih + om * (K.photon_equilibrium(Fn["T_R"], wl.omega.shape[0], model.sigma_R)
+                       - K.photon_equilibrium(Fh["T_R"], wl.omega.shape[0], model.sigma_R))
+    F_new = K.moments(f_new, I_new, wl.xi, wl.w, wl.omega, wl.wo, dim, model)
+    return f_new, I_new, epsilon(F_new, F_old, geo.vol, model, dim), F_new
+
+
+def solve(f, I, wl, mode="gsis", max_iter=None, tol=None, history=None):
+    """Outer iterations until epsilon < tol: CIS throughout (mode "cis"), or the first
+    n_cis_precond iterations CIS and GSIS afterwards (Section 6).  Returns
+    (f, I, fields, iterations)."""
+    from . import macro as MA
+    geo = K.Geometry(wl.mesh)
+    faces = MA.Faces(geo) if mode == "gsis" else None
+    max_iter = max_iter or wl.solver.max_outer
+    tol = tol or wl.solver.tol_outer
+    F = None
+    for k in range(max_iter):
+        if mode == "gsis" and k >= wl.solver.n_cis_precond:
+            f, I, eps, F = gsis_step(f, I, wl, geo, faces, F)
+        else:
+            f, I, eps, F = cis_step(f, I, wl, geo)
+        if history is not None:
+            history.append(eps)
+        if not np.isfinite(eps) or eps < tol:
+            return f, I, F, k + 1
+    return f, I, F, max_iter
