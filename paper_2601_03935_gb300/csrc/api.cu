@@ -15,9 +15,12 @@ using namespace gsis;
 
 namespace {
 
-enum KernelId { K_COEF, K_WALL, K_SWEEP_GAS, K_SWEEP_PHOTON, K_FINISH, K_EPS, K_EQUIL, K_MOMENTS, K_COUNT };
-const char *kKernelNames[K_COUNT] = {"coefficients", "wall_density", "sweep_gas", "sweep_photon",
-                                     "finish",       "eps_reduce",   "equilibrium", "moments_only"};
+enum KernelId {
+    K_COEF, K_WALL, K_SLOPE_GAS, K_SWEEP_GAS, K_SLOPE_PHOTON, K_SWEEP_PHOTON, K_FINISH, K_EPS, K_EQUIL, K_MOMENTS,
+    K_COUNT
+};
+const char *kKernelNames[K_COUNT] = {"coefficients", "wall_density", "slopes_gas", "sweep_gas",   "slopes_photon",
+                                     "sweep_photon", "finish",       "eps_reduce", "equilibrium", "moments_only"};
 
 }  // namespace
 
@@ -34,6 +37,7 @@ struct gsis_ctx {
     void *f[2] = {nullptr, nullptr}, *I[2] = {nullptr, nullptr};
     int cur = 0;
     void *coef = nullptr, *bcoef = nullptr, *partial = nullptr, *opartial = nullptr;
+    void *slope = nullptr, *oslope = nullptr;   // limited slopes [nc][Vp][dim][4], [nc][Op][dim] (order 2)
     double *fields = nullptr, *fields_old = nullptr, *eps_terms = nullptr, *eps_sums = nullptr;
     int *err = nullptr;
     double *vol = nullptr, *cell_dx = nullptr;
@@ -227,15 +231,26 @@ int cis_iteration(gsis_ctx *c) {
         return launch_wall_density<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_T, c->patch_u, c->patch_kind,
                                          (const Real *)c->f[c->cur], (Real *)c->bcoef);
     }));
+    if (c->order == 2) {
+        TRY(launch(c, K_SLOPE_GAS, [&] {
+            return launch_slopes<Real>(c->stream, c->dim, 4, g, c->Vp, (const Real *)c->f[c->cur], (Real *)c->slope);
+        }));
+    }
     TRY(launch(c, K_SWEEP_GAS, [&] {
         return launch_sweep_gas<Real>(c->stream, c->dim, c->order, g, vquad<Real>(c), (const Real *)c->coef,
-                                      (const Real *)c->bcoef, (const Real *)c->f[c->cur], (Real *)c->f[nxt],
-                                      (Real *)c->partial);
+                                      (const Real *)c->bcoef, (const Real *)c->f[c->cur], (const Real *)c->slope,
+                                      (Real *)c->f[nxt], (Real *)c->partial);
     }));
+    if (c->order == 2) {
+        TRY(launch(c, K_SLOPE_PHOTON, [&] {
+            return launch_slopes<Real>(c->stream, c->dim, 1, g, c->Op, (const Real *)c->I[c->cur],
+                                       (Real *)c->oslope);
+        }));
+    }
     TRY(launch(c, K_SWEEP_PHOTON, [&] {
         return launch_sweep_photon<Real>(c->stream, c->dim, c->order, g, oquad<Real>(c), (const Real *)c->coef,
-                                         (const Real *)c->bcoef, (const Real *)c->I[c->cur], (Real *)c->I[nxt],
-                                         (Real *)c->opartial);
+                                         (const Real *)c->bcoef, (const Real *)c->I[c->cur], (const Real *)c->oslope,
+                                         (Real *)c->I[nxt], (Real *)c->opartial);
     }));
     std::swap(c->fields, c->fields_old);
     TRY(launch(c, K_FINISH, [&] {
@@ -287,11 +302,10 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
     if (sp->precision != GSIS_FP32 && sp->precision != GSIS_FP64) return why = "bad precision", GSIS_ERR_INVALID_ARG;
     if (sp->order != 1 && sp->order != 2) return why = "order must be 1 or 2", GSIS_ERR_INVALID_ARG;
     if (sp->relax_block < 1 || sp->relax_block > MAXB) return why = "relax_block must be in 1..64", GSIS_ERR_INVALID_ARG;
-    {   // the gas sweep keeps block x VCH x 4 values in shared memory
+    {   // the gas sweep keeps a block's residuals and diagonals in shared memory
         const size_t rs = sp->precision == GSIS_FP64 ? 8 : 4;
-        if ((size_t)sp->relax_block * VCH * 4 * rs > 200 * 1024)
-            return why = "relax_block too large for the shared memory of one CTA (FP64: at most 50)",
-                   GSIS_ERR_INVALID_ARG;
+        if (sweep_smem_bytes(sp->relax_block, 4, 2, rs) > 227 * 1024)
+            return why = "relax_block too large for the shared memory of one CTA", GSIS_ERR_INVALID_ARG;
     }
     if (!(sp->cfl_meso > 0) || !(sp->venkat_K > 0)) return why = "bad CFL or limiter constant", GSIS_ERR_INVALID_ARG;
     if (!(mp->Kn > 0) || !(mp->Kn_p > 0) || !(mp->sigma_R >= 0) || !(mp->Z_r > 0) || !(mp->Z_v > 0) ||
@@ -586,6 +600,10 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc_real(c, &c->bcoef, bco.size()));
     A_(dalloc_real(c, &c->partial, (size_t)nc * c->nch * NMP));
     A_(dalloc_real(c, &c->opartial, (size_t)nc * c->och * NMO));
+    if (c->order == 2) {
+        A_(dalloc_real(c, &c->slope, (size_t)nc * c->Vp * dim * 4));
+        A_(dalloc_real(c, &c->oslope, (size_t)nc * c->Op * dim));
+    }
     A_(dalloc(c, &c->fields, (size_t)nc * NF));
     A_(dalloc(c, &c->fields_old, (size_t)nc * NF));
     A_(dalloc(c, &c->eps_terms, (size_t)nc * NEPS));

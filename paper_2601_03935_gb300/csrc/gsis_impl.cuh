@@ -9,8 +9,10 @@ namespace gsis {
 constexpr int MAXF = 4;        // faces per cell (segments, triangles, quads, tetrahedra)
 constexpr int MAXS = 12;       // least-squares stencil: face neighbours and their face neighbours
 constexpr int NF = 26;         // per-cell field record, see gsis.h
-constexpr int VCH = 128;       // discrete velocities per CTA of the gas sweep
-constexpr int OCH = 64;        // photon directions per CTA of the photon sweep
+constexpr int SV = 64;         // discrete velocities (or photon directions) per sweep CTA
+constexpr int SROWS = 4;       // thread rows of a sweep CTA (the block's cells are dealt to them)
+constexpr int VCH = SV;        // velocity chunk of the gas moment partials
+constexpr int OCH = SV;        // direction chunk of the photon moment partials
 constexpr int NMP = 20;        // stride of per-(cell, chunk) gas moment partials
 constexpr int NMO = 4;         // stride of per-(cell, chunk) photon moment partials
 constexpr int MAXB = 64;       // largest relaxation block
@@ -90,13 +92,17 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
                                 const double *patch_T, const double *patch_u, const int *patch_kind,
                                 const Real *f, Real *bcoef);
 template <typename Real>
+cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, int n_pad, const Real *f,
+                          Real *slope);
+size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size);
+template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
-                             const Real *coef, const Real *bcoef, const Real *f_in, Real *f_out,
-                             Real *partial);
+                             const Real *coef, const Real *bcoef, const Real *f_in, const Real *slope,
+                             Real *f_out, Real *partial);
 template <typename Real>
 cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
-                                const Real *coef, const Real *bcoef, const Real *I_in, Real *I_out,
-                                Real *partial);
+                                const Real *coef, const Real *bcoef, const Real *I_in, const Real *slope,
+                                Real *I_out, Real *partial);
 template <typename Real>
 cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const ModelDev &m,
                           const Real *coef, const Real *partial, const Real *opartial, const double *vol,

@@ -3,11 +3,13 @@
 //  coefficients   per-cell reference-distribution coefficients from the FP64 fields
 //                 (Section 2.1; Eq. reference_distribution)
 //  wall_density   density of diffusely re-emitted molecules at each wall face
+//  slopes         Venkatakrishnan-limited least-squares slopes of every (cell, velocity)
+//                 for the second-order residual (Eq. deltaflux_micro)
 //  sweep_gas      implicit finite-volume kinetic step of Eq. (dis_micro) for the four
-//                 gas planes: upwind (order 1) or Venkatakrishnan-limited linear
-//                 (order 2, Eq. deltaflux_micro) residual, then forward/backward
-//                 Gauss-Seidel point relaxation inside a block of consecutive cells,
-//                 then the velocity moments of the new distribution (Eq. getmoment)
+//                 gas planes: upwind (order 1) or limited linear (order 2) residual,
+//                 then forward/backward Gauss-Seidel point relaxation inside a block of
+//                 consecutive cells, then the velocity moments of the new distribution
+//                 (Eq. getmoment)
 //  sweep_photon   the same step for the gray intensity I_R
 //  finish         FP64 macroscopic fields from the moment partials, and the per-cell
 //                 terms of the convergence measure of Section 6
@@ -198,7 +200,9 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
     }
     const int4 info = g.info[j];
     const int ns = info.y, nfn = info.z;
-    for (int k = 0; k < ns; ++k) {
+#pragma unroll
+    for (int k = 0; k < MAXS; ++k) {
+        if (k >= ns) break;
         const int s = g.stn[j * MAXS + k];
         const V<Real, N> fs = ldv<Real, N>(f, (size_t)s * stride + v);
         const Real *w = g.lsq + ((size_t)j * MAXS + k) * 2;
@@ -311,105 +315,123 @@ __device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Rea
     }
 }
 
+// ------------------------------------------------------------------ limited slopes
+// One thread per (cell, velocity): the Venkatakrishnan-limited least-squares slope of
+// every plane, stored as slope[(cell * n_pad + v) * DIM + d][plane].  The sweep reads a
+// cell's slope for its outflow faces and a neighbour's for the inflow faces, so each
+// slope is computed once per iteration.
+template <typename Real, int N, int DIM>
+__global__ void __launch_bounds__(SV * 4) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ f,
+                                                   Real *__restrict__ slope) {
+    const int v = blockIdx.y * SV + threadIdx.x;
+    const int j = blockIdx.x * 4 + threadIdx.y;
+    if (j >= g.n_cells) return;
+    const size_t idx = (size_t)j * n_pad + v;
+    const V<Real, N> fj = ldv<Real, N>(f, idx);
+    V<Real, N> s[DIM];
+    limited_slope<Real, N, DIM>(g, f, n_pad, j, v, fj, s);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        if constexpr (N == 1) {
+            slope[idx * DIM + d] = s[d].x[0];
+        } else {
+            Vec<Real, N> t;
+#pragma unroll
+            for (int p = 0; p < N; ++p) t.v[p] = s[d].x[p];
+            vstore<Real, N>(slope + (idx * DIM + d) * N, t);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ the sweep
-// One CTA = one block of consecutive cells x NT discrete velocities (N = 4 gas planes)
-// or photon directions (N = 1); thread = velocity.
-//  1. residuals at f^k, assembled face by face: each cell's limited slope is computed
-//     once; the flux leaving a cell through an outflow face is subtracted from its
-//     residual and added to the in-block neighbour's; inflow from outside the block
-//     (boundary states, or a halo cell reconstructed here) is added directly;
-//  2. forward and backward Gauss-Seidel inside the block (first-order operator);
-//  3. f^{k+1/2} = f^k + delta, and its velocity moments per (cell, chunk).
-template <typename Real, int N, int DIM, int ORDER, int NT>
-__global__ void __launch_bounds__(NT) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
-                                               const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
-                                               Real *__restrict__ f_out, Real *__restrict__ partial) {
+// One CTA = one relaxation block of consecutive cells x SV discrete velocities (N = 4 gas
+// planes) or photon directions (N = 1); thread (tx, ty) = (velocity, row), and the
+// block's cells are dealt to the SROWS rows round-robin.
+//  1. residual and diagonal of every (cell, velocity) at f^k, independently: upwind
+//     face values are the cell's own reconstruction on outflow faces and the
+//     neighbour's (or the boundary state) on inflow faces;
+//  2. forward and backward Gauss-Seidel inside the block with the first-order
+//     operator, one thread per velocity (row 0);
+//  3. f^{k+1/2} = f^k + delta, staged in shared memory;
+//  4. velocity moments per (cell, chunk), eight lanes per cell.
+template <typename Real, int N, int DIM, int ORDER>
+__global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
+                                                      const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
+                                                      const Real *__restrict__ slope, Real *__restrict__ f_out,
+                                                      Real *__restrict__ partial) {
     constexpr bool PHOTON = (N == 1);
     extern __shared__ unsigned char smem_raw[];
-    Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][NT]
-    Real *sxi = reinterpret_cast<Real *>(R + g.block * NT);              // [DIM+1][NT]
-    const int tid = threadIdx.x;
+    Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][SV]
+    Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] diagonal
+    Real *Ag = Dg + g.block * SV;                                       // [block][MAXF][SV] S/V xi_n, in-block inflow
+    Real *sxi = Ag + g.block * MAXF * SV;                               // [DIM+1][SV]
+    int *Lg = reinterpret_cast<int *>(sxi + (DIM + 1) * SV);            // [block][MAXF] in-block neighbour or -1
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int c0 = blockIdx.x * g.block;
     const int nb = min(g.block, g.n_cells - c0);
     const int chunk = blockIdx.y;
-    const int v = chunk * NT + tid;
+    const int v = chunk * SV + tx;
     const int stride = q.n_pad;
     Real xi[DIM];
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-        xi[a] = q.x[a * stride + v];
-        sxi[a * NT + tid] = xi[a];
+    for (int a = 0; a < DIM; ++a) xi[a] = q.x[a * stride + v];
+    if (ty == 0) {
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) sxi[a * SV + tx] = xi[a];
+        sxi[DIM * SV + tx] = q.w[v];
     }
-    sxi[DIM * NT + tid] = q.w[v];
-
-    auto Rget = [&](int l) {
-        V<Real, N> r;
-        const Vec<Real, N> t = R[l * NT + tid];
+    auto slope_at = [&](int c, V<Real, N> (&s)[DIM]) {
+        const size_t idx = (size_t)c * stride + v;
 #pragma unroll
-        for (int p = 0; p < N; ++p) r.x[p] = t.v[p];
-        return r;
+        for (int d = 0; d < DIM; ++d) s[d] = ldv<Real, N>(slope, idx * DIM + d);
     };
-    auto Rset = [&](int l, const V<Real, N> &r) {
-        Vec<Real, N> t;
-#pragma unroll
-        for (int p = 0; p < N; ++p) t.v[p] = r.x[p];
-        R[l * NT + tid] = t;
-    };
-    {
-        V<Real, N> z;
-#pragma unroll
-        for (int p = 0; p < N; ++p) z.x[p] = Real(0);
-        for (int l = 0; l < nb; ++l) Rset(l, z);
-    }
 
-    // ---- 1. residuals
-    for (int l = 0; l < nb; ++l) {
+    // ---- 1. residuals and diagonals
+    for (int l = ty; l < nb; l += SROWS) {
         const int i = c0 + l;
         const Real *C = coef + (size_t)i * cf::NC;
         const V<Real, N> fi = ldv<Real, N>(f_in, (size_t)i * stride + v);
-        V<Real, N> r = Rget(l);
+        V<Real, N> r;
+        const Vec<Real, 4> cc = vload<Real, 4>(C + cf::RATE);
+        Real d;
         if constexpr (PHOTON) {
-            const Vec<Real, 4> cc = vload<Real, 4>(C + cf::RATE);
-            r.x[0] += vload<Real, 4>(C + cf::KEFF).v[0] * (cc.v[3] - fi.x[0]);
+            const Real keff = vload<Real, 4>(C + cf::KEFF).v[0];
+            r.x[0] = keff * (cc.v[3] - fi.x[0]);
+            d = cc.v[1] + keff;
         } else {
             Real gp[4];
             reference<Real, DIM>(C, xi, gp);
-            const Vec<Real, 4> cc = vload<Real, 4>(C + cf::RATE);
             const Real rate = cc.v[0];
 #pragma unroll
-            for (int p = 0; p < 4; ++p) r.x[p] = fma(gp[p] - fi.x[p], rate, r.x[p]);
+            for (int p = 0; p < 4; ++p) r.x[p] = (gp[p] - fi.x[p]) * rate;
             r.x[3] = fma(cc.v[2], fi.x[0], r.x[3]);
+            d = cc.v[1] + rate;
         }
-        V<Real, N> slope_i[DIM];
-        if constexpr (ORDER == 2) limited_slope<Real, N, DIM>(g, f_in, stride, i, v, fi, slope_i);
+        V<Real, N> si[DIM];
+        if constexpr (ORDER == 2) slope_at(i, si);
         const int nf = g.info[i].x;
-#pragma unroll 1
+        if (tx == 0)
+            for (int k = 0; k < MAXF; ++k) Lg[l * MAXF + k] = k < nf ? g.fnb[i * MAXF + k].y : -1;
         for (int k = 0; k < nf; ++k) {
             const Face<Real> F = load_face(g.fgeo, i, k);
             const int2 nl = g.fnb[i * MAXF + k];
             Real xn = xi[0] * F.n[0];
             if constexpr (DIM > 1) xn = fma(xi[1], F.n[1], xn);
+            Ag[(l * MAXF + k) * SV + tx] = (nl.y >= 0 && xn < Real(0)) ? F.sv * xn : Real(0);
+            V<Real, N> fv;
             if (xn > Real(0)) {
-                V<Real, N> fv = fi;
+                fv = fi;
+                d = fma(F.sv, xn, d);
                 if constexpr (ORDER == 2) {
                     if (nl.x >= 0) {
 #pragma unroll
                         for (int p = 0; p < N; ++p) {
-                            fv.x[p] = fma(slope_i[0].x[p], F.df[0], fv.x[p]);
-                            if constexpr (DIM > 1) fv.x[p] = fma(slope_i[1].x[p], F.df[1], fv.x[p]);
+                            fv.x[p] = fma(si[0].x[p], F.df[0], fv.x[p]);
+                            if constexpr (DIM > 1) fv.x[p] = fma(si[1].x[p], F.df[1], fv.x[p]);
                         }
                     }
                 }
-#pragma unroll
-                for (int p = 0; p < N; ++p) r.x[p] = fma(-F.sv * xn, fv.x[p], r.x[p]);
-                if (nl.y >= 0) {
-                    V<Real, N> rn = Rget(nl.y);
-#pragma unroll
-                    for (int p = 0; p < N; ++p) rn.x[p] = fma(F.svn * xn, fv.x[p], rn.x[p]);
-                    Rset(nl.y, rn);
-                }
-            } else if (xn < Real(0) && nl.y < 0) {
-                V<Real, N> fv;
+            } else if (xn < Real(0)) {
                 if (nl.x < 0) {
                     const Real *B = bcoef + (size_t)(-1 - nl.x) * bc::NB;
                     if constexpr (PHOTON) {
@@ -430,111 +452,103 @@ __global__ void __launch_bounds__(NT) k_sweep(Geom<Real> g, Quad<Real> q, const 
                 } else {
                     fv = ldv<Real, N>(f_in, (size_t)nl.x * stride + v);
                     if constexpr (ORDER == 2) {
-                        V<Real, N> slope_j[DIM];
-                        limited_slope<Real, N, DIM>(g, f_in, stride, nl.x, v, fv, slope_j);
+                        V<Real, N> sj[DIM];
+                        slope_at(nl.x, sj);
 #pragma unroll
                         for (int p = 0; p < N; ++p) {
-                            fv.x[p] = fma(slope_j[0].x[p], F.dn[0], fv.x[p]);
-                            if constexpr (DIM > 1) fv.x[p] = fma(slope_j[1].x[p], F.dn[1], fv.x[p]);
+                            fv.x[p] = fma(sj[0].x[p], F.dn[0], fv.x[p]);
+                            if constexpr (DIM > 1) fv.x[p] = fma(sj[1].x[p], F.dn[1], fv.x[p]);
                         }
                     }
                 }
-#pragma unroll
-                for (int p = 0; p < N; ++p) r.x[p] = fma(-F.sv * xn, fv.x[p], r.x[p]);
+            } else {
+                continue;
             }
+#pragma unroll
+            for (int p = 0; p < N; ++p) r.x[p] = fma(-F.sv * xn, fv.x[p], r.x[p]);
         }
-        Rset(l, r);
+        Vec<Real, N> t;
+#pragma unroll
+        for (int p = 0; p < N; ++p) t.v[p] = r.x[p];
+        R[l * SV + tx] = t;
+        Dg[l * SV + tx] = d;
     }
+    __syncthreads();
 
-    // ---- 2. Gauss-Seidel inside the block with the first-order operator
-    //   d_i = 1/dt + rate + sum S/V xi_n^+ ;  off-diagonal S/V xi_n^- for in-block neighbours
-    auto diag = [&](int i, Real &d) {
-        const Vec<Real, 4> cc = vload<Real, 4>(coef + (size_t)i * cf::NC + cf::RATE);
-        d = cc.v[1] + (PHOTON ? vload<Real, 4>(coef + (size_t)i * cf::NC + cf::KEFF).v[0] : cc.v[0]);
-    };
-    for (int l = 0; l < nb; ++l) {
-        const int i = c0 + l;
-        Real d;
-        diag(i, d);
-        V<Real, N> acc = Rget(l);
-        const int nf = g.info[i].x;
-        for (int k = 0; k < nf; ++k) {
-            const Real *p4 = g.fgeo + ((size_t)i * MAXF + k) * fr::SIZE;
-            const Vec<Real, 4> a = vload<Real, 4>(p4);
-            Real xn = xi[0] * a.v[0];
-            if constexpr (DIM > 1) xn = fma(xi[1], a.v[1], xn);
-            if (xn > Real(0)) d = fma(a.v[2], xn, d);
-            const int lj = g.fnb[i * MAXF + k].y;
-            if (lj >= 0 && lj < l && xn < Real(0)) {
-                const V<Real, N> dj = Rget(lj);
+    // ---- 2. Gauss-Seidel inside the block with the first-order operator, from the
+    // coefficients phase 1 left in shared memory (a = S/V xi_n < 0 on in-block inflow faces):
+    //   forward  delta*_l = (r_l - sum_{j<l} a delta*_j) / d_l
+    //   backward delta_l  = delta*_l - (sum_{j>l} a delta_j) / d_l
+    if (ty == 0) {
+        for (int l = 0; l < nb; ++l) {
+            Vec<Real, N> acc = R[l * SV + tx];
 #pragma unroll
-                for (int p = 0; p < N; ++p) acc.x[p] = fma(-a.v[2] * xn, dj.x[p], acc.x[p]);
+            for (int k = 0; k < MAXF; ++k) {
+                const int lj = Lg[l * MAXF + k];
+                if (lj < 0 || lj >= l) continue;
+                const Real a = Ag[(l * MAXF + k) * SV + tx];
+                const Vec<Real, N> dj = R[lj * SV + tx];
+#pragma unroll
+                for (int p = 0; p < N; ++p) acc.v[p] = fma(-a, dj.v[p], acc.v[p]);
             }
+            const Real inv = Real(1) / Dg[l * SV + tx];
+#pragma unroll
+            for (int p = 0; p < N; ++p) acc.v[p] *= inv;
+            R[l * SV + tx] = acc;
         }
-        const Real inv = Real(1) / d;
+        for (int l = nb - 1; l >= 0; --l) {
+            Real corr[N];
 #pragma unroll
-        for (int p = 0; p < N; ++p) acc.x[p] *= inv;
-        Rset(l, acc);
-    }
-    for (int l = nb - 1; l >= 0; --l) {
-        const int i = c0 + l;
-        Real d;
-        diag(i, d);
-        V<Real, N> corr;
+            for (int p = 0; p < N; ++p) corr[p] = Real(0);
 #pragma unroll
-        for (int p = 0; p < N; ++p) corr.x[p] = Real(0);
-        const int nf = g.info[i].x;
-        for (int k = 0; k < nf; ++k) {
-            const Real *p4 = g.fgeo + ((size_t)i * MAXF + k) * fr::SIZE;
-            const Vec<Real, 4> a = vload<Real, 4>(p4);
-            Real xn = xi[0] * a.v[0];
-            if constexpr (DIM > 1) xn = fma(xi[1], a.v[1], xn);
-            if (xn > Real(0)) d = fma(a.v[2], xn, d);
-            const int lj = g.fnb[i * MAXF + k].y;
-            if (lj > l && xn < Real(0)) {
-                const V<Real, N> dj = Rget(lj);
+            for (int k = 0; k < MAXF; ++k) {
+                const int lj = Lg[l * MAXF + k];
+                if (lj <= l) continue;
+                const Real a = Ag[(l * MAXF + k) * SV + tx];
+                const Vec<Real, N> dj = R[lj * SV + tx];
 #pragma unroll
-                for (int p = 0; p < N; ++p) corr.x[p] = fma(a.v[2] * xn, dj.x[p], corr.x[p]);
+                for (int p = 0; p < N; ++p) corr[p] = fma(a, dj.v[p], corr[p]);
             }
-        }
-        V<Real, N> acc = Rget(l);
-        const Real inv = Real(1) / d;
+            Vec<Real, N> acc = R[l * SV + tx];
+            const Real inv = Real(1) / Dg[l * SV + tx];
 #pragma unroll
-        for (int p = 0; p < N; ++p) acc.x[p] = fma(-corr.x[p], inv, acc.x[p]);
-        Rset(l, acc);
+            for (int p = 0; p < N; ++p) acc.v[p] = fma(-corr[p], inv, acc.v[p]);
+            R[l * SV + tx] = acc;
+        }
     }
+    __syncthreads();
 
     // ---- 3. f^{k+1/2} = f^k + delta, staged for the moments
-    for (int l = 0; l < nb; ++l) {
+    for (int l = ty; l < nb; l += SROWS) {
         const size_t idx = (size_t)(c0 + l) * stride + v;
         V<Real, N> fo = ldv<Real, N>(f_in, idx);
-        const V<Real, N> dl = Rget(l);
+        Vec<Real, N> t = R[l * SV + tx];
 #pragma unroll
-        for (int p = 0; p < N; ++p) fo.x[p] += dl.x[p];
-        Rset(l, fo);
+        for (int p = 0; p < N; ++p) t.v[p] += fo.x[p];
+        R[l * SV + tx] = t;
         if constexpr (N == 1) {
-            f_out[idx] = fo.x[0];
+            f_out[idx] = t.v[0];
         } else {
-            Vec<Real, N> t;
-#pragma unroll
-            for (int p = 0; p < N; ++p) t.v[p] = fo.x[p];
             vstore<Real, N>(f_out + idx * N, t);
         }
     }
     __syncthreads();
+
+    // ---- 4. moments of the new distribution, eight lanes per cell
     constexpr int TPC = 8;
+    const int tid = ty * SV + tx;
     const int sub = tid % TPC;
     const unsigned gmask = 0xFFu << ((tid & 31) & ~(TPC - 1));
-    if constexpr (PHOTON) {
-        for (int l = tid / TPC; l < nb; l += NT / TPC) {
+    for (int l = tid / TPC; l < nb; l += SV * SROWS / TPC) {
+        if constexpr (PHOTON) {
             Real acc[1 + DIM];
 #pragma unroll
             for (int m = 0; m <= DIM; ++m) acc[m] = Real(0);
-            for (int ol = sub; ol < NT; ol += TPC) {
-                const Real wI = sxi[DIM * NT + ol] * R[l * NT + ol].v[0];
+            for (int ol = sub; ol < SV; ol += TPC) {
+                const Real wI = sxi[DIM * SV + ol] * R[l * SV + ol].v[0];
                 acc[0] += wI;
 #pragma unroll
-                for (int a = 0; a < DIM; ++a) acc[1 + a] += wI * sxi[a * NT + ol];
+                for (int a = 0; a < DIM; ++a) acc[1 + a] += wI * sxi[a * SV + ol];
             }
 #pragma unroll
             for (int m = 0; m <= DIM; ++m)
@@ -545,21 +559,19 @@ __global__ void __launch_bounds__(NT) k_sweep(Geom<Real> g, Quad<Real> q, const 
 #pragma unroll
                 for (int m = 0; m <= DIM; ++m) P[m] = acc[m];
             }
-        }
-    } else {
-        constexpr int NM = n_gas_moments<DIM>();
-        for (int l = tid / TPC; l < nb; l += NT / TPC) {
+        } else {
+            constexpr int NM = n_gas_moments<DIM>();
             const Vec<Real, 4> u4 = vload<Real, 4>(coef + (size_t)(c0 + l) * cf::NC + cf::U);
             Real acc[NMP];
 #pragma unroll
             for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
-            for (int vl = sub; vl < NT; vl += TPC) {
-                const Vec<Real, N> fv4 = R[l * NT + vl];
+            for (int vl = sub; vl < SV; vl += TPC) {
+                const Vec<Real, N> fv4 = R[l * SV + vl];
                 Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};
                 Real c[DIM];
 #pragma unroll
-                for (int a = 0; a < DIM; ++a) c[a] = sxi[a * NT + vl] - u4.v[a];
-                add_moments<Real, DIM>(acc, c, sxi[DIM * NT + vl], fv);
+                for (int a = 0; a < DIM; ++a) c[a] = sxi[a * SV + vl] - u4.v[a];
+                add_moments<Real, DIM>(acc, c, sxi[DIM * SV + vl], fv);
             }
 #pragma unroll
             for (int m = 0; m < NM; ++m)
@@ -836,36 +848,61 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
     return cudaGetLastError();
 }
 
-template <typename Real, int N, int DIM, int ORDER, int NT>
+template <typename Real, int N, int DIM>
+static cudaError_t slopes_t(cudaStream_t s, const Geom<Real> &g, int n_pad, const Real *f, Real *slope) {
+    dim3 grid((g.n_cells + 3) / 4, n_pad / SV), block(SV, 4);
+    k_slopes<Real, N, DIM><<<grid, block, 0, s>>>(g, n_pad, f, slope);
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, int n_pad, const Real *f,
+                          Real *slope) {
+    if (planes == 4) {
+        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 4, DIM>(s, g, n_pad, f, slope)));
+    } else if (planes == 1) {
+        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 1, DIM>(s, g, n_pad, f, slope)));
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size) {
+    return (size_t)block * SV * (planes + 1 + MAXF) * real_size + (size_t)(dim + 1) * SV * real_size +
+           (size_t)block * MAXF * sizeof(int);
+}
+
+template <typename Real, int N, int DIM, int ORDER>
 static cudaError_t sweep_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *coef,
-                           const Real *bcoef, const Real *f_in, Real *f_out, Real *partial) {
-    const size_t smem = (size_t)g.block * NT * sizeof(Vec<Real, N>) + (DIM + 1) * NT * sizeof(Real);
-    auto kern = k_sweep<Real, N, DIM, ORDER, NT>;
+                           const Real *bcoef, const Real *f_in, const Real *slope, Real *f_out, Real *partial) {
+    const size_t smem = sweep_smem_bytes(g.block, N, DIM, sizeof(Real));
+    auto kern = k_sweep<Real, N, DIM, ORDER>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.n_cells + g.block - 1) / g.block, q.n_pad / NT);
-    kern<<<grid, NT, smem, s>>>(g, q, coef, bcoef, f_in, f_out, partial);
+    dim3 grid((g.n_cells + g.block - 1) / g.block, q.n_pad / SV), block(SV, SROWS);
+    kern<<<grid, block, smem, s>>>(g, q, coef, bcoef, f_in, slope, f_out, partial);
     return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
-                             const Real *coef, const Real *bcoef, const Real *f_in, Real *f_out, Real *partial) {
+                             const Real *coef, const Real *bcoef, const Real *f_in, const Real *slope, Real *f_out,
+                             Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 1, VCH>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 1>(s, g, vq, coef, bcoef, f_in, slope, f_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 2, VCH>(s, g, vq, coef, bcoef, f_in, f_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 2>(s, g, vq, coef, bcoef, f_in, slope, f_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename Real>
 cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
-                                const Real *coef, const Real *bcoef, const Real *I_in, Real *I_out, Real *partial) {
+                                const Real *coef, const Real *bcoef, const Real *I_in, const Real *slope,
+                                Real *I_out, Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 1, OCH>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 1>(s, g, oq, coef, bcoef, I_in, slope, I_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 2, OCH>(s, g, oq, coef, bcoef, I_in, I_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 2>(s, g, oq, coef, bcoef, I_in, slope, I_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
@@ -912,10 +949,14 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, const Quad
     template cudaError_t launch_wall_density<Real>(cudaStream_t, int, const Geom<Real> &, const Quad<Real> &,     \
                                                    const double *, const double *, const int *, const Real *,      \
                                                    Real *);                                                        \
+    template cudaError_t launch_slopes<Real>(cudaStream_t, int, int, const Geom<Real> &, int, const Real *,       \
+                                             Real *);                                                              \
     template cudaError_t launch_sweep_gas<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,    \
-                                                const Real *, const Real *, const Real *, Real *, Real *);         \
+                                                const Real *, const Real *, const Real *, const Real *, Real *,    \
+                                                Real *);                                                           \
     template cudaError_t launch_sweep_photon<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &, \
-                                                   const Real *, const Real *, const Real *, Real *, Real *);      \
+                                                   const Real *, const Real *, const Real *, const Real *, Real *, \
+                                                   Real *);                                                        \
     template cudaError_t launch_finish<Real>(cudaStream_t, int, int, int, int, const ModelDev &, const Real *,     \
                                              const Real *, const Real *, const double *, const double *, double *, \
                                              double *, int *, int);                                                \

@@ -80,7 +80,7 @@ def test_cis_step_matches_oracle(case, precision, order):
     assert abs(eps - eps_o) <= 1e-4 * eps_o if precision == "fp32" else abs(eps - eps_o) <= 1e-9 * eps_o
 
 
-@pytest.mark.parametrize("block", [1, 5, 50])
+@pytest.mark.parametrize("block", [1, 5, 49])
 def test_block_sizes_and_jacobi(block):
     wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=9), precision="fp64", order=2, relax_block=block)
     f, I = _inputs(wl, 11, "fp64", smooth=True)
