@@ -123,6 +123,8 @@ typedef struct {
     int32_t n_cis_precond;      /* CIS iterations before GSIS starts                        */
     int32_t max_outer, max_inner, macro_sweeps;
     double tol_outer, tol_inner;
+    double sync_relax;          /* w in f^{k+1} = f^{k+1/2} + w [f_eq(M^{k+1}) - f_eq(M^{k+1/2})],
+                                   0 < w <= 1 (Section 3 has w = 1)                          */
 } gsis_solver_params;
 
 typedef struct gsis_ctx gsis_ctx;

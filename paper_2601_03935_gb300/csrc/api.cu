@@ -17,10 +17,13 @@ namespace {
 
 enum KernelId {
     K_COEF, K_WALL, K_SLOPE_GAS, K_SWEEP_GAS, K_SLOPE_PHOTON, K_SWEEP_PHOTON, K_FINISH, K_EPS, K_EQUIL, K_MOMENTS,
-    K_COUNT
+    K_KBFLUX, K_HOT, K_MGRAD, K_MBFLUX, K_MRES, K_MNORM, K_MJACOBI, K_MCONV, K_SYNC, K_COUNT
 };
-const char *kKernelNames[K_COUNT] = {"coefficients", "wall_density", "slopes_gas", "sweep_gas",   "slopes_photon",
-                                     "sweep_photon", "finish",       "eps_reduce", "equilibrium", "moments_only"};
+const char *kKernelNames[K_COUNT] = {"coefficients", "wall_density",  "slopes_gas",    "sweep_gas",
+                                     "slopes_photon", "sweep_photon", "finish",        "eps_reduce",
+                                     "equilibrium",  "moments_only",  "kinetic_bflux", "macro_hot",
+                                     "macro_grad",   "macro_bflux",   "macro_residual", "macro_norm",
+                                     "macro_jacobi", "macro_convert", "sync"};
 
 }  // namespace
 
@@ -49,6 +52,22 @@ struct gsis_ctx {
     double *patch_T = nullptr, *patch_u = nullptr;
     int *patch_kind = nullptr;
     double *h_pinned = nullptr;  // NEPS sums + error word
+
+    // synthetic equations (FP64): geometry, quadratures in FP64, state and work arrays
+    MacroGeom mg{};
+    bool closed = true;          // walls only: the synthetic solution keeps the mass
+    int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
+    double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
+           *m_fi_xf = nullptr, *m_lsq = nullptr, *m_eps2 = nullptr, *m_xc = nullptr, *m_bf_n = nullptr,
+           *m_bf_S = nullptr, *m_bf_dn = nullptr, *m_pstate = nullptr;
+    double *vqd_x = nullptr, *vqd_w = nullptr, *oqd_x = nullptr, *oqd_w = nullptr;
+    double *W[2] = {nullptr, nullptr}, *mq = nullptr, *mgrad = nullptr, *mphi = nullptr, *Rg = nullptr,
+           *Dinv = nullptr, *gam = nullptr, *dG[2] = {nullptr, nullptr}, *rpart = nullptr, *hot = nullptr,
+           *hot_b = nullptr, *kbf = nullptr, *mbf = nullptr, *fields_h = nullptr, *fields_n = nullptr,
+           *mhist = nullptr;
+    MacroState *mstate = nullptr;
+    MacroState *h_mstate = nullptr;   // pinned: initial state and the polled stop flag
+    int last_inner = 0;
 
     bool have_eps = false;
     double last_eps = 0.0;
@@ -221,12 +240,11 @@ int refresh_fields(gsis_ctx *c) {
 
 int refresh(gsis_ctx *c) { return c->precision == GSIS_FP64 ? refresh_fields<double>(c) : refresh_fields<float>(c); }
 
-// One CIS iteration: coefficients are current (built from the fields of f^k).
+// The kinetic step of Eq. (dis_micro) from f^k (buffers cur) into buffers nxt, with the
+// moment partials of f^{k+1/2}; coefficients are current (built from the fields of f^k).
 template <typename Real>
-int cis_iteration(gsis_ctx *c) {
+int kinetic_step(gsis_ctx *c, int nxt) {
     const Geom<Real> g = geom<Real>(c);
-    const int nxt = 1 - c->cur;
-    CUDA_TRY(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
     TRY(launch(c, K_WALL, [&] {
         return launch_wall_density<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_T, c->patch_u, c->patch_kind,
                                          (const Real *)c->f[c->cur], (Real *)c->bcoef);
@@ -252,6 +270,14 @@ int cis_iteration(gsis_ctx *c) {
                                          (const Real *)c->bcoef, (const Real *)c->I[c->cur], (const Real *)c->oslope,
                                          (Real *)c->I[nxt], (Real *)c->opartial);
     }));
+    return GSIS_OK;
+}
+
+// fields of the new distribution from the partials, epsilon against the fields of f^k,
+// coefficients for the next iteration, and the asynchronous read-back of epsilon
+template <typename Real>
+int close_iteration(gsis_ctx *c, int nxt) {
+    const Geom<Real> g = geom<Real>(c);
     std::swap(c->fields, c->fields_old);
     TRY(launch(c, K_FINISH, [&] {
         return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
@@ -267,6 +293,117 @@ int cis_iteration(gsis_ctx *c) {
     c->cur = nxt;
     c->have_eps = true;
     return GSIS_OK;
+}
+
+// One CIS iteration: f^{k+1} = f^{k+1/2}.
+template <typename Real>
+int cis_iteration(gsis_ctx *c) {
+    const int nxt = 1 - c->cur;
+    CUDA_TRY(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    TRY(kinetic_step<Real>(c, nxt));
+    return close_iteration<Real>(c, nxt);
+}
+
+QuadD vquad_d(const gsis_ctx *c) { return QuadD{c->V, c->Vp, c->vqd_x, c->vqd_w}; }
+QuadD oquad_d(const gsis_ctx *c) { return QuadD{c->NO, c->Op, c->oqd_x, c->oqd_w}; }
+
+// Pseudo-time iterations of the synthetic equations from W[0] until ||R|| <= tol_inner
+// ||R_0|| or max_inner; returns the index of the buffer that holds the result.  The
+// device stop flag is polled every POLL iterations (one stream synchronisation each).
+int macro_solve(gsis_ctx *c, int *w_out) {
+    constexpr int POLL = 8;
+    const MacroGeom &g = c->mg;
+    const gsis_solver_params &sp = c->solver;
+    c->h_mstate->it = 0;
+    c->h_mstate->done = 0;
+    c->h_mstate->max_inner = sp.max_inner;
+    c->h_mstate->r0 = 0.0;
+    c->h_mstate->rn = 0.0;
+    c->h_mstate->tol = sp.tol_inner;
+    CUDA_TRY(c, cudaMemcpyAsync(c->mstate, c->h_mstate, sizeof(MacroState), cudaMemcpyHostToDevice, c->stream));
+    const int nparts = macro_rpart_count((int)c->nc);
+    const int sweeps = std::max(sp.macro_sweeps, 1);
+    int w = 0, it = 0;
+    for (; it < sp.max_inner; ++it) {
+        TRY(launch(c, K_MGRAD, [&] {
+            return launch_macro_grad(c->stream, g, c->order, c->model, c->mstate, c->W[w], c->mq, c->mgrad, c->mphi);
+        }));
+        TRY(launch(c, K_MBFLUX, [&] {
+            return launch_macro_bflux(c->stream, g, c->model, vquad_d(c), oquad_d(c), c->mstate, c->mq, c->mbf);
+        }));
+        TRY(launch(c, K_MRES, [&] {
+            return launch_macro_residual(c->stream, g, c->order, c->model, sp.cfl_macro, c->mstate, c->W[w], c->mq,
+                                         c->mgrad, c->mphi, c->hot, c->mbf, c->hot_b, c->Rg, c->Dinv, c->gam,
+                                         c->rpart);
+        }));
+        TRY(launch(c, K_MNORM, [&] { return launch_macro_norm(c->stream, nparts, c->rpart, c->mstate, c->mhist); }));
+        for (int sw = 0; sw < sweeps; ++sw) {
+            TRY(launch(c, K_MJACOBI, [&] {
+                return launch_macro_jacobi(c->stream, g, c->model, c->mstate, sw == 0, sw == sweeps - 1, c->W[w],
+                                           c->Rg, c->Dinv, c->gam, c->dG[sw & 1], c->dG[(sw + 1) & 1], c->W[1 - w]);
+            }));
+        }
+        w = 1 - w;
+        if ((it + 1) % POLL == 0 && it + 1 < sp.max_inner) {
+            CUDA_TRY(c, cudaMemcpyAsync(c->h_mstate, c->mstate, sizeof(MacroState), cudaMemcpyDeviceToHost,
+                                        c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            if (c->h_mstate->done) {
+                ++it;
+                break;
+            }
+        }
+    }
+    *w_out = w;
+    return GSIS_OK;
+}
+
+// One GSIS iteration (Section 3): kinetic step, high-order terms from f^{k+1/2}, the
+// synthetic equations, f^{k+1} = f^{k+1/2} + w [f_eq(M^{k+1}) - f_eq(M^{k+1/2})].
+template <typename Real>
+int gsis_iteration(gsis_ctx *c) {
+    const int nxt = 1 - c->cur;
+    const MacroGeom &g = c->mg;
+    CUDA_TRY(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    TRY(kinetic_step<Real>(c, nxt));
+    TRY(launch(c, K_FINISH, [&] {       // M^{k+1/2}
+        return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
+                                   (const Real *)c->partial, (const Real *)c->opartial, c->vol, nullptr,
+                                   c->fields_h, c->eps_terms, c->err, 0);
+    }));
+    TRY(launch(c, K_KBFLUX, [&] {
+        return launch_kinetic_bflux<Real>(c->stream, g, c->model, vquad<Real>(c), oquad<Real>(c),
+                                          (const Real *)c->f[nxt], (const Real *)c->I[nxt], c->kbf);
+    }));
+    TRY(launch(c, K_MCONV, [&] {
+        return launch_macro_from_fields(c->stream, c->dim, (int)c->nc, c->model, c->fields_h, c->W[0]);
+    }));
+    TRY(launch(c, K_MGRAD, [&] {
+        return launch_macro_grad(c->stream, g, 1, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
+    }));
+    TRY(launch(c, K_MBFLUX, [&] {
+        return launch_macro_bflux(c->stream, g, c->model, vquad_d(c), oquad_d(c), nullptr, c->mq, c->mbf);
+    }));
+    TRY(launch(c, K_HOT, [&] {
+        return launch_macro_hot(c->stream, g, c->model, c->fields_h, c->mq, c->mgrad, c->kbf, c->mbf, c->hot,
+                                c->hot_b);
+    }));
+    int w = 0;
+    TRY(macro_solve(c, &w));
+    if (c->closed) {
+        TRY(launch(c, K_MCONV, [&] {
+            return launch_macro_mass_rescale(c->stream, c->dim, (int)c->nc, c->vol, c->fields, c->W[w]);
+        }));
+    }
+    TRY(launch(c, K_MCONV, [&] {
+        return launch_macro_fields_from_W(c->stream, c->dim, (int)c->nc, c->model, c->W[w], c->fields_n);
+    }));
+    TRY(launch(c, K_SYNC, [&] {
+        return launch_sync<Real>(c->stream, c->dim, (int)c->nc, vquad<Real>(c), oquad<Real>(c), c->model,
+                                 c->solver.sync_relax, c->fields_n, c->fields_h, (const Real *)c->coef,
+                                 (Real *)c->f[nxt], (Real *)c->I[nxt], (Real *)c->partial, (Real *)c->opartial);
+    }));
+    return close_iteration<Real>(c, nxt);
 }
 
 int read_eps(gsis_ctx *c, double *eps) {
@@ -308,6 +445,9 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
             return why = "relax_block too large for the shared memory of one CTA", GSIS_ERR_INVALID_ARG;
     }
     if (!(sp->cfl_meso > 0) || !(sp->venkat_K > 0)) return why = "bad CFL or limiter constant", GSIS_ERR_INVALID_ARG;
+    if (!(sp->cfl_macro > 0) || sp->max_inner < 1 || sp->macro_sweeps < 1 || !(sp->tol_inner >= 0))
+        return why = "bad synthetic-equation parameters", GSIS_ERR_INVALID_ARG;
+    if (!(sp->sync_relax > 0) || !(sp->sync_relax <= 1)) return why = "sync_relax must be in (0, 1]", GSIS_ERR_INVALID_ARG;
     if (!(mp->Kn > 0) || !(mp->Kn_p > 0) || !(mp->sigma_R >= 0) || !(mp->Z_r > 0) || !(mp->Z_v > 0) ||
         !(mp->d_r >= 0) || !(mp->d_v > 0) || !(mp->d_r > 0))
         return why = "bad model parameters", GSIS_ERR_INVALID_ARG;
@@ -380,6 +520,7 @@ void gsis_destroy(gsis_ctx *ctx) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     for (void *p : ctx->allocations) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->h_mstate) cudaFreeHost(ctx->h_mstate);
     delete ctx;
 }
 
@@ -588,6 +729,75 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         B[bc::IIN] = mp->sigma_R * TR * TR * TR * TR / M_PI;
     }
 
+    // ---- synthetic-equation geometry: interior faces (owner -> neighbour), the cell -> face
+    // map in the cell's face order, boundary faces, FP64 quadratures and patch states
+    std::vector<int> fi_i, fi_j, cface(nc * MAXF, 0), mpk(std::max(m->n_patches, 1), 0);
+    std::vector<double> fi_n, fi_S, fi_dn, fi_dist, fi_t, fi_xf, mxc(nc * 2, 0.0), mbn, mbS, mbdn,
+        mps(8 * std::max(m->n_patches, 1), 0.0);
+    {
+        std::vector<int> id_of(nfc, -1);
+        for (int64_t f = 0; f < nfc; ++f) {
+            const int o = m->face_owner[f], nb = m->face_nbr[f];
+            if (nb < 0) continue;
+            id_of[f] = (int)fi_i.size();
+            fi_i.push_back(o);
+            fi_j.push_back(nb);
+            double d[2] = {0, 0}, dn = 0.0, dd = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                d[a] = m->cell_centroid[nb * dim + a] - m->cell_centroid[o * dim + a];
+                dn += m->face_normal[f * dim + a] * d[a];
+                dd += d[a] * d[a];
+            }
+            dd = std::sqrt(dd);
+            for (int a = 0; a < 2; ++a) {
+                fi_n.push_back(a < dim ? m->face_normal[f * dim + a] : 0.0);
+                fi_t.push_back(d[a] / dd);
+                fi_xf.push_back(a < dim ? m->face_centroid[f * dim + a] : 0.0);
+            }
+            fi_S.push_back(m->face_area[f]);
+            fi_dn.push_back(std::fabs(dn));
+            fi_dist.push_back(dd);
+        }
+        for (int64_t i = 0; i < nc; ++i) {
+            for (int a = 0; a < dim; ++a) mxc[i * 2 + a] = m->cell_centroid[i * dim + a];
+            for (int k = 0; k < MAXF; ++k) {
+                if (k >= nf[i]) { cface[i * MAXF + k] = -1 - std::max(c->n_bf, 1); continue; }
+                const int j = nbr[i * MAXF + k];
+                cface[i * MAXF + k] = j >= 0 ? id_of[face_of[i * MAXF + k]] : j;
+            }
+        }
+        // boundary faces in the order the kinetic connectivity numbered them
+        mbn.assign(2 * std::max(c->n_bf, 1), 0.0);
+        mbS.assign(std::max(c->n_bf, 1), 0.0);
+        mbdn.assign(std::max(c->n_bf, 1), 0.0);
+        for (int64_t i = 0; i < nc; ++i)
+            for (int k = 0; k < nf[i]; ++k) {
+                const int j = nbr[i * MAXF + k];
+                if (j >= 0) continue;
+                const int b = -1 - j;
+                const int64_t f = face_of[i * MAXF + k];
+                double dn = 0.0;
+                for (int a = 0; a < dim; ++a) {
+                    mbn[b * 2 + a] = m->face_normal[f * dim + a];
+                    dn += m->face_normal[f * dim + a] * (m->face_centroid[f * dim + a] - m->cell_centroid[i * dim + a]);
+                }
+                mbS[b] = m->face_area[f];
+                mbdn[b] = std::fabs(dn);
+            }
+        for (int p = 0; p < m->n_patches; ++p) {
+            const gsis_patch &P = m->patches[p];
+            mpk[p] = P.kind;
+            if (P.kind != GSIS_PATCH_WALL) c->closed = false;
+            const double st[8] = {P.rho, P.u[0], P.u[1], P.u[2], P.T_t, P.T_r, P.T_v, P.T_R};
+            for (int k = 0; k < 8; ++k) mps[p * 8 + k] = st[k];
+        }
+        if (fi_i.empty()) {   // keep every device array non-empty
+            fi_i.push_back(0); fi_j.push_back(0); fi_S.push_back(0.0); fi_dn.push_back(1.0); fi_dist.push_back(1.0);
+            for (int a = 0; a < 2; ++a) { fi_n.push_back(0.0); fi_t.push_back(0.0); fi_xf.push_back(0.0); }
+        }
+    }
+    const int n_fi = (int)std::count_if(fi_S.begin(), fi_S.end(), [](double x) { return x > 0.0; });
+
     // ---- device allocations
     const size_t fsz = (size_t)nc * c->Vp * 4, isz = (size_t)nc * c->Op;
     rc = GSIS_OK;
@@ -628,6 +838,99 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc(c, &c->patch_u, pu.size()));
     A_(dalloc(c, &c->patch_kind, pk.size()));
     if (cudaMallocHost(&c->h_pinned, (NEPS + 1) * sizeof(double)) != cudaSuccess) return bail(GSIS_ERR_OUT_OF_MEMORY);
+    if (cudaMallocHost(&c->h_mstate, sizeof(MacroState)) != cudaSuccess) return bail(GSIS_ERR_OUT_OF_MEMORY);
+    {
+        const size_t nbf1 = std::max(c->n_bf, 1), nfi1 = fi_i.size();
+        A_(dalloc(c, &c->m_fi_i, nfi1));
+        A_(dalloc(c, &c->m_fi_j, nfi1));
+        A_(dalloc(c, &c->m_cface, (size_t)nc * MAXF));
+        A_(dalloc(c, &c->m_pkind, mpk.size()));
+        A_(dalloc(c, &c->m_fi_n, nfi1 * 2));
+        A_(dalloc(c, &c->m_fi_S, nfi1));
+        A_(dalloc(c, &c->m_fi_dn, nfi1));
+        A_(dalloc(c, &c->m_fi_dist, nfi1));
+        A_(dalloc(c, &c->m_fi_t, nfi1 * 2));
+        A_(dalloc(c, &c->m_fi_xf, nfi1 * 2));
+        A_(dalloc(c, &c->m_lsq, (size_t)nc * MAXS * 2));
+        A_(dalloc(c, &c->m_eps2, (size_t)nc));
+        A_(dalloc(c, &c->m_xc, (size_t)nc * 2));
+        A_(dalloc(c, &c->m_bf_n, nbf1 * 2));
+        A_(dalloc(c, &c->m_bf_S, nbf1));
+        A_(dalloc(c, &c->m_bf_dn, nbf1));
+        A_(dalloc(c, &c->m_pstate, mps.size()));
+        A_(dalloc(c, &c->vqd_x, vx.size()));
+        A_(dalloc(c, &c->vqd_w, vw.size()));
+        A_(dalloc(c, &c->oqd_x, ox.size()));
+        A_(dalloc(c, &c->oqd_w, ow.size()));
+        for (int k = 0; k < 2; ++k) {
+            A_(dalloc(c, &c->W[k], (size_t)nc * NVM));
+            A_(dalloc(c, &c->dG[k], (size_t)nc * NVM));
+        }
+        A_(dalloc(c, &c->mq, (size_t)nc * NVM));
+        A_(dalloc(c, &c->mgrad, (size_t)nc * 2 * NVM));
+        A_(dalloc(c, &c->mphi, (size_t)nc * NVM));
+        A_(dalloc(c, &c->Rg, (size_t)nc * NVM));
+        A_(dalloc(c, &c->Dinv, (size_t)nc * 24));
+        A_(dalloc(c, &c->gam, (size_t)nc * MAXF * 2));
+        A_(dalloc(c, &c->rpart, (size_t)macro_rpart_count((int)nc)));
+        A_(dalloc(c, &c->hot, nfi1 * NHOT));
+        A_(dalloc(c, &c->hot_b, nbf1 * NVM));
+        A_(dalloc(c, &c->kbf, nbf1 * NVM));
+        A_(dalloc(c, &c->mbf, nbf1 * NVM));
+        A_(dalloc(c, &c->fields_h, (size_t)nc * NF));
+        A_(dalloc(c, &c->fields_n, (size_t)nc * NF));
+        A_(dalloc(c, &c->mhist, (size_t)std::max(sp->max_inner, 1)));
+        A_(dalloc(c, &c->mstate, 1));
+        A_(upload(c, c->m_fi_i, fi_i));
+        A_(upload(c, c->m_fi_j, fi_j));
+        A_(upload(c, c->m_cface, cface));
+        A_(upload(c, c->m_pkind, mpk));
+        A_(upload(c, c->m_fi_n, fi_n));
+        A_(upload(c, c->m_fi_S, fi_S));
+        A_(upload(c, c->m_fi_dn, fi_dn));
+        A_(upload(c, c->m_fi_dist, fi_dist));
+        A_(upload(c, c->m_fi_t, fi_t));
+        A_(upload(c, c->m_fi_xf, fi_xf));
+        A_(upload(c, c->m_lsq, lsq));
+        A_(upload(c, c->m_eps2, eps2));
+        A_(upload(c, c->m_xc, mxc));
+        A_(upload(c, c->m_bf_n, mbn));
+        A_(upload(c, c->m_bf_S, mbS));
+        A_(upload(c, c->m_bf_dn, mbdn));
+        A_(upload(c, c->m_pstate, mps));
+        A_(upload(c, c->vqd_x, vx));
+        A_(upload(c, c->vqd_w, vw));
+        A_(upload(c, c->oqd_x, ox));
+        A_(upload(c, c->oqd_w, ow));
+        MacroGeom &G = c->mg;
+        G.n_cells = (int)nc;
+        G.dim = dim;
+        G.n_fi = n_fi;
+        G.n_bf = c->n_bf;
+        G.fi_i = c->m_fi_i;
+        G.fi_j = c->m_fi_j;
+        G.fi_n = c->m_fi_n;
+        G.fi_S = c->m_fi_S;
+        G.fi_dn = c->m_fi_dn;
+        G.fi_dist = c->m_fi_dist;
+        G.fi_t = c->m_fi_t;
+        G.fi_xf = c->m_fi_xf;
+        G.cface = c->m_cface;
+        G.info = c->g_info;
+        G.stn = c->g_stn;
+        G.lsq = c->m_lsq;
+        G.eps2 = c->m_eps2;
+        G.vol = c->vol;
+        G.dx = c->cell_dx;
+        G.xc = c->m_xc;
+        G.bf_cell = c->bf_cell;
+        G.bf_patch = c->bf_patch;
+        G.bf_n = c->m_bf_n;
+        G.bf_S = c->m_bf_S;
+        G.bf_dn = c->m_bf_dn;
+        G.patch_kind = c->m_pkind;
+        G.patch_state = c->m_pstate;
+    }
 
     if (bfn.empty()) bfn.assign(3, 0.0);
     if (bf_cell.empty()) { bf_cell.push_back(0); bf_patch.push_back(0); }
@@ -745,7 +1048,8 @@ int gsis_download_fields_async(gsis_ctx *c, double *out, int64_t len) {
 
 int gsis_step_async(gsis_ctx *c, int32_t mode) {
     if (!c) return GSIS_ERR_INVALID_ARG;
-    if (mode == GSIS_MODE_GSIS) return fail(c, GSIS_ERR_UNSUPPORTED, "GSIS mode is not built yet");
+    if (mode == GSIS_MODE_GSIS)
+        return c->precision == GSIS_FP64 ? gsis_iteration<double>(c) : gsis_iteration<float>(c);
     if (mode != GSIS_MODE_CIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
     return c->precision == GSIS_FP64 ? cis_iteration<double>(c) : cis_iteration<float>(c);
 }

@@ -83,6 +83,83 @@ struct ModelDev {
     double cfl_meso;
 };
 
+// ---- synthetic (macroscopic) equations, FP64 throughout (macro.cu)
+// Conservative variables W = [rho, rho u (dim), e, e_r, e_v, e_R] (nv = dim + 5) and
+// primitive variables q = [rho, u (dim), T_t, T_r, T_v, e_R] (the same count).
+constexpr int NVM = 7;         // largest nv (dim = 2)
+constexpr int NHOT = 12;       // per-face high-order terms: sigma (dim x dim), q_t, q_r, q_v, q_R (dim each)
+
+struct MacroGeom {
+    int n_cells, dim, n_fi, n_bf;
+    const int *fi_i, *fi_j;    // [n_fi] owner and neighbour of each interior face
+    const double *fi_n;        // [n_fi][2] unit normal, owner -> neighbour
+    const double *fi_S;        // [n_fi] area
+    const double *fi_dn;       // [n_fi] |n . (x_j - x_i)|
+    const double *fi_dist;     // [n_fi] |x_j - x_i|
+    const double *fi_t;        // [n_fi][2] (x_j - x_i) / |x_j - x_i|
+    const double *fi_xf;       // [n_fi][2] face centroid
+    const int *cface;          // [nc][MAXF] interior face id, or -1 - boundary face id; -1 - n_bf.. unused
+    const int4 *info;          // [nc] faces, stencil size, face neighbours leading the stencil
+    const int *stn;            // [nc][MAXS]
+    const double *lsq;         // [nc][MAXS][2]
+    const double *eps2;        // [nc] (K dx)^3
+    const double *vol, *dx, *xc;   // [nc], [nc], [nc][2]
+    const int *bf_cell, *bf_patch; // [n_bf]
+    const double *bf_n;        // [n_bf][2] outward normal
+    const double *bf_S;        // [n_bf]
+    const double *bf_dn;       // [n_bf] |n . (x_f - x_c)|
+    const int *patch_kind;     // [n_patches]
+    const double *patch_state; // [n_patches][8]: rho, u[3], T_t, T_r, T_v, T_R
+};
+
+// Double-precision quadratures for the macroscopic boundary fluxes.
+struct QuadD {
+    int n, n_pad;
+    const double *x;           // [3][n_pad]
+    const double *w;           // [n_pad]
+};
+
+// Device-side state of one synthetic solve: inner iteration counter, first and
+// current residual norms, and the stop flag every macro kernel reads first.
+struct MacroState {
+    int it, done, max_inner, pad;
+    double r0, rn, tol;
+};
+
+template <int DIM> struct MacroDims {
+    static constexpr int NV = DIM + 5, E = 1 + DIM, ER = 4 + DIM, NQ = DIM + 5;
+};
+
+cudaError_t launch_macro_from_fields(cudaStream_t s, int dim, int n_cells, const ModelDev &m, const double *F,
+                                     double *W);
+cudaError_t launch_macro_fields_from_W(cudaStream_t s, int dim, int n_cells, const ModelDev &m, const double *W,
+                                       double *F);
+cudaError_t launch_macro_grad(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m,
+                              const MacroState *st, const double *W, double *q, double *grad, double *phi);
+cudaError_t launch_macro_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const QuadD &vq,
+                               const QuadD &oq, const MacroState *st, const double *q, double *bflux);
+cudaError_t launch_macro_hot(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const double *F_kin,
+                             const double *q, const double *grad, const double *kin_bflux, const double *mac_bflux,
+                             double *hot, double *hot_b);
+cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m, double cfl_macro,
+                                  const MacroState *st, const double *W, const double *q, const double *grad,
+                                  const double *phi, const double *hot, const double *bflux, const double *hot_b,
+                                  double *Rg, double *Dinv, double *gam, double *rpart);
+cudaError_t launch_macro_norm(cudaStream_t s, int n_parts, const double *rpart, MacroState *st, double *history);
+cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const MacroState *st,
+                                int first, int last, const double *W, const double *Rg, const double *Dinv,
+                                const double *gam, const double *dG_in, double *dG_out, double *W_next);
+cudaError_t launch_macro_mass_rescale(cudaStream_t s, int dim, int n_cells, const double *vol, const double *F_ref,
+                                      double *W);
+template <typename Real>
+cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const Quad<Real> &vq,
+                                 const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux);
+template <typename Real>
+cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+                        const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
+                        Real *f, Real *I, Real *partial, Real *opartial);
+int macro_rpart_count(int n_cells);
+
 // ---- kernel launchers (kernels.cu); every launcher returns the launch status
 template <typename Real>
 cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, const ModelDev &m,

@@ -647,6 +647,188 @@ __global__ void k_moments_photon(int n_cells, Quad<Real> oq, const Real *__restr
     }
 }
 
+// ------------------------------------------------------------------ GSIS synchronisation
+// f <- f + w [f_eq(M_new) - f_eq(M_half)] with multi-temperature equilibria (planes
+// F0, m T_t F0, d_r/2 T_r F0, d_v/2 T_v F0), fused with the moments of the result about
+// the coefficient velocity; one warp per (cell, chunk).  Padding velocities are left alone.
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, ModelDev m, double om,
+                                                   const double *__restrict__ Fn, const double *__restrict__ Fh,
+                                                   const Real *__restrict__ coef, Real *__restrict__ f,
+                                                   Real *__restrict__ partial) {
+    constexpr int MH = 3 - DIM;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (VCH / 32) + warp;
+    const int chunk = blockIdx.y;
+    if (i >= n_cells) return;
+    Real A[2], Bq[2], u[2][DIM], mul[2][4];
+    for (int s = 0; s < 2; ++s) {
+        const double *r = (s == 0 ? Fn : Fh) + (size_t)i * NF;
+        const double T = r[4];
+        A[s] = (Real)(r[0] * pow(2.0 * 3.14159265358979323846 * T, -0.5 * DIM));
+        Bq[s] = (Real)(0.5 / T);
+        for (int a = 0; a < DIM; ++a) u[s][a] = (Real)r[1 + a];
+        mul[s][0] = Real(1);
+        mul[s][1] = (Real)(MH * T);
+        mul[s][2] = (Real)(0.5 * m.d_r * r[5]);
+        mul[s][3] = (Real)(0.5 * m.d_v * r[6]);
+    }
+    const Real w = (Real)om;
+    constexpr int NM = n_gas_moments<DIM>();
+    const Real *C = coef + (size_t)i * cf::NC;
+    Real acc[NMP];
+#pragma unroll
+    for (int k = 0; k < NMP; ++k) acc[k] = Real(0);
+    for (int vl = lane; vl < VCH; vl += 32) {
+        const int v = chunk * VCH + vl;
+        Real *fp = f + ((size_t)i * vq.n_pad + v) * 4;
+        Vec<Real, 4> fv4 = vload<Real, 4>(fp);
+        Real xi[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) xi[a] = vq.x[a * vq.n_pad + v];
+        if (v < vq.n) {
+            Real E[2];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                Real c2 = Real(0);
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) c2 += (xi[a] - u[s][a]) * (xi[a] - u[s][a]);
+                E[s] = A[s] * fexp(-Bq[s] * c2);
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p) fv4.v[p] += w * (mul[0][p] * E[0] - mul[1][p] * E[1]);
+            vstore<Real, 4>(fp, fv4);
+        }
+        Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};
+        Real c[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) c[a] = xi[a] - C[cf::U + a];
+        add_moments<Real, DIM>(acc, c, vq.w[v], fv);
+    }
+#pragma unroll
+    for (int k = 0; k < NM; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (lane == 0) {
+        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMP;
+#pragma unroll
+        for (int k = 0; k < NM; ++k) P[k] = acc[k];
+    }
+}
+
+template <typename Real, int DIM>
+__global__ void k_sync_photon(int n_cells, Quad<Real> oq, ModelDev m, double om, const double *__restrict__ Fn,
+                              const double *__restrict__ Fh, Real *__restrict__ I, Real *__restrict__ partial) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x / 32) + warp;
+    const int chunk = blockIdx.y;
+    if (i >= n_cells) return;
+    const double Tn = Fn[(size_t)i * NF + 7], Th = Fh[(size_t)i * NF + 7];
+    const Real dI = (Real)(om * (m.sigma_R * Tn * Tn * Tn * Tn / 3.14159265358979323846 -
+                                 m.sigma_R * Th * Th * Th * Th / 3.14159265358979323846));
+    Real acc[1 + DIM];
+#pragma unroll
+    for (int k = 0; k <= DIM; ++k) acc[k] = Real(0);
+    for (int ol = lane; ol < OCH; ol += 32) {
+        const int o = chunk * OCH + ol;
+        Real *ip = I + (size_t)i * oq.n_pad + o;
+        Real x = *ip;
+        if (o < oq.n) {
+            x += dI;
+            *ip = x;
+        }
+        const Real wI = oq.w[o] * x;
+        acc[0] += wI;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) acc[1 + a] += wI * oq.x[a * oq.n_pad + o];
+    }
+#pragma unroll
+    for (int k = 0; k <= DIM; ++k)
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], s);
+    if (lane == 0) {
+        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMO;
+#pragma unroll
+        for (int k = 0; k <= DIM; ++k) P[k] = acc[k];
+    }
+}
+
+// ------------------------------------------------------------------ kinetic boundary fluxes
+// Moments of the kinetic flux through every boundary face (one CTA per face): outgoing
+// molecules carry the cell's distribution, incoming ones the wall Maxwellian (density
+// from zero net mass flux of the outgoing ones) or the far-field state; photons likewise.
+// Rows as the synthetic equations: mass, momentum, total energy, e_r, e_v, e_R.
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, Quad<Real> vq, Quad<Real> oq,
+                                                       const Real *__restrict__ f, const Real *__restrict__ I,
+                                                       double *__restrict__ out) {
+    constexpr int MH = 3 - DIM, E = 1 + DIM, NS = DIM + 4;
+    const int b = blockIdx.x;
+    const int c = g.bf_cell[b];
+    const int pid = g.bf_patch[b];
+    const bool wall = g.patch_kind[pid] == 0;
+    const double *P = g.patch_state + (size_t)pid * 8;
+    const double *n = g.bf_n + (size_t)b * 2;
+    const double T = P[4], Tr = wall ? P[4] : P[5], Tv = wall ? P[4] : P[6], TR = wall ? P[4] : P[7];
+    const double Aw = pow(2.0 * 3.14159265358979323846 * T, -0.5 * DIM), Bw = 0.5 / T;
+    double acc[2 * NS + 1];
+    for (int k = 0; k < 2 * NS + 1; ++k) acc[k] = 0.0;
+    for (int v = threadIdx.x; v < vq.n; v += blockDim.x) {
+        double xi[DIM], xn = 0.0, x2 = 0.0;
+        for (int a = 0; a < DIM; ++a) {
+            xi[a] = (double)vq.x[a * vq.n_pad + v];
+            xn += xi[a] * n[a];
+            x2 += xi[a] * xi[a];
+        }
+        const double wf = (double)vq.w[v] * xn;
+        double f0, fh, f1, f2, *s;
+        if (xn > 0.0) {
+            const Vec<Real, 4> fv = vload<Real, 4>(f + ((size_t)c * vq.n_pad + v) * 4);
+            f0 = fv.v[0];
+            fh = fv.v[1];
+            f1 = fv.v[2];
+            f2 = fv.v[3];
+            s = acc;
+        } else {
+            double c2 = 0.0;
+            for (int a = 0; a < DIM; ++a) c2 += (xi[a] - P[1 + a]) * (xi[a] - P[1 + a]);
+            f0 = Aw * exp(-Bw * c2);
+            fh = MH * T * f0;
+            f1 = 0.5 * m.d_r * Tr * f0;
+            f2 = 0.5 * m.d_v * Tv * f0;
+            s = acc + NS;
+        }
+        s[0] += wf * f0;
+        for (int a = 0; a < DIM; ++a) s[1 + a] += wf * f0 * xi[a];
+        s[E] += wf * (0.5 * x2 * f0 + 0.5 * fh + f1 + f2);
+        s[E + 1] += wf * f1;
+        s[E + 2] += wf * f2;
+    }
+    const double Iin = m.sigma_R * TR * TR * TR * TR / 3.14159265358979323846;
+    for (int o = threadIdx.x; o < oq.n; o += blockDim.x) {
+        double on = 0.0;
+        for (int a = 0; a < DIM; ++a) on += (double)oq.x[a * oq.n_pad + o] * n[a];
+        acc[2 * NS] += (double)oq.w[o] * on * (on > 0.0 ? (double)I[(size_t)c * oq.n_pad + o] : Iin);
+    }
+    __shared__ double buf[4][2 * NS + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < 2 * NS + 1; ++k) {
+        double x = acc[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) buf[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[2 * NS + 1];
+        for (int k = 0; k < 2 * NS + 1; ++k) r[k] = buf[0][k] + buf[1][k] + buf[2][k] + buf[3][k];
+        const double scale = wall ? -r[0] / r[NS] : P[0];
+        double *o = out + (size_t)b * NVM;
+        for (int k = 0; k < NS; ++k) o[k] = r[k] + scale * r[NS + k];
+        o[E + 3] = r[2 * NS];
+        o[E] += o[E + 3];
+    }
+}
+
 // ------------------------------------------------------------------ finish (FP64)
 // Shifted moments S about the coefficient velocity u0 (the shift the sweep used):
 // with delta = S_c / rho the flow velocity is u0 + delta and every central moment
@@ -943,6 +1125,29 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, const Quad
     return cudaGetLastError();
 }
 
+template <typename Real>
+cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const Quad<Real> &vq,
+                                 const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux) {
+    if (g.n_bf == 0) return cudaSuccess;
+    GSIS_DISPATCH_DIM(g.dim, (k_kinetic_bflux<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, f, I, kin_bflux)));
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+                        const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
+                        Real *f, Real *I, Real *partial, Real *opartial) {
+    dim3 gg((n_cells + VCH / 32 - 1) / (VCH / 32), vq.n_pad / VCH);
+    dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
+    GSIS_DISPATCH_DIM(dim, (k_sync_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, m, omega, F_new, F_half, coef, f,
+                                                                     partial)));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    GSIS_DISPATCH_DIM(dim, (k_sync_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, m, omega, F_new, F_half, I,
+                                                                        opartial)));
+    return cudaGetLastError();
+}
+
 #define GSIS_INSTANTIATE(Real)                                                                                     \
     template cudaError_t launch_coefficients<Real>(cudaStream_t, int, const Geom<Real> &, const ModelDev &,        \
                                                    const double *, const double *, Real *);                        \
@@ -963,7 +1168,13 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, const Quad
     template cudaError_t launch_equilibrium<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &,  \
                                                   const ModelDev &, const double *, Real *, Real *);               \
     template cudaError_t launch_moments_only<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &, \
-                                                   const Real *, const Real *, const Real *, Real *, Real *);
+                                                   const Real *, const Real *, const Real *, Real *, Real *);      \
+    template cudaError_t launch_kinetic_bflux<Real>(cudaStream_t, const MacroGeom &, const ModelDev &,             \
+                                                    const Quad<Real> &, const Quad<Real> &, const Real *,          \
+                                                    const Real *, double *);                                       \
+    template cudaError_t launch_sync<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &,         \
+                                           const ModelDev &, double, const double *, const double *, const Real *, \
+                                           Real *, Real *, Real *, Real *);
 
 GSIS_INSTANTIATE(float)
 GSIS_INSTANTIATE(double)

@@ -1,0 +1,904 @@
+// Synthetic (macroscopic) equations of GSIS in FP64 (Sections 2.2, 3 and 5).
+//
+//  macro_from_fields   W = conservative variables of a field record
+//  macro_grad          primitive variables, least-squares gradients and Venkatakrishnan
+//                      limiters of every cell (the stencil of the kinetic sweep)
+//  macro_bflux         macroscopic flux through every boundary face: at walls the flux of
+//                      an equilibrium leaving at the cell state against the diffuse wall
+//                      (discrete velocity and direction sums), at the far field Rusanov
+//                      plus NSF against the free stream
+//  macro_hot           face high-order terms of Eq. (getHoTs): kinetic stress and heat
+//                      fluxes averaged to the face minus the NSF values of the kinetic
+//                      state; boundary terms = kinetic minus macroscopic boundary flux
+//  macro_residual      R = -(1/V) sum (F_c + F_v) S + Q (Eq. delta_macro, right-hand side),
+//                      the implicit diagonal D (with the exact local Jacobian of the energy
+//                      sources) and its inverse, and the per-block partial sums of |R|^2
+//  macro_norm          ||R||_2, the first-iteration reference and the stop flag
+//  macro_jacobi        one point-relaxation sweep of
+//                      D dW_i + (1/(2V)) sum_j (dF_j - Gamma dW_j) S = R_i
+//                      in the gas-energy form, W_next = W + dW after the last sweep
+//  kinetic_bflux       moments of the kinetic boundary fluxes of the current distribution
+//  sync                f <- f + w [f_eq(M^{k+1}) - f_eq(M^{k+1/2})] (Section 3) fused with
+//                      the velocity moments of the result
+//
+// Every kernel of the inner loop returns at once when the solve's stop flag is set,
+// so a fixed launch sequence can run past convergence without changing W.
+#include <cmath>
+
+#include "gsis_impl.cuh"
+
+namespace gsis {
+
+namespace {
+
+constexpr double PI = 3.14159265358979323846;
+
+__device__ __forceinline__ double viscosity(double T_t, const ModelDev &m) {
+    return sqrt(2.0 / PI) * m.Kn * pow(T_t, m.omega);          // mu = p_t tau
+}
+__device__ __forceinline__ double sound_speed(double T_t) { return sqrt(5.0 * T_t / 3.0); }
+__device__ __forceinline__ double absorption(double rho, const ModelDev &m) {
+    const double k = 1.0 / m.Kn_p;
+    return m.k_eff_density_scaled ? k * rho : k;
+}
+
+// base = A^-1 diag(5, d_r, d_v); kappa_gas = mu/2 base (Eq. NSF_thermal_conductivities)
+__device__ void kappa_base(const ModelDev &m, double (&B)[3][3]) {
+    const double *A = m.A;
+    const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                       A[2] * (A[3] * A[7] - A[4] * A[6]);
+    double Ai[3][3];
+    Ai[0][0] = (A[4] * A[8] - A[5] * A[7]) / det;
+    Ai[0][1] = (A[2] * A[7] - A[1] * A[8]) / det;
+    Ai[0][2] = (A[1] * A[5] - A[2] * A[4]) / det;
+    Ai[1][0] = (A[5] * A[6] - A[3] * A[8]) / det;
+    Ai[1][1] = (A[0] * A[8] - A[2] * A[6]) / det;
+    Ai[1][2] = (A[2] * A[3] - A[0] * A[5]) / det;
+    Ai[2][0] = (A[3] * A[7] - A[4] * A[6]) / det;
+    Ai[2][1] = (A[1] * A[6] - A[0] * A[7]) / det;
+    Ai[2][2] = (A[0] * A[4] - A[1] * A[3]) / det;
+    const double dg[3] = {5.0, m.d_r, m.d_v};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) B[a][b] = Ai[a][b] * dg[b];
+}
+
+template <int DIM>
+__device__ __forceinline__ void primitive(const double *W, const ModelDev &m, double *q) {
+    constexpr int E = 1 + DIM;
+    const double rho = W[0];
+    double ke = 0.0;
+    q[0] = rho;
+    for (int a = 0; a < DIM; ++a) {
+        q[1 + a] = W[1 + a] / rho;
+        ke += q[1 + a] * q[1 + a];
+    }
+    const double e = W[E], er = W[E + 1], ev = W[E + 2], eR = W[E + 3];
+    q[E] = (e - eR - er - ev - 0.5 * rho * ke) / (1.5 * rho);
+    q[E + 1] = 2.0 * er / (m.d_r * rho);
+    q[E + 2] = 2.0 * ev / (m.d_v * rho);
+    q[E + 3] = eR;
+}
+
+template <int DIM>
+__device__ __forceinline__ void prim_to_W(const double *q, const ModelDev &m, double *W) {
+    constexpr int E = 1 + DIM;
+    const double rho = q[0];
+    double uu = 0.0;
+    for (int a = 0; a < DIM; ++a) uu += q[1 + a] * q[1 + a];
+    const double er = 0.5 * m.d_r * rho * q[E + 1], ev = 0.5 * m.d_v * rho * q[E + 2];
+    W[0] = rho;
+    for (int a = 0; a < DIM; ++a) W[1 + a] = rho * q[1 + a];
+    W[E] = 1.5 * rho * q[E] + 0.5 * rho * uu + er + ev + q[E + 3];
+    W[E + 1] = er;
+    W[E + 2] = ev;
+    W[E + 3] = q[E + 3];
+}
+
+// F_c . n of Eq. (macroscopic_equation); e_R has no convective flux
+template <int DIM>
+__device__ __forceinline__ void convective_flux(const double *q, const double *n, const ModelDev &m, double *F) {
+    constexpr int E = 1 + DIM;
+    const double rho = q[0], T_t = q[E];
+    double un = 0.0, uu = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        un += q[1 + a] * n[a];
+        uu += q[1 + a] * q[1 + a];
+    }
+    const double p = rho * T_t;
+    const double er = 0.5 * m.d_r * rho * q[E + 1], ev = 0.5 * m.d_v * rho * q[E + 2];
+    const double eg = 1.5 * rho * T_t + 0.5 * rho * uu + er + ev;
+    F[0] = rho * un;
+    for (int a = 0; a < DIM; ++a) F[1 + a] = rho * q[1 + a] * un + p * n[a];
+    F[E] = un * (eg + p);
+    F[E + 1] = un * er;
+    F[E + 2] = un * ev;
+    F[E + 3] = 0.0;
+}
+
+// Rusanov flux: average of the two fluxes minus half the largest |u_n| + c_s times the
+// jump of the convected variables (gas energy, not e_R)
+template <int DIM>
+__device__ void rusanov(const double *qL, const double *qR, const double *n, const ModelDev &m, double *F) {
+    constexpr int NV = DIM + 5, E = 1 + DIM;
+    double FL[NV], FR[NV], WL[NV], WR[NV];
+    convective_flux<DIM>(qL, n, m, FL);
+    convective_flux<DIM>(qR, n, m, FR);
+    double unL = 0.0, unR = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        unL += qL[1 + a] * n[a];
+        unR += qR[1 + a] * n[a];
+    }
+    const double lam = fmax(fabs(unL) + sound_speed(qL[E]), fabs(unR) + sound_speed(qR[E]));
+    prim_to_W<DIM>(qL, m, WL);
+    prim_to_W<DIM>(qR, m, WR);
+    for (int k = 0; k < NV; ++k) {
+        double dW = WR[k] - WL[k];
+        if (k == E) dW -= WR[E + 3] - WL[E + 3];
+        if (k == E + 3) dW = 0.0;
+        F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * lam * dW;
+    }
+}
+
+// Venkatakrishnan's limiter function
+__device__ __forceinline__ double venkat(double d1, double d2, double eps2) {
+    return (d1 * d1 + eps2 + 2.0 * d1 * d2) / (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2);
+}
+
+// Q of Section 5: rotational and vibrational relaxation, gas-photon exchange
+template <int DIM>
+__device__ void source(const double *q, const ModelDev &m, double *Q) {
+    constexpr int NV = DIM + 5, E = 1 + DIM;
+    const double rho = q[0], Tt = q[E], Tr = q[E + 1], Tv = q[E + 2], eR = q[E + 3];
+    const double Ttr = (3.0 * Tt + m.d_r * Tr) / (3.0 + m.d_r);
+    const double Ttv = (3.0 * Tt + m.d_v * Tv) / (3.0 + m.d_v);
+    const double tau = sqrt(2.0 / PI) * pow(Tt, m.omega - 1.0) * m.Kn / rho;
+    const double k = absorption(rho, m);
+    const double evR = 4.0 * m.sigma_R * Tv * Tv * Tv * Tv;
+    for (int a = 0; a < NV; ++a) Q[a] = 0.0;
+    Q[E + 1] = 0.5 * m.d_r * rho * (Ttr - Tr) / (m.Z_r * tau);
+    Q[E + 2] = 0.5 * m.d_v * rho * (Ttv - Tv) / (m.Z_v * tau) - k * (evR - eR);
+    Q[E + 3] = k * (evR - eR);
+}
+
+// exact d(Q_egas, Q_r, Q_v, Q_R)/d(e_gas, e_r, e_v, e_R) with rho, rho u, tau, k_eff frozen
+template <int DIM>
+__device__ void source_jacobian(const double *q, const ModelDev &m, double (&J)[4][4]) {
+    constexpr int E = 1 + DIM;
+    const double rho = q[0], Tt = q[E], Tv = q[E + 2];
+    const double tau = sqrt(2.0 / PI) * pow(Tt, m.omega - 1.0) * m.Kn / rho;
+    const double k = absorption(rho, m);
+    const double cr = rho * 1.5 * m.d_r / (3.0 + m.d_r) / (m.Z_r * tau);
+    const double cv = rho * 1.5 * m.d_v / (3.0 + m.d_v) / (m.Z_v * tau);
+    const double beta = 16.0 * m.sigma_R * Tv * Tv * Tv * 2.0 / (m.d_v * rho);
+    const double a = 1.0 / (1.5 * rho);
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) J[r][c] = 0.0;
+    J[0][2] = -k * beta;
+    J[0][3] = k;
+    J[1][0] = cr * a;
+    J[1][1] = -cr * (a + 2.0 / (m.d_r * rho));
+    J[1][2] = -cr * a;
+    J[2][0] = cv * a;
+    J[2][1] = -cv * a;
+    J[2][2] = -cv * (a + 2.0 / (m.d_v * rho)) - k * beta;
+    J[2][3] = k;
+    J[3][2] = k * beta;
+    J[3][3] = -k;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ conversions
+template <int DIM>
+__global__ void k_macro_from_fields(int n_cells, ModelDev m, const double *__restrict__ F, double *__restrict__ W) {
+    constexpr int NV = DIM + 5, E = 1 + DIM;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    const double *r = F + (size_t)i * NF;
+    double q[NV];
+    q[0] = r[0];
+    for (int a = 0; a < DIM; ++a) q[1 + a] = r[1 + a];
+    q[E] = r[4];
+    q[E + 1] = r[5];
+    q[E + 2] = r[6];
+    const double TR = r[7];
+    q[E + 3] = 4.0 * m.sigma_R * TR * TR * TR * TR;
+    prim_to_W<DIM>(q, m, W + (size_t)i * NVM);
+}
+
+template <int DIM>
+__global__ void k_macro_fields_from_W(int n_cells, ModelDev m, const double *__restrict__ W, double *__restrict__ F) {
+    constexpr int NV = DIM + 5, E = 1 + DIM;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    double q[NV];
+    primitive<DIM>(W + (size_t)i * NVM, m, q);
+    double *r = F + (size_t)i * NF;
+    for (int k = 0; k < NF; ++k) r[k] = 0.0;
+    r[0] = q[0];
+    for (int a = 0; a < DIM; ++a) r[1 + a] = q[1 + a];
+    r[4] = q[E];
+    r[5] = q[E + 1];
+    r[6] = q[E + 2];
+    r[7] = sqrt(sqrt(fmax(q[E + 3], 0.0) / (4.0 * m.sigma_R)));
+}
+
+// ------------------------------------------------------------------ gradients and limiters
+// q [nc][NVM], grad [nc][2][NVM], phi [nc][NVM]
+template <int DIM, int ORDER>
+__global__ void k_macro_grad(MacroGeom g, ModelDev m, const MacroState *__restrict__ st, const double *__restrict__ W,
+                             double *__restrict__ qo, double *__restrict__ grad, double *__restrict__ phi) {
+    constexpr int NQ = DIM + 5;
+    if (st && st->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_cells) return;
+    double qi[NQ], gr[DIM][NQ], dmax[NQ], dmin[NQ];
+    primitive<DIM>(W + (size_t)i * NVM, m, qi);
+    for (int k = 0; k < NQ; ++k) {
+        dmax[k] = 0.0;
+        dmin[k] = 0.0;
+        for (int a = 0; a < DIM; ++a) gr[a][k] = 0.0;
+    }
+    const int4 info = g.info[i];
+    for (int k = 0; k < info.y; ++k) {
+        const int s = g.stn[i * MAXS + k];
+        double qs[NQ];
+        primitive<DIM>(W + (size_t)s * NVM, m, qs);
+        const double *C = g.lsq + ((size_t)i * MAXS + k) * 2;
+        for (int v = 0; v < NQ; ++v) {
+            const double dq = qs[v] - qi[v];
+            for (int a = 0; a < DIM; ++a) gr[a][v] += C[a] * dq;
+            if (k < info.z) {
+                dmax[v] = fmax(dmax[v], dq);
+                dmin[v] = fmin(dmin[v], dq);
+            }
+        }
+    }
+    for (int v = 0; v < NQ; ++v) {
+        qo[(size_t)i * NVM + v] = qi[v];
+        for (int a = 0; a < DIM; ++a) grad[((size_t)i * 2 + a) * NVM + v] = gr[a][v];
+    }
+    if constexpr (ORDER != 2) return;
+    double ph[NQ];
+    for (int v = 0; v < NQ; ++v) ph[v] = 1.0;
+    const double eps2 = g.eps2[i];
+    for (int k = 0; k < info.x; ++k) {
+        const int fid = g.cface[i * MAXF + k];
+        if (fid < 0) continue;
+        double d[DIM];
+        for (int a = 0; a < DIM; ++a) d[a] = g.fi_xf[fid * 2 + a] - g.xc[i * 2 + a];
+        for (int v = 0; v < NQ; ++v) {
+            double d2 = 0.0;
+            for (int a = 0; a < DIM; ++a) d2 += gr[a][v] * d[a];
+            const double d1 = d2 > 0.0 ? dmax[v] : dmin[v];
+            const double pf = d2 != 0.0 ? venkat(d1, d2, eps2) : 1.0;
+            ph[v] = fmin(ph[v], pf);
+        }
+    }
+    for (int v = 0; v < NQ; ++v) phi[(size_t)i * NVM + v] = ph[v];
+}
+
+// ------------------------------------------------------------------ face fluxes
+namespace {
+
+// NSF stress and heat fluxes of Eqs. (NSF_constitutive) and (NSF_thermal_conductivities)
+// at an interior face from the face-average state pf and the face gradient fg[a][v]
+// (gradient component a of primitive variable v); out layout as the high-order terms:
+// sigma (DIM x DIM), q_t, q_r, q_v, q_R (DIM each).
+template <int DIM>
+__device__ void nsf_face(const double *pf, const double (&fg)[DIM][DIM + 5], const ModelDev &m,
+                         const double (&base)[3][3], double *out) {
+    constexpr int E = 1 + DIM;
+    const double mu = viscosity(pf[E], m);
+    double div = 0.0;
+    for (int d = 0; d < DIM; ++d) div += fg[d][1 + d];
+    for (int a = 0; a < DIM; ++a)
+        for (int b = 0; b < DIM; ++b) {
+            const double S = fg[a][1 + b] + fg[b][1 + a];
+            out[a * DIM + b] = -mu * (S - (a == b ? 2.0 / 3.0 * div : 0.0));
+        }
+    for (int md = 0; md < 3; ++md)
+        for (int d = 0; d < DIM; ++d) {
+            double s = 0.0;
+            for (int nn = 0; nn < 3; ++nn) s += 0.5 * mu * base[md][nn] * fg[d][E + nn];
+            out[DIM * DIM + md * DIM + d] = -s;
+        }
+    const double kR = 1.0 / (3.0 * absorption(pf[0], m));
+    for (int d = 0; d < DIM; ++d) out[DIM * DIM + 3 * DIM + d] = -kR * fg[d][E + 3];
+}
+
+// face-average state and face gradient (average of the cells' least-squares gradients
+// with the component along x_j - x_i replaced by the difference quotient)
+template <int DIM>
+__device__ void face_state(const MacroGeom &g, int fid, const double *q, const double *grad, double *pf,
+                           double (&fg)[DIM][DIM + 5]) {
+    constexpr int NQ = DIM + 5;
+    const int i = g.fi_i[fid], j = g.fi_j[fid];
+    const double *qi = q + (size_t)i * NVM, *qj = q + (size_t)j * NVM;
+    const double *t = g.fi_t + (size_t)fid * 2;
+    const double dist = g.fi_dist[fid];
+    for (int v = 0; v < NQ; ++v) {
+        pf[v] = 0.5 * (qi[v] + qj[v]);
+        double along = 0.0;
+        double avg[DIM];
+        for (int a = 0; a < DIM; ++a) {
+            avg[a] = 0.5 * (grad[((size_t)i * 2 + a) * NVM + v] + grad[((size_t)j * 2 + a) * NVM + v]);
+            along += t[a] * avg[a];
+        }
+        const double jump = (qj[v] - qi[v]) / dist;
+        for (int a = 0; a < DIM; ++a) fg[a][v] = avg[a] + t[a] * (jump - along);
+    }
+}
+
+// (F_c + F_v) . n of interior face fid (owner -> neighbour orientation)
+template <int DIM, int ORDER>
+__device__ void interior_flux(const MacroGeom &g, const ModelDev &m, const double (&base)[3][3], int fid,
+                              const double *q, const double *grad, const double *phi, const double *hot, double *F) {
+    constexpr int NV = DIM + 5, E = 1 + DIM;
+    const int i = g.fi_i[fid], j = g.fi_j[fid];
+    const double *n = g.fi_n + (size_t)fid * 2;
+    double qL[NV], qR[NV];
+    for (int v = 0; v < NV; ++v) {
+        qL[v] = q[(size_t)i * NVM + v];
+        qR[v] = q[(size_t)j * NVM + v];
+    }
+    if (ORDER == 2) {
+        const double *xf = g.fi_xf + (size_t)fid * 2;
+        for (int v = 0; v < NV; ++v) {
+            double dL = 0.0, dR = 0.0;
+            for (int a = 0; a < DIM; ++a) {
+                dL += grad[((size_t)i * 2 + a) * NVM + v] * (xf[a] - g.xc[i * 2 + a]);
+                dR += grad[((size_t)j * 2 + a) * NVM + v] * (xf[a] - g.xc[j * 2 + a]);
+            }
+            qL[v] += phi[(size_t)i * NVM + v] * dL;
+            qR[v] += phi[(size_t)j * NVM + v] * dR;
+        }
+    }
+    rusanov<DIM>(qL, qR, n, m, F);
+    double pf[NV], fg[DIM][DIM + 5], s[NHOT];
+    face_state<DIM>(g, fid, q, grad, pf, fg);
+    nsf_face<DIM>(pf, fg, m, base, s);
+    const double *h = hot + (size_t)fid * NHOT;
+    for (int k = 0; k < DIM * DIM + 4 * DIM; ++k) s[k] += h[k];
+    double sn[DIM], un = 0.0, qn[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int a = 0; a < DIM; ++a) {
+        sn[a] = 0.0;
+        for (int b = 0; b < DIM; ++b) sn[a] += s[a * DIM + b] * n[b];
+        un += sn[a] * pf[1 + a];
+    }
+    double qtot = 0.0;
+    for (int d = 0; d < DIM; ++d) {
+        const double *qq = s + DIM * DIM;
+        qtot += (qq[d] + qq[DIM + d] + qq[2 * DIM + d] + qq[3 * DIM + d]) * n[d];
+        for (int md = 0; md < 4; ++md) qn[md] += qq[md * DIM + d] * n[d];
+    }
+    for (int a = 0; a < DIM; ++a) F[1 + a] += sn[a];
+    F[E] += un + qtot;
+    F[E + 1] += qn[1];
+    F[E + 2] += qn[2];
+    F[E + 3] += qn[3];
+}
+
+// Far-field boundary flux: Rusanov against the free stream plus NSF terms over the
+// distance from the cell centre to the face
+template <int DIM>
+__device__ void farfield_flux(const MacroGeom &g, const ModelDev &m, const double (&base)[3][3], int b,
+                              const double *qc, double *F) {
+    constexpr int E = 1 + DIM;
+    const double *P = g.patch_state + (size_t)g.bf_patch[b] * 8;
+    const double *n = g.bf_n + (size_t)b * 2;
+    const double dn = g.bf_dn[b];
+    double qf[DIM + 5];
+    qf[0] = P[0];
+    for (int a = 0; a < DIM; ++a) qf[1 + a] = P[1 + a];
+    qf[E] = P[4];
+    qf[E + 1] = P[5];
+    qf[E + 2] = P[6];
+    qf[E + 3] = 4.0 * m.sigma_R * P[7] * P[7] * P[7] * P[7];
+    rusanov<DIM>(qc, qf, n, m, F);
+    const double mu = viscosity(0.5 * (qc[E] + P[4]), m);
+    double du[DIM], dun = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        du[a] = P[1 + a] - qc[1 + a];
+        dun += n[a] * du[a];
+    }
+    double sn[DIM], snu = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        sn[a] = -mu / dn * (du[a] + (dun / 3.0) * n[a]);
+        snu += sn[a] * 0.5 * (P[1 + a] + qc[1 + a]);
+    }
+    const double dT[3] = {P[4] - qc[E], P[5] - qc[E + 1], P[6] - qc[E + 2]};
+    double qm[3];
+    for (int md = 0; md < 3; ++md) {
+        double s = 0.0;
+        for (int nn = 0; nn < 3; ++nn) s += 0.5 * mu * base[md][nn] * dT[nn];
+        qm[md] = -s / dn;
+    }
+    const double keff = absorption(qc[0], m);
+    const double qR = -(qf[E + 3] - qc[E + 3]) / (3.0 * keff * dn);
+    for (int a = 0; a < DIM; ++a) F[1 + a] += sn[a];
+    F[E] += snu + (qm[0] + qm[1] + qm[2]) + qR;
+    F[E + 1] += qm[1];
+    F[E + 2] += qm[2];
+    F[E + 3] += qR;
+}
+
+// block-wide sum of n values per thread into shared memory red[n]; all threads get it
+template <int NT>
+__device__ void block_sum(double *vals, int n, double *red) {
+    __shared__ double buf[NT / 32][16];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int k = 0; k < n; ++k) {
+        double x = vals[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) buf[w][k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < n) {
+        double x = 0.0;
+        for (int ww = 0; ww < NT / 32; ++ww) x += buf[ww][threadIdx.x];
+        red[threadIdx.x] = x;
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ boundary fluxes
+// One CTA per boundary face.  Walls: outgoing molecules in equilibrium at the cell state,
+// incoming ones the diffuse wall Maxwellian with the density that zeroes the mass flux;
+// photons leave isotropically (e_R / 4 pi) and enter black-body (sigma_R T_w^4 / pi).
+// The incoming sums are linear in the wall density and are taken for unit density.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, QuadD vq, QuadD oq,
+                                                     const MacroState *__restrict__ st, const double *__restrict__ q,
+                                                     double *__restrict__ bflux) {
+    constexpr int NV = DIM + 5, E = 1 + DIM, MH = 3 - DIM;
+    constexpr int NS = DIM + 4;   // mass, momentum, gas energy, e_r, e_v
+    if (st && st->done) return;
+    const int b = blockIdx.x;
+    const int c = g.bf_cell[b];
+    const double *qc = q + (size_t)c * NVM;
+    double *out = bflux + (size_t)b * NVM;
+    const int pk = g.patch_kind[g.bf_patch[b]];
+    __shared__ double red[2 * NS + 2];
+    if (pk != 0) {   // far field
+        if (threadIdx.x == 0) {
+            double base[3][3], F[NV];
+            kappa_base(m, base);
+            farfield_flux<DIM>(g, m, base, b, qc, F);
+            for (int k = 0; k < NV; ++k) out[k] = F[k];
+        }
+        return;
+    }
+    const double *P = g.patch_state + (size_t)g.bf_patch[b] * 8;
+    const double *n = g.bf_n + (size_t)b * 2;
+    const double rho = qc[0], Tt = qc[E], Tr = qc[E + 1], Tv = qc[E + 2], eR = qc[E + 3];
+    const double Tw = P[4];
+    const double Ac = rho * pow(2.0 * PI * Tt, -0.5 * DIM), Bc = 0.5 / Tt;
+    const double Aw = pow(2.0 * PI * Tw, -0.5 * DIM), Bw = 0.5 / Tw;
+    double acc[2 * NS + 2];
+    for (int k = 0; k < 2 * NS + 2; ++k) acc[k] = 0.0;
+    for (int v = threadIdx.x; v < vq.n; v += blockDim.x) {
+        double xi[DIM], xn = 0.0, x2 = 0.0;
+        for (int a = 0; a < DIM; ++a) {
+            xi[a] = vq.x[a * vq.n_pad + v];
+            xn += xi[a] * n[a];
+            x2 += xi[a] * xi[a];
+        }
+        const double wf = vq.w[v] * xn;
+        double f0, fh, f1, f2;
+        double *s;
+        if (xn > 0.0) {
+            double c2 = 0.0;
+            for (int a = 0; a < DIM; ++a) c2 += (xi[a] - qc[1 + a]) * (xi[a] - qc[1 + a]);
+            f0 = Ac * exp(-Bc * c2);
+            fh = MH * Tt * f0;
+            f1 = 0.5 * m.d_r * Tr * f0;
+            f2 = 0.5 * m.d_v * Tv * f0;
+            s = acc;
+        } else {
+            double c2 = 0.0;
+            for (int a = 0; a < DIM; ++a) c2 += (xi[a] - P[1 + a]) * (xi[a] - P[1 + a]);
+            f0 = Aw * exp(-Bw * c2);
+            fh = MH * Tw * f0;
+            f1 = 0.5 * m.d_r * Tw * f0;
+            f2 = 0.5 * m.d_v * Tw * f0;
+            s = acc + NS;
+        }
+        s[0] += wf * f0;
+        for (int a = 0; a < DIM; ++a) s[1 + a] += wf * f0 * xi[a];
+        s[E] += wf * (0.5 * x2 * f0 + 0.5 * fh + f1 + f2);
+        s[E + 1] += wf * f1;
+        s[E + 2] += wf * f2;
+    }
+    const double Iw = m.sigma_R * Tw * Tw * Tw * Tw / PI, Io = eR / (4.0 * PI);
+    for (int o = threadIdx.x; o < oq.n; o += blockDim.x) {
+        double on = 0.0;
+        for (int a = 0; a < DIM; ++a) on += oq.x[a * oq.n_pad + o] * n[a];
+        acc[2 * NS] += oq.w[o] * on * (on > 0.0 ? Io : Iw);
+    }
+    block_sum<128>(acc, 2 * NS + 1, red);
+    if (threadIdx.x == 0) {
+        const double rw = -red[0] / red[NS];
+        double F[NV];
+        for (int k = 0; k < NS; ++k) F[k] = red[k] + rw * red[NS + k];
+        F[E + 3] = red[2 * NS];
+        F[E] += F[E + 3];
+        for (int k = 0; k < NV; ++k) out[k] = F[k];
+    }
+}
+
+// ------------------------------------------------------------------ high-order terms
+// one thread per interior face, then one per boundary face
+template <int DIM>
+__global__ void k_macro_hot(MacroGeom g, ModelDev m, const double *__restrict__ Fk, const double *__restrict__ q,
+                            const double *__restrict__ grad, const double *__restrict__ kin_bflux,
+                            const double *__restrict__ mac_bflux, double *__restrict__ hot,
+                            double *__restrict__ hot_b) {
+    constexpr int NV = DIM + 5;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < g.n_fi) {
+        double base[3][3];
+        kappa_base(m, base);
+        double pf[NV], fg[DIM][DIM + 5], s[NHOT];
+        face_state<DIM>(g, t, q, grad, pf, fg);
+        nsf_face<DIM>(pf, fg, m, base, s);
+        const double *ri = Fk + (size_t)g.fi_i[t] * NF, *rj = Fk + (size_t)g.fi_j[t] * NF;
+        auto sig = [&](const double *r, int a, int b) {
+            const int idx[3][3] = {{20, 23, 24}, {23, 21, 25}, {24, 25, 22}};
+            return r[idx[a][b]];
+        };
+        double *h = hot + (size_t)t * NHOT;
+        for (int a = 0; a < DIM; ++a)
+            for (int b = 0; b < DIM; ++b) h[a * DIM + b] = 0.5 * (sig(ri, a, b) + sig(rj, a, b)) - s[a * DIM + b];
+        for (int md = 0; md < 4; ++md)
+            for (int d = 0; d < DIM; ++d) {
+                const int k = 8 + 3 * md + d;
+                h[DIM * DIM + md * DIM + d] = 0.5 * (ri[k] + rj[k]) - s[DIM * DIM + md * DIM + d];
+            }
+        return;
+    }
+    const int b = t - g.n_fi;
+    if (b < g.n_bf)
+        for (int k = 0; k < NV; ++k)
+            hot_b[(size_t)b * NVM + k] = kin_bflux[(size_t)b * NVM + k] - mac_bflux[(size_t)b * NVM + k];
+}
+
+// ------------------------------------------------------------------ residual and diagonal
+constexpr int MR_NT = 128;     // threads per CTA of the residual kernel
+constexpr int DSTR = 24;       // Dinv record: NVM diagonal inverses (first E used), 4x4 block
+
+namespace {
+
+// Gauss-Jordan inverse of a 4x4 matrix with partial pivoting
+__device__ void inverse4(const double (&A)[4][4], double (&X)[4][4]) {
+    double M[4][8];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            M[r][c] = A[r][c];
+            M[r][4 + c] = r == c ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < 4; ++c) {
+        int p = c;
+        for (int r = c + 1; r < 4; ++r)
+            if (fabs(M[r][c]) > fabs(M[p][c])) p = r;
+        if (p != c)
+            for (int k = 0; k < 8; ++k) {
+                const double t = M[c][k];
+                M[c][k] = M[p][k];
+                M[p][k] = t;
+            }
+        const double inv = 1.0 / M[c][c];
+        for (int k = 0; k < 8; ++k) M[c][k] *= inv;
+        for (int r = 0; r < 4; ++r) {
+            if (r == c) continue;
+            const double f = M[r][c];
+            for (int k = 0; k < 8; ++k) M[r][k] -= f * M[c][k];
+        }
+    }
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) X[r][c] = M[r][4 + c];
+}
+
+}  // namespace
+
+template <int DIM, int ORDER>
+__global__ void __launch_bounds__(MR_NT) k_macro_residual(MacroGeom g, ModelDev m, double cfl_macro,
+                                                          const MacroState *__restrict__ st,
+                                                          const double *__restrict__ q, const double *__restrict__ grad,
+                                                          const double *__restrict__ phi, const double *__restrict__ hot,
+                                                          const double *__restrict__ bflux,
+                                                          const double *__restrict__ hot_b, double *__restrict__ Rg,
+                                                          double *__restrict__ Dinv, double *__restrict__ gam,
+                                                          double *__restrict__ rpart) {
+    constexpr int NV = DIM + 5, E = 1 + DIM, ER = 4 + DIM;
+    if (st && st->done) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double r2 = 0.0;
+    if (i < g.n_cells) {
+        double base[3][3];
+        kappa_base(m, base);
+        const double *qi = q + (size_t)i * NVM;
+        double R[NV], gsum = 0.0, gsumR = 0.0;
+        for (int k = 0; k < NV; ++k) R[k] = 0.0;
+        const int nf = g.info[i].x;
+        for (int k = 0; k < nf; ++k) {
+            const int fid = g.cface[i * MAXF + k];
+            if (fid >= 0) {
+                double F[NV];
+                interior_flux<DIM, ORDER>(g, m, base, fid, q, grad, phi, hot, F);
+                const double S = g.fi_S[fid];
+                const bool own = g.fi_i[fid] == i;
+                for (int v = 0; v < NV; ++v) R[v] += own ? -F[v] * S : F[v] * S;
+                const int o = own ? g.fi_j[fid] : g.fi_i[fid];
+                const double *qo = q + (size_t)o * NVM;
+                const double *n = g.fi_n + (size_t)fid * 2;
+                const double rf = 0.5 * (qi[0] + qo[0]), Tf = 0.5 * (qi[E] + qo[E]);
+                double un = 0.0;
+                for (int a = 0; a < DIM; ++a) un += 0.5 * (qi[1 + a] + qo[1 + a]) * n[a];
+                const double dn = g.fi_dn[fid];
+                const double gb = fabs(un) + sound_speed(Tf) + 2.0 * viscosity(Tf, m) / (rf * dn);
+                const double gR = 2.0 * (1.0 / (3.0 * absorption(rf, m))) / dn;
+                gam[((size_t)i * MAXF + k) * 2] = gb;
+                gam[((size_t)i * MAXF + k) * 2 + 1] = gR;
+                gsum += gb * S;
+                gsumR += gR * S;
+            } else {
+                const int b = -1 - fid;
+                const double S = g.bf_S[b];
+                for (int v = 0; v < NV; ++v)
+                    R[v] -= (bflux[(size_t)b * NVM + v] + hot_b[(size_t)b * NVM + v]) * S;
+                const double *n = g.bf_n + (size_t)b * 2;
+                double un = 0.0;
+                for (int a = 0; a < DIM; ++a) un += qi[1 + a] * n[a];
+                const double db = g.bf_dn[b];
+                const double gb = fabs(un) + sound_speed(qi[E]) + 2.0 * viscosity(qi[E], m) / (qi[0] * db);
+                const double gR = 2.0 * (1.0 / (3.0 * absorption(qi[0], m))) / db;
+                gsum += gb * S;
+                gsumR += gR * S;
+            }
+        }
+        const double V = g.vol[i];
+        double Q[NV];
+        source<DIM>(qi, m, Q);
+        for (int v = 0; v < NV; ++v) {
+            R[v] = R[v] / V + Q[v];
+            r2 += R[v] * R[v];
+        }
+        double *rg = Rg + (size_t)i * NVM;
+        for (int v = 0; v < NV; ++v) rg[v] = R[v];
+        rg[E] -= R[ER];
+        // D = diag(1/dt + sum Gamma S / V) - dQ/dW (energy rows)
+        double um = 0.0;
+        for (int a = 0; a < DIM; ++a) um += qi[1 + a] * qi[1 + a];
+        const double inv_dt = (sqrt(um) + sound_speed(qi[E])) / (cfl_macro * g.dx[i]);
+        double *Di = Dinv + (size_t)i * DSTR;
+        const double d0 = inv_dt + gsum / V;
+        for (int v = 0; v < E; ++v) Di[v] = 1.0 / d0;
+        double J[4][4], Dm[4][4], X[4][4];
+        source_jacobian<DIM>(qi, m, J);
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) Dm[r][c] = (r == c ? (r == 3 ? inv_dt + (gsum + gsumR) / V : d0) : 0.0) - J[r][c];
+        inverse4(Dm, X);
+        for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) Di[NVM + r * 4 + c] = X[r][c];
+    }
+    // deterministic per-CTA partial of |R|^2
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    __shared__ double wsum[MR_NT / 32];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = r2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < MR_NT / 32; ++w) s += wsum[w];
+        rpart[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_macro_norm(int n_parts, const double *__restrict__ rpart, MacroState *__restrict__ st,
+                             double *__restrict__ history) {
+    __shared__ double buf[256];
+    if (st->done) return;
+    if (st->it >= st->max_inner) {
+        if (threadIdx.x == 0) st->done = 1;
+        return;
+    }
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n_parts; k += blockDim.x) s += rpart[k];
+    buf[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) buf[threadIdx.x] += buf[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double rn = sqrt(buf[0]);
+        if (st->it == 0) st->r0 = rn;
+        st->rn = rn;
+        if (history) history[st->it] = rn;
+        st->it += 1;
+        if (!isfinite(rn) || rn <= st->tol * st->r0) st->done = 1;
+    }
+}
+
+// one point-relaxation sweep: every cell uses its neighbours' increments of the previous
+// sweep; increments are kept in the gas-energy form (row E holds d e_gas)
+template <int DIM>
+__global__ void k_macro_jacobi(MacroGeom g, ModelDev m, const MacroState *__restrict__ st, int first, int last,
+                               const double *__restrict__ W, const double *__restrict__ Rg,
+                               const double *__restrict__ Dinv, const double *__restrict__ gam,
+                               const double *__restrict__ dG_in, double *__restrict__ dG_out,
+                               double *__restrict__ W_next) {
+    constexpr int NV = DIM + 5, E = 1 + DIM, ER = 4 + DIM;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n_cells) return;
+    const double *Wi = W + (size_t)i * NVM;
+    if (st->done) {
+        if (last)
+            for (int v = 0; v < NV; ++v) W_next[(size_t)i * NVM + v] = Wi[v];
+        return;
+    }
+    double off[NV];
+    for (int v = 0; v < NV; ++v) off[v] = 0.0;
+    if (!first) {
+        const int nf = g.info[i].x;
+        for (int k = 0; k < nf; ++k) {
+            const int fid = g.cface[i * MAXF + k];
+            if (fid < 0) continue;
+            const bool own = g.fi_i[fid] == i;
+            const int o = own ? g.fi_j[fid] : g.fi_i[fid];
+            double n[2] = {0.0, 0.0};
+            for (int a = 0; a < DIM; ++a) n[a] = own ? g.fi_n[(size_t)fid * 2 + a] : -g.fi_n[(size_t)fid * 2 + a];
+            const double *Wo = W + (size_t)o * NVM, *dGo = dG_in + (size_t)o * NVM;
+            double Wp[NV], q0[NV], q1[NV], F0[NV], F1[NV];
+            for (int v = 0; v < NV; ++v) Wp[v] = Wo[v] + dGo[v];
+            Wp[E] += dGo[ER];
+            primitive<DIM>(Wo, m, q0);
+            primitive<DIM>(Wp, m, q1);
+            convective_flux<DIM>(q1, n, m, F1);
+            convective_flux<DIM>(q0, n, m, F0);
+            const double S = g.fi_S[fid];
+            const double gb = gam[((size_t)i * MAXF + k) * 2], gR = gam[((size_t)i * MAXF + k) * 2 + 1];
+            for (int v = 0; v < NV; ++v) {
+                const double G = v == ER ? gb + gR : gb;
+                off[v] += ((F1[v] - F0[v]) - G * dGo[v]) * S;
+            }
+        }
+    }
+    const double V = g.vol[i];
+    double x[NV];
+    const double *rg = Rg + (size_t)i * NVM;
+    for (int v = 0; v < NV; ++v) x[v] = rg[v] - off[v] / (2.0 * V);
+    const double *Di = Dinv + (size_t)i * DSTR;
+    double dG[NV];
+    for (int v = 0; v < E; ++v) dG[v] = Di[v] * x[v];
+    for (int r = 0; r < 4; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < 4; ++c) s += Di[NVM + r * 4 + c] * x[E + c];
+        dG[E + r] = s;
+    }
+    for (int v = 0; v < NV; ++v) dG_out[(size_t)i * NVM + v] = dG[v];
+    if (last) {
+        for (int v = 0; v < NV; ++v) W_next[(size_t)i * NVM + v] = Wi[v] + dG[v];
+        W_next[(size_t)i * NVM + E] += dG[ER];
+    }
+}
+
+// closed domains: scale W so that its total mass equals that of the reference fields
+__global__ void k_macro_mass_rescale(int nv, int n_cells, const double *__restrict__ vol,
+                                     const double *__restrict__ F_ref, double *__restrict__ W) {
+    __shared__ double a[1024], b[1024];
+    double sa = 0.0, sb = 0.0;
+    for (int i = threadIdx.x; i < n_cells; i += blockDim.x) {
+        sa += F_ref[(size_t)i * NF] * vol[i];
+        sb += W[(size_t)i * NVM] * vol[i];
+    }
+    a[threadIdx.x] = sa;
+    b[threadIdx.x] = sb;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            a[threadIdx.x] += a[threadIdx.x + w];
+            b[threadIdx.x] += b[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    const double fac = a[0] / b[0];
+    for (int i = threadIdx.x; i < n_cells; i += blockDim.x)
+        for (int v = 0; v < nv; ++v) W[(size_t)i * NVM + v] *= fac;
+}
+
+// ------------------------------------------------------------------ launchers
+#define MACRO_DISPATCH(dim, ...)          \
+    do {                                  \
+        if ((dim) == 1) {                 \
+            constexpr int DIM = 1;        \
+            __VA_ARGS__;                  \
+        } else {                          \
+            constexpr int DIM = 2;        \
+            __VA_ARGS__;                  \
+        }                                 \
+    } while (0)
+
+int macro_rpart_count(int n_cells) { return (n_cells + MR_NT - 1) / MR_NT; }
+
+cudaError_t launch_macro_from_fields(cudaStream_t s, int dim, int n_cells, const ModelDev &m, const double *F,
+                                     double *W) {
+    const int nb = (n_cells + 127) / 128;
+    MACRO_DISPATCH(dim, (k_macro_from_fields<DIM><<<nb, 128, 0, s>>>(n_cells, m, F, W)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_fields_from_W(cudaStream_t s, int dim, int n_cells, const ModelDev &m, const double *W,
+                                       double *F) {
+    const int nb = (n_cells + 127) / 128;
+    MACRO_DISPATCH(dim, (k_macro_fields_from_W<DIM><<<nb, 128, 0, s>>>(n_cells, m, W, F)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_grad(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m,
+                              const MacroState *st, const double *W, double *q, double *grad, double *phi) {
+    const int nb = (g.n_cells + 127) / 128;
+    if (order == 2) {
+        MACRO_DISPATCH(g.dim, (k_macro_grad<DIM, 2><<<nb, 128, 0, s>>>(g, m, st, W, q, grad, phi)));
+    } else {
+        MACRO_DISPATCH(g.dim, (k_macro_grad<DIM, 1><<<nb, 128, 0, s>>>(g, m, st, W, q, grad, phi)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const QuadD &vq,
+                               const QuadD &oq, const MacroState *st, const double *q, double *bflux) {
+    if (g.n_bf == 0) return cudaSuccess;
+    MACRO_DISPATCH(g.dim, (k_macro_bflux<DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, st, q, bflux)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_hot(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const double *F_kin,
+                             const double *q, const double *grad, const double *kin_bflux, const double *mac_bflux,
+                             double *hot, double *hot_b) {
+    const int n = g.n_fi + g.n_bf, nb = (n + 127) / 128;
+    if (n == 0) return cudaSuccess;
+    MACRO_DISPATCH(g.dim, (k_macro_hot<DIM><<<nb, 128, 0, s>>>(g, m, F_kin, q, grad, kin_bflux, mac_bflux, hot,
+                                                                hot_b)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m, double cfl_macro,
+                                  const MacroState *st, const double *W, const double *q, const double *grad,
+                                  const double *phi, const double *hot, const double *bflux, const double *hot_b,
+                                  double *Rg, double *Dinv, double *gam, double *rpart) {
+    (void)W;
+    const int nb = macro_rpart_count(g.n_cells);
+    if (order == 2) {
+        MACRO_DISPATCH(g.dim, (k_macro_residual<DIM, 2><<<nb, MR_NT, 0, s>>>(g, m, cfl_macro, st, q, grad, phi, hot,
+                                                                              bflux, hot_b, Rg, Dinv, gam, rpart)));
+    } else {
+        MACRO_DISPATCH(g.dim, (k_macro_residual<DIM, 1><<<nb, MR_NT, 0, s>>>(g, m, cfl_macro, st, q, grad, phi, hot,
+                                                                              bflux, hot_b, Rg, Dinv, gam, rpart)));
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_norm(cudaStream_t s, int n_parts, const double *rpart, MacroState *st, double *history) {
+    k_macro_norm<<<1, 256, 0, s>>>(n_parts, rpart, st, history);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const MacroState *st,
+                                int first, int last, const double *W, const double *Rg, const double *Dinv,
+                                const double *gam, const double *dG_in, double *dG_out, double *W_next) {
+    const int nb = (g.n_cells + 127) / 128;
+    MACRO_DISPATCH(g.dim, (k_macro_jacobi<DIM><<<nb, 128, 0, s>>>(g, m, st, first, last, W, Rg, Dinv, gam, dG_in,
+                                                                   dG_out, W_next)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_macro_mass_rescale(cudaStream_t s, int dim, int n_cells, const double *vol, const double *F_ref,
+                                      double *W) {
+    k_macro_mass_rescale<<<1, 1024, 0, s>>>(dim + 5, n_cells, vol, F_ref, W);
+    return cudaGetLastError();
+}
+
+}  // namespace gsis

@@ -61,7 +61,8 @@ class gsis_solver_params(C.Structure):
     _fields_ = [("precision", C.c_int32), ("order", C.c_int32), ("relax_block", C.c_int32),
                 ("cfl_meso", C.c_double), ("cfl_macro", C.c_double), ("venkat_K", C.c_double),
                 ("n_cis_precond", C.c_int32), ("max_outer", C.c_int32), ("max_inner", C.c_int32),
-                ("macro_sweeps", C.c_int32), ("tol_outer", C.c_double), ("tol_inner", C.c_double)]
+                ("macro_sweeps", C.c_int32), ("tol_outer", C.c_double), ("tol_inner", C.c_double),
+                ("sync_relax", C.c_double)]
 
 
 _LIB = None
@@ -169,7 +170,8 @@ def gsis_create(dim, face_owner, face_nbr, face_normal, face_area, face_centroid
     prec = {"fp32": GSIS_FP32, "fp64": GSIS_FP64}.get(solver.precision, solver.precision)
     sp = gsis_solver_params(prec, solver.order, getattr(solver, "relax_block", 16), solver.cfl_meso,
                             solver.cfl_macro, solver.venkat_K, solver.n_cis_precond, solver.max_outer,
-                            solver.max_inner, solver.macro_sweeps, solver.tol_outer, solver.tol_inner)
+                            solver.max_inner, solver.macro_sweeps, solver.tol_outer, solver.tol_inner,
+                            getattr(solver, "sync_relax", 1.0))
     out = C.c_void_p()
     rc = lib.gsis_create(C.byref(mesh), C.byref(vq), C.byref(pq), C.byref(mp), C.byref(sp), C.c_void_p(stream),
                          C.byref(out))

@@ -53,8 +53,8 @@ def _run(wl, f, I):
 
 
 CASES = {
-    # 338 cells: 21 blocks of 16 and a ragged block of 2; 784 velocities: 6 full chunks
-    # of 128 and a ragged one; 64 photon directions
+    # 338 cells: 21 blocks of 16 and a ragged block of 2; 784 velocities: 12 full chunks
+    # of 64 and a ragged one; 64 photon directions
     "cavity338": lambda: gi.workloads.cavity(n_side=13),
     # 64 cells, 32 Gauss-Hermite velocities and 16 photon directions (one ragged chunk each)
     "slab64": lambda: gi.workloads.slab(64),
