@@ -179,16 +179,36 @@ int gsis_download_fields_async(gsis_ctx *ctx, double *out, int64_t len);
 /* One outer iteration from the current distributions f^k (Section 3):
  * CIS:  moments M^k -> reference distributions -> one implicit sweep (Eq. dis_micro)
  *       for gas and photons -> f^{k+1} and M^{k+1}.
+ * GSIS: the same kinetic step gives f^{k+1/2} and M^{k+1/2}; the high-order terms of
+ *       Eq. (getHoTs) from f^{k+1/2} are frozen and the synthetic equations (Eq.
+ *       macroscopic_equation, implicit form Eq. delta_macro) are relaxed in FP64 for up
+ *       to max_inner pseudo-time steps of macro_sweeps point-relaxation sweeps, until
+ *       ||R|| <= tol_inner ||R_0||, giving M^{k+1} (in a domain bounded by walls only,
+ *       rescaled to the total mass of M^k); then f^{k+1} = f^{k+1/2} + sync_relax
+ *       [f_eq(M^{k+1}) - f_eq(M^{k+1/2})] and likewise for I.
  * *eps_out (may be NULL) receives the convergence measure of Section 6 between M^k
  * and M^{k+1}.  This call synchronises the stream to read eps.
- * Errors: DIVERGED (non-finite or non-positive density/temperature), CUDA, UNSUPPORTED. */
+ * Errors: DIVERGED (non-finite or non-positive density/temperature), CUDA, INVALID_ARG. */
 int gsis_step(gsis_ctx *ctx, int32_t mode, double *eps_out);
+
+/* Iterate to a steady state (Section 6): CIS for the first n_cis_precond iterations
+ * (mode GSIS_MODE_GSIS) or throughout (GSIS_MODE_CIS), then GSIS, until eps < tol or
+ * max_outer iterations.  max_outer <= 0 and tol <= 0 take the solver parameters'
+ * values.  *iters_out (may be NULL) receives the number of iterations; eps_history (may
+ * be NULL, else at least max_outer doubles, caller-owned) receives eps of each.
+ * Errors: NOT_CONVERGED (max_outer reached; the state is kept), DIVERGED, CUDA. */
+int gsis_solve(gsis_ctx *ctx, int32_t mode, int32_t max_outer, double tol, int32_t *iters_out,
+               double *eps_history);
 
 /* Same iteration without reading eps back: the device work is queued on the context
  * stream and the call returns at once.  gsis_last_eps() synchronises and returns the
  * measure of the most recent iteration. */
 int gsis_step_async(gsis_ctx *ctx, int32_t mode);
 int gsis_last_eps(gsis_ctx *ctx, double *eps_out);
+
+/* The synthetic solve of the most recent GSIS iteration: inner iterations taken and the
+ * first and last residual norms ||R||_2.  Synchronises the context stream. */
+int gsis_macro_stats(gsis_ctx *ctx, int32_t *inner_iters, double *r0, double *rn);
 
 /* Kernel timing.  While enabled, the library brackets each of its kernel launches with
  * CUDA events on the context stream and accumulates device time per kernel id.

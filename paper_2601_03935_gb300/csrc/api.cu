@@ -1065,6 +1065,33 @@ int gsis_step(gsis_ctx *c, int32_t mode, double *eps_out) {
     return read_eps(c, eps_out);
 }
 
+int gsis_solve(gsis_ctx *c, int32_t mode, int32_t max_outer, double tol, int32_t *iters_out, double *eps_history) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (mode != GSIS_MODE_CIS && mode != GSIS_MODE_GSIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
+    const int n = max_outer > 0 ? max_outer : c->solver.max_outer;
+    const double t = tol > 0 ? tol : c->solver.tol_outer;
+    if (iters_out) *iters_out = 0;
+    for (int k = 0; k < n; ++k) {
+        const int md = (mode == GSIS_MODE_GSIS && k >= c->solver.n_cis_precond) ? GSIS_MODE_GSIS : GSIS_MODE_CIS;
+        double e = 0.0;
+        TRY(gsis_step(c, md, &e));
+        if (eps_history) eps_history[k] = e;
+        if (iters_out) *iters_out = k + 1;
+        if (e < t) return GSIS_OK;
+    }
+    return fail(c, GSIS_ERR_NOT_CONVERGED, "max_outer reached before tol");
+}
+
+int gsis_macro_stats(gsis_ctx *c, int32_t *inner_iters, double *r0, double *rn) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_mstate, c->mstate, sizeof(MacroState), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (inner_iters) *inner_iters = c->h_mstate->it;
+    if (r0) *r0 = c->h_mstate->r0;
+    if (rn) *rn = c->h_mstate->rn;
+    return GSIS_OK;
+}
+
 int gsis_profile_enable(gsis_ctx *c, int32_t on) {
     if (!c) return GSIS_ERR_INVALID_ARG;
     c->prof = on != 0;

@@ -93,6 +93,8 @@ def load():
         "gsis_download_fields_async": (C.c_int, [vp, _dp, C.c_int64]),
         "gsis_step": (C.c_int, [vp, C.c_int32, _dp]),
         "gsis_step_async": (C.c_int, [vp, C.c_int32]),
+        "gsis_solve": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_double, _ip, _dp]),
+        "gsis_macro_stats": (C.c_int, [vp, _ip, _dp, _dp]),
         "gsis_last_eps": (C.c_int, [vp, _dp]),
         "gsis_profile_enable": (C.c_int, [vp, C.c_int32]),
         "gsis_profile_reset": (C.c_int, [vp]),
@@ -221,6 +223,25 @@ def gsis_step(ctx, mode=GSIS_MODE_CIS):
     return eps.value
 
 
+def gsis_solve(ctx, mode=GSIS_MODE_GSIS, max_outer=0, tol=0.0, raise_on_max=False):
+    """Iterate to eps < tol; returns (iterations, eps history).  Reaching max_outer is
+    reported by the history (and raises only with raise_on_max)."""
+    n = max_outer if max_outer > 0 else 100000
+    hist = np.zeros(n)
+    it = C.c_int32(0)
+    rc = load().gsis_solve(ctx, mode, max_outer, tol, C.byref(it), _ptr(hist))
+    if rc != GSIS_OK and not (rc == GSIS_ERR_NOT_CONVERGED and not raise_on_max):
+        _check(rc, ctx)
+    return it.value, hist[:it.value].copy()
+
+
+def gsis_macro_stats(ctx):
+    """(inner iterations, first residual norm, last residual norm) of the last synthetic solve."""
+    it, r0, rn = C.c_int32(0), C.c_double(0.0), C.c_double(0.0)
+    _check(load().gsis_macro_stats(ctx, C.byref(it), C.byref(r0), C.byref(rn)), ctx)
+    return it.value, r0.value, rn.value
+
+
 def gsis_step_async(ctx, mode=GSIS_MODE_CIS):
     _check(load().gsis_step_async(ctx, mode), ctx)
 
@@ -240,7 +261,7 @@ def gsis_profile_reset(ctx):
 
 
 def gsis_profile_read(ctx):
-    n = 16
+    n = 64
     names = (C.c_char_p * n)()
     ms = (C.c_double * n)()
     cnt = (C.c_int64 * n)()
