@@ -44,6 +44,7 @@ class SolverParams:
     tol_outer: float = 1e-6
     tol_inner: float = 1e-7
     sync_relax: float = 1.0              # weight of the equilibrium correction in the synchronisation
+    macro_fp32: int = 0                  # library FP32 path: synthetic residual side in FP32
 
 
 @dataclass

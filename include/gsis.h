@@ -125,6 +125,10 @@ typedef struct {
     double tol_outer, tol_inner;
     double sync_relax;          /* w in f^{k+1} = f^{k+1/2} + w [f_eq(M^{k+1}) - f_eq(M^{k+1/2})],
                                    0 < w <= 1 (Section 3 has w = 1)                          */
+    int32_t macro_fp32;         /* GSIS_FP32 contexts only: 1 evaluates the synthetic
+                                   equations' residual side (gradients, fluxes, high-order
+                                   terms, D) in FP32; the relaxation sweeps and norms stay
+                                   FP64.  0 (default): all FP64.                             */
 } gsis_solver_params;
 
 typedef struct gsis_ctx gsis_ctx;

@@ -56,6 +56,7 @@ struct gsis_ctx {
     // synthetic equations (FP64): geometry, quadratures in FP64, state and work arrays
     MacroGeom mg{};
     bool closed = true;          // walls only: the synthetic solution keeps the mass
+    int mfp32 = 0;               // FP32 path: residual side of the synthetic equations in FP32
     int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
     double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
            *m_fi_xf = nullptr, *m_lsq = nullptr, *m_eps2 = nullptr, *m_xc = nullptr, *m_bf_n = nullptr,
@@ -68,6 +69,8 @@ struct gsis_ctx {
     MacroState *mstate = nullptr;
     MacroState *h_mstate = nullptr;   // pinned: initial state and the polled stop flag
     int last_inner = 0;
+    cudaGraphExec_t macro_exec = nullptr;   // POLL inner iterations, captured once
+    int macro_nodes = 0;
 
     bool have_eps = false;
     double last_eps = 0.0;
@@ -310,9 +313,36 @@ QuadD oquad_d(const gsis_ctx *c) { return QuadD{c->NO, c->Op, c->oqd_x, c->oqd_w
 // Pseudo-time iterations of the synthetic equations from W[0] until ||R|| <= tol_inner
 // ||R_0|| or max_inner; returns the index of the buffer that holds the result.  The
 // device stop flag is polled every POLL iterations (one stream synchronisation each).
+// enqueue one inner iteration reading W[w] and writing W[1 - w]; returns a CUDA status
+cudaError_t enqueue_inner(gsis_ctx *c, int w, int *kernels) {
+    const MacroGeom &g = c->mg;
+    const gsis_solver_params &sp = c->solver;
+    const int nparts = macro_rpart_count((int)c->nc);
+    const int sweeps = std::max(sp.macro_sweeps, 1);
+    cudaError_t e;
+    if ((e = launch_macro_grad(c->stream, g, c->order, c->mfp32, c->model, c->mstate, c->W[w], c->mq, c->mgrad, c->mphi)))
+        return e;
+    if ((e = launch_macro_bflux(c->stream, g, c->mfp32, c->model, vquad_d(c), oquad_d(c), c->mstate, c->mq, c->mbf))) return e;
+    if ((e = launch_macro_residual(c->stream, g, c->order, c->mfp32, c->model, sp.cfl_macro, c->mstate, c->W[w], c->mq,
+                                   c->mgrad, c->mphi, c->hot, c->mbf, c->hot_b, c->Rg, c->Dinv, c->gam, c->rpart)))
+        return e;
+    if ((e = launch_macro_norm(c->stream, nparts, c->rpart, c->mstate, c->mhist))) return e;
+    for (int sw = 0; sw < sweeps; ++sw)
+        if ((e = launch_macro_jacobi(c->stream, g, c->model, c->mstate, sw == 0, sw == sweeps - 1, c->W[w], c->Rg,
+                                     c->Dinv, c->gam, c->dG[sw & 1], c->dG[(sw + 1) & 1], c->W[1 - w])))
+            return e;
+    *kernels += 4 + sweeps - (g.n_bf == 0 ? 1 : 0);
+    return cudaSuccess;
+}
+
+// Pseudo-time iterations of the synthetic equations from W[0] until ||R|| <= tol_inner
+// ||R_0|| or max_inner; returns the index of the buffer that holds the result.  Every
+// kernel returns at once after the device stop flag is set, so the host polls the flag
+// only every POLL iterations (one stream synchronisation each).  Without kernel
+// profiling, and on a non-default stream, the POLL iterations are a CUDA graph captured
+// once per context.
 int macro_solve(gsis_ctx *c, int *w_out) {
     constexpr int POLL = 8;
-    const MacroGeom &g = c->mg;
     const gsis_solver_params &sp = c->solver;
     c->h_mstate->it = 0;
     c->h_mstate->done = 0;
@@ -321,40 +351,71 @@ int macro_solve(gsis_ctx *c, int *w_out) {
     c->h_mstate->rn = 0.0;
     c->h_mstate->tol = sp.tol_inner;
     CUDA_TRY(c, cudaMemcpyAsync(c->mstate, c->h_mstate, sizeof(MacroState), cudaMemcpyHostToDevice, c->stream));
-    const int nparts = macro_rpart_count((int)c->nc);
-    const int sweeps = std::max(sp.macro_sweeps, 1);
-    int w = 0, it = 0;
-    for (; it < sp.max_inner; ++it) {
-        TRY(launch(c, K_MGRAD, [&] {
-            return launch_macro_grad(c->stream, g, c->order, c->model, c->mstate, c->W[w], c->mq, c->mgrad, c->mphi);
-        }));
-        TRY(launch(c, K_MBFLUX, [&] {
-            return launch_macro_bflux(c->stream, g, c->model, vquad_d(c), oquad_d(c), c->mstate, c->mq, c->mbf);
-        }));
-        TRY(launch(c, K_MRES, [&] {
-            return launch_macro_residual(c->stream, g, c->order, c->model, sp.cfl_macro, c->mstate, c->W[w], c->mq,
-                                         c->mgrad, c->mphi, c->hot, c->mbf, c->hot_b, c->Rg, c->Dinv, c->gam,
-                                         c->rpart);
-        }));
-        TRY(launch(c, K_MNORM, [&] { return launch_macro_norm(c->stream, nparts, c->rpart, c->mstate, c->mhist); }));
-        for (int sw = 0; sw < sweeps; ++sw) {
-            TRY(launch(c, K_MJACOBI, [&] {
-                return launch_macro_jacobi(c->stream, g, c->model, c->mstate, sw == 0, sw == sweeps - 1, c->W[w],
-                                           c->Rg, c->Dinv, c->gam, c->dG[sw & 1], c->dG[(sw + 1) & 1], c->W[1 - w]);
-            }));
+    const bool graph = !c->prof && c->stream != nullptr;
+    if (graph && !c->macro_exec) {
+        cudaGraph_t gr = nullptr;
+        int nodes = 0;
+        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < POLL && e == cudaSuccess; ++k) e = enqueue_inner(c, k & 1, &nodes);
+        cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            return fail(c, GSIS_ERR_CUDA, std::string("capture of the synthetic solve: ") +
+                                              cudaGetErrorString(e != cudaSuccess ? e : e2));
         }
-        w = 1 - w;
-        if ((it + 1) % POLL == 0 && it + 1 < sp.max_inner) {
+        e = cudaGraphInstantiate(&c->macro_exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            c->macro_exec = nullptr;
+            return fail(c, GSIS_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+        }
+        c->macro_nodes = nodes;
+    }
+    int w = 0;
+    for (int it = 0; it < sp.max_inner; it += POLL) {
+        if (graph) {
+            CUDA_TRY(c, cudaGraphLaunch(c->macro_exec, c->stream));
+            c->launches += c->macro_nodes;
+        } else {
+            for (int k = 0; k < POLL; ++k) {
+                int nodes = 0;
+                const int wk = k & 1;
+                TRY(launch(c, K_MGRAD, [&] {
+                    return launch_macro_grad(c->stream, c->mg, c->order, c->mfp32, c->model, c->mstate, c->W[wk], c->mq,
+                                             c->mgrad, c->mphi);
+                }));
+                TRY(launch(c, K_MBFLUX, [&] {
+                    return launch_macro_bflux(c->stream, c->mg, c->mfp32, c->model, vquad_d(c), oquad_d(c), c->mstate, c->mq,
+                                              c->mbf);
+                }));
+                TRY(launch(c, K_MRES, [&] {
+                    return launch_macro_residual(c->stream, c->mg, c->order, c->mfp32, c->model, sp.cfl_macro, c->mstate,
+                                                 c->W[wk], c->mq, c->mgrad, c->mphi, c->hot, c->mbf, c->hot_b, c->Rg,
+                                                 c->Dinv, c->gam, c->rpart);
+                }));
+                TRY(launch(c, K_MNORM, [&] {
+                    return launch_macro_norm(c->stream, macro_rpart_count((int)c->nc), c->rpart, c->mstate,
+                                             c->mhist);
+                }));
+                const int sweeps = std::max(sp.macro_sweeps, 1);
+                for (int sw = 0; sw < sweeps; ++sw)
+                    TRY(launch(c, K_MJACOBI, [&] {
+                        return launch_macro_jacobi(c->stream, c->mg, c->model, c->mstate, sw == 0, sw == sweeps - 1,
+                                                   c->W[wk], c->Rg, c->Dinv, c->gam, c->dG[sw & 1],
+                                                   c->dG[(sw + 1) & 1], c->W[1 - wk]);
+                    }));
+                (void)nodes;
+            }
+        }
+        if (it + POLL < sp.max_inner) {
             CUDA_TRY(c, cudaMemcpyAsync(c->h_mstate, c->mstate, sizeof(MacroState), cudaMemcpyDeviceToHost,
                                         c->stream));
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-            if (c->h_mstate->done) {
-                ++it;
-                break;
-            }
+            if (c->h_mstate->done) break;
         }
     }
-    *w_out = w;
+    *w_out = w;   // POLL is even: every chunk ends where it started
     return GSIS_OK;
 }
 
@@ -379,13 +440,13 @@ int gsis_iteration(gsis_ctx *c) {
         return launch_macro_from_fields(c->stream, c->dim, (int)c->nc, c->model, c->fields_h, c->W[0]);
     }));
     TRY(launch(c, K_MGRAD, [&] {
-        return launch_macro_grad(c->stream, g, 1, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
+        return launch_macro_grad(c->stream, g, 1, c->mfp32, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
     }));
     TRY(launch(c, K_MBFLUX, [&] {
-        return launch_macro_bflux(c->stream, g, c->model, vquad_d(c), oquad_d(c), nullptr, c->mq, c->mbf);
+        return launch_macro_bflux(c->stream, g, c->mfp32, c->model, vquad_d(c), oquad_d(c), nullptr, c->mq, c->mbf);
     }));
     TRY(launch(c, K_HOT, [&] {
-        return launch_macro_hot(c->stream, g, c->model, c->fields_h, c->mq, c->mgrad, c->kbf, c->mbf, c->hot,
+        return launch_macro_hot(c->stream, g, c->mfp32, c->model, c->fields_h, c->mq, c->mgrad, c->kbf, c->mbf, c->hot,
                                 c->hot_b);
     }));
     int w = 0;
@@ -518,6 +579,7 @@ void gsis_destroy(gsis_ctx *ctx) {
         cudaEventDestroy(p.e1);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->macro_exec) cudaGraphExecDestroy(ctx->macro_exec);
     for (void *p : ctx->allocations) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_mstate) cudaFreeHost(ctx->h_mstate);
@@ -541,6 +603,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     c->dim = dim;
     c->precision = sp->precision;
     c->real_size = sp->precision == GSIS_FP64 ? 8 : 4;
+    c->mfp32 = sp->precision == GSIS_FP32 && sp->macro_fp32 != 0;
     c->order = sp->order;
     c->block = sp->relax_block;
     c->solver = *sp;

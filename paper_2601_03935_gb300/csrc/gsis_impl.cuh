@@ -134,17 +134,19 @@ cudaError_t launch_macro_from_fields(cudaStream_t s, int dim, int n_cells, const
                                      double *W);
 cudaError_t launch_macro_fields_from_W(cudaStream_t s, int dim, int n_cells, const ModelDev &m, const double *W,
                                        double *F);
-cudaError_t launch_macro_grad(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m,
+// fp32 != 0: the residual side (gradients, limiters, fluxes, high-order terms, D) is
+// evaluated in FP32 with FP64 storage; the relaxation sweeps and norms stay FP64
+cudaError_t launch_macro_grad(cudaStream_t s, const MacroGeom &g, int order, int fp32, const ModelDev &m,
                               const MacroState *st, const double *W, double *q, double *grad, double *phi);
-cudaError_t launch_macro_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const QuadD &vq,
+cudaError_t launch_macro_bflux(cudaStream_t s, const MacroGeom &g, int fp32, const ModelDev &m, const QuadD &vq,
                                const QuadD &oq, const MacroState *st, const double *q, double *bflux);
-cudaError_t launch_macro_hot(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const double *F_kin,
+cudaError_t launch_macro_hot(cudaStream_t s, const MacroGeom &g, int fp32, const ModelDev &m, const double *F_kin,
                              const double *q, const double *grad, const double *kin_bflux, const double *mac_bflux,
                              double *hot, double *hot_b);
-cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m, double cfl_macro,
-                                  const MacroState *st, const double *W, const double *q, const double *grad,
-                                  const double *phi, const double *hot, const double *bflux, const double *hot_b,
-                                  double *Rg, double *Dinv, double *gam, double *rpart);
+cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order, int fp32, const ModelDev &m,
+                                  double cfl_macro, const MacroState *st, const double *W, const double *q,
+                                  const double *grad, const double *phi, const double *hot, const double *bflux,
+                                  const double *hot_b, double *Rg, double *Dinv, double *gam, double *rpart);
 cudaError_t launch_macro_norm(cudaStream_t s, int n_parts, const double *rpart, MacroState *st, double *history);
 cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const MacroState *st,
                                 int first, int last, const double *W, const double *Rg, const double *Dinv,

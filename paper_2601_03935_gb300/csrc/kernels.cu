@@ -39,6 +39,8 @@ __device__ __forceinline__ void vstore(Real *p, const Vec<Real, N> &x) {
 }
 
 __device__ __forceinline__ float fexp(float x) { return __expf(x); }
+__device__ __forceinline__ float expm1_r(float x) { return expm1f(x); }
+__device__ __forceinline__ double expm1_r(double x) { return expm1(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
@@ -661,17 +663,29 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
     const int i = blockIdx.x * (VCH / 32) + warp;
     const int chunk = blockIdx.y;
     if (i >= n_cells) return;
-    Real A[2], Bq[2], u[2][DIM], mul[2][4];
-    for (int s = 0; s < 2; ++s) {
-        const double *r = (s == 0 ? Fn : Fh) + (size_t)i * NF;
-        const double T = r[4];
-        A[s] = (Real)(r[0] * pow(2.0 * 3.14159265358979323846 * T, -0.5 * DIM));
-        Bq[s] = (Real)(0.5 / T);
-        for (int a = 0; a < DIM; ++a) u[s][a] = (Real)r[1 + a];
-        mul[s][0] = Real(1);
-        mul[s][1] = (Real)(MH * T);
-        mul[s][2] = (Real)(0.5 * m.d_r * r[5]);
-        mul[s][3] = (Real)(0.5 * m.d_v * r[6]);
+    // The correction is the difference of two nearly equal Maxwellians near convergence.
+    // It is evaluated as E_h [A_n expm1(-delta) + (A_n - A_h)] with
+    // delta = B_n c_n^2 - B_h c_h^2 formed from per-cell differences taken in FP64, so that
+    // its relative accuracy does not degrade as M^{k+1} -> M^{k+1/2}.
+    const double *rn = Fn + (size_t)i * NF, *rh = Fh + (size_t)i * NF;
+    const double An = rn[0] * pow(2.0 * 3.14159265358979323846 * rn[4], -0.5 * DIM);
+    const double Ah = rh[0] * pow(2.0 * 3.14159265358979323846 * rh[4], -0.5 * DIM);
+    const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
+    const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
+    const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
+    const Real An_r = (Real)An, dA = (Real)(An - Ah), Ah_r = (Real)Ah, Bn_r = (Real)Bn, Bh_r = (Real)Bh,
+               dB = (Real)(Bn - Bh);
+    Real uh[DIM], du[DIM], su[DIM], mul_n[4], dmul[4];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        uh[a] = (Real)rh[1 + a];
+        du[a] = (Real)(rh[1 + a] - rn[1 + a]);
+        su[a] = (Real)(rh[1 + a] + rn[1 + a]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        mul_n[p] = (Real)mn[p];
+        dmul[p] = (Real)(mn[p] - mh[p]);
     }
     const Real w = (Real)om;
     constexpr int NM = n_gas_moments<DIM>();
@@ -687,16 +701,19 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
 #pragma unroll
         for (int a = 0; a < DIM; ++a) xi[a] = vq.x[a * vq.n_pad + v];
         if (v < vq.n) {
-            Real E[2];
+            Real c2h = Real(0), dc2 = Real(0);
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                Real c2 = Real(0);
-#pragma unroll
-                for (int a = 0; a < DIM; ++a) c2 += (xi[a] - u[s][a]) * (xi[a] - u[s][a]);
-                E[s] = A[s] * fexp(-Bq[s] * c2);
+            for (int a = 0; a < DIM; ++a) {
+                const Real ch = xi[a] - uh[a];
+                c2h += ch * ch;
+                dc2 += du[a] * (Real(2) * xi[a] - su[a]);    // c_n^2 - c_h^2
             }
+            const Real Eh = fexp(-Bh_r * c2h);
+            const Real delta = Bn_r * dc2 + dB * c2h;
+            const Real d0 = Eh * (An_r * expm1_r(-delta) + dA);  // F0_n - F0_h
+            const Real e0h = Ah_r * Eh;                           // F0_h
 #pragma unroll
-            for (int p = 0; p < 4; ++p) fv4.v[p] += w * (mul[0][p] * E[0] - mul[1][p] * E[1]);
+            for (int p = 0; p < 4; ++p) fv4.v[p] += w * (mul_n[p] * d0 + dmul[p] * e0h);
             vstore<Real, 4>(fp, fv4);
         }
         Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};

@@ -33,17 +33,24 @@ namespace {
 
 constexpr double PI = 3.14159265358979323846;
 
-__device__ __forceinline__ double viscosity(double T_t, const ModelDev &m) {
-    return sqrt(2.0 / PI) * m.Kn * pow(T_t, m.omega);          // mu = p_t tau
+// Helpers are templates on the compute type R (double for the plain FP64 path, float for
+// the FP32 path's residual evaluation); literals are written R(x) so that a float
+// instantiation issues no FP64 instruction.
+template <typename R>
+__device__ __forceinline__ R viscosity(R T_t, const ModelDev &m) {
+    return R(sqrt(2.0 / PI)) * R(m.Kn) * pow(T_t, R(m.omega));          // mu = p_t tau
 }
-__device__ __forceinline__ double sound_speed(double T_t) { return sqrt(5.0 * T_t / 3.0); }
-__device__ __forceinline__ double absorption(double rho, const ModelDev &m) {
-    const double k = 1.0 / m.Kn_p;
+template <typename R>
+__device__ __forceinline__ R sound_speed(R T_t) { return sqrt(R(5) * T_t / R(3)); }
+template <typename R>
+__device__ __forceinline__ R absorption(R rho, const ModelDev &m) {
+    const R k = R(1) / R(m.Kn_p);
     return m.k_eff_density_scaled ? k * rho : k;
 }
 
 // base = A^-1 diag(5, d_r, d_v); kappa_gas = mu/2 base (Eq. NSF_thermal_conductivities)
-__device__ void kappa_base(const ModelDev &m, double (&B)[3][3]) {
+template <typename R>
+__device__ void kappa_base(const ModelDev &m, R (&B)[3][3]) {
     const double *A = m.A;
     const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
                        A[2] * (A[3] * A[7] - A[4] * A[6]);
@@ -59,128 +66,131 @@ __device__ void kappa_base(const ModelDev &m, double (&B)[3][3]) {
     Ai[2][2] = (A[0] * A[4] - A[1] * A[3]) / det;
     const double dg[3] = {5.0, m.d_r, m.d_v};
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) B[a][b] = Ai[a][b] * dg[b];
+        for (int b = 0; b < 3; ++b) B[a][b] = R(Ai[a][b] * dg[b]);
 }
 
-template <int DIM>
-__device__ __forceinline__ void primitive(const double *W, const ModelDev &m, double *q) {
+template <typename R, int DIM, typename S>
+__device__ __forceinline__ void primitive(const S *W, const ModelDev &m, R *q) {
     constexpr int E = 1 + DIM;
-    const double rho = W[0];
-    double ke = 0.0;
+    const R rho = R(W[0]);
+    R ke = R(0);
     q[0] = rho;
     for (int a = 0; a < DIM; ++a) {
-        q[1 + a] = W[1 + a] / rho;
+        q[1 + a] = R(W[1 + a]) / rho;
         ke += q[1 + a] * q[1 + a];
     }
-    const double e = W[E], er = W[E + 1], ev = W[E + 2], eR = W[E + 3];
-    q[E] = (e - eR - er - ev - 0.5 * rho * ke) / (1.5 * rho);
-    q[E + 1] = 2.0 * er / (m.d_r * rho);
-    q[E + 2] = 2.0 * ev / (m.d_v * rho);
+    const R e = R(W[E]), er = R(W[E + 1]), ev = R(W[E + 2]), eR = R(W[E + 3]);
+    q[E] = (e - eR - er - ev - R(0.5) * rho * ke) / (R(1.5) * rho);
+    q[E + 1] = R(2) * er / (R(m.d_r) * rho);
+    q[E + 2] = R(2) * ev / (R(m.d_v) * rho);
     q[E + 3] = eR;
 }
 
-template <int DIM>
-__device__ __forceinline__ void prim_to_W(const double *q, const ModelDev &m, double *W) {
+template <typename R, int DIM>
+__device__ __forceinline__ void prim_to_W(const R *q, const ModelDev &m, R *W) {
     constexpr int E = 1 + DIM;
-    const double rho = q[0];
-    double uu = 0.0;
+    const R rho = q[0];
+    R uu = R(0);
     for (int a = 0; a < DIM; ++a) uu += q[1 + a] * q[1 + a];
-    const double er = 0.5 * m.d_r * rho * q[E + 1], ev = 0.5 * m.d_v * rho * q[E + 2];
+    const R er = R(0.5) * R(m.d_r) * rho * q[E + 1], ev = R(0.5) * R(m.d_v) * rho * q[E + 2];
     W[0] = rho;
     for (int a = 0; a < DIM; ++a) W[1 + a] = rho * q[1 + a];
-    W[E] = 1.5 * rho * q[E] + 0.5 * rho * uu + er + ev + q[E + 3];
+    W[E] = R(1.5) * rho * q[E] + R(0.5) * rho * uu + er + ev + q[E + 3];
     W[E + 1] = er;
     W[E + 2] = ev;
     W[E + 3] = q[E + 3];
 }
 
 // F_c . n of Eq. (macroscopic_equation); e_R has no convective flux
-template <int DIM>
-__device__ __forceinline__ void convective_flux(const double *q, const double *n, const ModelDev &m, double *F) {
+template <typename R, int DIM>
+__device__ __forceinline__ void convective_flux(const R *q, const R *n, const ModelDev &m, R *F) {
     constexpr int E = 1 + DIM;
-    const double rho = q[0], T_t = q[E];
-    double un = 0.0, uu = 0.0;
+    const R rho = q[0], T_t = q[E];
+    R un = R(0), uu = R(0);
     for (int a = 0; a < DIM; ++a) {
         un += q[1 + a] * n[a];
         uu += q[1 + a] * q[1 + a];
     }
-    const double p = rho * T_t;
-    const double er = 0.5 * m.d_r * rho * q[E + 1], ev = 0.5 * m.d_v * rho * q[E + 2];
-    const double eg = 1.5 * rho * T_t + 0.5 * rho * uu + er + ev;
+    const R p = rho * T_t;
+    const R er = R(0.5) * R(m.d_r) * rho * q[E + 1], ev = R(0.5) * R(m.d_v) * rho * q[E + 2];
+    const R eg = R(1.5) * rho * T_t + R(0.5) * rho * uu + er + ev;
     F[0] = rho * un;
     for (int a = 0; a < DIM; ++a) F[1 + a] = rho * q[1 + a] * un + p * n[a];
     F[E] = un * (eg + p);
     F[E + 1] = un * er;
     F[E + 2] = un * ev;
-    F[E + 3] = 0.0;
+    F[E + 3] = R(0);
 }
 
 // Rusanov flux: average of the two fluxes minus half the largest |u_n| + c_s times the
 // jump of the convected variables (gas energy, not e_R)
-template <int DIM>
-__device__ void rusanov(const double *qL, const double *qR, const double *n, const ModelDev &m, double *F) {
+template <typename R, int DIM>
+__device__ void rusanov(const R *qL, const R *qR, const R *n, const ModelDev &m, R *F) {
     constexpr int NV = DIM + 5, E = 1 + DIM;
-    double FL[NV], FR[NV], WL[NV], WR[NV];
-    convective_flux<DIM>(qL, n, m, FL);
-    convective_flux<DIM>(qR, n, m, FR);
-    double unL = 0.0, unR = 0.0;
+    R FL[NV], FR[NV], WL[NV], WR[NV];
+    convective_flux<R, DIM>(qL, n, m, FL);
+    convective_flux<R, DIM>(qR, n, m, FR);
+    R unL = R(0), unR = R(0);
     for (int a = 0; a < DIM; ++a) {
         unL += qL[1 + a] * n[a];
         unR += qR[1 + a] * n[a];
     }
-    const double lam = fmax(fabs(unL) + sound_speed(qL[E]), fabs(unR) + sound_speed(qR[E]));
-    prim_to_W<DIM>(qL, m, WL);
-    prim_to_W<DIM>(qR, m, WR);
+    const R lam = fmax(fabs(unL) + sound_speed(qL[E]), fabs(unR) + sound_speed(qR[E]));
+    prim_to_W<R, DIM>(qL, m, WL);
+    prim_to_W<R, DIM>(qR, m, WR);
     for (int k = 0; k < NV; ++k) {
-        double dW = WR[k] - WL[k];
+        R dW = WR[k] - WL[k];
         if (k == E) dW -= WR[E + 3] - WL[E + 3];
-        if (k == E + 3) dW = 0.0;
-        F[k] = 0.5 * (FL[k] + FR[k]) - 0.5 * lam * dW;
+        if (k == E + 3) dW = R(0);
+        F[k] = R(0.5) * (FL[k] + FR[k]) - R(0.5) * lam * dW;
     }
 }
 
 // Venkatakrishnan's limiter function
-__device__ __forceinline__ double venkat(double d1, double d2, double eps2) {
-    return (d1 * d1 + eps2 + 2.0 * d1 * d2) / (d1 * d1 + 2.0 * d2 * d2 + d1 * d2 + eps2);
+template <typename R>
+__device__ __forceinline__ R venkat(R d1, R d2, R eps2) {
+    return (d1 * d1 + eps2 + R(2) * d1 * d2) / (d1 * d1 + R(2) * d2 * d2 + d1 * d2 + eps2);
 }
 
 // Q of Section 5: rotational and vibrational relaxation, gas-photon exchange
-template <int DIM>
-__device__ void source(const double *q, const ModelDev &m, double *Q) {
+template <typename R, int DIM>
+__device__ void source(const R *q, const ModelDev &m, R *Q) {
     constexpr int NV = DIM + 5, E = 1 + DIM;
-    const double rho = q[0], Tt = q[E], Tr = q[E + 1], Tv = q[E + 2], eR = q[E + 3];
-    const double Ttr = (3.0 * Tt + m.d_r * Tr) / (3.0 + m.d_r);
-    const double Ttv = (3.0 * Tt + m.d_v * Tv) / (3.0 + m.d_v);
-    const double tau = sqrt(2.0 / PI) * pow(Tt, m.omega - 1.0) * m.Kn / rho;
-    const double k = absorption(rho, m);
-    const double evR = 4.0 * m.sigma_R * Tv * Tv * Tv * Tv;
-    for (int a = 0; a < NV; ++a) Q[a] = 0.0;
-    Q[E + 1] = 0.5 * m.d_r * rho * (Ttr - Tr) / (m.Z_r * tau);
-    Q[E + 2] = 0.5 * m.d_v * rho * (Ttv - Tv) / (m.Z_v * tau) - k * (evR - eR);
+    const R rho = q[0], Tt = q[E], Tr = q[E + 1], Tv = q[E + 2], eR = q[E + 3];
+    const R dr = R(m.d_r), dv = R(m.d_v);
+    const R Ttr = (R(3) * Tt + dr * Tr) / (R(3) + dr);
+    const R Ttv = (R(3) * Tt + dv * Tv) / (R(3) + dv);
+    const R tau = R(sqrt(2.0 / PI)) * pow(Tt, R(m.omega - 1.0)) * R(m.Kn) / rho;
+    const R k = absorption(rho, m);
+    const R evR = R(4) * R(m.sigma_R) * Tv * Tv * Tv * Tv;
+    for (int a = 0; a < NV; ++a) Q[a] = R(0);
+    Q[E + 1] = R(0.5) * dr * rho * (Ttr - Tr) / (R(m.Z_r) * tau);
+    Q[E + 2] = R(0.5) * dv * rho * (Ttv - Tv) / (R(m.Z_v) * tau) - k * (evR - eR);
     Q[E + 3] = k * (evR - eR);
 }
 
 // exact d(Q_egas, Q_r, Q_v, Q_R)/d(e_gas, e_r, e_v, e_R) with rho, rho u, tau, k_eff frozen
-template <int DIM>
-__device__ void source_jacobian(const double *q, const ModelDev &m, double (&J)[4][4]) {
+template <typename R, int DIM>
+__device__ void source_jacobian(const R *q, const ModelDev &m, R (&J)[4][4]) {
     constexpr int E = 1 + DIM;
-    const double rho = q[0], Tt = q[E], Tv = q[E + 2];
-    const double tau = sqrt(2.0 / PI) * pow(Tt, m.omega - 1.0) * m.Kn / rho;
-    const double k = absorption(rho, m);
-    const double cr = rho * 1.5 * m.d_r / (3.0 + m.d_r) / (m.Z_r * tau);
-    const double cv = rho * 1.5 * m.d_v / (3.0 + m.d_v) / (m.Z_v * tau);
-    const double beta = 16.0 * m.sigma_R * Tv * Tv * Tv * 2.0 / (m.d_v * rho);
-    const double a = 1.0 / (1.5 * rho);
+    const R rho = q[0], Tt = q[E], Tv = q[E + 2];
+    const R dr = R(m.d_r), dv = R(m.d_v);
+    const R tau = R(sqrt(2.0 / PI)) * pow(Tt, R(m.omega - 1.0)) * R(m.Kn) / rho;
+    const R k = absorption(rho, m);
+    const R cr = rho * R(1.5) * dr / (R(3) + dr) / (R(m.Z_r) * tau);
+    const R cv = rho * R(1.5) * dv / (R(3) + dv) / (R(m.Z_v) * tau);
+    const R beta = R(16) * R(m.sigma_R) * Tv * Tv * Tv * R(2) / (dv * rho);
+    const R a = R(1) / (R(1.5) * rho);
     for (int r = 0; r < 4; ++r)
-        for (int c = 0; c < 4; ++c) J[r][c] = 0.0;
+        for (int c = 0; c < 4; ++c) J[r][c] = R(0);
     J[0][2] = -k * beta;
     J[0][3] = k;
     J[1][0] = cr * a;
-    J[1][1] = -cr * (a + 2.0 / (m.d_r * rho));
+    J[1][1] = -cr * (a + R(2) / (dr * rho));
     J[1][2] = -cr * a;
     J[2][0] = cv * a;
     J[2][1] = -cv * a;
-    J[2][2] = -cv * (a + 2.0 / (m.d_v * rho)) - k * beta;
+    J[2][2] = -cv * (a + R(2) / (dv * rho)) - k * beta;
     J[2][3] = k;
     J[3][2] = k * beta;
     J[3][3] = -k;
@@ -188,7 +198,7 @@ __device__ void source_jacobian(const double *q, const ModelDev &m, double (&J)[
 
 }  // namespace
 
-// ------------------------------------------------------------------ conversions
+// ------------------------------------------------------------------ conversions (FP64)
 template <int DIM>
 __global__ void k_macro_from_fields(int n_cells, ModelDev m, const double *__restrict__ F, double *__restrict__ W) {
     constexpr int NV = DIM + 5, E = 1 + DIM;
@@ -203,7 +213,7 @@ __global__ void k_macro_from_fields(int n_cells, ModelDev m, const double *__res
     q[E + 2] = r[6];
     const double TR = r[7];
     q[E + 3] = 4.0 * m.sigma_R * TR * TR * TR * TR;
-    prim_to_W<DIM>(q, m, W + (size_t)i * NVM);
+    prim_to_W<double, DIM>(q, m, W + (size_t)i * NVM);
 }
 
 template <int DIM>
@@ -212,7 +222,7 @@ __global__ void k_macro_fields_from_W(int n_cells, ModelDev m, const double *__r
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_cells) return;
     double q[NV];
-    primitive<DIM>(W + (size_t)i * NVM, m, q);
+    primitive<double, DIM>(W + (size_t)i * NVM, m, q);
     double *r = F + (size_t)i * NF;
     for (int k = 0; k < NF; ++k) r[k] = 0.0;
     r[0] = q[0];
@@ -224,30 +234,30 @@ __global__ void k_macro_fields_from_W(int n_cells, ModelDev m, const double *__r
 }
 
 // ------------------------------------------------------------------ gradients and limiters
-// q [nc][NVM], grad [nc][2][NVM], phi [nc][NVM]
-template <int DIM, int ORDER>
+// q [nc][NVM], grad [nc][2][NVM], phi [nc][NVM] (stored in FP64, computed in R)
+template <typename R, int DIM, int ORDER>
 __global__ void k_macro_grad(MacroGeom g, ModelDev m, const MacroState *__restrict__ st, const double *__restrict__ W,
                              double *__restrict__ qo, double *__restrict__ grad, double *__restrict__ phi) {
     constexpr int NQ = DIM + 5;
     if (st && st->done) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_cells) return;
-    double qi[NQ], gr[DIM][NQ], dmax[NQ], dmin[NQ];
-    primitive<DIM>(W + (size_t)i * NVM, m, qi);
+    R qi[NQ], gr[DIM][NQ], dmax[NQ], dmin[NQ];
+    primitive<R, DIM>(W + (size_t)i * NVM, m, qi);
     for (int k = 0; k < NQ; ++k) {
-        dmax[k] = 0.0;
-        dmin[k] = 0.0;
-        for (int a = 0; a < DIM; ++a) gr[a][k] = 0.0;
+        dmax[k] = R(0);
+        dmin[k] = R(0);
+        for (int a = 0; a < DIM; ++a) gr[a][k] = R(0);
     }
     const int4 info = g.info[i];
     for (int k = 0; k < info.y; ++k) {
         const int s = g.stn[i * MAXS + k];
-        double qs[NQ];
-        primitive<DIM>(W + (size_t)s * NVM, m, qs);
+        R qs[NQ];
+        primitive<R, DIM>(W + (size_t)s * NVM, m, qs);
         const double *C = g.lsq + ((size_t)i * MAXS + k) * 2;
         for (int v = 0; v < NQ; ++v) {
-            const double dq = qs[v] - qi[v];
-            for (int a = 0; a < DIM; ++a) gr[a][v] += C[a] * dq;
+            const R dq = qs[v] - qi[v];
+            for (int a = 0; a < DIM; ++a) gr[a][v] += R(C[a]) * dq;
             if (k < info.z) {
                 dmax[v] = fmax(dmax[v], dq);
                 dmin[v] = fmin(dmin[v], dq);
@@ -259,19 +269,19 @@ __global__ void k_macro_grad(MacroGeom g, ModelDev m, const MacroState *__restri
         for (int a = 0; a < DIM; ++a) grad[((size_t)i * 2 + a) * NVM + v] = gr[a][v];
     }
     if constexpr (ORDER != 2) return;
-    double ph[NQ];
-    for (int v = 0; v < NQ; ++v) ph[v] = 1.0;
-    const double eps2 = g.eps2[i];
+    R ph[NQ];
+    for (int v = 0; v < NQ; ++v) ph[v] = R(1);
+    const R eps2 = R(g.eps2[i]);
     for (int k = 0; k < info.x; ++k) {
         const int fid = g.cface[i * MAXF + k];
         if (fid < 0) continue;
-        double d[DIM];
-        for (int a = 0; a < DIM; ++a) d[a] = g.fi_xf[fid * 2 + a] - g.xc[i * 2 + a];
+        R d[DIM];
+        for (int a = 0; a < DIM; ++a) d[a] = R(g.fi_xf[fid * 2 + a] - g.xc[i * 2 + a]);
         for (int v = 0; v < NQ; ++v) {
-            double d2 = 0.0;
+            R d2 = R(0);
             for (int a = 0; a < DIM; ++a) d2 += gr[a][v] * d[a];
-            const double d1 = d2 > 0.0 ? dmax[v] : dmin[v];
-            const double pf = d2 != 0.0 ? venkat(d1, d2, eps2) : 1.0;
+            const R d1 = d2 > R(0) ? dmax[v] : dmin[v];
+            const R pf = d2 != R(0) ? venkat(d1, d2, eps2) : R(1);
             ph[v] = fmin(ph[v], pf);
         }
     }
@@ -285,90 +295,96 @@ namespace {
 // at an interior face from the face-average state pf and the face gradient fg[a][v]
 // (gradient component a of primitive variable v); out layout as the high-order terms:
 // sigma (DIM x DIM), q_t, q_r, q_v, q_R (DIM each).
-template <int DIM>
-__device__ void nsf_face(const double *pf, const double (&fg)[DIM][DIM + 5], const ModelDev &m,
-                         const double (&base)[3][3], double *out) {
+template <typename R, int DIM>
+__device__ void nsf_face(const R *pf, const R (&fg)[DIM][DIM + 5], const ModelDev &m, const R (&base)[3][3], R *out) {
     constexpr int E = 1 + DIM;
-    const double mu = viscosity(pf[E], m);
-    double div = 0.0;
+    const R mu = viscosity(pf[E], m);
+    R div = R(0);
     for (int d = 0; d < DIM; ++d) div += fg[d][1 + d];
     for (int a = 0; a < DIM; ++a)
         for (int b = 0; b < DIM; ++b) {
-            const double S = fg[a][1 + b] + fg[b][1 + a];
-            out[a * DIM + b] = -mu * (S - (a == b ? 2.0 / 3.0 * div : 0.0));
+            const R S = fg[a][1 + b] + fg[b][1 + a];
+            out[a * DIM + b] = -mu * (S - (a == b ? R(2) / R(3) * div : R(0)));
         }
     for (int md = 0; md < 3; ++md)
         for (int d = 0; d < DIM; ++d) {
-            double s = 0.0;
-            for (int nn = 0; nn < 3; ++nn) s += 0.5 * mu * base[md][nn] * fg[d][E + nn];
+            R s = R(0);
+            for (int nn = 0; nn < 3; ++nn) s += R(0.5) * mu * base[md][nn] * fg[d][E + nn];
             out[DIM * DIM + md * DIM + d] = -s;
         }
-    const double kR = 1.0 / (3.0 * absorption(pf[0], m));
+    const R kR = R(1) / (R(3) * absorption(pf[0], m));
     for (int d = 0; d < DIM; ++d) out[DIM * DIM + 3 * DIM + d] = -kR * fg[d][E + 3];
 }
 
 // face-average state and face gradient (average of the cells' least-squares gradients
 // with the component along x_j - x_i replaced by the difference quotient)
-template <int DIM>
-__device__ void face_state(const MacroGeom &g, int fid, const double *q, const double *grad, double *pf,
-                           double (&fg)[DIM][DIM + 5]) {
+template <typename R, int DIM>
+__device__ void face_state(const MacroGeom &g, int fid, const double *q, const double *grad, R *pf,
+                           R (&fg)[DIM][DIM + 5]) {
     constexpr int NQ = DIM + 5;
     const int i = g.fi_i[fid], j = g.fi_j[fid];
     const double *qi = q + (size_t)i * NVM, *qj = q + (size_t)j * NVM;
     const double *t = g.fi_t + (size_t)fid * 2;
-    const double dist = g.fi_dist[fid];
+    const R dist = R(g.fi_dist[fid]);
     for (int v = 0; v < NQ; ++v) {
-        pf[v] = 0.5 * (qi[v] + qj[v]);
-        double along = 0.0;
-        double avg[DIM];
+        const R qiv = R(qi[v]), qjv = R(qj[v]);
+        pf[v] = R(0.5) * (qiv + qjv);
+        R along = R(0);
+        R avg[DIM];
         for (int a = 0; a < DIM; ++a) {
-            avg[a] = 0.5 * (grad[((size_t)i * 2 + a) * NVM + v] + grad[((size_t)j * 2 + a) * NVM + v]);
-            along += t[a] * avg[a];
+            avg[a] = R(0.5) * (R(grad[((size_t)i * 2 + a) * NVM + v]) + R(grad[((size_t)j * 2 + a) * NVM + v]));
+            along += R(t[a]) * avg[a];
         }
-        const double jump = (qj[v] - qi[v]) / dist;
-        for (int a = 0; a < DIM; ++a) fg[a][v] = avg[a] + t[a] * (jump - along);
+        const R jump = (qjv - qiv) / dist;
+        for (int a = 0; a < DIM; ++a) fg[a][v] = avg[a] + R(t[a]) * (jump - along);
     }
 }
 
 // (F_c + F_v) . n of interior face fid (owner -> neighbour orientation)
-template <int DIM, int ORDER>
-__device__ void interior_flux(const MacroGeom &g, const ModelDev &m, const double (&base)[3][3], int fid,
-                              const double *q, const double *grad, const double *phi, const double *hot, double *F) {
+template <typename R, int DIM, int ORDER>
+__device__ void interior_flux(const MacroGeom &g, const ModelDev &m, const R (&base)[3][3], int fid, const double *q,
+                              const double *grad, const double *phi, const double *hot, R *F) {
     constexpr int NV = DIM + 5, E = 1 + DIM;
     const int i = g.fi_i[fid], j = g.fi_j[fid];
-    const double *n = g.fi_n + (size_t)fid * 2;
-    double qL[NV], qR[NV];
+    R n[DIM];
+    for (int a = 0; a < DIM; ++a) n[a] = R(g.fi_n[(size_t)fid * 2 + a]);
+    R qL[NV], qR[NV];
     for (int v = 0; v < NV; ++v) {
-        qL[v] = q[(size_t)i * NVM + v];
-        qR[v] = q[(size_t)j * NVM + v];
+        qL[v] = R(q[(size_t)i * NVM + v]);
+        qR[v] = R(q[(size_t)j * NVM + v]);
     }
     if (ORDER == 2) {
         const double *xf = g.fi_xf + (size_t)fid * 2;
+        R di[DIM], dj[DIM];
+        for (int a = 0; a < DIM; ++a) {
+            di[a] = R(xf[a] - g.xc[i * 2 + a]);
+            dj[a] = R(xf[a] - g.xc[j * 2 + a]);
+        }
         for (int v = 0; v < NV; ++v) {
-            double dL = 0.0, dR = 0.0;
+            R dL = R(0), dR = R(0);
             for (int a = 0; a < DIM; ++a) {
-                dL += grad[((size_t)i * 2 + a) * NVM + v] * (xf[a] - g.xc[i * 2 + a]);
-                dR += grad[((size_t)j * 2 + a) * NVM + v] * (xf[a] - g.xc[j * 2 + a]);
+                dL += R(grad[((size_t)i * 2 + a) * NVM + v]) * di[a];
+                dR += R(grad[((size_t)j * 2 + a) * NVM + v]) * dj[a];
             }
-            qL[v] += phi[(size_t)i * NVM + v] * dL;
-            qR[v] += phi[(size_t)j * NVM + v] * dR;
+            qL[v] += R(phi[(size_t)i * NVM + v]) * dL;
+            qR[v] += R(phi[(size_t)j * NVM + v]) * dR;
         }
     }
-    rusanov<DIM>(qL, qR, n, m, F);
-    double pf[NV], fg[DIM][DIM + 5], s[NHOT];
-    face_state<DIM>(g, fid, q, grad, pf, fg);
-    nsf_face<DIM>(pf, fg, m, base, s);
+    rusanov<R, DIM>(qL, qR, n, m, F);
+    R pf[NV], fg[DIM][DIM + 5], s[NHOT];
+    face_state<R, DIM>(g, fid, q, grad, pf, fg);
+    nsf_face<R, DIM>(pf, fg, m, base, s);
     const double *h = hot + (size_t)fid * NHOT;
-    for (int k = 0; k < DIM * DIM + 4 * DIM; ++k) s[k] += h[k];
-    double sn[DIM], un = 0.0, qn[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < DIM * DIM + 4 * DIM; ++k) s[k] += R(h[k]);
+    R sn[DIM], un = R(0), qn[4] = {R(0), R(0), R(0), R(0)};
     for (int a = 0; a < DIM; ++a) {
-        sn[a] = 0.0;
+        sn[a] = R(0);
         for (int b = 0; b < DIM; ++b) sn[a] += s[a * DIM + b] * n[b];
         un += sn[a] * pf[1 + a];
     }
-    double qtot = 0.0;
+    R qtot = R(0);
     for (int d = 0; d < DIM; ++d) {
-        const double *qq = s + DIM * DIM;
+        const R *qq = s + DIM * DIM;
         qtot += (qq[d] + qq[DIM + d] + qq[2 * DIM + d] + qq[3 * DIM + d]) * n[d];
         for (int md = 0; md < 4; ++md) qn[md] += qq[md * DIM + d] * n[d];
     }
@@ -381,41 +397,41 @@ __device__ void interior_flux(const MacroGeom &g, const ModelDev &m, const doubl
 
 // Far-field boundary flux: Rusanov against the free stream plus NSF terms over the
 // distance from the cell centre to the face
-template <int DIM>
-__device__ void farfield_flux(const MacroGeom &g, const ModelDev &m, const double (&base)[3][3], int b,
-                              const double *qc, double *F) {
+template <typename R, int DIM>
+__device__ void farfield_flux(const MacroGeom &g, const ModelDev &m, const R (&base)[3][3], int b, const R *qc, R *F) {
     constexpr int E = 1 + DIM;
     const double *P = g.patch_state + (size_t)g.bf_patch[b] * 8;
-    const double *n = g.bf_n + (size_t)b * 2;
-    const double dn = g.bf_dn[b];
-    double qf[DIM + 5];
-    qf[0] = P[0];
-    for (int a = 0; a < DIM; ++a) qf[1 + a] = P[1 + a];
-    qf[E] = P[4];
-    qf[E + 1] = P[5];
-    qf[E + 2] = P[6];
-    qf[E + 3] = 4.0 * m.sigma_R * P[7] * P[7] * P[7] * P[7];
-    rusanov<DIM>(qc, qf, n, m, F);
-    const double mu = viscosity(0.5 * (qc[E] + P[4]), m);
-    double du[DIM], dun = 0.0;
+    R n[DIM];
+    for (int a = 0; a < DIM; ++a) n[a] = R(g.bf_n[(size_t)b * 2 + a]);
+    const R dn = R(g.bf_dn[b]);
+    R qf[DIM + 5];
+    qf[0] = R(P[0]);
+    for (int a = 0; a < DIM; ++a) qf[1 + a] = R(P[1 + a]);
+    qf[E] = R(P[4]);
+    qf[E + 1] = R(P[5]);
+    qf[E + 2] = R(P[6]);
+    qf[E + 3] = R(4.0 * m.sigma_R * P[7] * P[7] * P[7] * P[7]);
+    rusanov<R, DIM>(qc, qf, n, m, F);
+    const R mu = viscosity(R(0.5) * (qc[E] + qf[E]), m);
+    R du[DIM], dun = R(0);
     for (int a = 0; a < DIM; ++a) {
-        du[a] = P[1 + a] - qc[1 + a];
+        du[a] = qf[1 + a] - qc[1 + a];
         dun += n[a] * du[a];
     }
-    double sn[DIM], snu = 0.0;
+    R sn[DIM], snu = R(0);
     for (int a = 0; a < DIM; ++a) {
-        sn[a] = -mu / dn * (du[a] + (dun / 3.0) * n[a]);
-        snu += sn[a] * 0.5 * (P[1 + a] + qc[1 + a]);
+        sn[a] = -mu / dn * (du[a] + (dun / R(3)) * n[a]);
+        snu += sn[a] * R(0.5) * (qf[1 + a] + qc[1 + a]);
     }
-    const double dT[3] = {P[4] - qc[E], P[5] - qc[E + 1], P[6] - qc[E + 2]};
-    double qm[3];
+    const R dT[3] = {qf[E] - qc[E], qf[E + 1] - qc[E + 1], qf[E + 2] - qc[E + 2]};
+    R qm[3];
     for (int md = 0; md < 3; ++md) {
-        double s = 0.0;
-        for (int nn = 0; nn < 3; ++nn) s += 0.5 * mu * base[md][nn] * dT[nn];
+        R s = R(0);
+        for (int nn = 0; nn < 3; ++nn) s += R(0.5) * mu * base[md][nn] * dT[nn];
         qm[md] = -s / dn;
     }
-    const double keff = absorption(qc[0], m);
-    const double qR = -(qf[E + 3] - qc[E + 3]) / (3.0 * keff * dn);
+    const R keff = absorption(qc[0], m);
+    const R qR = -(qf[E + 3] - qc[E + 3]) / (R(3) * keff * dn);
     for (int a = 0; a < DIM; ++a) F[1 + a] += sn[a];
     F[E] += snu + (qm[0] + qm[1] + qm[2]) + qR;
     F[E + 1] += qm[1];
@@ -423,19 +439,19 @@ __device__ void farfield_flux(const MacroGeom &g, const ModelDev &m, const doubl
     F[E + 3] += qR;
 }
 
-// block-wide sum of n values per thread into shared memory red[n]; all threads get it
-template <int NT>
-__device__ void block_sum(double *vals, int n, double *red) {
-    __shared__ double buf[NT / 32][16];
+// block-wide sum of n values per thread; red[k] holds the sums for every thread after return
+template <int NT, typename R>
+__device__ void block_sum(R *vals, int n, R *red) {
+    __shared__ R buf[NT / 32][16];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int k = 0; k < n; ++k) {
-        double x = vals[k];
+        R x = vals[k];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
         if (lane == 0) buf[w][k] = x;
     }
     __syncthreads();
     if (threadIdx.x < n) {
-        double x = 0.0;
+        R x = R(0);
         for (int ww = 0; ww < NT / 32; ++ww) x += buf[ww][threadIdx.x];
         red[threadIdx.x] = x;
     }
@@ -449,7 +465,7 @@ __device__ void block_sum(double *vals, int n, double *red) {
 // incoming ones the diffuse wall Maxwellian with the density that zeroes the mass flux;
 // photons leave isotropically (e_R / 4 pi) and enter black-body (sigma_R T_w^4 / pi).
 // The incoming sums are linear in the wall density and are taken for unit density.
-template <int DIM>
+template <typename R, int DIM>
 __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, QuadD vq, QuadD oq,
                                                      const MacroState *__restrict__ st, const double *__restrict__ q,
                                                      double *__restrict__ bflux) {
@@ -458,70 +474,76 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
     if (st && st->done) return;
     const int b = blockIdx.x;
     const int c = g.bf_cell[b];
-    const double *qc = q + (size_t)c * NVM;
+    R qc[NV];
+    for (int k = 0; k < NV; ++k) qc[k] = R(q[(size_t)c * NVM + k]);
     double *out = bflux + (size_t)b * NVM;
     const int pk = g.patch_kind[g.bf_patch[b]];
-    __shared__ double red[2 * NS + 2];
+    __shared__ R red[2 * NS + 2];
     if (pk != 0) {   // far field
         if (threadIdx.x == 0) {
-            double base[3][3], F[NV];
-            kappa_base(m, base);
-            farfield_flux<DIM>(g, m, base, b, qc, F);
+            R base[3][3], F[NV];
+            kappa_base<R>(m, base);
+            farfield_flux<R, DIM>(g, m, base, b, qc, F);
             for (int k = 0; k < NV; ++k) out[k] = F[k];
         }
         return;
     }
     const double *P = g.patch_state + (size_t)g.bf_patch[b] * 8;
-    const double *n = g.bf_n + (size_t)b * 2;
-    const double rho = qc[0], Tt = qc[E], Tr = qc[E + 1], Tv = qc[E + 2], eR = qc[E + 3];
-    const double Tw = P[4];
-    const double Ac = rho * pow(2.0 * PI * Tt, -0.5 * DIM), Bc = 0.5 / Tt;
-    const double Aw = pow(2.0 * PI * Tw, -0.5 * DIM), Bw = 0.5 / Tw;
-    double acc[2 * NS + 2];
-    for (int k = 0; k < 2 * NS + 2; ++k) acc[k] = 0.0;
+    R n[DIM], uw[DIM];
+    for (int a = 0; a < DIM; ++a) {
+        n[a] = R(g.bf_n[(size_t)b * 2 + a]);
+        uw[a] = R(P[1 + a]);
+    }
+    const R rho = qc[0], Tt = qc[E], Tr = qc[E + 1], Tv = qc[E + 2], eR = qc[E + 3];
+    const R Tw = R(P[4]);
+    const R Ac = rho * pow(R(2.0 * PI) * Tt, R(-0.5 * DIM)), Bc = R(0.5) / Tt;
+    const R Aw = pow(R(2.0 * PI) * Tw, R(-0.5 * DIM)), Bw = R(0.5) / Tw;
+    const R hr = R(0.5 * m.d_r), hv = R(0.5 * m.d_v);
+    R acc[2 * NS + 2];
+    for (int k = 0; k < 2 * NS + 2; ++k) acc[k] = R(0);
     for (int v = threadIdx.x; v < vq.n; v += blockDim.x) {
-        double xi[DIM], xn = 0.0, x2 = 0.0;
+        R xi[DIM], xn = R(0), x2 = R(0);
         for (int a = 0; a < DIM; ++a) {
-            xi[a] = vq.x[a * vq.n_pad + v];
+            xi[a] = R(vq.x[a * vq.n_pad + v]);
             xn += xi[a] * n[a];
             x2 += xi[a] * xi[a];
         }
-        const double wf = vq.w[v] * xn;
-        double f0, fh, f1, f2;
-        double *s;
-        if (xn > 0.0) {
-            double c2 = 0.0;
+        const R wf = R(vq.w[v]) * xn;
+        R f0, fh, f1, f2;
+        R *s;
+        if (xn > R(0)) {
+            R c2 = R(0);
             for (int a = 0; a < DIM; ++a) c2 += (xi[a] - qc[1 + a]) * (xi[a] - qc[1 + a]);
             f0 = Ac * exp(-Bc * c2);
-            fh = MH * Tt * f0;
-            f1 = 0.5 * m.d_r * Tr * f0;
-            f2 = 0.5 * m.d_v * Tv * f0;
+            fh = R(MH) * Tt * f0;
+            f1 = hr * Tr * f0;
+            f2 = hv * Tv * f0;
             s = acc;
         } else {
-            double c2 = 0.0;
-            for (int a = 0; a < DIM; ++a) c2 += (xi[a] - P[1 + a]) * (xi[a] - P[1 + a]);
+            R c2 = R(0);
+            for (int a = 0; a < DIM; ++a) c2 += (xi[a] - uw[a]) * (xi[a] - uw[a]);
             f0 = Aw * exp(-Bw * c2);
-            fh = MH * Tw * f0;
-            f1 = 0.5 * m.d_r * Tw * f0;
-            f2 = 0.5 * m.d_v * Tw * f0;
+            fh = R(MH) * Tw * f0;
+            f1 = hr * Tw * f0;
+            f2 = hv * Tw * f0;
             s = acc + NS;
         }
         s[0] += wf * f0;
         for (int a = 0; a < DIM; ++a) s[1 + a] += wf * f0 * xi[a];
-        s[E] += wf * (0.5 * x2 * f0 + 0.5 * fh + f1 + f2);
+        s[E] += wf * (R(0.5) * x2 * f0 + R(0.5) * fh + f1 + f2);
         s[E + 1] += wf * f1;
         s[E + 2] += wf * f2;
     }
-    const double Iw = m.sigma_R * Tw * Tw * Tw * Tw / PI, Io = eR / (4.0 * PI);
+    const R Iw = R(m.sigma_R) * Tw * Tw * Tw * Tw / R(PI), Io = eR / R(4.0 * PI);
     for (int o = threadIdx.x; o < oq.n; o += blockDim.x) {
-        double on = 0.0;
-        for (int a = 0; a < DIM; ++a) on += oq.x[a * oq.n_pad + o] * n[a];
-        acc[2 * NS] += oq.w[o] * on * (on > 0.0 ? Io : Iw);
+        R on = R(0);
+        for (int a = 0; a < DIM; ++a) on += R(oq.x[a * oq.n_pad + o]) * n[a];
+        acc[2 * NS] += R(oq.w[o]) * on * (on > R(0) ? Io : Iw);
     }
-    block_sum<128>(acc, 2 * NS + 1, red);
+    block_sum<128, R>(acc, 2 * NS + 1, red);
     if (threadIdx.x == 0) {
-        const double rw = -red[0] / red[NS];
-        double F[NV];
+        const R rw = -red[0] / red[NS];
+        R F[NV];
         for (int k = 0; k < NS; ++k) F[k] = red[k] + rw * red[NS + k];
         F[E + 3] = red[2 * NS];
         F[E] += F[E + 3];
@@ -531,7 +553,7 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
 
 // ------------------------------------------------------------------ high-order terms
 // one thread per interior face, then one per boundary face
-template <int DIM>
+template <typename R, int DIM>
 __global__ void k_macro_hot(MacroGeom g, ModelDev m, const double *__restrict__ Fk, const double *__restrict__ q,
                             const double *__restrict__ grad, const double *__restrict__ kin_bflux,
                             const double *__restrict__ mac_bflux, double *__restrict__ hot,
@@ -539,11 +561,11 @@ __global__ void k_macro_hot(MacroGeom g, ModelDev m, const double *__restrict__ 
     constexpr int NV = DIM + 5;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < g.n_fi) {
-        double base[3][3];
-        kappa_base(m, base);
-        double pf[NV], fg[DIM][DIM + 5], s[NHOT];
-        face_state<DIM>(g, t, q, grad, pf, fg);
-        nsf_face<DIM>(pf, fg, m, base, s);
+        R base[3][3];
+        kappa_base<R>(m, base);
+        R pf[NV], fg[DIM][DIM + 5], s[NHOT];
+        face_state<R, DIM>(g, t, q, grad, pf, fg);
+        nsf_face<R, DIM>(pf, fg, m, base, s);
         const double *ri = Fk + (size_t)g.fi_i[t] * NF, *rj = Fk + (size_t)g.fi_j[t] * NF;
         auto sig = [&](const double *r, int a, int b) {
             const int idx[3][3] = {{20, 23, 24}, {23, 21, 25}, {24, 25, 22}};
@@ -551,11 +573,11 @@ __global__ void k_macro_hot(MacroGeom g, ModelDev m, const double *__restrict__ 
         };
         double *h = hot + (size_t)t * NHOT;
         for (int a = 0; a < DIM; ++a)
-            for (int b = 0; b < DIM; ++b) h[a * DIM + b] = 0.5 * (sig(ri, a, b) + sig(rj, a, b)) - s[a * DIM + b];
+            for (int b = 0; b < DIM; ++b) h[a * DIM + b] = 0.5 * (sig(ri, a, b) + sig(rj, a, b)) - (double)s[a * DIM + b];
         for (int md = 0; md < 4; ++md)
             for (int d = 0; d < DIM; ++d) {
                 const int k = 8 + 3 * md + d;
-                h[DIM * DIM + md * DIM + d] = 0.5 * (ri[k] + rj[k]) - s[DIM * DIM + md * DIM + d];
+                h[DIM * DIM + md * DIM + d] = 0.5 * (ri[k] + rj[k]) - (double)s[DIM * DIM + md * DIM + d];
             }
         return;
     }
@@ -566,18 +588,19 @@ __global__ void k_macro_hot(MacroGeom g, ModelDev m, const double *__restrict__ 
 }
 
 // ------------------------------------------------------------------ residual and diagonal
-constexpr int MR_NT = 128;     // threads per CTA of the residual kernel
+constexpr int MR_NT = 32;      // threads per CTA of the per-cell kernels (small CTAs spread FP64 work over SMs)
 constexpr int DSTR = 24;       // Dinv record: NVM diagonal inverses (first E used), 4x4 block
 
 namespace {
 
 // Gauss-Jordan inverse of a 4x4 matrix with partial pivoting
-__device__ void inverse4(const double (&A)[4][4], double (&X)[4][4]) {
-    double M[4][8];
+template <typename R>
+__device__ void inverse4(const R (&A)[4][4], R (&X)[4][4]) {
+    R M[4][8];
     for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) {
             M[r][c] = A[r][c];
-            M[r][4 + c] = r == c ? 1.0 : 0.0;
+            M[r][4 + c] = r == c ? R(1) : R(0);
         }
     for (int c = 0; c < 4; ++c) {
         int p = c;
@@ -585,15 +608,15 @@ __device__ void inverse4(const double (&A)[4][4], double (&X)[4][4]) {
             if (fabs(M[r][c]) > fabs(M[p][c])) p = r;
         if (p != c)
             for (int k = 0; k < 8; ++k) {
-                const double t = M[c][k];
+                const R t = M[c][k];
                 M[c][k] = M[p][k];
                 M[p][k] = t;
             }
-        const double inv = 1.0 / M[c][c];
+        const R inv = R(1) / M[c][c];
         for (int k = 0; k < 8; ++k) M[c][k] *= inv;
         for (int r = 0; r < 4; ++r) {
             if (r == c) continue;
-            const double f = M[r][c];
+            const R f = M[r][c];
             for (int k = 0; k < 8; ++k) M[r][k] -= f * M[c][k];
         }
     }
@@ -603,97 +626,101 @@ __device__ void inverse4(const double (&A)[4][4], double (&X)[4][4]) {
 
 }  // namespace
 
-template <int DIM, int ORDER>
-__global__ void __launch_bounds__(MR_NT) k_macro_residual(MacroGeom g, ModelDev m, double cfl_macro,
-                                                          const MacroState *__restrict__ st,
-                                                          const double *__restrict__ q, const double *__restrict__ grad,
-                                                          const double *__restrict__ phi, const double *__restrict__ hot,
-                                                          const double *__restrict__ bflux,
-                                                          const double *__restrict__ hot_b, double *__restrict__ Rg,
-                                                          double *__restrict__ Dinv, double *__restrict__ gam,
-                                                          double *__restrict__ rpart) {
-    constexpr int NV = DIM + 5, E = 1 + DIM, ER = 4 + DIM;
+// four lanes per cell (lane k = face k): each lane evaluates one face flux and its Gamma;
+// lane 0 adds the sources and builds D^-1
+template <typename R, int DIM, int ORDER>
+__global__ void __launch_bounds__(128) k_macro_residual(MacroGeom g, ModelDev m, double cfl_macro,
+                                                        const MacroState *__restrict__ st,
+                                                        const double *__restrict__ q, const double *__restrict__ grad,
+                                                        const double *__restrict__ phi, const double *__restrict__ hot,
+                                                        const double *__restrict__ bflux,
+                                                        const double *__restrict__ hot_b, double *__restrict__ Rg,
+                                                        double *__restrict__ Dinv, double *__restrict__ gam,
+                                                        double *__restrict__ rpart) {
+    constexpr int NV = DIM + 5, E = 1 + DIM, ER = 4 + DIM, L = 4;
     if (st && st->done) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double r2 = 0.0;
-    if (i < g.n_cells) {
-        double base[3][3];
-        kappa_base(m, base);
-        const double *qi = q + (size_t)i * NVM;
-        double R[NV], gsum = 0.0, gsumR = 0.0;
-        for (int k = 0; k < NV; ++k) R[k] = 0.0;
-        const int nf = g.info[i].x;
-        for (int k = 0; k < nf; ++k) {
-            const int fid = g.cface[i * MAXF + k];
-            if (fid >= 0) {
-                double F[NV];
-                interior_flux<DIM, ORDER>(g, m, base, fid, q, grad, phi, hot, F);
-                const double S = g.fi_S[fid];
-                const bool own = g.fi_i[fid] == i;
-                for (int v = 0; v < NV; ++v) R[v] += own ? -F[v] * S : F[v] * S;
-                const int o = own ? g.fi_j[fid] : g.fi_i[fid];
-                const double *qo = q + (size_t)o * NVM;
-                const double *n = g.fi_n + (size_t)fid * 2;
-                const double rf = 0.5 * (qi[0] + qo[0]), Tf = 0.5 * (qi[E] + qo[E]);
-                double un = 0.0;
-                for (int a = 0; a < DIM; ++a) un += 0.5 * (qi[1 + a] + qo[1 + a]) * n[a];
-                const double dn = g.fi_dn[fid];
-                const double gb = fabs(un) + sound_speed(Tf) + 2.0 * viscosity(Tf, m) / (rf * dn);
-                const double gR = 2.0 * (1.0 / (3.0 * absorption(rf, m))) / dn;
-                gam[((size_t)i * MAXF + k) * 2] = gb;
-                gam[((size_t)i * MAXF + k) * 2 + 1] = gR;
-                gsum += gb * S;
-                gsumR += gR * S;
-            } else {
-                const int b = -1 - fid;
-                const double S = g.bf_S[b];
-                for (int v = 0; v < NV; ++v)
-                    R[v] -= (bflux[(size_t)b * NVM + v] + hot_b[(size_t)b * NVM + v]) * S;
-                const double *n = g.bf_n + (size_t)b * 2;
-                double un = 0.0;
-                for (int a = 0; a < DIM; ++a) un += qi[1 + a] * n[a];
-                const double db = g.bf_dn[b];
-                const double gb = fabs(un) + sound_speed(qi[E]) + 2.0 * viscosity(qi[E], m) / (qi[0] * db);
-                const double gR = 2.0 * (1.0 / (3.0 * absorption(qi[0], m))) / db;
-                gsum += gb * S;
-                gsumR += gR * S;
-            }
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / L, k = gt % L;
+    const bool valid = i < g.n_cells;
+    const unsigned gmask = 0xFu << ((threadIdx.x & 31) & ~(L - 1));
+    R Rr[NV], gsum = R(0), gsumR = R(0);
+    for (int v = 0; v < NV; ++v) Rr[v] = R(0);
+    R qi[NV];
+    for (int v = 0; v < NV; ++v) qi[v] = valid ? R(q[(size_t)i * NVM + v]) : R(1);
+    if (valid && k < g.info[i].x) {
+        const int fid = g.cface[i * MAXF + k];
+        if (fid >= 0) {
+            R base[3][3];
+            kappa_base<R>(m, base);
+            R F[NV];
+            interior_flux<R, DIM, ORDER>(g, m, base, fid, q, grad, phi, hot, F);
+            const R S = R(g.fi_S[fid]);
+            const bool own = g.fi_i[fid] == i;
+            for (int v = 0; v < NV; ++v) Rr[v] = own ? -F[v] * S : F[v] * S;
+            const int o = own ? g.fi_j[fid] : g.fi_i[fid];
+            const double *qo = q + (size_t)o * NVM;
+            const R rf = R(0.5) * (qi[0] + R(qo[0])), Tf = R(0.5) * (qi[E] + R(qo[E]));
+            R un = R(0);
+            for (int a = 0; a < DIM; ++a) un += R(0.5) * (qi[1 + a] + R(qo[1 + a])) * R(g.fi_n[(size_t)fid * 2 + a]);
+            const R dn = R(g.fi_dn[fid]);
+            const R gb = fabs(un) + sound_speed(Tf) + R(2) * viscosity(Tf, m) / (rf * dn);
+            const R gR = R(2) * (R(1) / (R(3) * absorption(rf, m))) / dn;
+            gam[((size_t)i * MAXF + k) * 2] = gb;
+            gam[((size_t)i * MAXF + k) * 2 + 1] = gR;
+            gsum = gb * S;
+            gsumR = gR * S;
+        } else {
+            const int b = -1 - fid;
+            const R S = R(g.bf_S[b]);
+            for (int v = 0; v < NV; ++v) Rr[v] = -R(bflux[(size_t)b * NVM + v] + hot_b[(size_t)b * NVM + v]) * S;
+            R un = R(0);
+            for (int a = 0; a < DIM; ++a) un += qi[1 + a] * R(g.bf_n[(size_t)b * 2 + a]);
+            const R db = R(g.bf_dn[b]);
+            const R gb = fabs(un) + sound_speed(qi[E]) + R(2) * viscosity(qi[E], m) / (qi[0] * db);
+            const R gR = R(2) * (R(1) / (R(3) * absorption(qi[0], m))) / db;
+            gsum = gb * S;
+            gsumR = gR * S;
         }
-        const double V = g.vol[i];
-        double Q[NV];
-        source<DIM>(qi, m, Q);
+    }
+    for (int o = 1; o < L; o <<= 1) {
+        for (int v = 0; v < NV; ++v) Rr[v] += __shfl_xor_sync(gmask, Rr[v], o);
+        gsum += __shfl_xor_sync(gmask, gsum, o);
+        gsumR += __shfl_xor_sync(gmask, gsumR, o);
+    }
+    double r2 = 0.0;
+    if (valid && k == 0) {
+        const R V = R(g.vol[i]);
+        R Q[NV];
+        source<R, DIM>(qi, m, Q);
         for (int v = 0; v < NV; ++v) {
-            R[v] = R[v] / V + Q[v];
-            r2 += R[v] * R[v];
+            Rr[v] = Rr[v] / V + Q[v];
+            r2 += (double)Rr[v] * (double)Rr[v];
         }
         double *rg = Rg + (size_t)i * NVM;
-        for (int v = 0; v < NV; ++v) rg[v] = R[v];
-        rg[E] -= R[ER];
+        for (int v = 0; v < NV; ++v) rg[v] = Rr[v];
+        rg[E] -= (double)Rr[ER];
         // D = diag(1/dt + sum Gamma S / V) - dQ/dW (energy rows)
-        double um = 0.0;
+        R um = R(0);
         for (int a = 0; a < DIM; ++a) um += qi[1 + a] * qi[1 + a];
-        const double inv_dt = (sqrt(um) + sound_speed(qi[E])) / (cfl_macro * g.dx[i]);
+        const R inv_dt = (sqrt(um) + sound_speed(qi[E])) / (R(cfl_macro) * R(g.dx[i]));
         double *Di = Dinv + (size_t)i * DSTR;
-        const double d0 = inv_dt + gsum / V;
-        for (int v = 0; v < E; ++v) Di[v] = 1.0 / d0;
-        double J[4][4], Dm[4][4], X[4][4];
-        source_jacobian<DIM>(qi, m, J);
+        const R d0 = inv_dt + gsum / V;
+        for (int v = 0; v < E; ++v) Di[v] = R(1) / d0;
+        R J[4][4], Dm[4][4], X[4][4];
+        source_jacobian<R, DIM>(qi, m, J);
         for (int r = 0; r < 4; ++r)
-            for (int c = 0; c < 4; ++c) Dm[r][c] = (r == c ? (r == 3 ? inv_dt + (gsum + gsumR) / V : d0) : 0.0) - J[r][c];
-        inverse4(Dm, X);
+            for (int c = 0; c < 4; ++c)
+                Dm[r][c] = (r == c ? (r == 3 ? inv_dt + (gsum + gsumR) / V : d0) : R(0)) - J[r][c];
+        inverse4<R>(Dm, X);
         for (int r = 0; r < 4; ++r)
             for (int c = 0; c < 4; ++c) Di[NVM + r * 4 + c] = X[r][c];
     }
     // deterministic per-CTA partial of |R|^2
     for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
-    __shared__ double wsum[MR_NT / 32];
+    __shared__ double wsum[4];
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = r2;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < MR_NT / 32; ++w) s += wsum[w];
-        rpart[blockIdx.x] = s;
-    }
+    if (threadIdx.x == 0) rpart[blockIdx.x] = wsum[0] + wsum[1] + wsum[2] + wsum[3];
 }
 
 __global__ void k_macro_norm(int n_parts, const double *__restrict__ rpart, MacroState *__restrict__ st,
@@ -724,28 +751,32 @@ __global__ void k_macro_norm(int n_parts, const double *__restrict__ rpart, Macr
 
 // one point-relaxation sweep: every cell uses its neighbours' increments of the previous
 // sweep; increments are kept in the gas-energy form (row E holds d e_gas)
+// four lanes per cell (lane k = face k), summed with shuffles inside each group of four
+constexpr int LPC = 4;
+static_assert(LPC == MAXF, "one lane per cell face");
+
 template <int DIM>
-__global__ void k_macro_jacobi(MacroGeom g, ModelDev m, const MacroState *__restrict__ st, int first, int last,
-                               const double *__restrict__ W, const double *__restrict__ Rg,
-                               const double *__restrict__ Dinv, const double *__restrict__ gam,
-                               const double *__restrict__ dG_in, double *__restrict__ dG_out,
-                               double *__restrict__ W_next) {
+__global__ void __launch_bounds__(128) k_macro_jacobi(MacroGeom g, ModelDev m, const MacroState *__restrict__ st,
+                                                      int first, int last, const double *__restrict__ W,
+                                                      const double *__restrict__ Rg, const double *__restrict__ Dinv,
+                                                      const double *__restrict__ gam,
+                                                      const double *__restrict__ dG_in, double *__restrict__ dG_out,
+                                                      double *__restrict__ W_next) {
     constexpr int NV = DIM + 5, E = 1 + DIM, ER = 4 + DIM;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n_cells) return;
-    const double *Wi = W + (size_t)i * NVM;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = gt / LPC, k = gt % LPC;
+    const bool valid = i < g.n_cells;
+    const unsigned gmask = 0xFu << ((threadIdx.x & 31) & ~(LPC - 1));
     if (st->done) {
-        if (last)
-            for (int v = 0; v < NV; ++v) W_next[(size_t)i * NVM + v] = Wi[v];
+        if (last && valid && k == 0)
+            for (int v = 0; v < NV; ++v) W_next[(size_t)i * NVM + v] = W[(size_t)i * NVM + v];
         return;
     }
     double off[NV];
     for (int v = 0; v < NV; ++v) off[v] = 0.0;
-    if (!first) {
-        const int nf = g.info[i].x;
-        for (int k = 0; k < nf; ++k) {
-            const int fid = g.cface[i * MAXF + k];
-            if (fid < 0) continue;
+    if (valid && !first && k < g.info[i].x) {
+        const int fid = g.cface[i * MAXF + k];
+        if (fid >= 0) {
             const bool own = g.fi_i[fid] == i;
             const int o = own ? g.fi_j[fid] : g.fi_i[fid];
             double n[2] = {0.0, 0.0};
@@ -754,18 +785,21 @@ __global__ void k_macro_jacobi(MacroGeom g, ModelDev m, const MacroState *__rest
             double Wp[NV], q0[NV], q1[NV], F0[NV], F1[NV];
             for (int v = 0; v < NV; ++v) Wp[v] = Wo[v] + dGo[v];
             Wp[E] += dGo[ER];
-            primitive<DIM>(Wo, m, q0);
-            primitive<DIM>(Wp, m, q1);
-            convective_flux<DIM>(q1, n, m, F1);
-            convective_flux<DIM>(q0, n, m, F0);
+            primitive<double, DIM>(Wo, m, q0);
+            primitive<double, DIM>(Wp, m, q1);
+            convective_flux<double, DIM>(q1, n, m, F1);
+            convective_flux<double, DIM>(q0, n, m, F0);
             const double S = g.fi_S[fid];
             const double gb = gam[((size_t)i * MAXF + k) * 2], gR = gam[((size_t)i * MAXF + k) * 2 + 1];
             for (int v = 0; v < NV; ++v) {
                 const double G = v == ER ? gb + gR : gb;
-                off[v] += ((F1[v] - F0[v]) - G * dGo[v]) * S;
+                off[v] = ((F1[v] - F0[v]) - G * dGo[v]) * S;
             }
         }
     }
+    for (int v = 0; v < NV; ++v)
+        for (int o = 1; o < LPC; o <<= 1) off[v] += __shfl_xor_sync(gmask, off[v], o);
+    if (!valid || k != 0) return;
     const double V = g.vol[i];
     double x[NV];
     const double *rg = Rg + (size_t)i * NVM;
@@ -780,7 +814,7 @@ __global__ void k_macro_jacobi(MacroGeom g, ModelDev m, const MacroState *__rest
     }
     for (int v = 0; v < NV; ++v) dG_out[(size_t)i * NVM + v] = dG[v];
     if (last) {
-        for (int v = 0; v < NV; ++v) W_next[(size_t)i * NVM + v] = Wi[v] + dG[v];
+        for (int v = 0; v < NV; ++v) W_next[(size_t)i * NVM + v] = W[(size_t)i * NVM + v] + dG[v];
         W_next[(size_t)i * NVM + E] += dG[ER];
     }
 }
@@ -821,7 +855,7 @@ __global__ void k_macro_mass_rescale(int nv, int n_cells, const double *__restri
         }                                 \
     } while (0)
 
-int macro_rpart_count(int n_cells) { return (n_cells + MR_NT - 1) / MR_NT; }
+int macro_rpart_count(int n_cells) { return (n_cells * 4 + 127) / 128; }
 
 cudaError_t launch_macro_from_fields(cudaStream_t s, int dim, int n_cells, const ModelDev &m, const double *F,
                                      double *W) {
@@ -837,47 +871,60 @@ cudaError_t launch_macro_fields_from_W(cudaStream_t s, int dim, int n_cells, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro_grad(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m,
+#define MACRO_DISPATCH_R(fp32, ...)      \
+    do {                                  \
+        if (fp32) {                       \
+            using R = float;              \
+            __VA_ARGS__;                  \
+        } else {                          \
+            using R = double;             \
+            __VA_ARGS__;                  \
+        }                                 \
+    } while (0)
+
+cudaError_t launch_macro_grad(cudaStream_t s, const MacroGeom &g, int order, int fp32, const ModelDev &m,
                               const MacroState *st, const double *W, double *q, double *grad, double *phi) {
-    const int nb = (g.n_cells + 127) / 128;
-    if (order == 2) {
-        MACRO_DISPATCH(g.dim, (k_macro_grad<DIM, 2><<<nb, 128, 0, s>>>(g, m, st, W, q, grad, phi)));
-    } else {
-        MACRO_DISPATCH(g.dim, (k_macro_grad<DIM, 1><<<nb, 128, 0, s>>>(g, m, st, W, q, grad, phi)));
-    }
+    const int nb = (g.n_cells + MR_NT - 1) / MR_NT;
+    MACRO_DISPATCH_R(fp32, MACRO_DISPATCH(g.dim, {
+        if (order == 2) k_macro_grad<R, DIM, 2><<<nb, MR_NT, 0, s>>>(g, m, st, W, q, grad, phi);
+        else k_macro_grad<R, DIM, 1><<<nb, MR_NT, 0, s>>>(g, m, st, W, q, grad, phi);
+    }));
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const QuadD &vq,
+cudaError_t launch_macro_bflux(cudaStream_t s, const MacroGeom &g, int fp32, const ModelDev &m, const QuadD &vq,
                                const QuadD &oq, const MacroState *st, const double *q, double *bflux) {
     if (g.n_bf == 0) return cudaSuccess;
-    MACRO_DISPATCH(g.dim, (k_macro_bflux<DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, st, q, bflux)));
+    MACRO_DISPATCH_R(fp32, MACRO_DISPATCH(g.dim, (k_macro_bflux<R, DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, st, q,
+                                                                                                bflux))));
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro_hot(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const double *F_kin,
+cudaError_t launch_macro_hot(cudaStream_t s, const MacroGeom &g, int fp32, const ModelDev &m, const double *F_kin,
                              const double *q, const double *grad, const double *kin_bflux, const double *mac_bflux,
                              double *hot, double *hot_b) {
-    const int n = g.n_fi + g.n_bf, nb = (n + 127) / 128;
+    const int n = g.n_fi + g.n_bf, nb = (n + MR_NT - 1) / MR_NT;
     if (n == 0) return cudaSuccess;
-    MACRO_DISPATCH(g.dim, (k_macro_hot<DIM><<<nb, 128, 0, s>>>(g, m, F_kin, q, grad, kin_bflux, mac_bflux, hot,
-                                                                hot_b)));
+    MACRO_DISPATCH_R(fp32, MACRO_DISPATCH(g.dim, (k_macro_hot<R, DIM><<<nb, MR_NT, 0, s>>>(g, m, F_kin, q, grad,
+                                                                                          kin_bflux, mac_bflux, hot,
+                                                                                          hot_b))));
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order, const ModelDev &m, double cfl_macro,
-                                  const MacroState *st, const double *W, const double *q, const double *grad,
-                                  const double *phi, const double *hot, const double *bflux, const double *hot_b,
-                                  double *Rg, double *Dinv, double *gam, double *rpart) {
+cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order, int fp32, const ModelDev &m,
+                                  double cfl_macro, const MacroState *st, const double *W, const double *q,
+                                  const double *grad, const double *phi, const double *hot, const double *bflux,
+                                  const double *hot_b, double *Rg, double *Dinv, double *gam, double *rpart) {
     (void)W;
     const int nb = macro_rpart_count(g.n_cells);
-    if (order == 2) {
-        MACRO_DISPATCH(g.dim, (k_macro_residual<DIM, 2><<<nb, MR_NT, 0, s>>>(g, m, cfl_macro, st, q, grad, phi, hot,
-                                                                              bflux, hot_b, Rg, Dinv, gam, rpart)));
-    } else {
-        MACRO_DISPATCH(g.dim, (k_macro_residual<DIM, 1><<<nb, MR_NT, 0, s>>>(g, m, cfl_macro, st, q, grad, phi, hot,
-                                                                              bflux, hot_b, Rg, Dinv, gam, rpart)));
-    }
+    MACRO_DISPATCH_R(fp32, MACRO_DISPATCH(g.dim, {
+        if (order == 2)
+            k_macro_residual<R, DIM, 2><<<nb, 128, 0, s>>>(g, m, cfl_macro, st, q, grad, phi, hot, bflux, hot_b, Rg,
+                                                              Dinv, gam, rpart);
+        else
+            k_macro_residual<R, DIM, 1><<<nb, 128, 0, s>>>(g, m, cfl_macro, st, q, grad, phi, hot, bflux, hot_b, Rg,
+                                                              Dinv, gam, rpart);
+    }));
     return cudaGetLastError();
 }
 
@@ -889,7 +936,7 @@ cudaError_t launch_macro_norm(cudaStream_t s, int n_parts, const double *rpart, 
 cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const MacroState *st,
                                 int first, int last, const double *W, const double *Rg, const double *Dinv,
                                 const double *gam, const double *dG_in, double *dG_out, double *W_next) {
-    const int nb = (g.n_cells + 127) / 128;
+    const int nb = (g.n_cells * LPC + 127) / 128;
     MACRO_DISPATCH(g.dim, (k_macro_jacobi<DIM><<<nb, 128, 0, s>>>(g, m, st, first, last, W, Rg, Dinv, gam, dG_in,
                                                                    dG_out, W_next)));
     return cudaGetLastError();

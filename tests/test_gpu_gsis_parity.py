@@ -115,3 +115,14 @@ def test_gsis_inner_convergence_stops_early():
     fg, Ig, rec, eps = _run(wl, f, I, 1)
     fo, Io, Fo, eps_o = _oracle(wl, f, I, 1)
     assert_planes_close(fg, fo, 1e-9, "f^{k+1}")
+
+
+def test_gsis_step_fp32_residual_side():
+    """FP32 contexts may evaluate the synthetic residual side in FP32 (relaxation stays FP64)."""
+    wl = gi.workloads.with_solver(CASES["cavity72"](), precision="fp32", order=2, relax_block=16, max_inner=12,
+                                  tol_inner=0.0, macro_fp32=1)
+    f, I = _inputs(wl, 5, "fp32")
+    fg, Ig, rec, eps = _run(wl, f, I, 1)
+    fo, Io, Fo, eps_o = _oracle(wl, f, I, 1)
+    assert_planes_close(fg, fo, TOL["fp32"], "f^{k+1}")
+    assert_fields_close(rec, Fo, TOL["fp32"], wl.dim, "moments of f^{k+1}")
