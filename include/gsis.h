@@ -214,6 +214,44 @@ int gsis_last_eps(gsis_ctx *ctx, double *eps_out);
  * first and last residual norms ||R||_2.  Synchronises the context stream. */
 int gsis_macro_stats(gsis_ctx *ctx, int32_t *inner_iters, double *r0, double *rn);
 
+/* ---- learned closure (warm start) -----------------------------------------------
+ * A perceptron 16 -> 128 -> 128 -> 128 -> 12 (GELU hidden layers) maps the state of a
+ * cell to its high-order terms (Eq. getHoTs):
+ *   inputs  rho, u_x, u_y, T_t, T_r, T_v, T_R, the magnitudes of their least-squares
+ *           gradients (T_R through e_R), Kn, 1/Kn_p;
+ *   outputs HoT_sigma (xx, xy, yy, zz) / (rho T_t), HoT_q (t, r, v, R) x (x, y) /
+ *           (rho T_t^1.5).
+ * Weights are used in BF16 with FP32 accumulation; FP32 master weights are trained by
+ * Adam on the mean squared error of standardised outputs.  The parameter blob
+ * (GSIS_MLP_NPARAM floats) is W0 b0 W1 b1 W2 b2 W3 b3 (W row-major [out][in]) followed
+ * by the input and output standardisation (x_mean[16] x_std[16] y_mean[12] y_std[12]).
+ * All buffers are host memory owned by the caller; sample arrays are row-major. */
+#define GSIS_MLP_NPARAM 36804
+#define GSIS_MLP_NW 36748
+
+/* He-normal weights from a seeded generator, zero biases, identity standardisation. */
+int gsis_mlp_init(gsis_ctx *ctx, uint64_t seed);
+int gsis_mlp_set_params(gsis_ctx *ctx, const float *params, int64_t len);
+int gsis_mlp_get_params(gsis_ctx *ctx, float *params, int64_t len);
+/* Features X [n_cells][16] and targets Y [n_cells][12] (Y may be NULL) of the current
+ * fields: training samples taken from the solver's own iterations. */
+int gsis_mlp_samples(gsis_ctx *ctx, float *X, float *Y, int64_t n_cells);
+/* Standardisation from the samples, then epochs of shuffled mini-batches of `batch`
+ * rows (seeded); *loss_out (may be NULL) receives the last batch's loss. */
+int gsis_mlp_train(gsis_ctx *ctx, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch,
+                   double lr, uint64_t seed, double *loss_out);
+/* Outputs (in target units) for raw inputs. */
+int gsis_mlp_predict(gsis_ctx *ctx, const float *X, int64_t n, float *Y);
+/* Loss on standardised targets and its gradient with respect to W0..b3 (grad: NULL or
+ * GSIS_MLP_NW floats), without updating the parameters. */
+int gsis_mlp_loss_grad(gsis_ctx *ctx, const float *X, const float *Y, int64_t n, double *loss, float *grad);
+/* Warm start: n_presolve synthetic solves from the current fields with high-order terms
+ * predicted by the network (use_mlp = 1) or zero (use_mlp = 0, the NSF limit), then
+ * f = f_eq(M) and I = sigma_R T_R^4 / pi.  GSIS from there converges to the kinetic
+ * solution whatever the prediction: the network only moves the starting point.
+ * Errors: INVALID_ARG (use_mlp without a trained or set network), CUDA. */
+int gsis_warm_start(gsis_ctx *ctx, int32_t n_presolve, int32_t use_mlp);
+
 /* Kernel timing.  While enabled, the library brackets each of its kernel launches with
  * CUDA events on the context stream and accumulates device time per kernel id.
  * gsis_profile_read fills up to n entries of names/ms/launches (arrays of length n)

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <algorithm>
 #include <new>
+#include <random>
 #include <string>
 #include <vector>
 
@@ -17,13 +18,13 @@ namespace {
 
 enum KernelId {
     K_COEF, K_WALL, K_SLOPE_GAS, K_SWEEP_GAS, K_SLOPE_PHOTON, K_SWEEP_PHOTON, K_FINISH, K_EPS, K_EQUIL, K_MOMENTS,
-    K_KBFLUX, K_HOT, K_MGRAD, K_MBFLUX, K_MRES, K_MNORM, K_MJACOBI, K_MCONV, K_SYNC, K_COUNT
+    K_KBFLUX, K_HOT, K_MGRAD, K_MBFLUX, K_MRES, K_MNORM, K_MJACOBI, K_MCONV, K_SYNC, K_MLP, K_COUNT
 };
 const char *kKernelNames[K_COUNT] = {"coefficients", "wall_density",  "slopes_gas",    "sweep_gas",
                                      "slopes_photon", "sweep_photon", "finish",        "eps_reduce",
                                      "equilibrium",  "moments_only",  "kinetic_bflux", "macro_hot",
                                      "macro_grad",   "macro_bflux",   "macro_residual", "macro_norm",
-                                     "macro_jacobi", "macro_convert", "sync"};
+                                     "macro_jacobi", "macro_convert", "sync",          "mlp"};
 
 }  // namespace
 
@@ -56,6 +57,12 @@ struct gsis_ctx {
     // synthetic equations (FP64): geometry, quadratures in FP64, state and work arrays
     MacroGeom mg{};
     bool closed = true;          // walls only: the synthetic solution keeps the mass
+    MlpDev mlp;                  // learned closure (allocated on first use)
+    std::vector<void *> mlp_alloc;
+    float *mlp_X = nullptr, *mlp_Y = nullptr;   // per-cell features / predictions [nc][16], [nc][12]
+    int *mlp_idx = nullptr;
+    float *mlp_data = nullptr;   // training data on the device
+    int64_t mlp_data_cap = 0;
     int mfp32 = 0;               // FP32 path: residual side of the synthetic equations in FP32
     int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
     double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
@@ -580,6 +587,7 @@ void gsis_destroy(gsis_ctx *ctx) {
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->macro_exec) cudaGraphExecDestroy(ctx->macro_exec);
+    for (void *p : ctx->mlp_alloc) cudaFree(p);
     for (void *p : ctx->allocations) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_mstate) cudaFreeHost(ctx->h_mstate);
@@ -1143,6 +1151,304 @@ int gsis_solve(gsis_ctx *c, int32_t mode, int32_t max_outer, double tol, int32_t
         if (e < t) return GSIS_OK;
     }
     return fail(c, GSIS_ERR_NOT_CONVERGED, "max_outer reached before tol");
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- learned closure
+namespace {
+
+int mlp_malloc(gsis_ctx *c, void **p, size_t bytes) {
+    if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        *p = nullptr;
+        return fail(c, GSIS_ERR_OUT_OF_MEMORY, "learned-closure buffers");
+    }
+    c->mlp_alloc.push_back(*p);
+    return GSIS_OK;
+}
+
+void mlp_free(gsis_ctx *c, void *p) {
+    if (!p) return;
+    cudaFree(p);
+    c->mlp_alloc.erase(std::remove(c->mlp_alloc.begin(), c->mlp_alloc.end(), p), c->mlp_alloc.end());
+}
+
+// parameters, moments and per-cell buffers once; work buffers for at least n rows
+int mlp_ensure(gsis_ctx *c, int64_t n) {
+    MlpDev &d = c->mlp;
+    if (!d.p) {
+        TRY(mlp_malloc(c, (void **)&d.p, MLP_NPARAM * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&d.g, MLP_NW * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&d.m1, MLP_NW * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&d.m2, MLP_NW * sizeof(float)));
+        TRY(mlp_malloc(c, &d.pb, MLP_NW * 2));
+        TRY(mlp_malloc(c, (void **)&c->mlp_X, (size_t)c->nc * MLP_IN * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&c->mlp_Y, (size_t)c->nc * MLP_OUT * sizeof(float)));
+        CUDA_TRY(c, cudaMemsetAsync(d.p, 0, MLP_NPARAM * sizeof(float), c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(d.m1, 0, MLP_NW * sizeof(float), c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(d.m2, 0, MLP_NW * sizeof(float), c->stream));
+    }
+    if (n > d.cap) {
+        const int widths[MLP_LAYERS + 1] = {MLP_IN, MLP_H, MLP_H, MLP_H, MLP_OUT};
+        for (int l = 0; l <= MLP_LAYERS; ++l) mlp_free(c, d.act[l]);
+        for (int l = 0; l < MLP_LAYERS; ++l) mlp_free(c, d.pre[l]);
+        mlp_free(c, d.dA[0]);
+        mlp_free(c, d.dA[1]);
+        mlp_free(c, d.T);
+        mlp_free(c, d.lpart);
+        mlp_free(c, c->mlp_idx);
+        for (int l = 0; l <= MLP_LAYERS; ++l) TRY(mlp_malloc(c, (void **)&d.act[l], n * widths[l] * sizeof(float)));
+        for (int l = 0; l < MLP_LAYERS; ++l) TRY(mlp_malloc(c, (void **)&d.pre[l], n * widths[l + 1] * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&d.dA[0], n * MLP_H * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&d.dA[1], n * MLP_H * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&d.T, n * MLP_OUT * sizeof(float)));
+        TRY(mlp_malloc(c, (void **)&d.lpart, (size_t)mlp_loss_parts((int)n) * sizeof(double)));
+        TRY(mlp_malloc(c, (void **)&c->mlp_idx, n * sizeof(int)));
+        d.cap = (int)n;
+    }
+    return GSIS_OK;
+}
+
+const float *x_mean(const gsis_ctx *c) { return c->mlp.p + MLP_NW; }
+const float *x_std(const gsis_ctx *c) { return c->mlp.p + MLP_NW + MLP_IN; }
+const float *y_mean(const gsis_ctx *c) { return c->mlp.p + MLP_NW + 2 * MLP_IN; }
+const float *y_std(const gsis_ctx *c) { return c->mlp.p + MLP_NW + 2 * MLP_IN + MLP_OUT; }
+
+// forward pass of n rows already standardised in act[0]; loss over standardised targets in T
+int mlp_loss(gsis_ctx *c, int n, double *loss) {
+    MlpDev &d = c->mlp;
+    CUDA_TRY(c, launch_mlp_forward(c->stream, d, n));
+    CUDA_TRY(c, launch_mlp_loss_backward(c->stream, d, n));
+    c->launches += 4 + 1 + 3 + 4 + 3;
+    if (loss) {
+        const int np = mlp_loss_parts(n);
+        std::vector<double> part(np);
+        CUDA_TRY(c, cudaMemcpyAsync(part.data(), d.lpart, np * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        double sum = 0.0;
+        for (double x : part) sum += x;
+        *loss = sum / ((double)n * MLP_OUT);
+    }
+    return GSIS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsis_mlp_set_params(gsis_ctx *c, const float *p, int64_t len) {
+    if (!c || !p || len < MLP_NPARAM) return fail(c, GSIS_ERR_INVALID_ARG, "parameter buffer too short");
+    TRY(mlp_ensure(c, 1));
+    CUDA_TRY(c, cudaMemcpyAsync(c->mlp.p, p, MLP_NPARAM * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->mlp.m1, 0, MLP_NW * sizeof(float), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->mlp.m2, 0, MLP_NW * sizeof(float), c->stream));
+    CUDA_TRY(c, launch_mlp_to_bf16(c->stream, c->mlp));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->mlp.step = 0;
+    c->mlp.trained = true;
+    return GSIS_OK;
+}
+
+int gsis_mlp_get_params(gsis_ctx *c, float *p, int64_t len) {
+    if (!c || !p || len < MLP_NPARAM) return fail(c, GSIS_ERR_INVALID_ARG, "parameter buffer too short");
+    if (!c->mlp.p) return fail(c, GSIS_ERR_INVALID_ARG, "no network parameters yet");
+    CUDA_TRY(c, cudaMemcpyAsync(p, c->mlp.p, MLP_NPARAM * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return GSIS_OK;
+}
+
+int gsis_mlp_init(gsis_ctx *c, uint64_t seed) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    std::vector<float> p(MLP_NPARAM, 0.0f);
+    std::mt19937_64 rng(seed);
+    size_t o = 0;
+    const int ins[MLP_LAYERS] = {MLP_IN, MLP_H, MLP_H, MLP_H}, outs[MLP_LAYERS] = {MLP_H, MLP_H, MLP_H, MLP_OUT};
+    for (int l = 0; l < MLP_LAYERS; ++l) {
+        std::normal_distribution<double> nd(0.0, std::sqrt(2.0 / ins[l]));
+        for (int k = 0; k < outs[l] * ins[l]; ++k) p[o++] = (float)nd(rng);
+        o += outs[l];   // zero biases
+    }
+    for (int k = 0; k < MLP_IN; ++k) p[MLP_NW + MLP_IN + k] = 1.0f;                       // x_std
+    for (int k = 0; k < MLP_OUT; ++k) p[MLP_NW + 2 * MLP_IN + MLP_OUT + k] = 1.0f;        // y_std
+    TRY(gsis_mlp_set_params(c, p.data(), MLP_NPARAM));
+    c->mlp.trained = false;
+    return GSIS_OK;
+}
+
+int gsis_mlp_loss_grad(gsis_ctx *c, const float *X, const float *Y, int64_t n, double *loss, float *grad) {
+    if (!c || !X || !Y || n <= 0) return fail(c, GSIS_ERR_INVALID_ARG, "bad samples");
+    if (!c->mlp.p) return fail(c, GSIS_ERR_INVALID_ARG, "no network parameters yet");
+    TRY(mlp_ensure(c, n));
+    MlpDev &d = c->mlp;
+    CUDA_TRY(c, cudaMemcpyAsync(d.act[0], X, n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(d.T, Y, n * MLP_OUT * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)n, MLP_IN, d.act[0], x_mean(c), x_std(c), 0));
+    CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)n, MLP_OUT, d.T, y_mean(c), y_std(c), 0));
+    TRY(mlp_loss(c, (int)n, loss));
+    if (grad) {
+        CUDA_TRY(c, cudaMemcpyAsync(grad, d.g, MLP_NW * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    return GSIS_OK;
+}
+
+int gsis_mlp_predict(gsis_ctx *c, const float *X, int64_t n, float *Y) {
+    if (!c || !X || !Y || n <= 0) return fail(c, GSIS_ERR_INVALID_ARG, "bad samples");
+    if (!c->mlp.p) return fail(c, GSIS_ERR_INVALID_ARG, "no network parameters yet");
+    TRY(mlp_ensure(c, n));
+    MlpDev &d = c->mlp;
+    CUDA_TRY(c, cudaMemcpyAsync(d.act[0], X, n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)n, MLP_IN, d.act[0], x_mean(c), x_std(c), 0));
+    CUDA_TRY(c, launch_mlp_forward(c->stream, d, (int)n));
+    CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)n, MLP_OUT, d.act[MLP_LAYERS], y_mean(c), y_std(c), 1));
+    CUDA_TRY(c, cudaMemcpyAsync(Y, d.act[MLP_LAYERS], n * MLP_OUT * sizeof(float), cudaMemcpyDeviceToHost,
+                                c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->launches += 6;
+    return GSIS_OK;
+}
+
+int gsis_mlp_train(gsis_ctx *c, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch, double lr,
+                   uint64_t seed, double *loss_out) {
+    if (!c || !X || !Y || n <= 0 || epochs < 0 || batch <= 0 || !(lr > 0))
+        return fail(c, GSIS_ERR_INVALID_ARG, "bad training arguments");
+    if (!c->mlp.p) TRY(gsis_mlp_init(c, seed));
+    const int64_t b = std::min<int64_t>(batch, n);
+    TRY(mlp_ensure(c, b));
+    MlpDev &d = c->mlp;
+    // standardisation from the data (FP64 sums), kept with the parameters
+    std::vector<float> stat(MLP_NSTAT);
+    auto moments = [&](const float *A, int m, float *mean, float *sd) {
+        for (int j = 0; j < m; ++j) {
+            double s = 0.0, s2 = 0.0;
+            for (int64_t r = 0; r < n; ++r) {
+                const double x = A[r * m + j];
+                s += x;
+                s2 += x * x;
+            }
+            const double mu = s / n, var = std::max(s2 / n - mu * mu, 0.0);
+            mean[j] = (float)mu;
+            sd[j] = var > 0 ? (float)std::sqrt(var) : 1.0f;
+        }
+    };
+    moments(X, MLP_IN, stat.data(), stat.data() + MLP_IN);
+    moments(Y, MLP_OUT, stat.data() + 2 * MLP_IN, stat.data() + 2 * MLP_IN + MLP_OUT);
+    CUDA_TRY(c, cudaMemcpyAsync(d.p + MLP_NW, stat.data(), MLP_NSTAT * sizeof(float), cudaMemcpyHostToDevice,
+                                c->stream));
+    // the data set on the device, standardised
+    const int64_t need = n * (MLP_IN + MLP_OUT);
+    if (need > c->mlp_data_cap) {
+        mlp_free(c, c->mlp_data);
+        TRY(mlp_malloc(c, (void **)&c->mlp_data, need * sizeof(float)));
+        c->mlp_data_cap = need;
+    }
+    float *Xd = c->mlp_data, *Yd = c->mlp_data + n * MLP_IN;
+    CUDA_TRY(c, cudaMemcpyAsync(Xd, X, n * MLP_IN * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(Yd, Y, n * MLP_OUT * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)n, MLP_IN, Xd, x_mean(c), x_std(c), 0));
+    CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)n, MLP_OUT, Yd, y_mean(c), y_std(c), 0));
+    std::vector<int> perm(n);
+    for (int64_t r = 0; r < n; ++r) perm[r] = (int)r;
+    std::mt19937_64 rng(seed ^ 0x9E3779B97F4A7C15ull);
+    double last = 0.0;
+    for (int ep = 0; ep < epochs; ++ep) {
+        std::shuffle(perm.begin(), perm.end(), rng);
+        for (int64_t s0 = 0; s0 + b <= n; s0 += b) {
+            CUDA_TRY(c, cudaMemcpyAsync(c->mlp_idx, perm.data() + s0, b * sizeof(int), cudaMemcpyHostToDevice,
+                                        c->stream));
+            CUDA_TRY(c, launch_mlp_gather(c->stream, (int)b, MLP_IN, c->mlp_idx, Xd, d.act[0]));
+            CUDA_TRY(c, launch_mlp_gather(c->stream, (int)b, MLP_OUT, c->mlp_idx, Yd, d.T));
+            const bool report = ep == epochs - 1 && s0 + 2 * b > n;
+            TRY(mlp_loss(c, (int)b, report ? &last : nullptr));
+            CUDA_TRY(c, launch_mlp_adam(c->stream, d, (float)lr));
+            c->launches += 3;
+        }
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    d.trained = true;
+    if (loss_out) *loss_out = last;
+    return GSIS_OK;
+}
+
+int gsis_mlp_samples(gsis_ctx *c, float *X, float *Y, int64_t n_cells) {
+    if (!c || !X || n_cells < c->nc) return fail(c, GSIS_ERR_INVALID_ARG, "sample buffers too short");
+    TRY(mlp_ensure(c, 1));
+    TRY(launch(c, K_MCONV, [&] {
+        return launch_macro_from_fields(c->stream, c->dim, (int)c->nc, c->model, c->fields, c->W[0]);
+    }));
+    TRY(launch(c, K_MGRAD, [&] {
+        return launch_macro_grad(c->stream, c->mg, 1, 0, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
+    }));
+    TRY(launch(c, K_MLP, [&] {
+        return launch_cell_features(c->stream, c->mg, c->model, c->fields, c->mq, c->mgrad, c->mlp_X,
+                                    Y ? c->mlp_Y : nullptr);
+    }));
+    CUDA_TRY(c, cudaMemcpyAsync(X, c->mlp_X, c->nc * MLP_IN * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (Y)
+        CUDA_TRY(c, cudaMemcpyAsync(Y, c->mlp_Y, c->nc * MLP_OUT * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return GSIS_OK;
+}
+
+}  // extern "C"
+
+template <typename Real>
+int warm_start(gsis_ctx *c, int n_presolve, bool use_mlp) {
+    const MacroGeom &g = c->mg;
+    if (use_mlp) TRY(mlp_ensure(c, c->nc));
+    for (int k = 0; k < n_presolve; ++k) {
+        TRY(launch(c, K_MCONV, [&] {
+            return launch_macro_from_fields(c->stream, c->dim, (int)c->nc, c->model, c->fields, c->W[0]);
+        }));
+        TRY(launch(c, K_MGRAD, [&] {
+            return launch_macro_grad(c->stream, g, 1, 0, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
+        }));
+        if (use_mlp) {
+            MlpDev &d = c->mlp;
+            TRY(launch(c, K_MLP, [&] {
+                return launch_cell_features(c->stream, g, c->model, c->fields, c->mq, c->mgrad, d.act[0], nullptr);
+            }));
+            CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)c->nc, MLP_IN, d.act[0], x_mean(c), x_std(c), 0));
+            CUDA_TRY(c, launch_mlp_forward(c->stream, d, (int)c->nc));
+            CUDA_TRY(c, launch_mlp_standardise(c->stream, (int)c->nc, MLP_OUT, d.act[MLP_LAYERS], y_mean(c), y_std(c),
+                                               1));
+            c->launches += 6;
+            TRY(launch(c, K_MLP, [&] {
+                return launch_hot_from_cells(c->stream, g, c->mq, d.act[MLP_LAYERS], c->hot, c->hot_b);
+            }));
+        } else {
+            CUDA_TRY(c, cudaMemsetAsync(c->hot, 0, (size_t)std::max(g.n_fi, 1) * NHOT * sizeof(double), c->stream));
+            CUDA_TRY(c, cudaMemsetAsync(c->hot_b, 0, (size_t)std::max(g.n_bf, 1) * NVM * sizeof(double), c->stream));
+        }
+        int w = 0;
+        TRY(macro_solve(c, &w));
+        if (c->closed) {
+            TRY(launch(c, K_MCONV, [&] {
+                return launch_macro_mass_rescale(c->stream, c->dim, (int)c->nc, c->vol, c->fields, c->W[w]);
+            }));
+        }
+        TRY(launch(c, K_MCONV, [&] {
+            return launch_macro_fields_from_W(c->stream, c->dim, (int)c->nc, c->model, c->W[w], c->fields_n);
+        }));
+        std::swap(c->fields, c->fields_n);
+    }
+    TRY(launch(c, K_EQUIL, [&] {
+        return launch_equilibrium<Real>(c->stream, c->dim, (int)c->nc, vquad<Real>(c), oquad<Real>(c), c->model,
+                                        c->fields, (Real *)c->f[c->cur], (Real *)c->I[c->cur]);
+    }));
+    TRY(refresh(c));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return GSIS_OK;
+}
+
+extern "C" {
+
+int gsis_warm_start(gsis_ctx *c, int32_t n_presolve, int32_t use_mlp) {
+    if (!c || n_presolve < 0) return GSIS_ERR_INVALID_ARG;
+    if (use_mlp && (!c->mlp.p || !c->mlp.trained))
+        return fail(c, GSIS_ERR_INVALID_ARG, "the learned closure has not been trained or set");
+    return c->precision == GSIS_FP64 ? warm_start<double>(c, n_presolve, use_mlp != 0)
+                                     : warm_start<float>(c, n_presolve, use_mlp != 0);
 }
 
 int gsis_macro_stats(gsis_ctx *c, int32_t *inner_iters, double *r0, double *rn) {

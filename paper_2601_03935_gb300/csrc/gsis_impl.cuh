@@ -162,6 +162,41 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, const Quad<Real> &
                         Real *f, Real *I, Real *partial, Real *opartial);
 int macro_rpart_count(int n_cells);
 
+// ---- learned closure (mlp.cu)
+constexpr int MLP_IN = 16, MLP_H = 128, MLP_OUT = 12, MLP_LAYERS = 4;
+// parameter blob: W0 b0 W1 b1 W2 b2 W3 b3 (W row-major [out][in]), then the input and
+// target standardisation: x_mean[16] x_std[16] y_mean[12] y_std[12]
+constexpr int MLP_NW = MLP_H * MLP_IN + MLP_H + 2 * (MLP_H * MLP_H + MLP_H) + MLP_OUT * MLP_H + MLP_OUT;
+constexpr int MLP_NSTAT = 2 * MLP_IN + 2 * MLP_OUT;
+constexpr int MLP_NPARAM = MLP_NW + MLP_NSTAT;
+
+struct MlpDev {
+    int cap = 0;                       // rows the work buffers hold
+    float *p = nullptr;                // FP32 master parameters + statistics [MLP_NPARAM]
+    float *g = nullptr, *m1 = nullptr, *m2 = nullptr;   // gradients and Adam moments [MLP_NW]
+    void *pb = nullptr;                // BF16 copy of the weights and biases [MLP_NW]
+    float *act[MLP_LAYERS + 1] = {};   // layer inputs/outputs [cap][width]
+    float *pre[MLP_LAYERS] = {};       // pre-activations [cap][width]
+    float *dA[2] = {nullptr, nullptr}; // back-propagated gradients [cap][MLP_H]
+    float *T = nullptr;                // targets [cap][MLP_OUT]
+    double *lpart = nullptr;           // loss partials
+    int64_t step = 0;                  // Adam step count
+    bool trained = false;
+};
+
+cudaError_t launch_mlp_forward(cudaStream_t s, MlpDev &d, int n);       // act[0] (standardised) -> act[4]
+cudaError_t launch_mlp_loss_backward(cudaStream_t s, MlpDev &d, int n); // needs act/pre of a forward and T
+cudaError_t launch_mlp_adam(cudaStream_t s, MlpDev &d, float lr);
+cudaError_t launch_mlp_to_bf16(cudaStream_t s, MlpDev &d);
+cudaError_t launch_mlp_standardise(cudaStream_t s, int n, int m, float *X, const float *mean, const float *sd,
+                                   int inv);
+int mlp_loss_parts(int n);
+cudaError_t launch_mlp_gather(cudaStream_t s, int n, int width, const int *idx, const float *src, float *dst);
+cudaError_t launch_cell_features(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const double *F,
+                                 const double *q, const double *grad, float *X, float *Y);
+cudaError_t launch_hot_from_cells(cudaStream_t s, const MacroGeom &g, const double *q, const float *Yc,
+                                  double *hot, double *hot_b);
+
 // ---- kernel launchers (kernels.cu); every launcher returns the launch status
 template <typename Real>
 cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, const ModelDev &m,

@@ -29,6 +29,7 @@ GSIS_MODE_GSIS = 1
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
+_fp = C.POINTER(C.c_float)
 
 
 class gsis_patch(C.Structure):
@@ -95,6 +96,14 @@ def load():
         "gsis_step_async": (C.c_int, [vp, C.c_int32]),
         "gsis_solve": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_double, _ip, _dp]),
         "gsis_macro_stats": (C.c_int, [vp, _ip, _dp, _dp]),
+        "gsis_mlp_init": (C.c_int, [vp, C.c_uint64]),
+        "gsis_mlp_set_params": (C.c_int, [vp, _fp, C.c_int64]),
+        "gsis_mlp_get_params": (C.c_int, [vp, _fp, C.c_int64]),
+        "gsis_mlp_samples": (C.c_int, [vp, _fp, _fp, C.c_int64]),
+        "gsis_mlp_train": (C.c_int, [vp, _fp, _fp, C.c_int64, C.c_int32, C.c_int32, C.c_double, C.c_uint64, _dp]),
+        "gsis_mlp_predict": (C.c_int, [vp, _fp, C.c_int64, _fp]),
+        "gsis_mlp_loss_grad": (C.c_int, [vp, _fp, _fp, C.c_int64, _dp, _fp]),
+        "gsis_warm_start": (C.c_int, [vp, C.c_int32, C.c_int32]),
         "gsis_last_eps": (C.c_int, [vp, _dp]),
         "gsis_profile_enable": (C.c_int, [vp, C.c_int32]),
         "gsis_profile_reset": (C.c_int, [vp]),
@@ -233,6 +242,65 @@ def gsis_solve(ctx, mode=GSIS_MODE_GSIS, max_outer=0, tol=0.0, raise_on_max=Fals
     if rc != GSIS_OK and not (rc == GSIS_ERR_NOT_CONVERGED and not raise_on_max):
         _check(rc, ctx)
     return it.value, hist[:it.value].copy()
+
+
+GSIS_MLP_NPARAM = 36804
+GSIS_MLP_NW = 36748
+
+
+def _f(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def gsis_mlp_init(ctx, seed=0):
+    _check(load().gsis_mlp_init(ctx, seed), ctx)
+
+
+def gsis_mlp_set_params(ctx, params):
+    p = _f(params)
+    _check(load().gsis_mlp_set_params(ctx, p.ctypes.data_as(_fp), p.size), ctx)
+
+
+def gsis_mlp_get_params(ctx):
+    p = np.zeros(GSIS_MLP_NPARAM, np.float32)
+    _check(load().gsis_mlp_get_params(ctx, p.ctypes.data_as(_fp), p.size), ctx)
+    return p
+
+
+def gsis_mlp_samples(ctx, n_cells, targets=True):
+    X = np.zeros((n_cells, 16), np.float32)
+    Y = np.zeros((n_cells, 12), np.float32) if targets else None
+    _check(load().gsis_mlp_samples(ctx, X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp) if targets else None,
+                                   n_cells), ctx)
+    return (X, Y) if targets else X
+
+
+def gsis_mlp_train(ctx, X, Y, epochs=10, batch=1024, lr=1e-3, seed=0):
+    X, Y = _f(X), _f(Y)
+    loss = C.c_double(0.0)
+    _check(load().gsis_mlp_train(ctx, X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp), X.shape[0], epochs, batch, lr,
+                                 seed, C.byref(loss)), ctx)
+    return loss.value
+
+
+def gsis_mlp_predict(ctx, X):
+    X = _f(X)
+    Y = np.zeros((X.shape[0], 12), np.float32)
+    _check(load().gsis_mlp_predict(ctx, X.ctypes.data_as(_fp), X.shape[0], Y.ctypes.data_as(_fp)), ctx)
+    return Y
+
+
+def gsis_mlp_loss_grad(ctx, X, Y):
+    X, Y = _f(X), _f(Y)
+    loss = C.c_double(0.0)
+    g = np.zeros(GSIS_MLP_NW, np.float32)
+    _check(load().gsis_mlp_loss_grad(ctx, X.ctypes.data_as(_fp), Y.ctypes.data_as(_fp), X.shape[0], C.byref(loss),
+                                     g.ctypes.data_as(_fp)), ctx)
+    return loss.value, g
+
+
+def gsis_warm_start(ctx, n_presolve=1, use_mlp=False):
+    _check(load().gsis_warm_start(ctx, n_presolve, int(use_mlp)), ctx)
 
 
 def gsis_macro_stats(ctx):
