@@ -35,10 +35,10 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-METRIC = "DVM cell-velocity updates/s"
+METRIC = "DVM cell-velocity updates/s (% HBM roofline); time-to-steady vs plain FP64 GSIS"
 # DRAM bytes (read + write) of one gas sweep on the 20 000-cell cavity, from the ncu capture
 # summarised in profiles/sweep_gas_cavity20k_order2.md; update it whenever the kernels change.
-SWEEP_TRAFFIC = {("fp32", 2): 296.4e6 + 485.2e6 + 877.2e6 + 268.2e6}
+SWEEP_TRAFFIC = {("fp32", 2): 297.0e6 + 485.5e6 + 878.5e6 + 265.5e6}
 UNIT = "updates/s"
 
 
@@ -185,6 +185,78 @@ def run_reference(args):
     return 0
 
 
+def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=150, inner=400,
+                   train_kn=(0.02, 0.05)):
+    """Wall time from a uniform rest state to eps < tol (Section 6 criterion) with GSIS:
+    plain FP64, plain FP32, and FP32 with the learned warm start.  The network is trained
+    on the solver's own samples from runs at other Knudsen numbers; collection and
+    training are timed separately from the solve."""
+    import torch
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import gsis as G
+
+    def make(prec, k):
+        wl = gi.workloads.cavity(n_side=n_side, Kn=k, Kn_p=kn_p)
+        return gi.workloads.with_solver(wl, precision=prec, order=1, relax_block=16, max_inner=inner,
+                                        n_cis_precond=10)
+
+    def fresh(wl):
+        ctx = create_ctx(wl, stream.cuda_stream)
+        f, I = initial_state(wl)
+        G.gsis_set_distributions(ctx, f, I)
+        torch.cuda.synchronize()
+        return ctx
+
+    def run(prec, params=None):
+        wl = make(prec, kn)
+        ctx = fresh(wl)
+        try:
+            t0 = time.perf_counter()
+            tw = 0.0
+            if params is not None:
+                G.gsis_mlp_set_params(ctx, params)
+                G.gsis_warm_start(ctx, 2, use_mlp=True)
+                tw = time.perf_counter() - t0
+            it, hist = G.gsis_solve(ctx, G.GSIS_MODE_GSIS, max_outer, tol)
+            dt = time.perf_counter() - t0
+        finally:
+            G.gsis_destroy(ctx)
+        return {"seconds": dt, "iterations": it, "final_eps": float(hist[-1]) if len(hist) else None,
+                "converged": bool(len(hist) and hist[-1] < tol), "warm_start_seconds": tw}
+
+    out = {"workload": "cavity 2-D, %d triangles (%dx%d), Kn=%g, Kn_p=%g, order 1, %d inner iterations"
+                       % (2 * n_side * n_side, n_side, n_side, kn, kn_p, inner), "tol": tol}
+    out["fp64_plain"] = run("fp64")
+    out["fp32_plain"] = run("fp32")
+    t0 = time.perf_counter()
+    Xs, Ys = [], []
+    for k in train_kn:
+        wl = make("fp32", k)
+        ctx = fresh(wl)
+        try:
+            for j in range(40):
+                G.gsis_step(ctx, G.GSIS_MODE_GSIS if j >= 10 else G.GSIS_MODE_CIS)
+                if j >= 10:
+                    X, Y = G.gsis_mlp_samples(ctx, wl.mesh.n_cells)
+                    Xs.append(X)
+                    Ys.append(Y)
+            if k == train_kn[-1]:
+                collect = time.perf_counter() - t0
+                G.gsis_mlp_init(ctx, 3)
+                t1 = time.perf_counter()
+                loss = G.gsis_mlp_train(ctx, np.concatenate(Xs), np.concatenate(Ys), epochs=40, batch=2048,
+                                        lr=1e-3, seed=4)
+                train = time.perf_counter() - t1
+                params = G.gsis_mlp_get_params(ctx)
+        finally:
+            G.gsis_destroy(ctx)
+    out["fp32_learned"] = run("fp32", params)
+    out["fp32_learned"].update({"train_samples": int(sum(x.shape[0] for x in Xs)), "collect_seconds": collect,
+                                "train_seconds": train, "train_loss": loss, "trained_on_Kn": list(train_kn)})
+    out["speedup_fp32_learned_vs_fp64_plain"] = out["fp64_plain"]["seconds"] / out["fp32_learned"]["seconds"]
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2601_03935_gb300 import build
@@ -295,6 +367,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": nc * (V * 4 + NO) * rs, "d2h_bytes_per_step": nc * G.GSIS_NF * 8},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "last_eps": eps,
     }
+    if not args.no_tts:
+        line["time_to_steady"] = time_to_steady(stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
     print(json.dumps(line))
@@ -316,6 +390,7 @@ def main():
     ap.add_argument("--kn-p", type=float, default=10.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -1312,6 +1312,10 @@ int gsis_mlp_train(gsis_ctx *c, const float *X, const float *Y, int64_t n, int32
                    uint64_t seed, double *loss_out) {
     if (!c || !X || !Y || n <= 0 || epochs < 0 || batch <= 0 || !(lr > 0))
         return fail(c, GSIS_ERR_INVALID_ARG, "bad training arguments");
+    for (int64_t k = 0; k < n * MLP_IN; ++k)
+        if (!std::isfinite(X[k])) return fail(c, GSIS_ERR_INVALID_ARG, "non-finite training input");
+    for (int64_t k = 0; k < n * MLP_OUT; ++k)
+        if (!std::isfinite(Y[k])) return fail(c, GSIS_ERR_INVALID_ARG, "non-finite training target");
     if (!c->mlp.p) TRY(gsis_mlp_init(c, seed));
     const int64_t b = std::min<int64_t>(batch, n);
     TRY(mlp_ensure(c, b));

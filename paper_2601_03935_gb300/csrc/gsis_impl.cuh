@@ -10,7 +10,7 @@ constexpr int MAXF = 4;        // faces per cell (segments, triangles, quads, te
 constexpr int MAXS = 12;       // least-squares stencil: face neighbours and their face neighbours
 constexpr int NF = 26;         // per-cell field record, see gsis.h
 constexpr int SV = 64;         // discrete velocities (or photon directions) per sweep CTA
-constexpr int SROWS = 4;       // thread rows of a sweep CTA (the block's cells are dealt to them)
+constexpr int SROWS = 2;       // thread rows of a sweep CTA (the block's cells are dealt to them)
 constexpr int VCH = SV;        // velocity chunk of the gas moment partials
 constexpr int OCH = SV;        // direction chunk of the photon moment partials
 constexpr int NMP = 20;        // stride of per-(cell, chunk) gas moment partials

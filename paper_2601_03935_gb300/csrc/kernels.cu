@@ -221,10 +221,18 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
             if constexpr (DIM > 1) slope[1].x[p] = fma(c1, dq, slope[1].x[p]);
         }
     }
+    // phi = min(1, min over interior faces of phi_V(Delta_1, Delta_2)).  On the faces with
+    // Delta_2 > 0 (Delta_1 = Delta_max >= 0) phi_V >= 1 while Delta_2 <= Delta_1 / 2 and
+    // phi_V decreases for Delta_2 > Delta_1 / 4, so the minimum is taken at the largest
+    // Delta_2; likewise at the most negative Delta_2 with Delta_min.  Two evaluations per
+    // plane replace one per face.
     const Real eps2 = g.eps2[j];
-    V<Real, N> phi;
+    V<Real, N> hi, lo;
 #pragma unroll
-    for (int p = 0; p < N; ++p) phi.x[p] = Real(1);
+    for (int p = 0; p < N; ++p) {
+        hi.x[p] = Real(0);
+        lo.x[p] = Real(0);
+    }
     const int nf = info.x;
     for (int k = 0; k < nf; ++k) {
         if (g.fnb[j * MAXF + k].x < 0) continue;
@@ -234,12 +242,23 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
         for (int p = 0; p < N; ++p) {
             Real d2 = slope[0].x[p] * dx0;
             if constexpr (DIM > 1) d2 = fma(slope[1].x[p], dx1, d2);
-            const Real d1 = d2 > Real(0) ? dmax.x[p] : dmin.x[p];
-            const Real num = fma(d1, d1 + Real(2) * d2, eps2);
-            const Real den = fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2));
-            const Real pf = d2 != Real(0) ? fdiv(num, den) : Real(1);
-            phi.x[p] = fmin(phi.x[p], pf);
+            hi.x[p] = fmax(hi.x[p], d2);
+            lo.x[p] = fmin(lo.x[p], d2);
         }
+    }
+    V<Real, N> phi;
+#pragma unroll
+    for (int p = 0; p < N; ++p) {
+        Real ph = Real(1);
+        if (hi.x[p] > Real(0)) {
+            const Real d1 = dmax.x[p], d2 = hi.x[p];
+            ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+        }
+        if (lo.x[p] < Real(0)) {
+            const Real d1 = dmin.x[p], d2 = lo.x[p];
+            ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+        }
+        phi.x[p] = ph;
     }
 #pragma unroll
     for (int d = 0; d < DIM; ++d)
@@ -414,7 +433,12 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
         const int nf = g.info[i].x;
         if (tx == 0)
             for (int k = 0; k < MAXF; ++k) Lg[l * MAXF + k] = k < nf ? g.fnb[i * MAXF + k].y : -1;
-        for (int k = 0; k < nf; ++k) {
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            if (k >= nf) {
+                Ag[(l * MAXF + k) * SV + tx] = Real(0);
+                continue;
+            }
             const Face<Real> F = load_face(g.fgeo, i, k);
             const int2 nl = g.fnb[i * MAXF + k];
             Real xn = xi[0] * F.n[0];
