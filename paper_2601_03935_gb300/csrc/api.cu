@@ -50,7 +50,8 @@ struct gsis_ctx {
     int2 *g_fnb = nullptr;
     void *g_fgeo = nullptr, *g_lsq = nullptr, *g_eps2 = nullptr, *bf_nrm = nullptr;
     void *vq_x = nullptr, *vq_w = nullptr, *oq_x = nullptr, *oq_w = nullptr;
-    double *patch_T = nullptr, *patch_u = nullptr;
+    double *patch_T = nullptr, *patch_u = nullptr, *bf_inc = nullptr, *eps_part = nullptr;
+    unsigned int *eps_ticket = nullptr;
     int *patch_kind = nullptr;
     double *h_pinned = nullptr;  // NEPS sums + error word
 
@@ -256,7 +257,7 @@ template <typename Real>
 int kinetic_step(gsis_ctx *c, int nxt) {
     const Geom<Real> g = geom<Real>(c);
     TRY(launch(c, K_WALL, [&] {
-        return launch_wall_density<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_T, c->patch_u, c->patch_kind,
+        return launch_wall_density<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_T, c->bf_inc, c->patch_kind,
                                          (const Real *)c->f[c->cur], (Real *)c->bcoef);
     }));
     if (c->order == 2) {
@@ -294,7 +295,9 @@ int close_iteration(gsis_ctx *c, int nxt) {
                                    (const Real *)c->partial, (const Real *)c->opartial, c->vol, c->fields_old,
                                    c->fields, c->eps_terms, c->err, 1);
     }));
-    TRY(launch(c, K_EPS, [&] { return launch_eps_reduce(c->stream, (int)c->nc, c->eps_terms, c->eps_sums); }));
+    TRY(launch(c, K_EPS, [&] {
+        return launch_eps_reduce(c->stream, (int)c->nc, c->eps_terms, c->eps_part, c->eps_ticket, c->eps_sums);
+    }));
     TRY(launch(c, K_COEF, [&] {
         return launch_coefficients<Real>(c->stream, c->dim, g, c->model, c->fields, c->cell_dx, (Real *)c->coef);
     }));
@@ -907,6 +910,9 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc_real(c, &c->oq_w, ow.size()));
     A_(dalloc(c, &c->patch_T, pT.size()));
     A_(dalloc(c, &c->patch_u, pu.size()));
+    A_(dalloc(c, &c->bf_inc, (size_t)std::max(c->n_bf, 1)));
+    A_(dalloc(c, &c->eps_part, (size_t)64 * NEPS));
+    A_(dalloc(c, &c->eps_ticket, 1));
     A_(dalloc(c, &c->patch_kind, pk.size()));
     if (cudaMallocHost(&c->h_pinned, (NEPS + 1) * sizeof(double)) != cudaSuccess) return bail(GSIS_ERR_OUT_OF_MEMORY);
     if (cudaMallocHost(&c->h_mstate, sizeof(MacroState)) != cudaSuccess) return bail(GSIS_ERR_OUT_OF_MEMORY);
@@ -1023,6 +1029,27 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(upload_real(c, c->bcoef, bco));
     A_(upload(c, c->patch_T, pT));
     A_(upload(c, c->patch_u, pu));
+    {   // incoming mass flux of the unit-density wall Maxwellian at every wall face
+        std::vector<double> inc(std::max(c->n_bf, 1), 0.0);
+        for (int b = 0; b < c->n_bf; ++b) {
+            const gsis_patch &P = m->patches[bf_patch[b]];
+            if (P.kind != GSIS_PATCH_WALL) continue;
+            const double norm = std::pow(2.0 * M_PI * P.T_t, -0.5 * dim);
+            double acc = 0.0;
+            for (int v = 0; v < vq->n; ++v) {
+                double xn = 0.0, c2 = 0.0;
+                for (int a = 0; a < dim; ++a) {
+                    const double x = vq->xi[v * dim + a];
+                    xn += x * bfn[b * 3 + a];
+                    c2 += (x - P.u[a]) * (x - P.u[a]);
+                }
+                if (xn < 0.0) acc += vq->w[v] * xn * norm * std::exp(-c2 / (2.0 * P.T_t));
+            }
+            inc[b] = acc;
+        }
+        A_(upload(c, c->bf_inc, inc));
+    }
+    if (cudaMemset(c->eps_ticket, 0, sizeof(unsigned int)) != cudaSuccess) return bail(GSIS_ERR_CUDA);
     A_(upload(c, c->patch_kind, pk));
     if (cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess) return bail(GSIS_ERR_CUDA);
     if (cudaMemset(c->coef, 0, (size_t)nc * cf::NC * c->real_size) != cudaSuccess) return bail(GSIS_ERR_CUDA);

@@ -202,8 +202,10 @@ template <typename Real>
 cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, const ModelDev &m,
                                 const double *fields, const double *cell_dx, Real *coef);
 template <typename Real>
+// bf_inc: per boundary face, sum over incoming velocities of w xi.n times the unit-density
+// wall Maxwellian (constant; built at creation)
 cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
-                                const double *patch_T, const double *patch_u, const int *patch_kind,
+                                const double *patch_T, const double *bf_inc, const int *patch_kind,
                                 const Real *f, Real *bcoef);
 template <typename Real>
 cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, int n_pad, const Real *f,
@@ -222,7 +224,8 @@ cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, in
                           const Real *coef, const Real *partial, const Real *opartial, const double *vol,
                           const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
                           int have_old);
-cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_sums);
+cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_part,
+                              unsigned int *ticket, double *eps_sums);
 template <typename Real>
 cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
                                const ModelDev &m, const double *fields, Real *f, Real *I);

@@ -107,39 +107,29 @@ __global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restric
 // One warp per boundary face; far-field records are constant and left untouched.
 template <typename Real, int DIM>
 __global__ void k_wall_density(Geom<Real> g, Quad<Real> vq, const double *__restrict__ patch_T,
-                               const double *__restrict__ patch_u, const int *__restrict__ patch_kind,
+                               const double *__restrict__ bf_inc, const int *__restrict__ patch_kind,
                                const Real *__restrict__ f, Real *__restrict__ bcoef) {
+    // one warp per boundary face: the outgoing mass flux of the current f; the incoming
+    // flux of the unit-density wall Maxwellian is a per-face constant (bf_inc)
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= g.n_bf) return;
     const int p = g.bf_patch[warp];
     if (patch_kind[p] != 0) return;
     const int cell = g.bf_cell[warp];
-    const double Tw = patch_T[p];
-    double n[3], uw[3];
-    for (int a = 0; a < 3; ++a) {
-        n[a] = (double)g.bf_nrm[warp * 3 + a];
-        uw[a] = patch_u[p * 3 + a];
-    }
-    const double norm = pow(6.283185307179586 * Tw, -0.5 * DIM);
-    double out = 0.0, inc = 0.0;
+    Real n[DIM];
+    for (int a = 0; a < DIM; ++a) n[a] = g.bf_nrm[warp * 3 + a];
+    double out = 0.0;
     for (int v = lane; v < vq.n_pad; v += 32) {
-        double xn = 0.0, c2 = 0.0;
-        for (int a = 0; a < DIM; ++a) {
-            const double x = (double)vq.x[a * vq.n_pad + v];
-            xn += x * n[a];
-            c2 += (x - uw[a]) * (x - uw[a]);
-        }
-        const double w = (double)vq.w[v];
-        if (xn > 0.0) out += w * xn * (double)f[((size_t)cell * vq.n_pad + v) * 4];
-        else if (xn < 0.0) inc += w * xn * norm * exp(-c2 / (2.0 * Tw));
+        Real xn = Real(0);
+        for (int a = 0; a < DIM; ++a) xn += vq.x[a * vq.n_pad + v] * n[a];
+        if (xn > Real(0)) out += (double)(vq.w[v] * xn) * (double)f[((size_t)cell * vq.n_pad + v) * 4];
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        out += __shfl_xor_sync(0xffffffffu, out, o);
-        inc += __shfl_xor_sync(0xffffffffu, inc, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
     if (lane == 0) {
+        const double inc = bf_inc[warp];
         const double rho_w = inc < 0.0 ? -out / inc : 0.0;
+        const double norm = pow(6.283185307179586 * patch_T[p], -0.5 * DIM);
         bcoef[(size_t)warp * bc::NB + bc::A] = (Real)(rho_w * norm);
     }
 }
@@ -1002,11 +992,20 @@ __global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, co
     }
 }
 
-__global__ void k_eps_reduce(int n_cells, const double *__restrict__ terms, double *__restrict__ sums) {
+// Per-CTA partial sums of contiguous cell ranges; the last CTA to finish (counted with an
+// atomic ticket after a fence, no waiting) adds the partials in CTA order, so the result
+// does not depend on scheduling.
+constexpr int EPS_CTAS = 64;
+__global__ void __launch_bounds__(256) k_eps_reduce(int n_cells, const double *__restrict__ terms,
+                                                    double *__restrict__ part, unsigned int *__restrict__ ticket,
+                                                    double *__restrict__ sums) {
     __shared__ double sh[NEPS][256];
+    __shared__ bool last;
+    const int per = (n_cells + EPS_CTAS - 1) / EPS_CTAS;
+    const int i0 = blockIdx.x * per, i1 = min(n_cells, i0 + per);
     double acc[NEPS];
     for (int q = 0; q < NEPS; ++q) acc[q] = 0.0;
-    for (int i = threadIdx.x; i < n_cells; i += blockDim.x)
+    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
         for (int q = 0; q < NEPS; ++q) acc[q] += terms[(size_t)i * NEPS + q];
     for (int q = 0; q < NEPS; ++q) sh[q][threadIdx.x] = acc[q];
     __syncthreads();
@@ -1015,8 +1014,20 @@ __global__ void k_eps_reduce(int n_cells, const double *__restrict__ terms, doub
             for (int q = 0; q < NEPS; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0)
-        for (int q = 0; q < NEPS; ++q) sums[q] = sh[q][0];
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NEPS; ++q) part[blockIdx.x * NEPS + q] = sh[q][0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < NEPS) {
+        double s = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double *)part)[b * NEPS + threadIdx.x];
+        sums[threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // ------------------------------------------------------------------ equilibrium
@@ -1056,18 +1067,18 @@ __global__ void k_equilibrium(int n_cells, Quad<Real> vq, Quad<Real> oq, ModelDe
 template <typename Real>
 cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, const ModelDev &m, const double *fields,
                                 const double *cell_dx, Real *coef) {
-    const int nt = 128, nbk = (g.n_cells + nt - 1) / nt;
+    const int nt = 32, nbk = (g.n_cells + nt - 1) / nt;   // small CTAs spread the FP64 work over SMs
     GSIS_DISPATCH_DIM(dim, (k_coefficients<Real, DIM><<<nbk, nt, 0, s>>>(g, m, fields, cell_dx, coef)));
     return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
-                                const double *patch_T, const double *patch_u, const int *patch_kind, const Real *f,
+                                const double *patch_T, const double *bf_inc, const int *patch_kind, const Real *f,
                                 Real *bcoef) {
     if (g.n_bf == 0) return cudaSuccess;
-    const int nt = 256, nbk = (g.n_bf * 32 + nt - 1) / nt;
-    GSIS_DISPATCH_DIM(dim, (k_wall_density<Real, DIM><<<nbk, nt, 0, s>>>(g, vq, patch_T, patch_u, patch_kind, f, bcoef)));
+    const int nt = 64, nbk = (g.n_bf * 32 + nt - 1) / nt;
+    GSIS_DISPATCH_DIM(dim, (k_wall_density<Real, DIM><<<nbk, nt, 0, s>>>(g, vq, patch_T, bf_inc, patch_kind, f, bcoef)));
     return cudaGetLastError();
 }
 
@@ -1135,15 +1146,16 @@ cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, in
                           const Real *coef, const Real *partial, const Real *opartial, const double *vol,
                           const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
                           int have_old) {
-    const int nt = 128, nbk = (n_cells + nt - 1) / nt;
+    const int nt = 32, nbk = (n_cells + nt - 1) / nt;
     GSIS_DISPATCH_DIM(dim, (k_finish<Real, DIM><<<nbk, nt, 0, s>>>(n_cells, n_chunks, o_chunks, m, coef, partial,
                                                                     opartial, vol, fields_old, fields_new, eps_terms,
                                                                     err_flag, have_old)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_sums) {
-    k_eps_reduce<<<1, 256, 0, s>>>(n_cells, eps_terms, eps_sums);
+cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_part,
+                              unsigned int *ticket, double *eps_sums) {
+    k_eps_reduce<<<EPS_CTAS, 256, 0, s>>>(n_cells, eps_terms, eps_part, ticket, eps_sums);
     return cudaGetLastError();
 }
 
