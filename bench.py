@@ -45,14 +45,15 @@ UNIT = "updates/s"
 def workload(args):
     import gsis_inputs as gi
     wl = gi.workloads.cavity(n_side=100, Kn=args.kn, Kn_p=args.kn_p)
-    return gi.workloads.with_solver(wl, precision=args.precision, order=args.order, relax_block=args.block)
+    return gi.workloads.with_solver(wl, precision=args.precision, order=args.order, relax_block=args.block,
+                                    tc_moments=args.tc_moments)
 
 
 def config(args, wl):
     return {"workload": "cavity 2-D, %d triangles, 28x28 closed Newton-Cotes (trapezoid) velocities (%d), %d photon directions"
                         % (wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]),
             "n_cells": wl.mesh.n_cells, "n_xi": int(wl.xi.shape[0]), "n_omega": int(wl.omega.shape[0]),
-            "order": args.order, "relax_block": args.block, "Kn": args.kn, "Kn_photon": args.kn_p,
+            "order": args.order, "relax_block": args.block, "tc_moments": args.tc_moments, "Kn": args.kn, "Kn_photon": args.kn_p,
             "step": "one CIS outer iteration (kinetic sweep + moments + fields + epsilon)",
             "l2": "inputs larger than L2 (f: 2 x %.0f MB)" % (wl.mesh.n_cells * 896 * 16 / 1e6),
             "parallelism": "replicas" if args.gpus > 1 else "1 GPU"}
@@ -386,6 +387,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--tc-moments", type=int, default=1, choices=[0, 1, 2],
+                    help="FP32 gas moments: 0 CUDA cores, 1 tensor cores in the standalone and sync passes, "
+                         "2 also in the sweep epilogue")
     ap.add_argument("--kn", type=float, default=0.01)
     ap.add_argument("--kn-p", type=float, default=10.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

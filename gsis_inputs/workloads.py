@@ -45,6 +45,8 @@ class SolverParams:
     tol_inner: float = 1e-7
     sync_relax: float = 1.0              # weight of the equilibrium correction in the synchronisation
     macro_fp32: int = 0                  # library FP32 path: synthetic residual side in FP32
+    tc_moments: int = 1                  # library FP32 path: 0 CUDA cores, 1 tensor cores in the moment/sync
+                                         # passes, 2 also in the sweep epilogue
 
 
 @dataclass

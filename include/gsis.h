@@ -129,6 +129,13 @@ typedef struct {
                                    equations' residual side (gradients, fluxes, high-order
                                    terms, D) in FP32; the relaxation sweeps and norms stay
                                    FP64.  0 (default): all FP64.                             */
+    int32_t tc_moments;         /* GSIS_FP32 contexts only: where the gas velocity moments
+                                   (Eq. getmoment) are contracted.  0: CUDA cores;
+                                   1: tensor cores (split-TF32 tcgen05) in the standalone and
+                                   synchronisation passes, CUDA cores in the sweep epilogue;
+                                   2: tensor cores in the sweep epilogue too (relaxation
+                                   blocks that divide 16 cells; other blocks keep the
+                                   CUDA-core epilogue).  FP64 contexts ignore it.            */
 } gsis_solver_params;
 
 typedef struct gsis_ctx gsis_ctx;

@@ -65,6 +65,7 @@ struct gsis_ctx {
     float *mlp_data = nullptr;   // training data on the device
     int64_t mlp_data_cap = 0;
     int mfp32 = 0;               // FP32 path: residual side of the synthetic equations in FP32
+    int tcm = 0;                 // FP32 path: gas moments on tensor cores (1: standalone passes, 2: also the sweep)
     int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
     double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
            *m_fi_xf = nullptr, *m_lsq = nullptr, *m_eps2 = nullptr, *m_xc = nullptr, *m_bf_n = nullptr,
@@ -149,6 +150,7 @@ Geom<Real> geom(const gsis_ctx *c) {
     g.n_cells = (int)c->nc;
     g.dim = c->dim;
     g.block = c->block;
+    g.tc = c->tcm >= 2 && MT % c->block == 0;
     g.info = c->g_info;
     g.fnb = c->g_fnb;
     g.fgeo = (const Real *)c->g_fgeo;
@@ -232,7 +234,7 @@ int refresh_fields(gsis_ctx *c) {
     CUDA_TRY(c, cudaMemsetAsync(c->coef, 0, (size_t)c->nc * cf::NC * c->real_size, c->stream));
     for (int pass = 0; pass < 2; ++pass) {
         TRY(launch(c, K_MOMENTS, [&] {
-            return launch_moments_only<Real>(c->stream, c->dim, (int)c->nc, vquad<Real>(c), oquad<Real>(c),
+            return launch_moments_only<Real>(c->stream, c->dim, (int)c->nc, c->tcm >= 1, vquad<Real>(c), oquad<Real>(c),
                                              (const Real *)c->coef, (const Real *)c->f[c->cur],
                                              (const Real *)c->I[c->cur], (Real *)c->partial, (Real *)c->opartial);
         }));
@@ -470,7 +472,7 @@ int gsis_iteration(gsis_ctx *c) {
         return launch_macro_fields_from_W(c->stream, c->dim, (int)c->nc, c->model, c->W[w], c->fields_n);
     }));
     TRY(launch(c, K_SYNC, [&] {
-        return launch_sync<Real>(c->stream, c->dim, (int)c->nc, vquad<Real>(c), oquad<Real>(c), c->model,
+        return launch_sync<Real>(c->stream, c->dim, (int)c->nc, c->tcm >= 1, vquad<Real>(c), oquad<Real>(c), c->model,
                                  c->solver.sync_relax, c->fields_n, c->fields_h, (const Real *)c->coef,
                                  (Real *)c->f[nxt], (Real *)c->I[nxt], (Real *)c->partial, (Real *)c->opartial);
     }));
@@ -512,13 +514,15 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
     if (sp->relax_block < 1 || sp->relax_block > MAXB) return why = "relax_block must be in 1..64", GSIS_ERR_INVALID_ARG;
     {   // the gas sweep keeps a block's residuals and diagonals in shared memory
         const size_t rs = sp->precision == GSIS_FP64 ? 8 : 4;
-        if (sweep_smem_bytes(sp->relax_block, 4, 2, rs) > 227 * 1024)
+        const bool tc = rs == 4 && sp->tc_moments >= 2 && MT % sp->relax_block == 0;
+        if (sweep_smem_bytes(sp->relax_block, 4, 2, rs, tc) > 227 * 1024)
             return why = "relax_block too large for the shared memory of one CTA", GSIS_ERR_INVALID_ARG;
     }
     if (!(sp->cfl_meso > 0) || !(sp->venkat_K > 0)) return why = "bad CFL or limiter constant", GSIS_ERR_INVALID_ARG;
     if (!(sp->cfl_macro > 0) || sp->max_inner < 1 || sp->macro_sweeps < 1 || !(sp->tol_inner >= 0))
         return why = "bad synthetic-equation parameters", GSIS_ERR_INVALID_ARG;
     if (!(sp->sync_relax > 0) || !(sp->sync_relax <= 1)) return why = "sync_relax must be in (0, 1]", GSIS_ERR_INVALID_ARG;
+    if (sp->tc_moments < 0 || sp->tc_moments > 2) return why = "tc_moments must be 0, 1 or 2", GSIS_ERR_INVALID_ARG;
     if (!(mp->Kn > 0) || !(mp->Kn_p > 0) || !(mp->sigma_R >= 0) || !(mp->Z_r > 0) || !(mp->Z_v > 0) ||
         !(mp->d_r >= 0) || !(mp->d_v > 0) || !(mp->d_r > 0))
         return why = "bad model parameters", GSIS_ERR_INVALID_ARG;
@@ -615,6 +619,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     c->precision = sp->precision;
     c->real_size = sp->precision == GSIS_FP64 ? 8 : 4;
     c->mfp32 = sp->precision == GSIS_FP32 && sp->macro_fp32 != 0;
+    c->tcm = sp->precision == GSIS_FP32 ? sp->tc_moments : 0;
     c->order = sp->order;
     c->block = sp->relax_block;
     c->solver = *sp;

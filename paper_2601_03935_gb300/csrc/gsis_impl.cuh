@@ -16,6 +16,8 @@ constexpr int OCH = SV;        // direction chunk of the photon moment partials
 constexpr int NMP = 20;        // stride of per-(cell, chunk) gas moment partials
 constexpr int NMO = 4;         // stride of per-(cell, chunk) photon moment partials
 constexpr int MAXB = 64;       // largest relaxation block
+constexpr int MT = 16;         // moment tile: gas moments are taken about the velocity of the
+                               // tile's first cell (cells MT*t .. MT*t + MT - 1 share it)
 constexpr int NEPS = 8;        // per-cell terms of the convergence measure
 
 // ---- per-cell coefficient record (Real), built from the FP64 fields each iteration,
@@ -56,6 +58,7 @@ constexpr int NX = 0, NY = 1, SV = 2, SVN = 3, DFX = 4, DFY = 5, DNX = 6, DNY = 
 template <typename Real>
 struct Geom {
     int n_cells, dim, block;
+    int tc;                    // FP32 gas sweep: moments on the tensor cores (block divides MT)
     const int4 *info;          // [nc]: faces, stencil size, face neighbours leading the stencil, -
     const int2 *fnb;           // [nc][MAXF]: neighbour (>= 0 cell, < 0: -1 - boundary face), in-block index or -1
     const Real *fgeo;          // [nc][MAXF][fr::SIZE]
@@ -157,7 +160,7 @@ template <typename Real>
 cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const Quad<Real> &vq,
                                  const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux);
 template <typename Real>
-cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                         const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
                         Real *f, Real *I, Real *partial, Real *opartial);
 int macro_rpart_count(int n_cells);
@@ -210,7 +213,7 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
 template <typename Real>
 cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, int n_pad, const Real *f,
                           Real *slope);
-size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size);
+size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size, bool tc);
 template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
                              const Real *coef, const Real *bcoef, const Real *f_in, const Real *slope,
@@ -230,7 +233,7 @@ template <typename Real>
 cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
                                const ModelDev &m, const double *fields, Real *f, Real *I);
 template <typename Real>
-cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                                 const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial);
 
 }  // namespace gsis

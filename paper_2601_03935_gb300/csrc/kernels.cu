@@ -16,10 +16,18 @@
 //  eps_reduce     deterministic single-CTA reduction of those terms
 //  equilibrium    multi-temperature local equilibrium of given fields
 //  moments_only   velocity moments of the current distributions
+//
+// Gas moments are taken about a shift velocity u0 per moment tile of MT consecutive
+// cells (the velocity field of the tile's first cell), so that one tile shares one
+// polynomial basis.  In FP32 the contraction over velocities can run on the tensor cores
+// (tc_moments.cuh): in the standalone and synchronisation passes, and in the sweep's
+// epilogue when a relaxation block lies inside one tile.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 
 #include "gsis_impl.cuh"
+#include "tc_moments.cuh"
 
 namespace gsis {
 
@@ -355,6 +363,16 @@ __global__ void __launch_bounds__(SV * 4) k_slopes(Geom<Real> g, int n_pad, cons
 }
 
 // ------------------------------------------------------------------ the sweep
+// Shared memory of a sweep CTA: the main area (residuals, diagonals, in-block inflow
+// coefficients; with `tc`, at least the tensor-core operand stage, which reuses it after
+// the relaxation), then the chunk's velocities and weights, the in-block neighbour table
+// and the tensor-core control words.  `tc`: an FP32 gas sweep with Geom::tc set.
+__host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, size_t real_size, bool tc) {
+    return (tc && (size_t)block * SV * (planes + 1 + MAXF) * real_size < (size_t)tcm::STAGE_BYTES)
+               ? (size_t)tcm::STAGE_BYTES
+               : (size_t)block * SV * (planes + 1 + MAXF) * real_size;
+}
+
 // One CTA = one relaxation block of consecutive cells x SV discrete velocities (N = 4 gas
 // planes) or photon directions (N = 1); thread (tx, ty) = (velocity, row), and the
 // block's cells are dealt to the SROWS rows round-robin.
@@ -375,8 +393,11 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][SV]
     Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] diagonal
     Real *Ag = Dg + g.block * SV;                                       // [block][MAXF][SV] S/V xi_n, in-block inflow
-    Real *sxi = Ag + g.block * MAXF * SV;                               // [DIM+1][SV]
-    int *Lg = reinterpret_cast<int *>(sxi + (DIM + 1) * SV);            // [block][MAXF] in-block neighbour or -1
+    constexpr bool TCM = std::is_same<Real, float>::value && N == 4;
+    const bool tc = TCM && g.tc;
+    Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, sizeof(Real), tc));   // [DIM+1][SV]
+    signed char *Lg = reinterpret_cast<signed char *>(sxi + (DIM + 1) * SV);   // [block][MAXF] in-block neighbour or -1
+    tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(Lg + ((g.block * MAXF + 15) & ~15));
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int c0 = blockIdx.x * g.block;
     const int nb = min(g.block, g.n_cells - c0);
@@ -391,6 +412,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
         for (int a = 0; a < DIM; ++a) sxi[a * SV + tx] = xi[a];
         sxi[DIM * SV + tx] = q.w[v];
     }
+    if (tc) tcm::start(ctl, ty * SV + tx);   // the allocation completes during phase 1
     auto slope_at = [&](int c, V<Real, N> (&s)[DIM]) {
         const size_t idx = (size_t)c * stride + v;
 #pragma unroll
@@ -422,7 +444,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
         if constexpr (ORDER == 2) slope_at(i, si);
         const int nf = g.info[i].x;
         if (tx == 0)
-            for (int k = 0; k < MAXF; ++k) Lg[l * MAXF + k] = k < nf ? g.fnb[i * MAXF + k].y : -1;
+            for (int k = 0; k < MAXF; ++k) Lg[l * MAXF + k] = (signed char)(k < nf ? g.fnb[i * MAXF + k].y : -1);
 #pragma unroll
         for (int k = 0; k < MAXF; ++k) {
             if (k >= nf) {
@@ -534,7 +556,60 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     }
     __syncthreads();
 
-    // ---- 3. f^{k+1/2} = f^k + delta, staged for the moments
+    // ---- 3. f^{k+1/2} = f^k + delta
+    if constexpr (TCM) {
+        if (tc) {
+            // Tensor-core moments: the tile's operand stage overlays R, the dead diagonal
+            // and inflow areas and B; f^{k+1/2} waits in registers until every R read is done.
+            unsigned char *stage = smem_raw;
+            const int tile = c0 / MT * MT, lt0 = c0 - tile;
+            constexpr int PER = MT / SROWS;
+            Vec<float, 4> th[PER];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int l = ty + j * SROWS;
+                if (l < nb) {
+                    const size_t idx = (size_t)(c0 + l) * stride + v;
+                    const Vec<float, 4> fo = vload<float, 4>(reinterpret_cast<const float *>(f_in) + idx * 4);
+                    Vec<float, 4> t = *reinterpret_cast<const Vec<float, 4> *>(&R[l * SV + tx]);
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) t.v[p] += fo.v[p];
+                    vstore<float, 4>(reinterpret_cast<float *>(f_out) + idx * 4, t);
+                    th[j] = t;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int l = ty + j * SROWS;
+                if (l < nb) tcm::put_a4(stage, lt0 + l, tx, th[j].v);
+            }
+            if (ty == 0) {
+                const Vec<float, 4> u4 =
+                    vload<float, 4>(reinterpret_cast<const float *>(coef) + (size_t)tile * cf::NC + cf::U);
+                float c[DIM];
+#pragma unroll
+                for (int a = 0; a < DIM; ++a) c[a] = (float)sxi[a * SV + tx] - u4.v[a];
+                tcm::put_b<DIM>(stage, tx, c, (float)sxi[DIM * SV + tx]);
+            }
+            tcm::fence_smem_to_async();
+            __syncthreads();
+            // ---- 4. moments: one M = 128, N = 16, K = 64 contraction per CTA
+            const int tid = ty * SV + tx;
+            const uint32_t taddr = tcm::accumulator(ctl);
+            float m[tcm::NBASIS];
+            bool ok;
+            if (tcm::contract(ctl, taddr, stage, tid, m, ok)) {
+                const int l = (tid & 15) - lt0;
+                if (l >= 0 && l < nb)
+                    tcm::store_row<DIM>(reinterpret_cast<float *>(partial) +
+                                            ((size_t)(c0 + l) * gridDim.y + chunk) * NMP,
+                                        tid >> 5, m);
+            }
+            tcm::end(ctl, taddr, tid, ok);
+            return;
+        }
+    }
     for (int l = ty; l < nb; l += SROWS) {
         const size_t idx = (size_t)(c0 + l) * stride + v;
         V<Real, N> fo = ldv<Real, N>(f_in, idx);
@@ -550,7 +625,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     }
     __syncthreads();
 
-    // ---- 4. moments of the new distribution, eight lanes per cell
+    // ---- 4. moments of the new distribution on CUDA cores, eight lanes per cell
     constexpr int TPC = 8;
     const int tid = ty * SV + tx;
     const int sub = tid % TPC;
@@ -577,7 +652,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
             }
         } else {
             constexpr int NM = n_gas_moments<DIM>();
-            const Vec<Real, 4> u4 = vload<Real, 4>(coef + (size_t)(c0 + l) * cf::NC + cf::U);
+            const Vec<Real, 4> u4 = vload<Real, 4>(coef + (size_t)((c0 + l) / MT * MT) * cf::NC + cf::U);
             Real acc[NMP];
 #pragma unroll
             for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
@@ -612,7 +687,7 @@ __global__ void __launch_bounds__(VCH) k_moments_gas(int n_cells, Quad<Real> vq,
     const int chunk = blockIdx.y;
     if (i >= n_cells) return;
     constexpr int NM = n_gas_moments<DIM>();
-    const Real *C = coef + (size_t)i * cf::NC;
+    const Real *C = coef + (size_t)(i / MT * MT) * cf::NC;   // the tile's shift velocity
     Real acc[NMP];
 #pragma unroll
     for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
@@ -703,7 +778,7 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
     }
     const Real w = (Real)om;
     constexpr int NM = n_gas_moments<DIM>();
-    const Real *C = coef + (size_t)i * cf::NC;
+    const Real *C = coef + (size_t)(i / MT * MT) * cf::NC;   // the tile's shift velocity
     Real acc[NMP];
 #pragma unroll
     for (int k = 0; k < NMP; ++k) acc[k] = Real(0);
@@ -745,6 +820,134 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
 #pragma unroll
         for (int k = 0; k < NM; ++k) P[k] = acc[k];
     }
+}
+
+// ------------------------------------------------------------------ FP32 moments on tensor cores
+// One CTA of 128 threads per (moment tile of MT cells, chunk of 64 velocities): thread
+// (v = tid % 64, half = tid / 64) holds the tile's cells 8 * half .. 8 * half + 7 at
+// velocity v, and the contraction of tc_moments.cuh gives the partials.  Rows of cells
+// beyond n_cells are zero.
+template <int DIM>
+__device__ __forceinline__ void tc_tile_moments(unsigned char *smem, int tid, int tile, int chunk, int n_cells,
+                                                const Quad<float> &vq, const float *coef,
+                                                const Vec<float, 4> (&fv)[MT / 2], float *partial) {
+    unsigned char *stage = smem;
+    tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(smem + tcm::STAGE_BYTES);
+    const int v = tid & 63, half = tid >> 6;
+#pragma unroll
+    for (int j = 0; j < MT / 2; ++j) tcm::put_a4(stage, half * (MT / 2) + j, v, fv[j].v);
+    if (half == 0) {
+        const int vg = chunk * tcm::K + v;
+        const Vec<float, 4> u4 = vload<float, 4>(coef + (size_t)tile * cf::NC + cf::U);
+        float c[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) c[a] = vq.x[a * vq.n_pad + vg] - u4.v[a];
+        tcm::put_b<DIM>(stage, v, c, vq.w[vg]);
+    }
+    tcm::fence_smem_to_async();
+    __syncthreads();
+    const uint32_t taddr = tcm::accumulator(ctl);
+    float m[tcm::NBASIS];
+    bool ok;
+    if (tcm::contract(ctl, taddr, stage, tid, m, ok)) {
+        const int i = tile + (tid & 15);
+        if (i < n_cells) tcm::store_row<DIM>(partial + ((size_t)i * gridDim.y + chunk) * NMP, tid >> 5, m);
+    }
+    tcm::end(ctl, taddr, tid, ok);
+}
+
+constexpr int TC_SMEM = tcm::STAGE_BYTES + (int)sizeof(tcm::Ctl);
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_moments_gas_tc(int n_cells, Quad<float> vq, const float *__restrict__ coef,
+                                                        const float *__restrict__ f, float *__restrict__ partial) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    const int tid = threadIdx.x, v = tid & 63, half = tid >> 6;
+    const int tile = blockIdx.x * MT, chunk = blockIdx.y;
+    tcm::start(reinterpret_cast<tcm::Ctl *>(tc_smem + tcm::STAGE_BYTES), tid);
+    Vec<float, 4> fv[MT / 2];
+#pragma unroll
+    for (int j = 0; j < MT / 2; ++j) {
+        const int i = tile + half * (MT / 2) + j;
+        fv[j] = i < n_cells ? vload<float, 4>(f + ((size_t)i * vq.n_pad + chunk * tcm::K + v) * 4) : Vec<float, 4>{};
+    }
+    tc_tile_moments<DIM>(tc_smem, tid, tile, chunk, n_cells, vq, coef, fv, partial);
+}
+
+// The synchronisation of k_sync_gas for a moment tile, then its moments on the tensor
+// cores.  The per-cell constants (FP64 differences rounded once) are formed by 16 threads.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_sync_gas_tc(int n_cells, Quad<float> vq, ModelDev m, double om,
+                                                     const double *__restrict__ Fn, const double *__restrict__ Fh,
+                                                     const float *__restrict__ coef, float *__restrict__ f,
+                                                     float *__restrict__ partial) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    constexpr int MH = 3 - DIM;
+    constexpr int NK = 6 + 3 * DIM + 8;     // An, dA, Ah, Bn, Bh, dB, uh, du, su, mul_n[4], dmul[4]
+    float *kc = reinterpret_cast<float *>(tc_smem + TC_SMEM);   // [MT][NK]
+    const int tid = threadIdx.x, v = tid & 63, half = tid >> 6;
+    const int tile = blockIdx.x * MT, chunk = blockIdx.y;
+    tcm::start(reinterpret_cast<tcm::Ctl *>(tc_smem + tcm::STAGE_BYTES), tid);
+    if (tid < MT && tile + tid < n_cells) {
+        const int i = tile + tid;
+        const double *rn = Fn + (size_t)i * NF, *rh = Fh + (size_t)i * NF;
+        const double An = rn[0] * pow(2.0 * 3.14159265358979323846 * rn[4], -0.5 * DIM);
+        const double Ah = rh[0] * pow(2.0 * 3.14159265358979323846 * rh[4], -0.5 * DIM);
+        const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
+        const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
+        const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
+        float *Kc = kc + tid * NK;
+        Kc[0] = (float)An;
+        Kc[1] = (float)(An - Ah);
+        Kc[2] = (float)Ah;
+        Kc[3] = (float)Bn;
+        Kc[4] = (float)Bh;
+        Kc[5] = (float)(Bn - Bh);
+        for (int a = 0; a < DIM; ++a) {
+            Kc[6 + a] = (float)rh[1 + a];
+            Kc[6 + DIM + a] = (float)(rh[1 + a] - rn[1 + a]);
+            Kc[6 + 2 * DIM + a] = (float)(rh[1 + a] + rn[1 + a]);
+        }
+        for (int p = 0; p < 4; ++p) {
+            Kc[6 + 3 * DIM + p] = (float)mn[p];
+            Kc[10 + 3 * DIM + p] = (float)(mn[p] - mh[p]);
+        }
+    }
+    __syncthreads();
+    const int vg = chunk * tcm::K + v;
+    float xi[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) xi[a] = vq.x[a * vq.n_pad + vg];
+    const float w = (float)om;
+    Vec<float, 4> fv[MT / 2];
+#pragma unroll
+    for (int j = 0; j < MT / 2; ++j) {
+        const int i = tile + half * (MT / 2) + j;
+        fv[j] = i < n_cells ? vload<float, 4>(f + ((size_t)i * vq.n_pad + vg) * 4) : Vec<float, 4>{};
+    }
+#pragma unroll
+    for (int j = 0; j < MT / 2; ++j) {
+        const int l = half * (MT / 2) + j, i = tile + l;
+        if (i < n_cells && vg < vq.n) {
+            // E_h [A_n expm1(-delta) + (A_n - A_h)], delta = B_n c_n^2 - B_h c_h^2, as in k_sync_gas
+            const float *Kc = kc + l * NK;
+            float c2h = 0.f, dc2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                const float ch = xi[a] - Kc[6 + a];
+                c2h += ch * ch;
+                dc2 += Kc[6 + DIM + a] * (2.f * xi[a] - Kc[6 + 2 * DIM + a]);
+            }
+            const float Eh = fexp(-Kc[4] * c2h);
+            const float delta = Kc[3] * dc2 + Kc[5] * c2h;
+            const float d0 = Eh * (Kc[0] * expm1_r(-delta) + Kc[1]);
+            const float e0h = Kc[2] * Eh;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) fv[j].v[p] += w * (Kc[6 + 3 * DIM + p] * d0 + Kc[10 + 3 * DIM + p] * e0h);
+            vstore<float, 4>(f + ((size_t)i * vq.n_pad + vg) * 4, fv[j]);
+        }
+    }
+    tc_tile_moments<DIM>(tc_smem, tid, tile, chunk, n_cells, vq, coef, fv, partial);
 }
 
 template <typename Real, int DIM>
@@ -861,7 +1064,8 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
 }
 
 // ------------------------------------------------------------------ finish (FP64)
-// Shifted moments S about the coefficient velocity u0 (the shift the sweep used):
+// Shifted moments S about the moment tile's velocity u0 (the velocity field of the
+// tile's first cell, the shift every gas moment pass uses):
 // with delta = S_c / rho the flow velocity is u0 + delta and every central moment
 // follows from the binomial shift by delta.
 template <typename Real, int DIM>
@@ -924,7 +1128,7 @@ __global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, co
     const double int_c2 = trP + H0;                       // int c^2 f0 over all velocity components
     double *Fn = F_new + (size_t)i * NF;
     for (int q = 0; q < NF; ++q) Fn[q] = 0.0;
-    const Real *C = coef + (size_t)i * cf::NC;
+    const Real *C = coef + (size_t)(i / MT * MT) * cf::NC;   // the tile's shift velocity
     Fn[0] = rho;
     for (int a = 0; a < DIM; ++a) Fn[1 + a] = (double)C[cf::U + a] + dl[a];
     const double Tt = int_c2 / (3.0 * rho);
@@ -1100,15 +1304,17 @@ cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> 
     return cudaErrorInvalidValue;
 }
 
-size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size) {
-    return (size_t)block * SV * (planes + 1 + MAXF) * real_size + (size_t)(dim + 1) * SV * real_size +
-           (size_t)block * MAXF * sizeof(int);
+size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size, bool tc) {
+    return sweep_main_bytes(block, planes, real_size, tc) + (size_t)(dim + 1) * SV * real_size +
+           (size_t)((block * MAXF + 15) & ~15) + (tc ? sizeof(tcm::Ctl) : 0);
 }
 
 template <typename Real, int N, int DIM, int ORDER>
 static cudaError_t sweep_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *coef,
                            const Real *bcoef, const Real *f_in, const Real *slope, Real *f_out, Real *partial) {
-    const size_t smem = sweep_smem_bytes(g.block, N, DIM, sizeof(Real));
+    const bool tc = N == 4 && sizeof(Real) == 4 && g.tc;
+    if (g.tc && (MT % g.block != 0)) return cudaErrorInvalidValue;
+    const size_t smem = sweep_smem_bytes(g.block, N, DIM, sizeof(Real), tc);
     auto kern = k_sweep<Real, N, DIM, ORDER>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1167,11 +1373,20 @@ cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<
 }
 
 template <typename Real>
-cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
-                                const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial) {
+cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq,
+                                const Quad<Real> &oq, const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial) {
     dim3 gg((n_cells + VCH / 32 - 1) / (VCH / 32), vq.n_pad / VCH);
     dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
-    GSIS_DISPATCH_DIM(dim, (k_moments_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, coef, f, partial)));
+    static_assert(VCH == tcm::K && SV == tcm::K, "moment chunks are the tensor-core K");
+    bool on_tc = false;
+    if constexpr (std::is_same<Real, float>::value) {
+        if (tc) {
+            dim3 gt((n_cells + MT - 1) / MT, vq.n_pad / tcm::K);
+            GSIS_DISPATCH_DIM(dim, (k_moments_gas_tc<DIM><<<gt, 128, TC_SMEM, s>>>(n_cells, vq, coef, f, partial)));
+            on_tc = true;
+        }
+    }
+    if (!on_tc) GSIS_DISPATCH_DIM(dim, (k_moments_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, coef, f, partial)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     GSIS_DISPATCH_DIM(dim, (k_moments_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, I, opartial)));
@@ -1187,13 +1402,24 @@ cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const Model
 }
 
 template <typename Real>
-cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
+cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                         const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
                         Real *f, Real *I, Real *partial, Real *opartial) {
     dim3 gg((n_cells + VCH / 32 - 1) / (VCH / 32), vq.n_pad / VCH);
     dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
-    GSIS_DISPATCH_DIM(dim, (k_sync_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, m, omega, F_new, F_half, coef, f,
-                                                                     partial)));
+    bool on_tc = false;
+    if constexpr (std::is_same<Real, float>::value) {
+        if (tc) {
+            dim3 gt((n_cells + MT - 1) / MT, vq.n_pad / tcm::K);
+            const int smem = TC_SMEM + MT * (6 + 3 * 2 + 8) * (int)sizeof(float);
+            GSIS_DISPATCH_DIM(dim, (k_sync_gas_tc<DIM><<<gt, 128, smem, s>>>(n_cells, vq, m, omega, F_new, F_half,
+                                                                             coef, f, partial)));
+            on_tc = true;
+        }
+    }
+    if (!on_tc)
+        GSIS_DISPATCH_DIM(dim, (k_sync_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, m, omega, F_new, F_half, coef,
+                                                                         f, partial)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     GSIS_DISPATCH_DIM(dim, (k_sync_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, m, omega, F_new, F_half, I,
@@ -1220,12 +1446,13 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, const Quad<Real> &
                                              double *, int *, int);                                                \
     template cudaError_t launch_equilibrium<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &,  \
                                                   const ModelDev &, const double *, Real *, Real *);               \
-    template cudaError_t launch_moments_only<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &, \
+    template cudaError_t launch_moments_only<Real>(cudaStream_t, int, int, bool, const Quad<Real> &,               \
+                                                   const Quad<Real> &,                                             \
                                                    const Real *, const Real *, const Real *, Real *, Real *);      \
     template cudaError_t launch_kinetic_bflux<Real>(cudaStream_t, const MacroGeom &, const ModelDev &,             \
                                                     const Quad<Real> &, const Quad<Real> &, const Real *,          \
                                                     const Real *, double *);                                       \
-    template cudaError_t launch_sync<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &,         \
+    template cudaError_t launch_sync<Real>(cudaStream_t, int, int, bool, const Quad<Real> &, const Quad<Real> &,   \
                                            const ModelDev &, double, const double *, const double *, const Real *, \
                                            Real *, Real *, Real *, Real *);
 

@@ -117,6 +117,19 @@ def test_gsis_inner_convergence_stops_early():
     assert_planes_close(fg, fo, 1e-9, "f^{k+1}")
 
 
+@pytest.mark.parametrize("tc", [0, 2])
+def test_gsis_step_fp32_moment_engines(tc):
+    """The synchronisation pass with its moments on CUDA cores (tc 0) and on the tensor
+    cores (tc 2, also the sweep epilogue)."""
+    wl = gi.workloads.with_solver(CASES["cavity72"](), precision="fp32", order=2, relax_block=16, max_inner=12,
+                                  tol_inner=0.0, tc_moments=tc)
+    f, I = _inputs(wl, 9, "fp32")
+    fg, Ig, rec, _ = _run(wl, f, I, 1)
+    fo, Io, Fo, _ = _oracle(wl, f, I, 1)
+    assert_planes_close(fg, fo, TOL["fp32"], "f^{k+1}")
+    assert_fields_close(rec, Fo, TOL["fp32"], wl.dim, "moments of f^{k+1}")
+
+
 def test_gsis_step_fp32_residual_side():
     """FP32 contexts may evaluate the synthetic residual side in FP32 (relaxation stays FP64)."""
     wl = gi.workloads.with_solver(CASES["cavity72"](), precision="fp32", order=2, relax_block=16, max_inner=12,

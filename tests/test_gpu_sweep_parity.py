@@ -80,6 +80,23 @@ def test_cis_step_matches_oracle(case, precision, order):
     assert abs(eps - eps_o) <= 1e-4 * eps_o if precision == "fp32" else abs(eps - eps_o) <= 1e-9 * eps_o
 
 
+@pytest.mark.parametrize("tc,block", [(0, 16), (1, 16), (2, 16), (2, 8), (2, 1), (2, 5), (2, 64)])
+def test_fp32_moment_engines(tc, block):
+    """Every place the FP32 gas moments are contracted: CUDA cores (tc 0), the tensor-core
+    standalone pass (tc >= 1, the moments of f^k) and the tensor-core sweep epilogue (tc 2,
+    blocks dividing 16; blocks 5 and 64 keep the CUDA-core epilogue), on 338 cells (ragged
+    last tile) x 784 velocities (ragged last chunk), flow speeds up to 0.6."""
+    wl = gi.workloads.with_solver(CASES["cavity338"](), precision="fp32", order=2, relax_block=block, tc_moments=tc)
+    f, I = _inputs(wl, 17, "fp32", u_scale=0.6)
+    rec0, rec1, fg, Ig, _ = _run(wl, f, I)
+    F0 = K.moments(f, I, wl.xi, wl.w, wl.omega, wl.wo, wl.dim, wl.model)
+    fo, Io = K.kinetic_sweep(f, I, wl, relax_block=block, F=F0)
+    F1 = K.moments(fo, Io, wl.xi, wl.w, wl.omega, wl.wo, wl.dim, wl.model)
+    assert_fields_close(rec0, F0, 1e-5, wl.dim, "moments of f^k")
+    assert_planes_close(fg, fo, 1e-5, "f^{k+1}")
+    assert_fields_close(rec1, F1, 1e-5, wl.dim, "moments of f^{k+1}")
+
+
 @pytest.mark.parametrize("block", [1, 5, 49])
 def test_block_sizes_and_jacobi(block):
     wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=9), precision="fp64", order=2, relax_block=block)
