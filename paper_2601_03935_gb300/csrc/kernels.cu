@@ -412,7 +412,12 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
         for (int a = 0; a < DIM; ++a) sxi[a * SV + tx] = xi[a];
         sxi[DIM * SV + tx] = q.w[v];
     }
-    if (tc) tcm::start(ctl, ty * SV + tx);   // the allocation completes during phase 1
+    if constexpr (TCM) {
+        if (tc)
+            tcm::start(ctl, ty * SV + tx);   // the allocation completes during phase 1
+        else if (ty == 0 && tx < 32)
+            tcm::relinquish();               // CUDA-core epilogue: let further CTAs onto the SM
+    }
     auto slope_at = [&](int c, V<Real, N> (&s)[DIM]) {
         const size_t idx = (size_t)c * stride + v;
 #pragma unroll

@@ -121,6 +121,12 @@ __device__ __forceinline__ void tmem_alloc(uint32_t slot_addr) {   // one full w
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
+// A CTA of a kernel that contains tcgen05.alloc holds the SM's allocation permit until it
+// relinquishes it, and while it holds it no further CTA of the kernel is scheduled on that
+// SM.  CTAs that take a path without tensor memory therefore give it up at once (one warp).
+__device__ __forceinline__ void relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr) {     // the allocating warp
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS) : "memory");
 }
