@@ -338,6 +338,16 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+
+    # ---- the standalone moment pass (Eq. getmoment): in FP32 with tc_moments >= 1 the gas
+    # moments are one split-TF32 tcgen05 contraction per (16-cell tile, 64 velocities)
+    G.gsis_profile_enable(ctx, True)
+    G.gsis_profile_reset(ctx)
+    for _ in range(5):
+        G.gsis_refresh_fields(ctx)
+    torch.cuda.synchronize()
+    mprof = G.gsis_profile_read(ctx)
+    G.gsis_profile_enable(ctx, False)
     G.gsis_destroy(ctx)
 
     if rank != 0:
@@ -351,6 +361,11 @@ def run_ours(args):
     alg_bytes = nc * V * 4 * rs * 2                     # read and write the four planes once
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / (avg_sweep * 1e-3) / 1e9
+    # moment pass: read f and I once, write the per-(cell, chunk) partials
+    Vp, Op = -(-V // 64) * 64, -(-NO // 64) * 64
+    m_bytes = nc * V * 4 * rs + nc * NO * rs + nc * (Vp // 64) * 20 * rs + nc * (Op // 64) * 4 * rs
+    m_ms = mprof["moments_only"][0] / max(mprof["moments_only"][1], 1)
+    tc_on = args.precision == "fp32" and args.tc_moments >= 1
     value = world * nc * V / (ms * 1e-3)
     kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)} for k, v in prof.items() if v[1]}
@@ -367,6 +382,10 @@ def run_ours(args):
         "e2e": {"value": world * nc * V / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": nc * (V * 4 + NO) * rs, "d2h_bytes_per_step": nc * G.GSIS_NF * 8},
         "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "last_eps": eps,
+        "moment_pass": {"kernel": ("k_moments_gas_tc (tcgen05, split TF32)" if tc_on else "k_moments_gas (CUDA cores)")
+                        + " + k_moments_photon", "bound": "hbm", "ms_per_launch": m_ms,
+                        "algorithmic_bytes_per_launch": m_bytes, "achieved": m_bytes / (m_ms * 1e-3) / 1e9,
+                        "peak": peak, "unit": "GB/s", "frac": m_bytes / (m_ms * 1e-3) / 1e9 / peak},
     }
     if not args.no_tts:
         line["time_to_steady"] = time_to_steady(stream)

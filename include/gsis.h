@@ -177,6 +177,13 @@ int gsis_get_distributions(gsis_ctx *ctx, double *f, int64_t f_len, double *I, i
  * stream; the call returns without synchronising. */
 int gsis_upload_distributions(gsis_ctx *ctx, const void *f, const void *I);
 
+/* Recompute the macroscopic fields from the distributions now on the device (the velocity
+ * moments of Eq. getmoment and the fields of Section 2, the same pass that follows an
+ * upload), asynchronously on the context stream.  In FP32 contexts with tc_moments >= 1
+ * the gas moments are one split-TF32 tensor-core contraction per (16-cell tile, 64
+ * velocities).  Errors: INVALID_ARG, CUDA. */
+int gsis_refresh_fields(gsis_ctx *ctx);
+
 /* Macroscopic fields of the current distributions, [n_cells][GSIS_NF] doubles. */
 int gsis_get_fields(gsis_ctx *ctx, double *out, int64_t len);
 

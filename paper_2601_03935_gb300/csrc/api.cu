@@ -41,6 +41,7 @@ struct gsis_ctx {
     void *f[2] = {nullptr, nullptr}, *I[2] = {nullptr, nullptr};
     int cur = 0;
     void *coef = nullptr, *bcoef = nullptr, *partial = nullptr, *opartial = nullptr;
+    void *sync_kc = nullptr;                    // FP32: per-cell synchronisation constants [nc][SYNC_KC] floats
     void *slope = nullptr, *oslope = nullptr;   // limited slopes [nc][Vp][dim][4], [nc][Op][dim] (order 2)
     double *fields = nullptr, *fields_old = nullptr, *eps_terms = nullptr, *eps_sums = nullptr;
     int *err = nullptr;
@@ -474,7 +475,8 @@ int gsis_iteration(gsis_ctx *c) {
     TRY(launch(c, K_SYNC, [&] {
         return launch_sync<Real>(c->stream, c->dim, (int)c->nc, c->tcm >= 1, vquad<Real>(c), oquad<Real>(c), c->model,
                                  c->solver.sync_relax, c->fields_n, c->fields_h, (const Real *)c->coef,
-                                 (Real *)c->f[nxt], (Real *)c->I[nxt], (Real *)c->partial, (Real *)c->opartial);
+                                 (Real *)c->f[nxt], (Real *)c->I[nxt], (Real *)c->partial, (Real *)c->opartial,
+                                 c->sync_kc);
     }));
     return close_iteration<Real>(c, nxt);
 }
@@ -889,6 +891,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc_real(c, &c->bcoef, bco.size()));
     A_(dalloc_real(c, &c->partial, (size_t)nc * c->nch * NMP));
     A_(dalloc_real(c, &c->opartial, (size_t)nc * c->och * NMO));
+    if (c->precision == GSIS_FP32) A_(dalloc_real(c, &c->sync_kc, (size_t)nc * SYNC_KC));
     if (c->order == 2) {
         A_(dalloc_real(c, &c->slope, (size_t)nc * c->Vp * dim * 4));
         A_(dalloc_real(c, &c->oslope, (size_t)nc * c->Op * dim));
@@ -1095,6 +1098,11 @@ int gsis_upload_distributions(gsis_ctx *c, const void *f, const void *I) {
                                   (size_t)c->nc, cudaMemcpyHostToDevice, c->stream));
     TRY(refresh(c));
     return GSIS_OK;
+}
+
+int gsis_refresh_fields(gsis_ctx *c) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    return refresh(c);
 }
 
 int gsis_set_distributions(gsis_ctx *c, const double *f, int64_t f_len, const double *I, int64_t I_len) {

@@ -16,6 +16,7 @@ constexpr int OCH = SV;        // direction chunk of the photon moment partials
 constexpr int NMP = 20;        // stride of per-(cell, chunk) gas moment partials
 constexpr int NMO = 4;         // stride of per-(cell, chunk) photon moment partials
 constexpr int MAXB = 64;       // largest relaxation block
+constexpr int SYNC_KC = 20;    // floats per cell of the synchronisation constants (FP32 tensor-core pass)
 constexpr int MT = 16;         // moment tile: gas moments are taken about the velocity of the
                                // tile's first cell (cells MT*t .. MT*t + MT - 1 share it)
 constexpr int NEPS = 8;        // per-cell terms of the convergence measure
@@ -162,7 +163,7 @@ cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const Model
 template <typename Real>
 cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                         const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
-                        Real *f, Real *I, Real *partial, Real *opartial);
+                        Real *f, Real *I, Real *partial, Real *opartial, void *scratch);
 int macro_rpart_count(int n_cells);
 
 // ---- learned closure (mlp.cu)

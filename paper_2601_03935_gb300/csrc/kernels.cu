@@ -22,6 +22,7 @@
 // polynomial basis.  In FP32 the contraction over velocities can run on the tensor cores
 // (tc_moments.cuh): in the standalone and synchronisation passes, and in the sweep's
 // epilogue when a relaxation block lies inside one tile.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
@@ -611,7 +612,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
                                             ((size_t)(c0 + l) * gridDim.y + chunk) * NMP,
                                         tid >> 5, m);
             }
-            tcm::end(ctl, taddr, tid, ok);
+            tcm::end(ctl, taddr, tid, ok, 0);
             return;
         }
     }
@@ -828,131 +829,182 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
 }
 
 // ------------------------------------------------------------------ FP32 moments on tensor cores
-// One CTA of 128 threads per (moment tile of MT cells, chunk of 64 velocities): thread
-// (v = tid % 64, half = tid / 64) holds the tile's cells 8 * half .. 8 * half + 7 at
-// velocity v, and the contraction of tc_moments.cuh gives the partials.  Rows of cells
-// beyond n_cells are zero.
+// Per-cell constants of the synchronisation (see k_sync_gas), formed once per cell in FP64
+// and rounded once: [0] A_n, [1] A_n - A_h, [2] A_h, [3] B_n, [4] B_h, [5] B_n - B_h,
+// [6..] u_h, [6 + DIM..] u_h - u_n, [6 + 2 DIM..] u_h + u_n, [6 + 3 DIM..] the plane
+// multipliers of M_n, [10 + 3 DIM..] their change; SKC floats per cell.
+constexpr int SKC = SYNC_KC;
+static_assert(SKC % 4 == 0, "constants are staged as float4");
+
 template <int DIM>
-__device__ __forceinline__ void tc_tile_moments(unsigned char *smem, int tid, int tile, int chunk, int n_cells,
-                                                const Quad<float> &vq, const float *coef,
-                                                const Vec<float, 4> (&fv)[MT / 2], float *partial) {
-    unsigned char *stage = smem;
-    tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(smem + tcm::STAGE_BYTES);
-    const int v = tid & 63, half = tid >> 6;
-#pragma unroll
-    for (int j = 0; j < MT / 2; ++j) tcm::put_a4(stage, half * (MT / 2) + j, v, fv[j].v);
-    if (half == 0) {
-        const int vg = chunk * tcm::K + v;
-        const Vec<float, 4> u4 = vload<float, 4>(coef + (size_t)tile * cf::NC + cf::U);
-        float c[DIM];
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) c[a] = vq.x[a * vq.n_pad + vg] - u4.v[a];
-        tcm::put_b<DIM>(stage, v, c, vq.w[vg]);
+__global__ void k_sync_coef(int n_cells, ModelDev m, const double *__restrict__ Fn, const double *__restrict__ Fh,
+                            float *__restrict__ kc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    constexpr int MH = 3 - DIM;
+    const double *rn = Fn + (size_t)i * NF, *rh = Fh + (size_t)i * NF;
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    // rho (2 pi T)^(-DIM/2)
+    const double An = DIM == 2 ? rn[0] / (two_pi * rn[4]) : rn[0] / sqrt(two_pi * rn[4]);
+    const double Ah = DIM == 2 ? rh[0] / (two_pi * rh[4]) : rh[0] / sqrt(two_pi * rh[4]);
+    const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
+    const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
+    const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
+    float K[SKC];
+    for (int q = 0; q < SKC; ++q) K[q] = 0.f;
+    K[0] = (float)An;
+    K[1] = (float)(An - Ah);
+    K[2] = (float)Ah;
+    K[3] = (float)Bn;
+    K[4] = (float)Bh;
+    K[5] = (float)(Bn - Bh);
+    for (int a = 0; a < DIM; ++a) {
+        K[6 + a] = (float)rh[1 + a];
+        K[6 + DIM + a] = (float)(rh[1 + a] - rn[1 + a]);
+        K[6 + 2 * DIM + a] = (float)(rh[1 + a] + rn[1 + a]);
     }
-    tcm::fence_smem_to_async();
-    __syncthreads();
-    const uint32_t taddr = tcm::accumulator(ctl);
-    float m[tcm::NBASIS];
-    bool ok;
-    if (tcm::contract(ctl, taddr, stage, tid, m, ok)) {
-        const int i = tile + (tid & 15);
-        if (i < n_cells) tcm::store_row<DIM>(partial + ((size_t)i * gridDim.y + chunk) * NMP, tid >> 5, m);
+    for (int p = 0; p < 4; ++p) {
+        K[6 + 3 * DIM + p] = (float)mn[p];
+        K[10 + 3 * DIM + p] = (float)(mn[p] - mh[p]);
     }
-    tcm::end(ctl, taddr, tid, ok);
+    for (int q = 0; q < SKC; ++q) kc[(size_t)i * SKC + q] = K[q];
 }
 
 constexpr int TC_SMEM = tcm::STAGE_BYTES + (int)sizeof(tcm::Ctl);
 
-template <int DIM>
-__global__ void __launch_bounds__(128) k_moments_gas_tc(int n_cells, Quad<float> vq, const float *__restrict__ coef,
-                                                        const float *__restrict__ f, float *__restrict__ partial) {
+// Persistent, pipelined pass over the work items (moment tile of MT cells, chunk of 64
+// velocities), one CTA of 128 threads per SM slot: thread (v = tid % 64, half = tid / 64)
+// holds cells 8 * half .. 8 * half + 7 of a tile at velocity v.  While the tensor cores
+// contract item k, the f loads of item k + 1 are in flight; the accumulator columns are
+// allocated once per CTA and the completion barrier alternates phases.  SYNC: the
+// synchronisation of k_sync_gas is applied to f (and stored) before the moments.
+template <int DIM, bool SYNC>
+__global__ void __launch_bounds__(128) k_tc_pass(int n_cells, int n_chunks, int n_items, Quad<float> vq, float om,
+                                                 const float4 *__restrict__ kc_g, const float *__restrict__ coef,
+                                                 float *__restrict__ f, float *__restrict__ partial) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
+    unsigned char *stage = tc_smem;
+    tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(tc_smem + tcm::STAGE_BYTES);
+    float4 *kc = reinterpret_cast<float4 *>(tc_smem + TC_SMEM);   // [MT][SKC / 4] (SYNC)
     const int tid = threadIdx.x, v = tid & 63, half = tid >> 6;
-    const int tile = blockIdx.x * MT, chunk = blockIdx.y;
-    tcm::start(reinterpret_cast<tcm::Ctl *>(tc_smem + tcm::STAGE_BYTES), tid);
-    Vec<float, 4> fv[MT / 2];
+    tcm::start(ctl, tid);
+    __syncthreads();
+    const uint32_t taddr = tcm::accumulator(ctl);
+
+    auto fetch = [&](int item, Vec<float, 4>(&x)[MT / 2]) {
+        const int tile = item / n_chunks * MT, vg = (item % n_chunks) * tcm::K + v;
 #pragma unroll
-    for (int j = 0; j < MT / 2; ++j) {
-        const int i = tile + half * (MT / 2) + j;
-        fv[j] = i < n_cells ? vload<float, 4>(f + ((size_t)i * vq.n_pad + chunk * tcm::K + v) * 4) : Vec<float, 4>{};
+        for (int j = 0; j < MT / 2; ++j) {
+            const int i = tile + half * (MT / 2) + j;
+            x[j] = i < n_cells ? vload<float, 4>(f + ((size_t)i * vq.n_pad + vg) * 4) : Vec<float, 4>{};
+        }
+    };
+    int item = blockIdx.x, prev = -1;
+    uint32_t parity = 0;
+    bool ok = true;
+    auto drain = [&](int it) {
+        float m[tcm::NBASIS];
+        bool okk;
+        if (tcm::collect(ctl, taddr, tid, parity, m, okk)) {
+            const int i = it / n_chunks * MT + (tid & 15);
+            if (i < n_cells)
+                tcm::store_row<DIM>(partial + ((size_t)i * n_chunks + it % n_chunks) * NMP, tid >> 5, m);
+        }
+        ok = ok && okk;
+        parity ^= 1u;
+    };
+    Vec<float, 4> fv[MT / 2];
+    if (item < n_items) fetch(item, fv);
+    while (item < n_items) {
+        const int next = item + gridDim.x;
+        Vec<float, 4> fn[MT / 2];
+        if (next < n_items) fetch(next, fn);              // in flight during the rest of the item
+        if (prev >= 0) drain(prev);
+        tcm::fence_before_sync();
+        __syncthreads();                                   // accumulator read, stage free
+        const int tile = item / n_chunks * MT, vg = (item % n_chunks) * tcm::K + v;
+        if constexpr (SYNC) {
+            if (tid < MT * (SKC / 4)) {
+                const int i = tile + tid / (SKC / 4);
+                kc[tid] = i < n_cells ? kc_g[(size_t)tile * (SKC / 4) + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            float xi[DIM];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) xi[a] = vq.x[a * vq.n_pad + vg];
+#pragma unroll
+            for (int j = 0; j < MT / 2; ++j) {
+                const int l = half * (MT / 2) + j, i = tile + l;
+                if (i < n_cells && vg < vq.n) {
+                    // E_h [A_n expm1(-delta) + (A_n - A_h)], delta = B_n c_n^2 - B_h c_h^2
+                    const float *Kc = reinterpret_cast<const float *>(kc + l * (SKC / 4));
+                    float c2h = 0.f, dc2 = 0.f;
+#pragma unroll
+                    for (int a = 0; a < DIM; ++a) {
+                        const float ch = xi[a] - Kc[6 + a];
+                        c2h += ch * ch;
+                        dc2 += Kc[6 + DIM + a] * (2.f * xi[a] - Kc[6 + 2 * DIM + a]);
+                    }
+                    const float Eh = fexp(-Kc[4] * c2h);
+                    const float delta = Kc[3] * dc2 + Kc[5] * c2h;
+                    const float d0 = Eh * (Kc[0] * expm1_r(-delta) + Kc[1]);
+                    const float e0h = Kc[2] * Eh;
+#pragma unroll
+                    for (int p = 0; p < 4; ++p)
+                        fv[j].v[p] += om * (Kc[6 + 3 * DIM + p] * d0 + Kc[10 + 3 * DIM + p] * e0h);
+                    vstore<float, 4>(f + ((size_t)i * vq.n_pad + vg) * 4, fv[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < MT / 2; ++j) tcm::put_a4(stage, half * (MT / 2) + j, v, fv[j].v);
+        if (half == 0) {
+            const Vec<float, 4> u4 = vload<float, 4>(coef + (size_t)tile * cf::NC + cf::U);
+            float c[DIM];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) c[a] = vq.x[a * vq.n_pad + vg] - u4.v[a];
+            tcm::put_b<DIM>(stage, v, c, vq.w[vg]);
+        }
+        tcm::fence_smem_to_async();
+        __syncthreads();
+        if (tid == 0) {
+            tcm::fence_after_sync();
+            tcm::issue(taddr, tcm::smem_u32(stage), tcm::smem_u32(&ctl->mbar));
+        }
+        prev = item;
+        item = next;
+#pragma unroll
+        for (int j = 0; j < MT / 2; ++j) fv[j] = fn[j];
     }
-    tc_tile_moments<DIM>(tc_smem, tid, tile, chunk, n_cells, vq, coef, fv, partial);
+    if (prev >= 0) drain(prev);
+    tcm::end(ctl, taddr, tid, ok, parity ^ 1u);
 }
 
-// The synchronisation of k_sync_gas for a moment tile, then its moments on the tensor
-// cores.  The per-cell constants (FP64 differences rounded once) are formed by 16 threads.
-template <int DIM>
-__global__ void __launch_bounds__(128) k_sync_gas_tc(int n_cells, Quad<float> vq, ModelDev m, double om,
-                                                     const double *__restrict__ Fn, const double *__restrict__ Fh,
-                                                     const float *__restrict__ coef, float *__restrict__ f,
-                                                     float *__restrict__ partial) {
-    extern __shared__ __align__(1024) unsigned char tc_smem[];
-    constexpr int MH = 3 - DIM;
-    constexpr int NK = 6 + 3 * DIM + 8;     // An, dA, Ah, Bn, Bh, dB, uh, du, su, mul_n[4], dmul[4]
-    float *kc = reinterpret_cast<float *>(tc_smem + TC_SMEM);   // [MT][NK]
-    const int tid = threadIdx.x, v = tid & 63, half = tid >> 6;
-    const int tile = blockIdx.x * MT, chunk = blockIdx.y;
-    tcm::start(reinterpret_cast<tcm::Ctl *>(tc_smem + tcm::STAGE_BYTES), tid);
-    if (tid < MT && tile + tid < n_cells) {
-        const int i = tile + tid;
-        const double *rn = Fn + (size_t)i * NF, *rh = Fh + (size_t)i * NF;
-        const double An = rn[0] * pow(2.0 * 3.14159265358979323846 * rn[4], -0.5 * DIM);
-        const double Ah = rh[0] * pow(2.0 * 3.14159265358979323846 * rh[4], -0.5 * DIM);
-        const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
-        const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
-        const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
-        float *Kc = kc + tid * NK;
-        Kc[0] = (float)An;
-        Kc[1] = (float)(An - Ah);
-        Kc[2] = (float)Ah;
-        Kc[3] = (float)Bn;
-        Kc[4] = (float)Bh;
-        Kc[5] = (float)(Bn - Bh);
-        for (int a = 0; a < DIM; ++a) {
-            Kc[6 + a] = (float)rh[1 + a];
-            Kc[6 + DIM + a] = (float)(rh[1 + a] - rn[1 + a]);
-            Kc[6 + 2 * DIM + a] = (float)(rh[1 + a] + rn[1 + a]);
-        }
-        for (int p = 0; p < 4; ++p) {
-            Kc[6 + 3 * DIM + p] = (float)mn[p];
-            Kc[10 + 3 * DIM + p] = (float)(mn[p] - mh[p]);
-        }
+// Grid of a persistent pass: every resident CTA slot of the device, at most one per item.
+// The slots per SM follow from the kernel's registers and shared memory (the occupancy
+// query reports a single CTA for kernels that allocate tensor memory); they are computed
+// once per (instantiation, device) and cached, so that a launch costs no host-side query.
+template <int DIM, bool SYNC>
+static int persistent_grid(int smem, int n_items) {
+    constexpr int MAXDEV = 64;
+    static int slots[MAXDEV] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return n_items;
+    if (slots[dev] == 0) {
+        int sms = 0, smem_sm = 0, regs_sm = 0;
+        cudaFuncAttributes fa;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, k_tc_pass<DIM, SYNC>) != cudaSuccess)
+            return n_items;
+        const int regs_cta = (fa.numRegs * 32 + 255) / 256 * 256 * 4;   // 4 warps, 256-register granules
+        const int reserved = 1024;                                       // per-CTA system shared memory
+        const int per = std::max(1, std::min({regs_sm / std::max(regs_cta, 1),
+                                              smem_sm / (smem + (int)fa.sharedSizeBytes + reserved), 16}));
+        slots[dev] = sms * per;
     }
-    __syncthreads();
-    const int vg = chunk * tcm::K + v;
-    float xi[DIM];
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) xi[a] = vq.x[a * vq.n_pad + vg];
-    const float w = (float)om;
-    Vec<float, 4> fv[MT / 2];
-#pragma unroll
-    for (int j = 0; j < MT / 2; ++j) {
-        const int i = tile + half * (MT / 2) + j;
-        fv[j] = i < n_cells ? vload<float, 4>(f + ((size_t)i * vq.n_pad + vg) * 4) : Vec<float, 4>{};
-    }
-#pragma unroll
-    for (int j = 0; j < MT / 2; ++j) {
-        const int l = half * (MT / 2) + j, i = tile + l;
-        if (i < n_cells && vg < vq.n) {
-            // E_h [A_n expm1(-delta) + (A_n - A_h)], delta = B_n c_n^2 - B_h c_h^2, as in k_sync_gas
-            const float *Kc = kc + l * NK;
-            float c2h = 0.f, dc2 = 0.f;
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) {
-                const float ch = xi[a] - Kc[6 + a];
-                c2h += ch * ch;
-                dc2 += Kc[6 + DIM + a] * (2.f * xi[a] - Kc[6 + 2 * DIM + a]);
-            }
-            const float Eh = fexp(-Kc[4] * c2h);
-            const float delta = Kc[3] * dc2 + Kc[5] * c2h;
-            const float d0 = Eh * (Kc[0] * expm1_r(-delta) + Kc[1]);
-            const float e0h = Kc[2] * Eh;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) fv[j].v[p] += w * (Kc[6 + 3 * DIM + p] * d0 + Kc[10 + 3 * DIM + p] * e0h);
-            vstore<float, 4>(f + ((size_t)i * vq.n_pad + vg) * 4, fv[j]);
-        }
-    }
-    tc_tile_moments<DIM>(tc_smem, tid, tile, chunk, n_cells, vq, coef, fv, partial);
+    return std::max(1, std::min(n_items, slots[dev]));
 }
 
 template <typename Real, int DIM>
@@ -1386,8 +1438,12 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, c
     bool on_tc = false;
     if constexpr (std::is_same<Real, float>::value) {
         if (tc) {
-            dim3 gt((n_cells + MT - 1) / MT, vq.n_pad / tcm::K);
-            GSIS_DISPATCH_DIM(dim, (k_moments_gas_tc<DIM><<<gt, 128, TC_SMEM, s>>>(n_cells, vq, coef, f, partial)));
+            const int nch = vq.n_pad / tcm::K, n_items = (n_cells + MT - 1) / MT * nch;
+            GSIS_DISPATCH_DIM(dim, {
+                auto kern = k_tc_pass<DIM, false>;
+                kern<<<persistent_grid<DIM, false>(TC_SMEM, n_items), 128, TC_SMEM, s>>>(
+                    n_cells, nch, n_items, vq, 0.f, nullptr, coef, const_cast<float *>(f), partial);
+            });
             on_tc = true;
         }
     }
@@ -1409,16 +1465,22 @@ cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const Model
 template <typename Real>
 cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                         const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
-                        Real *f, Real *I, Real *partial, Real *opartial) {
+                        Real *f, Real *I, Real *partial, Real *opartial, void *scratch) {
     dim3 gg((n_cells + VCH / 32 - 1) / (VCH / 32), vq.n_pad / VCH);
     dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
     bool on_tc = false;
     if constexpr (std::is_same<Real, float>::value) {
         if (tc) {
-            dim3 gt((n_cells + MT - 1) / MT, vq.n_pad / tcm::K);
-            const int smem = TC_SMEM + MT * (6 + 3 * 2 + 8) * (int)sizeof(float);
-            GSIS_DISPATCH_DIM(dim, (k_sync_gas_tc<DIM><<<gt, 128, smem, s>>>(n_cells, vq, m, omega, F_new, F_half,
-                                                                             coef, f, partial)));
+            if (!scratch) return cudaErrorInvalidValue;
+            float *kc = static_cast<float *>(scratch);
+            const int nch = vq.n_pad / tcm::K, n_items = (n_cells + MT - 1) / MT * nch;
+            const int smem = TC_SMEM + MT * SKC * (int)sizeof(float);
+            GSIS_DISPATCH_DIM(dim, {
+                k_sync_coef<DIM><<<(n_cells + 127) / 128, 128, 0, s>>>(n_cells, m, F_new, F_half, kc);
+                auto kern = k_tc_pass<DIM, true>;
+                kern<<<persistent_grid<DIM, true>(smem, n_items), 128, smem, s>>>(
+                    n_cells, nch, n_items, vq, (float)omega, reinterpret_cast<const float4 *>(kc), coef, f, partial);
+            });
             on_tc = true;
         }
     }
@@ -1459,7 +1521,7 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                                                     const Real *, double *);                                       \
     template cudaError_t launch_sync<Real>(cudaStream_t, int, int, bool, const Quad<Real> &, const Quad<Real> &,   \
                                            const ModelDev &, double, const double *, const double *, const Real *, \
-                                           Real *, Real *, Real *, Real *);
+                                           Real *, Real *, Real *, Real *, void *);
 
 GSIS_INSTANTIATE(float)
 GSIS_INSTANTIATE(double)

@@ -207,16 +207,13 @@ __device__ __forceinline__ uint32_t accumulator(const Ctl *ctl) {
     return *reinterpret_cast<const volatile uint32_t *>(&ctl->taddr);
 }
 
-// Contraction, all 128 threads, after the operands are in the stage and visible to the
-// tensor core (fence_smem_to_async by every writer, then a CTA barrier).  Thread 0 issues
-// the chain; everyone waits and reads its row; the tail row (lane + 16) is folded into the
-// head row by a shuffle.  Returns true on lanes 0..15, which then own row
-// (plane = warp, cell = lane) with its 8 moments in m.  `ok` turns false if the completion
-// wait ran out; m is NaN then.
-__device__ __forceinline__ bool contract(Ctl *ctl, uint32_t taddr, const unsigned char *stage, int tid,
-                                         float (&m)[NBASIS], bool &ok) {
-    if (tid == 0) issue(taddr, smem_u32(stage), smem_u32(&ctl->mbar));
-    ok = mbar_wait(smem_u32(&ctl->mbar), 0);
+// Results of a chain whose commit completes barrier phase `parity`, all 128 threads: wait,
+// read the thread's row, fold the tail row (lane + 16) into the head row by a shuffle.
+// Returns true on lanes 0..15, which then own row (plane = warp, cell = lane) with its 8
+// moments in m.  `ok` turns false if the completion wait ran out; m is NaN then.
+__device__ __forceinline__ bool collect(Ctl *ctl, uint32_t taddr, int tid, uint32_t parity, float (&m)[NBASIS],
+                                        bool &ok) {
+    ok = mbar_wait(smem_u32(&ctl->mbar), parity);
     fence_after_sync();
     float d[16];
     tmem_row(taddr, tid >> 5, d);
@@ -229,11 +226,20 @@ __device__ __forceinline__ bool contract(Ctl *ctl, uint32_t taddr, const unsigne
     return (tid & 31) < 16;
 }
 
+// One contraction, all 128 threads, after the operands are in the stage and visible to
+// the tensor core (fence_smem_to_async by every writer, then a CTA barrier): thread 0
+// issues the chain, then collect() on the barrier's first phase.
+__device__ __forceinline__ bool contract(Ctl *ctl, uint32_t taddr, const unsigned char *stage, int tid,
+                                         float (&m)[NBASIS], bool &ok) {
+    if (tid == 0) issue(taddr, smem_u32(stage), smem_u32(&ctl->mbar));
+    return collect(ctl, taddr, tid, 0, m, ok);
+}
+
 // Release the accumulator (all 128 threads; every tensor-memory read has completed).  If
-// the completion wait ran out, wait once more (bounded) so that no MMA is in flight when
-// the columns are freed.
-__device__ __forceinline__ void end(Ctl *ctl, uint32_t taddr, int tid, bool ok) {
-    if (!ok && tid == 0) mbar_wait(smem_u32(&ctl->mbar), 0);
+// a completion wait ran out, wait once more (bounded) on the last phase `parity` so that
+// no MMA is in flight when the columns are freed.
+__device__ __forceinline__ void end(Ctl *ctl, uint32_t taddr, int tid, bool ok, uint32_t parity) {
+    if (!ok && tid == 0) mbar_wait(smem_u32(&ctl->mbar), parity);
     fence_before_sync();
     __syncthreads();
     if (tid < 32) {

@@ -90,6 +90,7 @@ def load():
         "gsis_set_distributions": (C.c_int, [vp, _dp, C.c_int64, _dp, C.c_int64]),
         "gsis_get_distributions": (C.c_int, [vp, _dp, C.c_int64, _dp, C.c_int64]),
         "gsis_upload_distributions": (C.c_int, [vp, vp, vp]),
+        "gsis_refresh_fields": (C.c_int, [vp]),
         "gsis_get_fields": (C.c_int, [vp, _dp, C.c_int64]),
         "gsis_download_fields_async": (C.c_int, [vp, _dp, C.c_int64]),
         "gsis_step": (C.c_int, [vp, C.c_int32, _dp]),
@@ -215,6 +216,11 @@ def gsis_get_distributions(ctx, n_cells, n_xi, n_omega):
 def gsis_upload_distributions(ctx, f_ptr, I_ptr):
     """Host pointers (ints) to buffers in the storage precision."""
     _check(load().gsis_upload_distributions(ctx, C.c_void_p(f_ptr), C.c_void_p(I_ptr)), ctx)
+
+
+def gsis_refresh_fields(ctx):
+    """Recompute the fields from the distributions on the device (asynchronous)."""
+    _check(load().gsis_refresh_fields(ctx), ctx)
 
 
 def gsis_get_fields(ctx, n_cells):
