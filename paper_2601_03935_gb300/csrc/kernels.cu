@@ -879,7 +879,7 @@ constexpr int TC_SMEM = tcm::STAGE_BYTES + (int)sizeof(tcm::Ctl);
 // allocated once per CTA and the completion barrier alternates phases.  SYNC: the
 // synchronisation of k_sync_gas is applied to f (and stored) before the moments.
 template <int DIM, bool SYNC>
-__global__ void __launch_bounds__(128) k_tc_pass(int n_cells, int n_chunks, int n_items, Quad<float> vq, float om,
+__global__ void __launch_bounds__(128, 5) k_tc_pass(int n_cells, int n_chunks, int n_items, Quad<float> vq, float om,
                                                  const float4 *__restrict__ kc_g, const float *__restrict__ coef,
                                                  float *__restrict__ f, float *__restrict__ partial) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
