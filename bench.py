@@ -54,7 +54,9 @@ def config(args, wl):
                         % (wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]),
             "n_cells": wl.mesh.n_cells, "n_xi": int(wl.xi.shape[0]), "n_omega": int(wl.omega.shape[0]),
             "order": args.order, "relax_block": args.block, "tc_moments": args.tc_moments, "Kn": args.kn, "Kn_photon": args.kn_p,
-            "step": "one CIS outer iteration (kinetic sweep + moments + fields + epsilon)",
+            "step": ("one CIS outer iteration (kinetic sweep + moments + fields + epsilon)" if args.mode == "cis" else
+                     "one GSIS outer iteration (kinetic sweep + moments + high-order terms + synthetic solve + "
+                     "synchronisation + epsilon)"),
             "l2": "inputs larger than L2 (f: 2 x %.0f MB)" % (wl.mesh.n_cells * 896 * 16 / 1e6),
             "parallelism": "replicas" if args.gpus > 1 else "1 GPU"}
 
@@ -282,6 +284,7 @@ def run_ours(args):
     ctx = create_ctx(wl, stream.cuda_stream)
     f, I = initial_state(wl)
     G.gsis_set_distributions(ctx, f, I)
+    mode = G.GSIS_MODE_CIS if args.mode == "cis" else G.GSIS_MODE_GSIS
 
     def barrier():
         if dist is not None:
@@ -289,7 +292,7 @@ def run_ours(args):
 
     # ---- device-resident throughput
     for _ in range(args.warmup):
-        G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+        G.gsis_step_async(ctx, mode)
     G.gsis_last_eps(ctx)
     G.gsis_profile_enable(ctx, True)
     G.gsis_profile_reset(ctx)
@@ -300,7 +303,7 @@ def run_ours(args):
     with ClockSampler(local) as clk:
         e0.record(stream)
         for _ in range(args.steps):
-            G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+            G.gsis_step_async(ctx, mode)
         e1.record(stream)
         torch.cuda.synchronize()
     barrier()
@@ -323,7 +326,7 @@ def run_ours(args):
 
     def e2e_step():
         G.gsis_upload_distributions(ctx, hf.data_ptr(), hI.data_ptr())
-        G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+        G.gsis_step_async(ctx, mode)
         G.gsis_download_fields_async(ctx, hout.data_ptr(), nc)
         stream.synchronize()
 
@@ -406,6 +409,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--block", type=int, default=16)
+    ap.add_argument("--mode", default="cis", choices=["cis", "gsis"],
+                    help="outer iteration timed: cis (the kinetic sweep and moments) or gsis (adds the synthetic "
+                         "solve and the synchronisation pass)")
     ap.add_argument("--tc-moments", type=int, default=1, choices=[0, 1, 2],
                     help="FP32 gas moments: 0 CUDA cores, 1 tensor cores in the standalone and sync passes, "
                          "2 also in the sweep epilogue")
