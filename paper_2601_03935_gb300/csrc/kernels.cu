@@ -183,42 +183,50 @@ __device__ __forceinline__ Face<Real> load_face(const Real *__restrict__ fgeo, i
     return F;
 }
 
-// Venkatakrishnan-limited least-squares slope of cell j at one discrete velocity:
-// grad = sum_s C_js (f_s - f_j) over the stencil (face neighbours and their face
-// neighbours); phi = min(1, min_faces phi_V(Delta_1, Delta_2)) per plane with the
-// bounds Delta_max/min taken over the interior face neighbours (the first entries of
-// the stencil).  Returns the slope multiplied by phi.
-template <typename Real, int N, int DIM>
+// Venkatakrishnan-limited least-squares slope of cell j at VPT discrete velocities
+// v, v + 32, ..., v + 32 (VPT - 1), which share the cell's stencil indices, weights and
+// face offsets: grad = sum_s C_js (f_s - f_j) over the stencil (face neighbours and their
+// face neighbours); phi = min(1, min_faces phi_V(Delta_1, Delta_2)) per plane with the
+// bounds Delta_max/min taken over the interior face neighbours (the first entries of the
+// stencil).  Returns the slope multiplied by phi.
+template <typename Real, int N, int DIM, int VPT>
 __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *__restrict__ f, int stride, int j,
-                                              int v, const V<Real, N> &fj, V<Real, N> (&slope)[DIM]) {
-    V<Real, N> dmax, dmin;
+                                              int v, const V<Real, N> (&fj)[VPT], V<Real, N> (&slope)[VPT][DIM]) {
+    V<Real, N> dmax[VPT], dmin[VPT];
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
-        dmax.x[p] = Real(0);
-        dmin.x[p] = Real(0);
+    for (int u = 0; u < VPT; ++u)
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) slope[d].x[p] = Real(0);
-    }
+        for (int p = 0; p < N; ++p) {
+            dmax[u].x[p] = Real(0);
+            dmin[u].x[p] = Real(0);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) slope[u][d].x[p] = Real(0);
+        }
     const int4 info = g.info[j];
     const int ns = info.y, nfn = info.z;
+    const int *stn = g.stn + (size_t)j * MAXS;
+    const Real *lw = g.lsq + (size_t)j * MAXS * 2;
 #pragma unroll
     for (int k = 0; k < MAXS; ++k) {
         if (k >= ns) break;
-        const int s = g.stn[j * MAXS + k];
-        const V<Real, N> fs = ldv<Real, N>(f, (size_t)s * stride + v);
-        const Real *w = g.lsq + ((size_t)j * MAXS + k) * 2;
-        const Real c0 = w[0], c1 = DIM > 1 ? w[1] : Real(0);
+        const size_t row = (size_t)stn[k] * stride + v;
+        V<Real, N> fs[VPT];
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) fs[u] = ldv<Real, N>(f, row + 32 * u);
+        const Real c0 = lw[2 * k], c1 = DIM > 1 ? lw[2 * k + 1] : Real(0);
         const bool face_nbr = k < nfn;
 #pragma unroll
-        for (int p = 0; p < N; ++p) {
-            const Real dq = fs.x[p] - fj.x[p];
-            if (face_nbr) {
-                dmax.x[p] = fmax(dmax.x[p], dq);
-                dmin.x[p] = fmin(dmin.x[p], dq);
+        for (int u = 0; u < VPT; ++u)
+#pragma unroll
+            for (int p = 0; p < N; ++p) {
+                const Real dq = fs[u].x[p] - fj[u].x[p];
+                if (face_nbr) {
+                    dmax[u].x[p] = fmax(dmax[u].x[p], dq);
+                    dmin[u].x[p] = fmin(dmin[u].x[p], dq);
+                }
+                slope[u][0].x[p] = fma(c0, dq, slope[u][0].x[p]);
+                if constexpr (DIM > 1) slope[u][1].x[p] = fma(c1, dq, slope[u][1].x[p]);
             }
-            slope[0].x[p] = fma(c0, dq, slope[0].x[p]);
-            if constexpr (DIM > 1) slope[1].x[p] = fma(c1, dq, slope[1].x[p]);
-        }
     }
     // phi = min(1, min over interior faces of phi_V(Delta_1, Delta_2)).  On the faces with
     // Delta_2 > 0 (Delta_1 = Delta_max >= 0) phi_V >= 1 while Delta_2 <= Delta_1 / 2 and
@@ -226,43 +234,45 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
     // Delta_2; likewise at the most negative Delta_2 with Delta_min.  Two evaluations per
     // plane replace one per face.
     const Real eps2 = g.eps2[j];
-    V<Real, N> hi, lo;
+    V<Real, N> hi[VPT], lo[VPT];
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
-        hi.x[p] = Real(0);
-        lo.x[p] = Real(0);
-    }
+    for (int u = 0; u < VPT; ++u)
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            hi[u].x[p] = Real(0);
+            lo[u].x[p] = Real(0);
+        }
     const int nf = info.x;
     for (int k = 0; k < nf; ++k) {
         if (g.fnb[j * MAXF + k].x < 0) continue;
         const Real *q = g.fgeo + ((size_t)j * MAXF + k) * fr::SIZE + fr::DFX;
         const Real dx0 = q[0], dx1 = DIM > 1 ? q[1] : Real(0);
 #pragma unroll
+        for (int u = 0; u < VPT; ++u)
+#pragma unroll
+            for (int p = 0; p < N; ++p) {
+                Real d2 = slope[u][0].x[p] * dx0;
+                if constexpr (DIM > 1) d2 = fma(slope[u][1].x[p], dx1, d2);
+                hi[u].x[p] = fmax(hi[u].x[p], d2);
+                lo[u].x[p] = fmin(lo[u].x[p], d2);
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < VPT; ++u)
+#pragma unroll
         for (int p = 0; p < N; ++p) {
-            Real d2 = slope[0].x[p] * dx0;
-            if constexpr (DIM > 1) d2 = fma(slope[1].x[p], dx1, d2);
-            hi.x[p] = fmax(hi.x[p], d2);
-            lo.x[p] = fmin(lo.x[p], d2);
-        }
-    }
-    V<Real, N> phi;
+            Real ph = Real(1);
+            if (hi[u].x[p] > Real(0)) {
+                const Real d1 = dmax[u].x[p], d2 = hi[u].x[p];
+                ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+            }
+            if (lo[u].x[p] < Real(0)) {
+                const Real d1 = dmin[u].x[p], d2 = lo[u].x[p];
+                ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+            }
 #pragma unroll
-    for (int p = 0; p < N; ++p) {
-        Real ph = Real(1);
-        if (hi.x[p] > Real(0)) {
-            const Real d1 = dmax.x[p], d2 = hi.x[p];
-            ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+            for (int d = 0; d < DIM; ++d) slope[u][d].x[p] *= ph;
         }
-        if (lo.x[p] < Real(0)) {
-            const Real d1 = dmin.x[p], d2 = lo.x[p];
-            ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
-        }
-        phi.x[p] = ph;
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d)
-#pragma unroll
-        for (int p = 0; p < N; ++p) slope[d].x[p] *= phi.x[p];
 }
 
 // Reference distribution of the four gas planes at one (cell, velocity).
@@ -336,31 +346,39 @@ __device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Rea
 }
 
 // ------------------------------------------------------------------ limited slopes
-// One thread per (cell, velocity): the Venkatakrishnan-limited least-squares slope of
-// every plane, stored as slope[(cell * n_pad + v) * DIM + d][plane].  The sweep reads a
-// cell's slope for its outflow faces and a neighbour's for the inflow faces, so each
-// slope is computed once per iteration.
+// Thread (tx, ty) of a 32 x SLOPE_ROWS CTA: cell blockIdx.x * SLOPE_ROWS + ty, velocities
+// blockIdx.y * SV + tx + 32 u (u < 2).  Stores the Venkatakrishnan-limited least-squares
+// slope of every plane as slope[(cell * n_pad + v) * DIM + d][plane].  The sweep reads a
+// cell's slope for its outflow faces and a neighbour's for the inflow faces, so each slope
+// is computed once per iteration.
+constexpr int SLOPE_ROWS = 8;
 template <typename Real, int N, int DIM>
-__global__ void __launch_bounds__(SV * 4) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ f,
-                                                   Real *__restrict__ slope) {
+__global__ void __launch_bounds__(32 * SLOPE_ROWS) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ f,
+                                                            Real *__restrict__ slope) {
+    constexpr int VPT = SV / 32;
     const int v = blockIdx.y * SV + threadIdx.x;
-    const int j = blockIdx.x * 4 + threadIdx.y;
+    const int j = blockIdx.x * SLOPE_ROWS + threadIdx.y;
     if (j >= g.n_cells) return;
     const size_t idx = (size_t)j * n_pad + v;
-    const V<Real, N> fj = ldv<Real, N>(f, idx);
-    V<Real, N> s[DIM];
-    limited_slope<Real, N, DIM>(g, f, n_pad, j, v, fj, s);
+    V<Real, N> fj[VPT];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        if constexpr (N == 1) {
-            slope[idx * DIM + d] = s[d].x[0];
-        } else {
-            Vec<Real, N> t;
+    for (int u = 0; u < VPT; ++u) fj[u] = ldv<Real, N>(f, idx + 32 * u);
+    V<Real, N> sl[VPT][DIM];
+    limited_slope<Real, N, DIM, VPT>(g, f, n_pad, j, v, fj, sl);
 #pragma unroll
-            for (int p = 0; p < N; ++p) t.v[p] = s[d].x[p];
-            vstore<Real, N>(slope + (idx * DIM + d) * N, t);
+    for (int u = 0; u < VPT; ++u)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const size_t o = (idx + 32 * u) * DIM + d;
+            if constexpr (N == 1) {
+                slope[o] = sl[u][d].x[0];
+            } else {
+                Vec<Real, N> t;
+#pragma unroll
+                for (int p = 0; p < N; ++p) t.v[p] = sl[u][d].x[p];
+                vstore<Real, N>(slope + o * N, t);
+            }
         }
-    }
 }
 
 // ------------------------------------------------------------------ the sweep
@@ -1345,7 +1363,7 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
 
 template <typename Real, int N, int DIM>
 static cudaError_t slopes_t(cudaStream_t s, const Geom<Real> &g, int n_pad, const Real *f, Real *slope) {
-    dim3 grid((g.n_cells + 3) / 4, n_pad / SV), block(SV, 4);
+    dim3 grid((g.n_cells + SLOPE_ROWS - 1) / SLOPE_ROWS, n_pad / SV), block(32, SLOPE_ROWS);
     k_slopes<Real, N, DIM><<<grid, block, 0, s>>>(g, n_pad, f, slope);
     return cudaGetLastError();
 }
