@@ -35,9 +35,10 @@ def epsilon(F_new, F_old, vol, model, dim):
 
 
 def cis_step(f, I, wl, geo):
-    """One conventional iteration: moments of f^k, one kinetic sweep, f^{k+1} = f^{k+1/2}."""
+    """One conventional iteration: moments of f^k, one kinetic sweep (Gauss-Seidel inside
+    relaxation blocks of wl.solver.relax_block cells, as in gsis_step), f^{k+1} = f^{k+1/2}."""
     F_old = K.moments(f, I, wl.xi, wl.w, wl.omega, wl.wo, wl.dim, wl.model)
-    f_new, I_new = K.kinetic_sweep(f, I, wl, geo=geo, F=F_old)
+    f_new, I_new = K.kinetic_sweep(f, I, wl, geo=geo, F=F_old, relax_block=wl.solver.relax_block)
     F_new = K.moments(f_new, I_new, wl.xi, wl.w, wl.omega, wl.wo, wl.dim, wl.model)
     return f_new, I_new, epsilon(F_new, F_old, geo.vol, wl.model, wl.dim), F_new
 
