@@ -260,6 +260,38 @@ def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=15
     return out
 
 
+def normal_shock(max_gsis=300):
+    """The paper's Mach-5 normal shock (FP64, order 2): CIS and GSIS outer iterations to
+    eps < 2e-6 for (Z_r, Z_v) = (2.6, 26) on 200 L0 and (8, 100) on 350 L0, with the
+    paper's iteration counts beside them.  GSIS stops at max_gsis iterations."""
+    import torch
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import gsis as G
+    paper = {26.0: {"cis": 991, "gsis": 68}, 100.0: {"cis": 2566, "gsis": 90}}
+    out = {}
+    for Zr, Zv, L in ((2.6, 26.0, 200.0), (8.0, 100.0, 350.0)):
+        wl = gi.workloads.with_solver(gi.workloads.normal_shock(Z_r=Zr, Z_v=Zv, length=L), precision="fp64",
+                                      order=2, relax_block=16, venkat_K=0.01, max_inner=100, tol_inner=1e-7)
+        M = gi.fields.shock_fields(wl)
+        f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 1, wl.model.d_r, wl.model.d_v, wl.model.sigma_R,
+                                           0, noise=0.0)
+        res = {"cells": wl.mesh.n_cells, "n_xi": wl.xi.shape[0], "n_omega": wl.omega.shape[0],
+               "paper_iterations": paper[Zv]}
+        for mode, name, mx in ((G.GSIS_MODE_CIS, "cis", 6000), (G.GSIS_MODE_GSIS, "gsis", max_gsis)):
+            ctx = create_ctx(wl, 0)
+            G.gsis_set_distributions(ctx, f, I)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist = G.gsis_solve(ctx, mode, mx, 2e-6)
+            torch.cuda.synchronize()
+            res[name] = {"iterations": it, "seconds": time.perf_counter() - t0, "final_eps": float(hist[-1]),
+                         "converged": bool(hist[-1] < 2e-6),
+                         "eps_at": {str(k): float(hist[k]) for k in (9, 49, 99, 199) if k < len(hist)}}
+            G.gsis_destroy(ctx)
+        out["Zr%g_Zv%g_L%g" % (Zr, Zv, L)] = res
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2601_03935_gb300 import build
@@ -392,6 +424,8 @@ def run_ours(args):
     }
     if not args.no_tts:
         line["time_to_steady"] = time_to_steady(stream)
+    if not args.no_shock:
+        line["normal_shock"] = normal_shock()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
     print(json.dumps(line))
@@ -420,6 +454,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady measurement")
+    ap.add_argument("--no-shock", action="store_true", help="skip the normal-shock convergence measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -63,6 +63,19 @@ def uniform_fields(n_cells: int, rho=1.0, u=(0.0, 0.0, 0.0), T=1.0, T_R=None) ->
     return M
 
 
+def shock_fields(wl) -> np.ndarray:
+    """Step initial state of the normal shock: the upstream patch state for x <= 0, the
+    downstream patch state for x > 0 (all temperatures equal on each side)."""
+    up, down = wl.mesh.patches[0], wl.mesh.patches[1]
+    x = wl.mesh.cell_centroid[:, 0]
+    M = np.zeros((wl.mesh.n_cells, NF))
+    for sel, P in ((x <= 0.0, up), (x > 0.0, down)):
+        M[sel, RHO] = P.rho
+        M[sel, UX:UZ + 1] = np.asarray(P.u, np.float64)
+        M[sel, TT], M[sel, TR], M[sel, TV], M[sel, TRAD] = P.T_t, P.T_r, P.T_v, P.T_R
+    return M
+
+
 def noisy_equilibrium(M, xi, omega, dim, d_r, d_v, sigma_R, seed, noise=0.05):
     """Multi-temperature local equilibrium of each cell's (rho, u, T_t, T_r, T_v, T_R),
     each value multiplied by (1 + noise*U(-1, 1)).

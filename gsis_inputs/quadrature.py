@@ -83,6 +83,17 @@ def gauss_legendre_slab(n: int):
     return om, 2.0 * np.pi * wmu
 
 
+def uniform_polar_slab(n: int):
+    """Photon directions for a plane-parallel slab from n uniform cells of the polar angle
+    theta in [0, pi] (the azimuth integrates out): each cell is one ring of directions at
+    its mid angle, weighted by the exact solid angle 2 pi (cos theta_lo - cos theta_hi)."""
+    edges = np.linspace(0.0, np.pi, n + 1)
+    th = 0.5 * (edges[1:] + edges[:-1])
+    w = 2.0 * np.pi * (np.cos(edges[:-1]) - np.cos(edges[1:]))
+    om = np.stack([np.cos(th), np.sin(th), np.zeros(n)], axis=1)
+    return om, w
+
+
 def photon_product(n_polar: int, n_azim: int):
     """Gauss-Legendre in cos(polar angle about z) x uniform azimuth in the x-y plane."""
     mu, wmu = np.polynomial.legendre.leggauss(n_polar)

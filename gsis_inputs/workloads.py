@@ -113,6 +113,44 @@ def cylinder(n_theta: int = 200, n_radial: int = 100, n_v: int = 48, n_polar: in
                     ModelParams(Kn=Kn, Kn_p=Kn_p, sigma_R=sigma_R, k_eff_density_scaled=True))
 
 
+def rankine_hugoniot(Mach: float, gamma: float):
+    """Downstream (rho, u, T) of a normal shock with upstream rho = T = 1 and
+    u = sqrt(gamma) Mach (velocity unit sqrt(R T0)), from the Rankine-Hugoniot relations
+    as the paper's normal-shock case states them (Section 'Normal shock wave')."""
+    M2 = Mach * Mach
+    rho_d = (gamma + 1.0) * M2 / (2.0 + (gamma - 1.0) * M2)
+    u_u = np.sqrt(gamma) * Mach
+    T_d = (2.0 + (gamma - 1.0) * M2) * (2.0 * gamma * M2 - (gamma - 1.0)) / ((gamma + 1.0) ** 2 * M2)
+    return rho_d, u_u / rho_d, T_d
+
+
+def normal_shock(Z_r: float = 2.6, Z_v: float = 26.0, length: float = 200.0, dx: float = 0.25,
+                 Mach: float = 5.0, n_xi: int = 64, xi_max: float = 15.0, n_theta: int = 48,
+                 x_shock: float = 0.25) -> Workload:
+    """The paper's Mach-5 normal shock (Section 'Normal shock wave'): a uniform 1-D mesh of
+    spacing dx over `length` (in the unit L0 of the paper, so Kn = 5 pi / 16), fixed
+    upstream and Rankine-Hugoniot downstream equilibrium states at the two ends (far-field
+    patches), Kn_p = 10, sigma_R = 0.01, n_xi uniform velocities on [-xi_max, xi_max]
+    (trapezoid weights) and n_theta uniform polar cells for the photons.  The initial
+    discontinuity sits at the fraction `x_shock` of the domain."""
+    d_r, d_v = 2.0, 1.16
+    gamma = (5.0 + d_r + d_v) / (3.0 + d_r + d_v)
+    rho_d, u_d, T_d = rankine_hugoniot(Mach, gamma)
+    u_u = np.sqrt(gamma) * Mach
+    n = int(round(length / dx))
+    m = _mesh.slab_1d(n, length, patches=[
+        _mesh.Patch(_mesh.FARFIELD, rho=1.0, u=(u_u, 0.0, 0.0), T_t=1.0, T_r=1.0, T_v=1.0, T_R=1.0),
+        _mesh.Patch(_mesh.FARFIELD, rho=rho_d, u=(u_d, 0.0, 0.0), T_t=T_d, T_r=T_d, T_v=T_d, T_R=T_d)])
+    m.cell_centroid = m.cell_centroid - x_shock * length
+    m.face_centroid = m.face_centroid - x_shock * length
+    xi, w = _q.trapezoid_nd(n_xi, xi_max, 1)
+    om, wo = _q.uniform_polar_slab(n_theta)
+    return Workload("shock_Zv%g_%d" % (Z_v, n), m, xi, w, om, wo,
+                    ModelParams(d_r=d_r, d_v=d_v, Z_r=Z_r, Z_v=Z_v, Kn=5.0 * np.pi / 16.0, Kn_p=10.0,
+                                sigma_R=0.01),
+                    SolverParams(precision="fp64", tol_outer=2e-6, max_outer=4000))
+
+
 def with_solver(wl: Workload, **kw) -> Workload:
     return replace(wl, solver=replace(wl.solver, **kw))
 

@@ -84,6 +84,40 @@ def test_gsis_step_matches_oracle_fp64(case, order):
     assert abs(eps[0] - eps_o[0]) <= 1e-9 * eps_o[0]
 
 
+def test_normal_shock_steps_match_oracle():
+    """The Mach-5 normal shock (1-D, far-field upstream state and Rankine-Hugoniot
+    downstream state at the two ends) from its step initial state: two CIS and one GSIS
+    iteration in FP64, order 2, on 24 cells x 48 velocities (one ragged chunk) x 8 polar
+    cells."""
+    wl = gi.workloads.with_solver(gi.workloads.normal_shock(length=12.0, dx=0.5, n_xi=48, n_theta=8),
+                                  precision="fp64", order=2, relax_block=16, max_inner=12, tol_inner=0.0,
+                                  venkat_K=0.01)
+    M = gi.fields.shock_fields(wl)
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 1, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, 0,
+                                       noise=0.0)
+    ctx = create(wl)
+    try:
+        G.gsis_set_distributions(ctx, f, I)
+        eps = [G.gsis_step(ctx, m) for m in (G.GSIS_MODE_CIS, G.GSIS_MODE_CIS, G.GSIS_MODE_GSIS)]
+        fg, Ig = G.gsis_get_distributions(ctx, wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0])
+        rec = G.gsis_get_fields(ctx, wl.mesh.n_cells)
+    finally:
+        G.gsis_destroy(ctx)
+    geo = K.Geometry(wl.mesh)
+    faces = MA.Faces(geo)
+    eps_o = []
+    fo, Io = f, I
+    for _ in range(2):
+        fo, Io, e, Fo = OG.cis_step(fo, Io, wl, geo)
+        eps_o.append(e)
+    fo, Io, e, Fo = OG.gsis_step(fo, Io, wl, geo, faces)
+    eps_o.append(e)
+    assert_planes_close(fg, fo, TOL["fp64"], "f^{k+3}")
+    assert_planes_close(Ig, Io, TOL["fp64"], "I^{k+3}")
+    assert_fields_close(rec, Fo, TOL["fp64"], wl.dim, "moments of f^{k+3}")
+    assert np.allclose(eps, eps_o, rtol=1e-9)
+
+
 def test_gsis_two_steps_fp64():
     wl = gi.workloads.with_solver(CASES["cavity72"](), precision="fp64", order=2, relax_block=16, max_inner=10,
                                   tol_inner=0.0)
@@ -139,3 +173,38 @@ def test_gsis_step_fp32_residual_side():
     fo, Io, Fo, eps_o = _oracle(wl, f, I, 1)
     assert_planes_close(fg, fo, TOL["fp32"], "f^{k+1}")
     assert_fields_close(rec, Fo, TOL["fp32"], wl.dim, "moments of f^{k+1}")
+
+
+def test_normal_shock_conserves_fluxes_at_convergence():
+    """A converged Mach-5 shock (the paper's case: 200 L0 at spacing 0.25 L0, Z_v = 26, CIS
+    to its tolerance eps < 2e-6) carries uniform mass,
+    momentum and energy fluxes through the domain: rho u, rho u^2 + rho T_t + sigma_xx and
+    u (E + p + sigma_xx) + q (gas modes and radiation) from the library's field records;
+    mass and momentum equal those of the upstream state.  Cell values of a resolved shock
+    differ from the conserved face fluxes by the scheme's truncation error, hence 1e-2."""
+    wl = gi.workloads.with_solver(gi.workloads.normal_shock(length=200.0, dx=0.25, n_xi=64, n_theta=48),
+                                  precision="fp64", order=2, relax_block=16, venkat_K=0.01)
+    M = gi.fields.shock_fields(wl)
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 1, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, 0,
+                                       noise=0.0)
+    ctx = create(wl)
+    try:
+        G.gsis_set_distributions(ctx, f, I)
+        it, hist = G.gsis_solve(ctx, G.GSIS_MODE_CIS, 6000, 2e-6)
+        F = G.gsis_get_fields(ctx, wl.mesh.n_cells)
+    finally:
+        G.gsis_destroy(ctx)
+    assert hist[-1] < 2e-6, "CIS reached %.2e after %d iterations" % (hist[-1], it)
+    d_r, d_v = wl.model.d_r, wl.model.d_v
+    rho, u, Tt, Tr, Tv = F[:, 0], F[:, 1], F[:, 4], F[:, 5], F[:, 6]
+    sxx = F[:, 20]
+    q = F[:, 8] + F[:, 11] + F[:, 14] + F[:, 17]
+    p = rho * Tt
+    E = rho * (0.5 * u * u + 0.5 * (3.0 * Tt + d_r * Tr + d_v * Tv))
+    fluxes = {"mass": rho * u, "momentum": rho * u * u + p + sxx, "energy": u * (E + p + sxx) + q}
+    for name, fl in fluxes.items():
+        dev = (fl.max() - fl.min()) / abs(fl.mean())
+        assert dev < 1e-2, "%s flux varies by %.2e of its mean" % (name, dev)
+    up = wl.mesh.patches[0]
+    assert abs(fluxes["mass"].mean() - up.rho * up.u[0]) < 1e-2 * up.rho * up.u[0]
+    assert abs(fluxes["momentum"].mean() - up.rho * (up.u[0] ** 2 + up.T_t)) < 1e-2 * up.rho * up.u[0] ** 2
