@@ -177,6 +177,22 @@ int gsis_get_distributions(gsis_ctx *ctx, double *f, int64_t f_len, double *I, i
  * stream; the call returns without synchronising. */
 int gsis_upload_distributions(gsis_ctx *ctx, const void *f, const void *I);
 
+/* Double-buffered uploads: copy the next state while the current one is being computed.
+ * gsis_stage_distributions starts an asynchronous copy of host buffers in the storage
+ * precision (layout as gsis_upload_distributions; pinned for true asynchrony) into a
+ * staging pair of device buffers, on a copy stream of the context's own.  It waits on the
+ * device only for the previous commit, never for the compute stream's current work, and
+ * returns at once; the host buffers must stay valid until the copy completes (it has when
+ * the commit's work has run).  The first call allocates the staging pair (the size of the
+ * distributions) and the copy stream.  gsis_commit_staged makes the staged state current
+ * on the context stream (waiting for the copy there, not on the host) and takes its fields
+ * as gsis_refresh_fields does.  One upload can be staged at a time.  The paper has no
+ * counterpart: this is how the step overlaps its host-to-device input with compute.
+ * Errors: INVALID_ARG (null buffer, a second stage before a commit, a commit with nothing
+ * staged), OUT_OF_MEMORY, CUDA. */
+int gsis_stage_distributions(gsis_ctx *ctx, const void *f, const void *I);
+int gsis_commit_staged(gsis_ctx *ctx);
+
 /* Recompute the macroscopic fields from the distributions now on the device (the velocity
  * moments of Eq. getmoment and the fields of Section 2, the same pass that follows an
  * upload), asynchronously on the context stream.  In FP32 contexts with tc_moments >= 1

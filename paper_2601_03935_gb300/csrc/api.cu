@@ -40,6 +40,14 @@ struct gsis_ctx {
     // device buffers; Real-typed ones are void* and cast by precision
     void *f[2] = {nullptr, nullptr}, *I[2] = {nullptr, nullptr};
     int cur = 0;
+    // staged uploads (created on first use): a buffer pair with the layout of f[cur] and
+    // I[cur] filled on a copy stream while the context stream computes; stage_ready marks
+    // the copy done, stage_free the point after which the context stream no longer reads
+    // the pair's previous contents
+    void *f_stage = nullptr, *I_stage = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t stage_ready = nullptr, stage_free = nullptr;
+    bool staged = false;
     void *coef = nullptr, *bcoef = nullptr, *partial = nullptr, *opartial = nullptr;
     void *sync_kc = nullptr;                    // FP32: per-cell synchronisation constants [nc][SYNC_KC] floats
     void *slope = nullptr, *oslope = nullptr;   // limited slopes [nc][Vp][dim][4], [nc][Op][dim] (order 2)
@@ -595,6 +603,12 @@ void gsis_destroy(gsis_ctx *ctx) {
         cudaEventDestroy(p.e1);
     }
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    if (ctx->stage_ready) cudaEventDestroy(ctx->stage_ready);
+    if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     if (ctx->macro_exec) cudaGraphExecDestroy(ctx->macro_exec);
     for (void *p : ctx->mlp_alloc) cudaFree(p);
     for (void *p : ctx->allocations) cudaFree(p);
@@ -1098,6 +1112,41 @@ int gsis_upload_distributions(gsis_ctx *c, const void *f, const void *I) {
                                   (size_t)c->nc, cudaMemcpyHostToDevice, c->stream));
     TRY(refresh(c));
     return GSIS_OK;
+}
+
+int gsis_stage_distributions(gsis_ctx *c, const void *f, const void *I) {
+    if (!c || !f || !I) return fail(c, GSIS_ERR_INVALID_ARG, "null buffer");
+    const size_t rs = c->real_size;
+    if (!c->f_stage) {
+        TRY(dalloc_real(c, &c->f_stage, (size_t)c->nc * c->Vp * 4));
+        TRY(dalloc_real(c, &c->I_stage, (size_t)c->nc * c->Op));
+        CUDA_TRY(c, cudaMemsetAsync(c->f_stage, 0, (size_t)c->nc * c->Vp * 4 * rs, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(c->I_stage, 0, (size_t)c->nc * c->Op * rs, c->stream));
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->stage_ready, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->stage_free, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventRecord(c->stage_free, c->stream));
+    }
+    if (c->staged) return fail(c, GSIS_ERR_INVALID_ARG, "a staged upload is pending: commit it first");
+    CUDA_TRY(c, cudaStreamWaitEvent(c->copy_stream, c->stage_free, 0));
+    CUDA_TRY(c, cudaMemcpy2DAsync(c->f_stage, (size_t)c->Vp * 4 * rs, f, (size_t)c->V * 4 * rs, (size_t)c->V * 4 * rs,
+                                  (size_t)c->nc, cudaMemcpyHostToDevice, c->copy_stream));
+    CUDA_TRY(c, cudaMemcpy2DAsync(c->I_stage, (size_t)c->Op * rs, I, (size_t)c->NO * rs, (size_t)c->NO * rs,
+                                  (size_t)c->nc, cudaMemcpyHostToDevice, c->copy_stream));
+    CUDA_TRY(c, cudaEventRecord(c->stage_ready, c->copy_stream));
+    c->staged = true;
+    return GSIS_OK;
+}
+
+int gsis_commit_staged(gsis_ctx *c) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (!c->staged) return fail(c, GSIS_ERR_INVALID_ARG, "nothing staged");
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->stage_ready, 0));
+    std::swap(c->f[c->cur], c->f_stage);
+    std::swap(c->I[c->cur], c->I_stage);
+    CUDA_TRY(c, cudaEventRecord(c->stage_free, c->stream));
+    c->staged = false;
+    return refresh(c);
 }
 
 int gsis_refresh_fields(gsis_ctx *c) {

@@ -91,6 +91,8 @@ def load():
         "gsis_get_distributions": (C.c_int, [vp, _dp, C.c_int64, _dp, C.c_int64]),
         "gsis_upload_distributions": (C.c_int, [vp, vp, vp]),
         "gsis_refresh_fields": (C.c_int, [vp]),
+        "gsis_stage_distributions": (C.c_int, [vp, vp, vp]),
+        "gsis_commit_staged": (C.c_int, [vp]),
         "gsis_get_fields": (C.c_int, [vp, _dp, C.c_int64]),
         "gsis_download_fields_async": (C.c_int, [vp, _dp, C.c_int64]),
         "gsis_step": (C.c_int, [vp, C.c_int32, _dp]),
@@ -216,6 +218,16 @@ def gsis_get_distributions(ctx, n_cells, n_xi, n_omega):
 def gsis_upload_distributions(ctx, f_ptr, I_ptr):
     """Host pointers (ints) to buffers in the storage precision."""
     _check(load().gsis_upload_distributions(ctx, C.c_void_p(f_ptr), C.c_void_p(I_ptr)), ctx)
+
+
+def gsis_stage_distributions(ctx, f_ptr, I_ptr):
+    """Start the asynchronous upload of the next state (host pointers, storage precision)."""
+    _check(load().gsis_stage_distributions(ctx, C.c_void_p(f_ptr), C.c_void_p(I_ptr)), ctx)
+
+
+def gsis_commit_staged(ctx):
+    """Make the staged state current and take its fields (asynchronous on the context stream)."""
+    _check(load().gsis_commit_staged(ctx), ctx)
 
 
 def gsis_refresh_fields(ctx):

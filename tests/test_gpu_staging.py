@@ -1,0 +1,80 @@
+"""Double-buffered uploads (gsis_stage_distributions / gsis_commit_staged): staging the next
+state while a step runs gives exactly the results of plain uploads, and misuse is rejected."""
+import numpy as np
+import pytest
+import torch
+
+import gsis_inputs as gi
+from paper_2601_03935_gb300 import build
+from paper_2601_03935_gb300 import gsis as G
+
+from _ctx import create
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    build.build()
+    G.load()
+
+
+def _states(wl, n):
+    out = []
+    for s in range(n):
+        M = gi.fields.smooth_random_fields(wl.mesh.cell_centroid, 30 + s, u_scale=0.2)
+        f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, wl.dim, wl.model.d_r, wl.model.d_v,
+                                           wl.model.sigma_R, 40 + s, noise=0.02)
+        out.append((torch.from_numpy(f.astype(np.float32)).pin_memory(),
+                    torch.from_numpy(I.astype(np.float32)).pin_memory()))
+    return out
+
+
+def test_staged_pipeline_matches_plain_uploads():
+    wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=13), precision="fp32", order=2, relax_block=16)
+    nc, V, NO = wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]
+    states = _states(wl, 3)
+    stream = torch.cuda.Stream()
+
+    def run(staged):
+        ctx = create(wl, stream.cuda_stream)
+        res = []
+        try:
+            if staged:
+                G.gsis_stage_distributions(ctx, states[0][0].data_ptr(), states[0][1].data_ptr())
+            for k in range(len(states)):
+                if staged:
+                    G.gsis_commit_staged(ctx)
+                    if k + 1 < len(states):      # the next state uploads while this step computes
+                        G.gsis_stage_distributions(ctx, states[k + 1][0].data_ptr(), states[k + 1][1].data_ptr())
+                else:
+                    G.gsis_upload_distributions(ctx, states[k][0].data_ptr(), states[k][1].data_ptr())
+                F0 = G.gsis_get_fields(ctx, nc)
+                eps = G.gsis_step(ctx, G.GSIS_MODE_CIS)
+                f, I = G.gsis_get_distributions(ctx, nc, V, NO)
+                res.append((F0, eps, f, I))
+        finally:
+            G.gsis_destroy(ctx)
+        return res
+
+    plain, piped = run(False), run(True)
+    for (F0a, ea, fa, Ia), (F0b, eb, fb, Ib) in zip(plain, piped):
+        assert np.array_equal(F0a, F0b)
+        assert ea == eb
+        assert np.array_equal(fa, fb) and np.array_equal(Ia, Ib)
+
+
+def test_staging_misuse_is_rejected():
+    wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=4), precision="fp32", order=1, relax_block=16)
+    f, I = _states(wl, 1)[0]
+    ctx = create(wl)
+    try:
+        with pytest.raises(G.GsisError):
+            G.gsis_commit_staged(ctx)                                # nothing staged
+        G.gsis_stage_distributions(ctx, f.data_ptr(), I.data_ptr())
+        with pytest.raises(G.GsisError):
+            G.gsis_stage_distributions(ctx, f.data_ptr(), I.data_ptr())   # a second stage before the commit
+        G.gsis_commit_staged(ctx)
+        assert np.isfinite(G.gsis_step(ctx, G.GSIS_MODE_CIS))
+    finally:
+        G.gsis_destroy(ctx)
