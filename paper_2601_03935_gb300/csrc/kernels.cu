@@ -51,6 +51,14 @@ __device__ __forceinline__ float fexp(float x) { return __expf(x); }
 __device__ __forceinline__ float expm1_r(float x) { return expm1f(x); }
 __device__ __forceinline__ double expm1_r(double x) { return expm1(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
+
+// x^(-DIM/2) of the Maxwellian normalisation (2 pi T)^(-DIM/2), without a general pow.
+template <int DIM>
+__device__ __forceinline__ double pow_neg_half_dim(double x) {
+    if constexpr (DIM == 2) return 1.0 / x;
+    else if constexpr (DIM == 1) return 1.0 / sqrt(x);
+    else return 1.0 / (x * sqrt(x));
+}
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 
@@ -88,7 +96,7 @@ __global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restric
     for (int c = 0; c < 3; ++c) {
         Real *Cc = C + cf::COMP + c * cf::CSZ;
         const double T = Ta[c];
-        Cc[cf::A] = (Real)(alpha[c] * rho * pow(two_pi * T, -0.5 * DIM));
+        Cc[cf::A] = (Real)(alpha[c] * rho * pow_neg_half_dim<DIM>(two_pi * T));
         Cc[cf::B] = (Real)(0.5 / T);
         Cc[cf::T] = (Real)T;
         const double s = 2.0 / (15.0 * T * rho * T);
@@ -138,7 +146,7 @@ __global__ void k_wall_density(Geom<Real> g, Quad<Real> vq, const double *__rest
     if (lane == 0) {
         const double inc = bf_inc[warp];
         const double rho_w = inc < 0.0 ? -out / inc : 0.0;
-        const double norm = pow(6.283185307179586 * patch_T[p], -0.5 * DIM);
+        const double norm = pow_neg_half_dim<DIM>(6.283185307179586 * patch_T[p]);
         bcoef[(size_t)warp * bc::NB + bc::A] = (Real)(rho_w * norm);
     }
 }
@@ -781,8 +789,8 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
     // delta = B_n c_n^2 - B_h c_h^2 formed from per-cell differences taken in FP64, so that
     // its relative accuracy does not degrade as M^{k+1} -> M^{k+1/2}.
     const double *rn = Fn + (size_t)i * NF, *rh = Fh + (size_t)i * NF;
-    const double An = rn[0] * pow(2.0 * 3.14159265358979323846 * rn[4], -0.5 * DIM);
-    const double Ah = rh[0] * pow(2.0 * 3.14159265358979323846 * rh[4], -0.5 * DIM);
+    const double An = rn[0] * pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * rn[4]);
+    const double Ah = rh[0] * pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * rh[4]);
     const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
     const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
     const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
@@ -862,9 +870,8 @@ __global__ void k_sync_coef(int n_cells, ModelDev m, const double *__restrict__ 
     constexpr int MH = 3 - DIM;
     const double *rn = Fn + (size_t)i * NF, *rh = Fh + (size_t)i * NF;
     const double two_pi = 2.0 * 3.14159265358979323846;
-    // rho (2 pi T)^(-DIM/2)
-    const double An = DIM == 2 ? rn[0] / (two_pi * rn[4]) : rn[0] / sqrt(two_pi * rn[4]);
-    const double Ah = DIM == 2 ? rh[0] / (two_pi * rh[4]) : rh[0] / sqrt(two_pi * rh[4]);
+    const double An = rn[0] * pow_neg_half_dim<DIM>(two_pi * rn[4]);
+    const double Ah = rh[0] * pow_neg_half_dim<DIM>(two_pi * rh[4]);
     const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
     const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
     const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
@@ -1079,7 +1086,7 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
     const double *P = g.patch_state + (size_t)pid * 8;
     const double *n = g.bf_n + (size_t)b * 2;
     const double T = P[4], Tr = wall ? P[4] : P[5], Tv = wall ? P[4] : P[6], TR = wall ? P[4] : P[7];
-    const double Aw = pow(2.0 * 3.14159265358979323846 * T, -0.5 * DIM), Bw = 0.5 / T;
+    const double Aw = pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * T), Bw = 0.5 / T;
     double acc[2 * NS + 1];
     for (int k = 0; k < 2 * NS + 1; ++k) acc[k] = 0.0;
     for (int v = threadIdx.x; v < vq.n; v += blockDim.x) {
@@ -1155,6 +1162,7 @@ __global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, co
     double S[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) S[k] = 0.0;
+#pragma unroll 4
     for (int c = 0; c < n_chunks; ++c) {
         const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
 #pragma unroll
@@ -1211,7 +1219,7 @@ __global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, co
     Fn[5] = 2.0 * G1 / (m.d_r * rho);
     Fn[6] = 2.0 * G2 / (m.d_v * rho);
     const double eR = Ph[0];
-    Fn[7] = m.sigma_R > 0.0 ? pow(fmax(eR, 0.0) / (4.0 * m.sigma_R), 0.25) : 0.0;
+    Fn[7] = m.sigma_R > 0.0 ? sqrt(sqrt(fmax(eR, 0.0) / (4.0 * m.sigma_R))) : 0.0;
     // heat fluxes: q_t,a = 1/2 int (c-d)_a ((c-d)^2 F0 + H0)
     //   int (c-d)_a |c-d|^2 F0 = Sc3_a - 2 sum_b d_b Scc_ab - d_a trScc + |d|^2 Sc_a
     //                            + 2 d_a (d . Sc) - rho d_a |d|^2  (Sc = rho d)
@@ -1316,7 +1324,7 @@ __global__ void k_equilibrium(int n_cells, Quad<Real> vq, Quad<Real> oq, ModelDe
     const int i = blockIdx.x;
     const double *M = F + (size_t)i * NF;
     const double rho = M[0], Tt = M[4];
-    const double norm = rho * pow(6.283185307179586 * Tt, -0.5 * DIM);
+    const double norm = rho * pow_neg_half_dim<DIM>(6.283185307179586 * Tt);
     for (int v = threadIdx.x; v < vq.n_pad; v += blockDim.x) {
         double c2 = 0.0;
         for (int a = 0; a < DIM; ++a) {
