@@ -116,8 +116,7 @@ typedef struct {
     int32_t order;              /* 1: first-order upwind residual; 2: Venkatakrishnan-limited
                                    linear reconstruction (Eq. deltaflux_micro)               */
     int32_t relax_block;        /* point relaxation: forward + backward Gauss-Seidel inside
-                                   blocks of this many consecutive cells (1..64; FP64: at
-                                   most 49, the shared memory of one CTA)                   */
+                                   blocks of this many consecutive cells (1..64)            */
     double cfl_meso, cfl_macro; /* pseudo time step dt = CFL dx / (|u| + c_s)              */
     double venkat_K;            /* limiter constant, eps^2 = (K dx)^3                       */
     int32_t n_cis_precond;      /* CIS iterations before GSIS starts                        */

@@ -390,14 +390,19 @@ __global__ void __launch_bounds__(32 * SLOPE_ROWS) k_slopes(Geom<Real> g, int n_
 }
 
 // ------------------------------------------------------------------ the sweep
-// Shared memory of a sweep CTA: the main area (residuals, diagonals, in-block inflow
-// coefficients; with `tc`, at least the tensor-core operand stage, which reuses it after
-// the relaxation), then the chunk's velocities and weights, the in-block neighbour table
-// and the tensor-core control words.  `tc`: an FP32 gas sweep with Geom::tc set.
+// Shared memory of a sweep CTA: the main area (residuals and diagonals per (cell,
+// velocity), S/V times the normal of every in-block neighbour face; with `tc`, at least the
+// tensor-core operand stage, which reuses it after the relaxation), then the chunk's
+// velocities and weights, the in-block neighbour table and the tensor-core control words.
+// `tc`: an FP32 gas sweep with Geom::tc set.
+__host__ __device__ constexpr size_t sweep_face_bytes(int block, size_t real_size) {
+    return ((size_t)block * MAXF * 2 * real_size + 15) / 16 * 16;
+}
 __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, size_t real_size, bool tc) {
-    return (tc && (size_t)block * SV * (planes + 1 + MAXF) * real_size < (size_t)tcm::STAGE_BYTES)
+    return (tc && (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, real_size) <
+                      (size_t)tcm::STAGE_BYTES)
                ? (size_t)tcm::STAGE_BYTES
-               : (size_t)block * SV * (planes + 1 + MAXF) * real_size;
+               : (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, real_size);
 }
 
 // One CTA = one relaxation block of consecutive cells x SV discrete velocities (N = 4 gas
@@ -419,7 +424,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     extern __shared__ unsigned char smem_raw[];
     Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][SV]
     Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] diagonal
-    Real *Ag = Dg + g.block * SV;                                       // [block][MAXF][SV] S/V xi_n, in-block inflow
+    Real *Nf = Dg + g.block * SV;                                       // [block][MAXF][2] S/V n, in-block faces
     constexpr bool TCM = std::is_same<Real, float>::value && N == 4;
     const bool tc = TCM && g.tc;
     Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, sizeof(Real), tc));   // [DIM+1][SV]
@@ -476,18 +481,22 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
         if constexpr (ORDER == 2) slope_at(i, si);
         const int nf = g.info[i].x;
         if (tx == 0)
-            for (int k = 0; k < MAXF; ++k) Lg[l * MAXF + k] = (signed char)(k < nf ? g.fnb[i * MAXF + k].y : -1);
+            for (int k = 0; k < MAXF; ++k) {
+                const int lj = k < nf ? g.fnb[i * MAXF + k].y : -1;
+                Lg[l * MAXF + k] = (signed char)lj;
+                if (lj >= 0) {
+                    const Face<Real> F = load_face(g.fgeo, i, k);
+                    Nf[(l * MAXF + k) * 2] = F.sv * F.n[0];
+                    Nf[(l * MAXF + k) * 2 + 1] = DIM > 1 ? F.sv * F.n[1] : Real(0);
+                }
+            }
 #pragma unroll
         for (int k = 0; k < MAXF; ++k) {
-            if (k >= nf) {
-                Ag[(l * MAXF + k) * SV + tx] = Real(0);
-                continue;
-            }
+            if (k >= nf) continue;
             const Face<Real> F = load_face(g.fgeo, i, k);
             const int2 nl = g.fnb[i * MAXF + k];
             Real xn = xi[0] * F.n[0];
             if constexpr (DIM > 1) xn = fma(xi[1], F.n[1], xn);
-            Ag[(l * MAXF + k) * SV + tx] = (nl.y >= 0 && xn < Real(0)) ? F.sv * xn : Real(0);
             V<Real, N> fv;
             if (xn > Real(0)) {
                 fv = fi;
@@ -545,8 +554,8 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     }
     __syncthreads();
 
-    // ---- 2. Gauss-Seidel inside the block with the first-order operator, from the
-    // coefficients phase 1 left in shared memory (a = S/V xi_n < 0 on in-block inflow faces):
+    // ---- 2. Gauss-Seidel inside the block with the first-order operator; a = S/V xi_n from
+    // the face records phase 1 left in shared memory, used where a < 0 (in-block inflow):
     //   forward  delta*_l = (r_l - sum_{j<l} a delta*_j) / d_l
     //   backward delta_l  = delta*_l - (sum_{j>l} a delta_j) / d_l
     if (ty == 0) {
@@ -556,7 +565,9 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
             for (int k = 0; k < MAXF; ++k) {
                 const int lj = Lg[l * MAXF + k];
                 if (lj < 0 || lj >= l) continue;
-                const Real a = Ag[(l * MAXF + k) * SV + tx];
+                Real a = Nf[(l * MAXF + k) * 2] * xi[0];
+                if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * 2 + 1], xi[1], a);
+                if (!(a < Real(0))) continue;
                 const Vec<Real, N> dj = R[lj * SV + tx];
 #pragma unroll
                 for (int p = 0; p < N; ++p) acc.v[p] = fma(-a, dj.v[p], acc.v[p]);
@@ -574,7 +585,9 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
             for (int k = 0; k < MAXF; ++k) {
                 const int lj = Lg[l * MAXF + k];
                 if (lj <= l) continue;
-                const Real a = Ag[(l * MAXF + k) * SV + tx];
+                Real a = Nf[(l * MAXF + k) * 2] * xi[0];
+                if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * 2 + 1], xi[1], a);
+                if (!(a < Real(0))) continue;
                 const Vec<Real, N> dj = R[lj * SV + tx];
 #pragma unroll
                 for (int p = 0; p < N; ++p) corr[p] = fma(a, dj.v[p], corr[p]);

@@ -97,7 +97,7 @@ def test_fp32_moment_engines(tc, block):
     assert_fields_close(rec1, F1, 1e-5, wl.dim, "moments of f^{k+1}")
 
 
-@pytest.mark.parametrize("block", [1, 5, 49])
+@pytest.mark.parametrize("block", [1, 5, 49, 64])
 def test_block_sizes_and_jacobi(block):
     wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=9), precision="fp64", order=2, relax_block=block)
     f, I = _inputs(wl, 11, "fp64", smooth=True)
