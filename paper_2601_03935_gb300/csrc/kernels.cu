@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     constexpr bool PHOTON = (N == 1);
     extern __shared__ unsigned char smem_raw[];
     Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][SV]
-    Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] diagonal
+    Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] 1 / diagonal
     Real *Nf = Dg + g.block * SV;                                       // [block][MAXF][2] S/V n, in-block faces
     constexpr bool TCM = std::is_same<Real, float>::value && N == 4;
     const bool tc = TCM && g.tc;
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
 #pragma unroll
         for (int p = 0; p < N; ++p) t.v[p] = r.x[p];
         R[l * SV + tx] = t;
-        Dg[l * SV + tx] = d;
+        Dg[l * SV + tx] = Real(1) / d;       // the relaxation multiplies by 1/d
     }
     __syncthreads();
 
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
 #pragma unroll
                 for (int p = 0; p < N; ++p) acc.v[p] = fma(-a, dj.v[p], acc.v[p]);
             }
-            const Real inv = Real(1) / Dg[l * SV + tx];
+            const Real inv = Dg[l * SV + tx];
 #pragma unroll
             for (int p = 0; p < N; ++p) acc.v[p] *= inv;
             R[l * SV + tx] = acc;
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
                 for (int p = 0; p < N; ++p) corr[p] = fma(a, dj.v[p], corr[p]);
             }
             Vec<Real, N> acc = R[l * SV + tx];
-            const Real inv = Real(1) / Dg[l * SV + tx];
+            const Real inv = Dg[l * SV + tx];
 #pragma unroll
             for (int p = 0; p < N; ++p) acc.v[p] = fma(-corr[p], inv, acc.v[p]);
             R[l * SV + tx] = acc;
