@@ -53,11 +53,11 @@ __device__ __forceinline__ double expm1_r(double x) { return expm1(x); }
 __device__ __forceinline__ double fexp(double x) { return exp(x); }
 
 // x^(-DIM/2) of the Maxwellian normalisation (2 pi T)^(-DIM/2), without a general pow.
-template <int DIM>
-__device__ __forceinline__ double pow_neg_half_dim(double x) {
-    if constexpr (DIM == 2) return 1.0 / x;
-    else if constexpr (DIM == 1) return 1.0 / sqrt(x);
-    else return 1.0 / (x * sqrt(x));
+template <int DIM, typename T>
+__device__ __forceinline__ T pow_neg_half_dim(T x) {
+    if constexpr (DIM == 2) return T(1) / x;
+    else if constexpr (DIM == 1) return T(1) / sqrt(x);
+    else return T(1) / (x * sqrt(x));
 }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
@@ -68,12 +68,16 @@ __global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restric
                                const double *__restrict__ cell_dx, Real *__restrict__ coef) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_cells) return;
+    // computed in the storage precision: the coefficients are stored as Real
+    using CT = Real;
     const double *M = F + (size_t)i * NF;
-    const double rho = M[0], Tt = M[4], Tr = M[5], Tv = M[6], TR = M[7];
-    const double dr = m.d_r, dv = m.d_v;
-    const double Ttr = (3.0 * Tt + dr * Tr) / (3.0 + dr);
-    const double Ttv = (3.0 * Tt + dv * Tv) / (3.0 + dv);
+    const CT rho = (CT)M[0], Tt = (CT)M[4], Tr = (CT)M[5], Tv = (CT)M[6];
+    const CT dr = (CT)m.d_r, dv = (CT)m.d_v;
+    const CT Ttr = (CT(3) * Tt + dr * Tr) / (CT(3) + dr);
+    const CT Ttv = (CT(3) * Tt + dv * Tv) / (CT(3) + dv);
     const int MH = 3 - DIM;
+    // the mixed heat fluxes and the radiative sink are differences of nearly equal terms
+    // near equilibrium: they stay FP64
     double q[3][3];  // [mode t,r,v][component]
     for (int a = 0; a < 3; ++a) {
         q[0][a] = M[8 + a];
@@ -83,40 +87,44 @@ __global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restric
     double qa[3][3];  // q0, q1, q2
     for (int r = 0; r < 3; ++r)
         for (int a = 0; a < 3; ++a) qa[r][a] = m.Mix[r * 3 + 0] * q[0][a] + m.Mix[r * 3 + 1] * q[1][a] + m.Mix[r * 3 + 2] * q[2][a];
-    const double alpha[3] = {1.0 - 1.0 / m.Z_r - 1.0 / m.Z_v, 1.0 / m.Z_r, 1.0 / m.Z_v};
-    const double Ta[3] = {Tt, Ttr, Ttv};
-    const double k1[3] = {0.5 * dr * Tr, 0.5 * dr * Ttr, 0.5 * dr * Tr};
-    const double k2[3] = {0.5 * dv * Tv, 0.5 * dv * Tv, 0.5 * dv * Ttv};
+    const CT alpha[3] = {(CT)(1.0 - 1.0 / m.Z_r - 1.0 / m.Z_v), (CT)(1.0 / m.Z_r), (CT)(1.0 / m.Z_v)};
+    const CT Ta[3] = {Tt, Ttr, Ttv};
+    const CT k1[3] = {CT(0.5) * dr * Tr, CT(0.5) * dr * Ttr, CT(0.5) * dr * Tr};
+    const CT k2[3] = {CT(0.5) * dv * Tv, CT(0.5) * dv * Tv, CT(0.5) * dv * Ttv};
     const double *qg0[3] = {q[0], qa[0], qa[0]};
     const double *qg1[3] = {q[1], qa[1], qa[1]};
     const double *qg2[3] = {q[2], qa[2], qa[2]};
     Real *C = coef + (size_t)i * cf::NC;
     for (int a = 0; a < 3; ++a) C[cf::U + a] = (Real)M[1 + a];
-    const double two_pi = 6.283185307179586;
+    const CT two_pi = (CT)6.283185307179586;
     for (int c = 0; c < 3; ++c) {
         Real *Cc = C + cf::COMP + c * cf::CSZ;
-        const double T = Ta[c];
+        const CT T = Ta[c];
         Cc[cf::A] = (Real)(alpha[c] * rho * pow_neg_half_dim<DIM>(two_pi * T));
-        Cc[cf::B] = (Real)(0.5 / T);
+        Cc[cf::B] = (Real)(CT(0.5) / T);
         Cc[cf::T] = (Real)T;
-        const double s = 2.0 / (15.0 * T * rho * T);
+        const CT s = CT(2) / (CT(15) * T * rho * T);
+        const CT irT = CT(1) / (rho * T);
         for (int a = 0; a < 3; ++a) {
-            Cc[cf::Q + a] = (Real)(s * qg0[c][a]);
-            Cc[cf::R1 + a] = (Real)(qg1[c][a] / (rho * T));
-            Cc[cf::R2 + a] = (Real)(qg2[c][a] / (rho * T));
+            Cc[cf::Q + a] = (Real)(s * (CT)qg0[c][a]);
+            Cc[cf::R1 + a] = (Real)((CT)qg1[c][a] * irT);
+            Cc[cf::R2 + a] = (Real)((CT)qg2[c][a] * irT);
         }
         Cc[cf::K1] = (Real)k1[c];
         Cc[cf::K2] = (Real)k2[c];
     }
     (void)MH;
-    const double tau = sqrt(2.0 / 3.141592653589793) * pow(Tt, m.omega - 1.0) * m.Kn / rho;
-    const double keff = m.k_eff_density_scaled ? rho / m.Kn_p : 1.0 / m.Kn_p;
-    const double umag = sqrt(M[1] * M[1] + M[2] * M[2] + M[3] * M[3]);
-    const double eR = 4.0 * m.sigma_R * TR * TR * TR * TR;
-    C[cf::RATE] = (Real)(1.0 / tau);
-    C[cf::INV_DT] = (Real)((umag + sqrt(5.0 * Tt / 3.0)) / (m.cfl_meso * cell_dx[i]));
-    C[cf::SINK] = (Real)(-keff * (4.0 * m.sigma_R * Tv * Tv * Tv * Tv - eR) / rho);
-    C[cf::GR] = (Real)(m.sigma_R * Tv * Tv * Tv * Tv / 3.141592653589793);
+    const CT tau = (CT)(0.7978845608028654 * m.Kn) * pow(Tt, (CT)(m.omega - 1.0)) / rho;   // sqrt(2/pi) Kn
+    const CT keff = m.k_eff_density_scaled ? rho / (CT)m.Kn_p : (CT)(1.0 / m.Kn_p);
+    const CT ux = (CT)M[1], uy = (CT)M[2], uz = (CT)M[3];
+    const CT umag = sqrt(ux * ux + uy * uy + uz * uz);
+    const CT sR = (CT)m.sigma_R;
+    const double Tv8 = M[6], TR8 = M[7];
+    const double sink = 4.0 * m.sigma_R * (Tv8 * Tv8 * Tv8 * Tv8 - TR8 * TR8 * TR8 * TR8);
+    C[cf::RATE] = (Real)(CT(1) / tau);
+    C[cf::INV_DT] = (Real)((umag + sqrt(CT(5) * Tt / CT(3))) / (CT)(m.cfl_meso * cell_dx[i]));
+    C[cf::SINK] = (Real)(-keff * (CT)sink / rho);
+    C[cf::GR] = (Real)(sR * Tv * Tv * Tv * Tv / (CT)3.141592653589793);
     C[cf::KEFF] = (Real)keff;
 }
 
