@@ -134,28 +134,34 @@ template <typename Real, int DIM>
 __global__ void k_wall_density(Geom<Real> g, Quad<Real> vq, const double *__restrict__ patch_T,
                                const double *__restrict__ bf_inc, const int *__restrict__ patch_kind,
                                const Real *__restrict__ f, Real *__restrict__ bcoef) {
-    // one warp per boundary face: the outgoing mass flux of the current f; the incoming
+    // one CTA of WDT threads per boundary face: the outgoing mass flux of the current f,
+    // summed per thread, per warp and then over the warps in a fixed order; the incoming
     // flux of the unit-density wall Maxwellian is a per-face constant (bf_inc)
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (warp >= g.n_bf) return;
-    const int p = g.bf_patch[warp];
+    constexpr int WDT = 128;
+    __shared__ double part[WDT / 32];
+    const int face = blockIdx.x;
+    const int p = g.bf_patch[face];
     if (patch_kind[p] != 0) return;
-    const int cell = g.bf_cell[warp];
+    const int cell = g.bf_cell[face];
     Real n[DIM];
-    for (int a = 0; a < DIM; ++a) n[a] = g.bf_nrm[warp * 3 + a];
+    for (int a = 0; a < DIM; ++a) n[a] = g.bf_nrm[face * 3 + a];
     double out = 0.0;
-    for (int v = lane; v < vq.n_pad; v += 32) {
+#pragma unroll 4
+    for (int v = threadIdx.x; v < vq.n_pad; v += WDT) {
         Real xn = Real(0);
         for (int a = 0; a < DIM; ++a) xn += vq.x[a * vq.n_pad + v] * n[a];
         if (xn > Real(0)) out += (double)(vq.w[v] * xn) * (double)f[((size_t)cell * vq.n_pad + v) * 4];
     }
     for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
-    if (lane == 0) {
-        const double inc = bf_inc[warp];
-        const double rho_w = inc < 0.0 ? -out / inc : 0.0;
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = out;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < WDT / 32; ++w) tot += part[w];
+        const double inc = bf_inc[face];
+        const double rho_w = inc < 0.0 ? -tot / inc : 0.0;
         const double norm = pow_neg_half_dim<DIM>(6.283185307179586 * patch_T[p]);
-        bcoef[(size_t)warp * bc::NB + bc::A] = (Real)(rho_w * norm);
+        bcoef[(size_t)face * bc::NB + bc::A] = (Real)(rho_w * norm);
     }
 }
 
@@ -1385,8 +1391,8 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
                                 const double *patch_T, const double *bf_inc, const int *patch_kind, const Real *f,
                                 Real *bcoef) {
     if (g.n_bf == 0) return cudaSuccess;
-    const int nt = 64, nbk = (g.n_bf * 32 + nt - 1) / nt;
-    GSIS_DISPATCH_DIM(dim, (k_wall_density<Real, DIM><<<nbk, nt, 0, s>>>(g, vq, patch_T, bf_inc, patch_kind, f, bcoef)));
+    GSIS_DISPATCH_DIM(dim, (k_wall_density<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, vq, patch_T, bf_inc, patch_kind, f,
+                                                                             bcoef)));
     return cudaGetLastError();
 }
 
