@@ -188,20 +188,22 @@ def run_reference(args):
     return 0
 
 
-def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=150, inner=400,
+def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=150, inner=100,
                    train_kn=(0.02, 0.05)):
-    """Wall time from a uniform rest state to eps < tol (Section 6 criterion) with GSIS:
-    plain FP64, plain FP32, and FP32 with the learned warm start.  The network is trained
-    on the solver's own samples from runs at other Knudsen numbers; collection and
-    training are timed separately from the solve."""
+    """Wall time from a uniform rest state to eps < tol (Section 6 criterion) with GSIS and
+    the paper's inner budget (100 synthetic iterations, tolerance 1e-7): plain FP64; FP32
+    distributions with tensor-core moments; the same with the synthetic residual side in
+    FP32 for all but the last 16 inner iterations (macro_fp32 = 2); and that with the
+    learned warm start.  The network is trained on the solver's own samples from runs at
+    other Knudsen numbers; collection and training are timed separately from the solve."""
     import torch
     import gsis_inputs as gi
     from paper_2601_03935_gb300 import gsis as G
 
-    def make(prec, k):
+    def make(prec, k, mixed=False):
         wl = gi.workloads.cavity(n_side=n_side, Kn=k, Kn_p=kn_p)
         return gi.workloads.with_solver(wl, precision=prec, order=1, relax_block=16, max_inner=inner,
-                                        n_cis_precond=10)
+                                        n_cis_precond=10, macro_fp32=2 if mixed else 0)
 
     def fresh(wl):
         ctx = create_ctx(wl, stream.cuda_stream)
@@ -210,8 +212,8 @@ def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=15
         torch.cuda.synchronize()
         return ctx
 
-    def run(prec, params=None):
-        wl = make(prec, kn)
+    def run(prec, params=None, mixed=False):
+        wl = make(prec, kn, mixed)
         ctx = fresh(wl)
         try:
             t0 = time.perf_counter()
@@ -231,6 +233,7 @@ def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=15
                        % (2 * n_side * n_side, n_side, n_side, kn, kn_p, inner), "tol": tol}
     out["fp64_plain"] = run("fp64")
     out["fp32_plain"] = run("fp32")
+    out["fp32_mixed"] = run("fp32", mixed=True)
     t0 = time.perf_counter()
     Xs, Ys = [], []
     for k in train_kn:
@@ -253,9 +256,10 @@ def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=15
                 params = G.gsis_mlp_get_params(ctx)
         finally:
             G.gsis_destroy(ctx)
-    out["fp32_learned"] = run("fp32", params)
+    out["fp32_learned"] = run("fp32", params, mixed=True)
     out["fp32_learned"].update({"train_samples": int(sum(x.shape[0] for x in Xs)), "collect_seconds": collect,
                                 "train_seconds": train, "train_loss": loss, "trained_on_Kn": list(train_kn)})
+    out["speedup_fp32_mixed_vs_fp64_plain"] = out["fp64_plain"]["seconds"] / out["fp32_mixed"]["seconds"]
     out["speedup_fp32_learned_vs_fp64_plain"] = out["fp64_plain"]["seconds"] / out["fp32_learned"]["seconds"]
     return out
 

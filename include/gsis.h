@@ -124,10 +124,12 @@ typedef struct {
     double tol_outer, tol_inner;
     double sync_relax;          /* w in f^{k+1} = f^{k+1/2} + w [f_eq(M^{k+1}) - f_eq(M^{k+1/2})],
                                    0 < w <= 1 (Section 3 has w = 1)                          */
-    int32_t macro_fp32;         /* GSIS_FP32 contexts only: 1 evaluates the synthetic
+    int32_t macro_fp32;         /* GSIS_FP32 contexts only: precision of the synthetic
                                    equations' residual side (gradients, fluxes, high-order
-                                   terms, D) in FP32; the relaxation sweeps and norms stay
-                                   FP64.  0 (default): all FP64.                             */
+                                   terms, D); the relaxation sweeps and norms stay FP64.
+                                   0 (default): FP64.  1: FP32.  2: FP32 except the last 16
+                                   inner iterations of every solve and the high-order terms,
+                                   which are FP64.                                           */
     int32_t tc_moments;         /* GSIS_FP32 contexts only: where the gas velocity moments
                                    (Eq. getmoment) are contracted.  0: CUDA cores;
                                    1: tensor cores (split-TF32 tcgen05) in the standalone and

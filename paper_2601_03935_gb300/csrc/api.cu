@@ -73,7 +73,8 @@ struct gsis_ctx {
     int *mlp_idx = nullptr;
     float *mlp_data = nullptr;   // training data on the device
     int64_t mlp_data_cap = 0;
-    int mfp32 = 0;               // FP32 path: residual side of the synthetic equations in FP32
+    int mfp32 = 0;               // FP32 path: residual side of the synthetic equations in FP32 (1), or in
+                                 // FP32 except the last MACRO_TAIL inner iterations (2)
     int tcm = 0;                 // FP32 path: gas moments on tensor cores (1: standalone passes, 2: also the sweep)
     int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
     double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
@@ -88,7 +89,8 @@ struct gsis_ctx {
     MacroState *h_mstate = nullptr;   // pinned: initial state and the polled stop flag
     int last_inner = 0;
     cudaGraphExec_t macro_exec = nullptr;   // POLL inner iterations, captured once
-    int macro_nodes = 0;
+    cudaGraphExec_t macro_exec64 = nullptr; // the same with the FP64 residual side (mixed schedule's tail)
+    int macro_nodes = 0, macro_nodes64 = 0;
 
     bool have_eps = false;
     double last_eps = 0.0;
@@ -335,16 +337,17 @@ QuadD oquad_d(const gsis_ctx *c) { return QuadD{c->NO, c->Op, c->oqd_x, c->oqd_w
 // ||R_0|| or max_inner; returns the index of the buffer that holds the result.  The
 // device stop flag is polled every POLL iterations (one stream synchronisation each).
 // enqueue one inner iteration reading W[w] and writing W[1 - w]; returns a CUDA status
-cudaError_t enqueue_inner(gsis_ctx *c, int w, int *kernels) {
+// fp32: the residual side of this iteration in FP32.
+cudaError_t enqueue_inner(gsis_ctx *c, int w, int fp32, int *kernels) {
     const MacroGeom &g = c->mg;
     const gsis_solver_params &sp = c->solver;
     const int nparts = macro_rpart_count((int)c->nc);
     const int sweeps = std::max(sp.macro_sweeps, 1);
     cudaError_t e;
-    if ((e = launch_macro_grad(c->stream, g, c->order, c->mfp32, c->model, c->mstate, c->W[w], c->mq, c->mgrad, c->mphi)))
+    if ((e = launch_macro_grad(c->stream, g, c->order, fp32, c->model, c->mstate, c->W[w], c->mq, c->mgrad, c->mphi)))
         return e;
-    if ((e = launch_macro_bflux(c->stream, g, c->mfp32, c->model, vquad_d(c), oquad_d(c), c->mstate, c->mq, c->mbf))) return e;
-    if ((e = launch_macro_residual(c->stream, g, c->order, c->mfp32, c->model, sp.cfl_macro, c->mstate, c->W[w], c->mq,
+    if ((e = launch_macro_bflux(c->stream, g, fp32, c->model, vquad_d(c), oquad_d(c), c->mstate, c->mq, c->mbf))) return e;
+    if ((e = launch_macro_residual(c->stream, g, c->order, fp32, c->model, sp.cfl_macro, c->mstate, c->W[w], c->mq,
                                    c->mgrad, c->mphi, c->hot, c->mbf, c->hot_b, c->Rg, c->Dinv, c->gam, c->rpart)))
         return e;
     if ((e = launch_macro_norm(c->stream, nparts, c->rpart, c->mstate, c->mhist))) return e;
@@ -362,56 +365,65 @@ cudaError_t enqueue_inner(gsis_ctx *c, int w, int *kernels) {
 // only every POLL iterations (one stream synchronisation each).  Without kernel
 // profiling, and on a non-default stream, the POLL iterations are a CUDA graph captured
 // once per context.
+// Captures POLL inner iterations (residual side in FP32 when fp32) as one graph.
+int capture_inner(gsis_ctx *c, int fp32, cudaGraphExec_t *exec, int *nodes_out) {
+    constexpr int POLL = 8;
+    cudaGraph_t gr = nullptr;
+    int nodes = 0;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < POLL && e == cudaSuccess; ++k) e = enqueue_inner(c, k & 1, fp32, &nodes);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (gr) cudaGraphDestroy(gr);
+        return fail(c, GSIS_ERR_CUDA, std::string("capture of the synthetic solve: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(exec, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        return fail(c, GSIS_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+    }
+    *nodes_out = nodes;
+    return GSIS_OK;
+}
+
 int macro_solve(gsis_ctx *c, int *w_out) {
     constexpr int POLL = 8;
+    constexpr int MACRO_TAIL = 16;   // FP64 inner iterations that end a mixed-precision solve
     const gsis_solver_params &sp = c->solver;
+    const bool mixed = c->mfp32 == 2;
+    const int fp_main = c->mfp32 != 0 ? 1 : 0;
+    const int tail = mixed ? std::min(MACRO_TAIL, sp.max_inner) : 0;
     c->h_mstate->it = 0;
     c->h_mstate->done = 0;
-    c->h_mstate->max_inner = sp.max_inner;
+    c->h_mstate->max_inner = sp.max_inner - tail;
     c->h_mstate->r0 = 0.0;
     c->h_mstate->rn = 0.0;
     c->h_mstate->tol = sp.tol_inner;
     CUDA_TRY(c, cudaMemcpyAsync(c->mstate, c->h_mstate, sizeof(MacroState), cudaMemcpyHostToDevice, c->stream));
     const bool graph = !c->prof && c->stream != nullptr;
-    if (graph && !c->macro_exec) {
-        cudaGraph_t gr = nullptr;
-        int nodes = 0;
-        CUDA_TRY(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t e = cudaSuccess;
-        for (int k = 0; k < POLL && e == cudaSuccess; ++k) e = enqueue_inner(c, k & 1, &nodes);
-        cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
-        if (e != cudaSuccess || e2 != cudaSuccess) {
-            if (gr) cudaGraphDestroy(gr);
-            return fail(c, GSIS_ERR_CUDA, std::string("capture of the synthetic solve: ") +
-                                              cudaGetErrorString(e != cudaSuccess ? e : e2));
-        }
-        e = cudaGraphInstantiate(&c->macro_exec, gr, 0);
-        cudaGraphDestroy(gr);
-        if (e != cudaSuccess) {
-            c->macro_exec = nullptr;
-            return fail(c, GSIS_ERR_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
-        }
-        c->macro_nodes = nodes;
-    }
-    int w = 0;
-    for (int it = 0; it < sp.max_inner; it += POLL) {
+    if (graph && !c->macro_exec) TRY(capture_inner(c, fp_main, &c->macro_exec, &c->macro_nodes));
+    if (graph && mixed && !c->macro_exec64) TRY(capture_inner(c, 0, &c->macro_exec64, &c->macro_nodes64));
+    // one chunk of POLL inner iterations, then (unless it is the last) a look at the stop flag
+    auto chunk = [&](int fp32, bool poll) -> int {
         if (graph) {
-            CUDA_TRY(c, cudaGraphLaunch(c->macro_exec, c->stream));
-            c->launches += c->macro_nodes;
+            CUDA_TRY(c, cudaGraphLaunch(fp32 ? c->macro_exec : c->macro_exec64, c->stream));
+            c->launches += fp32 ? c->macro_nodes : c->macro_nodes64;
         } else {
             for (int k = 0; k < POLL; ++k) {
-                int nodes = 0;
                 const int wk = k & 1;
                 TRY(launch(c, K_MGRAD, [&] {
-                    return launch_macro_grad(c->stream, c->mg, c->order, c->mfp32, c->model, c->mstate, c->W[wk], c->mq,
+                    return launch_macro_grad(c->stream, c->mg, c->order, fp32, c->model, c->mstate, c->W[wk], c->mq,
                                              c->mgrad, c->mphi);
                 }));
                 TRY(launch(c, K_MBFLUX, [&] {
-                    return launch_macro_bflux(c->stream, c->mg, c->mfp32, c->model, vquad_d(c), oquad_d(c), c->mstate, c->mq,
-                                              c->mbf);
+                    return launch_macro_bflux(c->stream, c->mg, fp32, c->model, vquad_d(c), oquad_d(c), c->mstate,
+                                              c->mq, c->mbf);
                 }));
                 TRY(launch(c, K_MRES, [&] {
-                    return launch_macro_residual(c->stream, c->mg, c->order, c->mfp32, c->model, sp.cfl_macro, c->mstate,
+                    return launch_macro_residual(c->stream, c->mg, c->order, fp32, c->model, sp.cfl_macro, c->mstate,
                                                  c->W[wk], c->mq, c->mgrad, c->mphi, c->hot, c->mbf, c->hot_b, c->Rg,
                                                  c->Dinv, c->gam, c->rpart);
                 }));
@@ -426,16 +438,31 @@ int macro_solve(gsis_ctx *c, int *w_out) {
                                                    c->W[wk], c->Rg, c->Dinv, c->gam, c->dG[sw & 1],
                                                    c->dG[(sw + 1) & 1], c->W[1 - wk]);
                     }));
-                (void)nodes;
             }
         }
-        if (it + POLL < sp.max_inner) {
+        if (poll) {
             CUDA_TRY(c, cudaMemcpyAsync(c->h_mstate, c->mstate, sizeof(MacroState), cudaMemcpyDeviceToHost,
                                         c->stream));
             CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-            if (c->h_mstate->done) break;
+        }
+        return GSIS_OK;
+    };
+    const int main_iters = sp.max_inner - tail;
+    for (int it = 0; it < main_iters; it += POLL) {
+        TRY(chunk(fp_main, it + POLL < main_iters || tail > 0));
+        if ((it + POLL < main_iters || tail > 0) && c->h_mstate->done) break;
+    }
+    if (tail > 0) {
+        // the FP64 residual side for up to `tail` more iterations, from where the FP32 ones stopped
+        c->h_mstate->done = 0;
+        c->h_mstate->max_inner = c->h_mstate->it + tail;
+        CUDA_TRY(c, cudaMemcpyAsync(c->mstate, c->h_mstate, sizeof(MacroState), cudaMemcpyHostToDevice, c->stream));
+        for (int it = 0; it < tail; it += POLL) {
+            TRY(chunk(0, it + POLL < tail));
+            if (it + POLL < tail && c->h_mstate->done) break;
         }
     }
+    int w = 0;
     *w_out = w;   // POLL is even: every chunk ends where it started
     return GSIS_OK;
 }
@@ -461,13 +488,13 @@ int gsis_iteration(gsis_ctx *c) {
         return launch_macro_from_fields(c->stream, c->dim, (int)c->nc, c->model, c->fields_h, c->W[0]);
     }));
     TRY(launch(c, K_MGRAD, [&] {
-        return launch_macro_grad(c->stream, g, 1, c->mfp32, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
+        return launch_macro_grad(c->stream, g, 1, c->mfp32 == 1, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
     }));
     TRY(launch(c, K_MBFLUX, [&] {
-        return launch_macro_bflux(c->stream, g, c->mfp32, c->model, vquad_d(c), oquad_d(c), nullptr, c->mq, c->mbf);
+        return launch_macro_bflux(c->stream, g, c->mfp32 == 1, c->model, vquad_d(c), oquad_d(c), nullptr, c->mq, c->mbf);
     }));
     TRY(launch(c, K_HOT, [&] {
-        return launch_macro_hot(c->stream, g, c->mfp32, c->model, c->fields_h, c->mq, c->mgrad, c->kbf, c->mbf, c->hot,
+        return launch_macro_hot(c->stream, g, c->mfp32 == 1, c->model, c->fields_h, c->mq, c->mgrad, c->kbf, c->mbf, c->hot,
                                 c->hot_b);
     }));
     int w = 0;
@@ -533,6 +560,7 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
         return why = "bad synthetic-equation parameters", GSIS_ERR_INVALID_ARG;
     if (!(sp->sync_relax > 0) || !(sp->sync_relax <= 1)) return why = "sync_relax must be in (0, 1]", GSIS_ERR_INVALID_ARG;
     if (sp->tc_moments < 0 || sp->tc_moments > 2) return why = "tc_moments must be 0, 1 or 2", GSIS_ERR_INVALID_ARG;
+    if (sp->macro_fp32 < 0 || sp->macro_fp32 > 2) return why = "macro_fp32 must be 0, 1 or 2", GSIS_ERR_INVALID_ARG;
     if (!(mp->Kn > 0) || !(mp->Kn_p > 0) || !(mp->sigma_R >= 0) || !(mp->Z_r > 0) || !(mp->Z_v > 0) ||
         !(mp->d_r >= 0) || !(mp->d_v > 0) || !(mp->d_r > 0))
         return why = "bad model parameters", GSIS_ERR_INVALID_ARG;
@@ -610,6 +638,7 @@ void gsis_destroy(gsis_ctx *ctx) {
     if (ctx->stage_ready) cudaEventDestroy(ctx->stage_ready);
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     if (ctx->macro_exec) cudaGraphExecDestroy(ctx->macro_exec);
+    if (ctx->macro_exec64) cudaGraphExecDestroy(ctx->macro_exec64);
     for (void *p : ctx->mlp_alloc) cudaFree(p);
     for (void *p : ctx->allocations) cudaFree(p);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -634,7 +663,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     c->dim = dim;
     c->precision = sp->precision;
     c->real_size = sp->precision == GSIS_FP64 ? 8 : 4;
-    c->mfp32 = sp->precision == GSIS_FP32 && sp->macro_fp32 != 0;
+    c->mfp32 = sp->precision == GSIS_FP32 ? sp->macro_fp32 : 0;
     c->tcm = sp->precision == GSIS_FP32 ? sp->tc_moments : 0;
     c->order = sp->order;
     c->block = sp->relax_block;

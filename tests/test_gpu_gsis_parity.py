@@ -164,10 +164,13 @@ def test_gsis_step_fp32_moment_engines(tc):
     assert_fields_close(rec, Fo, TOL["fp32"], wl.dim, "moments of f^{k+1}")
 
 
-def test_gsis_step_fp32_residual_side():
-    """FP32 contexts may evaluate the synthetic residual side in FP32 (relaxation stays FP64)."""
-    wl = gi.workloads.with_solver(CASES["cavity72"](), precision="fp32", order=2, relax_block=16, max_inner=12,
-                                  tol_inner=0.0, macro_fp32=1)
+@pytest.mark.parametrize("mode", [1, 2])
+def test_gsis_step_fp32_residual_side(mode):
+    """FP32 contexts may evaluate the synthetic residual side in FP32 (relaxation stays FP64):
+    throughout (mode 1), or for all but the last 16 inner iterations (mode 2: 8 FP32 and 16
+    FP64 iterations here)."""
+    wl = gi.workloads.with_solver(CASES["cavity72"](), precision="fp32", order=2, relax_block=16, max_inner=24,
+                                  tol_inner=0.0, macro_fp32=mode)
     f, I = _inputs(wl, 5, "fp32")
     fg, Ig, rec, eps = _run(wl, f, I, 1)
     fo, Io, Fo, eps_o = _oracle(wl, f, I, 1)
