@@ -406,11 +406,13 @@ int macro_solve(gsis_ctx *c, int *w_out) {
     const bool graph = !c->prof && c->stream != nullptr;
     if (graph && !c->macro_exec) TRY(capture_inner(c, fp_main, &c->macro_exec, &c->macro_nodes));
     if (graph && mixed && !c->macro_exec64) TRY(capture_inner(c, 0, &c->macro_exec64, &c->macro_nodes64));
-    // one chunk of POLL inner iterations, then (unless it is the last) a look at the stop flag
-    auto chunk = [&](int fp32, bool poll) -> int {
+    // one chunk of POLL inner iterations (the main phase's precision, or the FP64 tail),
+    // then (unless it is the last) a look at the stop flag
+    auto chunk = [&](bool tail_phase, bool poll) -> int {
+        const int fp32 = tail_phase ? 0 : fp_main;
         if (graph) {
-            CUDA_TRY(c, cudaGraphLaunch(fp32 ? c->macro_exec : c->macro_exec64, c->stream));
-            c->launches += fp32 ? c->macro_nodes : c->macro_nodes64;
+            CUDA_TRY(c, cudaGraphLaunch(tail_phase ? c->macro_exec64 : c->macro_exec, c->stream));
+            c->launches += tail_phase ? c->macro_nodes64 : c->macro_nodes;
         } else {
             for (int k = 0; k < POLL; ++k) {
                 const int wk = k & 1;
@@ -449,7 +451,7 @@ int macro_solve(gsis_ctx *c, int *w_out) {
     };
     const int main_iters = sp.max_inner - tail;
     for (int it = 0; it < main_iters; it += POLL) {
-        TRY(chunk(fp_main, it + POLL < main_iters || tail > 0));
+        TRY(chunk(false, it + POLL < main_iters || tail > 0));
         if ((it + POLL < main_iters || tail > 0) && c->h_mstate->done) break;
     }
     if (tail > 0) {
@@ -458,7 +460,7 @@ int macro_solve(gsis_ctx *c, int *w_out) {
         c->h_mstate->max_inner = c->h_mstate->it + tail;
         CUDA_TRY(c, cudaMemcpyAsync(c->mstate, c->h_mstate, sizeof(MacroState), cudaMemcpyHostToDevice, c->stream));
         for (int it = 0; it < tail; it += POLL) {
-            TRY(chunk(0, it + POLL < tail));
+            TRY(chunk(true, it + POLL < tail));
             if (it + POLL < tail && c->h_mstate->done) break;
         }
     }

@@ -211,3 +211,28 @@ def test_normal_shock_conserves_fluxes_at_convergence():
     up = wl.mesh.patches[0]
     assert abs(fluxes["mass"].mean() - up.rho * up.u[0]) < 1e-2 * up.rho * up.u[0]
     assert abs(fluxes["momentum"].mean() - up.rho * (up.u[0] ** 2 + up.T_t)) < 1e-2 * up.rho * up.u[0] ** 2
+
+
+@pytest.mark.parametrize("precision,mode", [("fp64", 0), ("fp32", 0), ("fp32", 1), ("fp32", 2)])
+def test_graph_path_matches_stepwise_launches(precision, mode):
+    """On a non-default stream the inner loop of the synthetic solve runs as captured CUDA
+    graphs (two of them in the mixed schedule, mode 2); on the default stream it is launched
+    kernel by kernel.  Both orders of work are the same, so the results are identical."""
+    import torch
+    wl = gi.workloads.with_solver(CASES["cavity72"](), precision=precision, order=2, relax_block=16, max_inner=40,
+                                  tol_inner=1e-6, macro_fp32=mode)
+    f, I = _inputs(wl, 7, precision)
+    stream = torch.cuda.Stream()
+    out = []
+    for st in (0, stream.cuda_stream):
+        ctx = create(wl, st)
+        try:
+            G.gsis_set_distributions(ctx, f, I)
+            eps = [G.gsis_step(ctx, G.GSIS_MODE_GSIS) for _ in range(2)]
+            fg, Ig = G.gsis_get_distributions(ctx, wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0])
+            out.append((eps, fg, G.gsis_get_fields(ctx, wl.mesh.n_cells)))
+        finally:
+            G.gsis_destroy(ctx)
+    (ea, fa, Fa), (eb, fb, Fb) = out
+    assert ea == eb
+    assert np.array_equal(fa, fb) and np.array_equal(Fa, Fb)
