@@ -50,7 +50,7 @@ struct gsis_ctx {
     bool staged = false;
     void *coef = nullptr, *bcoef = nullptr, *partial = nullptr, *opartial = nullptr;
     void *sync_kc = nullptr;                    // FP32: per-cell synchronisation constants [nc][SYNC_KC] floats
-    void *slope = nullptr, *oslope = nullptr;   // limited slopes [nc][Vp][dim][4], [nc][Op][dim] (order 2)
+    void *fface = nullptr, *oface = nullptr;    // upwind face values [n_fi][Vp][4], [n_fi][Op] (order 2)
     double *fields = nullptr, *fields_old = nullptr, *eps_terms = nullptr, *eps_sums = nullptr;
     int *err = nullptr;
     double *vol = nullptr, *cell_dx = nullptr;
@@ -164,6 +164,7 @@ Geom<Real> geom(const gsis_ctx *c) {
     g.tc = c->tcm >= 2 && MT % c->block == 0;
     g.info = c->g_info;
     g.fnb = c->g_fnb;
+    g.cface = c->m_cface;
     g.fgeo = (const Real *)c->g_fgeo;
     g.stn = c->g_stn;
     g.lsq = (const Real *)c->g_lsq;
@@ -275,23 +276,24 @@ int kinetic_step(gsis_ctx *c, int nxt) {
     }));
     if (c->order == 2) {
         TRY(launch(c, K_SLOPE_GAS, [&] {
-            return launch_slopes<Real>(c->stream, c->dim, 4, g, c->Vp, (const Real *)c->f[c->cur], (Real *)c->slope);
+            return launch_slopes<Real>(c->stream, c->dim, 4, g, vquad<Real>(c), (const Real *)c->f[c->cur],
+                                       (Real *)c->fface);
         }));
     }
     TRY(launch(c, K_SWEEP_GAS, [&] {
         return launch_sweep_gas<Real>(c->stream, c->dim, c->order, g, vquad<Real>(c), (const Real *)c->coef,
-                                      (const Real *)c->bcoef, (const Real *)c->f[c->cur], (const Real *)c->slope,
+                                      (const Real *)c->bcoef, (const Real *)c->f[c->cur], (const Real *)c->fface,
                                       (Real *)c->f[nxt], (Real *)c->partial);
     }));
     if (c->order == 2) {
         TRY(launch(c, K_SLOPE_PHOTON, [&] {
-            return launch_slopes<Real>(c->stream, c->dim, 1, g, c->Op, (const Real *)c->I[c->cur],
-                                       (Real *)c->oslope);
+            return launch_slopes<Real>(c->stream, c->dim, 1, g, oquad<Real>(c), (const Real *)c->I[c->cur],
+                                       (Real *)c->oface);
         }));
     }
     TRY(launch(c, K_SWEEP_PHOTON, [&] {
         return launch_sweep_photon<Real>(c->stream, c->dim, c->order, g, oquad<Real>(c), (const Real *)c->coef,
-                                         (const Real *)c->bcoef, (const Real *)c->I[c->cur], (const Real *)c->oslope,
+                                         (const Real *)c->bcoef, (const Real *)c->I[c->cur], (const Real *)c->oface,
                                          (Real *)c->I[nxt], (Real *)c->opartial);
     }));
     return GSIS_OK;
@@ -938,8 +940,8 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc_real(c, &c->opartial, (size_t)nc * c->och * NMO));
     if (c->precision == GSIS_FP32) A_(dalloc_real(c, &c->sync_kc, (size_t)nc * SYNC_KC));
     if (c->order == 2) {
-        A_(dalloc_real(c, &c->slope, (size_t)nc * c->Vp * dim * 4));
-        A_(dalloc_real(c, &c->oslope, (size_t)nc * c->Op * dim));
+        A_(dalloc_real(c, &c->fface, fi_i.size() * c->Vp * 4));
+        A_(dalloc_real(c, &c->oface, fi_i.size() * c->Op));
     }
     A_(dalloc(c, &c->fields, (size_t)nc * NF));
     A_(dalloc(c, &c->fields_old, (size_t)nc * NF));

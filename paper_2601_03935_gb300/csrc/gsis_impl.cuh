@@ -62,6 +62,7 @@ struct Geom {
     int tc;                    // FP32 gas sweep: moments on the tensor cores (block divides MT)
     const int4 *info;          // [nc]: faces, stencil size, face neighbours leading the stencil, -
     const int2 *fnb;           // [nc][MAXF]: neighbour (>= 0 cell, < 0: -1 - boundary face), in-block index or -1
+    const int *cface;          // [nc][MAXF]: interior face id (>= 0) or -1 - boundary face
     const Real *fgeo;          // [nc][MAXF][fr::SIZE]
     const int *stn;            // [nc][MAXS] stencil cells, interior face neighbours first
     const Real *lsq;           // [nc][MAXS][2] least-squares weights of the stencil cells
@@ -211,17 +212,18 @@ template <typename Real>
 cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
                                 const double *patch_T, const double *bf_inc, const int *patch_kind,
                                 const Real *f, Real *bcoef);
+// upwind second-order values per (interior face, velocity): fface [n_fi][n_pad][planes]
 template <typename Real>
-cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, int n_pad, const Real *f,
-                          Real *slope);
+cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, const Quad<Real> &q,
+                          const Real *f, Real *fface);
 size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size, bool tc);
 template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
-                             const Real *coef, const Real *bcoef, const Real *f_in, const Real *slope,
+                             const Real *coef, const Real *bcoef, const Real *f_in, const Real *fface,
                              Real *f_out, Real *partial);
 template <typename Real>
 cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
-                                const Real *coef, const Real *bcoef, const Real *I_in, const Real *slope,
+                                const Real *coef, const Real *bcoef, const Real *I_in, const Real *fface,
                                 Real *I_out, Real *partial);
 template <typename Real>
 cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const ModelDev &m,

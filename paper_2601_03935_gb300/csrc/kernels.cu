@@ -4,7 +4,8 @@
 //                 (Section 2.1; Eq. reference_distribution)
 //  wall_density   density of diffusely re-emitted molecules at each wall face
 //  slopes         Venkatakrishnan-limited least-squares slopes of every (cell, velocity)
-//                 for the second-order residual (Eq. deltaflux_micro)
+//                 and the upwind second-order value of every (interior face, velocity)
+//                 that they give, for the residual of Eq. (deltaflux_micro)
 //  sweep_gas      implicit finite-volume kinetic step of Eq. (dis_micro) for the four
 //                 gas planes: upwind (order 1) or limited linear (order 2) residual,
 //                 then forward/backward Gauss-Seidel point relaxation inside a block of
@@ -184,6 +185,63 @@ __device__ __forceinline__ V<Real, N> ldv(const Real *base, size_t idx) {
     return r;
 }
 
+// Per-plane arithmetic.  An even number of FP32 planes runs on the packed FP32x2 pipe,
+// two planes per instruction; each component rounds exactly as the scalar operation.
+template <typename Real, int N>
+__device__ __forceinline__ void vfma(Real c, const V<Real, N> &x, V<Real, N> &acc) {   // acc += c x
+    if constexpr (std::is_same<Real, float>::value && N % 2 == 0) {
+        const float2 cc = make_float2(c, c);
+#pragma unroll
+        for (int p = 0; p < N; p += 2) {
+            const float2 r = __ffma2_rn(cc, make_float2(x.x[p], x.x[p + 1]), make_float2(acc.x[p], acc.x[p + 1]));
+            acc.x[p] = r.x;
+            acc.x[p + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < N; ++p) acc.x[p] = fma(c, x.x[p], acc.x[p]);
+    }
+}
+template <typename Real, int N>
+__device__ __forceinline__ V<Real, N> vadd(const V<Real, N> &a, const V<Real, N> &b) {
+    V<Real, N> r;
+    if constexpr (std::is_same<Real, float>::value && N % 2 == 0) {
+#pragma unroll
+        for (int p = 0; p < N; p += 2) {
+            const float2 t = __fadd2_rn(make_float2(a.x[p], a.x[p + 1]), make_float2(b.x[p], b.x[p + 1]));
+            r.x[p] = t.x;
+            r.x[p + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < N; ++p) r.x[p] = a.x[p] + b.x[p];
+    }
+    return r;
+}
+template <typename Real, int N>
+__device__ __forceinline__ V<Real, N> vmul(const V<Real, N> &a, const V<Real, N> &b) {
+    V<Real, N> r;
+    if constexpr (std::is_same<Real, float>::value && N % 2 == 0) {
+#pragma unroll
+        for (int p = 0; p < N; p += 2) {
+            const float2 t = __fmul2_rn(make_float2(a.x[p], a.x[p + 1]), make_float2(b.x[p], b.x[p + 1]));
+            r.x[p] = t.x;
+            r.x[p + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < N; ++p) r.x[p] = a.x[p] * b.x[p];
+    }
+    return r;
+}
+template <typename Real, int N>
+__device__ __forceinline__ V<Real, N> vsplat(Real c) {
+    V<Real, N> r;
+#pragma unroll
+    for (int p = 0; p < N; ++p) r.x[p] = c;
+    return r;
+}
+
 template <typename Real>
 struct Face {
     Real n[2], sv, svn, df[2], dn[2];
@@ -224,6 +282,11 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
 #pragma unroll
             for (int d = 0; d < DIM; ++d) slope[u][d].x[p] = Real(0);
         }
+    V<Real, N> nfj[VPT];
+#pragma unroll
+    for (int u = 0; u < VPT; ++u)
+#pragma unroll
+        for (int p = 0; p < N; ++p) nfj[u].x[p] = -fj[u].x[p];
     const int4 info = g.info[j];
     const int ns = info.y, nfn = info.z;
     const int *stn = g.stn + (size_t)j * MAXS;
@@ -238,17 +301,18 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
         const Real c0 = lw[2 * k], c1 = DIM > 1 ? lw[2 * k + 1] : Real(0);
         const bool face_nbr = k < nfn;
 #pragma unroll
-        for (int u = 0; u < VPT; ++u)
+        for (int u = 0; u < VPT; ++u) {
+            const V<Real, N> dq = vadd(fs[u], nfj[u]);   // f_s - f_j
+            if (face_nbr) {
 #pragma unroll
-            for (int p = 0; p < N; ++p) {
-                const Real dq = fs[u].x[p] - fj[u].x[p];
-                if (face_nbr) {
-                    dmax[u].x[p] = fmax(dmax[u].x[p], dq);
-                    dmin[u].x[p] = fmin(dmin[u].x[p], dq);
+                for (int p = 0; p < N; ++p) {
+                    dmax[u].x[p] = fmax(dmax[u].x[p], dq.x[p]);
+                    dmin[u].x[p] = fmin(dmin[u].x[p], dq.x[p]);
                 }
-                slope[u][0].x[p] = fma(c0, dq, slope[u][0].x[p]);
-                if constexpr (DIM > 1) slope[u][1].x[p] = fma(c1, dq, slope[u][1].x[p]);
             }
+            vfma(c0, dq, slope[u][0]);
+            if constexpr (DIM > 1) vfma(c1, dq, slope[u][1]);
+        }
     }
     // phi = min(1, min over interior faces of phi_V(Delta_1, Delta_2)).  On the faces with
     // Delta_2 > 0 (Delta_1 = Delta_max >= 0) phi_V >= 1 while Delta_2 <= Delta_1 / 2 and
@@ -270,31 +334,36 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
         const Real *q = g.fgeo + ((size_t)j * MAXF + k) * fr::SIZE + fr::DFX;
         const Real dx0 = q[0], dx1 = DIM > 1 ? q[1] : Real(0);
 #pragma unroll
-        for (int u = 0; u < VPT; ++u)
+        for (int u = 0; u < VPT; ++u) {
+            V<Real, N> d2 = vmul(slope[u][0], vsplat<Real, N>(dx0));
+            if constexpr (DIM > 1) vfma(dx1, slope[u][1], d2);
 #pragma unroll
             for (int p = 0; p < N; ++p) {
-                Real d2 = slope[u][0].x[p] * dx0;
-                if constexpr (DIM > 1) d2 = fma(slope[u][1].x[p], dx1, d2);
-                hi[u].x[p] = fmax(hi[u].x[p], d2);
-                lo[u].x[p] = fmin(lo[u].x[p], d2);
+                hi[u].x[p] = fmax(hi[u].x[p], d2.x[p]);
+                lo[u].x[p] = fmin(lo[u].x[p], d2.x[p]);
             }
+        }
     }
 #pragma unroll
-    for (int u = 0; u < VPT; ++u)
+    for (int u = 0; u < VPT; ++u) {
+        V<Real, N> ph;
 #pragma unroll
         for (int p = 0; p < N; ++p) {
-            Real ph = Real(1);
+            ph.x[p] = Real(1);
             if (hi[u].x[p] > Real(0)) {
                 const Real d1 = dmax[u].x[p], d2 = hi[u].x[p];
-                ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+                ph.x[p] = fmin(ph.x[p], fdiv(fma(d1, d1 + Real(2) * d2, eps2),
+                                             fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
             }
             if (lo[u].x[p] < Real(0)) {
                 const Real d1 = dmin[u].x[p], d2 = lo[u].x[p];
-                ph = fmin(ph, fdiv(fma(d1, d1 + Real(2) * d2, eps2), fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+                ph.x[p] = fmin(ph.x[p], fdiv(fma(d1, d1 + Real(2) * d2, eps2),
+                                             fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
             }
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) slope[u][d].x[p] *= ph;
         }
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) slope[u][d] = vmul(slope[u][d], ph);
+    }
 }
 
 // Reference distribution of the four gas planes at one (cell, velocity).
@@ -367,16 +436,19 @@ __device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Rea
     }
 }
 
-// ------------------------------------------------------------------ limited slopes
+// ------------------------------------------------------------------ upwind face values
 // Thread (tx, ty) of a 32 x SLOPE_ROWS CTA: cell blockIdx.x * SLOPE_ROWS + ty, velocities
-// blockIdx.y * SV + tx + 32 u (u < 2).  Stores the Venkatakrishnan-limited least-squares
-// slope of every plane as slope[(cell * n_pad + v) * DIM + d][plane].  The sweep reads a
-// cell's slope for its outflow faces and a neighbour's for the inflow faces, so each slope
-// is computed once per iteration.
+// blockIdx.y * SV + tx + 32 u (u < 2).  Computes the cell's Venkatakrishnan-limited
+// least-squares slope and, on every interior face through which the velocity leaves the
+// cell (xi . n > 0), the second-order reconstruction f_j + phi grad f_j . (x_f - x_j) of
+// every plane: fface[(face * n_pad + v) * N + plane].  The two cells of a face hold exactly
+// opposite normals, so for each velocity exactly one of them (the upwind one) writes the
+// face's value, and none where xi . n = 0, which the sweep skips.  The sweep reads these
+// values for both its outflow and its inflow interior faces.
 constexpr int SLOPE_ROWS = 8;
 template <typename Real, int N, int DIM>
-__global__ void __launch_bounds__(32 * SLOPE_ROWS) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ f,
-                                                            Real *__restrict__ slope) {
+__global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? 4 : 1) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ xq,
+                                                            const Real *__restrict__ f, Real *__restrict__ fface) {
     constexpr int VPT = SV / 32;
     const int v = blockIdx.y * SV + threadIdx.x;
     const int j = blockIdx.x * SLOPE_ROWS + threadIdx.y;
@@ -387,20 +459,35 @@ __global__ void __launch_bounds__(32 * SLOPE_ROWS) k_slopes(Geom<Real> g, int n_
     for (int u = 0; u < VPT; ++u) fj[u] = ldv<Real, N>(f, idx + 32 * u);
     V<Real, N> sl[VPT][DIM];
     limited_slope<Real, N, DIM, VPT>(g, f, n_pad, j, v, fj, sl);
+    Real xi[VPT][DIM];
 #pragma unroll
     for (int u = 0; u < VPT; ++u)
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            const size_t o = (idx + 32 * u) * DIM + d;
+        for (int a = 0; a < DIM; ++a) xi[u][a] = xq[a * n_pad + v + 32 * u];
+    const int nf = g.info[j].x;
+    for (int k = 0; k < nf; ++k) {
+        const int fid = g.cface[j * MAXF + k];
+        if (fid < 0) continue;
+        const Face<Real> F = load_face(g.fgeo, j, k);
+#pragma unroll
+        for (int u = 0; u < VPT; ++u) {
+            Real xn = xi[u][0] * F.n[0];
+            if constexpr (DIM > 1) xn = fma(xi[u][1], F.n[1], xn);
+            if (!(xn > Real(0))) continue;
+            V<Real, N> fv = fj[u];
+            vfma(F.df[0], sl[u][0], fv);
+            if constexpr (DIM > 1) vfma(F.df[1], sl[u][1], fv);
+            const size_t o = (size_t)fid * n_pad + v + 32 * u;
             if constexpr (N == 1) {
-                slope[o] = sl[u][d].x[0];
+                fface[o] = fv.x[0];
             } else {
                 Vec<Real, N> t;
 #pragma unroll
-                for (int p = 0; p < N; ++p) t.v[p] = sl[u][d].x[p];
-                vstore<Real, N>(slope + o * N, t);
+                for (int p = 0; p < N; ++p) t.v[p] = fv.x[p];
+                vstore<Real, N>(fface + o * N, t);
             }
         }
+    }
 }
 
 // ------------------------------------------------------------------ the sweep
@@ -432,7 +519,7 @@ __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, siz
 template <typename Real, int N, int DIM, int ORDER>
 __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
                                                       const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
-                                                      const Real *__restrict__ slope, Real *__restrict__ f_out,
+                                                      const Real *__restrict__ fface, Real *__restrict__ f_out,
                                                       Real *__restrict__ partial) {
     constexpr bool PHOTON = (N == 1);
     extern __shared__ unsigned char smem_raw[];
@@ -464,11 +551,6 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
         else if (ty == 0 && tx < 32)
             tcm::relinquish();               // CUDA-core epilogue: let further CTAs onto the SM
     }
-    auto slope_at = [&](int c, V<Real, N> (&s)[DIM]) {
-        const size_t idx = (size_t)c * stride + v;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) s[d] = ldv<Real, N>(slope, idx * DIM + d);
-    };
 
     // ---- 1. residuals and diagonals
     for (int l = ty; l < nb; l += SROWS) {
@@ -491,8 +573,6 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
             r.x[3] = fma(cc.v[2], fi.x[0], r.x[3]);
             d = cc.v[1] + rate;
         }
-        V<Real, N> si[DIM];
-        if constexpr (ORDER == 2) slope_at(i, si);
         const int nf = g.info[i].x;
         if (tx == 0)
             for (int k = 0; k < MAXF; ++k) {
@@ -508,57 +588,40 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
         for (int k = 0; k < MAXF; ++k) {
             if (k >= nf) continue;
             const Face<Real> F = load_face(g.fgeo, i, k);
-            const int2 nl = g.fnb[i * MAXF + k];
+            // the neighbour (order 1) or the interior face id (order 2); < 0: -1 - boundary face
+            const int nl = ORDER == 2 ? g.cface[i * MAXF + k] : g.fnb[i * MAXF + k].x;
             Real xn = xi[0] * F.n[0];
             if constexpr (DIM > 1) xn = fma(xi[1], F.n[1], xn);
+            if (xn == Real(0)) continue;
+            if (xn > Real(0)) d = fma(F.sv, xn, d);
             V<Real, N> fv;
-            if (xn > Real(0)) {
+            if (ORDER == 2 && nl >= 0) {
+                // the face's upwind value, whichever side wrote it; the face (and nl) is the
+                // same for the whole warp, so both flow directions share one load
+                fv = ldv<Real, N>(fface, (size_t)nl * stride + v);
+            } else if (xn > Real(0)) {
                 fv = fi;
-                d = fma(F.sv, xn, d);
-                if constexpr (ORDER == 2) {
-                    if (nl.x >= 0) {
-#pragma unroll
-                        for (int p = 0; p < N; ++p) {
-                            fv.x[p] = fma(si[0].x[p], F.df[0], fv.x[p]);
-                            if constexpr (DIM > 1) fv.x[p] = fma(si[1].x[p], F.df[1], fv.x[p]);
-                        }
-                    }
-                }
-            } else if (xn < Real(0)) {
-                if (nl.x < 0) {
-                    const Real *B = bcoef + (size_t)(-1 - nl.x) * bc::NB;
-                    if constexpr (PHOTON) {
-                        fv.x[0] = B[bc::IIN];
-                    } else {
-                        Real c2 = Real(0);
-#pragma unroll
-                        for (int a = 0; a < DIM; ++a) {
-                            const Real c = xi[a] - B[bc::U + a];
-                            c2 = fma(c, c, c2);
-                        }
-                        const Real E = B[bc::A] * fexp(-B[bc::B] * c2);
-                        fv.x[0] = E * B[bc::M0];
-                        fv.x[1] = E * B[bc::MH];
-                        fv.x[2] = E * B[bc::M1];
-                        fv.x[3] = E * B[bc::M2];
-                    }
+            } else if (nl < 0) {
+                const Real *B = bcoef + (size_t)(-1 - nl) * bc::NB;
+                if constexpr (PHOTON) {
+                    fv.x[0] = B[bc::IIN];
                 } else {
-                    fv = ldv<Real, N>(f_in, (size_t)nl.x * stride + v);
-                    if constexpr (ORDER == 2) {
-                        V<Real, N> sj[DIM];
-                        slope_at(nl.x, sj);
+                    Real c2 = Real(0);
 #pragma unroll
-                        for (int p = 0; p < N; ++p) {
-                            fv.x[p] = fma(sj[0].x[p], F.dn[0], fv.x[p]);
-                            if constexpr (DIM > 1) fv.x[p] = fma(sj[1].x[p], F.dn[1], fv.x[p]);
-                        }
+                    for (int a = 0; a < DIM; ++a) {
+                        const Real c = xi[a] - B[bc::U + a];
+                        c2 = fma(c, c, c2);
                     }
+                    const Real E = B[bc::A] * fexp(-B[bc::B] * c2);
+                    fv.x[0] = E * B[bc::M0];
+                    fv.x[1] = E * B[bc::MH];
+                    fv.x[2] = E * B[bc::M1];
+                    fv.x[3] = E * B[bc::M2];
                 }
             } else {
-                continue;
+                fv = ldv<Real, N>(f_in, (size_t)nl * stride + v);
             }
-#pragma unroll
-            for (int p = 0; p < N; ++p) r.x[p] = fma(-F.sv * xn, fv.x[p], r.x[p]);
+            vfma(-F.sv * xn, fv, r);
         }
         Vec<Real, N> t;
 #pragma unroll
@@ -1397,19 +1460,20 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
 }
 
 template <typename Real, int N, int DIM>
-static cudaError_t slopes_t(cudaStream_t s, const Geom<Real> &g, int n_pad, const Real *f, Real *slope) {
-    dim3 grid((g.n_cells + SLOPE_ROWS - 1) / SLOPE_ROWS, n_pad / SV), block(32, SLOPE_ROWS);
-    k_slopes<Real, N, DIM><<<grid, block, 0, s>>>(g, n_pad, f, slope);
+static cudaError_t slopes_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *f,
+                            Real *fface) {
+    dim3 grid((g.n_cells + SLOPE_ROWS - 1) / SLOPE_ROWS, q.n_pad / SV), block(32, SLOPE_ROWS);
+    k_slopes<Real, N, DIM><<<grid, block, 0, s>>>(g, q.n_pad, q.x, f, fface);
     return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, int n_pad, const Real *f,
-                          Real *slope) {
+cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, const Quad<Real> &q,
+                          const Real *f, Real *fface) {
     if (planes == 4) {
-        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 4, DIM>(s, g, n_pad, f, slope)));
+        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 4, DIM>(s, g, q, f, fface)));
     } else if (planes == 1) {
-        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 1, DIM>(s, g, n_pad, f, slope)));
+        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 1, DIM>(s, g, q, f, fface)));
     }
     return cudaErrorInvalidValue;
 }
@@ -1421,7 +1485,7 @@ size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size, bool t
 
 template <typename Real, int N, int DIM, int ORDER>
 static cudaError_t sweep_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *coef,
-                           const Real *bcoef, const Real *f_in, const Real *slope, Real *f_out, Real *partial) {
+                           const Real *bcoef, const Real *f_in, const Real *fface, Real *f_out, Real *partial) {
     const bool tc = N == 4 && sizeof(Real) == 4 && g.tc;
     if (g.tc && (MT % g.block != 0)) return cudaErrorInvalidValue;
     const size_t smem = sweep_smem_bytes(g.block, N, DIM, sizeof(Real), tc);
@@ -1429,30 +1493,30 @@ static cudaError_t sweep_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real>
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.n_cells + g.block - 1) / g.block, q.n_pad / SV), block(SV, SROWS);
-    kern<<<grid, block, smem, s>>>(g, q, coef, bcoef, f_in, slope, f_out, partial);
+    kern<<<grid, block, smem, s>>>(g, q, coef, bcoef, f_in, fface, f_out, partial);
     return cudaGetLastError();
 }
 
 template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
-                             const Real *coef, const Real *bcoef, const Real *f_in, const Real *slope, Real *f_out,
+                             const Real *coef, const Real *bcoef, const Real *f_in, const Real *fface, Real *f_out,
                              Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 1>(s, g, vq, coef, bcoef, f_in, slope, f_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 1>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 2>(s, g, vq, coef, bcoef, f_in, slope, f_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 2>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
 
 template <typename Real>
 cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
-                                const Real *coef, const Real *bcoef, const Real *I_in, const Real *slope,
+                                const Real *coef, const Real *bcoef, const Real *I_in, const Real *fface,
                                 Real *I_out, Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 1>(s, g, oq, coef, bcoef, I_in, slope, I_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 1>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 2>(s, g, oq, coef, bcoef, I_in, slope, I_out, partial)));
+        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 2>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
@@ -1553,8 +1617,8 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
     template cudaError_t launch_wall_density<Real>(cudaStream_t, int, const Geom<Real> &, const Quad<Real> &,     \
                                                    const double *, const double *, const int *, const Real *,      \
                                                    Real *);                                                        \
-    template cudaError_t launch_slopes<Real>(cudaStream_t, int, int, const Geom<Real> &, int, const Real *,       \
-                                             Real *);                                                              \
+    template cudaError_t launch_slopes<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,      \
+                                             const Real *, Real *);                                                \
     template cudaError_t launch_sweep_gas<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,    \
                                                 const Real *, const Real *, const Real *, const Real *, Real *,    \
                                                 Real *);                                                           \
