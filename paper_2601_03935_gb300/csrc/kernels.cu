@@ -492,13 +492,21 @@ __global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? 4 : 1) k_
 
 // ------------------------------------------------------------------ the sweep
 // Shared memory of a sweep CTA: the main area (residuals and diagonals per (cell,
-// velocity), S/V times the normal of every in-block neighbour face; with `tc`, at least the
-// tensor-core operand stage, which reuses it after the relaxation), then the chunk's
-// velocities and weights, the in-block neighbour table and the tensor-core control words.
+// velocity), the face records of the block (normal, S/V and upwind source per face), S/V
+// times the normal of every in-block neighbour face; with `tc`, at least the tensor-core
+// operand stage, which reuses it after the relaxation), then the chunk's velocities and
+// weights, the in-block neighbour table and the tensor-core control words.
 // `tc`: an FP32 gas sweep with Geom::tc set.
 __host__ __device__ constexpr size_t sweep_face_bytes(int block, size_t real_size) {
-    return ((size_t)block * MAXF * 2 * real_size + 15) / 16 * 16;
+    return (size_t)block * MAXF * 4 * real_size + ((size_t)block * MAXF * 2 * real_size + 15) / 16 * 16;
 }
+
+// A face's upwind source (int) carried in the last slot of its Real face record, bit for bit.
+__device__ __forceinline__ float int_bits_as(int x, float) { return __int_as_float(x); }
+__device__ __forceinline__ double int_bits_as(int x, double) { return __longlong_as_double((long long)x); }
+__device__ __forceinline__ int bits_as_int(float x) { return __float_as_int(x); }
+__device__ __forceinline__ int bits_as_int(double x) { return (int)__double_as_longlong(x); }
+constexpr int NO_FACE = -2147483647 - 1;
 __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, size_t real_size, bool tc) {
     return (tc && (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, real_size) <
                       (size_t)tcm::STAGE_BYTES)
@@ -509,6 +517,8 @@ __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, siz
 // One CTA = one relaxation block of consecutive cells x SV discrete velocities (N = 4 gas
 // planes) or photon directions (N = 1); thread (tx, ty) = (velocity, row), and the
 // block's cells are dealt to the SROWS rows round-robin.
+//  0. the block's face records and in-block neighbour tables, staged in shared memory by
+//     all threads at once;
 //  1. residual and diagonal of every (cell, velocity) at f^k, independently: upwind
 //     face values are the cell's own reconstruction on outflow faces and the
 //     neighbour's (or the boundary state) on inflow faces;
@@ -517,7 +527,7 @@ __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, siz
 //  3. f^{k+1/2} = f^k + delta, staged in shared memory;
 //  4. velocity moments per (cell, chunk), eight lanes per cell.
 template <typename Real, int N, int DIM, int ORDER>
-__global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
+__global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
                                                       const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
                                                       const Real *__restrict__ fface, Real *__restrict__ f_out,
                                                       Real *__restrict__ partial) {
@@ -525,7 +535,8 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     extern __shared__ unsigned char smem_raw[];
     Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][SV]
     Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] 1 / diagonal
-    Real *Nf = Dg + g.block * SV;                                       // [block][MAXF][2] S/V n, in-block faces
+    Vec<Real, 4> *Fa = reinterpret_cast<Vec<Real, 4> *>(Dg + g.block * SV);   // [block][MAXF] n, S/V, source
+    Real *Nf = reinterpret_cast<Real *>(Fa + g.block * MAXF);           // [block][MAXF][2] S/V n, in-block faces
     constexpr bool TCM = std::is_same<Real, float>::value && N == 4;
     const bool tc = TCM && g.tc;
     Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, sizeof(Real), tc));   // [DIM+1][SV]
@@ -552,11 +563,48 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
             tcm::relinquish();               // CUDA-core epilogue: let further CTAs onto the SM
     }
 
+    // ---- 0. face records: source = interior face id (order 2) or neighbour cell (order 1),
+    // -1 - boundary face, NO_FACE past the cell's faces
+    for (int t = ty * SV + tx; t < nb * MAXF; t += SV * SROWS) {
+        const int l = t / MAXF, k = t - l * MAXF, i = c0 + l;
+        Vec<Real, 4> fa;
+        int lj = -1;
+        if (k < g.info[i].x) {
+            const Face<Real> F = load_face(g.fgeo, i, k);
+            const int2 nb2 = g.fnb[i * MAXF + k];
+            const int src = ORDER == 2 ? g.cface[i * MAXF + k] : nb2.x;
+            fa.v[0] = F.n[0];
+            fa.v[1] = DIM > 1 ? F.n[1] : Real(0);
+            fa.v[2] = F.sv;
+            fa.v[3] = int_bits_as(src, Real(0));
+            lj = nb2.y;
+            if (lj >= 0) {
+                Nf[t * 2] = F.sv * F.n[0];
+                Nf[t * 2 + 1] = DIM > 1 ? F.sv * F.n[1] : Real(0);
+            }
+        } else {
+            fa.v[0] = fa.v[1] = fa.v[2] = Real(0);
+            fa.v[3] = int_bits_as(NO_FACE, Real(0));
+        }
+        Fa[t] = fa;
+        Lg[t] = (signed char)lj;
+    }
+    __syncthreads();
+
     // ---- 1. residuals and diagonals
     for (int l = ty; l < nb; l += SROWS) {
         const int i = c0 + l;
         const Real *C = coef + (size_t)i * cf::NC;
         const V<Real, N> fi = ldv<Real, N>(f_in, (size_t)i * stride + v);
+        // the interior faces' values (order 2: the face's upwind value, whichever side wrote
+        // it; order 1: the neighbour's), issued before the reference distribution so that
+        // their latency overlaps it
+        V<Real, N> fk[MAXF];
+#pragma unroll
+        for (int k = 0; k < MAXF; ++k) {
+            const int src = bits_as_int(Fa[l * MAXF + k].v[3]);
+            if (src >= 0) fk[k] = ldv<Real, N>(ORDER == 2 ? fface : f_in, (size_t)src * stride + v);
+        }
         V<Real, N> r;
         const Vec<Real, 4> cc = vload<Real, 4>(C + cf::RATE);
         Real d;
@@ -573,36 +621,22 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
             r.x[3] = fma(cc.v[2], fi.x[0], r.x[3]);
             d = cc.v[1] + rate;
         }
-        const int nf = g.info[i].x;
-        if (tx == 0)
-            for (int k = 0; k < MAXF; ++k) {
-                const int lj = k < nf ? g.fnb[i * MAXF + k].y : -1;
-                Lg[l * MAXF + k] = (signed char)lj;
-                if (lj >= 0) {
-                    const Face<Real> F = load_face(g.fgeo, i, k);
-                    Nf[(l * MAXF + k) * 2] = F.sv * F.n[0];
-                    Nf[(l * MAXF + k) * 2 + 1] = DIM > 1 ? F.sv * F.n[1] : Real(0);
-                }
-            }
 #pragma unroll
         for (int k = 0; k < MAXF; ++k) {
-            if (k >= nf) continue;
-            const Face<Real> F = load_face(g.fgeo, i, k);
-            // the neighbour (order 1) or the interior face id (order 2); < 0: -1 - boundary face
-            const int nl = ORDER == 2 ? g.cface[i * MAXF + k] : g.fnb[i * MAXF + k].x;
-            Real xn = xi[0] * F.n[0];
-            if constexpr (DIM > 1) xn = fma(xi[1], F.n[1], xn);
+            const Vec<Real, 4> fa = Fa[l * MAXF + k];
+            const int src = bits_as_int(fa.v[3]);
+            if (src == NO_FACE) continue;
+            Real xn = xi[0] * fa.v[0];
+            if constexpr (DIM > 1) xn = fma(xi[1], fa.v[1], xn);
             if (xn == Real(0)) continue;
-            if (xn > Real(0)) d = fma(F.sv, xn, d);
+            if (xn > Real(0)) d = fma(fa.v[2], xn, d);
             V<Real, N> fv;
-            if (ORDER == 2 && nl >= 0) {
-                // the face's upwind value, whichever side wrote it; the face (and nl) is the
-                // same for the whole warp, so both flow directions share one load
-                fv = ldv<Real, N>(fface, (size_t)nl * stride + v);
+            if (src >= 0 && (ORDER == 2 || xn < Real(0))) {
+                fv = fk[k];
             } else if (xn > Real(0)) {
                 fv = fi;
-            } else if (nl < 0) {
-                const Real *B = bcoef + (size_t)(-1 - nl) * bc::NB;
+            } else {
+                const Real *B = bcoef + (size_t)(-1 - src) * bc::NB;
                 if constexpr (PHOTON) {
                     fv.x[0] = B[bc::IIN];
                 } else {
@@ -618,10 +652,8 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
                     fv.x[2] = E * B[bc::M1];
                     fv.x[3] = E * B[bc::M2];
                 }
-            } else {
-                fv = ldv<Real, N>(f_in, (size_t)nl * stride + v);
             }
-            vfma(-F.sv * xn, fv, r);
+            vfma(-fa.v[2] * xn, fv, r);
         }
         Vec<Real, N> t;
 #pragma unroll
@@ -632,7 +664,7 @@ __global__ void __launch_bounds__(SV * SROWS) k_sweep(Geom<Real> g, Quad<Real> q
     __syncthreads();
 
     // ---- 2. Gauss-Seidel inside the block with the first-order operator; a = S/V xi_n from
-    // the face records phase 1 left in shared memory, used where a < 0 (in-block inflow):
+    // the in-block face records of phase 0, used where a < 0 (in-block inflow):
     //   forward  delta*_l = (r_l - sum_{j<l} a delta*_j) / d_l
     //   backward delta_l  = delta*_l - (sum_{j>l} a delta_j) / d_l
     if (ty == 0) {
