@@ -493,12 +493,14 @@ __global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? 4 : 1) k_
 // ------------------------------------------------------------------ the sweep
 // Shared memory of a sweep CTA: the main area (residuals and diagonals per (cell,
 // velocity), the face records of the block (normal, S/V and upwind source per face), S/V
-// times the normal of every in-block neighbour face; with `tc`, at least the tensor-core
+// times the normal of every in-block neighbour face, the cells' coefficient records; with
+// `tc`, at least the tensor-core
 // operand stage, which reuses it after the relaxation), then the chunk's velocities and
 // weights, the in-block neighbour table and the tensor-core control words.
 // `tc`: an FP32 gas sweep with Geom::tc set.
 __host__ __device__ constexpr size_t sweep_face_bytes(int block, size_t real_size) {
-    return (size_t)block * MAXF * 4 * real_size + ((size_t)block * MAXF * 2 * real_size + 15) / 16 * 16;
+    return (size_t)block * MAXF * 4 * real_size + ((size_t)block * MAXF * 2 * real_size + 31) / 32 * 32 +
+           (size_t)block * cf::NC * real_size;
 }
 
 // A face's upwind source (int) carried in the last slot of its Real face record, bit for bit.
@@ -537,6 +539,8 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
     Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] 1 / diagonal
     Vec<Real, 4> *Fa = reinterpret_cast<Vec<Real, 4> *>(Dg + g.block * SV);   // [block][MAXF] n, S/V, source
     Real *Nf = reinterpret_cast<Real *>(Fa + g.block * MAXF);           // [block][MAXF][2] S/V n, in-block faces
+    Real *sC = reinterpret_cast<Real *>(reinterpret_cast<unsigned char *>(Nf) +
+                                        ((size_t)g.block * MAXF * 2 * sizeof(Real) + 31) / 32 * 32);   // [block][NC]
     constexpr bool TCM = std::is_same<Real, float>::value && N == 4;
     const bool tc = TCM && g.tc;
     Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, sizeof(Real), tc));   // [DIM+1][SV]
@@ -589,21 +593,41 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
         Fa[t] = fa;
         Lg[t] = (signed char)lj;
     }
+    // the block's coefficient records (gas planes; the photon plane reads two words per
+    // cell): consecutive cells, one contiguous run
+    if constexpr (!PHOTON)
+        for (int t = ty * SV + tx; t < nb * (cf::NC / 4); t += SV * SROWS)
+            reinterpret_cast<Vec<Real, 4> *>(sC)[t] = vload<Real, 4>(coef + (size_t)c0 * cf::NC + 4 * t);
     __syncthreads();
 
-    // ---- 1. residuals and diagonals
-    for (int l = ty; l < nb; l += SROWS) {
-        const int i = c0 + l;
-        const Real *C = coef + (size_t)i * cf::NC;
-        const V<Real, N> fi = ldv<Real, N>(f_in, (size_t)i * stride + v);
-        // the interior faces' values (order 2: the face's upwind value, whichever side wrote
-        // it; order 1: the neighbour's), issued before the reference distribution so that
-        // their latency overlaps it
-        V<Real, N> fk[MAXF];
+    // ---- 1. residuals and diagonals.  A cell's loads (its own value and the interior faces'
+    // values: order 2 the face's upwind value, whichever side wrote it; order 1 the
+    // neighbour's) are issued before its reference distribution, and for the single photon
+    // plane, whose registers allow it, one cell ahead.
+    auto issue = [&](int l, V<Real, N> &fi, V<Real, N> (&fk)[MAXF]) {
+        fi = ldv<Real, N>(f_in, (size_t)(c0 + l) * stride + v);
 #pragma unroll
         for (int k = 0; k < MAXF; ++k) {
             const int src = bits_as_int(Fa[l * MAXF + k].v[3]);
-            if (src >= 0) fk[k] = ldv<Real, N>(ORDER == 2 ? fface : f_in, (size_t)src * stride + v);
+            if (src >= 0)
+                fk[k] = ldv<Real, N>(ORDER == 2 ? fface : f_in, (size_t)src * stride + v);
+            else
+                fk[k] = vsplat<Real, N>(Real(0));
+        }
+    };
+    constexpr bool AHEAD = PHOTON;
+    V<Real, N> fi_next, fk_next[MAXF];
+    if (AHEAD && ty < nb) issue(ty, fi_next, fk_next);
+    for (int l = ty; l < nb; l += SROWS) {
+        const Real *C = PHOTON ? coef + (size_t)(c0 + l) * cf::NC : sC + l * cf::NC;
+        V<Real, N> fi, fk[MAXF];
+        if constexpr (AHEAD) {
+            fi = fi_next;
+#pragma unroll
+            for (int k = 0; k < MAXF; ++k) fk[k] = fk_next[k];
+            if (l + SROWS < nb) issue(l + SROWS, fi_next, fk_next);
+        } else {
+            issue(l, fi, fk);
         }
         V<Real, N> r;
         const Vec<Real, 4> cc = vload<Real, 4>(C + cf::RATE);
