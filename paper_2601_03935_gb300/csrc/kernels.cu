@@ -219,6 +219,24 @@ __device__ __forceinline__ V<Real, N> vadd(const V<Real, N> &a, const V<Real, N>
     return r;
 }
 template <typename Real, int N>
+__device__ __forceinline__ V<Real, N> vsub(const V<Real, N> &a, const V<Real, N> &b) {   // a - b
+    V<Real, N> r;
+    if constexpr (std::is_same<Real, float>::value && N % 2 == 0) {
+        // b (-1) + a: the product is exact, so the one rounding is that of a - b
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+        for (int p = 0; p < N; p += 2) {
+            const float2 t = __ffma2_rn(make_float2(b.x[p], b.x[p + 1]), m1, make_float2(a.x[p], a.x[p + 1]));
+            r.x[p] = t.x;
+            r.x[p + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < N; ++p) r.x[p] = a.x[p] - b.x[p];
+    }
+    return r;
+}
+template <typename Real, int N>
 __device__ __forceinline__ V<Real, N> vmul(const V<Real, N> &a, const V<Real, N> &b) {
     V<Real, N> r;
     if constexpr (std::is_same<Real, float>::value && N % 2 == 0) {
@@ -231,6 +249,23 @@ __device__ __forceinline__ V<Real, N> vmul(const V<Real, N> &a, const V<Real, N>
     } else {
 #pragma unroll
         for (int p = 0; p < N; ++p) r.x[p] = a.x[p] * b.x[p];
+    }
+    return r;
+}
+template <typename Real, int N>
+__device__ __forceinline__ V<Real, N> vfmav(const V<Real, N> &a, const V<Real, N> &b, const V<Real, N> &c) {
+    V<Real, N> r;   // a b + c per plane
+    if constexpr (std::is_same<Real, float>::value && N % 2 == 0) {
+#pragma unroll
+        for (int p = 0; p < N; p += 2) {
+            const float2 t = __ffma2_rn(make_float2(a.x[p], a.x[p + 1]), make_float2(b.x[p], b.x[p + 1]),
+                                        make_float2(c.x[p], c.x[p + 1]));
+            r.x[p] = t.x;
+            r.x[p + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < N; ++p) r.x[p] = fma(a.x[p], b.x[p], c.x[p]);
     }
     return r;
 }
@@ -282,11 +317,6 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
 #pragma unroll
             for (int d = 0; d < DIM; ++d) slope[u][d].x[p] = Real(0);
         }
-    V<Real, N> nfj[VPT];
-#pragma unroll
-    for (int u = 0; u < VPT; ++u)
-#pragma unroll
-        for (int p = 0; p < N; ++p) nfj[u].x[p] = -fj[u].x[p];
     const int4 info = g.info[j];
     const int ns = info.y, nfn = info.z;
     const int *stn = g.stn + (size_t)j * MAXS;
@@ -302,7 +332,7 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
         const bool face_nbr = k < nfn;
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
-            const V<Real, N> dq = vadd(fs[u], nfj[u]);   // f_s - f_j
+            const V<Real, N> dq = vsub(fs[u], fj[u]);
             if (face_nbr) {
 #pragma unroll
                 for (int p = 0; p < N; ++p) {
@@ -346,19 +376,40 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
     }
 #pragma unroll
     for (int u = 0; u < VPT; ++u) {
+        // phi_V(d1, d2) = (d1 (d1 + 2 d2) + eps2) / (d1 (d1 + d2) + 2 d2^2 + eps2)
         V<Real, N> ph;
+        if constexpr (std::is_same<Real, float>::value) {
+            // FP32: both bounds of every plane without branches (two planes per packed
+            // instruction); the select keeps 1 where a bound's side does not apply
+            const V<Real, N> e = vsplat<Real, N>(eps2);
+            auto venkat = [&](const V<Real, N> &d1, const V<Real, N> &d2) {
+                const V<Real, N> d2x2 = vadd(d2, d2);
+                const V<Real, N> num = vfmav(d1, vadd(d1, d2x2), e);
+                const V<Real, N> den = vfmav(d1, vadd(d1, d2), vfmav(d2x2, d2, e));
+                V<Real, N> r;
 #pragma unroll
-        for (int p = 0; p < N; ++p) {
-            ph.x[p] = Real(1);
-            if (hi[u].x[p] > Real(0)) {
-                const Real d1 = dmax[u].x[p], d2 = hi[u].x[p];
-                ph.x[p] = fmin(ph.x[p], fdiv(fma(d1, d1 + Real(2) * d2, eps2),
-                                             fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
-            }
-            if (lo[u].x[p] < Real(0)) {
-                const Real d1 = dmin[u].x[p], d2 = lo[u].x[p];
-                ph.x[p] = fmin(ph.x[p], fdiv(fma(d1, d1 + Real(2) * d2, eps2),
-                                             fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+                for (int p = 0; p < N; ++p) r.x[p] = fdiv(num.x[p], den.x[p]);
+                return r;
+            };
+            const V<Real, N> ph_hi = venkat(dmax[u], hi[u]), ph_lo = venkat(dmin[u], lo[u]);
+#pragma unroll
+            for (int p = 0; p < N; ++p)
+                ph.x[p] = fmin(fmin(Real(1), hi[u].x[p] > Real(0) ? ph_hi.x[p] : Real(1)),
+                               lo[u].x[p] < Real(0) ? ph_lo.x[p] : Real(1));
+        } else {
+#pragma unroll
+            for (int p = 0; p < N; ++p) {
+                ph.x[p] = Real(1);
+                if (hi[u].x[p] > Real(0)) {
+                    const Real d1 = dmax[u].x[p], d2 = hi[u].x[p];
+                    ph.x[p] = fmin(ph.x[p], fdiv(fma(d1, d1 + Real(2) * d2, eps2),
+                                                 fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+                }
+                if (lo[u].x[p] < Real(0)) {
+                    const Real d1 = dmin[u].x[p], d2 = lo[u].x[p];
+                    ph.x[p] = fmin(ph.x[p], fdiv(fma(d1, d1 + Real(2) * d2, eps2),
+                                                 fma(d1, d1 + d2, fma(Real(2) * d2, d2, eps2))));
+                }
             }
         }
 #pragma unroll
