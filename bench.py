@@ -38,7 +38,7 @@ import numpy as np  # noqa: E402
 METRIC = "DVM cell-velocity updates/s (% HBM roofline); time-to-steady vs plain FP64 GSIS"
 # DRAM bytes (read + write) of one gas sweep on the 20 000-cell cavity, from the ncu capture
 # summarised in profiles/sweep_gas_cavity20k_order2.md; update it whenever the kernels change.
-SWEEP_TRAFFIC = {("fp32", 2): 297.4e6 + 483.8e6 + 924.6e6 + 263.8e6}
+SWEEP_TRAFFIC = {("fp32", 2): 290.4e6 + 345.7e6 + 753.4e6 + 261.4e6}
 UNIT = "updates/s"
 
 
