@@ -103,3 +103,27 @@ def photon_product(n_polar: int, n_azim: int):
     s = np.sqrt(1.0 - M * M)
     om = np.stack([(s * np.cos(P)).ravel(), (s * np.sin(P)).ravel(), M.ravel()], axis=1)
     return om, (W[0] * W[1]).ravel()
+
+
+def disc_velocity_mesh(n_rings: int, r_max: float, stretch: float = 1.5, seed: int = 0):
+    """Unstructured 2-D velocity mesh on the disc |xi| <= r_max (no tensor product).
+
+    The disc is cut into n_rings annuli with edges r_k = r_max (k / n_rings)^stretch, so
+    that the rings cluster near low speeds. Annulus k is cut into n_k ~ 2 pi r_mid / dr
+    near-square sectors, and each ring is rotated by a seeded offset. A point sits at its
+    sector's area centroid and carries the sector's area. The rule is therefore exact for
+    polynomials of degree one on every sector, and its weights sum to pi r_max^2.
+    """
+    rng = np.random.default_rng(seed)
+    edges = r_max * (np.arange(n_rings + 1) / n_rings) ** stretch
+    pts, ws = [], []
+    for k in range(n_rings):
+        a, b = edges[k], edges[k + 1]
+        n = max(6, int(round(np.pi * (a + b) / (b - a))))
+        dth = 2.0 * np.pi / n
+        # area-centroid radius of an annular sector of opening angle dth
+        rc = (2.0 / 3.0) * (b ** 3 - a ** 3) / (b ** 2 - a ** 2) * np.sin(0.5 * dth) / (0.5 * dth)
+        th = (np.arange(n) + 0.5 + rng.uniform(-0.5, 0.5)) * dth
+        pts.append(np.stack([rc * np.cos(th), rc * np.sin(th)], axis=1))
+        ws.append(np.full(n, 0.5 * (b * b - a * a) * dth))
+    return np.concatenate(pts), np.concatenate(ws)

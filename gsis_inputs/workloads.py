@@ -84,12 +84,20 @@ def cavity(n_side: int = 100, n_v: int = 28, n_polar: int = 8, n_azim: int = 8, 
 
     The n_v x n_v uniform velocity grid spans +-(|u_lid| + 5 sqrt(T_lid)) with the
     composite closed Newton-Cotes rule of degree one (trapezoid) by default; "nc38"
-    selects the composite 3/8 rule."""
+    selects the composite 3/8 rule, and "disc" an unstructured mesh of n_v rings on the
+    disc of that radius (no tensor product)."""
     m = _mesh.cavity_triangles(n_side, seed=seed, patches=[
         _mesh.Patch(_mesh.WALL, T_t=1.0), _mesh.Patch(_mesh.WALL, T_t=1.0),
         _mesh.Patch(_mesh.WALL, u=(u_lid, 0.0, 0.0), T_t=T_lid), _mesh.Patch(_mesh.WALL, T_t=1.0)])
     L = abs(u_lid) + 5.0 * np.sqrt(max(T_lid, 1.0))
-    xi, w = _q.trapezoid_nd(n_v, L, 2) if rule == "trapezoid" else _q.newton_cotes_2d(n_v, L)
+    if rule == "trapezoid":
+        xi, w = _q.trapezoid_nd(n_v, L, 2)
+    elif rule == "nc38":
+        xi, w = _q.newton_cotes_2d(n_v, L)
+    elif rule == "disc":
+        xi, w = _q.disc_velocity_mesh(n_v, L, stretch=1.3, seed=seed)
+    else:
+        raise ValueError("unknown velocity rule %r" % rule)
     om, wo = _q.photon_product(n_polar, n_azim)
     return Workload("cavity%d" % (2 * n_side * n_side), m, xi, w, om, wo,
                     ModelParams(Kn=Kn, Kn_p=Kn_p, sigma_R=sigma_R))

@@ -42,6 +42,8 @@ CASES = {
     "slab16": lambda: gi.workloads.slab(16, Kn=0.05),
     # 72 triangles, heated moving lid: 2-D walls, a ragged relaxation block
     "cavity72": lambda: gi.workloads.cavity(n_side=6, Kn=0.05, Kn_p=1.0),
+    # the same cavity on an unstructured disc velocity mesh (245 velocities, no tensor product)
+    "cavity72_disc": lambda: gi.workloads.cavity(n_side=6, n_v=10, Kn=0.05, Kn_p=1.0, rule="disc"),
     # 64 triangles around a cylinder: a far-field patch (no mass rescaling)
     "cylinder64": lambda: gi.workloads.cylinder(n_theta=8, n_radial=4, n_v=16, n_polar=4, n_azim=8, Mach=0.5,
                                                 Kn=0.05, Kn_p=1.0),

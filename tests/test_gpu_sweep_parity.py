@@ -56,6 +56,9 @@ CASES = {
     # 338 cells: 21 blocks of 16 and a ragged block of 2; 784 velocities: 12 full chunks
     # of 64 and a ragged one; 64 photon directions
     "cavity338": lambda: gi.workloads.cavity(n_side=13),
+    # the same mesh on an unstructured disc velocity mesh: 477 velocities (7 full chunks
+    # and a ragged one), no tensor product
+    "cavity338_disc": lambda: gi.workloads.cavity(n_side=13, n_v=14, rule="disc"),
     # 64 cells, 32 Gauss-Hermite velocities and 16 photon directions (one ragged chunk each)
     "slab64": lambda: gi.workloads.slab(64),
 }
