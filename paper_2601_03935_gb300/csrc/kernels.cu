@@ -489,7 +489,7 @@ __device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Rea
 
 // ------------------------------------------------------------------ upwind face values
 // Thread (tx, ty) of a 32 x SLOPE_ROWS CTA: cell blockIdx.x * SLOPE_ROWS + ty, velocities
-// blockIdx.y * SV + tx + 32 u (u < 2).  Computes the cell's Venkatakrishnan-limited
+// blockIdx.y * 32 SLOPE_VPT + tx + 32 u (u < SLOPE_VPT).  Computes the cell's Venkatakrishnan-limited
 // least-squares slope and, on every interior face through which the velocity leaves the
 // cell (xi . n > 0), the second-order reconstruction f_j + phi grad f_j . (x_f - x_j) of
 // every plane: fface[(face * n_pad + v) * N + plane].  The two cells of a face hold exactly
@@ -497,11 +497,13 @@ __device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Rea
 // face's value, and none where xi . n = 0, which the sweep skips.  The sweep reads these
 // values for both its outflow and its inflow interior faces.
 constexpr int SLOPE_ROWS = 8;
+constexpr int SLOPE_VPT = 2;                      // velocities per thread (32 SLOPE_VPT per row)
+constexpr int SLOPE_MINB = SLOPE_VPT == 1 ? 6 : 4; // FP32 CTAs per SM the registers allow
 template <typename Real, int N, int DIM>
-__global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? 4 : 1) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ xq,
+__global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? SLOPE_MINB : 1) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ xq,
                                                             const Real *__restrict__ f, Real *__restrict__ fface) {
-    constexpr int VPT = SV / 32;
-    const int v = blockIdx.y * SV + threadIdx.x;
+    constexpr int VPT = SLOPE_VPT;
+    const int v = blockIdx.y * (32 * VPT) + threadIdx.x;
     const int j = blockIdx.x * SLOPE_ROWS + threadIdx.y;
     if (j >= g.n_cells) return;
     const size_t idx = (size_t)j * n_pad + v;
@@ -1569,7 +1571,8 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
 template <typename Real, int N, int DIM>
 static cudaError_t slopes_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *f,
                             Real *fface) {
-    dim3 grid((g.n_cells + SLOPE_ROWS - 1) / SLOPE_ROWS, q.n_pad / SV), block(32, SLOPE_ROWS);
+    static_assert(SV % (32 * SLOPE_VPT) == 0, "a row's velocities must tile the padding");
+    dim3 grid((g.n_cells + SLOPE_ROWS - 1) / SLOPE_ROWS, q.n_pad / (32 * SLOPE_VPT)), block(32, SLOPE_ROWS);
     k_slopes<Real, N, DIM><<<grid, block, 0, s>>>(g, q.n_pad, q.x, f, fface);
     return cudaGetLastError();
 }
