@@ -110,6 +110,20 @@ def test_block_sizes_and_jacobi(block):
     assert_planes_close(Ig, Io, 1e-10, "I block=%d" % block)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_zero_normal_velocity(precision):
+    """An odd velocity grid contains xi = 0, where xi . n = 0 on every face: no side writes
+    the face's upwind value and the sweep skips the face (order 2), as the oracle does."""
+    wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=9, n_v=15), precision=precision, order=2,
+                                  relax_block=16)
+    assert np.any(np.all(wl.xi == 0.0, axis=1))
+    f, I = _inputs(wl, 13, precision)
+    _, rec1, fg, Ig, _ = _run(wl, f, I)
+    fo, Io = K.kinetic_sweep(f, I, wl, relax_block=16)
+    assert_planes_close(fg, fo, TOL[precision], "f")
+    assert_planes_close(Ig, Io, TOL[precision], "I")
+
+
 def test_largest_fp32_block():
     wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=9), precision="fp32", order=2, relax_block=64)
     f, I = _inputs(wl, 12, "fp32", smooth=True)
