@@ -1361,19 +1361,25 @@ __global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, co
     double S[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) S[k] = 0.0;
-#pragma unroll 4
+    static_assert(NMP % 4 == 0 && NM <= NMP && NMO == 4 && DIM + 1 <= NMO, "partial records are read as 4-vectors");
+#pragma unroll 2
     for (int c = 0; c < n_chunks; ++c) {
         const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
 #pragma unroll
-        for (int k = 0; k < NM; ++k) S[k] += (double)P[k];
+        for (int q = 0; q < NMP / 4; ++q) {
+            const Vec<Real, 4> p4 = vload<Real, 4>(P + 4 * q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (4 * q + e < NM) S[4 * q + e] += (double)p4.v[e];
+        }
     }
     double Ph[1 + DIM];
 #pragma unroll
     for (int k = 0; k <= DIM; ++k) Ph[k] = 0.0;
     for (int c = 0; c < o_chunks; ++c) {
-        const Real *P = opartial + ((size_t)i * o_chunks + c) * NMO;
+        const Vec<Real, 4> p4 = vload<Real, 4>(opartial + ((size_t)i * o_chunks + c) * NMO);
 #pragma unroll
-        for (int k = 0; k <= DIM; ++k) Ph[k] += (double)P[k];
+        for (int k = 0; k <= DIM; ++k) Ph[k] += (double)p4.v[k];
     }
     // unpack
     int k = 0;
