@@ -192,8 +192,9 @@ def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=15
                    train_kn=(0.02, 0.05)):
     """Wall time from a uniform rest state to eps < tol (Section 6 criterion) with GSIS and
     the paper's inner budget (100 synthetic iterations, tolerance 1e-7): plain FP64; FP32
-    distributions with tensor-core moments; the same with the synthetic residual side in
-    FP32 for all but the last 16 inner iterations (macro_fp32 = 2); and that with the
+    distributions with tensor-core moments; the same with the synthetic residual side and
+    the relaxation's flux increments in FP32 for all but the last 16 inner iterations
+    (macro_fp32 = 2); and that with the
     learned warm start.  The network is trained on the solver's own samples from runs at
     other Knudsen numbers; collection and training are timed separately from the solve."""
     import torch

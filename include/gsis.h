@@ -126,7 +126,9 @@ typedef struct {
                                    0 < w <= 1 (Section 3 has w = 1)                          */
     int32_t macro_fp32;         /* GSIS_FP32 contexts only: precision of the synthetic
                                    equations' residual side (gradients, fluxes, high-order
-                                   terms, D); the relaxation sweeps and norms stay FP64.
+                                   terms, D) and of the neighbours' flux increments in the
+                                   relaxation sweeps; the sweeps' diagonal solves, the
+                                   updates of W and the norms stay FP64.
                                    0 (default): FP64.  1: FP32.  2: FP32 except the last 16
                                    inner iterations of every solve and the high-order terms,
                                    which are FP64.                                           */

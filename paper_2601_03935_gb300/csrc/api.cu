@@ -73,8 +73,9 @@ struct gsis_ctx {
     int *mlp_idx = nullptr;
     float *mlp_data = nullptr;   // training data on the device
     int64_t mlp_data_cap = 0;
-    int mfp32 = 0;               // FP32 path: residual side of the synthetic equations in FP32 (1), or in
-                                 // FP32 except the last MACRO_TAIL inner iterations (2)
+    int mfp32 = 0;               // FP32 path: residual side of the synthetic equations and the
+                                 // relaxation's flux increments in FP32 (1), or that except the
+                                 // last MACRO_TAIL inner iterations (2)
     int tcm = 0;                 // FP32 path: gas moments on tensor cores (1: standalone passes, 2: also the sweep)
     int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
     double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
@@ -354,8 +355,9 @@ cudaError_t enqueue_inner(gsis_ctx *c, int w, int fp32, int *kernels) {
         return e;
     if ((e = launch_macro_norm(c->stream, nparts, c->rpart, c->mstate, c->mhist))) return e;
     for (int sw = 0; sw < sweeps; ++sw)
-        if ((e = launch_macro_jacobi(c->stream, g, c->model, c->mstate, sw == 0, sw == sweeps - 1, c->W[w], c->Rg,
-                                     c->Dinv, c->gam, c->dG[sw & 1], c->dG[(sw + 1) & 1], c->W[1 - w])))
+        if ((e = launch_macro_jacobi(c->stream, g, fp32, c->model, c->mstate, sw == 0, sw == sweeps - 1, c->W[w],
+                                     c->mq, c->Rg, c->Dinv, c->gam, c->dG[sw & 1], c->dG[(sw + 1) & 1],
+                                     c->W[1 - w])))
             return e;
     *kernels += 4 + sweeps - (g.n_bf == 0 ? 1 : 0);
     return cudaSuccess;
@@ -438,9 +440,9 @@ int macro_solve(gsis_ctx *c, int *w_out) {
                 const int sweeps = std::max(sp.macro_sweeps, 1);
                 for (int sw = 0; sw < sweeps; ++sw)
                     TRY(launch(c, K_MJACOBI, [&] {
-                        return launch_macro_jacobi(c->stream, c->mg, c->model, c->mstate, sw == 0, sw == sweeps - 1,
-                                                   c->W[wk], c->Rg, c->Dinv, c->gam, c->dG[sw & 1],
-                                                   c->dG[(sw + 1) & 1], c->W[1 - wk]);
+                        return launch_macro_jacobi(c->stream, c->mg, fp32, c->model, c->mstate, sw == 0,
+                                                   sw == sweeps - 1, c->W[wk], c->mq, c->Rg, c->Dinv, c->gam,
+                                                   c->dG[sw & 1], c->dG[(sw + 1) & 1], c->W[1 - wk]);
                     }));
             }
         }

@@ -153,9 +153,12 @@ cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order,
                                   const double *grad, const double *phi, const double *hot, const double *bflux,
                                   const double *hot_b, double *Rg, double *Dinv, double *gam, double *rpart);
 cudaError_t launch_macro_norm(cudaStream_t s, int n_parts, const double *rpart, MacroState *st, double *history);
-cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const MacroState *st,
-                                int first, int last, const double *W, const double *Rg, const double *Dinv,
-                                const double *gam, const double *dG_in, double *dG_out, double *W_next);
+// one relaxation sweep; fp32: the neighbours' flux increments in FP32 from the primitive
+// state q of W (the diagonal solve and the update stay FP64)
+cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, int fp32, const ModelDev &m,
+                                const MacroState *st, int first, int last, const double *W, const double *q,
+                                const double *Rg, const double *Dinv, const double *gam, const double *dG_in,
+                                double *dG_out, double *W_next);
 cudaError_t launch_macro_mass_rescale(cudaStream_t s, int dim, int n_cells, const double *vol, const double *F_ref,
                                       double *W);
 template <typename Real>

@@ -755,9 +755,55 @@ __global__ void k_macro_norm(int n_parts, const double *__restrict__ rpart, Macr
 constexpr int LPC = 4;
 static_assert(LPC == MAXF, "one lane per cell face");
 
+// F_c(W + dW) . n - F_c(W) . n in FP32, from the primitive state q of W and the increment
+// dW (gas-energy form) without forming either flux: every term is a product of an increment
+// with a state value, so no two nearly equal fluxes are subtracted and the FP32 rounding
+// stays relative to the increment.
+//   rho1 = rho + drho, du = (dm - u drho) / rho1, d(rho |u|^2) = drho |u1|^2 + rho du.(u1 + u),
+//   dp = 2/3 (dEg - der - dev - d(rho |u|^2) / 2),
+//   d(m u_n) = dm u_n1 + rho u du_n, d(u_n X) = du_n X1 + u_n dX.
 template <int DIM>
+__device__ __forceinline__ void flux_increment(const double *q, const double *dW, const double *n,
+                                               const ModelDev &m, float *dF) {
+    constexpr int E = 1 + DIM;
+    const float rho = float(q[0]), T = float(q[E]);
+    const float er = 0.5f * float(m.d_r) * rho * float(q[E + 1]), ev = 0.5f * float(m.d_v) * rho * float(q[E + 2]);
+    float u[DIM], nf[DIM], dm[DIM], un = 0.0f, uu = 0.0f;
+    for (int a = 0; a < DIM; ++a) {
+        u[a] = float(q[1 + a]);
+        nf[a] = float(n[a]);
+        dm[a] = float(dW[1 + a]);
+        un += u[a] * nf[a];
+        uu += u[a] * u[a];
+    }
+    const float p = rho * T, Eg = 1.5f * p + 0.5f * rho * uu + er + ev;
+    const float drho = float(dW[0]), dEg = float(dW[E]), der = float(dW[E + 1]), dev = float(dW[E + 2]);
+    const float inv1 = 1.0f / (rho + drho);
+    float dun = 0.0f, dmn = 0.0f, uu1 = 0.0f, dq = 0.0f;
+    for (int a = 0; a < DIM; ++a) {
+        const float du = (dm[a] - u[a] * drho) * inv1, u1 = u[a] + du;
+        dun += du * nf[a];
+        dmn += dm[a] * nf[a];
+        uu1 += u1 * u1;
+        dq += du * (u1 + u[a]);
+    }
+    const float dK = drho * uu1 + rho * dq;
+    const float dp = (2.0f / 3.0f) * (dEg - der - dev - 0.5f * dK);
+    const float un1 = un + dun;
+    dF[0] = dmn;
+    for (int a = 0; a < DIM; ++a) dF[1 + a] = dm[a] * un1 + rho * u[a] * dun + dp * nf[a];
+    dF[E] = dun * (Eg + dEg + p + dp) + un * (dEg + dp);
+    dF[E + 1] = dun * (er + der) + un * der;
+    dF[E + 2] = dun * (ev + dev) + un * dev;
+    dF[E + 3] = 0.0f;
+}
+
+// R = double: the flux increment as the difference of the two fluxes in FP64; R = float:
+// flux_increment in FP32 (the residual side's FP32 mode)
+template <typename R, int DIM>
 __global__ void __launch_bounds__(128) k_macro_jacobi(MacroGeom g, ModelDev m, const MacroState *__restrict__ st,
                                                       int first, int last, const double *__restrict__ W,
+                                                      const double *__restrict__ qW,
                                                       const double *__restrict__ Rg, const double *__restrict__ Dinv,
                                                       const double *__restrict__ gam,
                                                       const double *__restrict__ dG_in, double *__restrict__ dG_out,
@@ -782,18 +828,27 @@ __global__ void __launch_bounds__(128) k_macro_jacobi(MacroGeom g, ModelDev m, c
             double n[2] = {0.0, 0.0};
             for (int a = 0; a < DIM; ++a) n[a] = own ? g.fi_n[(size_t)fid * 2 + a] : -g.fi_n[(size_t)fid * 2 + a];
             const double *Wo = W + (size_t)o * NVM, *dGo = dG_in + (size_t)o * NVM;
-            double Wp[NV], q0[NV], q1[NV], F0[NV], F1[NV];
-            for (int v = 0; v < NV; ++v) Wp[v] = Wo[v] + dGo[v];
-            Wp[E] += dGo[ER];
-            primitive<double, DIM>(Wo, m, q0);
-            primitive<double, DIM>(Wp, m, q1);
-            convective_flux<double, DIM>(q1, n, m, F1);
-            convective_flux<double, DIM>(q0, n, m, F0);
             const double S = g.fi_S[fid];
             const double gb = gam[((size_t)i * MAXF + k) * 2], gR = gam[((size_t)i * MAXF + k) * 2 + 1];
-            for (int v = 0; v < NV; ++v) {
-                const double G = v == ER ? gb + gR : gb;
-                off[v] = ((F1[v] - F0[v]) - G * dGo[v]) * S;
+            if constexpr (std::is_same<R, double>::value) {
+                double Wp[NV], q0[NV], q1[NV], F0[NV], F1[NV];
+                for (int v = 0; v < NV; ++v) Wp[v] = Wo[v] + dGo[v];
+                Wp[E] += dGo[ER];
+                primitive<double, DIM>(Wo, m, q0);
+                primitive<double, DIM>(Wp, m, q1);
+                convective_flux<double, DIM>(q1, n, m, F1);
+                convective_flux<double, DIM>(q0, n, m, F0);
+                for (int v = 0; v < NV; ++v) {
+                    const double G = v == ER ? gb + gR : gb;
+                    off[v] = ((F1[v] - F0[v]) - G * dGo[v]) * S;
+                }
+            } else {
+                float dF[NV];
+                flux_increment<DIM>(qW + (size_t)o * NVM, dGo, n, m, dF);
+                for (int v = 0; v < NV; ++v) {
+                    const float G = float(v == ER ? gb + gR : gb);
+                    off[v] = double((dF[v] - G * float(dGo[v])) * float(S));
+                }
             }
         }
     }
@@ -933,12 +988,14 @@ cudaError_t launch_macro_norm(cudaStream_t s, int n_parts, const double *rpart, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const MacroState *st,
-                                int first, int last, const double *W, const double *Rg, const double *Dinv,
-                                const double *gam, const double *dG_in, double *dG_out, double *W_next) {
+cudaError_t launch_macro_jacobi(cudaStream_t s, const MacroGeom &g, int fp32, const ModelDev &m,
+                                const MacroState *st, int first, int last, const double *W, const double *q,
+                                const double *Rg, const double *Dinv, const double *gam, const double *dG_in,
+                                double *dG_out, double *W_next) {
     const int nb = (g.n_cells * LPC + 127) / 128;
-    MACRO_DISPATCH(g.dim, (k_macro_jacobi<DIM><<<nb, 128, 0, s>>>(g, m, st, first, last, W, Rg, Dinv, gam, dG_in,
-                                                                   dG_out, W_next)));
+    MACRO_DISPATCH(g.dim, MACRO_DISPATCH_R(fp32, (k_macro_jacobi<R, DIM><<<nb, 128, 0, s>>>(
+                                                     g, m, st, first, last, W, q, Rg, Dinv, gam, dG_in, dG_out,
+                                                     W_next))));
     return cudaGetLastError();
 }
 

@@ -168,7 +168,8 @@ def test_gsis_step_fp32_moment_engines(tc):
 
 @pytest.mark.parametrize("mode", [1, 2])
 def test_gsis_step_fp32_residual_side(mode):
-    """FP32 contexts may evaluate the synthetic residual side in FP32 (relaxation stays FP64):
+    """FP32 contexts may evaluate the synthetic residual side and the relaxation sweeps' flux
+    increments in FP32 (the diagonal solves and updates stay FP64):
     throughout (mode 1), or for all but the last 16 inner iterations (mode 2: 8 FP32 and 16
     FP64 iterations here)."""
     wl = gi.workloads.with_solver(CASES["cavity72"](), precision="fp32", order=2, relax_block=16, max_inner=24,
