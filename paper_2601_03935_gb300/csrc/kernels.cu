@@ -986,7 +986,10 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
     // The correction is the difference of two nearly equal Maxwellians near convergence.
     // It is evaluated as E_h [A_n expm1(-delta) + (A_n - A_h)] with
     // delta = B_n c_n^2 - B_h c_h^2 formed from per-cell differences taken in FP64, so that
-    // its relative accuracy does not degrade as M^{k+1} -> M^{k+1/2}.
+    // its relative accuracy does not degrade as M^{k+1} -> M^{k+1/2}.  Where |delta| >= 1/2
+    // the two Maxwellians differ by a large factor and are subtracted directly,
+    // A_n exp(-B_h c_h^2 - delta) - A_h E_h: far out in velocity E_h underflows while
+    // expm1(-delta) overflows, and their product would be 0 x inf.
     const double *rn = Fn + (size_t)i * NF, *rh = Fh + (size_t)i * NF;
     const double An = rn[0] * pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * rn[4]);
     const double Ah = rh[0] * pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * rh[4]);
@@ -1030,8 +1033,9 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
             }
             const Real Eh = fexp(-Bh_r * c2h);
             const Real delta = Bn_r * dc2 + dB * c2h;
-            const Real d0 = Eh * (An_r * expm1_r(-delta) + dA);  // F0_n - F0_h
             const Real e0h = Ah_r * Eh;                           // F0_h
+            const Real d0 = fabs(delta) < Real(0.5) ? Eh * (An_r * expm1_r(-delta) + dA)
+                                                    : An_r * fexp(-(Bh_r * c2h + delta)) - e0h;   // F0_n - F0_h
 #pragma unroll
             for (int p = 0; p < 4; ++p) fv4.v[p] += w * (mul_n[p] * d0 + dmul[p] * e0h);
             vstore<Real, 4>(fp, fv4);
@@ -1160,7 +1164,8 @@ __global__ void __launch_bounds__(128, 5) k_tc_pass(int n_cells, int n_chunks, i
             for (int j = 0; j < MT / 2; ++j) {
                 const int l = half * (MT / 2) + j, i = tile + l;
                 if (i < n_cells && vg < vq.n) {
-                    // E_h [A_n expm1(-delta) + (A_n - A_h)], delta = B_n c_n^2 - B_h c_h^2
+                    // E_h [A_n expm1(-delta) + (A_n - A_h)], delta = B_n c_n^2 - B_h c_h^2, or
+                    // the direct difference where |delta| >= 1/2 (as in k_sync_gas)
                     const float *Kc = reinterpret_cast<const float *>(kc + l * (SKC / 4));
                     float c2h = 0.f, dc2 = 0.f;
 #pragma unroll
@@ -1171,8 +1176,9 @@ __global__ void __launch_bounds__(128, 5) k_tc_pass(int n_cells, int n_chunks, i
                     }
                     const float Eh = fexp(-Kc[4] * c2h);
                     const float delta = Kc[3] * dc2 + Kc[5] * c2h;
-                    const float d0 = Eh * (Kc[0] * expm1_r(-delta) + Kc[1]);
                     const float e0h = Kc[2] * Eh;
+                    const float d0 = fabsf(delta) < 0.5f ? Eh * (Kc[0] * expm1_r(-delta) + Kc[1])
+                                                         : Kc[0] * fexp(-(Kc[4] * c2h + delta)) - e0h;
 #pragma unroll
                     for (int p = 0; p < 4; ++p)
                         fv[j].v[p] += om * (Kc[6 + 3 * DIM + p] * d0 + Kc[10 + 3 * DIM + p] * e0h);
