@@ -297,6 +297,47 @@ def normal_shock(max_gsis=300):
     return out
 
 
+def cylinder(precond=150, max_iter=12000):
+    """Mach-5 flow past the cylinder (Kn_p = 1000, sigma_R = 0.1, the paper's first column
+    of its cylinder table), 3 072 triangles, 48 x 48 velocities, order 1, FP32 with the
+    mixed synthetic solve: outer iterations and seconds to eps < 1e-6 for CIS alone and
+    for GSIS switched on after `precond` CIS iterations, from the uniform free stream.
+    The paper starts from an Euler solution; from the impulsive start the wake first
+    empties, so GSIS begins once CIS has filled it."""
+    import torch
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import gsis as G
+    paper = {0.1: {"cis": 499, "gsis": 24}, 0.01: {"cis": 9582, "gsis": 25}}
+    out = {}
+    for kn in (0.1, 0.01):
+        base = gi.workloads.cylinder(n_theta=64, n_radial=24, n_v=48, n_polar=4, n_azim=8, Mach=5.0, Kn=kn,
+                                     Kn_p=1000.0, sigma_R=0.1)
+        res = {"cells": base.mesh.n_cells, "n_xi": base.xi.shape[0], "paper_iterations": paper[kn]}
+        for name, n0 in (("cis", max_iter), ("gsis", precond)):
+            wl = gi.workloads.with_solver(base, precision="fp32", order=1, relax_block=16, max_inner=100,
+                                          tol_inner=1e-7, n_cis_precond=n0, macro_fp32=2)
+            M = gi.fields.uniform_fields(wl.mesh.n_cells)
+            far = wl.mesh.patches[1]
+            M[:, 0], M[:, 1], M[:, 4:8] = far.rho, far.u[0], far.T_t
+            f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 2, wl.model.d_r, wl.model.d_v,
+                                               wl.model.sigma_R, 0, noise=0.0)
+            stream = torch.cuda.Stream()
+            ctx = create_ctx(wl, stream.cuda_stream)
+            G.gsis_set_distributions(ctx, f, I)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist = G.gsis_solve(ctx, G.GSIS_MODE_GSIS, max_iter, 1e-6)
+            torch.cuda.synchronize()
+            res[name] = {"iterations": it, "seconds": time.perf_counter() - t0, "final_eps": float(hist[-1]),
+                         "converged": bool(hist[-1] < 1e-6)}
+            if name == "gsis":
+                res[name]["cis_first"] = n0
+            G.gsis_destroy(ctx)
+        res["speedup_seconds"] = res["cis"]["seconds"] / res["gsis"]["seconds"]
+        out["Kn%g" % kn] = res
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2601_03935_gb300 import build
@@ -439,6 +480,8 @@ def run_ours(args):
         line["time_to_steady"] = time_to_steady(stream)
     if not args.no_shock:
         line["normal_shock"] = normal_shock()
+    if not args.no_cylinder:
+        line["cylinder"] = cylinder()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
     print(json.dumps(line))
@@ -468,6 +511,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady measurement")
     ap.add_argument("--no-shock", action="store_true", help="skip the normal-shock convergence measurement")
+    ap.add_argument("--no-cylinder", action="store_true", help="skip the Mach-5 cylinder CIS/GSIS measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
