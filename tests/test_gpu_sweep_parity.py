@@ -170,6 +170,32 @@ def test_full_size_cavity_sampled_blocks():
     assert_planes_close(Ig[cells], Io, 1e-5, "I sampled")
 
 
+def test_twenty_iterations_follow_the_oracle():
+    """Twenty CIS iterations on the 8 x 8 heated-lid cavity at Kn = 1, order 2, FP64: the
+    convergence measure of every iteration and the final distributions equal the oracle's
+    (fields, coefficients and sweeps accumulate over the iterations)."""
+    wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=8, Kn=1.0, Kn_p=10.0), precision="fp64", order=2,
+                                  relax_block=16)
+    M = gi.fields.uniform_fields(wl.mesh.n_cells)
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 2, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, 0,
+                                       noise=0.0)
+    ctx = create(wl)
+    try:
+        G.gsis_set_distributions(ctx, f, I)
+        eps_g = [G.gsis_step(ctx, G.GSIS_MODE_CIS) for _ in range(20)]
+        fg, Ig = G.gsis_get_distributions(ctx, wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0])
+    finally:
+        G.gsis_destroy(ctx)
+    geo = K.Geometry(wl.mesh)
+    eps_o = []
+    for _ in range(20):
+        f, I, e, _ = OG.cis_step(f, I, wl, geo)
+        eps_o.append(e)
+    assert np.allclose(eps_g, eps_o, rtol=1e-9, atol=0.0)
+    assert_planes_close(fg, f, 1e-9, "f after 20 iterations")
+    assert_planes_close(Ig, I, 1e-9, "I after 20 iterations")
+
+
 def test_divergence_is_reported_and_cleared():
     """A non-finite distribution value (injected on the host) makes the next iteration
     report DIVERGED; a following valid state iterates normally again."""
