@@ -309,10 +309,7 @@ int close_iteration(gsis_ctx *c, int nxt) {
     TRY(launch(c, K_FINISH, [&] {
         return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
                                    (const Real *)c->partial, (const Real *)c->opartial, c->vol, c->fields_old,
-                                   c->fields, c->eps_terms, c->err, 1);
-    }));
-    TRY(launch(c, K_EPS, [&] {
-        return launch_eps_reduce(c->stream, (int)c->nc, c->eps_terms, c->eps_part, c->eps_ticket, c->eps_sums);
+                                   c->fields, c->eps_terms, c->err, 1, c->eps_part, c->eps_ticket, c->eps_sums);
     }));
     TRY(launch(c, K_COEF, [&] {
         return launch_coefficients<Real>(c->stream, c->dim, g, c->model, c->fields, c->cell_dx, (Real *)c->coef);
@@ -968,7 +965,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc(c, &c->patch_T, pT.size()));
     A_(dalloc(c, &c->patch_u, pu.size()));
     A_(dalloc(c, &c->bf_inc, (size_t)std::max(c->n_bf, 1)));
-    A_(dalloc(c, &c->eps_part, (size_t)64 * NEPS));
+    A_(dalloc(c, &c->eps_part, (size_t)std::max<int64_t>(64, (nc + 31) / 32) * NEPS));
     A_(dalloc(c, &c->eps_ticket, 1));
     A_(dalloc(c, &c->patch_kind, pk.size()));
     if (cudaMallocHost(&c->h_pinned, (NEPS + 1) * sizeof(double)) != cudaSuccess) return bail(GSIS_ERR_OUT_OF_MEMORY);

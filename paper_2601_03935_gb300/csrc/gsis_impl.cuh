@@ -232,9 +232,8 @@ template <typename Real>
 cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const ModelDev &m,
                           const Real *coef, const Real *partial, const Real *opartial, const double *vol,
                           const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
-                          int have_old);
-cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_part,
-                              unsigned int *ticket, double *eps_sums);
+                          int have_old, double *eps_part = nullptr, unsigned int *ticket = nullptr,
+                          double *eps_sums = nullptr);   // eps_sums: also the convergence sums
 template <typename Real>
 cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
                                const ModelDev &m, const double *fields, Real *f, Real *I);

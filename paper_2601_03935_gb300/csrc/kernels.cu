@@ -12,9 +12,8 @@
 //                 consecutive cells, then the velocity moments of the new distribution
 //                 (Eq. getmoment)
 //  sweep_photon   the same step for the gray intensity I_R
-//  finish         FP64 macroscopic fields from the moment partials, and the per-cell
-//                 terms of the convergence measure of Section 6
-//  eps_reduce     deterministic single-CTA reduction of those terms
+//  finish         FP64 macroscopic fields from the moment partials, and the convergence
+//                 measure of Section 6 (per-cell terms and their deterministic sum)
 //  equilibrium    multi-temperature local equilibrium of given fields
 //  moments_only   velocity moments of the current distributions
 //
@@ -1356,12 +1355,12 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
 // with delta = S_c / rho the flow velocity is u0 + delta and every central moment
 // follows from the binomial shift by delta.
 template <typename Real, int DIM>
-__global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, const Real *__restrict__ coef,
-                         const Real *__restrict__ partial, const Real *__restrict__ opartial,
-                         const double *__restrict__ vol, const double *__restrict__ F_old, double *__restrict__ F_new,
-                         double *__restrict__ eps_terms, int *__restrict__ err, int have_old) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_cells) return;
+__device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, const ModelDev &m,
+                                            const Real *__restrict__ coef, const Real *__restrict__ partial,
+                                            const Real *__restrict__ opartial, const double *__restrict__ vol,
+                                            const double *__restrict__ F_old, double *__restrict__ F_new,
+                                            double *__restrict__ eps_terms, int *__restrict__ err, int have_old,
+                                            double (&E)[NEPS]) {
     constexpr int NM = n_gas_moments<DIM>();
     constexpr int MH = 3 - DIM;
     double S[NM];
@@ -1468,7 +1467,6 @@ __global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, co
     // convergence terms: (drho^2, rho^2, |du|^2, |u|^2, dT^2, T^2, T) * V
     const double V = vol[i];
     const double Ttot = (3.0 * Tt + m.d_r * Fn[5] + m.d_v * Fn[6]) / (3.0 + m.d_r + m.d_v);
-    double *E = eps_terms + (size_t)i * NEPS;
     if (have_old) {
         const double *Fo = F_old + (size_t)i * NF;
         const double To = (3.0 * Fo[4] + m.d_r * Fo[5] + m.d_v * Fo[6]) / (3.0 + m.d_r + m.d_v);
@@ -1488,44 +1486,53 @@ __global__ void k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m, co
     } else {
         for (int q = 0; q < NEPS; ++q) E[q] = 0.0;
     }
+    for (int q = 0; q < NEPS; ++q) eps_terms[(size_t)i * NEPS + q] = E[q];
 }
 
-// Per-CTA partial sums of contiguous cell ranges; the last CTA to finish (counted with an
-// atomic ticket after a fence, no waiting) adds the partials in CTA order, so the result
-// does not depend on scheduling.
-constexpr int EPS_CTAS = 64;
-__global__ void __launch_bounds__(256) k_eps_reduce(int n_cells, const double *__restrict__ terms,
-                                                    double *__restrict__ part, unsigned int *__restrict__ ticket,
-                                                    double *__restrict__ sums) {
-    __shared__ double sh[NEPS][256];
+// One cell per lane, 32-lane CTAs.  With `reduce`, the convergence terms are summed too:
+// each CTA adds its 32 cells in a fixed shuffle order, and the last CTA to finish (counted
+// with an atomic ticket after a fence, no waiting) adds the CTA partials in a fixed order,
+// so the result does not depend on scheduling.
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(32) k_finish(int n_cells, int n_chunks, int o_chunks, ModelDev m,
+                                               const Real *__restrict__ coef, const Real *__restrict__ partial,
+                                               const Real *__restrict__ opartial, const double *__restrict__ vol,
+                                               const double *__restrict__ F_old, double *__restrict__ F_new,
+                                               double *__restrict__ eps_terms, int *__restrict__ err, int have_old,
+                                               int reduce, double *__restrict__ eps_part,
+                                               unsigned int *__restrict__ ticket, double *__restrict__ eps_sums) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    double E[NEPS];
+    for (int q = 0; q < NEPS; ++q) E[q] = 0.0;
+    if (i < n_cells)
+        finish_cell<Real, DIM>(i, n_chunks, o_chunks, m, coef, partial, opartial, vol, F_old, F_new, eps_terms, err,
+                               have_old, E);
+    if (!reduce) return;
+#pragma unroll
+    for (int q = 0; q < NEPS; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) E[q] += __shfl_xor_sync(0xffffffffu, E[q], o);
     __shared__ bool last;
-    const int per = (n_cells + EPS_CTAS - 1) / EPS_CTAS;
-    const int i0 = blockIdx.x * per, i1 = min(n_cells, i0 + per);
-    double acc[NEPS];
-    for (int q = 0; q < NEPS; ++q) acc[q] = 0.0;
-    for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x)
-        for (int q = 0; q < NEPS; ++q) acc[q] += terms[(size_t)i * NEPS + q];
-    for (int q = 0; q < NEPS; ++q) sh[q][threadIdx.x] = acc[q];
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int q = 0; q < NEPS; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        for (int q = 0; q < NEPS; ++q) part[blockIdx.x * NEPS + q] = sh[q][0];
+        for (int q = 0; q < NEPS; ++q) eps_part[(size_t)blockIdx.x * NEPS + q] = E[q];
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x < NEPS) {
-        double s = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile double *)part)[b * NEPS + threadIdx.x];
-        sums[threadIdx.x] = s;
+    double acc[NEPS];
+    for (int q = 0; q < NEPS; ++q) acc[q] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+        for (int q = 0; q < NEPS; ++q) acc[q] += ((volatile double *)eps_part)[(size_t)b * NEPS + q];
+#pragma unroll
+    for (int q = 0; q < NEPS; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NEPS; ++q) eps_sums[q] = acc[q];
+        *ticket = 0u;
     }
-    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // ------------------------------------------------------------------ equilibrium
@@ -1647,19 +1654,16 @@ template <typename Real>
 cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const ModelDev &m,
                           const Real *coef, const Real *partial, const Real *opartial, const double *vol,
                           const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
-                          int have_old) {
+                          int have_old, double *eps_part, unsigned int *ticket, double *eps_sums) {
     const int nt = 32, nbk = (n_cells + nt - 1) / nt;
+    const int reduce = eps_sums != nullptr;
     GSIS_DISPATCH_DIM(dim, (k_finish<Real, DIM><<<nbk, nt, 0, s>>>(n_cells, n_chunks, o_chunks, m, coef, partial,
                                                                     opartial, vol, fields_old, fields_new, eps_terms,
-                                                                    err_flag, have_old)));
+                                                                    err_flag, have_old, reduce, eps_part, ticket,
+                                                                    eps_sums)));
     return cudaGetLastError();
 }
 
-cudaError_t launch_eps_reduce(cudaStream_t s, int n_cells, const double *eps_terms, double *eps_part,
-                              unsigned int *ticket, double *eps_sums) {
-    k_eps_reduce<<<EPS_CTAS, 256, 0, s>>>(n_cells, eps_terms, eps_part, ticket, eps_sums);
-    return cudaGetLastError();
-}
 
 template <typename Real>
 cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
@@ -1749,7 +1753,7 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                                                    Real *);                                                        \
     template cudaError_t launch_finish<Real>(cudaStream_t, int, int, int, int, const ModelDev &, const Real *,     \
                                              const Real *, const Real *, const double *, const double *, double *, \
-                                             double *, int *, int);                                                \
+                                             double *, int *, int, double *, unsigned int *, double *);            \
     template cudaError_t launch_equilibrium<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &,  \
                                                   const ModelDev &, const double *, Real *, Real *);               \
     template cudaError_t launch_moments_only<Real>(cudaStream_t, int, int, bool, const Quad<Real> &,               \
