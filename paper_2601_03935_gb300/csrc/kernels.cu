@@ -1364,18 +1364,45 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
     constexpr int NM = n_gas_moments<DIM>();
     constexpr int MH = 3 - DIM;
     double S[NM];
-#pragma unroll
-    for (int k = 0; k < NM; ++k) S[k] = 0.0;
     static_assert(NMP % 4 == 0 && NM <= NMP && NMO == 4 && DIM + 1 <= NMO, "partial records are read as 4-vectors");
+    if constexpr (std::is_same<Real, float>::value) {
+        // FP32 partials: a compensated FP32 sum (Knuth's two-sum, the rounding error of
+        // every addition carried in lo), as accurate as an FP64 sum of these few terms
+        // and off the slow FP64 pipe
+        float hi[NM], lo[NM];
+#pragma unroll
+        for (int k = 0; k < NM; ++k) hi[k] = lo[k] = 0.0f;
 #pragma unroll 2
-    for (int c = 0; c < n_chunks; ++c) {
-        const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
+        for (int c = 0; c < n_chunks; ++c) {
+            const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
 #pragma unroll
-        for (int q = 0; q < NMP / 4; ++q) {
-            const Vec<Real, 4> p4 = vload<Real, 4>(P + 4 * q);
+            for (int q = 0; q < NMP / 4; ++q) {
+                const Vec<Real, 4> p4 = vload<Real, 4>(P + 4 * q);
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (4 * q + e < NM) S[4 * q + e] += (double)p4.v[e];
+                for (int e = 0; e < 4; ++e)
+                    if (4 * q + e < NM) {
+                        const int k = 4 * q + e;
+                        const float a = hi[k], b = p4.v[e], t = a + b, bv = t - a;
+                        lo[k] += (a - (t - bv)) + (b - bv);
+                        hi[k] = t;
+                    }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NM; ++k) S[k] = (double)hi[k] + (double)lo[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < NM; ++k) S[k] = 0.0;
+#pragma unroll 2
+        for (int c = 0; c < n_chunks; ++c) {
+            const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
+#pragma unroll
+            for (int q = 0; q < NMP / 4; ++q) {
+                const Vec<Real, 4> p4 = vload<Real, 4>(P + 4 * q);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * q + e < NM) S[4 * q + e] += (double)p4.v[e];
+            }
         }
     }
     double Ph[1 + DIM];
@@ -1524,7 +1551,7 @@ __global__ void __launch_bounds__(32) k_finish(int n_cells, int n_chunks, int o_
     double acc[NEPS];
     for (int q = 0; q < NEPS; ++q) acc[q] = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
-        for (int q = 0; q < NEPS; ++q) acc[q] += ((volatile double *)eps_part)[(size_t)b * NEPS + q];
+        for (int q = 0; q < NEPS; ++q) acc[q] += __ldcg(eps_part + (size_t)b * NEPS + q);   // L2: other CTAs' writes
 #pragma unroll
     for (int q = 0; q < NEPS; ++q)
 #pragma unroll
