@@ -13,6 +13,13 @@ triangles, 28 x 28 closed Newton-Cotes (trapezoid) velocity grid, 64 photon dire
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
 workload (the only other place this script runs the oracle).
 
+Further keys of the line (each leg can be skipped with its --no-* flag):
+``time_to_steady``  wall time to eps < 1e-6 on the 32 x 32 cavity: plain FP64 GSIS
+                    against the FP32 forms and the learned warm start;
+``normal_shock``    CIS and GSIS iterations on the Mach-5 normal shock;
+``cylinder``        CIS and GSIS iterations and seconds on the Mach-5 cylinder;
+``cpu_baseline``    the oracle timed on a bounded sample, on the host cores.
+
 With ``--gpus N`` (torchrun, one rank per GPU) every rank runs its own replica; the
 timing is the maximum over ranks and value is the sum of all ranks' updates.
 """
