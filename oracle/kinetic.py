@@ -295,42 +295,7 @@ def relaxation_source(Fc, f, I, wl):
 
 
 # --------------------------------------------------------------------------- sweep
-def _relax_downwind(cells, res, dg, offdiag, geo, dirs, B, nc, which):
-    """Forward/backward Gauss-Seidel inside each block of B consecutive cells, with
-    the cells of a block visited, for each discrete velocity (or photon direction)
-    separately, in increasing order of (direction . centroid): the forward pass then
-    meets the upwind neighbours first.  Ties are broken by the cell index."""
-    pos = {int(c): k for k, c in enumerate(cells)}
-    out = np.zeros_like(res)
-    nv = res.shape[1]
-    for b in sorted(set(int(c) // B for c in cells)):
-        members = list(range(b * B, min((b + 1) * B, nc)))
-        proj = geo.xc[members] @ dirs.T                            # [m, nv]
-        order = np.lexsort((np.repeat(np.arange(len(members))[:, None], nv, 1), proj), axis=0)
-        rank = np.empty_like(order)
-        for v in range(nv):
-            rank[order[:, v], v] = np.arange(len(members))
-        local = {c: m for m, c in enumerate(members)}
-        for sweep in (0, 1):
-            seq = range(len(members)) if sweep == 0 else range(len(members) - 1, -1, -1)
-            for t in seq:
-                for v in range(nv):
-                    m = order[t, v]
-                    k = pos[members[m]]
-                    acc = res[k, v].copy() if sweep == 0 else out[k, v].copy()
-                    for j, a, aR in offdiag[k]:
-                        if j in local:
-                            rj = rank[local[j], v]
-                            coef = (a if which == 0 else aR)[v]
-                            if sweep == 0 and rj < t:
-                                acc -= coef * out[pos[j], v]
-                            elif sweep == 1 and rj > t:
-                                acc -= coef * out[pos[j], v] / dg[k, v]
-                    out[k, v] = acc / dg[k, v] if sweep == 0 else acc
-    return out
-
-
-def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None, ordering="natural"):
+def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
     """One implicit kinetic step (Eq. dis_micro) for the gas planes and photons.
 
     For every cell i and discrete velocity (photon direction):
@@ -417,7 +382,7 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None, orderin
     if relax_block == 1:
         df = res / dg[..., None]
         dI = resR / dR
-    elif ordering == "natural":
+    else:
         pos = {int(c): k for k, c in enumerate(cells)}
         df = np.zeros_like(res)
         dI = np.zeros_like(resR)
@@ -437,7 +402,4 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None, orderin
                     if i < j < b1:
                         df[k] -= a[:, None] * df[pos[j]] / dg[k][:, None]
                         dI[k] -= aR * dI[pos[j]] / dR[k]
-    else:
-        df = _relax_downwind(cells, res, dg, offdiag, geo, xi[:, :dim], relax_block, nc, 0)
-        dI = _relax_downwind(cells, resR[..., None], dR, offdiag, geo, om[:, :dim], relax_block, nc, 1)[..., 0]
     return f[cells] + df, I[cells] + dI
