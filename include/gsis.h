@@ -200,7 +200,8 @@ int gsis_commit_staged(gsis_ctx *ctx);
  * moments of Eq. getmoment and the fields of Section 2, the same pass that follows an
  * upload), asynchronously on the context stream.  In FP32 contexts with tc_moments >= 1
  * the gas moments are one split-TF32 tensor-core contraction per (16-cell tile, 64
- * velocities).  Errors: INVALID_ARG, CUDA. */
+ * velocities).  Synchronises the context stream to read the device error word.
+ * Errors: INVALID_ARG, TIMEOUT (see gsis_set_wait_limit), CUDA. */
 int gsis_refresh_fields(gsis_ctx *ctx);
 
 /* Macroscopic fields of the current distributions, [n_cells][GSIS_NF] doubles. */
@@ -225,12 +226,14 @@ int gsis_download_fields_async(gsis_ctx *ctx, double *out, int64_t len);
  *       [f_eq(M^{k+1}) - f_eq(M^{k+1/2})] and likewise for I.
  * *eps_out (may be NULL) receives the convergence measure of Section 6 between M^k
  * and M^{k+1}.  This call synchronises the stream to read eps.
- * Errors: DIVERGED (non-finite or non-positive density/temperature), CUDA, INVALID_ARG. */
+ * Errors: DIVERGED (non-finite or non-positive density/temperature), TIMEOUT (a
+ * tensor-core completion wait ran out, see gsis_set_wait_limit), CUDA, INVALID_ARG. */
 int gsis_step(gsis_ctx *ctx, int32_t mode, double *eps_out);
 
 /* Iterate to a steady state (Section 6): CIS for the first n_cis_precond iterations
- * (mode GSIS_MODE_GSIS) or throughout (GSIS_MODE_CIS), then GSIS, until eps < tol or
- * max_outer iterations.  max_outer <= 0 and tol <= 0 take the solver parameters'
+ * (mode GSIS_MODE_GSIS; counted from the last time the distributions were set, so a
+ * resumed run continues the count of the run it was exported from) or throughout
+ * (GSIS_MODE_CIS), then GSIS, until eps < tol or max_outer iterations.  max_outer <= 0 and tol <= 0 take the solver parameters'
  * values.  *iters_out (may be NULL) receives the number of iterations; eps_history (may
  * be NULL, else at least max_outer doubles, caller-owned) receives eps of each.
  * Errors: NOT_CONVERGED (max_outer reached; the state is kept), DIVERGED, CUDA. */
@@ -246,6 +249,40 @@ int gsis_last_eps(gsis_ctx *ctx, double *eps_out);
 /* The synthetic solve of the most recent GSIS iteration: inner iterations taken and the
  * first and last residual norms ||R||_2.  Synchronises the context stream. */
 int gsis_macro_stats(gsis_ctx *ctx, int32_t *inner_iters, double *r0, double *rn);
+
+/* ---- checkpoint / resume -----------------------------------------------------------
+ * The iteration state of Section 3's outer loop is the distributions f^k and I^k and the
+ * macroscopic fields M^k they define (the next iteration's reference distributions,
+ * shift velocities and convergence measure all follow from these), plus the outer
+ * iteration count since the distributions were set and the eps of each iteration that
+ * was read.  gsis_export_state writes that state into a caller-owned HOST buffer of at
+ * least gsis_state_size() bytes: a header (magic, version, dim, precision, n_xi,
+ * n_omega, n_cells, iteration count, history length, last eps), then the eps history
+ * (doubles), M^k ([n_cells][GSIS_NF] doubles), f ([n_cells][n_xi][4]) and I
+ * ([n_cells][n_omega]) in the context's storage type, unpadded.  gsis_import_state
+ * loads such an image into a context created with the same mesh, quadratures, model and
+ * solver parameters; the iterations that follow reproduce the exporting run's bit for
+ * bit.  Both synchronise the context stream.
+ * Errors: INVALID_ARG (null or short buffer; an image of another version, dimension,
+ * precision or size), CUDA. */
+int gsis_state_size(const gsis_ctx *ctx, int64_t *bytes);
+int gsis_export_state(gsis_ctx *ctx, void *buf, int64_t len);
+int gsis_import_state(gsis_ctx *ctx, const void *buf, int64_t len);
+
+/* Outer iterations since the distributions were last set (*iter) and the eps history
+ * kept by the context (up to len values into eps, caller-owned; *n_out its length). */
+int gsis_get_history(const gsis_ctx *ctx, int64_t *iter, double *eps, int64_t len, int64_t *n_out);
+
+/* ---- failure detection -------------------------------------------------------------
+ * Every device-side wait in the library is bounded.  The tensor-core moment contraction
+ * waits for its MMA chain on an mbarrier; this sets the number of polls of that first
+ * wait (default 2^22, about a second).  When it runs out the CTA skips the accumulator,
+ * issues no further chain, waits for the outstanding one with the full default bound
+ * before it frees its tensor memory, and sets an error bit: the step (or
+ * gsis_refresh_fields) then returns GSIS_ERR_TIMEOUT and the context stays usable.
+ * A budget of 0 makes every such wait run out at once (a test of the error path).
+ * The paper has no counterpart.  Errors: INVALID_ARG (negative budget). */
+int gsis_set_wait_limit(gsis_ctx *ctx, int32_t polls);
 
 /* ---- learned closure (warm start) -----------------------------------------------
  * A perceptron 16 -> 128 -> 128 -> 128 -> 12 (GELU hidden layers) maps the state of a
@@ -302,28 +339,33 @@ int64_t gsis_launch_count(const gsis_ctx *ctx);
 int gsis_get_layout(const gsis_ctx *ctx, int32_t *v_pad, int32_t *o_pad, int32_t *n_chunks,
                     int32_t *block);
 
-/* Allocation-free velocity moments (the paper has no counterpart: this serves callers
- * that cannot allocate device memory, e.g. a host framework that owns the whole device
- * heap through its own pool allocator, or a plugin that may only use the buffers it is
- * handed; such callers cannot create a context, because gsis_create allocates).
+/* Allocation-free velocity moments.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate device memory, e.g. a host framework that owns the
+ * whole device heap through its own pool allocator, or a plugin that may only use the
+ * buffers it is handed.  Such callers cannot create a context, because gsis_create
+ * allocates.
  *
- * Computes the per-cell field record (GSIS_NF doubles: rho, u, T_t, T_r, T_v, T_R, heat
- * fluxes, stress; the moments of Eq. getmoment) of DEVICE-resident distributions:
+ * Computes the per-cell field record (GSIS_NF doubles: rho, u, T_t, T_r, T_v, T_R, the
+ * four heat fluxes, the six stress components, as gsis_get_fields) of DEVICE-resident
+ * distributions:
  *   xi [n_xi][dim], w [n_xi], omega [n_omega][3], wo [n_omega]   doubles, device
  *   f  [n_cells][n_xi][4] planes [F0, H0, f1, f2], I [n_cells][n_omega]  in the
  *      storage type of `precision` (float for GSIS_FP32, double for GSIS_FP64), device
  *   fields [n_cells][GSIS_NF] doubles, device (output)
  * on cuda_stream (NULL: the legacy default stream); the call returns after queueing.
+ * The gas moments are summed about each cell's own mean velocity (found in a first pass),
+ * so FP32 storage keeps the heat fluxes to 1e-5 of rho T^1.5 at hypersonic speeds.
  *
- * It calls no cudaMalloc/cudaFree and no allocating library routine.  Its partial sums
- * live in one 32 MiB file-scope device array that every GPU loading the library holds
- * until the process exits; sizes whose partials do not fit,
- *   (n_cells * ceil(n_xi/128) * 20 + n_cells * ceil(n_omega/128) * 4) * sizeof(storage)
- *   > 32 MiB,
+ * It calls no cudaMalloc/cudaFree and no allocating library routine.  Its shift
+ * velocities and partial sums live in one 32 MiB file-scope device array that every GPU
+ * loading the library holds until the process exits; sizes that do not fit,
+ *   n_cells * 24 + (n_cells * ceil(n_xi/128) * 20 + n_cells * ceil(n_omega/128) * 4)
+ *   * sizeof(storage) > 32 MiB,
  * are rejected with GSIS_ERR_INVALID_ARG before anything is launched.  The first call on
- * a device looks up the array's device address (with that device current); make that
- * first call before any stream capture.  All calls share the array: calls whose kernels
- * overlap on one GPU race on it.
+ * a device looks up the array's device address (with that device current) and caches it
+ * for the life of the process; make that first call before any stream capture, and make
+ * no call after cudaDeviceReset on that device.  All calls share the array: calls whose
+ * kernels overlap on one GPU race on it.
  * Errors: INVALID_ARG (null pointer, non-positive size, too large), UNSUPPORTED (dim 3),
  * CUDA (address lookup or launch failure). */
 int gsis_moments_static(int32_t dim, int32_t precision, int64_t n_cells, int32_t n_xi, const double *xi,

@@ -77,6 +77,7 @@ struct gsis_ctx {
                                  // relaxation's flux increments in FP32 (1), or that except the
                                  // last MACRO_TAIL inner iterations (2)
     int tcm = 0;                 // FP32 path: gas moments on tensor cores (1: standalone passes, 2: also the sweep)
+    int tc_wait = 1 << 22;       // polls of the first tensor-core completion wait (gsis_set_wait_limit)
     int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
     double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
            *m_fi_xf = nullptr, *m_lsq = nullptr, *m_eps2 = nullptr, *m_xc = nullptr, *m_bf_n = nullptr,
@@ -95,6 +96,11 @@ struct gsis_ctx {
 
     bool have_eps = false;
     double last_eps = 0.0;
+    // outer iterations since the distributions were last set (the CIS preconditioning of
+    // gsis_solve counts from here) and the convergence measure of each one that was read
+    int64_t iter = 0;
+    bool eps_pending = false;
+    std::vector<double> eps_hist;
     bool prof = false;
     double prof_ms[K_COUNT] = {0};
     int64_t prof_n[K_COUNT] = {0};
@@ -174,6 +180,8 @@ Geom<Real> geom(const gsis_ctx *c) {
     g.bf_cell = c->bf_cell;
     g.bf_patch = c->bf_patch;
     g.bf_nrm = (const Real *)c->bf_nrm;
+    g.tc_wait = c->tc_wait;
+    g.err = c->err;
     return g;
 }
 
@@ -249,7 +257,8 @@ int refresh_fields(gsis_ctx *c) {
         TRY(launch(c, K_MOMENTS, [&] {
             return launch_moments_only<Real>(c->stream, c->dim, (int)c->nc, c->tcm >= 1, vquad<Real>(c), oquad<Real>(c),
                                              (const Real *)c->coef, (const Real *)c->f[c->cur],
-                                             (const Real *)c->I[c->cur], (Real *)c->partial, (Real *)c->opartial);
+                                             (const Real *)c->I[c->cur], (Real *)c->partial, (Real *)c->opartial,
+                                             c->tc_wait, c->err);
         }));
         TRY(launch(c, K_FINISH, [&] {
             return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
@@ -261,6 +270,9 @@ int refresh_fields(gsis_ctx *c) {
         }));
     }
     c->have_eps = false;
+    c->eps_pending = false;
+    c->iter = 0;
+    c->eps_hist.clear();
     return GSIS_OK;
 }
 
@@ -318,6 +330,8 @@ int close_iteration(gsis_ctx *c, int nxt) {
     CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned + NEPS, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     c->cur = nxt;
     c->have_eps = true;
+    c->eps_pending = true;
+    ++c->iter;
     return GSIS_OK;
 }
 
@@ -514,7 +528,7 @@ int gsis_iteration(gsis_ctx *c) {
         return launch_sync<Real>(c->stream, c->dim, (int)c->nc, c->tcm >= 1, vquad<Real>(c), oquad<Real>(c), c->model,
                                  c->solver.sync_relax, c->fields_n, c->fields_h, (const Real *)c->coef,
                                  (Real *)c->f[nxt], (Real *)c->I[nxt], (Real *)c->partial, (Real *)c->opartial,
-                                 c->sync_kc);
+                                 c->sync_kc, c->tc_wait, c->err);
     }));
     return close_iteration<Real>(c, nxt);
 }
@@ -524,6 +538,8 @@ int read_eps(gsis_ctx *c, double *eps) {
     const double *s = c->h_pinned;
     int errw = 0;
     std::memcpy(&errw, c->h_pinned + NEPS, sizeof(int));
+    if (errw & ERR_TIMEOUT_BIT)
+        return fail(c, GSIS_ERR_TIMEOUT, "a tensor-core completion wait ran out of its poll budget");
     if (errw) return fail(c, GSIS_ERR_DIVERGED, "non-finite or non-positive density or temperature");
     // Section 6: max over rho, u, T of the volume-weighted relative change; the
     // velocity denominator is floored at 1% of the thermal-speed norm
@@ -533,7 +549,23 @@ int read_eps(gsis_ctx *c, double *eps) {
     const double e_u = std::sqrt(s[2]) / den_u;
     double e = std::fmax(e_rho, std::fmax(e_T, e_u));
     c->last_eps = e;
+    if (c->eps_pending) {
+        c->eps_hist.push_back(e);
+        c->eps_pending = false;
+    }
     if (eps) *eps = e;
+    return GSIS_OK;
+}
+
+// Reads the device error word after the queued work (refresh passes report a tensor-core
+// completion wait that ran out, or non-finite moments, here).
+int check_err(gsis_ctx *c) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned + NEPS, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int errw = 0;
+    std::memcpy(&errw, c->h_pinned + NEPS, sizeof(int));
+    if (errw & ERR_TIMEOUT_BIT)
+        return fail(c, GSIS_ERR_TIMEOUT, "a tensor-core completion wait ran out of its poll budget");
     return GSIS_OK;
 }
 
@@ -1183,7 +1215,127 @@ int gsis_commit_staged(gsis_ctx *c) {
 
 int gsis_refresh_fields(gsis_ctx *c) {
     if (!c) return GSIS_ERR_INVALID_ARG;
-    return refresh(c);
+    TRY(refresh(c));
+    return check_err(c);
+}
+
+int gsis_set_wait_limit(gsis_ctx *c, int32_t polls) {
+    if (!c || polls < 0) return fail(c, GSIS_ERR_INVALID_ARG, "negative poll budget");
+    c->tc_wait = polls;
+    return GSIS_OK;
+}
+
+// ---- checkpoint / resume: a little-endian host image of the iteration state
+namespace {
+struct StateHeader {
+    char magic[8];
+    int32_t version, dim, precision, V, NO, pad;
+    int64_t nc, iter, n_hist;
+    double last_eps;
+};
+constexpr char kStateMagic[8] = {'G', 'S', 'I', 'S', 'S', 'T', 'A', 'T'};
+constexpr int32_t kStateVersion = 1;
+
+int64_t state_bytes(const gsis_ctx *c) {
+    return (int64_t)sizeof(StateHeader) + (int64_t)c->eps_hist.size() * 8 + c->nc * NF * 8 +
+           (c->nc * c->V * 4 + c->nc * c->NO) * (int64_t)c->real_size;
+}
+}  // namespace
+
+int gsis_state_size(const gsis_ctx *c, int64_t *bytes) {
+    if (!c || !bytes) return GSIS_ERR_INVALID_ARG;
+    *bytes = state_bytes(c);
+    return GSIS_OK;
+}
+
+int gsis_export_state(gsis_ctx *c, void *buf, int64_t len) {
+    if (!c || !buf) return fail(c, GSIS_ERR_INVALID_ARG, "null buffer");
+    if (len < state_bytes(c)) return fail(c, GSIS_ERR_INVALID_ARG, "state buffer too short");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    unsigned char *p = static_cast<unsigned char *>(buf);
+    StateHeader h{};
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = kStateVersion;
+    h.dim = c->dim;
+    h.precision = c->precision;
+    h.V = c->V;
+    h.NO = c->NO;
+    h.nc = c->nc;
+    h.iter = c->iter;
+    h.n_hist = (int64_t)c->eps_hist.size();
+    h.last_eps = c->last_eps;
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    if (h.n_hist) std::memcpy(p, c->eps_hist.data(), (size_t)h.n_hist * 8);
+    p += (size_t)h.n_hist * 8;
+    CUDA_TRY(c, cudaMemcpy(p, c->fields, (size_t)c->nc * NF * 8, cudaMemcpyDeviceToHost));
+    p += (size_t)c->nc * NF * 8;
+    const size_t rs = c->real_size;
+    CUDA_TRY(c, cudaMemcpy2D(p, (size_t)c->V * 4 * rs, c->f[c->cur], (size_t)c->Vp * 4 * rs, (size_t)c->V * 4 * rs,
+                             (size_t)c->nc, cudaMemcpyDeviceToHost));
+    p += (size_t)c->nc * c->V * 4 * rs;
+    CUDA_TRY(c, cudaMemcpy2D(p, (size_t)c->NO * rs, c->I[c->cur], (size_t)c->Op * rs, (size_t)c->NO * rs,
+                             (size_t)c->nc, cudaMemcpyDeviceToHost));
+    return GSIS_OK;
+}
+
+int gsis_import_state(gsis_ctx *c, const void *buf, int64_t len) {
+    if (!c || !buf) return fail(c, GSIS_ERR_INVALID_ARG, "null buffer");
+    if (len < (int64_t)sizeof(StateHeader)) return fail(c, GSIS_ERR_INVALID_ARG, "state buffer too short");
+    const unsigned char *p = static_cast<const unsigned char *>(buf);
+    StateHeader h;
+    std::memcpy(&h, p, sizeof h);
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != kStateVersion)
+        return fail(c, GSIS_ERR_INVALID_ARG, "not a state image of this library version");
+    if (h.dim != c->dim || h.precision != c->precision || h.V != c->V || h.NO != c->NO || h.nc != c->nc)
+        return fail(c, GSIS_ERR_INVALID_ARG, "state image of a different problem (dim, precision or sizes)");
+    if (h.n_hist < 0 || h.iter < 0) return fail(c, GSIS_ERR_INVALID_ARG, "corrupt state header");
+    const int64_t need = (int64_t)sizeof(StateHeader) + h.n_hist * 8 + c->nc * NF * 8 +
+                         (c->nc * c->V * 4 + c->nc * c->NO) * (int64_t)c->real_size;
+    if (len < need) return fail(c, GSIS_ERR_INVALID_ARG, "state buffer too short");
+    p += sizeof h;
+    std::vector<double> hist((size_t)h.n_hist);
+    if (h.n_hist) std::memcpy(hist.data(), p, (size_t)h.n_hist * 8);
+    p += (size_t)h.n_hist * 8;
+    const size_t rs = c->real_size;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    CUDA_TRY(c, cudaMemcpy(c->fields, p, (size_t)c->nc * NF * 8, cudaMemcpyHostToDevice));
+    p += (size_t)c->nc * NF * 8;
+    CUDA_TRY(c, cudaMemset(c->f[c->cur], 0, (size_t)c->nc * c->Vp * 4 * rs));
+    CUDA_TRY(c, cudaMemset(c->I[c->cur], 0, (size_t)c->nc * c->Op * rs));
+    CUDA_TRY(c, cudaMemcpy2D(c->f[c->cur], (size_t)c->Vp * 4 * rs, p, (size_t)c->V * 4 * rs, (size_t)c->V * 4 * rs,
+                             (size_t)c->nc, cudaMemcpyHostToDevice));
+    p += (size_t)c->nc * c->V * 4 * rs;
+    CUDA_TRY(c, cudaMemcpy2D(c->I[c->cur], (size_t)c->Op * rs, p, (size_t)c->NO * rs, (size_t)c->NO * rs,
+                             (size_t)c->nc, cudaMemcpyHostToDevice));
+    // the next iteration reads the coefficient record built from the fields, exactly as
+    // after the iteration that produced them
+    int rc = c->precision == GSIS_FP64 ? launch(c, K_COEF, [&] {
+        return launch_coefficients<double>(c->stream, c->dim, geom<double>(c), c->model, c->fields, c->cell_dx,
+                                           (double *)c->coef);
+    })
+                                       : launch(c, K_COEF, [&] {
+        return launch_coefficients<float>(c->stream, c->dim, geom<float>(c), c->model, c->fields, c->cell_dx,
+                                          (float *)c->coef);
+    });
+    TRY(rc);
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->iter = h.iter;
+    c->eps_hist = std::move(hist);
+    c->last_eps = h.last_eps;
+    c->have_eps = false;
+    c->eps_pending = false;
+    return GSIS_OK;
+}
+
+int gsis_get_history(const gsis_ctx *c, int64_t *iter, double *eps, int64_t len, int64_t *n_out) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (iter) *iter = c->iter;
+    const int64_t n = (int64_t)c->eps_hist.size();
+    if (n_out) *n_out = n;
+    if (eps)
+        for (int64_t k = 0; k < std::min(n, len); ++k) eps[k] = c->eps_hist[(size_t)k];
+    return GSIS_OK;
 }
 
 int gsis_set_distributions(gsis_ctx *c, const double *f, int64_t f_len, const double *I, int64_t I_len) {
@@ -1264,7 +1416,7 @@ int gsis_solve(gsis_ctx *c, int32_t mode, int32_t max_outer, double tol, int32_t
     const double t = tol > 0 ? tol : c->solver.tol_outer;
     if (iters_out) *iters_out = 0;
     for (int k = 0; k < n; ++k) {
-        const int md = (mode == GSIS_MODE_GSIS && k >= c->solver.n_cis_precond) ? GSIS_MODE_GSIS : GSIS_MODE_CIS;
+        const int md = (mode == GSIS_MODE_GSIS && c->iter >= c->solver.n_cis_precond) ? GSIS_MODE_GSIS : GSIS_MODE_CIS;
         double e = 0.0;
         TRY(gsis_step(c, md, &e));
         if (eps_history) eps_history[k] = e;

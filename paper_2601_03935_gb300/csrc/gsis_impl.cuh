@@ -20,6 +20,8 @@ constexpr int SYNC_KC = 20;    // floats per cell of the synchronisation constan
 constexpr int MT = 16;         // moment tile: gas moments are taken about the velocity of the
                                // tile's first cell (cells MT*t .. MT*t + MT - 1 share it)
 constexpr int NEPS = 8;        // per-cell terms of the convergence measure
+constexpr int ERR_DIVERGED_BIT = 1;   // bits of the device error word
+constexpr int ERR_TIMEOUT_BIT = 2;
 
 // ---- per-cell coefficient record (Real), built from the FP64 fields each iteration,
 // laid out for 16-byte vector loads:
@@ -71,6 +73,8 @@ struct Geom {
     const int *bf_cell;        // [n_bf]
     const int *bf_patch;       // [n_bf]
     const Real *bf_nrm;        // [n_bf][3] outward normal
+    int tc_wait;               // polls of the first tensor-core completion wait (ERR_TIMEOUT bit on expiry)
+    int *err;                  // device error word: bit 0 divergence, bit 1 a completion wait ran out
 };
 
 template <typename Real>
@@ -167,7 +171,7 @@ cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const Model
 template <typename Real>
 cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                         const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
-                        Real *f, Real *I, Real *partial, Real *opartial, void *scratch);
+                        Real *f, Real *I, Real *partial, Real *opartial, void *scratch, int tc_wait, int *err);
 int macro_rpart_count(int n_cells);
 
 // ---- learned closure (mlp.cu)
@@ -239,6 +243,7 @@ cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<
                                const ModelDev &m, const double *fields, Real *f, Real *I);
 template <typename Real>
 cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
-                                const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial);
+                                const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial,
+                                int tc_wait, int *err);
 
 }  // namespace gsis

@@ -829,13 +829,14 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
             const uint32_t taddr = tcm::accumulator(ctl);
             float m[tcm::NBASIS];
             bool ok;
-            if (tcm::contract(ctl, taddr, stage, tid, m, ok)) {
+            if (tcm::contract(ctl, taddr, stage, tid, m, ok, g.tc_wait)) {
                 const int l = (tid & 15) - lt0;
                 if (l >= 0 && l < nb)
                     tcm::store_row<DIM>(reinterpret_cast<float *>(partial) +
                                             ((size_t)(c0 + l) * gridDim.y + chunk) * NMP,
                                         tid >> 5, m);
             }
+            if (!ok && tid == 0) atomicOr(g.err, ERR_TIMEOUT_BIT);
             tcm::end(ctl, taddr, tid, ok, 0);
             return;
         }
@@ -1108,7 +1109,8 @@ constexpr int TC_SMEM = tcm::STAGE_BYTES + (int)sizeof(tcm::Ctl);
 template <int DIM, bool SYNC>
 __global__ void __launch_bounds__(128, 5) k_tc_pass(int n_cells, int n_chunks, int n_items, Quad<float> vq, float om,
                                                  const float4 *__restrict__ kc_g, const float *__restrict__ coef,
-                                                 float *__restrict__ f, float *__restrict__ partial) {
+                                                 float *__restrict__ f, float *__restrict__ partial, int wait_limit,
+                                                 int *__restrict__ err) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     unsigned char *stage = tc_smem;
     tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(tc_smem + tcm::STAGE_BYTES);
@@ -1129,15 +1131,18 @@ __global__ void __launch_bounds__(128, 5) k_tc_pass(int n_cells, int n_chunks, i
     int item = blockIdx.x, prev = -1;
     uint32_t parity = 0;
     bool ok = true;
+    // After a completion wait runs out (in any warp: the CTA agrees by a barrier vote)
+    // the CTA issues no further chain, so that the one outstanding phase is the one
+    // tcm::end waits for before it frees the accumulator.
     auto drain = [&](int it) {
         float m[tcm::NBASIS];
         bool okk;
-        if (tcm::collect(ctl, taddr, tid, parity, m, okk)) {
+        if (tcm::collect(ctl, taddr, tid, parity, m, okk, wait_limit)) {
             const int i = it / n_chunks * MT + (tid & 15);
             if (i < n_cells)
                 tcm::store_row<DIM>(partial + ((size_t)i * n_chunks + it % n_chunks) * NMP, tid >> 5, m);
         }
-        ok = ok && okk;
+        ok = __syncthreads_and(okk) != 0;
         parity ^= 1u;
     };
     Vec<float, 4> fv[MT / 2];
@@ -1146,7 +1151,10 @@ __global__ void __launch_bounds__(128, 5) k_tc_pass(int n_cells, int n_chunks, i
         const int next = item + gridDim.x;
         Vec<float, 4> fn[MT / 2];
         if (next < n_items) fetch(next, fn);              // in flight during the rest of the item
-        if (prev >= 0) drain(prev);
+        if (prev >= 0) {
+            drain(prev);
+            if (!ok) break;
+        }
         tcm::fence_before_sync();
         __syncthreads();                                   // accumulator read, stage free
         const int tile = item / n_chunks * MT, vg = (item % n_chunks) * tcm::K + v;
@@ -1205,7 +1213,8 @@ __global__ void __launch_bounds__(128, 5) k_tc_pass(int n_cells, int n_chunks, i
 #pragma unroll
         for (int j = 0; j < MT / 2; ++j) fv[j] = fn[j];
     }
-    if (prev >= 0) drain(prev);
+    if (prev >= 0 && ok) drain(prev);
+    if (!ok && tid == 0) atomicOr(err, ERR_TIMEOUT_BIT);
     tcm::end(ctl, taddr, tid, ok, parity ^ 1u);
 }
 
@@ -1701,7 +1710,8 @@ cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<
 
 template <typename Real>
 cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq,
-                                const Quad<Real> &oq, const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial) {
+                                const Quad<Real> &oq, const Real *coef, const Real *f, const Real *I, Real *partial, Real *opartial,
+                                int tc_wait, int *err) {
     dim3 gg((n_cells + VCH / 32 - 1) / (VCH / 32), vq.n_pad / VCH);
     dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
     static_assert(VCH == tcm::K && SV == tcm::K, "moment chunks are the tensor-core K");
@@ -1712,7 +1722,7 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, c
             GSIS_DISPATCH_DIM(dim, {
                 auto kern = k_tc_pass<DIM, false>;
                 kern<<<persistent_grid<DIM, false>(TC_SMEM, n_items), 128, TC_SMEM, s>>>(
-                    n_cells, nch, n_items, vq, 0.f, nullptr, coef, const_cast<float *>(f), partial);
+                    n_cells, nch, n_items, vq, 0.f, nullptr, coef, const_cast<float *>(f), partial, tc_wait, err);
             });
             on_tc = true;
         }
@@ -1735,7 +1745,7 @@ cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const Model
 template <typename Real>
 cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                         const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
-                        Real *f, Real *I, Real *partial, Real *opartial, void *scratch) {
+                        Real *f, Real *I, Real *partial, Real *opartial, void *scratch, int tc_wait, int *err) {
     dim3 gg((n_cells + VCH / 32 - 1) / (VCH / 32), vq.n_pad / VCH);
     dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
     bool on_tc = false;
@@ -1749,7 +1759,8 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                 k_sync_coef<DIM><<<(n_cells + 127) / 128, 128, 0, s>>>(n_cells, m, F_new, F_half, kc);
                 auto kern = k_tc_pass<DIM, true>;
                 kern<<<persistent_grid<DIM, true>(smem, n_items), 128, smem, s>>>(
-                    n_cells, nch, n_items, vq, (float)omega, reinterpret_cast<const float4 *>(kc), coef, f, partial);
+                    n_cells, nch, n_items, vq, (float)omega, reinterpret_cast<const float4 *>(kc), coef, f, partial,
+                    tc_wait, err);
             });
             on_tc = true;
         }
@@ -1785,13 +1796,14 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                                                   const ModelDev &, const double *, Real *, Real *);               \
     template cudaError_t launch_moments_only<Real>(cudaStream_t, int, int, bool, const Quad<Real> &,               \
                                                    const Quad<Real> &,                                             \
-                                                   const Real *, const Real *, const Real *, Real *, Real *);      \
+                                                   const Real *, const Real *, const Real *, Real *, Real *, int,  \
+                                                   int *);                                                         \
     template cudaError_t launch_kinetic_bflux<Real>(cudaStream_t, const MacroGeom &, const ModelDev &,             \
                                                     const Quad<Real> &, const Quad<Real> &, const Real *,          \
                                                     const Real *, double *);                                       \
     template cudaError_t launch_sync<Real>(cudaStream_t, int, int, bool, const Quad<Real> &, const Quad<Real> &,   \
                                            const ModelDev &, double, const double *, const double *, const Real *, \
-                                           Real *, Real *, Real *, Real *, void *);
+                                           Real *, Real *, Real *, Real *, void *, int, int *);
 
 GSIS_INSTANTIATE(float)
 GSIS_INSTANTIATE(double)

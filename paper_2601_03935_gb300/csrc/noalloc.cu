@@ -5,15 +5,22 @@
 // plugin that may only use the buffers it is handed), or latency-critical loops that
 // cannot afford a cudaMalloc/cudaFree pair per call.  Such callers cannot create a
 // gsis context (gsis_create allocates), so this entry point takes device pointers and
-// keeps its per-chunk partial sums in a file-scope device array instead of a buffer
-// of its own.
+// keeps its per-chunk partial sums and per-cell shift velocities in a file-scope device
+// array instead of a buffer of its own.
 //
 // The array (kScratchBytes) lives in every GPU that loads the library until the
 // process exits.  Its device address is looked up once per device, on the first call
 // made with that device current (cudaGetSymbolAddress); make that first call before
-// any stream capture.  All calls share the array: two calls whose kernels overlap on
-// a GPU race on it.  Every partial is written before it is read, so nothing in the
-// array has to start at zero and a call never sees the previous call's contents.
+// any stream capture.  The address is cached for the life of the process: calls made
+// after cudaDeviceReset on that device are not supported.  All calls share the array:
+// two calls whose kernels overlap on a GPU race on it.  Every word a call reads from
+// the array is written earlier by the same call, so nothing in it has to start at zero
+// and a call never sees the previous call's contents.
+//
+// Accuracy: the gas moments are summed about a per-cell shift velocity u0 (the cell's
+// own mean velocity from a first pass over its mass and momentum), so that the third
+// moments behind the heat fluxes do not cancel at high flow speeds; the FP32 storage
+// path keeps 1e-5 of rho T^1.5 at Mach 5.
 #include <cmath>
 #include <mutex>
 
@@ -48,15 +55,71 @@ constexpr int n_moments() {
     return 1 + DIM + DIM * (DIM + 1) / 2 + DIM + 3 * (1 + DIM);
 }
 
-// One warp per (cell, chunk): raw moments about zero velocity of the four planes.
+// Bytes of the array one call uses: the shift velocities (3 doubles per cell), then the
+// gas and photon partials in the storage type.
+size_t scratch_bytes(long long n_cells, int n_xi, int n_om, size_t real) {
+    const size_t n_chunks = (n_xi + kChunk - 1) / kChunk, o_chunks = (n_om + kChunk - 1) / kChunk;
+    return (size_t)n_cells * 3 * sizeof(double) + ((size_t)n_cells * n_chunks * kNMP + (size_t)n_cells * o_chunks * kNMO) * real;
+}
+
+// One warp per (cell, chunk): mass and momentum partials of F0 (the first pass).
+template <typename Real, int DIM>
+__global__ void k_static_mass(long long n_cells, int n_xi, int n_chunks, const double *__restrict__ xi,
+                              const double *__restrict__ w, const Real *__restrict__ f, Real *__restrict__ part) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int chunk = blockIdx.y;
+    if (i >= n_cells) return;
+    Real acc[1 + DIM];
+#pragma unroll
+    for (int m = 0; m <= DIM; ++m) acc[m] = Real(0);
+    for (int vl = lane; vl < kChunk; vl += 32) {
+        const int v = chunk * kChunk + vl;
+        if (v >= n_xi) break;
+        const Real w0 = (Real)w[v] * f[((size_t)i * n_xi + v) * 4];
+        acc[0] += w0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) acc[1 + a] += w0 * (Real)xi[(size_t)v * DIM + a];
+    }
+#pragma unroll
+    for (int m = 0; m <= DIM; ++m)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+    if (lane == 0) {
+        Real *P = part + ((size_t)i * n_chunks + chunk) * kNMP;
+#pragma unroll
+        for (int m = 0; m <= DIM; ++m) P[m] = acc[m];
+    }
+}
+
+// Per cell: the shift velocity u0 = sum m1 / sum m0 over the chunks, in FP64 (zero where
+// the cell has no mass).
+template <typename Real, int DIM>
+__global__ void k_static_shift(long long n_cells, int n_chunks, const Real *__restrict__ part,
+                               double *__restrict__ u0) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    double S[1 + DIM];
+    for (int m = 0; m <= DIM; ++m) S[m] = 0.0;
+    for (int c = 0; c < n_chunks; ++c)
+        for (int m = 0; m <= DIM; ++m) S[m] += (double)part[((size_t)i * n_chunks + c) * kNMP + m];
+    for (int a = 0; a < DIM; ++a) u0[(size_t)i * 3 + a] = S[0] > 0.0 ? S[1 + a] / S[0] : 0.0;
+}
+
+// One warp per (cell, chunk): moments of the four planes about the cell's shift velocity,
+// c = xi - u0.
 template <typename Real, int DIM>
 __global__ void k_static_gas(long long n_cells, int n_xi, int n_chunks, const double *__restrict__ xi,
-                             const double *__restrict__ w, const Real *__restrict__ f, Real *__restrict__ part) {
+                             const double *__restrict__ w, const double *__restrict__ u0,
+                             const Real *__restrict__ f, Real *__restrict__ part) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long i = (long long)blockIdx.x * (blockDim.x >> 5) + warp;
     const int chunk = blockIdx.y;
     if (i >= n_cells) return;
     constexpr int NM = n_moments<DIM>();
+    double us[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) us[a] = u0[(size_t)i * 3 + a];
     Real acc[NM];
 #pragma unroll
     for (int m = 0; m < NM; ++m) acc[m] = Real(0);
@@ -67,7 +130,7 @@ __global__ void k_static_gas(long long n_cells, int n_xi, int n_chunks, const do
         Real c[DIM], c2 = Real(0);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
-            c[a] = (Real)xi[(size_t)v * DIM + a];
+            c[a] = (Real)(xi[(size_t)v * DIM + a] - us[a]);
             c2 += c[a] * c[a];
         }
         const Real wv = (Real)w[v];
@@ -131,10 +194,12 @@ __global__ void k_static_photon(long long n_cells, int n_om, int o_chunks, const
 }
 
 // Partials -> per-cell field record (rho, u, T_t, T_r, T_v, T_R, heat fluxes, stress).
+// The partials are moments about u0; u below is the residual velocity u - u0, and the
+// central moments follow from them exactly as from moments about zero.
 template <typename Real, int DIM>
 __global__ void k_static_finish(long long n_cells, int n_chunks, int o_chunks, double d_r, double d_v,
-                                double sigma_R, const Real *__restrict__ part, const Real *__restrict__ opart,
-                                double *__restrict__ out) {
+                                double sigma_R, const double *__restrict__ u0, const Real *__restrict__ part,
+                                const Real *__restrict__ opart, double *__restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_cells) return;
     constexpr int NM = n_moments<DIM>();
@@ -180,7 +245,7 @@ __global__ void k_static_finish(long long n_cells, int n_chunks, int o_chunks, d
     double *F = out + (size_t)i * kNF;
     for (int q = 0; q < kNF; ++q) F[q] = 0.0;
     F[0] = rho;
-    for (int a = 0; a < DIM; ++a) F[1 + a] = u[a];
+    for (int a = 0; a < DIM; ++a) F[1 + a] = u0[(size_t)i * 3 + a] + u[a];
     F[4] = ic2 / (3.0 * rho);
     F[5] = 2.0 * G1 / (d_r * rho);
     F[6] = 2.0 * G2 / (d_v * rho);
@@ -211,19 +276,24 @@ int run(long long n_cells, int n_xi, const double *xi, const double *w, int n_om
         const double *wo, const void *f, const void *I, double d_r, double d_v, double sigma_R, double *out,
         cudaStream_t s) {
     const int n_chunks = (n_xi + kChunk - 1) / kChunk, o_chunks = (n_om + kChunk - 1) / kChunk;
-    const size_t need = ((size_t)n_cells * n_chunks * kNMP + (size_t)n_cells * o_chunks * kNMO) * sizeof(Real);
-    if (need > kScratchBytes) return GSIS_ERR_INVALID_ARG;
+    if (scratch_bytes(n_cells, n_xi, n_om, sizeof(Real)) > kScratchBytes) return GSIS_ERR_INVALID_ARG;
     void *base = nullptr;
     int rc = scratch_address(&base);
     if (rc != GSIS_OK) return rc;
-    Real *part = static_cast<Real *>(base);
+    double *u0 = static_cast<double *>(base);
+    Real *part = reinterpret_cast<Real *>(u0 + (size_t)n_cells * 3);
     Real *opart = part + (size_t)n_cells * n_chunks * kNMP;
     const int warps = 4;
-    dim3 gg((unsigned)((n_cells + warps - 1) / warps), n_chunks), go((unsigned)((n_cells + warps - 1) / warps), o_chunks);
-    k_static_gas<Real, DIM><<<gg, 32 * warps, 0, s>>>(n_cells, n_xi, n_chunks, xi, w, static_cast<const Real *>(f), part);
+    const unsigned cells_blocks = (unsigned)((n_cells + warps - 1) / warps);
+    const unsigned per_cell = (unsigned)((n_cells + 127) / 128);
+    dim3 gg(cells_blocks, n_chunks), go(cells_blocks, o_chunks);
+    const Real *fr = static_cast<const Real *>(f);
+    k_static_mass<Real, DIM><<<gg, 32 * warps, 0, s>>>(n_cells, n_xi, n_chunks, xi, w, fr, part);
+    k_static_shift<Real, DIM><<<per_cell, 128, 0, s>>>(n_cells, n_chunks, part, u0);
+    k_static_gas<Real, DIM><<<gg, 32 * warps, 0, s>>>(n_cells, n_xi, n_chunks, xi, w, u0, fr, part);
     k_static_photon<Real, DIM><<<go, 32 * warps, 0, s>>>(n_cells, n_om, o_chunks, om, wo, static_cast<const Real *>(I), opart);
-    k_static_finish<Real, DIM><<<(unsigned)((n_cells + 127) / 128), 128, 0, s>>>(n_cells, n_chunks, o_chunks, d_r, d_v,
-                                                                                 sigma_R, part, opart, out);
+    k_static_finish<Real, DIM><<<per_cell, 128, 0, s>>>(n_cells, n_chunks, o_chunks, d_r, d_v, sigma_R, u0, part,
+                                                        opart, out);
     return cudaGetLastError() == cudaSuccess ? GSIS_OK : GSIS_ERR_CUDA;
 }
 

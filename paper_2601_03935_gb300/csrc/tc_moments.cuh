@@ -138,9 +138,9 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
-// Bounded wait for the barrier's phase `parity` to complete; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (int it = 0; it < WAIT_LIMIT; ++it) {
+// Bounded wait for the barrier's phase `parity` to complete; false if `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, int limit = WAIT_LIMIT) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -207,21 +207,27 @@ __device__ __forceinline__ uint32_t accumulator(const Ctl *ctl) {
     return *reinterpret_cast<const volatile uint32_t *>(&ctl->taddr);
 }
 
-// Results of a chain whose commit completes barrier phase `parity`, all 128 threads: wait,
-// read the thread's row, fold the tail row (lane + 16) into the head row by a shuffle.
-// Returns true on lanes 0..15, which then own row (plane = warp, cell = lane) with its 8
-// moments in m.  `ok` turns false if the completion wait ran out; m is NaN then.
+// Results of a chain whose commit completes barrier phase `parity`, all 128 threads: wait
+// (at most `limit` polls), read the thread's row, fold the tail row (lane + 16) into the
+// head row by a shuffle.  Returns true on lanes 0..15, which then own row (plane = warp,
+// cell = lane) with its 8 moments in m.  `ok` turns false, the same in every lane of a
+// warp, if the completion wait ran out in any lane: the warp then skips the tensor-memory
+// read (a warp-wide instruction) and m is NaN.
 __device__ __forceinline__ bool collect(Ctl *ctl, uint32_t taddr, int tid, uint32_t parity, float (&m)[NBASIS],
-                                        bool &ok) {
-    ok = mbar_wait(smem_u32(&ctl->mbar), parity);
+                                        bool &ok, int limit = WAIT_LIMIT) {
+    ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&ctl->mbar), parity, limit));
     fence_after_sync();
-    float d[16];
-    tmem_row(taddr, tid >> 5, d);
+    if (ok) {
+        float d[16];
+        tmem_row(taddr, tid >> 5, d);
 #pragma unroll
-    for (int b = 0; b < NBASIS; ++b) {
-        m[b] = d[b] + d[NBASIS + b];
-        m[b] += __shfl_xor_sync(0xffffffffu, m[b], 16);
-        if (!ok) m[b] = __int_as_float(0x7fc00000);
+        for (int b = 0; b < NBASIS; ++b) {
+            m[b] = d[b] + d[NBASIS + b];
+            m[b] += __shfl_xor_sync(0xffffffffu, m[b], 16);
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < NBASIS; ++b) m[b] = __int_as_float(0x7fc00000);
     }
     return (tid & 31) < 16;
 }
@@ -230,14 +236,16 @@ __device__ __forceinline__ bool collect(Ctl *ctl, uint32_t taddr, int tid, uint3
 // the tensor core (fence_smem_to_async by every writer, then a CTA barrier): thread 0
 // issues the chain, then collect() on the barrier's first phase.
 __device__ __forceinline__ bool contract(Ctl *ctl, uint32_t taddr, const unsigned char *stage, int tid,
-                                         float (&m)[NBASIS], bool &ok) {
+                                         float (&m)[NBASIS], bool &ok, int limit = WAIT_LIMIT) {
     if (tid == 0) issue(taddr, smem_u32(stage), smem_u32(&ctl->mbar));
-    return collect(ctl, taddr, tid, 0, m, ok);
+    return collect(ctl, taddr, tid, 0, m, ok, limit);
 }
 
 // Release the accumulator (all 128 threads; every tensor-memory read has completed).  If
-// a completion wait ran out, wait once more (bounded) on the last phase `parity` so that
-// no MMA is in flight when the columns are freed.
+// a completion wait ran out (`ok` false in thread 0), wait once more, with the full bound
+// WAIT_LIMIT, on phase `parity` of the one chain still outstanding, so that no MMA is in
+// flight when the columns are freed; callers issue no further chain after a wait runs
+// out, which keeps that phase unambiguous.
 __device__ __forceinline__ void end(Ctl *ctl, uint32_t taddr, int tid, bool ok, uint32_t parity) {
     if (!ok && tid == 0) mbar_wait(smem_u32(&ctl->mbar), parity);
     fence_before_sync();

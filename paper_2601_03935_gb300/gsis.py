@@ -99,6 +99,11 @@ def load():
         "gsis_step_async": (C.c_int, [vp, C.c_int32]),
         "gsis_solve": (C.c_int, [vp, C.c_int32, C.c_int32, C.c_double, _ip, _dp]),
         "gsis_macro_stats": (C.c_int, [vp, _ip, _dp, _dp]),
+        "gsis_state_size": (C.c_int, [vp, C.POINTER(C.c_int64)]),
+        "gsis_export_state": (C.c_int, [vp, vp, C.c_int64]),
+        "gsis_import_state": (C.c_int, [vp, vp, C.c_int64]),
+        "gsis_get_history": (C.c_int, [vp, C.POINTER(C.c_int64), _dp, C.c_int64, C.POINTER(C.c_int64)]),
+        "gsis_set_wait_limit": (C.c_int, [vp, C.c_int32]),
         "gsis_mlp_init": (C.c_int, [vp, C.c_uint64]),
         "gsis_mlp_set_params": (C.c_int, [vp, _fp, C.c_int64]),
         "gsis_mlp_get_params": (C.c_int, [vp, _fp, C.c_int64]),
@@ -261,6 +266,38 @@ def gsis_solve(ctx, mode=GSIS_MODE_GSIS, max_outer=0, tol=0.0, raise_on_max=Fals
     if rc != GSIS_OK and not (rc == GSIS_ERR_NOT_CONVERGED and not raise_on_max):
         _check(rc, ctx)
     return it.value, hist[:it.value].copy()
+
+
+def gsis_state_size(ctx):
+    n = C.c_int64(0)
+    _check(load().gsis_state_size(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+def gsis_export_state(ctx):
+    """The context's iteration state as a bytes-like uint8 array."""
+    buf = np.zeros(gsis_state_size(ctx), np.uint8)
+    _check(load().gsis_export_state(ctx, buf.ctypes.data_as(C.c_void_p), buf.size), ctx)
+    return buf
+
+
+def gsis_import_state(ctx, buf):
+    b = np.ascontiguousarray(np.frombuffer(bytes(buf), np.uint8) if not isinstance(buf, np.ndarray) else buf,
+                             dtype=np.uint8)
+    _check(load().gsis_import_state(ctx, b.ctypes.data_as(C.c_void_p), b.size), ctx)
+
+
+def gsis_get_history(ctx):
+    """(iterations since the distributions were set, eps history)."""
+    it, n = C.c_int64(0), C.c_int64(0)
+    _check(load().gsis_get_history(ctx, C.byref(it), None, 0, C.byref(n)), ctx)
+    h = np.zeros(max(n.value, 1))
+    _check(load().gsis_get_history(ctx, C.byref(it), _ptr(h), n.value, C.byref(n)), ctx)
+    return it.value, h[:n.value].copy()
+
+
+def gsis_set_wait_limit(ctx, polls):
+    _check(load().gsis_set_wait_limit(ctx, polls), ctx)
 
 
 GSIS_MLP_NPARAM = 36804

@@ -170,6 +170,34 @@ def test_full_size_cavity_sampled_blocks():
     assert_planes_close(Ig[cells], Io, 1e-5, "I sampled")
 
 
+def test_full_size_cylinder_sampled_blocks():
+    """The Mach-5 cylinder at full size: 40 000 triangles x 2304 velocities (48 x 48,
+    truncated at 8 sqrt(2 T_0)) x 96 photon directions, density-scaled absorption, FP32,
+    order 2, blocks of 16, from a smooth state around the free stream.  Whole blocks at
+    the start, next to the wall, next to the far field, in the middle and at the end are
+    recomputed by the oracle."""
+    wl = gi.workloads.with_solver(gi.workloads.cylinder(), precision="fp32", order=2, relax_block=16)
+    assert wl.mesh.n_cells == 40000 and wl.xi.shape[0] == 2304 and wl.omega.shape[0] == 96
+    far = wl.mesh.patches[1]
+    M = gi.fields.smooth_random_fields(wl.mesh.cell_centroid / 8.0, 23, u_scale=0.5)
+    M[:, 1] += far.u[0]
+    M[:, 4:8] *= far.T_t
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 2, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, 24)
+    f, I = f.astype(np.float32).astype(np.float64), I.astype(np.float32).astype(np.float64)
+    _, _, fg, Ig, _ = _run(wl, f, I)
+    nc = wl.mesh.n_cells
+    m = wl.mesh
+    bnd = m.face_nbr < 0
+    wall = m.face_owner[bnd & (m.face_nbr == -1)]
+    farc = m.face_owner[bnd & (m.face_nbr == -2)]
+    blocks = sorted({0, int(wall[len(wall) // 3]) // 16, int(farc[len(farc) // 2]) // 16, nc // 32,
+                     (nc - 1) // 16})
+    cells = np.concatenate([np.arange(b * 16, min(b * 16 + 16, nc)) for b in blocks])
+    fo, Io = K.kinetic_sweep(f, I, wl, relax_block=16, cells=cells)
+    assert_planes_close(fg[cells], fo, 1e-5, "f sampled")
+    assert_planes_close(Ig[cells], Io, 1e-5, "I sampled")
+
+
 def test_twenty_iterations_follow_the_oracle():
     """Twenty CIS iterations on the 8 x 8 heated-lid cavity at Kn = 1, order 2, FP64: the
     convergence measure of every iteration and the final distributions equal the oracle's
