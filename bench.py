@@ -20,8 +20,11 @@ Further keys of the line (each leg can be skipped with its --no-* flag):
 ``cylinder``        CIS and GSIS iterations and seconds on the Mach-5 cylinder;
 ``cpu_baseline``    the oracle timed on a bounded sample, on the host cores.
 
-With ``--gpus N`` (torchrun, one rank per GPU) every rank runs its own replica; the
-timing is the maximum over ranks and value is the sum of all ranks' updates.
+With ``--gpus N`` (torchrun, one rank per GPU) the velocity and photon sets are cut into N
+contiguous ranges, one per rank (paper_2601_03935_gb300.shard): every rank sweeps all
+cells for its velocities, and one NCCL all-reduce per iteration sums the per-cell moment
+sums and wall outflow.  The work of one step is fixed (strong scaling); the timing is
+the maximum over ranks and value is the updates of the whole problem per second.
 """
 from __future__ import annotations
 
@@ -65,7 +68,7 @@ def config(args, wl):
                      "one GSIS outer iteration (kinetic sweep + moments + high-order terms + synthetic solve + "
                      "synchronisation + epsilon)"),
             "l2": "inputs larger than L2 (f: 2 x %.0f MB)" % (wl.mesh.n_cells * 896 * 16 / 1e6),
-            "parallelism": "replicas" if args.gpus > 1 else "1 GPU"}
+            "parallelism": "1 GPU"}
 
 
 class ClockSampler:
@@ -345,6 +348,222 @@ def cylinder(precond=150, max_iter=12000):
     return out
 
 
+def _smooth_state(wl, seed):
+    """Smooth seeded fields (around the free stream where the workload has one) and their
+    noisy multi-temperature equilibrium, FP32-rounded."""
+    import gsis_inputs as gi
+    far = [p for p in wl.mesh.patches if p.kind == 1]
+    if far:
+        M = gi.fields.smooth_random_fields(wl.mesh.cell_centroid / 8.0, seed, u_scale=0.5)
+        M[:, 1] += far[0].u[0]
+        M[:, 4:8] *= far[0].T_t
+    else:
+        M = gi.fields.smooth_random_fields(wl.mesh.cell_centroid, seed, u_scale=0.2)
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, wl.dim, wl.model.d_r, wl.model.d_v, wl.model.sigma_R,
+                                       seed + 1, noise=0.02)
+    return f.astype(np.float32).astype(np.float64), I.astype(np.float32).astype(np.float64)
+
+
+def field_errors(stream):
+    """Per-field error of one FP32 CIS iteration (order 2, blocks of 16) against the FP64
+    oracle from the same state, for the slab (all 64 cells), the 20 000-cell cavity and
+    the 40 000-cell Mach-5 cylinder (whole relaxation blocks at the start, middle and end
+    and next to the boundaries).  Densities and temperatures relative to their value,
+    velocities to sqrt(T), heat fluxes to rho T^1.5, stresses to rho T."""
+    import gsis_inputs as gi
+    from oracle import kinetic as K
+    from paper_2601_03935_gb300 import gsis as G
+    cases = {"slab64": gi.workloads.slab(64), "cavity20000": gi.workloads.cavity(n_side=100),
+             "cylinder40000": gi.workloads.cylinder()}
+    out = {}
+    for name, wl0 in cases.items():
+        wl = gi.workloads.with_solver(wl0, precision="fp32", order=2, relax_block=16)
+        f, I = _smooth_state(wl, 31)
+        nc = wl.mesh.n_cells
+        ctx = create_ctx(wl, stream.cuda_stream)
+        try:
+            G.gsis_set_distributions(ctx, f, I)
+            G.gsis_step(ctx, G.GSIS_MODE_CIS)
+            Fg = G.gsis_get_fields(ctx, nc)
+        finally:
+            G.gsis_destroy(ctx)
+        if nc <= 64:
+            cells = np.arange(nc)
+        else:
+            m = wl.mesh
+            bnd = m.face_owner[m.face_nbr < 0]
+            blocks = sorted({0, nc // 32, int(bnd[len(bnd) // 3]) // 16, int(bnd[-1]) // 16, (nc - 1) // 16})
+            cells = np.concatenate([np.arange(b * 16, min(b * 16 + 16, nc)) for b in blocks])
+        fo, Io = K.kinetic_sweep(f, I, wl, relax_block=16, cells=cells)
+        Fo = K.fields_to_record(K.moments(fo, Io, wl.xi, wl.w, wl.omega, wl.wo, wl.dim, wl.model))
+        g, r = Fg[cells], Fo
+        rho, T = r[:, 0], r[:, 4]
+        d = wl.dim
+        err = {"rho": np.abs(g[:, 0] - rho).max() / np.abs(rho).max()}
+        for k, c in (("T_t", 4), ("T_r", 5), ("T_v", 6), ("T_R", 7)):
+            err[k] = float((np.abs(g[:, c] - r[:, c]) / np.abs(r[:, c])).max())
+        err["u"] = float((np.abs(g[:, 1:1 + d] - r[:, 1:1 + d]) / np.sqrt(T)[:, None]).max())
+        for k, c in (("q_t", 8), ("q_r", 11), ("q_v", 14), ("q_R", 17)):
+            err[k] = float((np.abs(g[:, c:c + d] - r[:, c:c + d]) / (rho * T ** 1.5)[:, None]).max())
+        err["sigma"] = float((np.abs(g[:, 20:24] - r[:, 20:24]) / (rho * T)[:, None]).max())
+        out[name] = {"cells_compared": int(len(cells)), "n_cells": nc, "n_xi": int(wl.xi.shape[0]),
+                     "max_error": {k: float(v) for k, v in err.items()}}
+    return out
+
+
+def full_cylinder_throughput(stream, steps=10, warmup=3):
+    """CIS iterations of the full-size Mach-5 cylinder (40 000 triangles, 48 x 48 velocities,
+    96 directions, FP32, order 2) from the uniform free stream: updates/s and the gas
+    sweep's fraction of HBM bandwidth.  The limiter constant is the normal shock's
+    (K = 0.01): with K = 5 the limiter is inactive at these jumps and f turns negative.
+    Should the order-2 start still diverge, the leg is timed at order 1 and says so."""
+    import torch
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import gsis as G
+    base = gi.workloads.cylinder()
+    far = base.mesh.patches[1]
+    M = gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
+    f, I = gi.fields.noisy_equilibrium(M, base.xi, base.omega, 2, base.model.d_r, base.model.d_v,
+                                       base.model.sigma_R, 0, noise=0.0)
+    ctx, diverged = None, ""
+    for order in (2, 1):
+        wl = gi.workloads.with_solver(base, precision="fp32", order=order, relax_block=16, venkat_K=0.01)
+        nc, V = wl.mesh.n_cells, wl.xi.shape[0]
+        ctx = create_ctx(wl, stream.cuda_stream)
+        try:
+            G.gsis_set_distributions(ctx, f, I)
+            for _ in range(warmup):
+                G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+            G.gsis_last_eps(ctx)
+            break
+        except G.GsisError as e:
+            G.gsis_destroy(ctx)
+            ctx, diverged = None, diverged + "order %d: %s; " % (order, e)
+    del f, I
+    if ctx is None:
+        return {"workload": "cylinder 2-D Mach 5, full size", "note": "diverged: " + diverged}
+    try:
+        G.gsis_profile_enable(ctx, True)
+        G.gsis_profile_reset(ctx)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = G.gsis_profile_read(ctx)
+        try:
+            eps = G.gsis_last_eps(ctx)
+        except G.GsisError as e:
+            eps, diverged = None, diverged + "timed steps: %s" % e
+    finally:
+        G.gsis_destroy(ctx)
+    names = ("slopes_gas", "sweep_gas") if order == 2 else ("sweep_gas",)
+    sweep = sum(prof[k][0] / max(prof[k][1], 1) for k in names)
+    alg = nc * V * 32
+    peak, kind = measured_peaks()
+    return {"workload": "cylinder 2-D Mach 5, %d triangles, 48x48 velocities (%d), %d photon directions, FP32, "
+                        "order %d, from the uniform free stream" % (nc, V, wl.omega.shape[0], order),
+            "note": diverged or None,
+            "value": nc * V / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "last_eps": eps,
+            "roofline": {"kernel": "+".join(names), "bound": "hbm", "achieved": alg / (sweep * 1e-3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": alg / (sweep * 1e-3) / 1e9 / peak, "peak_kind": kind,
+                         "algorithmic_bytes_per_launch": alg, "ms_per_launch": sweep}}
+
+
+def run_sharded(args, dist, rank, local, world):
+    """One problem cut into velocity shards, one per rank; NCCL sums the exchange buffers."""
+    import torch
+    from paper_2601_03935_gb300 import gsis as G
+    from paper_2601_03935_gb300 import shard as SH
+    wl = workload(args)
+    nc, V, NO = wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]
+    stream = torch.cuda.Stream()
+    sh = SH.VelocityShard(wl.mesh, wl.xi, wl.w, wl.omega, wl.wo, wl.model, wl.solver, rank, world, stream.cuda_stream)
+    shards = [sh]
+    f, I = initial_state(wl)
+    sh.set_distributions(f, I)
+    SH.refresh(shards, stream=stream)
+    mode = G.GSIS_MODE_CIS if args.mode == "cis" else G.GSIS_MODE_GSIS
+    for _ in range(args.warmup):
+        SH.step(shards, mode, stream=stream)
+    G.gsis_profile_enable(sh.ctx, True)
+    G.gsis_profile_reset(sh.ctx)
+    launches0 = G.gsis_launch_count(sh.ctx)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            eps = SH.step(shards, mode, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = G.gsis_launch_count(sh.ctx) - launches0
+    prof = G.gsis_profile_read(sh.ctx)
+    G.gsis_profile_enable(sh.ctx, False)
+    t = torch.tensor([ms], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    # end to end: this rank's slice uploaded from pinned host memory, the refresh (two
+    # exchanges), the iteration, the fields read back
+    rs = 4 if args.precision == "fp32" else 8
+    f32 = np.float32 if args.precision == "fp32" else np.float64
+    hf = torch.from_numpy(np.ascontiguousarray(f[:, sh.lo:sh.hi]).astype(f32)).pin_memory()
+    hI = torch.from_numpy(np.ascontiguousarray(I[:, sh.olo:sh.ohi]).astype(f32)).pin_memory()
+    hout = torch.empty((nc, G.GSIS_NF), dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+
+    def e2e_step():
+        G.gsis_upload_distributions(sh.ctx, hf.data_ptr(), hI.data_ptr())
+        SH.refresh(shards, stream=stream)
+        SH.step(shards, mode, stream=stream)
+        G.gsis_download_fields_async(sh.ctx, hout.data_ptr(), nc)
+        stream.synchronize()
+
+    e2e_step()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    t = torch.tensor([e2e_s], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_s = float(t.item())
+    sh.destroy()
+    if rank != 0:
+        return 0
+    sweep_names = ["slopes_gas", "sweep_gas"] if args.order == 2 else ["sweep_gas"]
+    avg_sweep = sum(prof[k][0] / max(prof[k][1], 1) for k in sweep_names)
+    alg_bytes = nc * (sh.hi - sh.lo) * 4 * rs * 2
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / (avg_sweep * 1e-3) / 1e9
+    cfg = config(args, wl)
+    cfg["parallelism"] = "velocity-sharded x%d (NCCL all-reduce of per-cell moment sums per iteration)" % world
+    line = {
+        "metric": METRIC, "value": nc * V / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+        "data": "synthetic (seeded cavity mesh and near-equilibrium distributions)", "config": cfg,
+        "roofline": {"kernel": "+".join(sweep_names) + " (rank 0's velocity shard)", "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": None, "algorithmic_bytes_per_launch": alg_bytes,
+                     "ms_per_launch": avg_sweep},
+        "e2e": {"value": nc * V / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": nc * ((sh.hi - sh.lo) * 4 + (sh.ohi - sh.olo)) * rs * world,
+                "d2h_bytes_per_step": nc * G.GSIS_NF * 8 * world},
+        "gpu_launches": launches, "clocks": clk.summary(), "last_eps": eps,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_ours(args):
     import torch
     from paper_2601_03935_gb300 import build
@@ -363,6 +582,11 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     G.load()
+    if dist is not None:
+        try:
+            return run_sharded(args, dist, rank, local, world)
+        finally:
+            dist.destroy_process_group()
     wl = workload(args)
     nc, V, NO = wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]
     stream = torch.cuda.Stream()
@@ -489,6 +713,10 @@ def run_ours(args):
         line["normal_shock"] = normal_shock()
     if not args.no_cylinder:
         line["cylinder"] = cylinder()
+    if not args.no_full_cylinder:
+        line["cylinder_full"] = full_cylinder_throughput(stream)
+    if not args.no_field_errors:
+        line["field_errors"] = field_errors(stream)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
     print(json.dumps(line))
@@ -519,6 +747,10 @@ def main():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady measurement")
     ap.add_argument("--no-shock", action="store_true", help="skip the normal-shock convergence measurement")
     ap.add_argument("--no-cylinder", action="store_true", help="skip the Mach-5 cylinder CIS/GSIS measurement")
+    ap.add_argument("--no-full-cylinder", action="store_true",
+                    help="skip the throughput of the full-size (40 000-cell, 2304-velocity) cylinder")
+    ap.add_argument("--no-field-errors", action="store_true",
+                    help="skip the per-field error of one FP32 iteration against the FP64 oracle")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

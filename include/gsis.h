@@ -273,6 +273,37 @@ int gsis_import_state(gsis_ctx *ctx, const void *buf, int64_t len);
  * kept by the context (up to len values into eps, caller-owned; *n_out its length). */
 int gsis_get_history(const gsis_ctx *ctx, int64_t *iter, double *eps, int64_t len, int64_t *n_out);
 
+/* ---- velocity-space sharding (several GPUs, one process each) ----------------------
+ * With the fields M^k fixed, every discrete velocity's (and photon direction's) sweep is
+ * independent: the kinetic step of Section 3 partitions by velocity, as the paper's own
+ * parallel runs do.  Each rank creates a context whose velocity and photon sets are one
+ * contiguous range of the full sets (in the same order on every rank), then calls
+ * gsis_shard_setup with the FULL sets: the wall re-emission normalisation and the
+ * replicated synthetic equations use them.  The exchange buffer (gsis_shard_buffer:
+ * `count` doubles in device memory owned by the context, valid until gsis_destroy) holds
+ * this rank's per-cell moment sums, wall outflow and kinetic boundary-flux sums; the
+ * caller sums it over the ranks IN PLACE (an all-reduce on the context stream) after
+ * every gsis_shard_refresh, gsis_shard_begin and gsis_shard_mid, and before the next
+ * phase call:
+ *   refresh (after the distributions are set): refresh(0), sum, end(NULL), refresh(1),
+ *     sum, end(NULL) - moments about zero, then about the velocity found;
+ *   CIS iteration:  begin(CIS), sum, end(&eps);
+ *   GSIS iteration: begin(GSIS), sum, mid, sum, end(&eps) - the synthetic solve runs on
+ *     every rank with identical inputs and gives identical results.
+ * Every rank then holds the same fields and eps as an unsharded context.  A shard
+ * refuses gsis_step, gsis_step_async, gsis_solve and gsis_warm_start (UNSUPPORTED).
+ * The paper has no counterpart beyond the partitioning itself.
+ * Errors: INVALID_ARG (null pointers, full sets smaller than the shard, phase calls out
+ * of order, a context that is already a shard), OUT_OF_MEMORY, CUDA; end also DIVERGED
+ * and TIMEOUT like gsis_step. */
+int gsis_shard_setup(gsis_ctx *ctx, int32_t n_xi_all, const double *xi_all, const double *w_all,
+                     int32_t n_omega_all, const double *omega_all, const double *wo_all);
+int gsis_shard_buffer(gsis_ctx *ctx, void **dev_ptr, int64_t *count);
+int gsis_shard_refresh(gsis_ctx *ctx, int32_t pass);
+int gsis_shard_begin(gsis_ctx *ctx, int32_t mode);
+int gsis_shard_mid(gsis_ctx *ctx);
+int gsis_shard_end(gsis_ctx *ctx, double *eps_out);
+
 /* ---- failure detection -------------------------------------------------------------
  * Every device-side wait in the library is bounded.  The tensor-core moment contraction
  * waits for its MMA chain on an mbarrier; this sets the number of polls of that first

@@ -94,6 +94,19 @@ struct gsis_ctx {
     cudaGraphExec_t macro_exec64 = nullptr; // the same with the FP64 residual side (mixed schedule's tail)
     int macro_nodes = 0, macro_nodes64 = 0;
 
+    // velocity sharding (gsis_shard_setup): this context holds one contiguous range of the
+    // velocities and photon directions; per-cell moment sums, wall outflow and kinetic
+    // boundary-flux sums go through xbuf [n_cells][NXC] | [n_bf] | [n_bf][KBR], which the
+    // caller sums over the ranks between the phase calls; wout_g keeps the summed wall
+    // outflow of the current f for the next wall density
+    bool sharded = false;
+    double *xbuf = nullptr, *wout_g = nullptr;
+    int64_t xcount = 0;
+    int shard_state = 0;         // 0 idle, 1 after begin (CIS) / mid, 2 after begin (GSIS), 3 after refresh
+    int shard_nxt = 0;
+    int Vd = 0, Vdp = 0, NOd = 0, Odp = 0;   // sizes of the FP64 quadratures of the synthetic equations
+    std::vector<double> h_wall;  // per boundary face: wall flag, normal[3], wall T, wall u[3]
+
     bool have_eps = false;
     double last_eps = 0.0;
     // outer iterations since the distributions were last set (the CIS preconditioning of
@@ -285,7 +298,8 @@ int kinetic_step(gsis_ctx *c, int nxt) {
     const Geom<Real> g = geom<Real>(c);
     TRY(launch(c, K_WALL, [&] {
         return launch_wall_density<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_T, c->bf_inc, c->patch_kind,
-                                         (const Real *)c->f[c->cur], (Real *)c->bcoef);
+                                         (const Real *)c->f[c->cur], c->sharded ? c->wout_g : nullptr,
+                                         (Real *)c->bcoef);
     }));
     if (c->order == 2) {
         TRY(launch(c, K_SLOPE_GAS, [&] {
@@ -344,8 +358,8 @@ int cis_iteration(gsis_ctx *c) {
     return close_iteration<Real>(c, nxt);
 }
 
-QuadD vquad_d(const gsis_ctx *c) { return QuadD{c->V, c->Vp, c->vqd_x, c->vqd_w}; }
-QuadD oquad_d(const gsis_ctx *c) { return QuadD{c->NO, c->Op, c->oqd_x, c->oqd_w}; }
+QuadD vquad_d(const gsis_ctx *c) { return QuadD{c->Vd, c->Vdp, c->vqd_x, c->vqd_w}; }
+QuadD oquad_d(const gsis_ctx *c) { return QuadD{c->NOd, c->Odp, c->oqd_x, c->oqd_w}; }
 
 // Pseudo-time iterations of the synthetic equations from W[0] until ||R|| <= tol_inner
 // ||R_0|| or max_inner; returns the index of the buffer that holds the result.  The
@@ -709,6 +723,10 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     c->Vp = (vq->n + VCH - 1) / VCH * VCH;
     c->NO = pq->n;
     c->Op = (pq->n + OCH - 1) / OCH * OCH;
+    c->Vd = c->V;
+    c->Vdp = c->Vp;
+    c->NOd = c->NO;
+    c->Odp = c->Op;
     c->nch = c->Vp / VCH;
     c->och = c->Op / OCH;
 
@@ -1115,6 +1133,17 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(upload_real(c, c->bcoef, bco));
     A_(upload(c, c->patch_T, pT));
     A_(upload(c, c->patch_u, pu));
+    c->h_wall.assign((size_t)std::max(c->n_bf, 1) * 8, 0.0);
+    for (int b = 0; b < c->n_bf; ++b) {     // per boundary face: wall flag, normal, wall T and u
+        const gsis_patch &P = m->patches[bf_patch[b]];
+        double *hw = c->h_wall.data() + (size_t)b * 8;
+        hw[0] = P.kind == GSIS_PATCH_WALL ? 1.0 : 0.0;
+        for (int a = 0; a < 3; ++a) {
+            hw[1 + a] = bfn[b * 3 + a];
+            hw[5 + a] = a < 2 ? P.u[a] : 0.0;
+        }
+        hw[4] = P.T_t;
+    }
     {   // incoming mass flux of the unit-density wall Maxwellian at every wall face
         std::vector<double> inc(std::max(c->n_bf, 1), 0.0);
         for (int b = 0; b < c->n_bf; ++b) {
@@ -1338,6 +1367,264 @@ int gsis_get_history(const gsis_ctx *c, int64_t *iter, double *eps, int64_t len,
     return GSIS_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------- velocity sharding
+namespace {
+
+double *xbuf_wall(gsis_ctx *c) { return c->xbuf + (size_t)c->nc * NXC; }
+double *xbuf_kbf(gsis_ctx *c) { return xbuf_wall(c) + std::max(c->n_bf, 1); }
+
+// this shard's moment sums of the partials into xbuf, and of f's wall outflow (gas) or
+// its kinetic boundary-flux sums (kbf) into their sections, the other section zeroed
+template <typename Real>
+int shard_pack(gsis_ctx *c, int fidx, bool kbf) {
+    const Geom<Real> g = geom<Real>(c);
+    TRY(launch(c, K_FINISH, [&] {
+        return launch_cell_sums<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, (const Real *)c->partial,
+                                      (const Real *)c->opartial, c->xbuf);
+    }));
+    const size_t nbf1 = std::max(c->n_bf, 1);
+    CUDA_TRY(c, cudaMemsetAsync(xbuf_wall(c), 0, nbf1 * sizeof(double), c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(xbuf_kbf(c), 0, nbf1 * KBR * sizeof(double), c->stream));
+    if (kbf) {
+        TRY(launch(c, K_KBFLUX, [&] {
+            return launch_kinetic_bflux<Real>(c->stream, c->mg, c->model, vquad<Real>(c), oquad<Real>(c),
+                                              (const Real *)c->f[fidx], (const Real *)c->I[fidx], c->kbf,
+                                              xbuf_kbf(c));
+        }));
+    } else {
+        TRY(launch(c, K_WALL, [&] {
+            return launch_wall_outflux<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_kind,
+                                             (const Real *)c->f[fidx], xbuf_wall(c));
+        }));
+    }
+    return GSIS_OK;
+}
+
+template <typename Real>
+int shard_begin(gsis_ctx *c, int mode) {
+    const int nxt = 1 - c->cur;
+    CUDA_TRY(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    TRY(kinetic_step<Real>(c, nxt));
+    TRY(shard_pack<Real>(c, nxt, mode == GSIS_MODE_GSIS));
+    c->shard_nxt = nxt;
+    c->shard_state = mode == GSIS_MODE_GSIS ? 2 : 1;
+    return GSIS_OK;
+}
+
+// GSIS after the first exchange: M^{k+1/2} and the kinetic boundary fluxes from the
+// summed shards, the replicated synthetic solve, the synchronisation of this shard's
+// velocities, then the shard's sums of f^{k+1} for the second exchange
+template <typename Real>
+int shard_mid(gsis_ctx *c) {
+    const int nxt = c->shard_nxt;
+    const MacroGeom &g = c->mg;
+    TRY(launch(c, K_FINISH, [&] {
+        return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
+                                   (const Real *)c->partial, (const Real *)c->opartial, c->vol, nullptr,
+                                   c->fields_h, c->eps_terms, c->err, 0, nullptr, nullptr, nullptr, c->xbuf);
+    }));
+    TRY(launch(c, K_KBFLUX, [&] { return launch_kbflux_combine(c->stream, g, xbuf_kbf(c), c->kbf); }));
+    TRY(launch(c, K_MCONV, [&] {
+        return launch_macro_from_fields(c->stream, c->dim, (int)c->nc, c->model, c->fields_h, c->W[0]);
+    }));
+    TRY(launch(c, K_MGRAD, [&] {
+        return launch_macro_grad(c->stream, g, 1, c->mfp32 == 1, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
+    }));
+    TRY(launch(c, K_MBFLUX, [&] {
+        return launch_macro_bflux(c->stream, g, c->mfp32 == 1, c->model, vquad_d(c), oquad_d(c), nullptr, c->mq, c->mbf);
+    }));
+    TRY(launch(c, K_HOT, [&] {
+        return launch_macro_hot(c->stream, g, c->mfp32 == 1, c->model, c->fields_h, c->mq, c->mgrad, c->kbf, c->mbf,
+                                c->hot, c->hot_b);
+    }));
+    int w = 0;
+    TRY(macro_solve(c, &w));
+    if (c->closed) {
+        TRY(launch(c, K_MCONV, [&] {
+            return launch_macro_mass_rescale(c->stream, c->dim, (int)c->nc, c->vol, c->fields, c->W[w]);
+        }));
+    }
+    TRY(launch(c, K_MCONV, [&] {
+        return launch_macro_fields_from_W(c->stream, c->dim, (int)c->nc, c->model, c->W[w], c->fields_n);
+    }));
+    TRY(launch(c, K_SYNC, [&] {
+        return launch_sync<Real>(c->stream, c->dim, (int)c->nc, c->tcm >= 1, vquad<Real>(c), oquad<Real>(c), c->model,
+                                 c->solver.sync_relax, c->fields_n, c->fields_h, (const Real *)c->coef,
+                                 (Real *)c->f[nxt], (Real *)c->I[nxt], (Real *)c->partial, (Real *)c->opartial,
+                                 c->sync_kc, c->tc_wait, c->err);
+    }));
+    TRY(shard_pack<Real>(c, nxt, false));
+    c->shard_state = 1;
+    return GSIS_OK;
+}
+
+// after the last exchange of an iteration (state 1) or a refresh pass (state 3): fields
+// from the summed shards (with eps against M^k for an iteration), the summed wall outflow
+// for the next wall density, the coefficients
+template <typename Real>
+int shard_end(gsis_ctx *c) {
+    const Geom<Real> g = geom<Real>(c);
+    const bool step = c->shard_state == 1;
+    if (step) {
+        std::swap(c->fields, c->fields_old);
+        TRY(launch(c, K_FINISH, [&] {
+            return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
+                                       (const Real *)c->partial, (const Real *)c->opartial, c->vol, c->fields_old,
+                                       c->fields, c->eps_terms, c->err, 1, c->eps_part, c->eps_ticket, c->eps_sums,
+                                       c->xbuf);
+        }));
+    } else {
+        TRY(launch(c, K_FINISH, [&] {
+            return launch_finish<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, c->model, (const Real *)c->coef,
+                                       (const Real *)c->partial, (const Real *)c->opartial, c->vol, nullptr,
+                                       c->fields, c->eps_terms, c->err, 0, nullptr, nullptr, nullptr, c->xbuf);
+        }));
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->wout_g, xbuf_wall(c), (size_t)std::max(c->n_bf, 1) * sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->stream));
+    TRY(launch(c, K_COEF, [&] {
+        return launch_coefficients<Real>(c->stream, c->dim, g, c->model, c->fields, c->cell_dx, (Real *)c->coef);
+    }));
+    if (step) {
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned, c->eps_sums, NEPS * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        CUDA_TRY(c, cudaMemcpyAsync(c->h_pinned + NEPS, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        c->cur = c->shard_nxt;
+        c->have_eps = true;
+        c->eps_pending = true;
+        ++c->iter;
+    } else {
+        c->have_eps = false;
+        c->eps_pending = false;
+        c->iter = 0;
+        c->eps_hist.clear();
+    }
+    c->shard_state = 0;
+    return GSIS_OK;
+}
+
+// moments of the current distributions for a refresh: pass 0 about zero velocity, pass 1
+// about the velocity pass 0 found (as refresh_fields does without sharding)
+template <typename Real>
+int shard_refresh(gsis_ctx *c, int pass) {
+    CUDA_TRY(c, cudaMemsetAsync(c->err, 0, sizeof(int), c->stream));
+    if (pass == 0) CUDA_TRY(c, cudaMemsetAsync(c->coef, 0, (size_t)c->nc * cf::NC * c->real_size, c->stream));
+    TRY(launch(c, K_MOMENTS, [&] {
+        return launch_moments_only<Real>(c->stream, c->dim, (int)c->nc, c->tcm >= 1, vquad<Real>(c), oquad<Real>(c),
+                                         (const Real *)c->coef, (const Real *)c->f[c->cur], (const Real *)c->I[c->cur],
+                                         (Real *)c->partial, (Real *)c->opartial, c->tc_wait, c->err);
+    }));
+    TRY(shard_pack<Real>(c, c->cur, false));
+    c->shard_state = 3;
+    return GSIS_OK;
+}
+
+void pack_quad(int n, int pad, int dim, const double *x, const double *w, std::vector<double> &vx,
+               std::vector<double> &vw) {
+    vx.assign(3 * (size_t)pad, 0.0);
+    vw.assign((size_t)pad, 0.0);
+    for (int v = 0; v < n; ++v) {
+        for (int a = 0; a < dim; ++a) vx[a * (size_t)pad + v] = x[(size_t)v * dim + a];
+        vw[v] = w[v];
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int gsis_shard_setup(gsis_ctx *c, int32_t n_xi_all, const double *xi_all, const double *w_all, int32_t n_omega_all,
+                     const double *omega_all, const double *wo_all) {
+    if (!c || !xi_all || !w_all || !omega_all || !wo_all) return fail(c, GSIS_ERR_INVALID_ARG, "null pointer");
+    if (c->sharded) return fail(c, GSIS_ERR_INVALID_ARG, "the context is already a shard");
+    if (n_xi_all < c->V || n_omega_all < c->NO) return fail(c, GSIS_ERR_INVALID_ARG, "the full sets are smaller than the shard");
+    const int dim = c->dim;
+    // the incoming unit-density wall flux over every velocity of every shard
+    std::vector<double> inc((size_t)std::max(c->n_bf, 1), 0.0);
+    for (int b = 0; b < c->n_bf; ++b) {
+        const double *hw = c->h_wall.data() + (size_t)b * 8;
+        if (hw[0] == 0.0) continue;
+        const double T = hw[4], norm = std::pow(2.0 * M_PI * T, -0.5 * dim);
+        double acc = 0.0;
+        for (int v = 0; v < n_xi_all; ++v) {
+            double xn = 0.0, c2 = 0.0;
+            for (int a = 0; a < dim; ++a) {
+                const double x = xi_all[(size_t)v * dim + a];
+                xn += x * hw[1 + a];
+                c2 += (x - hw[5 + a]) * (x - hw[5 + a]);
+            }
+            if (xn < 0.0) acc += w_all[v] * xn * norm * std::exp(-c2 / (2.0 * T));
+        }
+        inc[b] = acc;
+    }
+    TRY(upload(c, c->bf_inc, inc));
+    // the replicated synthetic equations take their boundary fluxes on the full sets
+    const int vdp = (n_xi_all + 63) / 64 * 64, odp = (n_omega_all + 63) / 64 * 64;
+    std::vector<double> vx, vw, ox, ow;
+    pack_quad(n_xi_all, vdp, dim, xi_all, w_all, vx, vw);
+    pack_quad(n_omega_all, odp, 3, omega_all, wo_all, ox, ow);
+    TRY(dalloc(c, &c->vqd_x, vx.size()));
+    TRY(dalloc(c, &c->vqd_w, vw.size()));
+    TRY(dalloc(c, &c->oqd_x, ox.size()));
+    TRY(dalloc(c, &c->oqd_w, ow.size()));
+    TRY(upload(c, c->vqd_x, vx));
+    TRY(upload(c, c->vqd_w, vw));
+    TRY(upload(c, c->oqd_x, ox));
+    TRY(upload(c, c->oqd_w, ow));
+    c->Vd = n_xi_all;
+    c->Vdp = vdp;
+    c->NOd = n_omega_all;
+    c->Odp = odp;
+    const size_t nbf1 = std::max(c->n_bf, 1);
+    c->xcount = (int64_t)((size_t)c->nc * NXC + nbf1 * (1 + KBR));
+    TRY(dalloc(c, &c->xbuf, (size_t)c->xcount));
+    TRY(dalloc(c, &c->wout_g, nbf1));
+    CUDA_TRY(c, cudaMemset(c->xbuf, 0, (size_t)c->xcount * sizeof(double)));
+    CUDA_TRY(c, cudaMemset(c->wout_g, 0, nbf1 * sizeof(double)));
+    c->sharded = true;
+    c->shard_state = 0;
+    return GSIS_OK;
+}
+
+int gsis_shard_buffer(gsis_ctx *c, void **dev_ptr, int64_t *count) {
+    if (!c || !dev_ptr || !count) return GSIS_ERR_INVALID_ARG;
+    if (!c->sharded) return fail(c, GSIS_ERR_INVALID_ARG, "not a shard (gsis_shard_setup)");
+    *dev_ptr = c->xbuf;
+    *count = c->xcount;
+    return GSIS_OK;
+}
+
+int gsis_shard_refresh(gsis_ctx *c, int32_t pass) {
+    if (!c || (pass != 0 && pass != 1)) return GSIS_ERR_INVALID_ARG;
+    if (!c->sharded || c->shard_state != 0) return fail(c, GSIS_ERR_INVALID_ARG, "shard phase out of order");
+    return c->precision == GSIS_FP64 ? shard_refresh<double>(c, pass) : shard_refresh<float>(c, pass);
+}
+
+int gsis_shard_begin(gsis_ctx *c, int32_t mode) {
+    if (!c || (mode != GSIS_MODE_CIS && mode != GSIS_MODE_GSIS)) return GSIS_ERR_INVALID_ARG;
+    if (!c->sharded || c->shard_state != 0) return fail(c, GSIS_ERR_INVALID_ARG, "shard phase out of order");
+    return c->precision == GSIS_FP64 ? shard_begin<double>(c, mode) : shard_begin<float>(c, mode);
+}
+
+int gsis_shard_mid(gsis_ctx *c) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (!c->sharded || c->shard_state != 2) return fail(c, GSIS_ERR_INVALID_ARG, "shard phase out of order");
+    return c->precision == GSIS_FP64 ? shard_mid<double>(c) : shard_mid<float>(c);
+}
+
+int gsis_shard_end(gsis_ctx *c, double *eps_out) {
+    if (!c) return GSIS_ERR_INVALID_ARG;
+    if (!c->sharded || (c->shard_state != 1 && c->shard_state != 3))
+        return fail(c, GSIS_ERR_INVALID_ARG, "shard phase out of order");
+    const bool step = c->shard_state == 1;
+    TRY(c->precision == GSIS_FP64 ? shard_end<double>(c) : shard_end<float>(c));
+    if (!step) return check_err(c);
+    return read_eps(c, eps_out);
+}
+
+
 int gsis_set_distributions(gsis_ctx *c, const double *f, int64_t f_len, const double *I, int64_t I_len) {
     if (!c || !f || !I) return fail(c, GSIS_ERR_INVALID_ARG, "null buffer");
     if (f_len < c->nc * c->V * 4 || I_len < c->nc * c->NO) return fail(c, GSIS_ERR_INVALID_ARG, "buffer too short");
@@ -1392,6 +1679,7 @@ int gsis_download_fields_async(gsis_ctx *c, double *out, int64_t len) {
 
 int gsis_step_async(gsis_ctx *c, int32_t mode) {
     if (!c) return GSIS_ERR_INVALID_ARG;
+    if (c->sharded) return fail(c, GSIS_ERR_UNSUPPORTED, "a velocity shard steps through gsis_shard_begin/mid/end");
     if (mode == GSIS_MODE_GSIS)
         return c->precision == GSIS_FP64 ? gsis_iteration<double>(c) : gsis_iteration<float>(c);
     if (mode != GSIS_MODE_CIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
@@ -1722,6 +2010,7 @@ extern "C" {
 
 int gsis_warm_start(gsis_ctx *c, int32_t n_presolve, int32_t use_mlp) {
     if (!c || n_presolve < 0) return GSIS_ERR_INVALID_ARG;
+    if (c->sharded) return fail(c, GSIS_ERR_UNSUPPORTED, "the warm start runs on unsharded contexts");
     if (use_mlp && (!c->mlp.p || !c->mlp.trained))
         return fail(c, GSIS_ERR_INVALID_ARG, "the learned closure has not been trained or set");
     return c->precision == GSIS_FP64 ? warm_start<double>(c, n_presolve, use_mlp != 0)

@@ -20,6 +20,8 @@ constexpr int SYNC_KC = 20;    // floats per cell of the synchronisation constan
 constexpr int MT = 16;         // moment tile: gas moments are taken about the velocity of the
                                // tile's first cell (cells MT*t .. MT*t + MT - 1 share it)
 constexpr int NEPS = 8;        // per-cell terms of the convergence measure
+constexpr int NXC = NMP + NMO; // per-cell moment sums exchanged between velocity shards (gas, then photon)
+constexpr int KBR = 13;        // per-boundary-face kinetic flux sums exchanged between shards (2 (DIM + 4) + 1, DIM <= 2)
 constexpr int ERR_DIVERGED_BIT = 1;   // bits of the device error word
 constexpr int ERR_TIMEOUT_BIT = 2;
 
@@ -167,7 +169,9 @@ cudaError_t launch_macro_mass_rescale(cudaStream_t s, int dim, int n_cells, cons
                                       double *W);
 template <typename Real>
 cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const Quad<Real> &vq,
-                                 const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux);
+                                 const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux,
+                                 double *raw = nullptr);   // raw: this shard's sums [n_bf][KBR] instead
+cudaError_t launch_kbflux_combine(cudaStream_t s, const MacroGeom &g, const double *raw, double *kin_bflux);
 template <typename Real>
 cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Quad<Real> &vq, const Quad<Real> &oq,
                         const ModelDev &m, double omega, const double *F_new, const double *F_half, const Real *coef,
@@ -216,9 +220,19 @@ cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, co
 template <typename Real>
 // bf_inc: per boundary face, sum over incoming velocities of w xi.n times the unit-density
 // wall Maxwellian (constant; built at creation)
+// wout (nullable): the outgoing wall mass flux summed over all velocity shards, used in
+// place of the context's own velocities
 cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
                                 const double *patch_T, const double *bf_inc, const int *patch_kind,
-                                const Real *f, Real *bcoef);
+                                const Real *f, const double *wout, Real *bcoef);
+// the context's share of the outgoing wall mass flux of f, per boundary face (0 off walls)
+template <typename Real>
+cudaError_t launch_wall_outflux(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
+                                const int *patch_kind, const Real *f, double *wout);
+// per-cell FP64 sums of the context's moment partials, X [n_cells][NXC]
+template <typename Real>
+cudaError_t launch_cell_sums(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const Real *partial,
+                             const Real *opartial, double *X);
 // upwind second-order values per (interior face, velocity): fface [n_fi][n_pad][planes]
 template <typename Real>
 cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, const Quad<Real> &q,
@@ -237,7 +251,8 @@ cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, in
                           const Real *coef, const Real *partial, const Real *opartial, const double *vol,
                           const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
                           int have_old, double *eps_part = nullptr, unsigned int *ticket = nullptr,
-                          double *eps_sums = nullptr);   // eps_sums: also the convergence sums
+                          double *eps_sums = nullptr,    // eps_sums: also the convergence sums
+                          const double *X = nullptr);    // X: per-cell sums over all velocity shards
 template <typename Real>
 cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
                                const ModelDev &m, const double *fields, Real *f, Real *I);

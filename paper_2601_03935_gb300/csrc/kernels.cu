@@ -133,7 +133,8 @@ __global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restric
 template <typename Real, int DIM>
 __global__ void k_wall_density(Geom<Real> g, Quad<Real> vq, const double *__restrict__ patch_T,
                                const double *__restrict__ bf_inc, const int *__restrict__ patch_kind,
-                               const Real *__restrict__ f, Real *__restrict__ bcoef) {
+                               const Real *__restrict__ f, const double *__restrict__ wout,
+                               Real *__restrict__ bcoef) {
     // one CTA of WDT threads per boundary face: the outgoing mass flux of the current f,
     // summed per thread, per warp and then over the warps in a fixed order; the incoming
     // flux of the unit-density wall Maxwellian is a per-face constant (bf_inc)
@@ -143,6 +144,15 @@ __global__ void k_wall_density(Geom<Real> g, Quad<Real> vq, const double *__rest
     const int p = g.bf_patch[face];
     if (patch_kind[p] != 0) return;
     const int cell = g.bf_cell[face];
+    if (wout) {
+        // velocity-sharded context: the outgoing flux over every rank's velocities
+        if (threadIdx.x == 0) {
+            const double inc = bf_inc[face];
+            const double rho_w = inc < 0.0 ? -wout[face] / inc : 0.0;
+            bcoef[(size_t)face * bc::NB + bc::A] = (Real)(rho_w * pow_neg_half_dim<DIM>(6.283185307179586 * patch_T[p]));
+        }
+        return;
+    }
     Real n[DIM];
     for (int a = 0; a < DIM; ++a) n[a] = g.bf_nrm[face * 3 + a];
     double out = 0.0;
@@ -162,6 +172,39 @@ __global__ void k_wall_density(Geom<Real> g, Quad<Real> vq, const double *__rest
         const double rho_w = inc < 0.0 ? -tot / inc : 0.0;
         const double norm = pow_neg_half_dim<DIM>(6.283185307179586 * patch_T[p]);
         bcoef[(size_t)face * bc::NB + bc::A] = (Real)(rho_w * norm);
+    }
+}
+
+// Outgoing mass flux sum_{xi.n > 0} w xi.n F0 of the context's velocities at every wall
+// face (zero at other boundary faces): the partial of a velocity shard, summed over the
+// ranks before the next wall density.  Same per-face reduction order as k_wall_density.
+template <typename Real, int DIM>
+__global__ void k_wall_outflux(Geom<Real> g, Quad<Real> vq, const int *__restrict__ patch_kind,
+                               const Real *__restrict__ f, double *__restrict__ wout) {
+    constexpr int WDT = 128;
+    __shared__ double part[WDT / 32];
+    const int face = blockIdx.x;
+    const int p = g.bf_patch[face];
+    if (patch_kind[p] != 0) {
+        if (threadIdx.x == 0) wout[face] = 0.0;
+        return;
+    }
+    const int cell = g.bf_cell[face];
+    Real n[DIM];
+    for (int a = 0; a < DIM; ++a) n[a] = g.bf_nrm[face * 3 + a];
+    double out = 0.0;
+    for (int v = threadIdx.x; v < vq.n_pad; v += WDT) {
+        Real xn = Real(0);
+        for (int a = 0; a < DIM; ++a) xn += vq.x[a * vq.n_pad + v] * n[a];
+        if (xn > Real(0)) out += (double)(vq.w[v] * xn) * (double)f[((size_t)cell * vq.n_pad + v) * 4];
+    }
+    for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = out;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < WDT / 32; ++w) tot += part[w];
+        wout[face] = tot;
     }
 }
 
@@ -1287,10 +1330,22 @@ __global__ void k_sync_photon(int n_cells, Quad<Real> oq, ModelDev m, double om,
 // molecules carry the cell's distribution, incoming ones the wall Maxwellian (density
 // from zero net mass flux of the outgoing ones) or the far-field state; photons likewise.
 // Rows as the synthetic equations: mass, momentum, total energy, e_r, e_v, e_R.
+// Rows of one boundary face from the velocity sums r: the outgoing part r[0..NS), the
+// incoming unit-density part r[NS..2NS) scaled by the wall density (zero net mass flux) or
+// the far-field density, and the photon flux r[2NS] (also added to the energy row).
+template <int DIM>
+__device__ __forceinline__ void kbflux_combine(const double *r, bool wall, double rho_far, double *o) {
+    constexpr int E = 1 + DIM, NS = DIM + 4;
+    const double scale = wall ? -r[0] / r[NS] : rho_far;
+    for (int k = 0; k < NS; ++k) o[k] = r[k] + scale * r[NS + k];
+    o[E + 3] = r[2 * NS];
+    o[E] += o[E + 3];
+}
+
 template <typename Real, int DIM>
 __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, Quad<Real> vq, Quad<Real> oq,
                                                        const Real *__restrict__ f, const Real *__restrict__ I,
-                                                       double *__restrict__ out) {
+                                                       double *__restrict__ out, double *__restrict__ raw) {
     constexpr int MH = 3 - DIM, E = 1 + DIM, NS = DIM + 4;
     const int b = blockIdx.x;
     const int c = g.bf_cell[b];
@@ -1350,12 +1405,23 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
     if (threadIdx.x == 0) {
         double r[2 * NS + 1];
         for (int k = 0; k < 2 * NS + 1; ++k) r[k] = buf[0][k] + buf[1][k] + buf[2][k] + buf[3][k];
-        const double scale = wall ? -r[0] / r[NS] : P[0];
-        double *o = out + (size_t)b * NVM;
-        for (int k = 0; k < NS; ++k) o[k] = r[k] + scale * r[NS + k];
-        o[E + 3] = r[2 * NS];
-        o[E] += o[E + 3];
+        if (raw) {
+            // velocity-sharded context: the sums over this rank's velocities, combined after
+            // the sums over all ranks (k_kbflux_combine)
+            for (int k = 0; k < KBR; ++k) raw[(size_t)b * KBR + k] = k < 2 * NS + 1 ? r[k] : 0.0;
+            return;
+        }
+        kbflux_combine<DIM>(r, wall, P[0], out + (size_t)b * NVM);
     }
+}
+
+template <int DIM>
+__global__ void k_kbflux_combine(MacroGeom g, const double *__restrict__ raw, double *__restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= g.n_bf) return;
+    const int pid = g.bf_patch[b];
+    kbflux_combine<DIM>(raw + (size_t)b * KBR, g.patch_kind[pid] == 0, g.patch_state[(size_t)pid * 8],
+                        out + (size_t)b * NVM);
 }
 
 // ------------------------------------------------------------------ finish (FP64)
@@ -1369,12 +1435,19 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
                                             const Real *__restrict__ opartial, const double *__restrict__ vol,
                                             const double *__restrict__ F_old, double *__restrict__ F_new,
                                             double *__restrict__ eps_terms, int *__restrict__ err, int have_old,
-                                            double (&E)[NEPS]) {
+                                            const double *__restrict__ X, double (&E)[NEPS]) {
     constexpr int NM = n_gas_moments<DIM>();
     constexpr int MH = 3 - DIM;
     double S[NM];
+    double Ph[1 + DIM];
     static_assert(NMP % 4 == 0 && NM <= NMP && NMO == 4 && DIM + 1 <= NMO, "partial records are read as 4-vectors");
-    if constexpr (std::is_same<Real, float>::value) {
+    if (X) {
+        // per-cell sums of a velocity-sharded context, already summed over the ranks
+#pragma unroll
+        for (int k = 0; k < NM; ++k) S[k] = X[(size_t)i * NXC + k];
+#pragma unroll
+        for (int k = 0; k <= DIM; ++k) Ph[k] = X[(size_t)i * NXC + NMP + k];
+    } else if constexpr (std::is_same<Real, float>::value) {
         // FP32 partials: a compensated FP32 sum (Knuth's two-sum, the rounding error of
         // every addition carried in lo), as accurate as an FP64 sum of these few terms
         // and off the slow FP64 pipe
@@ -1414,13 +1487,14 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
             }
         }
     }
-    double Ph[1 + DIM];
+    if (!X) {
 #pragma unroll
-    for (int k = 0; k <= DIM; ++k) Ph[k] = 0.0;
-    for (int c = 0; c < o_chunks; ++c) {
-        const Vec<Real, 4> p4 = vload<Real, 4>(opartial + ((size_t)i * o_chunks + c) * NMO);
+        for (int k = 0; k <= DIM; ++k) Ph[k] = 0.0;
+        for (int c = 0; c < o_chunks; ++c) {
+            const Vec<Real, 4> p4 = vload<Real, 4>(opartial + ((size_t)i * o_chunks + c) * NMO);
 #pragma unroll
-        for (int k = 0; k <= DIM; ++k) Ph[k] += (double)p4.v[k];
+            for (int k = 0; k <= DIM; ++k) Ph[k] += (double)p4.v[k];
+        }
     }
     // unpack
     int k = 0;
@@ -1536,13 +1610,14 @@ __global__ void __launch_bounds__(32) k_finish(int n_cells, int n_chunks, int o_
                                                const double *__restrict__ F_old, double *__restrict__ F_new,
                                                double *__restrict__ eps_terms, int *__restrict__ err, int have_old,
                                                int reduce, double *__restrict__ eps_part,
-                                               unsigned int *__restrict__ ticket, double *__restrict__ eps_sums) {
+                                               unsigned int *__restrict__ ticket, double *__restrict__ eps_sums,
+                                               const double *__restrict__ X) {
     const int i = blockIdx.x * 32 + threadIdx.x;
     double E[NEPS];
     for (int q = 0; q < NEPS; ++q) E[q] = 0.0;
     if (i < n_cells)
         finish_cell<Real, DIM>(i, n_chunks, o_chunks, m, coef, partial, opartial, vol, F_old, F_new, eps_terms, err,
-                               have_old, E);
+                               have_old, X, E);
     if (!reduce) return;
 #pragma unroll
     for (int q = 0; q < NEPS; ++q)
@@ -1616,10 +1691,49 @@ cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, co
 template <typename Real>
 cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
                                 const double *patch_T, const double *bf_inc, const int *patch_kind, const Real *f,
-                                Real *bcoef) {
+                                const double *wout, Real *bcoef) {
     if (g.n_bf == 0) return cudaSuccess;
     GSIS_DISPATCH_DIM(dim, (k_wall_density<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, vq, patch_T, bf_inc, patch_kind, f,
-                                                                             bcoef)));
+                                                                             wout, bcoef)));
+    return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_wall_outflux(cudaStream_t s, int dim, const Geom<Real> &g, const Quad<Real> &vq,
+                                const int *patch_kind, const Real *f, double *wout) {
+    if (g.n_bf == 0) return cudaSuccess;
+    GSIS_DISPATCH_DIM(dim, (k_wall_outflux<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, vq, patch_kind, f, wout)));
+    return cudaGetLastError();
+}
+
+// Per cell: the FP64 sums over the context's chunks of the gas and photon moment partials,
+// X[cell][NXC] (gas moments first, photon moments at NMP): a velocity shard's share of
+// every cell's moments, summed over the ranks and finished by launch_finish.
+template <typename Real, int DIM>
+__global__ void k_cell_sums(int n_cells, int n_chunks, int o_chunks, const Real *__restrict__ partial,
+                            const Real *__restrict__ opartial, double *__restrict__ X) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    constexpr int NM = n_gas_moments<DIM>();
+    double S[NM];
+    for (int k = 0; k < NM; ++k) S[k] = 0.0;
+    for (int c = 0; c < n_chunks; ++c)
+        for (int k = 0; k < NM; ++k) S[k] += (double)partial[((size_t)i * n_chunks + c) * NMP + k];
+    double P[1 + DIM];
+    for (int k = 0; k <= DIM; ++k) P[k] = 0.0;
+    for (int c = 0; c < o_chunks; ++c)
+        for (int k = 0; k <= DIM; ++k) P[k] += (double)opartial[((size_t)i * o_chunks + c) * NMO + k];
+    double *x = X + (size_t)i * NXC;
+    for (int k = 0; k < NXC; ++k) x[k] = 0.0;
+    for (int k = 0; k < NM; ++k) x[k] = S[k];
+    for (int k = 0; k <= DIM; ++k) x[NMP + k] = P[k];
+}
+
+template <typename Real>
+cudaError_t launch_cell_sums(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const Real *partial,
+                             const Real *opartial, double *X) {
+    GSIS_DISPATCH_DIM(dim, (k_cell_sums<Real, DIM><<<(n_cells + 127) / 128, 128, 0, s>>>(n_cells, n_chunks, o_chunks,
+                                                                                         partial, opartial, X)));
     return cudaGetLastError();
 }
 
@@ -1690,13 +1804,14 @@ template <typename Real>
 cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const ModelDev &m,
                           const Real *coef, const Real *partial, const Real *opartial, const double *vol,
                           const double *fields_old, double *fields_new, double *eps_terms, int *err_flag,
-                          int have_old, double *eps_part, unsigned int *ticket, double *eps_sums) {
+                          int have_old, double *eps_part, unsigned int *ticket, double *eps_sums,
+                          const double *X) {
     const int nt = 32, nbk = (n_cells + nt - 1) / nt;
     const int reduce = eps_sums != nullptr;
     GSIS_DISPATCH_DIM(dim, (k_finish<Real, DIM><<<nbk, nt, 0, s>>>(n_cells, n_chunks, o_chunks, m, coef, partial,
                                                                     opartial, vol, fields_old, fields_new, eps_terms,
                                                                     err_flag, have_old, reduce, eps_part, ticket,
-                                                                    eps_sums)));
+                                                                    eps_sums, X)));
     return cudaGetLastError();
 }
 
@@ -1736,9 +1851,15 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, c
 
 template <typename Real>
 cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const Quad<Real> &vq,
-                                 const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux) {
+                                 const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux, double *raw) {
     if (g.n_bf == 0) return cudaSuccess;
-    GSIS_DISPATCH_DIM(g.dim, (k_kinetic_bflux<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, f, I, kin_bflux)));
+    GSIS_DISPATCH_DIM(g.dim, (k_kinetic_bflux<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, f, I, kin_bflux, raw)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kbflux_combine(cudaStream_t s, const MacroGeom &g, const double *raw, double *kin_bflux) {
+    if (g.n_bf == 0) return cudaSuccess;
+    GSIS_DISPATCH_DIM(g.dim, (k_kbflux_combine<DIM><<<(g.n_bf + 127) / 128, 128, 0, s>>>(g, raw, kin_bflux)));
     return cudaGetLastError();
 }
 
@@ -1780,7 +1901,11 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                                                    const double *, const double *, Real *);                        \
     template cudaError_t launch_wall_density<Real>(cudaStream_t, int, const Geom<Real> &, const Quad<Real> &,     \
                                                    const double *, const double *, const int *, const Real *,      \
-                                                   Real *);                                                        \
+                                                   const double *, Real *);                                        \
+    template cudaError_t launch_wall_outflux<Real>(cudaStream_t, int, const Geom<Real> &, const Quad<Real> &,     \
+                                                   const int *, const Real *, double *);                           \
+    template cudaError_t launch_cell_sums<Real>(cudaStream_t, int, int, int, int, const Real *, const Real *,      \
+                                                double *);                                                         \
     template cudaError_t launch_slopes<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,      \
                                              const Real *, Real *);                                                \
     template cudaError_t launch_sweep_gas<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,    \
@@ -1791,7 +1916,8 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                                                    Real *);                                                        \
     template cudaError_t launch_finish<Real>(cudaStream_t, int, int, int, int, const ModelDev &, const Real *,     \
                                              const Real *, const Real *, const double *, const double *, double *, \
-                                             double *, int *, int, double *, unsigned int *, double *);            \
+                                             double *, int *, int, double *, unsigned int *, double *,             \
+                                             const double *);                                                      \
     template cudaError_t launch_equilibrium<Real>(cudaStream_t, int, int, const Quad<Real> &, const Quad<Real> &,  \
                                                   const ModelDev &, const double *, Real *, Real *);               \
     template cudaError_t launch_moments_only<Real>(cudaStream_t, int, int, bool, const Quad<Real> &,               \
@@ -1800,7 +1926,7 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                                                    int *);                                                         \
     template cudaError_t launch_kinetic_bflux<Real>(cudaStream_t, const MacroGeom &, const ModelDev &,             \
                                                     const Quad<Real> &, const Quad<Real> &, const Real *,          \
-                                                    const Real *, double *);                                       \
+                                                    const Real *, double *, double *);                             \
     template cudaError_t launch_sync<Real>(cudaStream_t, int, int, bool, const Quad<Real> &, const Quad<Real> &,   \
                                            const ModelDev &, double, const double *, const double *, const Real *, \
                                            Real *, Real *, Real *, Real *, void *, int, int *);

@@ -104,6 +104,12 @@ def load():
         "gsis_import_state": (C.c_int, [vp, vp, C.c_int64]),
         "gsis_get_history": (C.c_int, [vp, C.POINTER(C.c_int64), _dp, C.c_int64, C.POINTER(C.c_int64)]),
         "gsis_set_wait_limit": (C.c_int, [vp, C.c_int32]),
+        "gsis_shard_setup": (C.c_int, [vp, C.c_int32, _dp, _dp, C.c_int32, _dp, _dp]),
+        "gsis_shard_buffer": (C.c_int, [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]),
+        "gsis_shard_refresh": (C.c_int, [vp, C.c_int32]),
+        "gsis_shard_begin": (C.c_int, [vp, C.c_int32]),
+        "gsis_shard_mid": (C.c_int, [vp]),
+        "gsis_shard_end": (C.c_int, [vp, _dp]),
         "gsis_mlp_init": (C.c_int, [vp, C.c_uint64]),
         "gsis_mlp_set_params": (C.c_int, [vp, _fp, C.c_int64]),
         "gsis_mlp_get_params": (C.c_int, [vp, _fp, C.c_int64]),
@@ -298,6 +304,37 @@ def gsis_get_history(ctx):
 
 def gsis_set_wait_limit(ctx, polls):
     _check(load().gsis_set_wait_limit(ctx, polls), ctx)
+
+
+def gsis_shard_setup(ctx, xi_all, w_all, omega_all, wo_all):
+    xi, w = _d(xi_all), _d(w_all)
+    om, wo = _d(omega_all), _d(wo_all)
+    _check(load().gsis_shard_setup(ctx, w.shape[0], _ptr(xi), _ptr(w), wo.shape[0], _ptr(om), _ptr(wo)), ctx)
+
+
+def gsis_shard_buffer(ctx):
+    """(device pointer, number of doubles) of the context's exchange buffer."""
+    p, n = C.c_void_p(0), C.c_int64(0)
+    _check(load().gsis_shard_buffer(ctx, C.byref(p), C.byref(n)), ctx)
+    return p.value, n.value
+
+
+def gsis_shard_refresh(ctx, pass_):
+    _check(load().gsis_shard_refresh(ctx, pass_), ctx)
+
+
+def gsis_shard_begin(ctx, mode):
+    _check(load().gsis_shard_begin(ctx, mode), ctx)
+
+
+def gsis_shard_mid(ctx):
+    _check(load().gsis_shard_mid(ctx), ctx)
+
+
+def gsis_shard_end(ctx):
+    eps = C.c_double(float("nan"))
+    _check(load().gsis_shard_end(ctx, C.byref(eps)), ctx)
+    return eps.value
 
 
 GSIS_MLP_NPARAM = 36804
