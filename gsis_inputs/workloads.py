@@ -26,6 +26,8 @@ class ModelParams:
     Kn_p: float = 1.0
     sigma_R: float = 0.01
     k_eff_density_scaled: bool = False
+    dv_temperature_dependent: bool = False   # d_v(T_v) = 2 x / (e^x - 1), x = Tv_ref / T_v (else d_v constant)
+    Tv_ref: float = 0.0                      # characteristic vibrational temperature (units of T_0)
     A: np.ndarray | None = None          # 3x3 relaxation-rate matrix, None = Mason-Monchick form
 
 

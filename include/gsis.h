@@ -96,7 +96,8 @@ typedef struct { int32_t n; const double *omega; const double *w; } gsis_photon_
 
 /* Model parameters of Section 2.1. */
 typedef struct {
-    double d_r, d_v;            /* rotational / vibrational degrees of freedom (d_v constant) */
+    double d_r, d_v;            /* rotational / vibrational degrees of freedom; d_v is used
+                                   when dv_temperature_dependent is 0                         */
     double Z_r, Z_v;            /* collision numbers                                          */
     double omega;               /* viscosity index: tau = sqrt(2/pi) T_t^(omega-1) Kn / rho   */
     double Sc;                  /* Schmidt number in the Mason-Monchick matrix A              */
@@ -105,6 +106,12 @@ typedef struct {
     int32_t k_eff_density_scaled; /* 0: k_eff = 1/Kn_p; 1: k_eff = rho/Kn_p                  */
     const double *A;            /* 3x3 row-major relaxation-rate matrix, or NULL for the
                                    Mason-Monchick form of Section 2.1                         */
+    double Tv_ref;              /* characteristic vibrational temperature (units of T_0)      */
+    int32_t dv_temperature_dependent; /* 1: d_v(T_v) = 2 x / (e^x - 1), x = Tv_ref / T_v
+                                   (Section 2.1): e_v = d_v(T_v) rho T_v / 2, T_tv and the
+                                   total T solved by Newton, A and the NSF conductivities at
+                                   the local d_v(T_v) (unless A is given), source Jacobian of
+                                   the synthetic equations re-derived; 0: d_v constant       */
 } gsis_model_params;
 
 #define GSIS_FP32 0             /* f and I stored and updated in FP32 */

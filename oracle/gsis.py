@@ -9,7 +9,7 @@ from . import model as mdl
 
 
 def total_temperature(F, model):
-    return mdl.mode_temperatures(F["T_t"], F["T_r"], F["T_v"], model.d_r, model.d_v)[2]
+    return mdl.mode_temperatures(F["T_t"], F["T_r"], F["T_v"], model)[2]
 
 
 def epsilon(F_new, F_old, vol, model, dim):

@@ -78,7 +78,7 @@ def moments(f, I, xi, w, omega, wo, dim, model):
     F["rho"], F["u"] = rho, u
     F["T_t"] = int_c2 / (3.0 * rho)
     F["T_r"] = 2.0 * (f1 @ w) / (model.d_r * rho)
-    F["T_v"] = 2.0 * (f2 @ w) / (model.d_v * rho)
+    F["T_v"] = mdl.vib_temperature((f2 @ w) / rho, model)     # int f2 = d_v(T_v) rho T_v / 2
     sig = np.zeros((n, 3, 3))
     for a in range(dim):
         for b in range(dim):
@@ -97,10 +97,6 @@ def moments(f, I, xi, w, omega, wo, dim, model):
     return F
 
 
-def select(F, idx):
-    return {k: v[idx] for k, v in F.items()}
-
-
 # --------------------------------------------------------------------------- distributions
 def unit_maxwellian(xi, u, T, dim):
     """(2 pi T)^(-dim/2) exp(-|xi - u|^2 / 2T) over the in-plane components (Eq.
@@ -117,20 +113,27 @@ def reference_planes(F, xi, dim, model):
     Returns [n, V, 4].  The q.c(...) Shakhov factors use the in-plane heat fluxes.
     """
     m = 3 - dim
-    d_r, d_v = model.d_r, model.d_v
-    A = mdl.relaxation_matrix(model)
-    Mix = mdl.aux_heat_flux_matrix(A, model.Z_r, model.Z_v)
-    qt, qr, qv = F["q_t"], F["q_r"], F["q_v"]
-    q0 = Mix[0, 0] * qt + Mix[0, 1] * qr + Mix[0, 2] * qv
-    q1 = Mix[1, 0] * qt + Mix[1, 1] * qr + Mix[1, 2] * qv
-    q2 = Mix[2, 0] * qt + Mix[2, 1] * qr + Mix[2, 2] * qv
+    d_r = model.d_r
     rho, T_t, T_r, T_v = F["rho"], F["T_t"], F["T_r"], F["T_v"]
-    T_tr, T_tv, _ = mdl.mode_temperatures(T_t, T_r, T_v, d_r, d_v)
+    # (q0, q1, q2) = Mix (q_t, q_r, q_v); with the temperature-dependent d_v, A and Mix are
+    # taken at each cell's d_v(T_v)
+    if getattr(model, "dv_temperature_dependent", False):
+        dvl = mdl.dv_local(T_v, model)
+        Mix = np.stack([mdl.aux_heat_flux_matrix(mdl.relaxation_matrix(model, dv), model.Z_r, model.Z_v)
+                        for dv in dvl])
+    else:
+        Mix = np.broadcast_to(mdl.aux_heat_flux_matrix(mdl.relaxation_matrix(model), model.Z_r, model.Z_v),
+                              (rho.shape[0], 3, 3))
+    qs = np.stack([F["q_t"], F["q_r"], F["q_v"]], 1)              # [n, mode, component]
+    q0, q1, q2 = (np.einsum("nj,nja->na", Mix[:, r], qs) for r in range(3))
+    qt, qr, qv = F["q_t"], F["q_r"], F["q_v"]
+    T_tr, T_tv, _ = mdl.mode_temperatures(T_t, T_r, T_v, model)
+    e_v, e_tv = mdl.vib_energy(T_v, model), mdl.vib_energy(T_tv, model)   # d_v(T) T / 2
     comps = (
         # weight, T_a, q in g0a, multiplier of g0a in g1a, in g2a, q in g1a, q in g2a
-        (1.0 - 1.0 / model.Z_r - 1.0 / model.Z_v, T_t, qt, 0.5 * d_r * T_r, 0.5 * d_v * T_v, qr, qv),
-        (1.0 / model.Z_r, T_tr, q0, 0.5 * d_r * T_tr, 0.5 * d_v * T_v, q1, q2),
-        (1.0 / model.Z_v, T_tv, q0, 0.5 * d_r * T_r, 0.5 * d_v * T_tv, q1, q2),
+        (1.0 - 1.0 / model.Z_r - 1.0 / model.Z_v, T_t, qt, 0.5 * d_r * T_r, e_v, qr, qv),
+        (1.0 / model.Z_r, T_tr, q0, 0.5 * d_r * T_tr, e_v, q1, q2),
+        (1.0 / model.Z_v, T_tv, q0, 0.5 * d_r * T_r, e_tv, q1, q2),
     )
     n, V = rho.shape[0], xi.shape[0]
     g = np.zeros((n, V, 4))
@@ -152,12 +155,12 @@ def reference_planes(F, xi, dim, model):
 
 def equilibrium_planes(F, xi, dim, model):
     """Multi-temperature local equilibrium: F0 = rho f_eq(T_t), H0 = m T_t F0,
-    f1 = (d_r/2) T_r F0, f2 = (d_v/2) T_v F0 (the moments of Eq. getmoment)."""
+    f1 = (d_r/2) T_r F0, f2 = (d_v(T_v)/2) T_v F0 (the moments of Eq. getmoment)."""
     m = 3 - dim
     feq, _, _ = unit_maxwellian(xi, F["u"], F["T_t"], dim)
     F0 = F["rho"][:, None] * feq
     return np.stack([F0, m * F["T_t"][:, None] * F0, 0.5 * model.d_r * F["T_r"][:, None] * F0,
-                     0.5 * model.d_v * F["T_v"][:, None] * F0], axis=-1)
+                     mdl.vib_energy(F["T_v"], model)[:, None] * F0], axis=-1)
 
 
 def photon_equilibrium(T, n_omega, sigma_R):
@@ -269,7 +272,7 @@ def incoming_gas(patch, rho_w, xi, dim, model):
         rho, T, Tr, Tv = patch.rho, patch.T_t, patch.T_r, patch.T_v
     Fw, _, _ = unit_maxwellian(xi, np.asarray(patch.u, np.float64)[None], np.array([T]), dim)
     F0 = rho * Fw[0]
-    return np.stack([F0, m * T * F0, 0.5 * model.d_r * Tr * F0, 0.5 * model.d_v * Tv * F0], axis=-1)
+    return np.stack([F0, m * T * F0, 0.5 * model.d_r * Tr * F0, float(mdl.vib_energy(Tv, model)) * F0], axis=-1)
 
 
 def incoming_photon(patch, model, n_omega):

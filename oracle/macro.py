@@ -61,7 +61,7 @@ def nvar(dim):
 def conservative(F, dim, model):
     rho, u = F["rho"], F["u"][:, :dim]
     e_r = 0.5 * model.d_r * rho * F["T_r"]
-    e_v = 0.5 * model.d_v * rho * F["T_v"]
+    e_v = rho * mdl.vib_energy(F["T_v"], model)
     e_R = 4.0 * model.sigma_R * F["T_R"] ** 4
     e = 1.5 * rho * F["T_t"] + 0.5 * rho * np.sum(u * u, axis=1) + e_r + e_v + e_R
     return np.column_stack([rho, rho[:, None] * u, e, e_r, e_v, e_R])
@@ -73,7 +73,7 @@ def primitive(W, dim, model):
     u = W[:, 1:1 + dim] / rho[:, None]
     e, e_r, e_v, e_R = W[:, 1 + dim], W[:, 2 + dim], W[:, 3 + dim], W[:, 4 + dim]
     T_t = (e - e_R - e_r - e_v - 0.5 * rho * np.sum(u * u, axis=1)) / (1.5 * rho)
-    return rho, u, T_t, 2.0 * e_r / (model.d_r * rho), 2.0 * e_v / (model.d_v * rho), e_R
+    return rho, u, T_t, 2.0 * e_r / (model.d_r * rho), mdl.vib_temperature(e_v / rho, model), e_R
 
 
 def fields_from_W(W, dim, model, template=None):
@@ -166,7 +166,7 @@ def convective_flux(prim, n, dim, model):
     un = np.sum(u * n, axis=1)
     p = rho * T_t
     e_r = 0.5 * model.d_r * rho * T_r
-    e_v = 0.5 * model.d_v * rho * T_v
+    e_v = rho * mdl.vib_energy(T_v, model)
     e_gas = 1.5 * rho * T_t + 0.5 * rho * np.sum(u * u, axis=1) + e_r + e_v
     F = np.zeros((rho.shape[0], nvar(dim)))
     F[:, 0] = rho * un
@@ -180,7 +180,7 @@ def convective_flux(prim, n, dim, model):
 def prim_to_W(prim, dim, model):
     rho, u, T_t, T_r, T_v, e_R = prim
     e_r = 0.5 * model.d_r * rho * T_r
-    e_v = 0.5 * model.d_v * rho * T_v
+    e_v = rho * mdl.vib_energy(T_v, model)
     e = 1.5 * rho * T_t + 0.5 * rho * np.sum(u * u, axis=1) + e_r + e_v + e_R
     return np.column_stack([rho, rho[:, None] * u, e, e_r, e_v, e_R])
 
@@ -206,6 +206,17 @@ def viscosity(T_t, model):
     return np.sqrt(2.0 / np.pi) * model.Kn * T_t ** model.omega
 
 
+def conductivity_base(T_v, model):
+    """A^-1 diag(5, d_r, d_v) of Eq. (NSF_thermal_conductivities) per state [n, 3, 3]: the
+    constant matrix, or with A and d_v taken at d_v(T_v) for the temperature-dependent d_v."""
+    T_v = np.atleast_1d(np.asarray(T_v, np.float64))
+    if not getattr(model, "dv_temperature_dependent", False):
+        base = np.linalg.inv(mdl.relaxation_matrix(model)) @ np.diag([5.0, model.d_r, model.d_v])
+        return np.broadcast_to(base, (T_v.shape[0], 3, 3))
+    return np.stack([np.linalg.inv(mdl.relaxation_matrix(model, dv)) @ np.diag([5.0, model.d_r, dv])
+                     for dv in mdl.dv_local(T_v, model)])
+
+
 def nsf_face(faces, prim_face, grads, dim, model):
     """NSF stress (in-plane, [nf, dim, dim]) and heat fluxes (q_t, q_r, q_v, q_R [nf, dim])
     from face states and face gradients of (u, T_t, T_r, T_v, e_R): Eqs. (NSF_constitutive),
@@ -216,8 +227,7 @@ def nsf_face(faces, prim_face, grads, dim, model):
     S = np.transpose(gu, (0, 2, 1)) + gu                        # du_a/dx_b + du_b/dx_a
     div = np.einsum("fdd->f", gu)
     sig = -mu[:, None, None] * (S - (2.0 / 3.0) * div[:, None, None] * np.eye(dim)[None])
-    A = mdl.relaxation_matrix(model)
-    kap = 0.5 * mu[:, None, None] * (np.linalg.inv(A) @ np.diag([5.0, model.d_r, model.d_v]))[None]
+    kap = 0.5 * mu[:, None, None] * conductivity_base(prim_face[4], model)
     gT = np.stack([grads["T_t"], grads["T_r"], grads["T_v"]], axis=1)     # [nf, 3, dim]
     q = -np.einsum("fij,fjd->fid", kap, gT)
     keff = mdl.absorption(rho, model)
@@ -290,8 +300,6 @@ def macro_boundary_flux(faces, prim, wl):
     rho, u, T_t, T_r, T_v, e_R = (x[c] for x in prim)
     xf = geo.mesh.face_centroid[geo.mesh.face_nbr < 0, :dim]
     dn = np.abs(np.sum(n * (xf - geo.xc[c]), axis=1))
-    A = mdl.relaxation_matrix(model)
-    base = np.linalg.inv(A) @ np.diag([5.0, model.d_r, model.d_v])
     for b in range(nb):
         patch = geo.mesh.patches[faces.bf_patch[b]]
         uw = np.asarray(patch.u, float)[:dim]
@@ -305,7 +313,7 @@ def macro_boundary_flux(faces, prim, wl):
         mu = viscosity(0.5 * (T_t[b] + patch.T_t), model)
         du = uw - u[b]
         sn = -mu / dn[b] * (du + (np.dot(n[b], du) / 3.0) * n[b])
-        kap = 0.5 * mu * base
+        kap = 0.5 * mu * conductivity_base(0.5 * (T_v[b] + patch.T_v), model)[0]
         q = -(kap @ (np.array([patch.T_t, patch.T_r, patch.T_v]) - np.array([T_t[b], T_r[b], T_v[b]]))) / dn[b]
         keff = mdl.absorption(rho[b:b + 1], model)[0]
         qR = -(far[5][0] - e_R[b]) / (3.0 * keff * dn[b])
@@ -351,28 +359,16 @@ def wall_equilibrium_flux(faces, state, wl, b):
 def source(prim, dim, model):
     """Q of Section 5: relaxation of e_r, e_v and the gas-photon exchange."""
     rho, u, T_t, T_r, T_v, e_R = prim
-    T_tr, T_tv, _ = mdl.mode_temperatures(T_t, T_r, T_v, model.d_r, model.d_v)
+    T_tr, T_tv, _ = mdl.mode_temperatures(T_t, T_r, T_v, model)
     tau = mdl.relaxation_time(rho, T_t, model.Kn, model.omega)
     k = mdl.absorption(rho, model)
     e_vR = 4.0 * model.sigma_R * T_v ** 4
     Q = np.zeros((rho.shape[0], nvar(dim)))
     Q[:, 2 + dim] = 0.5 * model.d_r * rho * (T_tr - T_r) / (model.Z_r * tau)
-    Q[:, 3 + dim] = 0.5 * model.d_v * rho * (T_tv - T_v) / (model.Z_v * tau) - k * (e_vR - e_R)
+    Q[:, 3 + dim] = rho * (mdl.vib_energy(T_tv, model) - mdl.vib_energy(T_v, model)) / (model.Z_v * tau) \
+        - k * (e_vR - e_R)                                      # (e_tv - e_v) / (Z_v tau) - k (e_vR - e_R)
     Q[:, 4 + dim] = k * (e_vR - e_R)
     return Q
-
-
-def source_jacobian_diag(prim, dim, model):
-    """diag(dQ/dW) of Appendix A (zero for rho, rho u, e)."""
-    rho, u, T_t, T_r, T_v, e_R = prim
-    T_tr, T_tv, _ = mdl.mode_temperatures(T_t, T_r, T_v, model.d_r, model.d_v)
-    tau = mdl.relaxation_time(rho, T_t, model.Kn, model.omega)
-    om, dr, dv, Zr, Zv = model.omega, model.d_r, model.d_v, model.Z_r, model.Z_v
-    J = np.zeros((rho.shape[0], nvar(dim)))
-    J[:, 2 + dim] = -3.0 / ((3.0 + dr) * Zr * tau) + 2.0 * (om - 1.0) * (T_tr - T_r) / (3.0 * Zr * tau * T_t)
-    J[:, 3 + dim] = -3.0 / ((3.0 + dv) * Zv * tau) + 2.0 * (om - 1.0) * (T_tv - T_v) / (3.0 * Zv * tau * T_t)
-    J[:, 4 + dim] = -mdl.absorption(rho, model)
-    return J
 
 
 # ----------------------------------------------------------------- kinetic boundary fluxes
@@ -463,20 +459,32 @@ def boundary_gamma(faces, prim, wl):
 
 def source_jacobian_block(prim, dim, model):
     """Exact d(Q_egas, Q_r, Q_v, Q_R)/d(e_gas, e_r, e_v, e_R) per cell [n, 4, 4] with rho, rho u,
-    tau and k_eff held fixed; e_gas = e - e_R, T_t = (e_gas - e_r - e_v - rho u^2/2)/(1.5 rho)."""
+    tau and k_eff held fixed; e_gas = e - e_R, T_t = (e_gas - e_r - e_v - rho u^2/2)/(1.5 rho).
+
+    Q_v = rho (eps(T_tv) - eps_v) / (Z_v tau) - k (e_vR - e_R) with eps(T) = d_v(T) T / 2,
+    eps_v = e_v / rho and T_tv defined by 3 T_tv + 2 eps(T_tv) = 3 T_t + 2 eps_v, so
+    dT_tv = (3 dT_t + 2 d eps_v) / (3 + 2 eps'(T_tv)) and, with dT_t = a (de_gas - de_r - de_v),
+    a = 2 / (3 rho):
+        d(rho eps(T_tv)) = b (3a de_gas - 3a de_r + (2/rho - 3a) de_v),  b = rho eps'(T_tv) / (3 + 2 eps'(T_tv)),
+    where 2/rho - 3a = 0; e_vR = 4 sigma_R T_v^4 gives d e_vR / d e_v = 16 sigma_R T_v^3 / (rho eps'(T_v)).
+    For constant d_v, eps' = d_v / 2 and these reduce to the constant-coefficient forms
+    (Appendix A's diagonal entries are the e_r, e_v and e_R diagonal of this block)."""
     rho, u, T_t, T_r, T_v, e_R = prim
     tau = mdl.relaxation_time(rho, T_t, model.Kn, model.omega)
     k = mdl.absorption(rho, model)
-    dr, dv = model.d_r, model.d_v
+    dr = model.d_r
+    T_tv = mdl.mode_temperatures(T_t, T_r, T_v, model)[1]
     cr = rho * 1.5 * dr / (3.0 + dr) / (model.Z_r * tau)          # Q_r = cr (T_t - T_r)
-    cv = rho * 1.5 * dv / (3.0 + dv) / (model.Z_v * tau)          # Q_v = cv (T_t - T_v) - k (e_vR - e_R)
-    beta = 16.0 * model.sigma_R * T_v ** 3 * 2.0 / (dv * rho)     # d e_vR / d e_v
+    ctv = mdl.vib_heat_capacity(T_tv, model)
+    b = rho * ctv / (3.0 + 2.0 * ctv)
+    beta = 16.0 * model.sigma_R * T_v ** 3 / (rho * mdl.vib_heat_capacity(T_v, model))   # d e_vR / d e_v
     a = 1.0 / (1.5 * rho)                                         # d T_t / d e_gas
+    zv = 1.0 / (model.Z_v * tau)
     J = np.zeros((rho.shape[0], 4, 4))
     J[:, 0, 2], J[:, 0, 3] = -k * beta, k
     J[:, 1, 0], J[:, 1, 1], J[:, 1, 2] = cr * a, -cr * (a + 2.0 / (dr * rho)), -cr * a
-    J[:, 2, 0], J[:, 2, 1] = cv * a, -cv * a
-    J[:, 2, 2], J[:, 2, 3] = -cv * (a + 2.0 / (dv * rho)) - k * beta, k
+    J[:, 2, 0], J[:, 2, 1] = 3.0 * a * b * zv, -3.0 * a * b * zv
+    J[:, 2, 2], J[:, 2, 3] = -zv - k * beta, k
     J[:, 3, 2], J[:, 3, 3] = k * beta, -k
     return J
 

@@ -21,11 +21,12 @@ def mason_monchick_A(d_r, d_v, Z_r, Z_v, Sc):
     return A
 
 
-def relaxation_matrix(model):
-    """A of the model: the user-given 3x3 matrix, else the Mason-Monchick form."""
+def relaxation_matrix(model, d_v=None):
+    """A of the model: the user-given 3x3 matrix, else the Mason-Monchick form at d_v
+    (default: the model's constant d_v; per cell, d_v(T_v) when it depends on T_v)."""
     if model.A is not None:
         return np.asarray(model.A, np.float64).reshape(3, 3)
-    return mason_monchick_A(model.d_r, model.d_v, model.Z_r, model.Z_v, model.Sc)
+    return mason_monchick_A(model.d_r, model.d_v if d_v is None else d_v, model.Z_r, model.Z_v, model.Sc)
 
 
 def aux_heat_flux_matrix(A, Z_r, Z_v):
@@ -38,18 +39,74 @@ def aux_heat_flux_matrix(A, Z_r, Z_v):
     ])
 
 
-def mode_temperatures(T_t, T_r, T_v, d_r, d_v):
-    """T_tr, T_tv and total T for constant d_v (Section 2.1)."""
-    T_tr = (3.0 * T_t + d_r * T_r) / (3.0 + d_r)
-    T_tv = (3.0 * T_t + d_v * T_v) / (3.0 + d_v)
-    T = (3.0 * T_t + d_r * T_r + d_v * T_v) / (3.0 + d_r + d_v)
-    return T_tr, T_tv, T
-
-
 def d_v_of_T(T_v, T_v_ref):
-    """Vibrational degrees of freedom d_v(T_v) (Section 2.1)."""
+    """Vibrational degrees of freedom d_v(T_v) = 2 x / (e^x - 1), x = T_v_ref / T_v (Section 2.1)."""
     x = T_v_ref / T_v
     return 2.0 * x / np.expm1(x)
+
+
+def vib_energy(T, model):
+    """Vibrational energy per unit density, d_v(T) T / 2 (Section 2.1: e_v = d_v(T_v) rho T_v / 2).
+    With the temperature-dependent d_v this is T_v_ref / (e^(T_v_ref / T) - 1)."""
+    T = np.asarray(T, np.float64)
+    if getattr(model, "dv_temperature_dependent", False):
+        return model.Tv_ref / np.expm1(model.Tv_ref / T)
+    return 0.5 * model.d_v * T
+
+
+def vib_temperature(eps, model):
+    """Inverse of vib_energy: the T with d_v(T) T / 2 = eps; in closed form
+    T_v_ref / ln(1 + T_v_ref / eps) for the temperature-dependent d_v."""
+    eps = np.asarray(eps, np.float64)
+    if getattr(model, "dv_temperature_dependent", False):
+        return model.Tv_ref / np.log1p(model.Tv_ref / eps)
+    return 2.0 * eps / model.d_v
+
+
+def vib_heat_capacity(T, model):
+    """d(vib_energy)/dT: x^2 e^x / (e^x - 1)^2 with x = T_v_ref / T, or d_v / 2."""
+    T = np.asarray(T, np.float64)
+    if getattr(model, "dv_temperature_dependent", False):
+        x = model.Tv_ref / T
+        return x * x * np.exp(x) / np.expm1(x) ** 2
+    return 0.5 * model.d_v * np.ones_like(T)
+
+
+def dv_local(T_v, model):
+    """d_v at the vibrational temperature: the constant, or d_v(T_v)."""
+    if getattr(model, "dv_temperature_dependent", False):
+        return d_v_of_T(np.asarray(T_v, np.float64), model.Tv_ref)
+    return model.d_v * np.ones_like(np.asarray(T_v, np.float64))
+
+
+def _solve_equal_temperature(base, rhs, model):
+    """The T with base T + 2 vib_energy(T) = rhs, by Newton from rhs / (base + d_v):
+    the left side increases with T, so the root is unique; iterate to |dT| <= 1e-15 T."""
+    T = rhs / (base + 2.0 * vib_heat_capacity(np.maximum(rhs / (base + 1.0), 1e-3), model))
+    for _ in range(60):
+        g = base * T + 2.0 * vib_energy(T, model) - rhs
+        dT = g / (base + 2.0 * vib_heat_capacity(T, model))
+        T = T - dT
+        if np.all(np.abs(dT) <= 1e-15 * np.abs(T)):
+            break
+    return T
+
+
+def mode_temperatures(T_t, T_r, T_v, model):
+    """T_tr, T_tv and total T (Section 2.1):
+        T_tr = (3 T_t + d_r T_r) / (3 + d_r),
+        (3 + d_v(T_tv)) T_tv = 3 T_t + d_v(T_v) T_v,
+        (3 + d_r + d_v(T)) T = 3 T_t + d_r T_r + d_v(T_v) T_v,
+    explicit for constant d_v and solved by Newton for the temperature-dependent one."""
+    d_r = model.d_r
+    T_tr = (3.0 * T_t + d_r * T_r) / (3.0 + d_r)
+    ev = 2.0 * vib_energy(T_v, model)
+    if not getattr(model, "dv_temperature_dependent", False):
+        d_v = model.d_v
+        return T_tr, (3.0 * T_t + d_v * T_v) / (3.0 + d_v), (3.0 * T_t + d_r * T_r + d_v * T_v) / (3.0 + d_r + d_v)
+    T_tv = _solve_equal_temperature(3.0, 3.0 * T_t + ev, model)
+    T = _solve_equal_temperature(3.0 + d_r, 3.0 * T_t + d_r * T_r + ev, model)
+    return T_tr, T_tv, T
 
 
 def relaxation_time(rho, T_t, Kn, omega):
@@ -61,15 +118,6 @@ def absorption(rho, model):
     """k_eff = 1/Kn_photon (Section 2.1); optionally scaled by the local density."""
     k = 1.0 / model.Kn_p
     return k * rho if model.k_eff_density_scaled else k * np.ones_like(rho)
-
-
-def kappa_gas(p_t, tau, A, d_r, d_v):
-    """kappa_gas = (p_t tau / 2) A^-1 diag(5, d_r, d_v) (Eq. NSF_thermal_conductivities).
-
-    Returns an array [..., 3, 3] for array-valued p_t*tau.
-    """
-    base = np.linalg.inv(A) @ np.diag([5.0, d_r, d_v])
-    return 0.5 * np.asarray(p_t * tau)[..., None, None] * base
 
 
 def sound_speed(T_t):

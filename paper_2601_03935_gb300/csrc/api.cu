@@ -614,6 +614,8 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
         !(mp->d_r >= 0) || !(mp->d_v > 0) || !(mp->d_r > 0))
         return why = "bad model parameters", GSIS_ERR_INVALID_ARG;
     if (!(mp->sigma_R > 0)) return why = "sigma_R must be positive (photons always on)", GSIS_ERR_INVALID_ARG;
+    if (mp->dv_temperature_dependent && !(mp->Tv_ref > 0))
+        return why = "a temperature-dependent d_v needs Tv_ref > 0", GSIS_ERR_INVALID_ARG;
     for (int p = 0; p < m->n_patches; ++p) {
         const gsis_patch &P = m->patches[p];
         if (P.kind != GSIS_PATCH_WALL && P.kind != GSIS_PATCH_FARFIELD) return why = "bad patch kind", GSIS_ERR_INVALID_ARG;
@@ -742,6 +744,9 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     md.sigma_R = mp->sigma_R;
     md.k_eff_density_scaled = mp->k_eff_density_scaled;
     md.cfl_meso = sp->cfl_meso;
+    md.dv_T = mp->dv_temperature_dependent ? 1 : 0;
+    md.Tv_ref = mp->Tv_ref;
+    md.userA = mp->A ? 1 : 0;
     if (mp->A) std::memcpy(md.A, mp->A, 9 * sizeof(double));
     else mason_monchick(mp, md.A);
     {   // auxiliary heat-flux matrix of Section 2.1
@@ -902,7 +907,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         B[bc::M0] = 1.0;
         B[bc::MH] = MH * T;
         B[bc::M1] = 0.5 * mp->d_r * Tr;
-        B[bc::M2] = 0.5 * mp->d_v * Tv;
+        B[bc::M2] = vib_energy<double>(c->model, Tv);       // d_v(T) T / 2 of the entering gas
         B[bc::IIN] = mp->sigma_R * TR * TR * TR * TR / M_PI;
     }
 

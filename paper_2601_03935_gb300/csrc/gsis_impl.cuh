@@ -92,7 +92,84 @@ struct ModelDev {
     double A[9];
     double Mix[9];             // (q0, q1, q2) = Mix (q_t, q_r, q_v)
     double cfl_meso;
+    int dv_T;                  // d_v(T_v) = 2 x / (e^x - 1), x = Tv_ref / T_v; else d_v constant
+    int userA;                 // A given by the caller (kept constant); else Mason-Monchick at d_v
+    double Tv_ref;
 };
+
+// ---- vibrational energy per unit density, eps(T) = d_v(T) T / 2 (Section 2.1), its
+// inverse and its derivative; with the temperature-dependent d_v, eps(T) =
+// Tv_ref / (e^(Tv_ref / T) - 1) and the inverse is closed-form.
+template <typename R>
+__host__ __device__ inline R vib_energy(const ModelDev &m, R T) {
+    if (m.dv_T) return R(m.Tv_ref) / expm1(R(m.Tv_ref) / T);
+    return R(0.5) * R(m.d_v) * T;
+}
+template <typename R>
+__host__ __device__ inline R vib_temperature(const ModelDev &m, R eps) {
+    if (m.dv_T) return R(m.Tv_ref) / log1p(R(m.Tv_ref) / eps);
+    return R(2) * eps / R(m.d_v);
+}
+template <typename R>
+__host__ __device__ inline R vib_cv(const ModelDev &m, R T) {
+    if (m.dv_T) {
+        const R x = R(m.Tv_ref) / T, em = expm1(x);
+        return x * x * (em + R(1)) / (em * em);
+    }
+    return R(0.5) * R(m.d_v);
+}
+__host__ __device__ inline double dv_at(const ModelDev &m, double T) {
+    if (m.dv_T) {
+        const double x = m.Tv_ref / T;
+        return 2.0 * x / expm1(x);
+    }
+    return m.d_v;
+}
+// The T with base T + 2 eps(T) = rhs: T_tv (base 3, rhs 3 T_t + 2 eps(T_v)) and the total T
+// (base 3 + d_r, rhs 3 T_t + d_r T_r + 2 eps(T_v)) of Section 2.1.  Explicit for constant
+// d_v; otherwise Newton (the left side increases with T) from rhs / (base + 2 eps'(T0)).
+template <typename R>
+__host__ __device__ inline R equal_temperature(const ModelDev &m, R base, R rhs) {
+    if (!m.dv_T) return rhs / (base + R(m.d_v));
+    const R tol = sizeof(R) == 4 ? R(1e-7) : R(1e-15);
+    const R T0 = rhs / (base + R(1));
+    R T = rhs / (base + R(2) * vib_cv(m, T0 > R(1e-3) ? T0 : R(1e-3)));
+    for (int it = 0; it < 60; ++it) {
+        const R dT = (base * T + R(2) * vib_energy(m, T) - rhs) / (base + R(2) * vib_cv(m, T));
+        T -= dT;
+        if (fabs(dT) <= tol * fabs(T)) break;
+    }
+    return T;
+}
+// Relaxation-rate matrix A at d_v (Mason-Monchick form of Section 2.1, or the caller's
+// constant A) and the auxiliary heat-flux matrix Mix built from it.
+__host__ __device__ inline void relaxation_matrix_at(const ModelDev &m, double dv, double *A) {
+    if (m.userA || !m.dv_T) {
+        for (int k = 0; k < 9; ++k) A[k] = m.A[k];
+        return;
+    }
+    const double dr = m.d_r, Zr = m.Z_r, Zv = m.Z_v;
+    for (int k = 0; k < 9; ++k) A[k] = 0.0;
+    A[0] = 2.0 / 3.0 + 5.0 / 6.0 * (dr / ((3 + dr) * Zr) + dv / ((3 + dv) * Zv));
+    A[1] = -5.0 / (2.0 * (3 + dr) * Zr);
+    A[2] = -5.0 / (2.0 * (3 + dv) * Zv);
+    A[3] = -dr / ((3 + dr) * Zr);
+    A[4] = m.Sc + 3.0 / (2.0 * (3 + dr) * Zr);
+    A[6] = -dv / ((3 + dv) * Zv);
+    A[8] = m.Sc + 3.0 / (2.0 * (3 + dv) * Zv);
+}
+__host__ __device__ inline void mix_from_A(const ModelDev &m, const double *A, double *Mx) {
+    const double Zi = 1.0 / (1.0 / m.Z_r + 1.0 / m.Z_v);
+    Mx[0] = (2.0 - 3.0 * A[0]) * Zi + 1.0;
+    Mx[1] = -3.0 * A[1] * Zi;
+    Mx[2] = -3.0 * A[2] * Zi;
+    Mx[3] = -A[3] * Zi;
+    Mx[4] = 1.0 - A[4] * Zi;
+    Mx[5] = -A[5] * Zi;
+    Mx[6] = -A[6] * Zi;
+    Mx[7] = -A[7] * Zi;
+    Mx[8] = 1.0 - A[8] * Zi;
+}
 
 // ---- synthetic (macroscopic) equations, FP64 throughout (macro.cu)
 // Conservative variables W = [rho, rho u (dim), e, e_r, e_v, e_R] (nv = dim + 5) and

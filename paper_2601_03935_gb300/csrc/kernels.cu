@@ -74,7 +74,9 @@ __global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restric
     const CT rho = (CT)M[0], Tt = (CT)M[4], Tr = (CT)M[5], Tv = (CT)M[6];
     const CT dr = (CT)m.d_r, dv = (CT)m.d_v;
     const CT Ttr = (CT(3) * Tt + dr * Tr) / (CT(3) + dr);
-    const CT Ttv = (CT(3) * Tt + dv * Tv) / (CT(3) + dv);
+    // T_tv of Section 2.1; with the temperature-dependent d_v solved in FP64
+    const double Ttv8 = m.dv_T ? equal_temperature<double>(m, 3.0, 3.0 * M[4] + 2.0 * vib_energy<double>(m, M[6])) : 0.0;
+    const CT Ttv = m.dv_T ? (CT)Ttv8 : (CT(3) * Tt + dv * Tv) / (CT(3) + dv);
     const int MH = 3 - DIM;
     // the mixed heat fluxes and the radiative sink are differences of nearly equal terms
     // near equilibrium: they stay FP64
@@ -84,13 +86,24 @@ __global__ void k_coefficients(Geom<Real> g, ModelDev m, const double *__restric
         q[1][a] = M[11 + a];
         q[2][a] = M[14 + a];
     }
+    double Mc[9];     // Mix, per cell at d_v(T_v) when d_v depends on T_v
+    if (m.dv_T) {
+        double Ac[9];
+        relaxation_matrix_at(m, dv_at(m, M[6]), Ac);
+        mix_from_A(m, Ac, Mc);
+    } else {
+        for (int k = 0; k < 9; ++k) Mc[k] = m.Mix[k];
+    }
     double qa[3][3];  // q0, q1, q2
     for (int r = 0; r < 3; ++r)
-        for (int a = 0; a < 3; ++a) qa[r][a] = m.Mix[r * 3 + 0] * q[0][a] + m.Mix[r * 3 + 1] * q[1][a] + m.Mix[r * 3 + 2] * q[2][a];
+        for (int a = 0; a < 3; ++a) qa[r][a] = Mc[r * 3 + 0] * q[0][a] + Mc[r * 3 + 1] * q[1][a] + Mc[r * 3 + 2] * q[2][a];
     const CT alpha[3] = {(CT)(1.0 - 1.0 / m.Z_r - 1.0 / m.Z_v), (CT)(1.0 / m.Z_r), (CT)(1.0 / m.Z_v)};
     const CT Ta[3] = {Tt, Ttr, Ttv};
     const CT k1[3] = {CT(0.5) * dr * Tr, CT(0.5) * dr * Ttr, CT(0.5) * dr * Tr};
-    const CT k2[3] = {CT(0.5) * dv * Tv, CT(0.5) * dv * Tv, CT(0.5) * dv * Ttv};
+    // d_v(T) T / 2 at T_v (translational and rotational parts) and at T_tv (vibrational part)
+    const CT ev = m.dv_T ? (CT)vib_energy<double>(m, M[6]) : CT(0.5) * dv * Tv;
+    const CT etv = m.dv_T ? (CT)vib_energy<double>(m, Ttv8) : CT(0.5) * dv * Ttv;
+    const CT k2[3] = {ev, ev, etv};
     const double *qg0[3] = {q[0], qa[0], qa[0]};
     const double *qg1[3] = {q[1], qa[1], qa[1]};
     const double *qg2[3] = {q[2], qa[2], qa[2]};
@@ -1037,8 +1050,8 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
     const double An = rn[0] * pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * rn[4]);
     const double Ah = rh[0] * pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * rh[4]);
     const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
-    const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
-    const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
+    const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], vib_energy<double>(m, rn[6])};
+    const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], vib_energy<double>(m, rh[6])};
     const Real An_r = (Real)An, dA = (Real)(An - Ah), Ah_r = (Real)Ah, Bn_r = (Real)Bn, Bh_r = (Real)Bh,
                dB = (Real)(Bn - Bh);
     Real uh[DIM], du[DIM], su[DIM], mul_n[4], dmul[4];
@@ -1119,8 +1132,8 @@ __global__ void k_sync_coef(int n_cells, ModelDev m, const double *__restrict__ 
     const double An = rn[0] * pow_neg_half_dim<DIM>(two_pi * rn[4]);
     const double Ah = rh[0] * pow_neg_half_dim<DIM>(two_pi * rh[4]);
     const double Bn = 0.5 / rn[4], Bh = 0.5 / rh[4];
-    const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], 0.5 * m.d_v * rn[6]};
-    const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], 0.5 * m.d_v * rh[6]};
+    const double mn[4] = {1.0, MH * rn[4], 0.5 * m.d_r * rn[5], vib_energy<double>(m, rn[6])};
+    const double mh[4] = {1.0, MH * rh[4], 0.5 * m.d_r * rh[5], vib_energy<double>(m, rh[6])};
     float K[SKC];
     for (int q = 0; q < SKC; ++q) K[q] = 0.f;
     K[0] = (float)An;
@@ -1379,7 +1392,7 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
             f0 = Aw * exp(-Bw * c2);
             fh = MH * T * f0;
             f1 = 0.5 * m.d_r * Tr * f0;
-            f2 = 0.5 * m.d_v * Tv * f0;
+            f2 = vib_energy<double>(m, Tv) * f0;
             s = acc + NS;
         }
         s[0] += wf * f0;
@@ -1537,7 +1550,7 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
     const double Tt = int_c2 / (3.0 * rho);
     Fn[4] = Tt;
     Fn[5] = 2.0 * G1 / (m.d_r * rho);
-    Fn[6] = 2.0 * G2 / (m.d_v * rho);
+    Fn[6] = vib_temperature<double>(m, G2 / rho);      // int f2 = d_v(T_v) rho T_v / 2
     const double eR = Ph[0];
     Fn[7] = m.sigma_R > 0.0 ? sqrt(sqrt(fmax(eR, 0.0) / (4.0 * m.sigma_R))) : 0.0;
     // heat fluxes: q_t,a = 1/2 int (c-d)_a ((c-d)^2 F0 + H0)
@@ -1576,10 +1589,15 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
     if (bad) atomicOr(err, 1);
     // convergence terms: (drho^2, rho^2, |du|^2, |u|^2, dT^2, T^2, T) * V
     const double V = vol[i];
-    const double Ttot = (3.0 * Tt + m.d_r * Fn[5] + m.d_v * Fn[6]) / (3.0 + m.d_r + m.d_v);
+    // total temperature of Section 2.1: (3 + d_r + d_v(T)) T = 3 T_t + d_r T_r + d_v(T_v) T_v
+    const double Ttot = m.dv_T ? equal_temperature<double>(m, 3.0 + m.d_r, 3.0 * Tt + m.d_r * Fn[5] +
+                                                                               2.0 * vib_energy<double>(m, Fn[6]))
+                               : (3.0 * Tt + m.d_r * Fn[5] + m.d_v * Fn[6]) / (3.0 + m.d_r + m.d_v);
     if (have_old) {
         const double *Fo = F_old + (size_t)i * NF;
-        const double To = (3.0 * Fo[4] + m.d_r * Fo[5] + m.d_v * Fo[6]) / (3.0 + m.d_r + m.d_v);
+        const double To = m.dv_T ? equal_temperature<double>(m, 3.0 + m.d_r, 3.0 * Fo[4] + m.d_r * Fo[5] +
+                                                                                 2.0 * vib_energy<double>(m, Fo[6]))
+                                 : (3.0 * Fo[4] + m.d_r * Fo[5] + m.d_v * Fo[6]) / (3.0 + m.d_r + m.d_v);
         double du2 = 0.0, uo2 = 0.0;
         for (int a = 0; a < DIM; ++a) {
             du2 += (Fn[1 + a] - Fo[1 + a]) * (Fn[1 + a] - Fo[1 + a]);
@@ -1665,7 +1683,7 @@ __global__ void k_equilibrium(int n_cells, Quad<Real> vq, Quad<Real> oq, ModelDe
         t.v[0] = (Real)F0;
         t.v[1] = (Real)((3 - DIM) * Tt * F0);
         t.v[2] = (Real)(0.5 * m.d_r * M[5] * F0);
-        t.v[3] = (Real)(0.5 * m.d_v * M[6] * F0);
+        t.v[3] = (Real)(vib_energy<double>(m, M[6]) * F0);
         vstore<Real, 4>(f + ((size_t)i * vq.n_pad + v) * 4, t);
     }
     const double B = m.sigma_R * M[7] * M[7] * M[7] * M[7] / 3.141592653589793;

@@ -48,10 +48,13 @@ __device__ __forceinline__ R absorption(R rho, const ModelDev &m) {
     return m.k_eff_density_scaled ? k * rho : k;
 }
 
-// base = A^-1 diag(5, d_r, d_v); kappa_gas = mu/2 base (Eq. NSF_thermal_conductivities)
+// base = A^-1 diag(5, d_r, d_v); kappa_gas = mu/2 base (Eq. NSF_thermal_conductivities).
+// dv < 0: the model's constant d_v and A; else A and the last diagonal entry at this d_v.
 template <typename R>
-__device__ void kappa_base(const ModelDev &m, R (&B)[3][3]) {
-    const double *A = m.A;
+__device__ void kappa_base(const ModelDev &m, R (&B)[3][3], double dv = -1.0) {
+    double Aloc[9];
+    if (dv >= 0.0) relaxation_matrix_at(m, dv, Aloc);
+    const double *A = dv >= 0.0 ? Aloc : m.A;
     const double det = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
                        A[2] * (A[3] * A[7] - A[4] * A[6]);
     double Ai[3][3];
@@ -64,7 +67,7 @@ __device__ void kappa_base(const ModelDev &m, R (&B)[3][3]) {
     Ai[2][0] = (A[3] * A[7] - A[4] * A[6]) / det;
     Ai[2][1] = (A[1] * A[6] - A[0] * A[7]) / det;
     Ai[2][2] = (A[0] * A[4] - A[1] * A[3]) / det;
-    const double dg[3] = {5.0, m.d_r, m.d_v};
+    const double dg[3] = {5.0, m.d_r, dv >= 0.0 ? dv : m.d_v};
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) B[a][b] = R(Ai[a][b] * dg[b]);
 }
@@ -82,7 +85,7 @@ __device__ __forceinline__ void primitive(const S *W, const ModelDev &m, R *q) {
     const R e = R(W[E]), er = R(W[E + 1]), ev = R(W[E + 2]), eR = R(W[E + 3]);
     q[E] = (e - eR - er - ev - R(0.5) * rho * ke) / (R(1.5) * rho);
     q[E + 1] = R(2) * er / (R(m.d_r) * rho);
-    q[E + 2] = R(2) * ev / (R(m.d_v) * rho);
+    q[E + 2] = vib_temperature<R>(m, ev / rho);
     q[E + 3] = eR;
 }
 
@@ -92,7 +95,7 @@ __device__ __forceinline__ void prim_to_W(const R *q, const ModelDev &m, R *W) {
     const R rho = q[0];
     R uu = R(0);
     for (int a = 0; a < DIM; ++a) uu += q[1 + a] * q[1 + a];
-    const R er = R(0.5) * R(m.d_r) * rho * q[E + 1], ev = R(0.5) * R(m.d_v) * rho * q[E + 2];
+    const R er = R(0.5) * R(m.d_r) * rho * q[E + 1], ev = rho * vib_energy<R>(m, q[E + 2]);
     W[0] = rho;
     for (int a = 0; a < DIM; ++a) W[1 + a] = rho * q[1 + a];
     W[E] = R(1.5) * rho * q[E] + R(0.5) * rho * uu + er + ev + q[E + 3];
@@ -112,7 +115,7 @@ __device__ __forceinline__ void convective_flux(const R *q, const R *n, const Mo
         uu += q[1 + a] * q[1 + a];
     }
     const R p = rho * T_t;
-    const R er = R(0.5) * R(m.d_r) * rho * q[E + 1], ev = R(0.5) * R(m.d_v) * rho * q[E + 2];
+    const R er = R(0.5) * R(m.d_r) * rho * q[E + 1], ev = rho * vib_energy<R>(m, q[E + 2]);
     const R eg = R(1.5) * rho * T_t + R(0.5) * rho * uu + er + ev;
     F[0] = rho * un;
     for (int a = 0; a < DIM; ++a) F[1 + a] = rho * q[1 + a] * un + p * n[a];
@@ -157,15 +160,17 @@ template <typename R, int DIM>
 __device__ void source(const R *q, const ModelDev &m, R *Q) {
     constexpr int NV = DIM + 5, E = 1 + DIM;
     const R rho = q[0], Tt = q[E], Tr = q[E + 1], Tv = q[E + 2], eR = q[E + 3];
-    const R dr = R(m.d_r), dv = R(m.d_v);
+    const R dr = R(m.d_r);
     const R Ttr = (R(3) * Tt + dr * Tr) / (R(3) + dr);
-    const R Ttv = (R(3) * Tt + dv * Tv) / (R(3) + dv);
+    const R ev = vib_energy<R>(m, Tv);
+    const R Ttv = equal_temperature<R>(m, R(3), R(3) * Tt + R(2) * ev);
     const R tau = R(sqrt(2.0 / PI)) * pow(Tt, R(m.omega - 1.0)) * R(m.Kn) / rho;
     const R k = absorption(rho, m);
     const R evR = R(4) * R(m.sigma_R) * Tv * Tv * Tv * Tv;
     for (int a = 0; a < NV; ++a) Q[a] = R(0);
     Q[E + 1] = R(0.5) * dr * rho * (Ttr - Tr) / (R(m.Z_r) * tau);
-    Q[E + 2] = R(0.5) * dv * rho * (Ttv - Tv) / (R(m.Z_v) * tau) - k * (evR - eR);
+    // (e_tv - e_v) / (Z_v tau) - k_eff (e_vR - e_R), e_tv = d_v(T_tv) rho T_tv / 2
+    Q[E + 2] = rho * (vib_energy<R>(m, Ttv) - ev) / (R(m.Z_v) * tau) - k * (evR - eR);
     Q[E + 3] = k * (evR - eR);
 }
 
@@ -173,13 +178,20 @@ __device__ void source(const R *q, const ModelDev &m, R *Q) {
 template <typename R, int DIM>
 __device__ void source_jacobian(const R *q, const ModelDev &m, R (&J)[4][4]) {
     constexpr int E = 1 + DIM;
+    // Q_v = rho (eps(T_tv) - eps_v) / (Z_v tau) - k (e_vR - e_R), eps(T) = d_v(T) T / 2,
+    // 3 T_tv + 2 eps(T_tv) = 3 T_t + 2 eps_v: d(rho eps(T_tv)) = 3 a b (de_gas - de_r) with
+    // b = rho eps'(T_tv) / (3 + 2 eps'(T_tv)), a = dT_t/de_gas (the de_v terms cancel);
+    // d e_vR / d e_v = 16 sigma_R T_v^3 / (rho eps'(T_v))
     const R rho = q[0], Tt = q[E], Tv = q[E + 2];
-    const R dr = R(m.d_r), dv = R(m.d_v);
+    const R dr = R(m.d_r);
     const R tau = R(sqrt(2.0 / PI)) * pow(Tt, R(m.omega - 1.0)) * R(m.Kn) / rho;
     const R k = absorption(rho, m);
     const R cr = rho * R(1.5) * dr / (R(3) + dr) / (R(m.Z_r) * tau);
-    const R cv = rho * R(1.5) * dv / (R(3) + dv) / (R(m.Z_v) * tau);
-    const R beta = R(16) * R(m.sigma_R) * Tv * Tv * Tv * R(2) / (dv * rho);
+    const R Ttv = equal_temperature<R>(m, R(3), R(3) * Tt + R(2) * vib_energy<R>(m, Tv));
+    const R ctv = vib_cv<R>(m, Ttv);
+    const R b = rho * ctv / (R(3) + R(2) * ctv);
+    const R zv = R(1) / (R(m.Z_v) * tau);
+    const R beta = R(16) * R(m.sigma_R) * Tv * Tv * Tv / (rho * vib_cv<R>(m, Tv));
     const R a = R(1) / (R(1.5) * rho);
     for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) J[r][c] = R(0);
@@ -188,9 +200,9 @@ __device__ void source_jacobian(const R *q, const ModelDev &m, R (&J)[4][4]) {
     J[1][0] = cr * a;
     J[1][1] = -cr * (a + R(2) / (dr * rho));
     J[1][2] = -cr * a;
-    J[2][0] = cv * a;
-    J[2][1] = -cv * a;
-    J[2][2] = -cv * (a + R(2) / (dv * rho)) - k * beta;
+    J[2][0] = R(3) * a * b * zv;
+    J[2][1] = -R(3) * a * b * zv;
+    J[2][2] = -zv - k * beta;
     J[2][3] = k;
     J[3][2] = k * beta;
     J[3][3] = -k;
@@ -296,8 +308,13 @@ namespace {
 // (gradient component a of primitive variable v); out layout as the high-order terms:
 // sigma (DIM x DIM), q_t, q_r, q_v, q_R (DIM each).
 template <typename R, int DIM>
-__device__ void nsf_face(const R *pf, const R (&fg)[DIM][DIM + 5], const ModelDev &m, const R (&base)[3][3], R *out) {
+__device__ void nsf_face(const R *pf, const R (&fg)[DIM][DIM + 5], const ModelDev &m, const R (&base0)[3][3], R *out) {
     constexpr int E = 1 + DIM;
+    R base[3][3];
+    if (m.dv_T) kappa_base<R>(m, base, dv_at(m, double(pf[E + 2])));   // at the face's T_v
+    else
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) base[a][c] = base0[a][c];
     const R mu = viscosity(pf[E], m);
     R div = R(0);
     for (int d = 0; d < DIM; ++d) div += fg[d][1 + d];
@@ -398,9 +415,14 @@ __device__ void interior_flux(const MacroGeom &g, const ModelDev &m, const R (&b
 // Far-field boundary flux: Rusanov against the free stream plus NSF terms over the
 // distance from the cell centre to the face
 template <typename R, int DIM>
-__device__ void farfield_flux(const MacroGeom &g, const ModelDev &m, const R (&base)[3][3], int b, const R *qc, R *F) {
+__device__ void farfield_flux(const MacroGeom &g, const ModelDev &m, const R (&base0)[3][3], int b, const R *qc, R *F) {
     constexpr int E = 1 + DIM;
     const double *P = g.patch_state + (size_t)g.bf_patch[b] * 8;
+    R base[3][3];
+    if (m.dv_T) kappa_base<R>(m, base, dv_at(m, 0.5 * (double(qc[E + 2]) + P[6])));   // at the face's T_v
+    else
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) base[a][c] = base0[a][c];
     R n[DIM];
     for (int a = 0; a < DIM; ++a) n[a] = R(g.bf_n[(size_t)b * 2 + a]);
     const R dn = R(g.bf_dn[b]);
@@ -498,7 +520,8 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
     const R Tw = R(P[4]);
     const R Ac = rho * pow(R(2.0 * PI) * Tt, R(-0.5 * DIM)), Bc = R(0.5) / Tt;
     const R Aw = pow(R(2.0 * PI) * Tw, R(-0.5 * DIM)), Bw = R(0.5) / Tw;
-    const R hr = R(0.5 * m.d_r), hv = R(0.5 * m.d_v);
+    const R hr = R(0.5 * m.d_r);
+    const R evc = vib_energy<R>(m, Tv), evw = vib_energy<R>(m, Tw);   // d_v(T) T / 2 of cell and wall
     R acc[2 * NS + 2];
     for (int k = 0; k < 2 * NS + 2; ++k) acc[k] = R(0);
     for (int v = threadIdx.x; v < vq.n; v += blockDim.x) {
@@ -517,7 +540,7 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
             f0 = Ac * exp(-Bc * c2);
             fh = R(MH) * Tt * f0;
             f1 = hr * Tr * f0;
-            f2 = hv * Tv * f0;
+            f2 = evc * f0;
             s = acc;
         } else {
             R c2 = R(0);
@@ -525,7 +548,7 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
             f0 = Aw * exp(-Bw * c2);
             fh = R(MH) * Tw * f0;
             f1 = hr * Tw * f0;
-            f2 = hv * Tw * f0;
+            f2 = evw * f0;
             s = acc + NS;
         }
         s[0] += wf * f0;
@@ -767,7 +790,7 @@ __device__ __forceinline__ void flux_increment(const double *q, const double *dW
                                                const ModelDev &m, float *dF) {
     constexpr int E = 1 + DIM;
     const float rho = float(q[0]), T = float(q[E]);
-    const float er = 0.5f * float(m.d_r) * rho * float(q[E + 1]), ev = 0.5f * float(m.d_v) * rho * float(q[E + 2]);
+    const float er = 0.5f * float(m.d_r) * rho * float(q[E + 1]), ev = rho * vib_energy<float>(m, float(q[E + 2]));
     float u[DIM], nf[DIM], dm[DIM], un = 0.0f, uu = 0.0f;
     for (int a = 0; a < DIM; ++a) {
         u[a] = float(q[1 + a]);

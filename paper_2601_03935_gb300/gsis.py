@@ -55,7 +55,8 @@ class gsis_photon_quad(C.Structure):
 class gsis_model_params(C.Structure):
     _fields_ = [("d_r", C.c_double), ("d_v", C.c_double), ("Z_r", C.c_double), ("Z_v", C.c_double),
                 ("omega", C.c_double), ("Sc", C.c_double), ("Kn", C.c_double), ("Kn_p", C.c_double),
-                ("sigma_R", C.c_double), ("k_eff_density_scaled", C.c_int32), ("A", _dp)]
+                ("sigma_R", C.c_double), ("k_eff_density_scaled", C.c_int32), ("A", _dp),
+                ("Tv_ref", C.c_double), ("dv_temperature_dependent", C.c_int32)]
 
 
 class gsis_solver_params(C.Structure):
@@ -191,7 +192,8 @@ def gsis_create(dim, face_owner, face_nbr, face_normal, face_area, face_centroid
     k.A = None if getattr(model, "A", None) is None else _d(model.A).reshape(9)
     mp = gsis_model_params(model.d_r, model.d_v, model.Z_r, model.Z_v, model.omega, model.Sc, model.Kn, model.Kn_p,
                            model.sigma_R, int(bool(model.k_eff_density_scaled)),
-                           None if k.A is None else _ptr(k.A))
+                           None if k.A is None else _ptr(k.A), float(getattr(model, "Tv_ref", 0.0)),
+                           int(bool(getattr(model, "dv_temperature_dependent", False))))
     prec = {"fp32": GSIS_FP32, "fp64": GSIS_FP64}.get(solver.precision, solver.precision)
     sp = gsis_solver_params(prec, solver.order, getattr(solver, "relax_block", 16), solver.cfl_meso,
                             solver.cfl_macro, solver.venkat_K, solver.n_cis_precond, solver.max_outer,
