@@ -142,57 +142,111 @@ def initial_state(wl):
                                        seed=1, noise=0.0)
 
 
-def cpu_baseline(wl, seconds=12.0):
-    """FP64 oracle sweep of whole relaxation blocks, as many as fit in ~``seconds``."""
+_ORACLE = {}
+
+
+def _oracle_worker_init(kn, kn_p, precision, order, block, tc_moments):
+    """Builds the workload, its initial state and the oracle's geometry once per worker."""
+    import types
     from oracle import kinetic as K
+    args = types.SimpleNamespace(kn=kn, kn_p=kn_p, precision=precision, order=order, block=block,
+                                 tc_moments=tc_moments)
+    wl = workload(args)
     f, I = initial_state(wl)
-    geo = K.Geometry(wl.mesh)
+    _ORACLE.update(wl=wl, f=f, I=I, geo=K.Geometry(wl.mesh))
+
+
+def _oracle_worker_run(seconds, seed):
+    """FP64 oracle sweeps of whole random relaxation blocks for about `seconds`: the cells
+    swept and the elapsed time.  Blocks are independent within one sweep (Jacobi between
+    blocks), so workers on different blocks do the work one sweep does, in parallel."""
+    from oracle import kinetic as K
+    wl, f, I, geo = _ORACLE["wl"], _ORACLE["f"], _ORACLE["I"], _ORACLE["geo"]
     B = wl.solver.relax_block
     n_blocks = (wl.mesh.n_cells + B - 1) // B
-    rng = np.random.default_rng(5)
-    done_cells, t0 = 0, time.perf_counter()
+    rng = np.random.default_rng(seed)
+    done, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
         b = int(rng.integers(n_blocks))
         cells = np.arange(b * B, min(b * B + B, wl.mesh.n_cells))
         K.kinetic_sweep(f, I, wl, geo=geo, cells=cells, relax_block=B)
-        done_cells += len(cells)
-    dt = time.perf_counter() - t0
-    return {"value": done_cells * wl.xi.shape[0] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d cells (%d random whole relaxation blocks of %d) x %d velocities, FP64 NumPy, "
-                      "one thread, %.1f s" % (done_cells, done_cells // B, B, wl.xi.shape[0], dt)}
+        done += len(cells)
+    return done, time.perf_counter() - t0
+
+
+def cpu_baseline(args, seconds=12.0, cores=None):
+    """The FP64 oracle on the host cores: a spawn process pool (safe after CUDA use), one
+    worker per core, each sweeping random whole relaxation blocks for ~`seconds`; also one
+    worker alone for the single-thread rate."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    init = (args.kn, args.kn_p, args.precision, args.order, args.block, args.tc_moments)
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=ctx, initializer=_oracle_worker_init,
+                                initargs=init) as ex:
+        list(ex.map(_oracle_worker_run, [0.01] * cores, range(cores)))          # every worker set up
+        res = list(ex.map(_oracle_worker_run, [seconds] * cores, range(100, 100 + cores)))
+        one = ex.submit(_oracle_worker_run, seconds / 2, 999).result()
+    n_xi = _n_xi_of(args)
+    cells = sum(r[0] for r in res)
+    wall = max(r[1] for r in res)
+    return {"value": cells * n_xi / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_thread_value": one[0] * n_xi / one[1],
+            "sample": "%d cells (random whole relaxation blocks of %d) x %d velocities, FP64 NumPy oracle, "
+                      "%d spawn processes on %d host cores (one NumPy thread each), %.1f s" % (
+                          cells, args.block, n_xi, cores, cores, wall)}
+
+
+def _n_xi_of(args):
+    import gsis_inputs as gi
+    return gi.workloads.cavity(n_side=2).xi.shape[0]
+
+
+def _oracle_worker_block(seed):
+    """One random whole relaxation block swept by the FP64 oracle: the cells swept."""
+    from oracle import kinetic as K
+    wl, f, I, geo = _ORACLE["wl"], _ORACLE["f"], _ORACLE["I"], _ORACLE["geo"]
+    B = wl.solver.relax_block
+    b = int(np.random.default_rng(seed).integers((wl.mesh.n_cells + B - 1) // B))
+    cells = np.arange(b * B, min(b * B + B, wl.mesh.n_cells))
+    K.kinetic_sweep(f, I, wl, geo=geo, cells=cells, relax_block=B)
+    return len(cells)
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on the host cores: a spawn process pool with one worker
+    per core; a step sweeps one random whole relaxation block on every worker."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     wl = workload(args)
-    from oracle import kinetic as K
-    f, I = initial_state(wl)
-    geo = K.Geometry(wl.mesh)
-    B = wl.solver.relax_block
-    n_blocks = (wl.mesh.n_cells + B - 1) // B
-    rng = np.random.default_rng(7)
+    cores = os.cpu_count() or 1
+    init = (args.kn, args.kn_p, args.precision, args.order, args.block, args.tc_moments)
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"),
+                                initializer=_oracle_worker_init, initargs=init) as ex:
+        seed = [0]
 
-    def step():
-        b = int(rng.integers(n_blocks))
-        cells = np.arange(b * B, min(b * B + B, wl.mesh.n_cells))
-        K.kinetic_sweep(f, I, wl, geo=geo, cells=cells, relax_block=B)
-        return len(cells)
+        def step():
+            seeds = list(range(seed[0], seed[0] + cores))
+            seed[0] += cores
+            return sum(ex.map(_oracle_worker_block, seeds))
 
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    cells = sum(step() for _ in range(args.steps))
-    dt = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        cells = sum(step() for _ in range(args.steps))
+        dt = time.perf_counter() - t0
     value = cells * wl.xi.shape[0] / dt
-    sample = "%d steps x one random relaxation block of %d cells x %d velocities (FP64 NumPy oracle, one thread)" % (
-        args.steps, B, wl.xi.shape[0])
+    sample = ("%d steps x %d random relaxation blocks of %d cells (one per worker) x %d velocities (FP64 NumPy oracle, "
+              "%d spawn processes on %d host cores)" % (args.steps, cores, args.block, wl.xi.shape[0], cores, cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args, wl),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -304,6 +358,56 @@ def normal_shock(max_gsis=300):
                          "eps_at": {str(k): float(hist[k]) for k in (9, 49, 99, 199) if k < len(hist)}}
             G.gsis_destroy(ctx)
         out["Zr%g_Zv%g_L%g" % (Zr, Zv, L)] = res
+    return out
+
+
+def slab_time_to_steady(oracle_seconds=40.0):
+    """The 1-D planar slab of config 1 (64 cells between walls at T = 1 and 1.5, optical
+    thickness 1, 32 Gauss-Hermite velocities, 16 Gauss-Legendre directions, order 2, FP64)
+    from the uniform rest state at T = 1.25: outer iterations and seconds to eps < 1e-8
+    on the GPU for CIS and for GSIS (3 CIS iterations first), at the config's Kn = 0.1 and
+    at Kn = 0.01; and the FP64 oracle's time to the same tolerance on one host core
+    (stopped after about `oracle_seconds`)."""
+    import torch
+    import gsis_inputs as gi
+    from oracle import gsis as OG
+    from oracle import kinetic as K
+    from oracle import macro as MA
+    from paper_2601_03935_gb300 import gsis as G
+    out = {}
+    for kn, inner, oracle_mode in ((0.1, 100, "cis"), (0.01, 200, "gsis")):
+        wl = gi.workloads.with_solver(gi.workloads.slab(64, Kn=kn), precision="fp64", order=2, relax_block=16,
+                                      max_inner=inner, tol_inner=1e-7, n_cis_precond=3)
+        M = gi.fields.uniform_fields(64, T=1.25)
+        f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 1, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, 0,
+                                           noise=0.0)
+        res = {"workload": "slab 1-D, 64 cells, 32 velocities, 16 directions, Kn %g, Kn_p 1, FP64, order 2, "
+                           "%d inner iterations, eps < 1e-8" % (kn, inner)}
+        for mode, name, mx in ((G.GSIS_MODE_GSIS, "gsis", 200), (G.GSIS_MODE_CIS, "cis", 20000)):
+            ctx = create_ctx(wl, 0)
+            G.gsis_set_distributions(ctx, f, I)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist = G.gsis_solve(ctx, mode, mx, 1e-8)
+            torch.cuda.synchronize()
+            res[name] = {"iterations": it, "seconds": time.perf_counter() - t0, "final_eps": float(hist[-1]),
+                         "converged": bool(hist[-1] < 1e-8)}
+            G.gsis_destroy(ctx)
+        geo = K.Geometry(wl.mesh)
+        faces = MA.Faces(geo)
+        fo, Io, F, h = f.copy(), I.copy(), None, []
+        t0 = time.perf_counter()
+        for k in range(20000):
+            if oracle_mode == "cis" or k < wl.solver.n_cis_precond:
+                fo, Io, e, F = OG.cis_step(fo, Io, wl, geo)
+            else:
+                fo, Io, e, F = OG.gsis_step(fo, Io, wl, geo, faces, F)
+            h.append(e)
+            if e < 1e-8 or time.perf_counter() - t0 > oracle_seconds:
+                break
+        res["oracle_" + oracle_mode] = {"iterations": len(h), "seconds": time.perf_counter() - t0,
+                                        "final_eps": float(h[-1]), "converged": bool(h[-1] < 1e-8), "cores": 1}
+        out["Kn%g" % kn] = res
     return out
 
 
@@ -709,6 +813,8 @@ def run_ours(args):
     }
     if not args.no_tts:
         line["time_to_steady"] = time_to_steady(stream)
+    if not args.no_tts:
+        line["slab_time_to_steady"] = slab_time_to_steady()
     if not args.no_shock:
         line["normal_shock"] = normal_shock()
     if not args.no_cylinder:
@@ -718,7 +824,7 @@ def run_ours(args):
     if not args.no_field_errors:
         line["field_errors"] = field_errors(stream)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args, seconds=args.cpu_seconds)
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -63,7 +63,10 @@ def test_loss_gradient_matches_oracle(ctx):
         for ref in (gW, gb):
             got = g[off:off + ref.size].reshape(ref.shape)
             off += ref.size
-            assert np.linalg.norm(got - ref) <= 1e-3 * np.linalg.norm(ref)
+            # element by element: 1e-3 relative, with a floor of 1e-4 of the tensor's largest
+            # entry for entries that nearly cancel (FP32 accumulation over 300 rows)
+            tol = 1e-3 * np.abs(ref) + 1e-4 * np.abs(ref).max()
+            assert np.all(np.abs(got - ref) <= tol), np.abs(got - ref).max()
     assert off == G.GSIS_MLP_NW
 
 
