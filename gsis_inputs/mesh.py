@@ -14,6 +14,7 @@ import numpy as np
 
 WALL = 0        # diffuse wall for the gas, black wall for photons
 FARFIELD = 1    # incoming characteristics carry a prescribed equilibrium state
+SYMMETRY = 2    # specular reflection of molecules and photons (a mirror plane)
 
 
 @dataclass

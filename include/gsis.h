@@ -59,6 +59,14 @@ extern "C" {
 #define GSIS_PATCH_WALL     0  /* gas: diffuse, fully accommodating at (T_t, u);
                                   photons: black at T_t                           */
 #define GSIS_PATCH_FARFIELD 1  /* incoming: equilibrium of (rho, u, T_t, T_r, T_v, T_R) */
+#define GSIS_PATCH_SYMMETRY 2  /* mirror plane: molecules and photons reflect specularly
+                                  (what enters at xi is what leaves at xi - 2 (xi.n) n);
+                                  the synthetic equations take the Rusanov flux against the
+                                  cell state with its normal velocity reversed, no viscous,
+                                  conductive or radiative flux.  The velocity and photon
+                                  sets must be symmetric under the reflection (gsis_create
+                                  returns INVALID_ARG otherwise); the patch's state fields
+                                  are ignored.  Not combinable with velocity sharding.      */
 
 typedef struct {
     int32_t kind;               /* GSIS_PATCH_*                                    */

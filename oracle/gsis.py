@@ -50,9 +50,9 @@ def gsis_step(f, I, wl, geo, faces, F_old=None):
     with multi-temperature equilibria (photons: sigma_R T_R^4 / pi).  The paper's
     step has w = 1; w = wl.solver.sync_relax.
 
-    In a closed domain (walls only) the total mass is not fixed by the steady equations,
-    and a synthetic solve stopped after a finite number of point-relaxation sweeps moves
-    it.  That drift would pass into f through the synchronisation every iteration, so
+    In a closed domain (walls and mirror planes only) the total mass is not fixed by the
+    steady equations, and a synthetic solve stopped after a finite number of
+    point-relaxation sweeps moves it.  That drift would pass into f through the synchronisation every iteration, so
     M^{k+1} is rescaled to the total mass of M^{k+1/2} there (a uniform factor on all
     conservative variables: velocities and temperatures are unchanged)."""
     from . import macro as MA
@@ -63,7 +63,7 @@ def gsis_step(f, I, wl, geo, faces, F_old=None):
     hot = MA.high_order_terms(faces, Fh, MA.kinetic_boundary_flux(faces, fh, Ih, wl), wl)
     Wh = MA.conservative(Fh, dim, model)
     W = MA.macro_solve(Wh, faces, hot, wl)
-    if all(p.kind == K.WALL for p in wl.mesh.patches):
+    if all(p.kind in (K.WALL, K.SYMMETRY) for p in wl.mesh.patches):
         W = W * (np.sum(F_old["rho"] * geo.vol) / np.sum(W[:, 0] * geo.vol))
     Fn = MA.fields_from_W(W, dim, model)
     om = wl.solver.sync_relax

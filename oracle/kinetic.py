@@ -21,7 +21,7 @@ import numpy as np
 
 from . import model as mdl
 
-WALL, FARFIELD = 0, 1
+WALL, FARFIELD, SYMMETRY = 0, 1, 2
 
 
 # --------------------------------------------------------------------------- fields
@@ -263,6 +263,22 @@ def wall_density(geo, f0_cell, xi, w, dim, patch, n):
     return -out / inc
 
 
+def reflection_index(points, n):
+    """For each point p of a velocity (or direction) set, the index of its mirror image
+    p - 2 (p.n) n under specular reflection at a plane of unit normal n (reading: the sets
+    must be symmetric under that reflection; the images are matched to 1e-9 of the set's
+    scale).  Photon directions are matched with all three components: reflection at an
+    in-plane normal keeps Omega_z."""
+    d = points.shape[1]
+    img = points - 2.0 * (points @ n[:d])[:, None] * n[None, :d]
+    scale = max(np.abs(points).max(), 1.0)
+    dist = np.abs(img[:, None, :] - points[None, :, :]).max(axis=-1)
+    idx = np.argmin(dist, axis=1)
+    if np.any(dist[np.arange(points.shape[0]), idx] > 1e-9 * scale):
+        raise ValueError("the set is not symmetric under reflection at this normal")
+    return idx
+
+
 def incoming_gas(patch, rho_w, xi, dim, model):
     """Planes entering the domain through a boundary face ([V, 4])."""
     m = 3 - dim
@@ -372,9 +388,14 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
                 od.append((nb, S * xm / geo.vol[i], S * omn / geo.vol[i]))
             else:
                 patch = mesh.patches[-1 - nb]
-                rw = wall_density(geo, f[i, :, 0], xi, w, dim, patch, n) if patch.kind == WALL else 1.0
-                fL, fR = f[i], incoming_gas(patch, rw, xi, dim, model)
-                IL, IR = I[i], incoming_photon(patch, model, om.shape[0])
+                if patch.kind == SYMMETRY:
+                    # specular reflection: what enters with xi is what leaves with its mirror image
+                    fL, fR = f[i], f[i][reflection_index(xi[:, :dim], n)]
+                    IL, IR = I[i], I[i][reflection_index(om, np.pad(n, (0, 3 - dim)))]   # directions in 3-D
+                else:
+                    rw = wall_density(geo, f[i, :, 0], xi, w, dim, patch, n) if patch.kind == WALL else 1.0
+                    fL, fR = f[i], incoming_gas(patch, rw, xi, dim, model)
+                    IL, IR = I[i], incoming_photon(patch, model, om.shape[0])
             r -= (S / geo.vol[i]) * (xp[:, None] * fL + xm[:, None] * fR)
             rR -= (S / geo.vol[i]) * (op * IL + omn * IR)
             d += S * xp / geo.vol[i]

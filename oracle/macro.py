@@ -306,6 +306,15 @@ def macro_boundary_flux(faces, prim, wl):
         if patch.kind == K.WALL:
             out[b] = wall_equilibrium_flux(faces, tuple(x[c[b]:c[b] + 1] for x in prim), wl, b)
             continue
+        if patch.kind == K.SYMMETRY:
+            # mirror state: the cell state with its normal velocity reversed; Rusanov between
+            # the two carries no mass or energy and the pressure plus the damped normal
+            # momentum; no viscous stress, conduction or radiative flux crosses a mirror
+            inside = tuple(x[b:b + 1] for x in (rho, u, T_t, T_r, T_v, e_R))
+            um = u[b:b + 1] - 2.0 * np.sum(u[b] * n[b]) * n[b:b + 1]
+            mirror = (rho[b:b + 1], um, T_t[b:b + 1], T_r[b:b + 1], T_v[b:b + 1], e_R[b:b + 1])
+            out[b] = rusanov(inside, mirror, n[b:b + 1], dim, model)[0]
+            continue
         inside = (rho[b:b + 1], u[b:b + 1], T_t[b:b + 1], T_r[b:b + 1], T_v[b:b + 1], e_R[b:b + 1])
         far = (np.array([patch.rho]), uw[None], np.array([patch.T_t]), np.array([patch.T_r]),
                np.array([patch.T_v]), np.array([4.0 * model.sigma_R * patch.T_R ** 4]))
@@ -383,8 +392,11 @@ def kinetic_boundary_flux(faces, f, I, wl):
     for b, (c, n, p) in enumerate(zip(faces.bf_cell, faces.bf_n, faces.bf_patch)):
         patch = mesh.patches[p]
         xn = xi[:, :dim] @ n
-        rw = K.wall_density(None, f[c, :, 0], xi, w, dim, patch, n) if patch.kind == K.WALL else 1.0
-        inc = K.incoming_gas(patch, rw, xi, dim, model)
+        if patch.kind == K.SYMMETRY:
+            inc = f[c][K.reflection_index(xi[:, :dim], n)]
+        else:
+            rw = K.wall_density(None, f[c, :, 0], xi, w, dim, patch, n) if patch.kind == K.WALL else 1.0
+            inc = K.incoming_gas(patch, rw, xi, dim, model)
         face = np.where((xn > 0)[:, None], f[c], inc)
         wf = w * xn
         out[b, 0] = wf @ face[:, 0]
@@ -393,7 +405,10 @@ def kinetic_boundary_flux(faces, f, I, wl):
         out[b, 2 + dim] = wf @ face[:, 2]
         out[b, 3 + dim] = wf @ face[:, 3]
         on = om[:, :dim] @ n
-        Iinc = K.incoming_photon(patch, model, om.shape[0])
+        if patch.kind == K.SYMMETRY:
+            Iinc = I[c][K.reflection_index(om, np.pad(n, (0, 3 - dim)))]
+        else:
+            Iinc = K.incoming_photon(patch, model, om.shape[0])
         Iface = np.where(on > 0, I[c], Iinc)
         qR = (wo * on) @ Iface
         out[b, 4 + dim] = qR
@@ -454,6 +469,11 @@ def boundary_gamma(faces, prim, wl):
     G = np.repeat(base[:, None], nvar(dim), axis=1)
     kR = 1.0 / (3.0 * mdl.absorption(rho, wl.model))
     G[:, 4 + dim] += 2.0 * kR / db
+    sym = np.array([geo.mesh.patches[p].kind == K.SYMMETRY for p in faces.bf_patch], bool)
+    if sym.any():
+        # a mirror face: the Rusanov part only, and no e_R flux
+        G[sym] = (np.abs(np.sum(u * n, axis=1)) + sound_speed(T_t))[sym, None]
+        G[sym, 4 + dim] = 0.0
     return G
 
 

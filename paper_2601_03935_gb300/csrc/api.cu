@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <array>
 #include <new>
 #include <random>
 #include <string>
@@ -106,6 +107,8 @@ struct gsis_ctx {
     int shard_nxt = 0;
     int Vd = 0, Vdp = 0, NOd = 0, Odp = 0;   // sizes of the FP64 quadratures of the synthetic equations
     std::vector<double> h_wall;  // per boundary face: wall flag, normal[3], wall T, wall u[3]
+    int *bf_tab = nullptr, *refl_v = nullptr, *refl_o = nullptr;   // mirror-plane reflection tables
+    bool mirrors = false;
 
     bool have_eps = false;
     double last_eps = 0.0;
@@ -195,6 +198,9 @@ Geom<Real> geom(const gsis_ctx *c) {
     g.bf_nrm = (const Real *)c->bf_nrm;
     g.tc_wait = c->tc_wait;
     g.err = c->err;
+    g.bf_tab = c->bf_tab;
+    g.refl_v = c->refl_v;
+    g.refl_o = c->refl_o;
     return g;
 }
 
@@ -618,7 +624,9 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
         return why = "a temperature-dependent d_v needs Tv_ref > 0", GSIS_ERR_INVALID_ARG;
     for (int p = 0; p < m->n_patches; ++p) {
         const gsis_patch &P = m->patches[p];
-        if (P.kind != GSIS_PATCH_WALL && P.kind != GSIS_PATCH_FARFIELD) return why = "bad patch kind", GSIS_ERR_INVALID_ARG;
+        if (P.kind != GSIS_PATCH_WALL && P.kind != GSIS_PATCH_FARFIELD && P.kind != GSIS_PATCH_SYMMETRY)
+            return why = "bad patch kind", GSIS_ERR_INVALID_ARG;
+        if (P.kind == GSIS_PATCH_SYMMETRY) continue;     // a mirror plane has no state
         if (!(P.T_t > 0) || (P.kind == GSIS_PATCH_FARFIELD && (!(P.rho > 0) || !(P.T_r > 0) || !(P.T_v > 0) || !(P.T_R >= 0))))
             return why = "bad patch state", GSIS_ERR_INVALID_ARG;
     }
@@ -969,7 +977,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         for (int p = 0; p < m->n_patches; ++p) {
             const gsis_patch &P = m->patches[p];
             mpk[p] = P.kind;
-            if (P.kind != GSIS_PATCH_WALL) c->closed = false;
+            if (P.kind != GSIS_PATCH_WALL && P.kind != GSIS_PATCH_SYMMETRY) c->closed = false;
             const double st[8] = {P.rho, P.u[0], P.u[1], P.u[2], P.T_t, P.T_r, P.T_v, P.T_R};
             for (int k = 0; k < 8; ++k) mps[p * 8 + k] = st[k];
         }
@@ -1138,6 +1146,62 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(upload_real(c, c->bcoef, bco));
     A_(upload(c, c->patch_T, pT));
     A_(upload(c, c->patch_u, pu));
+    {   // mirror planes: for each distinct face normal of a SYMMETRY patch, the index of the
+        // mirror image x - 2 (x.n) n of every velocity and photon direction (the sets must be
+        // symmetric under it; images matched to 1e-9 of the set's scale)
+        std::vector<int> tab((size_t)std::max(c->n_bf, 1), -1), rv, ro;
+        std::vector<std::array<double, 3>> normals;
+        auto mirror = [&](int n_pts, int pad, int d, const double *pts, const double *nn, std::vector<int> &out) {
+            double scale = 1.0;
+            for (int v = 0; v < n_pts * d; ++v) scale = std::max(scale, std::fabs(pts[v]));
+            const size_t base = out.size();
+            out.resize(base + (size_t)pad);
+            for (int v = 0; v < pad; ++v) out[base + v] = v;     // padding maps to itself
+            for (int v = 0; v < n_pts; ++v) {
+                double img[3] = {0, 0, 0}, dot = 0.0;
+                for (int a = 0; a < d; ++a) dot += pts[(size_t)v * d + a] * (a < dim ? nn[a] : 0.0);
+                for (int a = 0; a < d; ++a) img[a] = pts[(size_t)v * d + a] - 2.0 * dot * (a < dim ? nn[a] : 0.0);
+                int best = -1;
+                double bd = 1e300;
+                for (int w = 0; w < n_pts; ++w) {
+                    double e = 0.0;
+                    for (int a = 0; a < d; ++a) e = std::max(e, std::fabs(pts[(size_t)w * d + a] - img[a]));
+                    if (e < bd) bd = e, best = w;
+                }
+                if (bd > 1e-9 * scale) return false;
+                out[base + v] = best;
+            }
+            return true;
+        };
+        for (int b = 0; b < c->n_bf; ++b) {
+            if (m->patches[bf_patch[b]].kind != GSIS_PATCH_SYMMETRY) continue;
+            const std::array<double, 3> nb = {bfn[b * 3], bfn[b * 3 + 1], bfn[b * 3 + 2]};
+            int t = -1;
+            for (size_t k = 0; k < normals.size(); ++k)
+                if (std::fabs(normals[k][0] - nb[0]) + std::fabs(normals[k][1] - nb[1]) + std::fabs(normals[k][2] - nb[2]) < 1e-12)
+                    t = (int)k;
+            if (t < 0) {
+                t = (int)normals.size();
+                normals.push_back(nb);
+                if (!mirror(vq->n, c->Vp, dim, vq->xi, nb.data(), rv) || !mirror(pq->n, c->Op, 3, pq->omega, nb.data(), ro)) {
+                    fprintf(stderr, "gsis: a mirror plane needs velocity and photon sets symmetric under its reflection\n");
+                    return bail(GSIS_ERR_INVALID_ARG);
+                }
+            }
+            tab[b] = t;
+        }
+        if (rv.empty()) rv.assign(1, 0), ro.assign(1, 0);
+        A_(dalloc(c, &c->bf_tab, tab.size()));
+        A_(dalloc(c, &c->refl_v, rv.size()));
+        A_(dalloc(c, &c->refl_o, ro.size()));
+        A_(upload(c, c->bf_tab, tab));
+        A_(upload(c, c->refl_v, rv));
+        A_(upload(c, c->refl_o, ro));
+        c->mirrors = !normals.empty();
+        c->mg.bf_tab = c->bf_tab;       // the synthetic equations' geometry was filled above
+        c->mg.refl_v = c->refl_v;
+        c->mg.refl_o = c->refl_o;
+    }
     c->h_wall.assign((size_t)std::max(c->n_bf, 1) * 8, 0.0);
     for (int b = 0; b < c->n_bf; ++b) {     // per boundary face: wall flag, normal, wall T and u
         const gsis_patch &P = m->patches[bf_patch[b]];
@@ -1544,6 +1608,8 @@ int gsis_shard_setup(gsis_ctx *c, int32_t n_xi_all, const double *xi_all, const 
                      const double *omega_all, const double *wo_all) {
     if (!c || !xi_all || !w_all || !omega_all || !wo_all) return fail(c, GSIS_ERR_INVALID_ARG, "null pointer");
     if (c->sharded) return fail(c, GSIS_ERR_INVALID_ARG, "the context is already a shard");
+    if (c->mirrors)
+        return fail(c, GSIS_ERR_UNSUPPORTED, "mirror planes pair velocities across shards; shard a mesh without them");
     if (n_xi_all < c->V || n_omega_all < c->NO) return fail(c, GSIS_ERR_INVALID_ARG, "the full sets are smaller than the shard");
     const int dim = c->dim;
     // the incoming unit-density wall flux over every velocity of every shard

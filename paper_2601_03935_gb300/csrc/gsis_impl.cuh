@@ -75,6 +75,9 @@ struct Geom {
     const int *bf_cell;        // [n_bf]
     const int *bf_patch;       // [n_bf]
     const Real *bf_nrm;        // [n_bf][3] outward normal
+    const int *bf_tab;         // [n_bf] mirror-reflection table of the face (SYMMETRY patch) or -1
+    const int *refl_v;         // [tables][v_pad] index of the mirror image of each velocity
+    const int *refl_o;         // [tables][o_pad] index of the mirror image of each photon direction
     int tc_wait;               // polls of the first tensor-core completion wait (ERR_TIMEOUT bit on expiry)
     int *err;                  // device error word: bit 0 divergence, bit 1 a completion wait ran out
 };
@@ -196,8 +199,10 @@ struct MacroGeom {
     const double *bf_n;        // [n_bf][2] outward normal
     const double *bf_S;        // [n_bf]
     const double *bf_dn;       // [n_bf] |n . (x_f - x_c)|
-    const int *patch_kind;     // [n_patches]
+    const int *patch_kind;     // [n_patches]: 0 wall, 1 far field, 2 mirror plane
     const double *patch_state; // [n_patches][8]: rho, u[3], T_t, T_r, T_v, T_R
+    const int *bf_tab;         // [n_bf] mirror-reflection table of the face or -1 (as Geom)
+    const int *refl_v, *refl_o;
 };
 
 // Double-precision quadratures for the macroscopic boundary fluxes.

@@ -767,6 +767,11 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
                 fv = fk[k];
             } else if (xn > Real(0)) {
                 fv = fi;
+            } else if (g.bf_tab[-1 - src] >= 0) {
+                // mirror plane: what enters at this velocity leaves at its mirror image
+                const int t = g.bf_tab[-1 - src];
+                const int vr = PHOTON ? g.refl_o[(size_t)t * stride + v] : g.refl_v[(size_t)t * stride + v];
+                fv = ldv<Real, N>(f_in, (size_t)(c0 + l) * stride + vr);
             } else {
                 const Real *B = bcoef + (size_t)(-1 - src) * bc::NB;
                 if constexpr (PHOTON) {
@@ -1347,9 +1352,11 @@ __global__ void k_sync_photon(int n_cells, Quad<Real> oq, ModelDev m, double om,
 // incoming unit-density part r[NS..2NS) scaled by the wall density (zero net mass flux) or
 // the far-field density, and the photon flux r[2NS] (also added to the energy row).
 template <int DIM>
-__device__ __forceinline__ void kbflux_combine(const double *r, bool wall, double rho_far, double *o) {
+__device__ __forceinline__ void kbflux_combine(const double *r, int kind, double rho_far, double *o) {
     constexpr int E = 1 + DIM, NS = DIM + 4;
-    const double scale = wall ? -r[0] / r[NS] : rho_far;
+    // wall: the density with zero net mass flux; far field: its density; mirror plane: the
+    // incoming part is already in r[0..NS) (reflected cell values)
+    const double scale = kind == 0 ? -r[0] / r[NS] : (kind == 1 ? rho_far : 0.0);
     for (int k = 0; k < NS; ++k) o[k] = r[k] + scale * r[NS + k];
     o[E + 3] = r[2 * NS];
     o[E] += o[E + 3];
@@ -1364,6 +1371,7 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
     const int c = g.bf_cell[b];
     const int pid = g.bf_patch[b];
     const bool wall = g.patch_kind[pid] == 0;
+    const int tab = g.bf_tab[b];     // >= 0: a mirror plane, entering values are the cell's mirror images
     const double *P = g.patch_state + (size_t)pid * 8;
     const double *n = g.bf_n + (size_t)b * 2;
     const double T = P[4], Tr = wall ? P[4] : P[5], Tv = wall ? P[4] : P[6], TR = wall ? P[4] : P[7];
@@ -1381,6 +1389,14 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
         double f0, fh, f1, f2, *s;
         if (xn > 0.0) {
             const Vec<Real, 4> fv = vload<Real, 4>(f + ((size_t)c * vq.n_pad + v) * 4);
+            f0 = fv.v[0];
+            fh = fv.v[1];
+            f1 = fv.v[2];
+            f2 = fv.v[3];
+            s = acc;
+        } else if (tab >= 0) {
+            const Vec<Real, 4> fv =
+                vload<Real, 4>(f + ((size_t)c * vq.n_pad + g.refl_v[(size_t)tab * vq.n_pad + v]) * 4);
             f0 = fv.v[0];
             fh = fv.v[1];
             f1 = fv.v[2];
@@ -1405,7 +1421,8 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
     for (int o = threadIdx.x; o < oq.n; o += blockDim.x) {
         double on = 0.0;
         for (int a = 0; a < DIM; ++a) on += (double)oq.x[a * oq.n_pad + o] * n[a];
-        acc[2 * NS] += (double)oq.w[o] * on * (on > 0.0 ? (double)I[(size_t)c * oq.n_pad + o] : Iin);
+        const double Iw = tab >= 0 ? (double)I[(size_t)c * oq.n_pad + g.refl_o[(size_t)tab * oq.n_pad + o]] : Iin;
+        acc[2 * NS] += (double)oq.w[o] * on * (on > 0.0 ? (double)I[(size_t)c * oq.n_pad + o] : Iw);
     }
     __shared__ double buf[4][2 * NS + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1424,7 +1441,7 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
             for (int k = 0; k < KBR; ++k) raw[(size_t)b * KBR + k] = k < 2 * NS + 1 ? r[k] : 0.0;
             return;
         }
-        kbflux_combine<DIM>(r, wall, P[0], out + (size_t)b * NVM);
+        kbflux_combine<DIM>(r, g.patch_kind[pid], P[0], out + (size_t)b * NVM);
     }
 }
 
@@ -1433,7 +1450,7 @@ __global__ void k_kbflux_combine(MacroGeom g, const double *__restrict__ raw, do
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.n_bf) return;
     const int pid = g.bf_patch[b];
-    kbflux_combine<DIM>(raw + (size_t)b * KBR, g.patch_kind[pid] == 0, g.patch_state[(size_t)pid * 8],
+    kbflux_combine<DIM>(raw + (size_t)b * KBR, g.patch_kind[pid], g.patch_state[(size_t)pid * 8],
                         out + (size_t)b * NVM);
 }
 

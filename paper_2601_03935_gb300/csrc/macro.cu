@@ -501,6 +501,21 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
     double *out = bflux + (size_t)b * NVM;
     const int pk = g.patch_kind[g.bf_patch[b]];
     __shared__ R red[2 * NS + 2];
+    if (pk == 2) {   // mirror plane: Rusanov against the cell state with its normal velocity reversed
+        if (threadIdx.x == 0) {
+            R n[DIM], qm[NV], F[NV], un = R(0);
+            for (int a = 0; a < DIM; ++a) {
+                n[a] = R(g.bf_n[(size_t)b * 2 + a]);
+                un += qc[1 + a] * n[a];
+            }
+            for (int k = 0; k < NV; ++k) qm[k] = qc[k];
+            for (int a = 0; a < DIM; ++a) qm[1 + a] = qc[1 + a] - R(2) * un * n[a];
+            rusanov<R, DIM>(qc, qm, n, m, F);
+            F[E + 3] = R(0);
+            for (int k = 0; k < NV; ++k) out[k] = F[k];
+        }
+        return;
+    }
     if (pk != 0) {   // far field
         if (threadIdx.x == 0) {
             R base[3][3], F[NV];
@@ -699,8 +714,10 @@ __global__ void __launch_bounds__(128) k_macro_residual(MacroGeom g, ModelDev m,
             R un = R(0);
             for (int a = 0; a < DIM; ++a) un += qi[1 + a] * R(g.bf_n[(size_t)b * 2 + a]);
             const R db = R(g.bf_dn[b]);
-            const R gb = fabs(un) + sound_speed(qi[E]) + R(2) * viscosity(qi[E], m) / (qi[0] * db);
-            const R gR = R(2) * (R(1) / (R(3) * absorption(qi[0], m))) / db;
+            const bool mirror = g.patch_kind[g.bf_patch[b]] == 2;
+            // a mirror face: the Rusanov part only, and nothing in the e_R row
+            const R gb = fabs(un) + sound_speed(qi[E]) + (mirror ? R(0) : R(2) * viscosity(qi[E], m) / (qi[0] * db));
+            const R gR = mirror ? -gb : R(2) * (R(1) / (R(3) * absorption(qi[0], m))) / db;
             gsum = gb * S;
             gsumR = gR * S;
         }

@@ -22,6 +22,7 @@ GSIS_ERR_UNSUPPORTED = -8
 GSIS_NF = 26
 GSIS_PATCH_WALL = 0
 GSIS_PATCH_FARFIELD = 1
+GSIS_PATCH_SYMMETRY = 2
 GSIS_FP32 = 0
 GSIS_FP64 = 1
 GSIS_MODE_CIS = 0
