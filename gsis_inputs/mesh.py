@@ -192,3 +192,127 @@ def cylinder_ogrid(n_theta: int, n_radial: int, seed: int = 1, r_body: float = 0
     return Mesh(dim=2, n_cells=len(tris), face_owner=owner, face_nbr=nb, face_normal=n,
                 face_area=area, face_centroid=fc, cell_volume=vol, cell_centroid=cc,
                 patches=list(patches))
+
+
+def box_tetrahedra(n: int, seed: int = 2, jitter: float = 0.15, size=(1.0, 1.0, 1.0), patches=None) -> Mesh:
+    """Jittered tetrahedral mesh of a box: n^3 hexahedra, each cut into 6 tetrahedra along
+    its main diagonal (every hexahedron cut the same way, so neighbouring cuts match):
+    6 n^3 cells.  Interior vertices move by up to ``jitter*h`` per direction.  Hexahedra
+    are numbered along a 3-D Morton curve and each one's tetrahedra are consecutive, so
+    runs of consecutive cells are compact.  Patches: 0 x = 0, 1 x = L_x, 2 y = 0,
+    3 y = L_y, 4 z = 0, 5 z = L_z (walls by default)."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(size, np.float64)
+    g = np.linspace(0.0, 1.0, n + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    verts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    inner = np.all((verts > 0) & (verts < 1), axis=1)
+    verts[inner] += rng.uniform(-jitter / n, jitter / n, size=(int(inner.sum()), 3))
+    verts *= L[None]
+    vid = lambda i, j, k: (i * (n + 1) + j) * (n + 1) + k
+
+    def morton3(i, j, k):
+        code = np.zeros_like(i)
+        for b in range(11):
+            code |= (((i >> b) & 1) << (3 * b)) | (((j >> b) & 1) << (3 * b + 1)) | (((k >> b) & 1) << (3 * b + 2))
+        return code
+
+    I, J, Kk = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    I, J, Kk = I.ravel(), J.ravel(), Kk.ravel()
+    order = np.argsort(morton3(I, J, Kk), kind="stable")
+    I, J, Kk = I[order], J[order], Kk[order]
+    perms = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+    tets = []
+    for p in perms:
+        path = [np.zeros(3, int)]
+        for a in p:
+            step = path[-1].copy()
+            step[a] = 1
+            path.append(step)
+        tets.append(np.stack([vid(I + c[0], J + c[1], Kk + c[2]) for c in path], axis=1))
+    tets = np.stack(tets, axis=1).reshape(-1, 4)                 # [hex * 6 + t, 4]
+    P = verts[tets]                                             # [nc, 4, 3]
+    vol6 = np.einsum("nd,nd->n", np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), P[:, 3] - P[:, 0])
+    vol = np.abs(vol6) / 6.0
+    cc = P.mean(axis=1)
+    # faces: the triple opposite each vertex; shared triples pair owner and neighbour
+    tri = np.concatenate([tets[:, [1, 2, 3]], tets[:, [0, 2, 3]], tets[:, [0, 1, 3]], tets[:, [0, 1, 2]]])
+    cell = np.concatenate([np.arange(tets.shape[0])] * 4)
+    key = np.sort(tri, axis=1)
+    o = np.lexsort((key[:, 2], key[:, 1], key[:, 0]))
+    key, tri, cell = key[o], tri[o], cell[o]
+    same = np.all(key[1:] == key[:-1], axis=1)
+    first = np.ones(key.shape[0], bool)
+    first[1:] = ~same
+    owner = cell[first]
+    ftri = tri[first]
+    nb = np.full(owner.shape[0], -1, np.int64)
+    idx_first = np.nonzero(first)[0]
+    pair = np.zeros(key.shape[0], bool)
+    pair[:-1] = same
+    nb[np.searchsorted(idx_first, np.nonzero(pair)[0])] = cell[np.nonzero(pair)[0] + 1]
+    A, B, C = verts[ftri[:, 0]], verts[ftri[:, 1]], verts[ftri[:, 2]]
+    cr = np.cross(B - A, C - A)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    nrm = cr / (2.0 * area[:, None])
+    fc = (A + B + C) / 3.0
+    flip = np.einsum("fd,fd->f", nrm, fc - cc[owner]) < 0.0     # outward from the owner
+    nrm[flip] = -nrm[flip]
+    bnd = nb < 0
+    side = np.zeros(owner.shape[0], np.int64)
+    for a in range(3):
+        side[bnd & (np.abs(fc[:, a]) < 1e-9 * L[a])] = 2 * a
+        side[bnd & (np.abs(fc[:, a] - L[a]) < 1e-9 * L[a])] = 2 * a + 1
+    nb[bnd] = -1 - side[bnd]
+    if patches is None:
+        patches = [Patch(WALL, T_t=1.0) for _ in range(6)]
+    return Mesh(dim=3, n_cells=int(tets.shape[0]), face_owner=owner.astype(np.int32), face_nbr=nb.astype(np.int32),
+                face_normal=nrm, face_area=area, face_centroid=fc, cell_volume=vol, cell_centroid=cc,
+                patches=list(patches))
+
+
+def drop_cells(m: Mesh, keep, patch: int) -> Mesh:
+    """The mesh without the cells where ``keep`` is False, numbered in their old order.
+    Faces between a kept and a dropped cell become boundary faces of ``patch`` (normal
+    outward from the kept cell); faces of dropped cells only are removed."""
+    keep = np.asarray(keep, bool)
+    new = np.full(m.n_cells, -1, np.int64)
+    new[keep] = np.arange(int(keep.sum()))
+    o, nb = m.face_owner.astype(np.int64), m.face_nbr.astype(np.int64)
+    ko = keep[o]
+    kn = np.where(nb >= 0, keep[np.maximum(nb, 0)], False)
+    inner = nb >= 0
+    owner = np.where(ko, o, np.maximum(nb, 0))
+    nbr = np.where(ko & kn, nb, np.where(inner, -1 - patch, nb))
+    flip = ~ko & kn
+    use = ko | kn
+    normal = np.where(flip[:, None], -m.face_normal, m.face_normal)
+    owner, nbr = new[owner[use]], nbr[use]
+    nbr = np.where(nbr >= 0, new[np.maximum(nbr, 0)], nbr)
+    return Mesh(dim=m.dim, n_cells=int(keep.sum()), face_owner=owner.astype(np.int32), face_nbr=nbr.astype(np.int32),
+                face_normal=normal[use], face_area=m.face_area[use], face_centroid=m.face_centroid[use],
+                cell_volume=m.cell_volume[keep], cell_centroid=m.cell_centroid[keep], patches=list(m.patches))
+
+
+def capsule_tetrahedra(n: int, seed: int = 2, jitter: float = 0.15, patches=None) -> Mesh:
+    """Blunt re-entry capsule in the unit cube, tetrahedral: box_tetrahedra(n) without the
+    cells whose centroids lie inside the body.  The body's axis is the line y = z = 0.5;
+    its spherical heat shield (radius 0.3, stagnation point x = 0.3) faces -x and meets
+    the base radius 0.18 at x = 0.36, followed by a conical afterbody narrowing at 33
+    degrees to a flat back at x = 0.52.  The exposed faces form patch 0 (the body), the
+    six sides of the cube patch 1 (far field); ``patches`` gives those two."""
+    box = box_tetrahedra(n, seed=seed, jitter=jitter)
+    x, y, z = box.cell_centroid.T
+    r = np.hypot(y - 0.5, z - 0.5)
+    xn, Rs, Rb = 0.3, 0.3, 0.18
+    xs = xn + Rs - np.sqrt(Rs * Rs - Rb * Rb)
+    xe = 0.52
+    shield = np.sqrt(np.maximum(Rs * Rs - (xn + Rs - x) ** 2, 0.0))
+    cone = Rb - (x - xs) * np.tan(np.radians(33.0))
+    radius = np.where(x < xs, shield, cone)
+    inside = (x >= xn) & (x <= xe) & (r <= radius)
+    box.face_nbr = np.where(box.face_nbr < 0, -2, box.face_nbr).astype(np.int32)   # cube sides: patch 1
+    if patches is None:
+        patches = [Patch(WALL, T_t=1.0), Patch(FARFIELD)]
+    box.patches = list(patches)
+    return drop_cells(box, ~inside, 0)

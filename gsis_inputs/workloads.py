@@ -123,6 +123,29 @@ def cylinder(n_theta: int = 200, n_radial: int = 100, n_v: int = 48, n_polar: in
                     ModelParams(Kn=Kn, Kn_p=Kn_p, sigma_R=sigma_R, k_eff_density_scaled=True))
 
 
+def capsule(n: int = 32, n_v: int = 24, n_polar: int = 8, n_azim: int = 16, Mach: float = 10.0,
+            T_inf: float = 0.5, T_wall: float = 0.5, Kn: float = 0.01, Kn_p: float = 1000.0,
+            sigma_R: float = 0.1, seed: int = 2) -> Workload:
+    """3-D hypersonic flow past a blunt capsule (heat shield facing the stream, conical
+    afterbody) on a seeded tetrahedral mesh of the unit cube (about 6 n^3 cells); the
+    free stream flows along +x.  The n_v^3 uniform velocity grid (trapezoid weights) spans
+    +-(u_inf + 4 sqrt(T_0)), T_0 the stagnation temperature; n_polar x n_azim photon
+    directions.  FP32, order 2, CUDA-core moments."""
+    gamma = (5.0 + 2.0 + 1.16) / (3.0 + 2.0 + 1.16)
+    u_inf = Mach * np.sqrt(gamma * T_inf)
+    T0 = T_inf * (1.0 + 0.5 * (gamma - 1.0) * Mach * Mach)
+    m = _mesh.capsule_tetrahedra(n, seed=seed, patches=[
+        _mesh.Patch(_mesh.WALL, T_t=T_wall),
+        _mesh.Patch(_mesh.FARFIELD, rho=1.0, u=(u_inf, 0.0, 0.0), T_t=T_inf, T_r=T_inf,
+                    T_v=T_inf, T_R=T_inf)])
+    L = u_inf + 4.0 * np.sqrt(T0)
+    xi, w = _q.trapezoid_nd(n_v, L, 3)
+    om, wo = _q.photon_product(n_polar, n_azim)
+    return Workload("capsule%d" % m.n_cells, m, xi, w, om, wo,
+                    ModelParams(Kn=Kn, Kn_p=Kn_p, sigma_R=sigma_R, k_eff_density_scaled=True),
+                    SolverParams(tc_moments=0))
+
+
 def rankine_hugoniot(Mach: float, gamma: float):
     """Downstream (rho, u, T) of a normal shock with upstream rho = T = 1 and
     u = sqrt(gamma) Mach (velocity unit sqrt(R T0)), from the Rankine-Hugoniot relations
