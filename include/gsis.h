@@ -79,9 +79,16 @@ typedef struct {
  * face_nbr[f] >= 0 is the neighbour cell; face_nbr[f] = -1 - p marks a boundary face
  * of patch p.  face_normal is the unit normal from owner to neighbour (outward on the
  * boundary), [n_faces][dim] row-major.  Areas are lengths in 2-D and 1 in 1-D.
- * Cells are relaxed in blocks of consecutive indices: number them with locality. */
+ * Cells are relaxed in blocks of consecutive indices: number them with locality.
+ * Cells have at most 4 faces (segments, triangles, quadrilaterals, tetrahedra); the
+ * least-squares stencil (face neighbours and their face neighbours) holds at most 12
+ * cells in 1-D and 2-D and 16 in 3-D (UNSUPPORTED beyond).
+ * 3-D meshes run the kinetic iteration (GSIS_MODE_CIS: the sweeps of Eq. dis_micro, the
+ * moments, the fields and eps) in FP32 or FP64 with tc_moments = 0; the synthetic
+ * equations (GSIS_MODE_GSIS, gsis_warm_start), the learned closure's samples and
+ * velocity shards are built for 1-D and 2-D and return UNSUPPORTED on a 3-D context. */
 typedef struct {
-    int32_t dim;                      /* 1 or 2 in this build (3: GSIS_ERR_UNSUPPORTED) */
+    int32_t dim;                      /* 1, 2 or 3                                      */
     int64_t n_cells, n_faces;
     const int32_t *face_owner;        /* [n_faces]            */
     const int32_t *face_nbr;          /* [n_faces]            */

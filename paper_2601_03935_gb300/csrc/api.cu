@@ -592,8 +592,10 @@ int check_err(gsis_ctx *c) {
 int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon_quad *pq,
              const gsis_model_params *mp, const gsis_solver_params *sp, std::string &why) {
     if (!m || !vq || !pq || !mp || !sp) return why = "null argument", GSIS_ERR_INVALID_ARG;
-    if (m->dim == 3) return why = "3-D meshes are not supported by this build", GSIS_ERR_UNSUPPORTED;
-    if (m->dim < 1 || m->dim > 2) return why = "dim must be 1 or 2", GSIS_ERR_INVALID_ARG;
+    if (m->dim < 1 || m->dim > 3) return why = "dim must be 1, 2 or 3", GSIS_ERR_INVALID_ARG;
+    if (m->dim == 3 && sp->precision == GSIS_FP32 && sp->tc_moments != 0)
+        return why = "tensor-core moments are built for 1-D and 2-D: set tc_moments = 0 on a 3-D mesh",
+               GSIS_ERR_UNSUPPORTED;
     if (m->n_cells <= 0 || m->n_faces <= 0 || m->n_cells > (1LL << 30)) return why = "bad mesh sizes", GSIS_ERR_INVALID_ARG;
     if (!m->face_owner || !m->face_nbr || !m->face_normal || !m->face_area || !m->face_centroid || !m->cell_volume ||
         !m->cell_centroid)
@@ -607,7 +609,7 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
     {   // the gas sweep keeps a block's residuals and diagonals in shared memory
         const size_t rs = sp->precision == GSIS_FP64 ? 8 : 4;
         const bool tc = rs == 4 && sp->tc_moments >= 2 && MT % sp->relax_block == 0;
-        if (sweep_smem_bytes(sp->relax_block, 4, 2, rs, tc) > 227 * 1024)
+        if (sweep_smem_bytes(sp->relax_block, 4, m->dim, rs, tc) > 227 * 1024)
             return why = "relax_block too large for the shared memory of one CTA", GSIS_ERR_INVALID_ARG;
     }
     if (!(sp->cfl_meso > 0) || !(sp->venkat_K > 0)) return why = "bad CFL or limiter constant", GSIS_ERR_INVALID_ARG;
@@ -812,8 +814,10 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     // least-squares weights C_ij = (sum_k d_k d_k^T)^-1 d_j over the stencil of face
     // neighbours and their face neighbours (interior face neighbours first); a zero
     // gradient where the normal matrix is singular (det <= 1e-10 (tr/dim)^dim)
-    std::vector<double> lsq(nc * MAXS * 2, 0.0), eps2(nc), cdx(nc), vol(nc), fgeo(nc * MAXF * fr::SIZE, 0.0);
-    std::vector<int> stn(nc * MAXS, 0), info(nc * 4, 0), fnb(nc * MAXF * 2, -1);
+    // (layouts per dimension: stencil length MS, LW weights per entry, FRS Reals per face)
+    const int MS = lay_maxs(dim), LW = lay_lw(dim), FRS = lay_frs(dim);
+    std::vector<double> lsq(nc * MS * LW, 0.0), eps2(nc), cdx(nc), vol(nc), fgeo(nc * MAXF * FRS, 0.0);
+    std::vector<int> stn(nc * MS, 0), info(nc * 4, 0), fnb(nc * MAXF * 2, -1);
     for (int64_t i = 0; i < nc; ++i) {
         vol[i] = m->cell_volume[i];
         cdx[i] = std::pow(vol[i], 1.0 / dim);
@@ -822,17 +826,29 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         std::vector<int> first, rest;
         for (int k = 0; k < nf[i]; ++k) {
             const int j = nbr[i * MAXF + k];
-            double *F = &fgeo[((size_t)i * MAXF + k) * fr::SIZE];
-            F[fr::NX] = nrm[(i * MAXF + k) * 3 + 0];
-            F[fr::NY] = dim > 1 ? nrm[(i * MAXF + k) * 3 + 1] : 0.0;
-            F[fr::SV] = sv[i * MAXF + k];
-            F[fr::DFX] = dxf[(i * MAXF + k) * 3 + 0];
-            F[fr::DFY] = dim > 1 ? dxf[(i * MAXF + k) * 3 + 1] : 0.0;
+            double *F = &fgeo[((size_t)i * MAXF + k) * FRS];
+            const double *nk = &nrm[(i * MAXF + k) * 3], *fk = &dxf[(i * MAXF + k) * 3], *gk = &dxn[(i * MAXF + k) * 3];
+            const double svn = j >= 0 ? m->face_area[face_of[i * MAXF + k]] / m->cell_volume[j] : 0.0;
+            if (dim < 3) {
+                F[fr::NX] = nk[0];
+                F[fr::NY] = dim > 1 ? nk[1] : 0.0;
+                F[fr::SV] = sv[i * MAXF + k];
+                F[fr::DFX] = fk[0];
+                F[fr::DFY] = dim > 1 ? fk[1] : 0.0;
+                F[fr::SVN] = svn;
+                F[fr::DNX] = j >= 0 ? gk[0] : 0.0;
+                F[fr::DNY] = j >= 0 && dim > 1 ? gk[1] : 0.0;
+            } else {   // n (3), S/V, S/V of the neighbour, face - cell (3), face - neighbour (3), pad
+                for (int a = 0; a < 3; ++a) {
+                    F[a] = nk[a];
+                    F[5 + a] = fk[a];
+                    F[8 + a] = j >= 0 ? gk[a] : 0.0;
+                }
+                F[3] = sv[i * MAXF + k];
+                F[4] = svn;
+            }
             fnb[(i * MAXF + k) * 2 + 0] = j;
             if (j < 0) continue;
-            F[fr::SVN] = m->face_area[face_of[i * MAXF + k]] / m->cell_volume[j];
-            F[fr::DNX] = dxn[(i * MAXF + k) * 3 + 0];
-            F[fr::DNY] = dim > 1 ? dxn[(i * MAXF + k) * 3 + 1] : 0.0;
             if (j / c->block == i / c->block) fnb[(i * MAXF + k) * 2 + 1] = (int)(j - (i / c->block) * c->block);
             if (std::find(first.begin(), first.end(), j) == first.end()) first.push_back(j);
         }
@@ -845,24 +861,28 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         rest.erase(std::unique(rest.begin(), rest.end()), rest.end());
         std::vector<int> st(first);
         st.insert(st.end(), rest.begin(), rest.end());
-        if ((int)st.size() > MAXS) return bail(fail(c, GSIS_ERR_UNSUPPORTED, "least-squares stencil larger than 12"));
+        if ((int)st.size() > MS) {
+            fprintf(stderr, "gsis: least-squares stencil of %d cells, more than %d\n", (int)st.size(), MS);
+            return bail(GSIS_ERR_UNSUPPORTED);
+        }
         info[i * 4 + 0] = nf[i];
         info[i * 4 + 1] = (int)st.size();
         info[i * 4 + 2] = (int)first.size();
-        for (size_t k = 0; k < st.size(); ++k) stn[i * MAXS + k] = st[k];
+        for (size_t k = 0; k < st.size(); ++k) stn[i * MS + k] = st[k];
         if ((int)st.size() < dim) continue;
-        double G[2][2] = {{0, 0}, {0, 0}};
+        double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         for (int j : st) {
-            double d[2] = {0, 0};
+            double d[3] = {0, 0, 0};
             for (int a = 0; a < dim; ++a) d[a] = m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a];
             for (int a = 0; a < dim; ++a)
                 for (int b = 0; b < dim; ++b) G[a][b] += d[a] * d[b];
         }
-        double Gi[2][2] = {{0, 0}, {0, 0}};
+        // inverse of the normal matrix; singular when det <= 1e-10 (trace / dim)^dim
+        double Gi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         if (dim == 1) {
             if (!(G[0][0] > 0.0)) continue;
             Gi[0][0] = 1.0 / G[0][0];
-        } else {
+        } else if (dim == 2) {
             const double det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
             const double sc = 0.5 * (G[0][0] + G[1][1]);
             if (!(det > 1e-10 * sc * sc)) continue;
@@ -870,15 +890,31 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             Gi[1][1] = G[0][0] / det;
             Gi[0][1] = -G[0][1] / det;
             Gi[1][0] = -G[1][0] / det;
+        } else {
+            // adjugate / determinant
+            const double c00 = G[1][1] * G[2][2] - G[1][2] * G[2][1], c01 = G[1][2] * G[2][0] - G[1][0] * G[2][2],
+                         c02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
+            const double det = G[0][0] * c00 + G[0][1] * c01 + G[0][2] * c02;
+            const double sc = (G[0][0] + G[1][1] + G[2][2]) / 3.0;
+            if (!(det > 1e-10 * sc * sc * sc)) continue;
+            Gi[0][0] = c00 / det;
+            Gi[1][0] = c01 / det;
+            Gi[2][0] = c02 / det;
+            Gi[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) / det;
+            Gi[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) / det;
+            Gi[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) / det;
+            Gi[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) / det;
+            Gi[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) / det;
+            Gi[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) / det;
         }
         for (size_t k = 0; k < st.size(); ++k) {
             const int j = st[k];
-            double d[2] = {0, 0};
+            double d[3] = {0, 0, 0};
             for (int a = 0; a < dim; ++a) d[a] = m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a];
             for (int a = 0; a < dim; ++a) {
                 double s = 0.0;
                 for (int b = 0; b < dim; ++b) s += Gi[a][b] * d[b];
-                lsq[(i * MAXS + k) * 2 + a] = s;
+                lsq[(i * MS + k) * LW + a] = s;
             }
         }
     }
@@ -932,7 +968,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             id_of[f] = (int)fi_i.size();
             fi_i.push_back(o);
             fi_j.push_back(nb);
-            double d[2] = {0, 0}, dn = 0.0, dd = 0.0;
+            double d[3] = {0, 0, 0}, dn = 0.0, dd = 0.0;
             for (int a = 0; a < dim; ++a) {
                 d[a] = m->cell_centroid[nb * dim + a] - m->cell_centroid[o * dim + a];
                 dn += m->face_normal[f * dim + a] * d[a];
@@ -949,7 +985,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             fi_dist.push_back(dd);
         }
         for (int64_t i = 0; i < nc; ++i) {
-            for (int a = 0; a < dim; ++a) mxc[i * 2 + a] = m->cell_centroid[i * dim + a];
+            for (int a = 0; a < std::min(dim, 2); ++a) mxc[i * 2 + a] = m->cell_centroid[i * dim + a];
             for (int k = 0; k < MAXF; ++k) {
                 if (k >= nf[i]) { cface[i * MAXF + k] = -1 - std::max(c->n_bf, 1); continue; }
                 const int j = nbr[i * MAXF + k];
@@ -968,7 +1004,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
                 const int64_t f = face_of[i * MAXF + k];
                 double dn = 0.0;
                 for (int a = 0; a < dim; ++a) {
-                    mbn[b * 2 + a] = m->face_normal[f * dim + a];
+                    if (a < 2) mbn[b * 2 + a] = m->face_normal[f * dim + a];
                     dn += m->face_normal[f * dim + a] * (m->face_centroid[f * dim + a] - m->cell_centroid[i * dim + a]);
                 }
                 mbS[b] = m->face_area[f];
@@ -998,7 +1034,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc_real(c, &c->I[1], isz));
     A_(dalloc_real(c, &c->coef, (size_t)nc * cf::NC));
     A_(dalloc_real(c, &c->bcoef, bco.size()));
-    A_(dalloc_real(c, &c->partial, (size_t)nc * c->nch * NMP));
+    A_(dalloc_real(c, &c->partial, (size_t)nc * c->nch * lay_nmp(dim)));
     A_(dalloc_real(c, &c->opartial, (size_t)nc * c->och * NMO));
     if (c->precision == GSIS_FP32) A_(dalloc_real(c, &c->sync_kc, (size_t)nc * SYNC_KC));
     if (c->order == 2) {
@@ -1016,9 +1052,9 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     A_(dalloc(c, &c->g_fnb, nc * MAXF));
     A_(dalloc(c, &c->bf_cell, std::max(c->n_bf, 1)));
     A_(dalloc(c, &c->bf_patch, std::max(c->n_bf, 1)));
-    A_(dalloc_real(c, &c->g_fgeo, nc * MAXF * fr::SIZE));
-    A_(dalloc_real(c, &c->g_lsq, nc * MAXS * 2));
-    A_(dalloc(c, &c->g_stn, nc * MAXS));
+    A_(dalloc_real(c, &c->g_fgeo, fgeo.size()));
+    A_(dalloc_real(c, &c->g_lsq, lsq.size()));
+    A_(dalloc(c, &c->g_stn, stn.size()));
     A_(dalloc_real(c, &c->g_eps2, nc));
     A_(dalloc_real(c, &c->bf_nrm, 3 * std::max(c->n_bf, 1)));
     A_(dalloc_real(c, &c->vq_x, vx.size()));
@@ -1045,7 +1081,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         A_(dalloc(c, &c->m_fi_dist, nfi1));
         A_(dalloc(c, &c->m_fi_t, nfi1 * 2));
         A_(dalloc(c, &c->m_fi_xf, nfi1 * 2));
-        A_(dalloc(c, &c->m_lsq, (size_t)nc * MAXS * 2));
+        A_(dalloc(c, &c->m_lsq, lsq.size()));
         A_(dalloc(c, &c->m_eps2, (size_t)nc));
         A_(dalloc(c, &c->m_xc, (size_t)nc * 2));
         A_(dalloc(c, &c->m_bf_n, nbf1 * 2));
@@ -1209,7 +1245,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         hw[0] = P.kind == GSIS_PATCH_WALL ? 1.0 : 0.0;
         for (int a = 0; a < 3; ++a) {
             hw[1 + a] = bfn[b * 3 + a];
-            hw[5 + a] = a < 2 ? P.u[a] : 0.0;
+            hw[5 + a] = P.u[a];
         }
         hw[4] = P.T_t;
     }
@@ -1610,6 +1646,7 @@ int gsis_shard_setup(gsis_ctx *c, int32_t n_xi_all, const double *xi_all, const 
     if (c->sharded) return fail(c, GSIS_ERR_INVALID_ARG, "the context is already a shard");
     if (c->mirrors)
         return fail(c, GSIS_ERR_UNSUPPORTED, "mirror planes pair velocities across shards; shard a mesh without them");
+    if (c->dim == 3) return fail(c, GSIS_ERR_UNSUPPORTED, "velocity shards are built for 1-D and 2-D meshes");
     if (n_xi_all < c->V || n_omega_all < c->NO) return fail(c, GSIS_ERR_INVALID_ARG, "the full sets are smaller than the shard");
     const int dim = c->dim;
     // the incoming unit-density wall flux over every velocity of every shard
@@ -1751,8 +1788,11 @@ int gsis_download_fields_async(gsis_ctx *c, double *out, int64_t len) {
 int gsis_step_async(gsis_ctx *c, int32_t mode) {
     if (!c) return GSIS_ERR_INVALID_ARG;
     if (c->sharded) return fail(c, GSIS_ERR_UNSUPPORTED, "a velocity shard steps through gsis_shard_begin/mid/end");
-    if (mode == GSIS_MODE_GSIS)
+    if (mode == GSIS_MODE_GSIS) {
+        if (c->dim == 3)
+            return fail(c, GSIS_ERR_UNSUPPORTED, "the synthetic equations are built for 1-D and 2-D meshes");
         return c->precision == GSIS_FP64 ? gsis_iteration<double>(c) : gsis_iteration<float>(c);
+    }
     if (mode != GSIS_MODE_CIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
     return c->precision == GSIS_FP64 ? cis_iteration<double>(c) : cis_iteration<float>(c);
 }
@@ -1771,6 +1811,8 @@ int gsis_step(gsis_ctx *c, int32_t mode, double *eps_out) {
 int gsis_solve(gsis_ctx *c, int32_t mode, int32_t max_outer, double tol, int32_t *iters_out, double *eps_history) {
     if (!c) return GSIS_ERR_INVALID_ARG;
     if (mode != GSIS_MODE_CIS && mode != GSIS_MODE_GSIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
+    if (mode == GSIS_MODE_GSIS && c->dim == 3)
+        return fail(c, GSIS_ERR_UNSUPPORTED, "the synthetic equations are built for 1-D and 2-D meshes");
     const int n = max_outer > 0 ? max_outer : c->solver.max_outer;
     const double t = tol > 0 ? tol : c->solver.tol_outer;
     if (iters_out) *iters_out = 0;
@@ -2008,6 +2050,7 @@ int gsis_mlp_train(gsis_ctx *c, const float *X, const float *Y, int64_t n, int32
 
 int gsis_mlp_samples(gsis_ctx *c, float *X, float *Y, int64_t n_cells) {
     if (!c || !X || n_cells < c->nc) return fail(c, GSIS_ERR_INVALID_ARG, "sample buffers too short");
+    if (c->dim == 3) return fail(c, GSIS_ERR_UNSUPPORTED, "the learned closure's features are built for 1-D and 2-D");
     TRY(mlp_ensure(c, 1));
     TRY(launch(c, K_MCONV, [&] {
         return launch_macro_from_fields(c->stream, c->dim, (int)c->nc, c->model, c->fields, c->W[0]);
@@ -2082,6 +2125,7 @@ extern "C" {
 int gsis_warm_start(gsis_ctx *c, int32_t n_presolve, int32_t use_mlp) {
     if (!c || n_presolve < 0) return GSIS_ERR_INVALID_ARG;
     if (c->sharded) return fail(c, GSIS_ERR_UNSUPPORTED, "the warm start runs on unsharded contexts");
+    if (c->dim == 3) return fail(c, GSIS_ERR_UNSUPPORTED, "the synthetic equations are built for 1-D and 2-D meshes");
     if (use_mlp && (!c->mlp.p || !c->mlp.trained))
         return fail(c, GSIS_ERR_INVALID_ARG, "the learned closure has not been trained or set");
     return c->precision == GSIS_FP64 ? warm_start<double>(c, n_presolve, use_mlp != 0)

@@ -53,12 +53,29 @@ constexpr int IIN = 9;         // incoming photon intensity
 constexpr int NB = 12;
 }  // namespace bc
 
-// Per cell-face record (Real x 8): outward normal (x, y), S/V of this cell, S/V of the
-// neighbour (0 on the boundary), face centroid - cell centroid (x, y), face centroid -
-// neighbour centroid (x, y).  Up to two spatial dimensions.
+// Per cell-face record (Real x 8 in 1-D and 2-D): outward normal (x, y), S/V of this cell,
+// S/V of the neighbour (0 on the boundary), face centroid - cell centroid (x, y), face
+// centroid - neighbour centroid (x, y).  In 3-D (Real x 12): normal (x, y, z), S/V, then
+// S/V of the neighbour, face - cell (x, y, z), then face - neighbour (x, y, z), a pad.
 namespace fr {
 constexpr int NX = 0, NY = 1, SV = 2, SVN = 3, DFX = 4, DFY = 5, DNX = 6, DNY = 7, SIZE = 8;
+constexpr int SIZE3 = 12;
 }
+
+// Layout sizes that depend on the spatial dimension; the 1-D and 2-D values are the
+// ones the constants above name.  Tetrahedra have up to 14 cells in their face
+// neighbours' face neighbourhood and 3-D gas moments need 21 partial sums.
+template <int DIM>
+struct Lay {
+    static constexpr int MAXS = DIM < 3 ? 12 : 16;   // least-squares stencil entries
+    static constexpr int LW = DIM < 3 ? 2 : 3;       // least-squares weights per entry
+    static constexpr int FRS = DIM < 3 ? fr::SIZE : fr::SIZE3;
+    static constexpr int NMP = DIM < 3 ? 20 : 24;    // stride of per-(cell, chunk) gas moment partials
+};
+inline int lay_maxs(int dim) { return dim < 3 ? 12 : 16; }
+inline int lay_lw(int dim) { return dim < 3 ? 2 : 3; }
+inline int lay_frs(int dim) { return dim < 3 ? fr::SIZE : fr::SIZE3; }
+inline int lay_nmp(int dim) { return dim < 3 ? 20 : 24; }
 
 template <typename Real>
 struct Geom {
@@ -67,9 +84,9 @@ struct Geom {
     const int4 *info;          // [nc]: faces, stencil size, face neighbours leading the stencil, -
     const int2 *fnb;           // [nc][MAXF]: neighbour (>= 0 cell, < 0: -1 - boundary face), in-block index or -1
     const int *cface;          // [nc][MAXF]: interior face id (>= 0) or -1 - boundary face
-    const Real *fgeo;          // [nc][MAXF][fr::SIZE]
-    const int *stn;            // [nc][MAXS] stencil cells, interior face neighbours first
-    const Real *lsq;           // [nc][MAXS][2] least-squares weights of the stencil cells
+    const Real *fgeo;          // [nc][MAXF][Lay::FRS]
+    const int *stn;            // [nc][Lay::MAXS] stencil cells, interior face neighbours first
+    const Real *lsq;           // [nc][Lay::MAXS][Lay::LW] least-squares weights of the stencil cells
     const Real *eps2;          // [nc] (K dx)^3
     int n_bf;
     const int *bf_cell;        // [n_bf]

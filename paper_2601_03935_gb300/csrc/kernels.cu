@@ -334,22 +334,39 @@ __device__ __forceinline__ V<Real, N> vsplat(Real c) {
 
 template <typename Real>
 struct Face {
-    Real n[2], sv, svn, df[2], dn[2];
+    Real n[3], sv, svn, df[3], dn[3];
 };
 
-template <typename Real>
+// The record of face k of cell c (layouts in gsis_impl.cuh: 8 Reals in 1-D/2-D, 12 in 3-D).
+template <typename Real, int DIM = 2>
 __device__ __forceinline__ Face<Real> load_face(const Real *__restrict__ fgeo, int c, int k) {
-    const Real *p = fgeo + ((size_t)c * MAXF + k) * fr::SIZE;
+    const Real *p = fgeo + ((size_t)c * MAXF + k) * Lay<DIM>::FRS;
     const Vec<Real, 4> a = vload<Real, 4>(p), b = vload<Real, 4>(p + 4);
     Face<Real> F;
-    F.n[0] = a.v[0];
-    F.n[1] = a.v[1];
-    F.sv = a.v[2];
-    F.svn = a.v[3];
-    F.df[0] = b.v[0];
-    F.df[1] = b.v[1];
-    F.dn[0] = b.v[2];
-    F.dn[1] = b.v[3];
+    if constexpr (DIM < 3) {
+        F.n[0] = a.v[0];
+        F.n[1] = a.v[1];
+        F.sv = a.v[2];
+        F.svn = a.v[3];
+        F.df[0] = b.v[0];
+        F.df[1] = b.v[1];
+        F.dn[0] = b.v[2];
+        F.dn[1] = b.v[3];
+        F.n[2] = F.df[2] = F.dn[2] = Real(0);
+    } else {
+        const Vec<Real, 4> c3 = vload<Real, 4>(p + 8);
+        F.n[0] = a.v[0];
+        F.n[1] = a.v[1];
+        F.n[2] = a.v[2];
+        F.sv = a.v[3];
+        F.svn = b.v[0];
+        F.df[0] = b.v[1];
+        F.df[1] = b.v[2];
+        F.df[2] = b.v[3];
+        F.dn[0] = c3.v[0];
+        F.dn[1] = c3.v[1];
+        F.dn[2] = c3.v[2];
+    }
     return F;
 }
 
@@ -374,16 +391,17 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
         }
     const int4 info = g.info[j];
     const int ns = info.y, nfn = info.z;
-    const int *stn = g.stn + (size_t)j * MAXS;
-    const Real *lw = g.lsq + (size_t)j * MAXS * 2;
+    constexpr int MS = Lay<DIM>::MAXS, LW = Lay<DIM>::LW;
+    const int *stn = g.stn + (size_t)j * MS;
+    const Real *lw = g.lsq + (size_t)j * MS * LW;
 #pragma unroll
-    for (int k = 0; k < MAXS; ++k) {
+    for (int k = 0; k < MS; ++k) {
         if (k >= ns) break;
         const size_t row = (size_t)stn[k] * stride + v;
         V<Real, N> fs[VPT];
 #pragma unroll
         for (int u = 0; u < VPT; ++u) fs[u] = ldv<Real, N>(f, row + 32 * u);
-        const Real c0 = lw[2 * k], c1 = DIM > 1 ? lw[2 * k + 1] : Real(0);
+        const Real c0 = lw[LW * k], c1 = DIM > 1 ? lw[LW * k + 1] : Real(0), c2 = DIM > 2 ? lw[LW * k + 2] : Real(0);
         const bool face_nbr = k < nfn;
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
@@ -397,6 +415,7 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
             }
             vfma(c0, dq, slope[u][0]);
             if constexpr (DIM > 1) vfma(c1, dq, slope[u][1]);
+            if constexpr (DIM > 2) vfma(c2, dq, slope[u][2]);
         }
     }
     // phi = min(1, min over interior faces of phi_V(Delta_1, Delta_2)).  On the faces with
@@ -416,12 +435,23 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
     const int nf = info.x;
     for (int k = 0; k < nf; ++k) {
         if (g.fnb[j * MAXF + k].x < 0) continue;
-        const Real *q = g.fgeo + ((size_t)j * MAXF + k) * fr::SIZE + fr::DFX;
-        const Real dx0 = q[0], dx1 = DIM > 1 ? q[1] : Real(0);
+        Real dx0, dx1, dx2;
+        if constexpr (DIM < 3) {
+            const Real *q = g.fgeo + ((size_t)j * MAXF + k) * fr::SIZE + fr::DFX;
+            dx0 = q[0];
+            dx1 = DIM > 1 ? q[1] : Real(0);
+            dx2 = Real(0);
+        } else {
+            const Face<Real> Fk = load_face<Real, DIM>(g.fgeo, j, k);
+            dx0 = Fk.df[0];
+            dx1 = Fk.df[1];
+            dx2 = Fk.df[2];
+        }
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             V<Real, N> d2 = vmul(slope[u][0], vsplat<Real, N>(dx0));
             if constexpr (DIM > 1) vfma(dx1, slope[u][1], d2);
+            if constexpr (DIM > 2) vfma(dx2, slope[u][2], d2);
 #pragma unroll
             for (int p = 0; p < N; ++p) {
                 hi[u].x[p] = fmax(hi[u].x[p], d2.x[p]);
@@ -518,7 +548,7 @@ constexpr int n_gas_moments() {
 
 // Accumulate the moments of one (cell, velocity) value into acc (shifted basis c = xi - u).
 template <typename Real, int DIM>
-__device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Real w, const Real (&fv)[4]) {
+__device__ __forceinline__ void add_moments(Real (&acc)[Lay<DIM>::NMP], const Real *c, Real w, const Real (&fv)[4]) {
     Real c2 = Real(0);
 #pragma unroll
     for (int a = 0; a < DIM; ++a) c2 = fma(c[a], c[a], c2);
@@ -552,12 +582,14 @@ __device__ __forceinline__ void add_moments(Real (&acc)[NMP], const Real *c, Rea
 // face's value, and none where xi . n = 0, which the sweep skips.  The sweep reads these
 // values for both its outflow and its inflow interior faces.
 constexpr int SLOPE_ROWS = 8;
-constexpr int SLOPE_VPT = 2;                      // velocities per thread (32 SLOPE_VPT per row)
-constexpr int SLOPE_MINB = SLOPE_VPT == 1 ? 6 : 4; // FP32 CTAs per SM the registers allow
+// velocities per thread (32 slope_vpt per row) and FP32 CTAs per SM the registers allow:
+// a 3-D slope of four planes takes 12 registers per velocity
+__host__ __device__ constexpr int slope_vpt(int dim) { return dim < 3 ? 2 : 1; }
+__host__ __device__ constexpr int slope_minb(int dim) { return dim < 3 ? 4 : 3; }
 template <typename Real, int N, int DIM>
-__global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? SLOPE_MINB : 1) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ xq,
+__global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? slope_minb(DIM) : 1) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ xq,
                                                             const Real *__restrict__ f, Real *__restrict__ fface) {
-    constexpr int VPT = SLOPE_VPT;
+    constexpr int VPT = slope_vpt(DIM);
     const int v = blockIdx.y * (32 * VPT) + threadIdx.x;
     const int j = blockIdx.x * SLOPE_ROWS + threadIdx.y;
     if (j >= g.n_cells) return;
@@ -576,15 +608,17 @@ __global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? SLOPE_MIN
     for (int k = 0; k < nf; ++k) {
         const int fid = g.cface[j * MAXF + k];
         if (fid < 0) continue;
-        const Face<Real> F = load_face(g.fgeo, j, k);
+        const Face<Real> F = load_face<Real, DIM>(g.fgeo, j, k);
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
             Real xn = xi[u][0] * F.n[0];
             if constexpr (DIM > 1) xn = fma(xi[u][1], F.n[1], xn);
+            if constexpr (DIM > 2) xn = fma(xi[u][2], F.n[2], xn);
             if (!(xn > Real(0))) continue;
             V<Real, N> fv = fj[u];
             vfma(F.df[0], sl[u][0], fv);
             if constexpr (DIM > 1) vfma(F.df[1], sl[u][1], fv);
+            if constexpr (DIM > 2) vfma(F.df[2], sl[u][2], fv);
             const size_t o = (size_t)fid * n_pad + v + 32 * u;
             if constexpr (N == 1) {
                 fface[o] = fv.x[0];
@@ -606,9 +640,10 @@ __global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? SLOPE_MIN
 // operand stage, which reuses it after the relaxation), then the chunk's velocities and
 // weights, the in-block neighbour table and the tensor-core control words.
 // `tc`: an FP32 gas sweep with Geom::tc set.
-__host__ __device__ constexpr size_t sweep_face_bytes(int block, size_t real_size) {
-    return (size_t)block * MAXF * 4 * real_size + ((size_t)block * MAXF * 2 * real_size + 31) / 32 * 32 +
-           (size_t)block * cf::NC * real_size;
+__host__ __device__ constexpr int sweep_nf_stride(int dim) { return dim < 3 ? 2 : 3; }
+__host__ __device__ constexpr size_t sweep_face_bytes(int block, int dim, size_t real_size) {
+    return (size_t)block * MAXF * 4 * real_size +
+           ((size_t)block * MAXF * sweep_nf_stride(dim) * real_size + 31) / 32 * 32 + (size_t)block * cf::NC * real_size;
 }
 
 // A face's upwind source (int) carried in the last slot of its Real face record, bit for bit.
@@ -617,11 +652,11 @@ __device__ __forceinline__ double int_bits_as(int x, double) { return __longlong
 __device__ __forceinline__ int bits_as_int(float x) { return __float_as_int(x); }
 __device__ __forceinline__ int bits_as_int(double x) { return (int)__double_as_longlong(x); }
 constexpr int NO_FACE = -2147483647 - 1;
-__host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, size_t real_size, bool tc) {
-    return (tc && (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, real_size) <
+__host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, int dim, size_t real_size, bool tc) {
+    return (tc && (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, dim, real_size) <
                       (size_t)tcm::STAGE_BYTES)
                ? (size_t)tcm::STAGE_BYTES
-               : (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, real_size);
+               : (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, dim, real_size);
 }
 
 // One CTA = one relaxation block of consecutive cells x SV discrete velocities (N = 4 gas
@@ -637,7 +672,7 @@ __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, siz
 //  3. f^{k+1/2} = f^k + delta, staged in shared memory;
 //  4. velocity moments per (cell, chunk), eight lanes per cell.
 template <typename Real, int N, int DIM, int ORDER>
-__global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
+__global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 : 6) : 1) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
                                                       const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
                                                       const Real *__restrict__ fface, Real *__restrict__ f_out,
                                                       Real *__restrict__ partial) {
@@ -645,13 +680,17 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
     extern __shared__ unsigned char smem_raw[];
     Vec<Real, N> *R = reinterpret_cast<Vec<Real, N> *>(smem_raw);       // [block][SV]
     Real *Dg = reinterpret_cast<Real *>(R + g.block * SV);              // [block][SV] 1 / diagonal
-    Vec<Real, 4> *Fa = reinterpret_cast<Vec<Real, 4> *>(Dg + g.block * SV);   // [block][MAXF] n, S/V, source
-    Real *Nf = reinterpret_cast<Real *>(Fa + g.block * MAXF);           // [block][MAXF][2] S/V n, in-block faces
+    // [block][MAXF] face records: (n_x, n_y, S/V, source) in 1-D and 2-D, (S/V n, source) in 3-D
+    Vec<Real, 4> *Fa = reinterpret_cast<Vec<Real, 4> *>(Dg + g.block * SV);
+    constexpr int NFS = sweep_nf_stride(DIM);
+    Real *Nf = reinterpret_cast<Real *>(Fa + g.block * MAXF);           // [block][MAXF][NFS] S/V n, in-block faces
     Real *sC = reinterpret_cast<Real *>(reinterpret_cast<unsigned char *>(Nf) +
-                                        ((size_t)g.block * MAXF * 2 * sizeof(Real) + 31) / 32 * 32);   // [block][NC]
-    constexpr bool TCM = std::is_same<Real, float>::value && N == 4;
+                                        ((size_t)g.block * MAXF * NFS * sizeof(Real) + 31) / 32 * 32);   // [block][NC]
+    // the tensor-core epilogue's basis covers the 1-D and 2-D moments
+    constexpr bool TCM = std::is_same<Real, float>::value && N == 4 && DIM < 3;
+    constexpr int NMPD = Lay<DIM>::NMP;
     const bool tc = TCM && g.tc;
-    Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, sizeof(Real), tc));   // [DIM+1][SV]
+    Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, DIM, sizeof(Real), tc));   // [DIM+1][SV]
     signed char *Lg = reinterpret_cast<signed char *>(sxi + (DIM + 1) * SV);   // [block][MAXF] in-block neighbour or -1
     tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(Lg + ((g.block * MAXF + 15) & ~15));
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -682,17 +721,23 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
         Vec<Real, 4> fa;
         int lj = -1;
         if (k < g.info[i].x) {
-            const Face<Real> F = load_face(g.fgeo, i, k);
+            const Face<Real> F = load_face<Real, DIM>(g.fgeo, i, k);
             const int2 nb2 = g.fnb[i * MAXF + k];
             const int src = ORDER == 2 ? g.cface[i * MAXF + k] : nb2.x;
-            fa.v[0] = F.n[0];
-            fa.v[1] = DIM > 1 ? F.n[1] : Real(0);
-            fa.v[2] = F.sv;
+            if constexpr (DIM < 3) {
+                fa.v[0] = F.n[0];
+                fa.v[1] = DIM > 1 ? F.n[1] : Real(0);
+                fa.v[2] = F.sv;
+            } else {
+                fa.v[0] = F.sv * F.n[0];
+                fa.v[1] = F.sv * F.n[1];
+                fa.v[2] = F.sv * F.n[2];
+            }
             fa.v[3] = int_bits_as(src, Real(0));
             lj = nb2.y;
             if (lj >= 0) {
-                Nf[t * 2] = F.sv * F.n[0];
-                Nf[t * 2 + 1] = DIM > 1 ? F.sv * F.n[1] : Real(0);
+#pragma unroll
+                for (int a = 0; a < NFS; ++a) Nf[t * NFS + a] = a < DIM ? F.sv * F.n[a] : Real(0);
             }
         } else {
             fa.v[0] = fa.v[1] = fa.v[2] = Real(0);
@@ -758,10 +803,15 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
             const Vec<Real, 4> fa = Fa[l * MAXF + k];
             const int src = bits_as_int(fa.v[3]);
             if (src == NO_FACE) continue;
+            // xn: xi . n (1-D, 2-D) or S/V xi . n (3-D); a: S/V xi . n
             Real xn = xi[0] * fa.v[0];
             if constexpr (DIM > 1) xn = fma(xi[1], fa.v[1], xn);
+            if constexpr (DIM > 2) xn = fma(xi[2], fa.v[2], xn);
             if (xn == Real(0)) continue;
-            if (xn > Real(0)) d = fma(fa.v[2], xn, d);
+            if (xn > Real(0)) {
+                if constexpr (DIM < 3) d = fma(fa.v[2], xn, d);
+                else d += xn;
+            }
             V<Real, N> fv;
             if (src >= 0 && (ORDER == 2 || xn < Real(0))) {
                 fv = fk[k];
@@ -790,7 +840,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
                     fv.x[3] = E * B[bc::M2];
                 }
             }
-            vfma(-fa.v[2] * xn, fv, r);
+            vfma(DIM < 3 ? -fa.v[2] * xn : -xn, fv, r);
         }
         Vec<Real, N> t;
 #pragma unroll
@@ -811,8 +861,9 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
             for (int k = 0; k < MAXF; ++k) {
                 const int lj = Lg[l * MAXF + k];
                 if (lj < 0 || lj >= l) continue;
-                Real a = Nf[(l * MAXF + k) * 2] * xi[0];
-                if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * 2 + 1], xi[1], a);
+                Real a = Nf[(l * MAXF + k) * NFS] * xi[0];
+                if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * NFS + 1], xi[1], a);
+                if constexpr (DIM > 2) a = fma(Nf[(l * MAXF + k) * NFS + 2], xi[2], a);
                 if (!(a < Real(0))) continue;
                 const Vec<Real, N> dj = R[lj * SV + tx];
 #pragma unroll
@@ -831,8 +882,9 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
             for (int k = 0; k < MAXF; ++k) {
                 const int lj = Lg[l * MAXF + k];
                 if (lj <= l) continue;
-                Real a = Nf[(l * MAXF + k) * 2] * xi[0];
-                if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * 2 + 1], xi[1], a);
+                Real a = Nf[(l * MAXF + k) * NFS] * xi[0];
+                if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * NFS + 1], xi[1], a);
+                if constexpr (DIM > 2) a = fma(Nf[(l * MAXF + k) * NFS + 2], xi[2], a);
                 if (!(a < Real(0))) continue;
                 const Vec<Real, N> dj = R[lj * SV + tx];
 #pragma unroll
@@ -894,7 +946,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
                 const int l = (tid & 15) - lt0;
                 if (l >= 0 && l < nb)
                     tcm::store_row<DIM>(reinterpret_cast<float *>(partial) +
-                                            ((size_t)(c0 + l) * gridDim.y + chunk) * NMP,
+                                            ((size_t)(c0 + l) * gridDim.y + chunk) * NMPD,
                                         tid >> 5, m);
             }
             if (!ok && tid == 0) atomicOr(g.err, ERR_TIMEOUT_BIT);
@@ -945,9 +997,9 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
         } else {
             constexpr int NM = n_gas_moments<DIM>();
             const Vec<Real, 4> u4 = vload<Real, 4>(coef + (size_t)((c0 + l) / MT * MT) * cf::NC + cf::U);
-            Real acc[NMP];
+            Real acc[NMPD];
 #pragma unroll
-            for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
+            for (int m = 0; m < NMPD; ++m) acc[m] = Real(0);
             for (int vl = sub; vl < SV; vl += TPC) {
                 const Vec<Real, N> fv4 = R[l * SV + vl];
                 Real fv[4] = {fv4.v[0], fv4.v[1], fv4.v[2], fv4.v[3]};
@@ -961,7 +1013,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? 8 : 1) k_sweep
 #pragma unroll
                 for (int o = 1; o < TPC; o <<= 1) acc[m] += __shfl_xor_sync(gmask, acc[m], o);
             if (sub == 0) {
-                Real *P = partial + ((size_t)(c0 + l) * gridDim.y + chunk) * NMP;
+                Real *P = partial + ((size_t)(c0 + l) * gridDim.y + chunk) * NMPD;
 #pragma unroll
                 for (int m = 0; m < NM; ++m) P[m] = acc[m];
             }
@@ -980,9 +1032,10 @@ __global__ void __launch_bounds__(VCH) k_moments_gas(int n_cells, Quad<Real> vq,
     if (i >= n_cells) return;
     constexpr int NM = n_gas_moments<DIM>();
     const Real *C = coef + (size_t)(i / MT * MT) * cf::NC;   // the tile's shift velocity
-    Real acc[NMP];
+    constexpr int NMPD = Lay<DIM>::NMP;
+    Real acc[NMPD];
 #pragma unroll
-    for (int m = 0; m < NMP; ++m) acc[m] = Real(0);
+    for (int m = 0; m < NMPD; ++m) acc[m] = Real(0);
     for (int vl = lane; vl < VCH; vl += 32) {
         const int v = chunk * VCH + vl;
         const Vec<Real, 4> fv4 = vload<Real, 4>(f + ((size_t)i * vq.n_pad + v) * 4);
@@ -997,7 +1050,7 @@ __global__ void __launch_bounds__(VCH) k_moments_gas(int n_cells, Quad<Real> vq,
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
     if (lane == 0) {
-        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMP;
+        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMPD;
 #pragma unroll
         for (int m = 0; m < NM; ++m) P[m] = acc[m];
     }
@@ -1470,13 +1523,18 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
     constexpr int MH = 3 - DIM;
     double S[NM];
     double Ph[1 + DIM];
-    static_assert(NMP % 4 == 0 && NM <= NMP && NMO == 4 && DIM + 1 <= NMO, "partial records are read as 4-vectors");
+    constexpr int NMPD = Lay<DIM>::NMP;   // partial stride
+    static_assert(NMPD % 4 == 0 && NM <= NMPD && NMO == 4 && DIM + 1 <= NMO, "partial records are read as 4-vectors");
     if (X) {
         // per-cell sums of a velocity-sharded context, already summed over the ranks
+        // (velocity shards are built for 1-D and 2-D)
+        if constexpr (DIM < 3) {
+            static_assert(DIM >= 3 || NM <= NMP, "exchange record");
 #pragma unroll
-        for (int k = 0; k < NM; ++k) S[k] = X[(size_t)i * NXC + k];
+            for (int k = 0; k < NM; ++k) S[k] = X[(size_t)i * NXC + k];
 #pragma unroll
-        for (int k = 0; k <= DIM; ++k) Ph[k] = X[(size_t)i * NXC + NMP + k];
+            for (int k = 0; k <= DIM; ++k) Ph[k] = X[(size_t)i * NXC + NMP + k];
+        }
     } else if constexpr (std::is_same<Real, float>::value) {
         // FP32 partials: a compensated FP32 sum (Knuth's two-sum, the rounding error of
         // every addition carried in lo), as accurate as an FP64 sum of these few terms
@@ -1486,9 +1544,9 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
         for (int k = 0; k < NM; ++k) hi[k] = lo[k] = 0.0f;
 #pragma unroll 2
         for (int c = 0; c < n_chunks; ++c) {
-            const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
+            const Real *P = partial + ((size_t)i * n_chunks + c) * NMPD;
 #pragma unroll
-            for (int q = 0; q < NMP / 4; ++q) {
+            for (int q = 0; q < NMPD / 4; ++q) {
                 const Vec<Real, 4> p4 = vload<Real, 4>(P + 4 * q);
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -1507,9 +1565,9 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
         for (int k = 0; k < NM; ++k) S[k] = 0.0;
 #pragma unroll 2
         for (int c = 0; c < n_chunks; ++c) {
-            const Real *P = partial + ((size_t)i * n_chunks + c) * NMP;
+            const Real *P = partial + ((size_t)i * n_chunks + c) * NMPD;
 #pragma unroll
-            for (int q = 0; q < NMP / 4; ++q) {
+            for (int q = 0; q < NMPD / 4; ++q) {
                 const Vec<Real, 4> p4 = vload<Real, 4>(P + 4 * q);
 #pragma unroll
                 for (int e = 0; e < 4; ++e)
@@ -1714,12 +1772,21 @@ __global__ void k_equilibrium(int n_cells, Quad<Real> vq, Quad<Real> oq, ModelDe
         case 2: { constexpr int DIM = 2; __VA_ARGS__; } break; \
         default: return cudaErrorInvalidValue;         \
     }
+// the kinetic path (coefficients, wall density, slopes, sweeps, moments, finish,
+// equilibrium) also runs on 3-D meshes
+#define GSIS_DISPATCH_DIM3(dim, ...)                   \
+    switch (dim) {                                     \
+        case 1: { constexpr int DIM = 1; __VA_ARGS__; } break; \
+        case 2: { constexpr int DIM = 2; __VA_ARGS__; } break; \
+        case 3: { constexpr int DIM = 3; __VA_ARGS__; } break; \
+        default: return cudaErrorInvalidValue;         \
+    }
 
 template <typename Real>
 cudaError_t launch_coefficients(cudaStream_t s, int dim, const Geom<Real> &g, const ModelDev &m, const double *fields,
                                 const double *cell_dx, Real *coef) {
     const int nt = 32, nbk = (g.n_cells + nt - 1) / nt;   // small CTAs spread the FP64 work over SMs
-    GSIS_DISPATCH_DIM(dim, (k_coefficients<Real, DIM><<<nbk, nt, 0, s>>>(g, m, fields, cell_dx, coef)));
+    GSIS_DISPATCH_DIM3(dim, (k_coefficients<Real, DIM><<<nbk, nt, 0, s>>>(g, m, fields, cell_dx, coef)));
     return cudaGetLastError();
 }
 
@@ -1728,7 +1795,7 @@ cudaError_t launch_wall_density(cudaStream_t s, int dim, const Geom<Real> &g, co
                                 const double *patch_T, const double *bf_inc, const int *patch_kind, const Real *f,
                                 const double *wout, Real *bcoef) {
     if (g.n_bf == 0) return cudaSuccess;
-    GSIS_DISPATCH_DIM(dim, (k_wall_density<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, vq, patch_T, bf_inc, patch_kind, f,
+    GSIS_DISPATCH_DIM3(dim, (k_wall_density<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, vq, patch_T, bf_inc, patch_kind, f,
                                                                              wout, bcoef)));
     return cudaGetLastError();
 }
@@ -1775,8 +1842,8 @@ cudaError_t launch_cell_sums(cudaStream_t s, int dim, int n_cells, int n_chunks,
 template <typename Real, int N, int DIM>
 static cudaError_t slopes_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *f,
                             Real *fface) {
-    static_assert(SV % (32 * SLOPE_VPT) == 0, "a row's velocities must tile the padding");
-    dim3 grid((g.n_cells + SLOPE_ROWS - 1) / SLOPE_ROWS, q.n_pad / (32 * SLOPE_VPT)), block(32, SLOPE_ROWS);
+    static_assert(SV % (32 * slope_vpt(DIM)) == 0, "a row's velocities must tile the padding");
+    dim3 grid((g.n_cells + SLOPE_ROWS - 1) / SLOPE_ROWS, q.n_pad / (32 * slope_vpt(DIM))), block(32, SLOPE_ROWS);
     k_slopes<Real, N, DIM><<<grid, block, 0, s>>>(g, q.n_pad, q.x, f, fface);
     return cudaGetLastError();
 }
@@ -1785,23 +1852,23 @@ template <typename Real>
 cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, const Quad<Real> &q,
                           const Real *f, Real *fface) {
     if (planes == 4) {
-        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 4, DIM>(s, g, q, f, fface)));
+        GSIS_DISPATCH_DIM3(dim, return (slopes_t<Real, 4, DIM>(s, g, q, f, fface)));
     } else if (planes == 1) {
-        GSIS_DISPATCH_DIM(dim, return (slopes_t<Real, 1, DIM>(s, g, q, f, fface)));
+        GSIS_DISPATCH_DIM3(dim, return (slopes_t<Real, 1, DIM>(s, g, q, f, fface)));
     }
     return cudaErrorInvalidValue;
 }
 
 size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size, bool tc) {
-    return sweep_main_bytes(block, planes, real_size, tc) + (size_t)(dim + 1) * SV * real_size +
+    return sweep_main_bytes(block, planes, dim, real_size, tc) + (size_t)(dim + 1) * SV * real_size +
            (size_t)((block * MAXF + 15) & ~15) + (tc ? sizeof(tcm::Ctl) : 0);
 }
 
 template <typename Real, int N, int DIM, int ORDER>
 static cudaError_t sweep_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *coef,
                            const Real *bcoef, const Real *f_in, const Real *fface, Real *f_out, Real *partial) {
-    const bool tc = N == 4 && sizeof(Real) == 4 && g.tc;
-    if (g.tc && (MT % g.block != 0)) return cudaErrorInvalidValue;
+    const bool tc = N == 4 && sizeof(Real) == 4 && DIM < 3 && g.tc;
+    if (g.tc && (DIM == 3 || MT % g.block != 0)) return cudaErrorInvalidValue;
     const size_t smem = sweep_smem_bytes(g.block, N, DIM, sizeof(Real), tc);
     auto kern = k_sweep<Real, N, DIM, ORDER>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1816,9 +1883,9 @@ cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real
                              const Real *coef, const Real *bcoef, const Real *f_in, const Real *fface, Real *f_out,
                              Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 1>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 1>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 4, DIM, 2>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 2>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
@@ -1828,9 +1895,9 @@ cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<R
                                 const Real *coef, const Real *bcoef, const Real *I_in, const Real *fface,
                                 Real *I_out, Real *partial) {
     if (order == 1) {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 1>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 1>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM(dim, return (sweep_t<Real, 1, DIM, 2>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 2>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
@@ -1843,7 +1910,7 @@ cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, in
                           const double *X) {
     const int nt = 32, nbk = (n_cells + nt - 1) / nt;
     const int reduce = eps_sums != nullptr;
-    GSIS_DISPATCH_DIM(dim, (k_finish<Real, DIM><<<nbk, nt, 0, s>>>(n_cells, n_chunks, o_chunks, m, coef, partial,
+    GSIS_DISPATCH_DIM3(dim, (k_finish<Real, DIM><<<nbk, nt, 0, s>>>(n_cells, n_chunks, o_chunks, m, coef, partial,
                                                                     opartial, vol, fields_old, fields_new, eps_terms,
                                                                     err_flag, have_old, reduce, eps_part, ticket,
                                                                     eps_sums, X)));
@@ -1854,7 +1921,7 @@ cudaError_t launch_finish(cudaStream_t s, int dim, int n_cells, int n_chunks, in
 template <typename Real>
 cudaError_t launch_equilibrium(cudaStream_t s, int dim, int n_cells, const Quad<Real> &vq, const Quad<Real> &oq,
                                const ModelDev &m, const double *fields, Real *f, Real *I) {
-    GSIS_DISPATCH_DIM(dim, (k_equilibrium<Real, DIM><<<n_cells, 256, 0, s>>>(n_cells, vq, oq, m, fields, f, I)));
+    GSIS_DISPATCH_DIM3(dim, (k_equilibrium<Real, DIM><<<n_cells, 256, 0, s>>>(n_cells, vq, oq, m, fields, f, I)));
     return cudaGetLastError();
 }
 
@@ -1867,7 +1934,7 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, c
     static_assert(VCH == tcm::K && SV == tcm::K, "moment chunks are the tensor-core K");
     bool on_tc = false;
     if constexpr (std::is_same<Real, float>::value) {
-        if (tc) {
+        if (tc && dim < 3) {     // the tensor-core basis covers the 1-D and 2-D moments
             const int nch = vq.n_pad / tcm::K, n_items = (n_cells + MT - 1) / MT * nch;
             GSIS_DISPATCH_DIM(dim, {
                 auto kern = k_tc_pass<DIM, false>;
@@ -1877,10 +1944,10 @@ cudaError_t launch_moments_only(cudaStream_t s, int dim, int n_cells, bool tc, c
             on_tc = true;
         }
     }
-    if (!on_tc) GSIS_DISPATCH_DIM(dim, (k_moments_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, coef, f, partial)));
+    if (!on_tc) GSIS_DISPATCH_DIM3(dim, (k_moments_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, coef, f, partial)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    GSIS_DISPATCH_DIM(dim, (k_moments_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, I, opartial)));
+    GSIS_DISPATCH_DIM3(dim, (k_moments_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, I, opartial)));
     return cudaGetLastError();
 }
 

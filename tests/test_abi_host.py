@@ -63,9 +63,16 @@ def test_validation_rejects_before_touching_the_device(lib):
         G.gsis_create(*_args(bad))
     assert e.value.code == G.GSIS_ERR_INVALID_ARG
     args = list(_args(wl))
-    args[0] = 3
+    args[0] = 4
     with pytest.raises(G.GsisError) as e:
         G.gsis_create(*args)
+    assert e.value.code == G.GSIS_ERR_INVALID_ARG
+    # 3-D meshes run the kinetic path on CUDA cores: tensor-core moments are refused
+    box = gi.workloads.Workload("box", gi.mesh.box_tetrahedra(1), *gi.quadrature.trapezoid_nd(4, 4.0, 3),
+                                *gi.quadrature.photon_product(2, 2), gi.workloads.ModelParams(),
+                                gi.workloads.SolverParams(tc_moments=1))
+    with pytest.raises(G.GsisError) as e:
+        G.gsis_create(*_args(box))
     assert e.value.code == G.GSIS_ERR_UNSUPPORTED
     out = C.c_void_p()
     assert lib.gsis_create(None, None, None, None, None, None, C.byref(out)) == G.GSIS_ERR_INVALID_ARG
