@@ -64,6 +64,24 @@ def slab_1d(n_cells: int, length: float = 1.0, patches=None) -> Mesh:
         patches=list(patches) if patches is not None else [Patch(WALL), Patch(WALL)])
 
 
+def ring_1d(n_cells: int, length: float = 1.0) -> Mesh:
+    """Uniform periodic 1-D row of cells on [0, L): the slab's interior faces plus one face
+    from the last cell to the first (normal +x), so every cell has an upstream and a
+    downstream neighbour.  No boundary patches.  Cell-centre differences across that
+    face are not those of a periodic geometry, so only first-order transport (which uses
+    no centroid differences) treats the ring as periodic."""
+    x = np.linspace(0.0, length, n_cells + 1)
+    owner = list(range(n_cells - 1)) + [n_cells - 1]
+    nbr = list(range(1, n_cells)) + [0]
+    fc = list(x[1:-1]) + [x[-1]]
+    return Mesh(
+        dim=1, n_cells=n_cells,
+        face_owner=np.asarray(owner, np.int32), face_nbr=np.asarray(nbr, np.int32),
+        face_normal=np.ones((n_cells, 1)), face_area=np.ones(n_cells),
+        face_centroid=np.asarray(fc, np.float64).reshape(-1, 1),
+        cell_volume=np.diff(x), cell_centroid=(0.5 * (x[1:] + x[:-1])).reshape(-1, 1), patches=[])
+
+
 def _faces_from_triangles(verts, tris, side_of_edge):
     """Build the face list of a triangle mesh.
 
@@ -294,23 +312,45 @@ def drop_cells(m: Mesh, keep, patch: int) -> Mesh:
                 cell_volume=m.cell_volume[keep], cell_centroid=m.cell_centroid[keep], patches=list(m.patches))
 
 
+def sphere_cone_radius(x, x_nose=0.3, D=0.4, half_angle=60.0, nose=0.25, shoulder=0.1, aft_angle=40.0,
+                       back=0.5):
+    """Body radius r(x) (0 outside the body) of an axisymmetric sphere-cone entry capsule
+    facing -x: a spherical nose of radius nose*D at x_nose, tangent to a cone of the given
+    half-angle, rounded at the base diameter D by a torus of radius shoulder*D, then a
+    conical afterbody narrowing at aft_angle to a flat back of radius back*D/2."""
+    x = np.asarray(x, np.float64)
+    R, Rn, Rs = 0.5 * D, nose * D, shoulder * D
+    th, ta = np.radians(half_angle), np.radians(aft_angle)
+    xc = x_nose + Rn                                    # nose centre
+    xt, rt = xc - Rn * np.sin(th), Rn * np.cos(th)      # nose-cone tangency
+    rp = R - Rs + Rs * np.cos(th)                       # cone-shoulder tangency
+    xp = xt + (rp - rt) / np.tan(th)
+    cx, cr = xp + Rs * np.sin(th), R - Rs               # shoulder centre
+    x2, r2 = cx + Rs * np.sin(ta), cr + Rs * np.cos(ta) # shoulder-afterbody tangency
+    rb = back * R
+    xb = x2 + (r2 - rb) / np.tan(ta)
+    r = np.zeros_like(x)
+    m = (x >= x_nose) & (x < xt)
+    r[m] = np.sqrt(np.maximum(Rn * Rn - (xc - x[m]) ** 2, 0.0))
+    m = (x >= xt) & (x < xp)
+    r[m] = rt + (x[m] - xt) * np.tan(th)
+    m = (x >= xp) & (x < x2)
+    r[m] = cr + np.sqrt(np.maximum(Rs * Rs - (x[m] - cx) ** 2, 0.0))
+    m = (x >= x2) & (x <= xb)
+    r[m] = r2 - (x[m] - x2) * np.tan(ta)
+    return r
+
+
 def capsule_tetrahedra(n: int, seed: int = 2, jitter: float = 0.15, patches=None) -> Mesh:
-    """Blunt re-entry capsule in the unit cube, tetrahedral: box_tetrahedra(n) without the
-    cells whose centroids lie inside the body.  The body's axis is the line y = z = 0.5;
-    its spherical heat shield (radius 0.3, stagnation point x = 0.3) faces -x and meets
-    the base radius 0.18 at x = 0.36, followed by a conical afterbody narrowing at 33
-    degrees to a flat back at x = 0.52.  The exposed faces form patch 0 (the body), the
-    six sides of the cube patch 1 (far field); ``patches`` gives those two."""
+    """Sphere-cone re-entry capsule in the unit cube, tetrahedral: box_tetrahedra(n)
+    without the cells whose centroids lie inside the body (sphere_cone_radius: axis
+    y = z = 0.5, stagnation point x = 0.3, base diameter D = 0.4, 60-degree forebody
+    cone with nose radius 0.25 D, shoulder radius 0.1 D, 40-degree afterbody to a flat
+    back of diameter D / 2).  The exposed faces form patch 0 (the body), the six sides
+    of the cube patch 1 (far field); ``patches`` gives those two."""
     box = box_tetrahedra(n, seed=seed, jitter=jitter)
     x, y, z = box.cell_centroid.T
-    r = np.hypot(y - 0.5, z - 0.5)
-    xn, Rs, Rb = 0.3, 0.3, 0.18
-    xs = xn + Rs - np.sqrt(Rs * Rs - Rb * Rb)
-    xe = 0.52
-    shield = np.sqrt(np.maximum(Rs * Rs - (xn + Rs - x) ** 2, 0.0))
-    cone = Rb - (x - xs) * np.tan(np.radians(33.0))
-    radius = np.where(x < xs, shield, cone)
-    inside = (x >= xn) & (x <= xe) & (r <= radius)
+    inside = np.hypot(y - 0.5, z - 0.5) <= sphere_cone_radius(x)
     box.face_nbr = np.where(box.face_nbr < 0, -2, box.face_nbr).astype(np.int32)   # cube sides: patch 1
     if patches is None:
         patches = [Patch(WALL, T_t=1.0), Patch(FARFIELD)]

@@ -126,9 +126,9 @@ def cylinder(n_theta: int = 200, n_radial: int = 100, n_v: int = 48, n_polar: in
 def capsule(n: int = 32, n_v: int = 24, n_polar: int = 8, n_azim: int = 16, Mach: float = 10.0,
             T_inf: float = 0.5, T_wall: float = 0.5, Kn: float = 0.01, Kn_p: float = 1000.0,
             sigma_R: float = 0.1, seed: int = 2) -> Workload:
-    """3-D hypersonic flow past a blunt capsule (heat shield facing the stream, conical
-    afterbody) on a seeded tetrahedral mesh of the unit cube (about 6 n^3 cells); the
-    free stream flows along +x.  The n_v^3 uniform velocity grid (trapezoid weights) spans
+    """3-D hypersonic flow past a sphere-cone re-entry capsule (60-degree forebody, shoulder
+    radius 0.1 D; mesh.capsule_tetrahedra) on a seeded tetrahedral mesh of the unit cube
+    (about 6 n^3 cells, 193 009 at n = 32); the free stream flows along +x.  The n_v^3 uniform velocity grid (trapezoid weights) spans
     +-(u_inf + 4 sqrt(T_0)), T_0 the stagnation temperature; n_polar x n_azim photon
     directions.  FP32, order 2, CUDA-core moments."""
     gamma = (5.0 + 2.0 + 1.16) / (3.0 + 2.0 + 1.16)

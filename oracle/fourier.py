@@ -10,6 +10,14 @@ is the spectral radius of C or of L^-1 R.
 
 Every quantity depends on Kn theta, Kn/Kn_p and sigma_R only; Kn = 1 is used.
 
+Discrete space: on a uniform periodic row of cells of width dx, first-order upwinding
+turns the transport symbol i a xi_x (continuous) into a |xi_x| (1 - exp(-i sgn(xi_x) h)) / h
+with h = theta dx, which tends to i a xi_x as h -> 0 (``transport_symbol``).  With
+``h`` given, ``cis_matrix`` uses that symbol for the gas and the photons; with the solver's
+own velocity nodes (``velocity_grid(x_nodes=...)``) and photon directions it is the
+iteration matrix of the discrete-velocity, finite-volume CIS step with exact transport
+(tests/test_oracle_fourier_link_pins.py).
+
 Velocity integrals: the kinetic responses are (polynomial x Gaussian) / (1 + i a xi_x)
 with a = sqrt(2/pi) Kn theta.  They are evaluated on a tensor grid (dense trapezoid in
 xi_x, Gauss-Hermite in xi_y, xi_z); the tests cross-check the xi_x integrals against the
@@ -43,12 +51,16 @@ class Params:
         self.A = mdl.mason_monchick_A(d_r, d_v, Z_r, Z_v, Sc)
 
 
-def velocity_grid(n_x=4001, L=12.0, n_t=8):
-    """Tensor grid: trapezoid in xi_x on [-L, L], Gauss-Hermite (weight exp(-x^2/2)) in
-    xi_y and xi_z.  Returns (xi [n, 3], w [n]) with sum w g(xi) ~ int g."""
-    x = np.linspace(-L, L, n_x)
-    wx = np.full(n_x, x[1] - x[0])
-    wx[0] = wx[-1] = 0.5 * (x[1] - x[0])
+def velocity_grid(n_x=4001, L=12.0, n_t=8, x_nodes=None):
+    """Tensor grid: trapezoid in xi_x on [-L, L] (or the given (nodes, weights) with
+    sum w g(x) ~ int g dx), Gauss-Hermite (weight exp(-x^2/2)) in xi_y and xi_z.
+    Returns (xi [n, 3], w [n]) with sum w g(xi) ~ int g."""
+    if x_nodes is None:
+        x = np.linspace(-L, L, n_x)
+        wx = np.full(n_x, x[1] - x[0])
+        wx[0] = wx[-1] = 0.5 * (x[1] - x[0])
+    else:
+        x, wx = (np.asarray(a, np.float64).ravel() for a in x_nodes)
     t, wt = np.polynomial.hermite_e.hermegauss(n_t)
     wt = wt * np.exp(0.5 * t * t)          # the integrands carry their own exp(-xi^2/2)
     X, Y, Z = np.meshgrid(x, t, t, indexing="ij")
@@ -60,9 +72,19 @@ def _feq(xi):
     return (2.0 * math.pi) ** -1.5 * np.exp(-0.5 * np.sum(xi * xi, axis=1))
 
 
-def kinetic_response(p, alpha, Kn_theta, xi):
+def transport_symbol(s, h=None):
+    """Fourier symbol of tau xi_x d/dx for s = tau theta xi_x: i s in continuous space,
+    |s| (1 - exp(-i sgn(s) h)) / h for first-order upwinding on cells of width h / theta."""
+    s = np.asarray(s, np.float64)
+    if h is None:
+        return 1j * s
+    return np.abs(s) * (1.0 - np.exp(-1j * np.sign(s) * h)) / h
+
+
+def kinetic_response(p, alpha, Kn_theta, xi, h=None):
     """y_0, y_1, y_2 on the grid and the photon amplitude (4 sigma_R / pi) alpha_Tv of one
-    CIS kinetic step driven by the macroscopic error alpha (Eq. error_function_propagation)."""
+    CIS kinetic step driven by the macroscopic error alpha (Eq. error_function_propagation);
+    ``h``: the upwind symbol of a periodic row of cells (see transport_symbol)."""
     a = math.sqrt(2.0 / math.pi) * Kn_theta
     f0 = _feq(xi)
     x2 = np.sum(xi * xi, axis=1)
@@ -77,7 +99,7 @@ def kinetic_response(p, alpha, Kn_theta, xi):
           + (xi @ (-A[1, 0] * qt + (1 - A[1, 1]) * qr - A[1, 2] * qv)) * (2.0 / p.d_r))
     r2 = (base + 3 / ((3 + p.d_v) * p.Z_v) * alpha[TT] + (1 - 3 / ((3 + p.d_v) * p.Z_v)) * alpha[TV]
           + (xi @ (-A[2, 0] * qt - A[2, 1] * qr + (1 - A[2, 2]) * qv)) * (2.0 / p.d_v))
-    den = 1.0 + 1j * a * xi[:, 0]
+    den = 1.0 + transport_symbol(a * xi[:, 0], h)
     y0 = f0 * base / den
     y1 = 0.5 * p.d_r * f0 * r1 / den
     y2 = (0.5 * p.d_v * f0 * r2 - math.sqrt(2.0 / math.pi) * p.ratio * f0
@@ -94,17 +116,25 @@ def photon_integrals(b):
     return i0, i1
 
 
-def cis_matrix(p, Kn_theta, grid=None):
-    """C (17 x 17) of Eq. eigenfunction_cis."""
+def cis_matrix(p, Kn_theta, grid=None, h=None, photons=None):
+    """C (17 x 17) of Eq. eigenfunction_cis.  ``h`` = theta dx selects the upwind symbol
+    of a periodic row of cells; ``photons`` = (mu, w), the x-cosines and weights of a
+    discrete direction set, replaces the exact sphere integral."""
     xi, w = grid if grid is not None else velocity_grid()
     x2 = np.sum(xi * xi, axis=1)
     b = Kn_theta / p.ratio                      # Kn_p theta with Kn = 1
-    i0, _ = photon_integrals(b)
+    if photons is None and h is None:
+        i0, _ = photon_integrals(b)
+    else:
+        mu, wmu = photons if photons is not None else np.polynomial.legendre.leggauss(400)
+        if photons is None:
+            wmu = 2.0 * math.pi * wmu
+        i0 = np.sum(wmu / (1.0 + transport_symbol(b * np.asarray(mu), h)))
     C = np.zeros((NM, NM), complex)
     for n in range(NM):
         e = np.zeros(NM)
         e[n] = 1.0
-        y0, y1, y2, yR = kinetic_response(p, e, Kn_theta, xi)
+        y0, y1, y2, yR = kinetic_response(p, e, Kn_theta, xi, h)
         col = np.zeros(NM, complex)
         col[RHO] = w @ y0
         col[1:4] = (w * y0) @ xi
@@ -181,8 +211,8 @@ def gsis_matrices(p, Kn_theta, grid=None):
     return L, Rm
 
 
-def spectral_radius_cis(p, Kn_theta, grid=None):
-    return float(np.max(np.abs(np.linalg.eigvals(cis_matrix(p, Kn_theta, grid)))))
+def spectral_radius_cis(p, Kn_theta, grid=None, h=None, photons=None):
+    return float(np.max(np.abs(np.linalg.eigvals(cis_matrix(p, Kn_theta, grid, h, photons)))))
 
 
 def spectral_radius_gsis(p, Kn_theta, grid=None):

@@ -59,6 +59,10 @@ def test_box_volume_and_capsule_body():
     xc = m.face_centroid[wall]
     r = np.hypot(xc[:, 1] - 0.5, xc[:, 2] - 0.5)
     assert xc[:, 0].min() > 0.25 and xc[:, 0].max() < 0.6 and r.max() < 0.25
+    # the body is the sphere-cone: every dropped cell's centroid lies inside its profile
+    inside = np.hypot(box.cell_centroid[:, 1] - 0.5, box.cell_centroid[:, 2] - 0.5) <= \
+        gi.mesh.sphere_cone_radius(box.cell_centroid[:, 0])
+    assert int(inside.sum()) == box.n_cells - m.n_cells
     far = m.face_nbr == -2
     assert np.all(np.min(np.minimum(m.face_centroid[far], 1.0 - m.face_centroid[far]), axis=1) < 1e-12)
 
