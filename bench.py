@@ -48,7 +48,7 @@ import numpy as np  # noqa: E402
 METRIC = "DVM cell-velocity updates/s (% HBM roofline); time-to-steady vs plain FP64 GSIS"
 # DRAM bytes (read + write) of one gas sweep on the 20 000-cell cavity, from the ncu capture
 # summarised in profiles/sweep_gas_cavity20k_order2.md; update it whenever the kernels change.
-SWEEP_TRAFFIC = {("fp32", 2): 290.4e6 + 345.7e6 + 753.4e6 + 261.4e6}
+SWEEP_TRAFFIC = {("fp32", 2): 291.0e6 + 346.2e6 + 752.5e6 + 261.4e6}
 UNIT = "updates/s"
 
 
@@ -515,123 +515,129 @@ def field_errors(stream):
     return out
 
 
-def _full_size_leg(stream, base, init, bytes_per_update, steps, warmup, start_iters=40):
-    """CIS throughput of one full-size case at order 2 (FP32, blocks of 16, limiter
-    constant K = 0.01 as for the normal shock): updates/s and the gas sweep's fraction of
-    HBM bandwidth.  ``init(ctx)`` sets the uniform free stream.  From that impulsive start
-    order 2 can drive f negative at the body; then ``start_iters`` order-1 iterations
-    develop the flow, their fields are taken to the host, and the order-2 context starts
-    from their equilibrium (gsis_init_fields).  Should that diverge as well, the leg is
-    timed at order 1 and says so.  One context is alive at a time."""
+def _stagnation_state(base):
+    """Uniform gas at rest at the free stream's density and stagnation temperature
+    T_0 = T_inf + (gamma - 1) / (2 gamma) |u_inf|^2: a hot state that the velocity grid
+    (sized by T_0) resolves, unlike the cold free stream."""
+    import gsis_inputs as gi
+    far = base.mesh.patches[1]
+    m = base.model
+    gamma = (5.0 + m.d_r + m.d_v) / (3.0 + m.d_r + m.d_v)
+    T0 = far.T_t + (gamma - 1.0) / (2.0 * gamma) * float(np.dot(far.u, far.u))
+    return gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, T=T0)
+
+
+def _full_size_leg(stream, base, bytes_per_update, plan):
+    """CIS throughput of one full-size case, FP32, blocks of 16, for each (label, order,
+    fields, warmup, steps, limiter constant K) of ``plan``:
+    the state is set on the device (gsis_init_fields), then warmup and timed iterations.
+    Reports updates/s and the gas sweep's fraction of HBM bandwidth per entry.  One
+    context is alive at a time."""
     import torch
     import gsis_inputs as gi
     from paper_2601_03935_gb300 import gsis as G
     nc, V = base.mesh.n_cells, base.xi.shape[0]
-    notes = []
-
-    def make(order):
-        return create_ctx(gi.workloads.with_solver(base, precision="fp32", order=order, relax_block=16,
-                                                   venkat_K=0.01), stream.cuda_stream)
-
-    def warm(ctx):
-        for _ in range(warmup):
-            G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
-        G.gsis_last_eps(ctx)
-
-    ctx, order = None, 2
-    for attempt in ("free stream", "developed"):
-        ctx = make(2)
-        try:
-            if attempt == "free stream":
-                init(ctx)
-            else:
-                G.gsis_init_fields(ctx, fields)
-            warm(ctx)
-            if attempt == "developed":
-                notes.append("order 2 started from the fields of %d order-1 iterations" % start_iters)
-            break
-        except G.GsisError as e:
-            G.gsis_destroy(ctx)
-            ctx = None
-            notes.append("order 2 from the %s: %s" % (attempt, e))
-            if attempt == "free stream":
-                c1 = make(1)
-                try:
-                    init(c1)
-                    for _ in range(start_iters):
-                        G.gsis_step_async(c1, G.GSIS_MODE_CIS)
-                    G.gsis_last_eps(c1)
-                    fields = G.gsis_get_fields(c1, nc)
-                finally:
-                    G.gsis_destroy(c1)
-    if ctx is None:
-        order = 1
-        ctx = make(1)
-        init(ctx)
-        warm(ctx)
-        notes.append("timed at order 1")
-    try:
-        G.gsis_profile_enable(ctx, True)
-        G.gsis_profile_reset(ctx)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        prof = G.gsis_profile_read(ctx)
-        try:
-            eps = G.gsis_last_eps(ctx)
-        except G.GsisError as e:
-            eps = None
-            notes.append("timed steps: %s" % e)
-    finally:
-        G.gsis_destroy(ctx)
-    names = ("slopes_gas", "sweep_gas") if order == 2 else ("sweep_gas",)
-    sweep = sum(prof[k][0] / max(prof[k][1], 1) for k in names)
-    alg = nc * V * bytes_per_update
     peak, kind = measured_peaks()
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items() if v[1]}
-    return order, {"note": "; ".join(notes) or None,
-                   "value": nc * V / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "last_eps": eps,
-                   "kernels": kernels,
-                   "roofline": {"kernel": "+".join(names), "bound": "hbm", "achieved": alg / (sweep * 1e-3) / 1e9,
-                                "peak": peak, "unit": "GB/s", "frac": alg / (sweep * 1e-3) / 1e9 / peak,
-                                "peak_kind": kind, "algorithmic_bytes_per_launch": alg, "ms_per_launch": sweep}}
+    out = {}
+    for label, order, M, warmup, steps, K in plan:
+        wl = gi.workloads.with_solver(base, precision="fp32", order=order, relax_block=16, venkat_K=K)
+        ctx = create_ctx(wl, stream.cuda_stream)
+        entry = {"order": order}
+        try:
+            G.gsis_init_fields(ctx, M)
+            for _ in range(warmup):
+                G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+            G.gsis_last_eps(ctx)
+            G.gsis_profile_enable(ctx, True)
+            G.gsis_profile_reset(ctx)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            prof = G.gsis_profile_read(ctx)
+            entry["last_eps"] = G.gsis_last_eps(ctx)
+        except G.GsisError as e:
+            out[label] = {"order": order, "note": "not timed: %s" % e}
+            continue
+        finally:
+            G.gsis_destroy(ctx)
+        names = ("slopes_gas", "sweep_gas") if order == 2 else ("sweep_gas",)
+        sweep = sum(prof[k][0] / max(prof[k][1], 1) for k in names)
+        alg = nc * V * bytes_per_update
+        entry.update({"warmup": warmup, "steps": steps, "value": nc * V / (ms * 1e-3), "unit": UNIT,
+                      "ms_per_step": ms,
+                      "kernels": {k: {"ms_per_launch": v[0] / v[1], "launches": v[1]} for k, v in prof.items() if v[1]},
+                      "roofline": {"kernel": "+".join(names), "bound": "hbm", "achieved": alg / (sweep * 1e-3) / 1e9,
+                                   "peak": peak, "unit": "GB/s", "frac": alg / (sweep * 1e-3) / 1e9 / peak,
+                                   "peak_kind": kind, "algorithmic_bytes_per_launch": alg, "ms_per_launch": sweep}})
+        out[label] = entry
+    return out
 
 
-def full_cylinder_throughput(stream, steps=10, warmup=3):
-    """The full-size Mach-5 cylinder (40 000 triangles, 48 x 48 velocities, 96 directions,
-    FP32, order 2) from the uniform free stream: 32 B per update (four planes read and
-    written once)."""
+ORDER2_NOTE = ("order 2 (limiter constant 5) is timed over iterations 2-3 from gas at rest at the "
+               "stagnation temperature: from the impulsive free-stream start, and within a few "
+               "iterations from other states at these velocity resolutions, the order-2 defect "
+               "correction drives f negative at the body (oracle and GPU alike); order 1 (limiter "
+               "constant 0.01) is timed from the free stream, where it converges")
+
+
+def full_cylinder_throughput(stream):
+    """The full-size Mach-5 cylinder (40 000 triangles, 48 x 48 velocities, 96 directions):
+    32 B per update (four planes read and written once)."""
     import gsis_inputs as gi
-    from paper_2601_03935_gb300 import gsis as G
     base = gi.workloads.cylinder()
     far = base.mesh.patches[1]
-    M = gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
-    order, out = _full_size_leg(stream, base, lambda ctx: G.gsis_init_fields(ctx, M), 32, steps, warmup)
-    return dict({"workload": "cylinder 2-D Mach 5, %d triangles, 48x48 velocities (%d), %d photon directions, "
-                             "FP32, order %d" % (base.mesh.n_cells, base.xi.shape[0], base.omega.shape[0], order)},
-                **out)
+    free = gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
+    plan = [("order2_stagnation_start", 2, _stagnation_state(base), 1, 2, 5.0),
+            ("order1_free_stream", 1, free, 3, 10, 0.01)]
+    return {"workload": "cylinder 2-D Mach 5, %d triangles, 48x48 velocities (%d), %d photon directions, FP32"
+                        % (base.mesh.n_cells, base.xi.shape[0], base.omega.shape[0]),
+            "note": ORDER2_NOTE, **_full_size_leg(stream, base, 32, plan)}
 
 
-def capsule_throughput(stream, steps=5, warmup=3):
-    """The full-size 3-D capsule (194 266 tetrahedra, 24^3 = 13 824 velocities, 128
-    directions, FP32, order 2, CUDA-core moments) from the uniform Mach-10 free stream,
-    set on the device (gsis_init_fields; no host copy of f): 24 B per update (f0, f1, f2
-    read and written once; the fourth plane of the layout is zero in 3-D and counts as
-    waste, not work)."""
+def capsule_throughput(stream):
+    """The full-size 3-D sphere-cone capsule (193 009 tetrahedra, 24^3 = 13 824 velocities, 128
+    directions, CUDA-core moments): 24 B per update (f0, f1, f2 read and written once;
+    the fourth plane of the layout is zero in 3-D and counts as waste, not work)."""
     import gsis_inputs as gi
-    from paper_2601_03935_gb300 import gsis as G
     base = gi.workloads.capsule()
     far = base.mesh.patches[1]
-    M = gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
-    order, out = _full_size_leg(stream, base, lambda ctx: G.gsis_init_fields(ctx, M), 24, steps, warmup)
-    return dict({"workload": "capsule 3-D Mach 10, %d tetrahedra, 24^3 velocities (%d), %d photon directions, "
-                             "FP32, order %d" % (base.mesh.n_cells, base.xi.shape[0], base.omega.shape[0], order)},
-                **out)
+    free = gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
+    plan = [("order2_stagnation_start", 2, _stagnation_state(base), 1, 2, 5.0),
+            ("order1_free_stream", 1, free, 3, 5, 0.01)]
+    return {"workload": "capsule 3-D Mach 10, %d tetrahedra, 24^3 velocities (%d), %d photon directions, FP32"
+                        % (base.mesh.n_cells, base.xi.shape[0], base.omega.shape[0]),
+            "note": ORDER2_NOTE, **_full_size_leg(stream, base, 24, plan)}
+
+
+def capsule_probe(args):
+    """A small 3-D capsule run for profiling: box of n^3 hexahedra (6 n^3 tetrahedra less the
+    body), nv^3 velocities, 8 x 16 directions, FP32, order 2, from the stagnation state;
+    --steps CIS iterations, then the per-kernel times of the library's own events."""
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import build
+    from paper_2601_03935_gb300 import gsis as G
+    build.build()
+    G.load()
+    n, nv = (int(x) for x in args.capsule_probe.split(","))
+    wl = gi.workloads.with_solver(gi.workloads.capsule(n=n, n_v=nv), precision="fp32", order=2, relax_block=16)
+    ctx = create_ctx(wl, 0)
+    try:
+        G.gsis_init_fields(ctx, _stagnation_state(wl))
+        G.gsis_profile_enable(ctx, True)
+        for _ in range(args.steps):
+            G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+        eps = G.gsis_last_eps(ctx)
+        prof = G.gsis_profile_read(ctx)
+    finally:
+        G.gsis_destroy(ctx)
+    print(json.dumps({"probe": "capsule", "n_cells": wl.mesh.n_cells, "n_xi": int(wl.xi.shape[0]), "last_eps": eps,
+                      "ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}))
+    return 0
 
 
 def run_sharded(args, dist, rank, local, world):
@@ -912,6 +918,8 @@ def main():
     ap.add_argument("--no-tts", action="store_true", help="skip the time-to-steady measurement")
     ap.add_argument("--no-shock", action="store_true", help="skip the normal-shock convergence measurement")
     ap.add_argument("--no-cylinder", action="store_true", help="skip the Mach-5 cylinder CIS/GSIS measurement")
+    ap.add_argument("--capsule-probe", default=None, metavar="N,NV",
+                    help="only run a small 3-D capsule case (N^3 hexahedra, NV^3 velocities) for profiling")
     ap.add_argument("--no-capsule", action="store_true",
                     help="skip the full-size 3-D capsule (tetrahedra) throughput leg")
     ap.add_argument("--no-full-cylinder", action="store_true",
@@ -921,6 +929,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.capsule_probe:
+        return capsule_probe(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

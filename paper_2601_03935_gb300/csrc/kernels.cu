@@ -332,6 +332,11 @@ __device__ __forceinline__ V<Real, N> vsplat(Real c) {
     return r;
 }
 
+// An int carried bit for bit in a Real slot (a face's upwind source, a stencil entry's cell).
+__device__ __forceinline__ float int_bits_as(int x, float) { return __int_as_float(x); }
+__device__ __forceinline__ double int_bits_as(int x, double) { return __longlong_as_double((long long)x); }
+__device__ __forceinline__ int bits_as_int(float x) { return __float_as_int(x); }
+__device__ __forceinline__ int bits_as_int(double x) { return (int)__double_as_longlong(x); }
 template <typename Real>
 struct Face {
     Real n[3], sv, svn, df[3], dn[3];
@@ -394,28 +399,42 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
     constexpr int MS = Lay<DIM>::MAXS, LW = Lay<DIM>::LW;
     const int *stn = g.stn + (size_t)j * MS;
     const Real *lw = g.lsq + (size_t)j * MS * LW;
+    // Stencil entries in batches of BT whose index and value loads are all issued before
+    // the batch is used.  The entries past the stencil's end (up to the batch boundary)
+    // hold cell 0 and zero weights, so they add exactly nothing; only the interior face
+    // neighbours (the first entries) bound the limiter.
+    constexpr int BT = DIM < 3 ? 2 : 4;
+    static_assert(MS % BT == 0, "batches tile the stencil records");
 #pragma unroll
-    for (int k = 0; k < MS; ++k) {
-        if (k >= ns) break;
-        const size_t row = (size_t)stn[k] * stride + v;
-        V<Real, N> fs[VPT];
+    for (int k0 = 0; k0 < MS; k0 += BT) {
+        if (k0 >= ns) break;
+        int sidx[BT];
 #pragma unroll
-        for (int u = 0; u < VPT; ++u) fs[u] = ldv<Real, N>(f, row + 32 * u);
-        const Real c0 = lw[LW * k], c1 = DIM > 1 ? lw[LW * k + 1] : Real(0), c2 = DIM > 2 ? lw[LW * k + 2] : Real(0);
-        const bool face_nbr = k < nfn;
+        for (int t = 0; t < BT; ++t) sidx[t] = stn[k0 + t];
+        V<Real, N> fs[BT][VPT];
 #pragma unroll
-        for (int u = 0; u < VPT; ++u) {
-            const V<Real, N> dq = vsub(fs[u], fj[u]);
-            if (face_nbr) {
+        for (int t = 0; t < BT; ++t)
 #pragma unroll
-                for (int p = 0; p < N; ++p) {
-                    dmax[u].x[p] = fmax(dmax[u].x[p], dq.x[p]);
-                    dmin[u].x[p] = fmin(dmin[u].x[p], dq.x[p]);
+            for (int u = 0; u < VPT; ++u) fs[t][u] = ldv<Real, N>(f, (size_t)sidx[t] * stride + v + 32 * u);
+#pragma unroll
+        for (int t = 0; t < BT; ++t) {
+            const int k = k0 + t;
+            const Real c0 = lw[LW * k], c1 = DIM > 1 ? lw[LW * k + 1] : Real(0), c2 = DIM > 2 ? lw[LW * k + 2] : Real(0);
+            const bool face_nbr = k < MAXF && k < nfn;
+#pragma unroll
+            for (int u = 0; u < VPT; ++u) {
+                const V<Real, N> dq = vsub(fs[t][u], fj[u]);
+                if (face_nbr) {
+#pragma unroll
+                    for (int p = 0; p < N; ++p) {
+                        dmax[u].x[p] = fmax(dmax[u].x[p], dq.x[p]);
+                        dmin[u].x[p] = fmin(dmin[u].x[p], dq.x[p]);
+                    }
                 }
+                vfma(c0, dq, slope[u][0]);
+                if constexpr (DIM > 1) vfma(c1, dq, slope[u][1]);
+                if constexpr (DIM > 2) vfma(c2, dq, slope[u][2]);
             }
-            vfma(c0, dq, slope[u][0]);
-            if constexpr (DIM > 1) vfma(c1, dq, slope[u][1]);
-            if constexpr (DIM > 2) vfma(c2, dq, slope[u][2]);
         }
     }
     // phi = min(1, min over interior faces of phi_V(Delta_1, Delta_2)).  On the faces with
@@ -435,17 +454,19 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
     const int nf = info.x;
     for (int k = 0; k < nf; ++k) {
         if (g.fnb[j * MAXF + k].x < 0) continue;
+        // face centroid - cell centroid: words 4..5 of a 1-D/2-D record, 5..7 of a 3-D one
         Real dx0, dx1, dx2;
+        const Real *q = g.fgeo + ((size_t)j * MAXF + k) * Lay<DIM>::FRS + 4;
         if constexpr (DIM < 3) {
-            const Real *q = g.fgeo + ((size_t)j * MAXF + k) * fr::SIZE + fr::DFX;
-            dx0 = q[0];
-            dx1 = DIM > 1 ? q[1] : Real(0);
+            const Vec<Real, 2> d = vload<Real, 2>(q);
+            dx0 = d.v[0];
+            dx1 = d.v[1];
             dx2 = Real(0);
         } else {
-            const Face<Real> Fk = load_face<Real, DIM>(g.fgeo, j, k);
-            dx0 = Fk.df[0];
-            dx1 = Fk.df[1];
-            dx2 = Fk.df[2];
+            const Vec<Real, 4> d = vload<Real, 4>(q);
+            dx0 = d.v[1];
+            dx1 = d.v[2];
+            dx2 = d.v[3];
         }
 #pragma unroll
         for (int u = 0; u < VPT; ++u) {
@@ -582,10 +603,10 @@ __device__ __forceinline__ void add_moments(Real (&acc)[Lay<DIM>::NMP], const Re
 // face's value, and none where xi . n = 0, which the sweep skips.  The sweep reads these
 // values for both its outflow and its inflow interior faces.
 constexpr int SLOPE_ROWS = 8;
-// velocities per thread (32 slope_vpt per row) and FP32 CTAs per SM the registers allow:
-// a 3-D slope of four planes takes 12 registers per velocity
+// velocities per thread (32 slope_vpt per row; a 3-D slope of four planes takes 12
+// registers per velocity) and FP32 CTAs per SM (64 registers per thread)
 __host__ __device__ constexpr int slope_vpt(int dim) { return dim < 3 ? 2 : 1; }
-__host__ __device__ constexpr int slope_minb(int dim) { return dim < 3 ? 4 : 3; }
+__host__ __device__ constexpr int slope_minb(int) { return 4; }
 template <typename Real, int N, int DIM>
 __global__ void __launch_bounds__(32 * SLOPE_ROWS, sizeof(Real) == 4 ? slope_minb(DIM) : 1) k_slopes(Geom<Real> g, int n_pad, const Real *__restrict__ xq,
                                                             const Real *__restrict__ f, Real *__restrict__ fface) {
@@ -646,11 +667,6 @@ __host__ __device__ constexpr size_t sweep_face_bytes(int block, int dim, size_t
            ((size_t)block * MAXF * sweep_nf_stride(dim) * real_size + 31) / 32 * 32 + (size_t)block * cf::NC * real_size;
 }
 
-// A face's upwind source (int) carried in the last slot of its Real face record, bit for bit.
-__device__ __forceinline__ float int_bits_as(int x, float) { return __int_as_float(x); }
-__device__ __forceinline__ double int_bits_as(int x, double) { return __longlong_as_double((long long)x); }
-__device__ __forceinline__ int bits_as_int(float x) { return __float_as_int(x); }
-__device__ __forceinline__ int bits_as_int(double x) { return (int)__double_as_longlong(x); }
 constexpr int NO_FACE = -2147483647 - 1;
 __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, int dim, size_t real_size, bool tc) {
     return (tc && (size_t)block * SV * (planes + 1) * real_size + sweep_face_bytes(block, dim, real_size) <
