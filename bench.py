@@ -329,6 +329,42 @@ def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=15
     return out
 
 
+def time_to_steady_full(stream, kn=0.01, kn_p=10.0, tol=1e-6, max_gsis=900, max_cis=3000, inner=100):
+    """Time to eps < tol on the full 20 000-cell cavity at Kn = 0.01 (order 1, blocks of 16,
+    100 synthetic iterations per outer iteration): GSIS in plain FP64 and in FP32 with the
+    mixed synthetic schedule, and CIS in FP32 (stopped at max_cis) for context.  From
+    uniform rest; the timing excludes creation, as the paper's does."""
+    import torch
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import gsis as G
+
+    def run(prec, mode, mixed, n):
+        wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=100, Kn=kn, Kn_p=kn_p), precision=prec, order=1,
+                                      relax_block=16, max_inner=inner, n_cis_precond=10,
+                                      macro_fp32=2 if mixed else 0)
+        ctx = create_ctx(wl, stream.cuda_stream)
+        try:
+            G.gsis_init_fields(ctx, gi.fields.uniform_fields(wl.mesh.n_cells))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist = G.gsis_solve(ctx, mode, n, tol)
+            dt = time.perf_counter() - t0
+        finally:
+            G.gsis_destroy(ctx)
+        return {"seconds": dt, "iterations": int(it), "final_eps": float(hist[-1]) if len(hist) else None,
+                "converged": bool(len(hist) and hist[-1] < tol),
+                "eps_every_100": [float(hist[k]) for k in range(99, len(hist), 100)]}
+
+    out = {"workload": "cavity 2-D, 20000 triangles, 28x28 velocities, 64 directions, Kn=%g, Kn_p=%g, order 1, "
+                       "%d synthetic iterations per GSIS iteration" % (kn, kn_p, inner), "tol": tol}
+    out["gsis_fp64_plain"] = run("fp64", G.GSIS_MODE_GSIS, False, max_gsis)
+    out["gsis_fp32_mixed"] = run("fp32", G.GSIS_MODE_GSIS, True, max_gsis)
+    out["cis_fp32"] = run("fp32", G.GSIS_MODE_CIS, False, max_cis)
+    if out["gsis_fp32_mixed"]["converged"] and out["gsis_fp64_plain"]["converged"]:
+        out["speedup_fp32_mixed_vs_fp64_plain"] = out["gsis_fp64_plain"]["seconds"] / out["gsis_fp32_mixed"]["seconds"]
+    return out
+
+
 def normal_shock(max_gsis=300):
     """The paper's Mach-5 normal shock (FP64, order 2): CIS and GSIS outer iterations to
     eps < 2e-6 for (Z_r, Z_v) = (2.6, 26) on 200 L0 and (8, 100) on 350 L0, with the
@@ -878,6 +914,8 @@ def run_ours(args):
         line["time_to_steady"] = time_to_steady(stream)
     if not args.no_tts:
         line["slab_time_to_steady"] = slab_time_to_steady()
+    if not args.no_tts:
+        line["time_to_steady_20k"] = time_to_steady_full(stream)
     if not args.no_shock:
         line["normal_shock"] = normal_shock()
     if not args.no_cylinder:

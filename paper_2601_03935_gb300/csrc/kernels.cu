@@ -880,7 +880,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
                 Real a = Nf[(l * MAXF + k) * NFS] * xi[0];
                 if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * NFS + 1], xi[1], a);
                 if constexpr (DIM > 2) a = fma(Nf[(l * MAXF + k) * NFS + 2], xi[2], a);
-                if (!(a < Real(0))) continue;
+                a = fmin(a, Real(0));   // outflow faces (a >= 0) add exactly nothing; no divergent branch
                 const Vec<Real, N> dj = R[lj * SV + tx];
 #pragma unroll
                 for (int p = 0; p < N; ++p) acc.v[p] = fma(-a, dj.v[p], acc.v[p]);
@@ -901,7 +901,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
                 Real a = Nf[(l * MAXF + k) * NFS] * xi[0];
                 if constexpr (DIM > 1) a = fma(Nf[(l * MAXF + k) * NFS + 1], xi[1], a);
                 if constexpr (DIM > 2) a = fma(Nf[(l * MAXF + k) * NFS + 2], xi[2], a);
-                if (!(a < Real(0))) continue;
+                a = fmin(a, Real(0));
                 const Vec<Real, N> dj = R[lj * SV + tx];
 #pragma unroll
                 for (int p = 0; p < N; ++p) corr[p] = fma(a, dj.v[p], corr[p]);
