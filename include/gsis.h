@@ -83,10 +83,10 @@ typedef struct {
  * Cells have at most 4 faces (segments, triangles, quadrilaterals, tetrahedra); the
  * least-squares stencil (face neighbours and their face neighbours) holds at most 12
  * cells in 1-D and 2-D and 16 in 3-D (UNSUPPORTED beyond).
- * 3-D meshes run the kinetic iteration (GSIS_MODE_CIS: the sweeps of Eq. dis_micro, the
- * moments, the fields and eps) in FP32 or FP64 with tc_moments = 0; the synthetic
- * equations (GSIS_MODE_GSIS, gsis_warm_start), the learned closure's samples and
- * velocity shards are built for 1-D and 2-D and return UNSUPPORTED on a 3-D context. */
+ * 3-D meshes run CIS and GSIS (the synthetic equations with five conservative gas
+ * variables, rho u in three components) in FP32 or FP64 with tc_moments = 0; the learned
+ * closure's samples (gsis_mlp_samples, gsis_warm_start with use_mlp) and velocity shards
+ * are built for 1-D and 2-D and return UNSUPPORTED on a 3-D context. */
 typedef struct {
     int32_t dim;                      /* 1, 2 or 3                                      */
     int64_t n_cells, n_faces;

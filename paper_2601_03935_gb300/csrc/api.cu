@@ -958,7 +958,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     // ---- synthetic-equation geometry: interior faces (owner -> neighbour), the cell -> face
     // map in the cell's face order, boundary faces, FP64 quadratures and patch states
     std::vector<int> fi_i, fi_j, cface(nc * MAXF, 0), mpk(std::max(m->n_patches, 1), 0);
-    std::vector<double> fi_n, fi_S, fi_dn, fi_dist, fi_t, fi_xf, mxc(nc * 2, 0.0), mbn, mbS, mbdn,
+    std::vector<double> fi_n, fi_S, fi_dn, fi_dist, fi_t, fi_xf, mxc(nc * MGS, 0.0), mbn, mbS, mbdn,
         mps(8 * std::max(m->n_patches, 1), 0.0);
     {
         std::vector<int> id_of(nfc, -1);
@@ -975,7 +975,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
                 dd += d[a] * d[a];
             }
             dd = std::sqrt(dd);
-            for (int a = 0; a < 2; ++a) {
+            for (int a = 0; a < MGS; ++a) {
                 fi_n.push_back(a < dim ? m->face_normal[f * dim + a] : 0.0);
                 fi_t.push_back(d[a] / dd);
                 fi_xf.push_back(a < dim ? m->face_centroid[f * dim + a] : 0.0);
@@ -985,7 +985,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             fi_dist.push_back(dd);
         }
         for (int64_t i = 0; i < nc; ++i) {
-            for (int a = 0; a < std::min(dim, 2); ++a) mxc[i * 2 + a] = m->cell_centroid[i * dim + a];
+            for (int a = 0; a < dim; ++a) mxc[i * MGS + a] = m->cell_centroid[i * dim + a];
             for (int k = 0; k < MAXF; ++k) {
                 if (k >= nf[i]) { cface[i * MAXF + k] = -1 - std::max(c->n_bf, 1); continue; }
                 const int j = nbr[i * MAXF + k];
@@ -993,7 +993,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             }
         }
         // boundary faces in the order the kinetic connectivity numbered them
-        mbn.assign(2 * std::max(c->n_bf, 1), 0.0);
+        mbn.assign(MGS * std::max(c->n_bf, 1), 0.0);
         mbS.assign(std::max(c->n_bf, 1), 0.0);
         mbdn.assign(std::max(c->n_bf, 1), 0.0);
         for (int64_t i = 0; i < nc; ++i)
@@ -1004,7 +1004,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
                 const int64_t f = face_of[i * MAXF + k];
                 double dn = 0.0;
                 for (int a = 0; a < dim; ++a) {
-                    if (a < 2) mbn[b * 2 + a] = m->face_normal[f * dim + a];
+                    mbn[b * MGS + a] = m->face_normal[f * dim + a];
                     dn += m->face_normal[f * dim + a] * (m->face_centroid[f * dim + a] - m->cell_centroid[i * dim + a]);
                 }
                 mbS[b] = m->face_area[f];
@@ -1019,7 +1019,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         }
         if (fi_i.empty()) {   // keep every device array non-empty
             fi_i.push_back(0); fi_j.push_back(0); fi_S.push_back(0.0); fi_dn.push_back(1.0); fi_dist.push_back(1.0);
-            for (int a = 0; a < 2; ++a) { fi_n.push_back(0.0); fi_t.push_back(0.0); fi_xf.push_back(0.0); }
+            for (int a = 0; a < MGS; ++a) { fi_n.push_back(0.0); fi_t.push_back(0.0); fi_xf.push_back(0.0); }
         }
     }
     const int n_fi = (int)std::count_if(fi_S.begin(), fi_S.end(), [](double x) { return x > 0.0; });
@@ -1075,16 +1075,16 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         A_(dalloc(c, &c->m_fi_j, nfi1));
         A_(dalloc(c, &c->m_cface, (size_t)nc * MAXF));
         A_(dalloc(c, &c->m_pkind, mpk.size()));
-        A_(dalloc(c, &c->m_fi_n, nfi1 * 2));
+        A_(dalloc(c, &c->m_fi_n, nfi1 * MGS));
         A_(dalloc(c, &c->m_fi_S, nfi1));
         A_(dalloc(c, &c->m_fi_dn, nfi1));
         A_(dalloc(c, &c->m_fi_dist, nfi1));
-        A_(dalloc(c, &c->m_fi_t, nfi1 * 2));
-        A_(dalloc(c, &c->m_fi_xf, nfi1 * 2));
+        A_(dalloc(c, &c->m_fi_t, nfi1 * MGS));
+        A_(dalloc(c, &c->m_fi_xf, nfi1 * MGS));
         A_(dalloc(c, &c->m_lsq, lsq.size()));
         A_(dalloc(c, &c->m_eps2, (size_t)nc));
-        A_(dalloc(c, &c->m_xc, (size_t)nc * 2));
-        A_(dalloc(c, &c->m_bf_n, nbf1 * 2));
+        A_(dalloc(c, &c->m_xc, (size_t)nc * MGS));
+        A_(dalloc(c, &c->m_bf_n, nbf1 * MGS));
         A_(dalloc(c, &c->m_bf_S, nbf1));
         A_(dalloc(c, &c->m_bf_dn, nbf1));
         A_(dalloc(c, &c->m_pstate, mps.size()));
@@ -1097,7 +1097,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             A_(dalloc(c, &c->dG[k], (size_t)nc * NVM));
         }
         A_(dalloc(c, &c->mq, (size_t)nc * NVM));
-        A_(dalloc(c, &c->mgrad, (size_t)nc * 2 * NVM));
+        A_(dalloc(c, &c->mgrad, (size_t)nc * MGS * NVM));
         A_(dalloc(c, &c->mphi, (size_t)nc * NVM));
         A_(dalloc(c, &c->Rg, (size_t)nc * NVM));
         A_(dalloc(c, &c->Dinv, (size_t)nc * 24));
@@ -1788,11 +1788,8 @@ int gsis_download_fields_async(gsis_ctx *c, double *out, int64_t len) {
 int gsis_step_async(gsis_ctx *c, int32_t mode) {
     if (!c) return GSIS_ERR_INVALID_ARG;
     if (c->sharded) return fail(c, GSIS_ERR_UNSUPPORTED, "a velocity shard steps through gsis_shard_begin/mid/end");
-    if (mode == GSIS_MODE_GSIS) {
-        if (c->dim == 3)
-            return fail(c, GSIS_ERR_UNSUPPORTED, "the synthetic equations are built for 1-D and 2-D meshes");
+    if (mode == GSIS_MODE_GSIS)
         return c->precision == GSIS_FP64 ? gsis_iteration<double>(c) : gsis_iteration<float>(c);
-    }
     if (mode != GSIS_MODE_CIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
     return c->precision == GSIS_FP64 ? cis_iteration<double>(c) : cis_iteration<float>(c);
 }
@@ -1811,8 +1808,6 @@ int gsis_step(gsis_ctx *c, int32_t mode, double *eps_out) {
 int gsis_solve(gsis_ctx *c, int32_t mode, int32_t max_outer, double tol, int32_t *iters_out, double *eps_history) {
     if (!c) return GSIS_ERR_INVALID_ARG;
     if (mode != GSIS_MODE_CIS && mode != GSIS_MODE_GSIS) return fail(c, GSIS_ERR_INVALID_ARG, "bad mode");
-    if (mode == GSIS_MODE_GSIS && c->dim == 3)
-        return fail(c, GSIS_ERR_UNSUPPORTED, "the synthetic equations are built for 1-D and 2-D meshes");
     const int n = max_outer > 0 ? max_outer : c->solver.max_outer;
     const double t = tol > 0 ? tol : c->solver.tol_outer;
     if (iters_out) *iters_out = 0;
@@ -2125,7 +2120,8 @@ extern "C" {
 int gsis_warm_start(gsis_ctx *c, int32_t n_presolve, int32_t use_mlp) {
     if (!c || n_presolve < 0) return GSIS_ERR_INVALID_ARG;
     if (c->sharded) return fail(c, GSIS_ERR_UNSUPPORTED, "the warm start runs on unsharded contexts");
-    if (c->dim == 3) return fail(c, GSIS_ERR_UNSUPPORTED, "the synthetic equations are built for 1-D and 2-D meshes");
+    if (c->dim == 3 && use_mlp)
+        return fail(c, GSIS_ERR_UNSUPPORTED, "the learned closure's features are built for 1-D and 2-D");
     if (use_mlp && (!c->mlp.p || !c->mlp.trained))
         return fail(c, GSIS_ERR_INVALID_ARG, "the learned closure has not been trained or set");
     return c->precision == GSIS_FP64 ? warm_start<double>(c, n_presolve, use_mlp != 0)

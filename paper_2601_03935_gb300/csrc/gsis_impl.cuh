@@ -194,26 +194,27 @@ __host__ __device__ inline void mix_from_A(const ModelDev &m, const double *A, d
 // ---- synthetic (macroscopic) equations, FP64 throughout (macro.cu)
 // Conservative variables W = [rho, rho u (dim), e, e_r, e_v, e_R] (nv = dim + 5) and
 // primitive variables q = [rho, u (dim), T_t, T_r, T_v, e_R] (the same count).
-constexpr int NVM = 7;         // largest nv (dim = 2)
-constexpr int NHOT = 12;       // per-face high-order terms: sigma (dim x dim), q_t, q_r, q_v, q_R (dim each)
+constexpr int NVM = 8;         // largest nv (dim = 3)
+constexpr int NHOT = 21;       // per-face high-order terms: sigma (dim x dim), q_t, q_r, q_v, q_R (dim each)
+constexpr int MGS = 3;         // stride of the synthetic equations' geometry vectors and gradients
 
 struct MacroGeom {
     int n_cells, dim, n_fi, n_bf;
     const int *fi_i, *fi_j;    // [n_fi] owner and neighbour of each interior face
-    const double *fi_n;        // [n_fi][2] unit normal, owner -> neighbour
+    const double *fi_n;        // [n_fi][MGS] unit normal, owner -> neighbour
     const double *fi_S;        // [n_fi] area
     const double *fi_dn;       // [n_fi] |n . (x_j - x_i)|
     const double *fi_dist;     // [n_fi] |x_j - x_i|
-    const double *fi_t;        // [n_fi][2] (x_j - x_i) / |x_j - x_i|
-    const double *fi_xf;       // [n_fi][2] face centroid
+    const double *fi_t;        // [n_fi][MGS] (x_j - x_i) / |x_j - x_i|
+    const double *fi_xf;       // [n_fi][MGS] face centroid
     const int *cface;          // [nc][MAXF] interior face id, or -1 - boundary face id; -1 - n_bf.. unused
     const int4 *info;          // [nc] faces, stencil size, face neighbours leading the stencil
-    const int *stn;            // [nc][MAXS]
-    const double *lsq;         // [nc][MAXS][2]
+    const int *stn;            // [nc][Lay::MAXS]
+    const double *lsq;         // [nc][Lay::MAXS][Lay::LW]
     const double *eps2;        // [nc] (K dx)^3
-    const double *vol, *dx, *xc;   // [nc], [nc], [nc][2]
+    const double *vol, *dx, *xc;   // [nc], [nc], [nc][MGS]
     const int *bf_cell, *bf_patch; // [n_bf]
-    const double *bf_n;        // [n_bf][2] outward normal
+    const double *bf_n;        // [n_bf][MGS] outward normal
     const double *bf_S;        // [n_bf]
     const double *bf_dn;       // [n_bf] |n . (x_f - x_c)|
     const int *patch_kind;     // [n_patches]: 0 wall, 1 far field, 2 mirror plane

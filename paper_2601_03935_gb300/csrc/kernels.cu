@@ -1143,9 +1143,10 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
     const Real w = (Real)om;
     constexpr int NM = n_gas_moments<DIM>();
     const Real *C = coef + (size_t)(i / MT * MT) * cf::NC;   // the tile's shift velocity
-    Real acc[NMP];
+    constexpr int NMPD = Lay<DIM>::NMP;
+    Real acc[NMPD];
 #pragma unroll
-    for (int k = 0; k < NMP; ++k) acc[k] = Real(0);
+    for (int k = 0; k < NMPD; ++k) acc[k] = Real(0);
     for (int vl = lane; vl < VCH; vl += 32) {
         const int v = chunk * VCH + vl;
         Real *fp = f + ((size_t)i * vq.n_pad + v) * 4;
@@ -1181,7 +1182,7 @@ __global__ void __launch_bounds__(VCH) k_sync_gas(int n_cells, Quad<Real> vq, Mo
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
     if (lane == 0) {
-        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMP;
+        Real *P = partial + ((size_t)i * gridDim.y + chunk) * NMPD;
 #pragma unroll
         for (int k = 0; k < NM; ++k) P[k] = acc[k];
     }
@@ -1442,7 +1443,7 @@ __global__ void __launch_bounds__(128) k_kinetic_bflux(MacroGeom g, ModelDev m, 
     const bool wall = g.patch_kind[pid] == 0;
     const int tab = g.bf_tab[b];     // >= 0: a mirror plane, entering values are the cell's mirror images
     const double *P = g.patch_state + (size_t)pid * 8;
-    const double *n = g.bf_n + (size_t)b * 2;
+    const double *n = g.bf_n + (size_t)b * MGS;
     const double T = P[4], Tr = wall ? P[4] : P[5], Tv = wall ? P[4] : P[6], TR = wall ? P[4] : P[7];
     const double Aw = pow_neg_half_dim<DIM>(2.0 * 3.14159265358979323846 * T), Bw = 0.5 / T;
     double acc[2 * NS + 1];
@@ -1971,7 +1972,8 @@ template <typename Real>
 cudaError_t launch_kinetic_bflux(cudaStream_t s, const MacroGeom &g, const ModelDev &m, const Quad<Real> &vq,
                                  const Quad<Real> &oq, const Real *f, const Real *I, double *kin_bflux, double *raw) {
     if (g.n_bf == 0) return cudaSuccess;
-    GSIS_DISPATCH_DIM(g.dim, (k_kinetic_bflux<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, f, I, kin_bflux, raw)));
+    if (raw && g.dim == 3) return cudaErrorInvalidValue;   // the shard exchange record holds 1-D/2-D sums
+    GSIS_DISPATCH_DIM3(g.dim, (k_kinetic_bflux<Real, DIM><<<g.n_bf, 128, 0, s>>>(g, m, vq, oq, f, I, kin_bflux, raw)));
     return cudaGetLastError();
 }
 
@@ -1989,7 +1991,7 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
     dim3 go((n_cells + 3) / 4, oq.n_pad / OCH);
     bool on_tc = false;
     if constexpr (std::is_same<Real, float>::value) {
-        if (tc) {
+        if (tc && dim < 3) {     // the tensor-core basis covers the 1-D and 2-D moments
             if (!scratch) return cudaErrorInvalidValue;
             float *kc = static_cast<float *>(scratch);
             const int nch = vq.n_pad / tcm::K, n_items = (n_cells + MT - 1) / MT * nch;
@@ -2005,12 +2007,12 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
         }
     }
     if (!on_tc)
-        GSIS_DISPATCH_DIM(dim, (k_sync_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, m, omega, F_new, F_half, coef,
-                                                                         f, partial)));
+        GSIS_DISPATCH_DIM3(dim, (k_sync_gas<Real, DIM><<<gg, VCH, 0, s>>>(n_cells, vq, m, omega, F_new, F_half, coef,
+                                                                          f, partial)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    GSIS_DISPATCH_DIM(dim, (k_sync_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, m, omega, F_new, F_half, I,
-                                                                        opartial)));
+    GSIS_DISPATCH_DIM3(dim, (k_sync_photon<Real, DIM><<<go, 128, 0, s>>>(n_cells, oq, m, omega, F_new, F_half, I,
+                                                                         opartial)));
     return cudaGetLastError();
 }
 

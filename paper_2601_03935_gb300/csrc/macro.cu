@@ -263,10 +263,10 @@ __global__ void k_macro_grad(MacroGeom g, ModelDev m, const MacroState *__restri
     }
     const int4 info = g.info[i];
     for (int k = 0; k < info.y; ++k) {
-        const int s = g.stn[i * MAXS + k];
+        const int s = g.stn[i * Lay<DIM>::MAXS + k];
         R qs[NQ];
         primitive<R, DIM>(W + (size_t)s * NVM, m, qs);
-        const double *C = g.lsq + ((size_t)i * MAXS + k) * 2;
+        const double *C = g.lsq + ((size_t)i * Lay<DIM>::MAXS + k) * Lay<DIM>::LW;
         for (int v = 0; v < NQ; ++v) {
             const R dq = qs[v] - qi[v];
             for (int a = 0; a < DIM; ++a) gr[a][v] += R(C[a]) * dq;
@@ -278,7 +278,7 @@ __global__ void k_macro_grad(MacroGeom g, ModelDev m, const MacroState *__restri
     }
     for (int v = 0; v < NQ; ++v) {
         qo[(size_t)i * NVM + v] = qi[v];
-        for (int a = 0; a < DIM; ++a) grad[((size_t)i * 2 + a) * NVM + v] = gr[a][v];
+        for (int a = 0; a < DIM; ++a) grad[((size_t)i * MGS + a) * NVM + v] = gr[a][v];
     }
     if constexpr (ORDER != 2) return;
     R ph[NQ];
@@ -288,7 +288,7 @@ __global__ void k_macro_grad(MacroGeom g, ModelDev m, const MacroState *__restri
         const int fid = g.cface[i * MAXF + k];
         if (fid < 0) continue;
         R d[DIM];
-        for (int a = 0; a < DIM; ++a) d[a] = R(g.fi_xf[fid * 2 + a] - g.xc[i * 2 + a]);
+        for (int a = 0; a < DIM; ++a) d[a] = R(g.fi_xf[fid * MGS + a] - g.xc[i * MGS + a]);
         for (int v = 0; v < NQ; ++v) {
             R d2 = R(0);
             for (int a = 0; a < DIM; ++a) d2 += gr[a][v] * d[a];
@@ -341,7 +341,7 @@ __device__ void face_state(const MacroGeom &g, int fid, const double *q, const d
     constexpr int NQ = DIM + 5;
     const int i = g.fi_i[fid], j = g.fi_j[fid];
     const double *qi = q + (size_t)i * NVM, *qj = q + (size_t)j * NVM;
-    const double *t = g.fi_t + (size_t)fid * 2;
+    const double *t = g.fi_t + (size_t)fid * MGS;
     const R dist = R(g.fi_dist[fid]);
     for (int v = 0; v < NQ; ++v) {
         const R qiv = R(qi[v]), qjv = R(qj[v]);
@@ -349,7 +349,7 @@ __device__ void face_state(const MacroGeom &g, int fid, const double *q, const d
         R along = R(0);
         R avg[DIM];
         for (int a = 0; a < DIM; ++a) {
-            avg[a] = R(0.5) * (R(grad[((size_t)i * 2 + a) * NVM + v]) + R(grad[((size_t)j * 2 + a) * NVM + v]));
+            avg[a] = R(0.5) * (R(grad[((size_t)i * MGS + a) * NVM + v]) + R(grad[((size_t)j * MGS + a) * NVM + v]));
             along += R(t[a]) * avg[a];
         }
         const R jump = (qjv - qiv) / dist;
@@ -364,24 +364,24 @@ __device__ void interior_flux(const MacroGeom &g, const ModelDev &m, const R (&b
     constexpr int NV = DIM + 5, E = 1 + DIM;
     const int i = g.fi_i[fid], j = g.fi_j[fid];
     R n[DIM];
-    for (int a = 0; a < DIM; ++a) n[a] = R(g.fi_n[(size_t)fid * 2 + a]);
+    for (int a = 0; a < DIM; ++a) n[a] = R(g.fi_n[(size_t)fid * MGS + a]);
     R qL[NV], qR[NV];
     for (int v = 0; v < NV; ++v) {
         qL[v] = R(q[(size_t)i * NVM + v]);
         qR[v] = R(q[(size_t)j * NVM + v]);
     }
     if (ORDER == 2) {
-        const double *xf = g.fi_xf + (size_t)fid * 2;
+        const double *xf = g.fi_xf + (size_t)fid * MGS;
         R di[DIM], dj[DIM];
         for (int a = 0; a < DIM; ++a) {
-            di[a] = R(xf[a] - g.xc[i * 2 + a]);
-            dj[a] = R(xf[a] - g.xc[j * 2 + a]);
+            di[a] = R(xf[a] - g.xc[i * MGS + a]);
+            dj[a] = R(xf[a] - g.xc[j * MGS + a]);
         }
         for (int v = 0; v < NV; ++v) {
             R dL = R(0), dR = R(0);
             for (int a = 0; a < DIM; ++a) {
-                dL += R(grad[((size_t)i * 2 + a) * NVM + v]) * di[a];
-                dR += R(grad[((size_t)j * 2 + a) * NVM + v]) * dj[a];
+                dL += R(grad[((size_t)i * MGS + a) * NVM + v]) * di[a];
+                dR += R(grad[((size_t)j * MGS + a) * NVM + v]) * dj[a];
             }
             qL[v] += R(phi[(size_t)i * NVM + v]) * dL;
             qR[v] += R(phi[(size_t)j * NVM + v]) * dR;
@@ -424,7 +424,7 @@ __device__ void farfield_flux(const MacroGeom &g, const ModelDev &m, const R (&b
         for (int a = 0; a < 3; ++a)
             for (int c = 0; c < 3; ++c) base[a][c] = base0[a][c];
     R n[DIM];
-    for (int a = 0; a < DIM; ++a) n[a] = R(g.bf_n[(size_t)b * 2 + a]);
+    for (int a = 0; a < DIM; ++a) n[a] = R(g.bf_n[(size_t)b * MGS + a]);
     const R dn = R(g.bf_dn[b]);
     R qf[DIM + 5];
     qf[0] = R(P[0]);
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
         if (threadIdx.x == 0) {
             R n[DIM], qm[NV], F[NV], un = R(0);
             for (int a = 0; a < DIM; ++a) {
-                n[a] = R(g.bf_n[(size_t)b * 2 + a]);
+                n[a] = R(g.bf_n[(size_t)b * MGS + a]);
                 un += qc[1 + a] * n[a];
             }
             for (int k = 0; k < NV; ++k) qm[k] = qc[k];
@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(128) k_macro_bflux(MacroGeom g, ModelDev m, Qu
     const double *P = g.patch_state + (size_t)g.bf_patch[b] * 8;
     R n[DIM], uw[DIM];
     for (int a = 0; a < DIM; ++a) {
-        n[a] = R(g.bf_n[(size_t)b * 2 + a]);
+        n[a] = R(g.bf_n[(size_t)b * MGS + a]);
         uw[a] = R(P[1 + a]);
     }
     const R rho = qc[0], Tt = qc[E], Tr = qc[E + 1], Tv = qc[E + 2], eR = qc[E + 3];
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(128) k_macro_residual(MacroGeom g, ModelDev m,
             const double *qo = q + (size_t)o * NVM;
             const R rf = R(0.5) * (qi[0] + R(qo[0])), Tf = R(0.5) * (qi[E] + R(qo[E]));
             R un = R(0);
-            for (int a = 0; a < DIM; ++a) un += R(0.5) * (qi[1 + a] + R(qo[1 + a])) * R(g.fi_n[(size_t)fid * 2 + a]);
+            for (int a = 0; a < DIM; ++a) un += R(0.5) * (qi[1 + a] + R(qo[1 + a])) * R(g.fi_n[(size_t)fid * MGS + a]);
             const R dn = R(g.fi_dn[fid]);
             const R gb = fabs(un) + sound_speed(Tf) + R(2) * viscosity(Tf, m) / (rf * dn);
             const R gR = R(2) * (R(1) / (R(3) * absorption(rf, m))) / dn;
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(128) k_macro_residual(MacroGeom g, ModelDev m,
             const R S = R(g.bf_S[b]);
             for (int v = 0; v < NV; ++v) Rr[v] = -R(bflux[(size_t)b * NVM + v] + hot_b[(size_t)b * NVM + v]) * S;
             R un = R(0);
-            for (int a = 0; a < DIM; ++a) un += qi[1 + a] * R(g.bf_n[(size_t)b * 2 + a]);
+            for (int a = 0; a < DIM; ++a) un += qi[1 + a] * R(g.bf_n[(size_t)b * MGS + a]);
             const R db = R(g.bf_dn[b]);
             const bool mirror = g.patch_kind[g.bf_patch[b]] == 2;
             // a mirror face: the Rusanov part only, and nothing in the e_R row
@@ -865,8 +865,8 @@ __global__ void __launch_bounds__(128) k_macro_jacobi(MacroGeom g, ModelDev m, c
         if (fid >= 0) {
             const bool own = g.fi_i[fid] == i;
             const int o = own ? g.fi_j[fid] : g.fi_i[fid];
-            double n[2] = {0.0, 0.0};
-            for (int a = 0; a < DIM; ++a) n[a] = own ? g.fi_n[(size_t)fid * 2 + a] : -g.fi_n[(size_t)fid * 2 + a];
+            double n[3] = {0.0, 0.0, 0.0};
+            for (int a = 0; a < DIM; ++a) n[a] = own ? g.fi_n[(size_t)fid * MGS + a] : -g.fi_n[(size_t)fid * MGS + a];
             const double *Wo = W + (size_t)o * NVM, *dGo = dG_in + (size_t)o * NVM;
             const double S = g.fi_S[fid];
             const double gb = gam[((size_t)i * MAXF + k) * 2], gR = gam[((size_t)i * MAXF + k) * 2 + 1];
@@ -944,8 +944,11 @@ __global__ void k_macro_mass_rescale(int nv, int n_cells, const double *__restri
         if ((dim) == 1) {                 \
             constexpr int DIM = 1;        \
             __VA_ARGS__;                  \
-        } else {                          \
+        } else if ((dim) == 2) {          \
             constexpr int DIM = 2;        \
+            __VA_ARGS__;                  \
+        } else {                          \
+            constexpr int DIM = 3;        \
             __VA_ARGS__;                  \
         }                                 \
     } while (0)

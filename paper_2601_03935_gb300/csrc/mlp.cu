@@ -160,7 +160,7 @@ __global__ void k_cell_features(MacroGeom g, ModelDev m, const double *__restric
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n_cells) return;
     const double *qi = q + (size_t)i * NVM, *r = F + (size_t)i * NF;
-    auto gr = [&](int d, int v) { return grad[((size_t)i * 2 + d) * NVM + v]; };
+    auto gr = [&](int d, int v) { return grad[((size_t)i * MGS + d) * NVM + v]; };
     auto mag = [&](int v) {
         double s = 0.0;
         for (int d = 0; d < DIM; ++d) s += gr(d, v) * gr(d, v);

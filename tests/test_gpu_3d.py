@@ -131,6 +131,70 @@ def test_3d_iterations_follow_the_oracle(case, order):
     assert_planes_close(Ig, I, 1e-9, "I after 8 iterations")
 
 
+def _gsis_inputs(wl, seed, precision):
+    M = gi.fields.smooth_random_fields(wl.mesh.cell_centroid, seed, u_scale=0.2)
+    if wl.mesh.patches[-1].kind == gi.mesh.FARFIELD:
+        M[:, 1] += 0.5 * wl.mesh.patches[-1].u[0]
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 3, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, seed + 1,
+                                       noise=0.02)
+    if precision == "fp32":
+        f, I = f.astype(np.float32).astype(np.float64), I.astype(np.float32).astype(np.float64)
+    return f, I
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_gsis_step_matches_oracle_3d(case, order, precision):
+    """One GSIS iteration (kinetic step, high-order terms, 3-D synthetic equations with a
+    fixed number of inner iterations, synchronisation) on tetrahedra: the closed box (walls
+    only, mass rescaling) and the capsule (wall and far field)."""
+    from oracle import macro as MA
+    wl = gi.workloads.with_solver(CASES[case](), precision=precision, order=order, relax_block=16, max_inner=12,
+                                  tol_inner=0.0, macro_sweeps=4, cfl_macro=200.0)
+    f, I = _gsis_inputs(wl, 71, precision)
+    ctx = create(wl)
+    try:
+        G.gsis_set_distributions(ctx, f, I)
+        eps = G.gsis_step(ctx, G.GSIS_MODE_GSIS)
+        fg, Ig = G.gsis_get_distributions(ctx, wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0])
+        rec = G.gsis_get_fields(ctx, wl.mesh.n_cells)
+    finally:
+        G.gsis_destroy(ctx)
+    geo = K.Geometry(wl.mesh)
+    fo, Io, e_o, Fo = OG.gsis_step(f, I, wl, geo, MA.Faces(geo))
+    tol = TOL[precision]
+    assert_planes_close(fg, fo, tol, "f^{k+1}")
+    assert_planes_close(Ig, Io, tol, "I^{k+1}")
+    assert_fields_close(rec, Fo, tol, 3, "moments of f^{k+1}")
+    assert abs(eps - e_o) <= (1e-4 if precision == "fp32" else 1e-9) * e_o
+
+
+def test_gsis_3d_iterations_follow_the_oracle():
+    """Four GSIS iterations on the closed box in FP64 (order 1): every eps and the final
+    distributions equal the oracle's."""
+    from oracle import macro as MA
+    wl = gi.workloads.with_solver(box162(), precision="fp64", order=1, relax_block=16, max_inner=12, tol_inner=0.0,
+                                  macro_sweeps=4, cfl_macro=200.0)
+    f, I = _gsis_inputs(wl, 72, "fp64")
+    ctx = create(wl)
+    try:
+        G.gsis_set_distributions(ctx, f, I)
+        eps_g = [G.gsis_step(ctx, G.GSIS_MODE_GSIS) for _ in range(4)]
+        fg, Ig = G.gsis_get_distributions(ctx, wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0])
+    finally:
+        G.gsis_destroy(ctx)
+    geo = K.Geometry(wl.mesh)
+    faces = MA.Faces(geo)
+    eps_o, F = [], None
+    for _ in range(4):
+        f, I, e, F = OG.gsis_step(f, I, wl, geo, faces, F)
+        eps_o.append(e)
+    assert np.allclose(eps_g, eps_o, rtol=1e-9, atol=0.0)
+    assert_planes_close(fg, f, 1e-9, "f after 4 GSIS iterations")
+    assert_planes_close(Ig, I, 1e-9, "I after 4 GSIS iterations")
+
+
 def test_3d_refuses_what_is_built_for_1d_and_2d():
     wl = gi.workloads.with_solver(box162(), precision="fp32", order=2)
     with pytest.raises(G.GsisError) as e:
@@ -138,14 +202,14 @@ def test_3d_refuses_what_is_built_for_1d_and_2d():
     assert e.value.code == G.GSIS_ERR_UNSUPPORTED
     ctx = create(wl)
     try:
-        for call in (lambda: G.gsis_step(ctx, G.GSIS_MODE_GSIS),
-                     lambda: G.gsis_solve(ctx, G.GSIS_MODE_GSIS, 2, 1e-9),
-                     lambda: G.gsis_warm_start(ctx, 1, 0),
+        for call in (lambda: G.gsis_mlp_samples(ctx, wl.mesh.n_cells),
+                     lambda: G.gsis_warm_start(ctx, 1, True),
                      lambda: G.gsis_shard_setup(ctx, wl.xi, wl.w, wl.omega, wl.wo)):
             with pytest.raises(G.GsisError) as e:
                 call()
             assert e.value.code == G.GSIS_ERR_UNSUPPORTED
         assert np.isfinite(G.gsis_step(ctx, G.GSIS_MODE_CIS))       # the context stays usable
+        assert np.isfinite(G.gsis_step(ctx, G.GSIS_MODE_GSIS))
     finally:
         G.gsis_destroy(ctx)
 
