@@ -365,6 +365,43 @@ def time_to_steady_full(stream, kn=0.01, kn_p=10.0, tol=1e-6, max_gsis=900, max_
     return out
 
 
+def time_to_steady_capsule(stream, n=12, n_v=16, Mach=3.0, tol=1e-6, max_gsis=300, max_cis=3000):
+    """Time to eps < tol on a reduced 3-D capsule (the config-4 geometry on 6 n^3 tetrahedra
+    less the body, n_v^3 velocities, 8 x 16 directions, Kn = 0.01) at Mach 3, where 16^3
+    velocities resolve the free stream, order 1, from the uniform free stream: GSIS in
+    plain FP64 and with FP32 distributions and the mixed synthetic schedule, and CIS in FP32."""
+    import torch
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import gsis as G
+    base = gi.workloads.capsule(n=n, n_v=n_v, Mach=Mach)
+    far = base.mesh.patches[1]
+
+    def run(prec, mode, mixed, nmax):
+        wl = gi.workloads.with_solver(base, precision=prec, order=1, relax_block=16, max_inner=100, n_cis_precond=10,
+                                      macro_fp32=2 if mixed else 0, venkat_K=0.01)
+        ctx = create_ctx(wl, stream.cuda_stream)
+        try:
+            G.gsis_init_fields(ctx, gi.fields.uniform_fields(wl.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            it, hist = G.gsis_solve(ctx, mode, nmax, tol)
+            dt = time.perf_counter() - t0
+        finally:
+            G.gsis_destroy(ctx)
+        return {"seconds": dt, "iterations": int(it), "final_eps": float(hist[-1]) if len(hist) else None,
+                "converged": bool(len(hist) and hist[-1] < tol)}
+
+    out = {"workload": "capsule 3-D Mach %g, %d tetrahedra, %d^3 velocities, %d directions, Kn=0.01, order 1, "
+                       "100 synthetic iterations per GSIS iteration" % (Mach, base.mesh.n_cells, n_v,
+                                                                          base.omega.shape[0]), "tol": tol}
+    out["gsis_fp64_plain"] = run("fp64", G.GSIS_MODE_GSIS, False, max_gsis)
+    out["gsis_fp32_mixed"] = run("fp32", G.GSIS_MODE_GSIS, True, max_gsis)
+    out["cis_fp32"] = run("fp32", G.GSIS_MODE_CIS, False, max_cis)
+    if out["gsis_fp32_mixed"]["converged"] and out["gsis_fp64_plain"]["converged"]:
+        out["speedup_fp32_mixed_vs_fp64_plain"] = out["gsis_fp64_plain"]["seconds"] / out["gsis_fp32_mixed"]["seconds"]
+    return out
+
+
 def normal_shock(max_gsis=300):
     """The paper's Mach-5 normal shock (FP64, order 2): CIS and GSIS outer iterations to
     eps < 2e-6 for (Z_r, Z_v) = (2.6, 26) on 200 L0 and (8, 100) on 350 L0, with the
@@ -564,8 +601,9 @@ def _stagnation_state(base):
 
 
 def _full_size_leg(stream, base, bytes_per_update, plan):
-    """CIS throughput of one full-size case, FP32, blocks of 16, for each (label, order,
-    fields, warmup, steps, limiter constant K) of ``plan``:
+    """Throughput of one full-size case, FP32, blocks of 16, for each (label, order,
+    fields, warmup, steps, limiter constant K, mode) of ``plan`` (mode "cis", or "gsis":
+    GSIS iterations with the mixed synthetic schedule):
     the state is set on the device (gsis_init_fields), then warmup and timed iterations.
     Reports updates/s and the gas sweep's fraction of HBM bandwidth per entry.  One
     context is alive at a time."""
@@ -575,22 +613,25 @@ def _full_size_leg(stream, base, bytes_per_update, plan):
     nc, V = base.mesh.n_cells, base.xi.shape[0]
     peak, kind = measured_peaks()
     out = {}
-    for label, order, M, warmup, steps, K in plan:
-        wl = gi.workloads.with_solver(base, precision="fp32", order=order, relax_block=16, venkat_K=K)
+    for label, order, M, warmup, steps, K, how in plan:
+        mode = G.GSIS_MODE_GSIS if how == "gsis" else G.GSIS_MODE_CIS
+        wl = gi.workloads.with_solver(base, precision="fp32", order=order, relax_block=16, venkat_K=K,
+                                      macro_fp32=2 if how == "gsis" else 0)
         ctx = create_ctx(wl, stream.cuda_stream)
         entry = {"order": order}
         try:
             G.gsis_init_fields(ctx, M)
             for _ in range(warmup):
-                G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+                G.gsis_step_async(ctx, mode)
             G.gsis_last_eps(ctx)
-            G.gsis_profile_enable(ctx, True)
-            G.gsis_profile_reset(ctx)
+            if how != "gsis":           # (profiling brackets would split the synthetic solve's graphs)
+                G.gsis_profile_enable(ctx, True)
+                G.gsis_profile_reset(ctx)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(steps):
-                G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
+                G.gsis_step_async(ctx, mode)
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
@@ -601,6 +642,12 @@ def _full_size_leg(stream, base, bytes_per_update, plan):
             continue
         finally:
             G.gsis_destroy(ctx)
+        if how == "gsis":
+            entry.update({"mode": "GSIS, FP32 distributions, mixed synthetic schedule, 100 inner iterations",
+                          "warmup": warmup, "steps": steps, "ms_per_gsis_iteration": ms,
+                          "value": nc * V / (ms * 1e-3), "unit": UNIT})
+            out[label] = entry
+            continue
         names = ("slopes_gas", "sweep_gas") if order == 2 else ("sweep_gas",)
         sweep = sum(prof[k][0] / max(prof[k][1], 1) for k in names)
         alg = nc * V * bytes_per_update
@@ -628,8 +675,8 @@ def full_cylinder_throughput(stream):
     base = gi.workloads.cylinder()
     far = base.mesh.patches[1]
     free = gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
-    plan = [("order2_stagnation_start", 2, _stagnation_state(base), 1, 2, 5.0),
-            ("order1_free_stream", 1, free, 3, 10, 0.01)]
+    plan = [("order2_stagnation_start", 2, _stagnation_state(base), 1, 2, 5.0, "cis"),
+            ("order1_free_stream", 1, free, 3, 10, 0.01, "cis")]
     return {"workload": "cylinder 2-D Mach 5, %d triangles, 48x48 velocities (%d), %d photon directions, FP32"
                         % (base.mesh.n_cells, base.xi.shape[0], base.omega.shape[0]),
             "note": ORDER2_NOTE, **_full_size_leg(stream, base, 32, plan)}
@@ -643,8 +690,9 @@ def capsule_throughput(stream):
     base = gi.workloads.capsule()
     far = base.mesh.patches[1]
     free = gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
-    plan = [("order2_stagnation_start", 2, _stagnation_state(base), 1, 2, 5.0),
-            ("order1_free_stream", 1, free, 3, 5, 0.01)]
+    plan = [("order2_stagnation_start", 2, _stagnation_state(base), 1, 2, 5.0, "cis"),
+            ("order1_free_stream", 1, free, 3, 5, 0.01, "cis"),
+            ("gsis_order1_stagnation_start", 1, _stagnation_state(base), 1, 2, 0.01, "gsis")]
     return {"workload": "capsule 3-D Mach 10, %d tetrahedra, 24^3 velocities (%d), %d photon directions, FP32"
                         % (base.mesh.n_cells, base.xi.shape[0], base.omega.shape[0]),
             "note": ORDER2_NOTE, **_full_size_leg(stream, base, 24, plan)}
@@ -916,6 +964,7 @@ def run_ours(args):
         line["slab_time_to_steady"] = slab_time_to_steady()
     if not args.no_tts:
         line["time_to_steady_20k"] = time_to_steady_full(stream)
+        line["time_to_steady_capsule"] = time_to_steady_capsule(stream)
     if not args.no_shock:
         line["normal_shock"] = normal_shock()
     if not args.no_cylinder:

@@ -1554,8 +1554,9 @@ __device__ __forceinline__ void finish_cell(int i, int n_chunks, int o_chunks, c
         }
     } else if constexpr (std::is_same<Real, float>::value) {
         // FP32 partials: a compensated FP32 sum (Knuth's two-sum, the rounding error of
-        // every addition carried in lo), as accurate as an FP64 sum of these few terms
-        // and off the slow FP64 pipe
+        // every addition carried in lo, lo itself summed plainly), off the slow FP64 pipe.
+        // The fields stay within 1e-5 of the FP64 oracle from 13 chunks (784 velocities)
+        // up to 216 (13 824 velocities of the 3-D capsule) in the parity tests.
         float hi[NM], lo[NM];
 #pragma unroll
         for (int k = 0; k < NM; ++k) hi[k] = lo[k] = 0.0f;
