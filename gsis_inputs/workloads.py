@@ -49,6 +49,7 @@ class SolverParams:
     macro_fp32: int = 0                  # library FP32 path: synthetic residual side in FP32
     tc_moments: int = 1                  # library FP32 path: 0 CUDA cores, 1 tensor cores in the moment/sync
                                          # passes, 2 also in the sweep epilogue
+    positivity: float = 0.0              # 0 <= theta < 1: the implicit update keeps f >= theta f_old (0: off)
 
 
 @dataclass

@@ -161,6 +161,12 @@ typedef struct {
                                    2: tensor cores in the sweep epilogue too (relaxation
                                    blocks that divide 16 cells; other blocks keep the
                                    CUDA-core epilogue).  FP64 contexts ignore it.            */
+    double positivity;          /* 0 <= theta < 1: after each kinetic sweep every value of f and
+                                   I is at least theta times its value before the sweep (a bound
+                                   on the implicit update, an extension of Section 5 that
+                                   leaves every steady state unchanged; it lets the order-2
+                                   defect correction start from impulsive hypersonic states).
+                                   0: off, the paper's scheme.                               */
 } gsis_solver_params;
 
 typedef struct gsis_ctx gsis_ctx;

@@ -327,6 +327,9 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
     Gauss-Seidel sweep inside each block of B consecutive cells (B = n_cells is the
     paper's natural-order symmetric sweep).
 
+    With wl.solver.positivity = theta > 0 every value of the result is at least theta times
+    its value in f (or I).
+
     Returns (f_new, I_new) for ``cells`` (default: all cells, in order).
     """
     mesh, model, solver = wl.mesh, wl.model, wl.solver
@@ -426,4 +429,12 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
                     if i < j < b1:
                         df[k] -= a[:, None] * df[pos[j]] / dg[k][:, None]
                         dI[k] -= aR * dI[pos[j]] / dR[k]
-    return f[cells] + df, I[cells] + dI
+    f_new, I_new = f[cells] + df, I[cells] + dI
+    theta = float(getattr(solver, "positivity", 0.0))
+    if theta > 0.0:
+        # positivity bound of the implicit update (an extension; 0 is the paper's scheme): no
+        # value falls below theta times its previous value.  At a steady state df = 0, so the
+        # fixed point is unchanged.
+        f_new = np.maximum(f_new, theta * f[cells])
+        I_new = np.maximum(I_new, theta * I[cells])
+    return f_new, I_new

@@ -197,6 +197,7 @@ Geom<Real> geom(const gsis_ctx *c) {
     g.bf_patch = c->bf_patch;
     g.bf_nrm = (const Real *)c->bf_nrm;
     g.tc_wait = c->tc_wait;
+    g.pos_theta = (Real)c->solver.positivity;
     g.err = c->err;
     g.bf_tab = c->bf_tab;
     g.refl_v = c->refl_v;
@@ -617,6 +618,7 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
         return why = "bad synthetic-equation parameters", GSIS_ERR_INVALID_ARG;
     if (!(sp->sync_relax > 0) || !(sp->sync_relax <= 1)) return why = "sync_relax must be in (0, 1]", GSIS_ERR_INVALID_ARG;
     if (sp->tc_moments < 0 || sp->tc_moments > 2) return why = "tc_moments must be 0, 1 or 2", GSIS_ERR_INVALID_ARG;
+    if (!(sp->positivity >= 0.0) || !(sp->positivity < 1.0)) return why = "positivity must be in [0, 1)", GSIS_ERR_INVALID_ARG;
     if (sp->macro_fp32 < 0 || sp->macro_fp32 > 2) return why = "macro_fp32 must be 0, 1 or 2", GSIS_ERR_INVALID_ARG;
     if (!(mp->Kn > 0) || !(mp->Kn_p > 0) || !(mp->sigma_R >= 0) || !(mp->Z_r > 0) || !(mp->Z_v > 0) ||
         !(mp->d_r >= 0) || !(mp->d_v > 0) || !(mp->d_r > 0))

@@ -96,6 +96,7 @@ struct Geom {
     const int *refl_v;         // [tables][v_pad] index of the mirror image of each velocity
     const int *refl_o;         // [tables][o_pad] index of the mirror image of each photon direction
     int tc_wait;               // polls of the first tensor-core completion wait (ERR_TIMEOUT bit on expiry)
+    Real pos_theta;            // > 0: the sweep keeps every value >= pos_theta times its previous value
     int *err;                  // device error word: bit 0 divergence, bit 1 a completion wait ran out
 };
 

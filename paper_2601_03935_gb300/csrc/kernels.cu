@@ -933,6 +933,10 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
                     Vec<float, 4> t = *reinterpret_cast<const Vec<float, 4> *>(&R[l * SV + tx]);
 #pragma unroll
                     for (int p = 0; p < 4; ++p) t.v[p] += fo.v[p];
+                    if (g.pos_theta > 0.0f) {
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) t.v[p] = fmaxf(t.v[p], g.pos_theta * fo.v[p]);
+                    }
                     vstore<float, 4>(reinterpret_cast<float *>(f_out) + idx * 4, t);
                     th[j] = t;
                 }
@@ -976,6 +980,10 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
         Vec<Real, N> t = R[l * SV + tx];
 #pragma unroll
         for (int p = 0; p < N; ++p) t.v[p] += fo.x[p];
+        if (g.pos_theta > Real(0)) {   // the positivity bound of the implicit update
+#pragma unroll
+            for (int p = 0; p < N; ++p) t.v[p] = fmax(t.v[p], g.pos_theta * fo.x[p]);
+        }
         R[l * SV + tx] = t;
         if constexpr (N == 1) {
             f_out[idx] = t.v[0];

@@ -195,6 +195,40 @@ def test_gsis_3d_iterations_follow_the_oracle():
     assert_planes_close(Ig, I, 1e-9, "I after 4 GSIS iterations")
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_positivity_bound_matches_oracle(precision):
+    """Order 2 from the impulsive Mach-3 free stream around the capsule, with the positivity
+    bound theta = 0.1 on the implicit update: one iteration, where the bound is active on
+    about a sixth of the values, equals the oracle's; five more follow its eps."""
+    wl = gi.workloads.with_solver(CASES["capsule1270"](), precision=precision, order=2, relax_block=16,
+                                  venkat_K=0.01, positivity=0.1)
+    far = wl.mesh.patches[1]
+    M = gi.fields.uniform_fields(wl.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 3, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, 0,
+                                       noise=0.0)
+    if precision == "fp32":
+        f, I = f.astype(np.float32).astype(np.float64), I.astype(np.float32).astype(np.float64)
+    _, rec1, fg, Ig, eps_g = _run(wl, f, I, steps=1)
+    F0 = K.moments(f, I, wl.xi, wl.w, wl.omega, wl.wo, 3, wl.model)
+    fo, Io = K.kinetic_sweep(f, I, wl, relax_block=16, F=F0)
+    fu, _ = K.kinetic_sweep(f, I, gi.workloads.with_solver(wl, positivity=0.0), relax_block=16, F=F0)
+    assert np.mean(fo != fu) > 0.05                                # the bound is active
+    assert np.all(fg >= 0.1 * f * (1 - 1e-6) - 1e-40)              # (FP32 subnormals round coarsely)
+    tol = TOL[precision]
+    assert_planes_close(fg, fo, tol, "f^{k+1}")
+    assert_planes_close(Ig, Io, tol, "I^{k+1}")
+    assert_fields_close(rec1, K.moments(fo, Io, wl.xi, wl.w, wl.omega, wl.wo, 3, wl.model), tol, 3, "fields")
+    if precision == "fp64":
+        _, _, fg6, _, eps6 = _run(wl, f, I, steps=6)
+        geo = K.Geometry(wl.mesh)
+        eps_o = []
+        for _ in range(6):
+            f, I, e, _ = OG.cis_step(f, I, wl, geo)
+            eps_o.append(e)
+        assert np.allclose(eps6, eps_o, rtol=1e-9, atol=0.0)
+        assert_planes_close(fg6, f, 1e-9, "f after 6 iterations")
+
+
 def test_3d_refuses_what_is_built_for_1d_and_2d():
     wl = gi.workloads.with_solver(box162(), precision="fp32", order=2)
     with pytest.raises(G.GsisError) as e:

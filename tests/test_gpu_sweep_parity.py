@@ -198,6 +198,30 @@ def test_full_size_cylinder_sampled_blocks():
     assert_planes_close(Ig[cells], Io, 1e-5, "I sampled")
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_positivity_bound_on_the_impulsive_cylinder(precision):
+    """Order 2 from the impulsive Mach-5 free stream around a cylinder with the positivity
+    bound theta = 0.1: the bound is active on many values and the iteration equals the
+    oracle's."""
+    wl = gi.workloads.with_solver(gi.workloads.cylinder(n_theta=8, n_radial=4, n_v=16, n_polar=4, n_azim=8),
+                                  precision=precision, order=2, relax_block=16, venkat_K=0.01, positivity=0.1)
+    far = wl.mesh.patches[1]
+    M = gi.fields.uniform_fields(wl.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t)
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, 2, wl.model.d_r, wl.model.d_v, wl.model.sigma_R, 0,
+                                       noise=0.0)
+    if precision == "fp32":
+        f, I = f.astype(np.float32).astype(np.float64), I.astype(np.float32).astype(np.float64)
+    _, rec1, fg, Ig, _ = _run(wl, f, I)
+    F0 = K.moments(f, I, wl.xi, wl.w, wl.omega, wl.wo, 2, wl.model)
+    fo, Io = K.kinetic_sweep(f, I, wl, relax_block=16, F=F0)
+    fu, _ = K.kinetic_sweep(f, I, gi.workloads.with_solver(wl, positivity=0.0), relax_block=16, F=F0)
+    assert np.mean(fo != fu) > 0.1
+    assert_planes_close(fg, fo, TOL[precision], "f^{k+1}")
+    assert_planes_close(Ig, Io, TOL[precision], "I^{k+1}")
+    assert_fields_close(rec1, K.moments(fo, Io, wl.xi, wl.w, wl.omega, wl.wo, 2, wl.model), TOL[precision], 2,
+                        "fields")
+
+
 def test_twenty_iterations_follow_the_oracle():
     """Twenty CIS iterations on the 8 x 8 heated-lid cavity at Kn = 1, order 2, FP64: the
     convergence measure of every iteration and the final distributions equal the oracle's
