@@ -46,9 +46,40 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "DVM cell-velocity updates/s (% HBM roofline); time-to-steady vs plain FP64 GSIS"
-# DRAM bytes (read + write) of one gas sweep on the 20 000-cell cavity, from the ncu capture
-# summarised in profiles/sweep_gas_cavity20k_order2.md; update it whenever the kernels change.
-SWEEP_TRAFFIC = {("fp32", 2): 291.0e6 + 346.2e6 + 752.5e6 + 261.4e6}
+# DRAM bytes (read + write) of one gas slope pass + sweep on the 20 000-cell cavity (FP32,
+# order 2) come from the ncu capture summarised in this file.  It records them with the
+# SHA-256 of the kernel sources the capture ran; the figure is reported only while those
+# sources are unchanged, and as null once a kernel has changed since the counters were taken.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "sweep_gas_cavity20k_order2.md")
+KERNEL_SOURCES = ("kernels.cu", "gsis_impl.cuh", "tc_moments.cuh")
+
+
+def kernel_sources_sha256(csrc=None):
+    import hashlib
+    csrc = csrc or os.path.join(ROOT, "paper_2601_03935_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def sweep_traffic(precision, order, path=TRAFFIC_FILE, csrc=None):
+    """(bytes per launch pair or None, note) from the recorded capture."""
+    import re
+    if (precision, order) != ("fp32", 2):
+        return None, "no capture of this precision and order"
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, "no capture recorded"
+    t = re.search(r"^traffic_bytes_per_launch_pair: (\d+)\s*$", text, re.M)
+    h = re.search(r"^kernel_sources_sha256: ([0-9a-f]{64})\s*$", text, re.M)
+    if not t or not h:
+        return None, "no capture recorded"
+    if h.group(1) != kernel_sources_sha256(csrc):
+        return None, "kernel sources changed since the capture"
+    return float(t.group(1)), "ncu capture of these kernel sources"
 UNIT = "updates/s"
 
 
@@ -937,6 +968,7 @@ def run_ours(args):
     m_ms = mprof["moments_only"][0] / max(mprof["moments_only"][1], 1)
     tc_on = args.precision == "fp32" and args.tc_moments >= 1
     value = world * nc * V / (ms * 1e-3)
+    traffic, traffic_note = sweep_traffic(args.precision, args.order)
     kernels = {k: {"ms_per_launch": (v[0] / v[1]) if v[1] else None, "launches": v[1],
                    "share": v[0] / max(sum(x[0] for x in prof.values()), 1e-30)} for k, v in prof.items() if v[1]}
     line = {
@@ -947,11 +979,15 @@ def run_ours(args):
         "config": config(args, wl),
         "roofline": {"kernel": "+".join(sweep_names), "bound": "hbm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
-                     "traffic": SWEEP_TRAFFIC.get((args.precision, args.order)),
+                     "traffic": traffic, "traffic_note": traffic_note,
                      "algorithmic_bytes_per_launch": alg_bytes, "ms_per_launch": avg_sweep},
         "e2e": {"value": world * nc * V / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": nc * (V * 4 + NO) * rs, "d2h_bytes_per_step": nc * G.GSIS_NF * 8},
-        "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels, "last_eps": eps,
+        "gpu_launches": launches, "clocks": clk.summary(), "kernels": kernels,
+        "kernels_note": "CUDA-event time per launch on the stream the kernel runs on, over the timed region; "
+                        "the photon slope pass and sweep run on a side stream concurrently with the gas kernels, "
+                        "so their brackets include the wait for free SMs",
+        "last_eps": eps,
         "moment_pass": {"kernel": ("k_moments_gas_tc (tcgen05, split TF32)" if tc_on else "k_moments_gas (CUDA cores)")
                         + " + k_moments_photon", "bound": "hbm", "ms_per_launch": m_ms,
                         "algorithmic_bytes_per_launch": m_bytes, "achieved": m_bytes / (m_ms * 1e-3) / 1e9,

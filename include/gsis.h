@@ -20,8 +20,10 @@
  *  - Output buffers are caller-owned host memory; their length (in elements) is
  *    passed and checked, GSIS_ERR_INVALID_ARG if too short.
  *  - One context belongs to one host thread at a time.  All device work of a
- *    context is issued on the CUDA stream given at creation (NULL: the legacy
- *    default stream); calls that return host data synchronise that stream.
+ *    context is ordered on the CUDA stream given at creation (NULL: the legacy
+ *    default stream): work the library runs on streams of its own (the photon sweep,
+ *    staged copies) starts after, and is waited for by, that stream through events.
+ *    Calls that return host data synchronise that stream.
  *  - Doubles at the boundary whatever the internal precision.
  *
  * Reduced velocity spaces: with dim in-plane velocity components (dim = spatial
@@ -382,7 +384,7 @@ int gsis_mlp_loss_grad(gsis_ctx *ctx, const float *X, const float *Y, int64_t n,
 int gsis_warm_start(gsis_ctx *ctx, int32_t n_presolve, int32_t use_mlp);
 
 /* Kernel timing.  While enabled, the library brackets each of its kernel launches with
- * CUDA events on the context stream and accumulates device time per kernel id.
+ * CUDA events on the stream it runs on and accumulates device time per kernel id.
  * gsis_profile_read fills up to n entries of names/ms/launches (arrays of length n)
  * and sets *n_out to the number of kernel ids. */
 int gsis_profile_enable(gsis_ctx *ctx, int32_t on);

@@ -48,6 +48,11 @@ struct gsis_ctx {
     void *f_stage = nullptr, *I_stage = nullptr;
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t stage_ready = nullptr, stage_free = nullptr;
+    // the photon slope pass and sweep run on side_stream, between fork_ev (recorded on the
+    // context stream after the wall densities) and join_ev (waited on before the moments
+    // are finished), concurrently with the gas kernels; created on first use
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool staged = false;
     void *coef = nullptr, *bcoef = nullptr, *partial = nullptr, *opartial = nullptr;
     void *sync_kc = nullptr;                    // FP32: per-cell synchronisation constants [nc][SYNC_KC] floats
@@ -240,20 +245,22 @@ int resolve_profile(gsis_ctx *c) {
 }
 
 // Launch bracket: counts launches and, when profiling, brackets the launch with two
-// events on the context stream (resolved later, so the stream never stalls).
+// events on the stream it is launched on (`st`, the context stream unless given; resolved
+// later, so the stream never stalls).
 template <typename F>
-int launch(gsis_ctx *c, int id, F &&fn) {
+int launch(gsis_ctx *c, int id, F &&fn, cudaStream_t st = nullptr) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!st) st = c->stream;
     if (c->prof) {
         if (take_event(c, &e0) != GSIS_OK || take_event(c, &e1) != GSIS_OK) return GSIS_ERR_CUDA;
-        CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+        CUDA_TRY(c, cudaEventRecord(e0, st));
     }
     cudaError_t e = fn();
     if (e != cudaSuccess)
         return fail(c, GSIS_ERR_CUDA, std::string("launch of ") + kKernelNames[id] + ": " + cudaGetErrorString(e));
     c->launches++;
     if (c->prof) {
-        CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+        CUDA_TRY(c, cudaEventRecord(e1, st));
         c->pending.push_back({id, e0, e1});
     }
     return GSIS_OK;
@@ -308,6 +315,27 @@ int kinetic_step(gsis_ctx *c, int nxt) {
                                          (const Real *)c->f[c->cur], c->sharded ? c->wout_g : nullptr,
                                          (Real *)c->bcoef);
     }));
+    // photon transport is independent of the gas planes: it runs on the side stream
+    if (!c->side_stream) {
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+        CUDA_TRY(c, cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    }
+    CUDA_TRY(c, cudaEventRecord(c->fork_ev, c->stream));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->side_stream, c->fork_ev, 0));
+    const cudaStream_t ps = c->side_stream;
+    if (c->order == 2) {
+        TRY(launch(c, K_SLOPE_PHOTON, [&] {
+            return launch_slopes<Real>(ps, c->dim, 1, g, oquad<Real>(c), (const Real *)c->I[c->cur],
+                                       (Real *)c->oface);
+        }, ps));
+    }
+    TRY(launch(c, K_SWEEP_PHOTON, [&] {
+        return launch_sweep_photon<Real>(ps, c->dim, c->order, g, oquad<Real>(c), (const Real *)c->coef,
+                                         (const Real *)c->bcoef, (const Real *)c->I[c->cur], (const Real *)c->oface,
+                                         (Real *)c->I[nxt], (Real *)c->opartial);
+    }, ps));
+    CUDA_TRY(c, cudaEventRecord(c->join_ev, ps));
     if (c->order == 2) {
         TRY(launch(c, K_SLOPE_GAS, [&] {
             return launch_slopes<Real>(c->stream, c->dim, 4, g, vquad<Real>(c), (const Real *)c->f[c->cur],
@@ -319,17 +347,7 @@ int kinetic_step(gsis_ctx *c, int nxt) {
                                       (const Real *)c->bcoef, (const Real *)c->f[c->cur], (const Real *)c->fface,
                                       (Real *)c->f[nxt], (Real *)c->partial);
     }));
-    if (c->order == 2) {
-        TRY(launch(c, K_SLOPE_PHOTON, [&] {
-            return launch_slopes<Real>(c->stream, c->dim, 1, g, oquad<Real>(c), (const Real *)c->I[c->cur],
-                                       (Real *)c->oface);
-        }));
-    }
-    TRY(launch(c, K_SWEEP_PHOTON, [&] {
-        return launch_sweep_photon<Real>(c->stream, c->dim, c->order, g, oquad<Real>(c), (const Real *)c->coef,
-                                         (const Real *)c->bcoef, (const Real *)c->I[c->cur], (const Real *)c->oface,
-                                         (Real *)c->I[nxt], (Real *)c->opartial);
-    }));
+    CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->join_ev, 0));
     return GSIS_OK;
 }
 
@@ -698,6 +716,12 @@ void gsis_destroy(gsis_ctx *ctx) {
         cudaStreamSynchronize(ctx->copy_stream);
         cudaStreamDestroy(ctx->copy_stream);
     }
+    if (ctx->side_stream) {
+        cudaStreamSynchronize(ctx->side_stream);
+        cudaStreamDestroy(ctx->side_stream);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     if (ctx->stage_ready) cudaEventDestroy(ctx->stage_ready);
     if (ctx->stage_free) cudaEventDestroy(ctx->stage_free);
     if (ctx->macro_exec) cudaGraphExecDestroy(ctx->macro_exec);

@@ -21,3 +21,23 @@ def test_reference_arm_prints_the_contract_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
     assert line["config"]["n_cells"] == 20000 and line["config"]["order"] == 2
+
+
+def test_recorded_traffic_is_reported_only_for_the_captured_sources(tmp_path):
+    """roofline.traffic comes from a recorded ncu capture and is null once the kernel
+    sources differ from those the capture ran."""
+    sys.path.insert(0, ROOT)
+    import bench
+    csrc = tmp_path / "csrc"
+    csrc.mkdir()
+    for name in bench.KERNEL_SOURCES:
+        (csrc / name).write_text("// " + name + "\n")
+    digest = bench.kernel_sources_sha256(str(csrc))
+    rec = tmp_path / "capture.md"
+    rec.write_text("summary\n\ntraffic_bytes_per_launch_pair: 1651000000\nkernel_sources_sha256: %s\n" % digest)
+    assert bench.sweep_traffic("fp32", 2, str(rec), str(csrc)) == (1651000000.0, "ncu capture of these kernel sources")
+    assert bench.sweep_traffic("fp64", 2, str(rec), str(csrc))[0] is None
+    (csrc / bench.KERNEL_SOURCES[0]).write_text("// changed\n")
+    t, note = bench.sweep_traffic("fp32", 2, str(rec), str(csrc))
+    assert t is None and "changed" in note
+    assert bench.sweep_traffic("fp32", 2, str(tmp_path / "missing.md"), str(csrc))[0] is None
