@@ -733,15 +733,32 @@ def capsule_probe(args):
     body), nv^3 velocities, 8 x 16 directions, FP32, order 2, from the stagnation state;
     --steps CIS iterations, then the per-kernel times of the library's own events."""
     import gsis_inputs as gi
+    n, nv = (int(x) for x in args.capsule_probe.split(","))
+    wl = gi.workloads.with_solver(gi.workloads.capsule(n=n, n_v=nv), precision="fp32", order=2, relax_block=16)
+    return _probe(args, "capsule", wl, _stagnation_state(wl))
+
+
+def cylinder_probe(args):
+    """A smaller Mach-5 cylinder for profiling: the full case's O-grid with n_theta x n_radial
+    quadrilaterals split into triangles, its 48 x 48 velocities and 96 directions, FP32, order
+    2 with the positivity bound (theta = 0.1, limiter constant 0.01) from the free stream, as
+    the full-size leg runs it; --steps CIS iterations."""
+    import gsis_inputs as gi
+    nt, nr = (int(x) for x in args.cylinder_probe.split(","))
+    base = gi.workloads.cylinder(n_theta=nt, n_radial=nr)
+    far = base.mesh.patches[1]
+    wl = gi.workloads.with_solver(base, precision="fp32", order=2, relax_block=16, venkat_K=0.01, positivity=0.1)
+    return _probe(args, "cylinder", wl, gi.fields.uniform_fields(base.mesh.n_cells, rho=far.rho, u=far.u, T=far.T_t))
+
+
+def _probe(args, name, wl, M):
     from paper_2601_03935_gb300 import build
     from paper_2601_03935_gb300 import gsis as G
     build.build()
     G.load()
-    n, nv = (int(x) for x in args.capsule_probe.split(","))
-    wl = gi.workloads.with_solver(gi.workloads.capsule(n=n, n_v=nv), precision="fp32", order=2, relax_block=16)
     ctx = create_ctx(wl, 0)
     try:
-        G.gsis_init_fields(ctx, _stagnation_state(wl))
+        G.gsis_init_fields(ctx, M)
         G.gsis_profile_enable(ctx, True)
         for _ in range(args.steps):
             G.gsis_step_async(ctx, G.GSIS_MODE_CIS)
@@ -749,7 +766,7 @@ def capsule_probe(args):
         prof = G.gsis_profile_read(ctx)
     finally:
         G.gsis_destroy(ctx)
-    print(json.dumps({"probe": "capsule", "n_cells": wl.mesh.n_cells, "n_xi": int(wl.xi.shape[0]), "last_eps": eps,
+    print(json.dumps({"probe": name, "n_cells": wl.mesh.n_cells, "n_xi": int(wl.xi.shape[0]), "last_eps": eps,
                       "ms_per_launch": {k: v[0] / v[1] for k, v in prof.items() if v[1]}}))
     return 0
 
@@ -1042,6 +1059,8 @@ def main():
     ap.add_argument("--no-cylinder", action="store_true", help="skip the Mach-5 cylinder CIS/GSIS measurement")
     ap.add_argument("--capsule-probe", default=None, metavar="N,NV",
                     help="only run a small 3-D capsule case (N^3 hexahedra, NV^3 velocities) for profiling")
+    ap.add_argument("--cylinder-probe", default=None, metavar="NT,NR",
+                    help="only run a smaller Mach-5 cylinder (NT x NR O-grid, 2 NT NR triangles) for profiling")
     ap.add_argument("--no-capsule", action="store_true",
                     help="skip the full-size 3-D capsule (tetrahedra) throughput leg")
     ap.add_argument("--no-full-cylinder", action="store_true",
@@ -1053,6 +1072,8 @@ def main():
         ap.error("--warmup must be at least 3")
     if args.capsule_probe:
         return capsule_probe(args)
+    if args.cylinder_probe:
+        return cylinder_probe(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 

@@ -83,3 +83,57 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.gsis_get_fields(None, None, 0) == G.GSIS_ERR_INVALID_ARG
     assert lib.gsis_launch_count(None) == 0
     lib.gsis_destroy(None)
+
+
+def _mesh_args(wl, **change):
+    m = wl.mesh
+    a = dict(dim=m.dim, face_owner=m.face_owner.copy(), face_nbr=m.face_nbr.copy(), face_normal=m.face_normal.copy(),
+             face_area=m.face_area.copy(), face_centroid=m.face_centroid.copy(), cell_volume=m.cell_volume.copy(),
+             cell_centroid=m.cell_centroid.copy())
+    for k, fn in change.items():
+        a[k] = fn(a[k])
+    return (a["dim"], a["face_owner"], a["face_nbr"], a["face_normal"], a["face_area"], a["face_centroid"],
+            a["cell_volume"], a["cell_centroid"], m.patches, wl.xi[:, :m.dim], wl.w, wl.omega, wl.wo, wl.model,
+            wl.solver, 0)
+
+
+def _code(args):
+    with pytest.raises(G.GsisError) as e:
+        G.gsis_create(*args)
+    return e.value.code
+
+
+def _set(i, v):
+    def fn(x):
+        x = x.copy()
+        x[i] = v
+        return x
+    return fn
+
+
+def test_bad_meshes_and_parameters_are_refused_on_the_host(lib):
+    """Malformed meshes return BAD_MESH, cells with more faces than the layout holds
+    UNSUPPORTED, and out-of-range sizes and solver parameters INVALID_ARG, all before a
+    kernel is launched (this runs without a GPU)."""
+    wl = gi.workloads.slab(n_cells=8)
+    nf = wl.mesh.n_faces
+    assert _code(_mesh_args(wl, face_owner=_set(0, 8))) == G.GSIS_ERR_BAD_MESH           # owner past the last cell
+    assert _code(_mesh_args(wl, face_owner=_set(0, -1))) == G.GSIS_ERR_BAD_MESH
+    assert _code(_mesh_args(wl, face_nbr=_set(0, 0))) == G.GSIS_ERR_BAD_MESH             # a face from a cell to itself
+    assert _code(_mesh_args(wl, face_nbr=_set(nf - 1, -1 - 7))) == G.GSIS_ERR_BAD_MESH   # a patch id with no patch
+    assert _code(_mesh_args(wl, face_area=_set(0, 0.0))) == G.GSIS_ERR_BAD_MESH
+    assert _code(_mesh_args(wl, face_normal=_set(0, 0.5))) == G.GSIS_ERR_BAD_MESH        # not a unit normal
+    assert _code(_mesh_args(wl, cell_volume=_set(3, 0.0))) == G.GSIS_ERR_BAD_MESH
+    # every face owned by cell 0 (its neighbours stay distinct): more faces than a 1-D cell holds
+    many = _mesh_args(wl, face_owner=lambda x: np.zeros_like(x),
+                      face_nbr=lambda x: np.where(x >= 0, np.arange(1, x.shape[0] + 1) % 8, x))
+    assert _code(many) in (G.GSIS_ERR_UNSUPPORTED, G.GSIS_ERR_BAD_MESH)
+    for kw in (dict(positivity=1.0), dict(positivity=-0.1), dict(sync_relax=0.0), dict(macro_fp32=3),
+               dict(tc_moments=3), dict(max_inner=0), dict(venkat_K=0.0)):
+        assert _code(_args(gi.workloads.with_solver(wl, **kw))) == G.GSIS_ERR_INVALID_ARG, kw
+    empty_v = list(_args(wl))
+    empty_v[9], empty_v[10] = wl.xi[:0, :1], wl.w[:0]
+    assert _code(empty_v) == G.GSIS_ERR_INVALID_ARG
+    empty_o = list(_args(wl))
+    empty_o[11], empty_o[12] = wl.omega[:0], wl.wo[:0]
+    assert _code(empty_o) == G.GSIS_ERR_INVALID_ARG
