@@ -40,6 +40,8 @@ class Mesh:
     cell_volume: np.ndarray
     cell_centroid: np.ndarray
     patches: list = field(default_factory=list)
+    # > 0: the domain is periodic in x with this period (centroid differences wrap)
+    period: float = 0.0
 
     @property
     def n_faces(self) -> int:
@@ -67,9 +69,10 @@ def slab_1d(n_cells: int, length: float = 1.0, patches=None) -> Mesh:
 def ring_1d(n_cells: int, length: float = 1.0) -> Mesh:
     """Uniform periodic 1-D row of cells on [0, L): the slab's interior faces plus one face
     from the last cell to the first (normal +x), so every cell has an upstream and a
-    downstream neighbour.  No boundary patches.  Cell-centre differences across that
-    face are not those of a periodic geometry, so only first-order transport (which uses
-    no centroid differences) treats the ring as periodic."""
+    downstream neighbour.  No boundary patches.  The mesh carries period = L, so that a
+    consumer that honours it takes centroid differences across that face as those of a
+    periodic domain (the minimal image); one that does not is periodic only where no
+    centroid difference enters (first-order transport)."""
     x = np.linspace(0.0, length, n_cells + 1)
     owner = list(range(n_cells - 1)) + [n_cells - 1]
     nbr = list(range(1, n_cells)) + [0]
@@ -79,7 +82,8 @@ def ring_1d(n_cells: int, length: float = 1.0) -> Mesh:
         face_owner=np.asarray(owner, np.int32), face_nbr=np.asarray(nbr, np.int32),
         face_normal=np.ones((n_cells, 1)), face_area=np.ones(n_cells),
         face_centroid=np.asarray(fc, np.float64).reshape(-1, 1),
-        cell_volume=np.diff(x), cell_centroid=(0.5 * (x[1:] + x[:-1])).reshape(-1, 1), patches=[])
+        cell_volume=np.diff(x), cell_centroid=(0.5 * (x[1:] + x[:-1])).reshape(-1, 1), patches=[],
+        period=float(length))
 
 
 def _faces_from_triangles(verts, tris, side_of_edge):

@@ -149,15 +149,24 @@ def cis_matrix(p, Kn_theta, grid=None, h=None, photons=None):
     return C
 
 
-def gsis_matrices(p, Kn_theta, grid=None):
+def gsis_matrices(p, Kn_theta, grid=None, h=None, photons=None):
     """L and R (17 x 17) of Eq. eigenfunction_gsis_matrix, with Kn = 1 and theta = Kn theta
-    along x."""
+    along x.  ``h`` and ``photons`` act on the kinetic half step only, as in cis_matrix (the
+    synthetic equations stay continuous)."""
     xi, w = grid if grid is not None else velocity_grid()
     x2 = np.sum(xi * xi, axis=1)
     th = Kn_theta
     kn, knp = 1.0, 1.0 / p.ratio
     b = knp * th
-    i0, i1 = photon_integrals(b)
+    if photons is None and h is None:
+        i0, i1 = photon_integrals(b)
+    else:
+        mu, wmu = photons if photons is not None else np.polynomial.legendre.leggauss(400)
+        mu = np.asarray(mu, np.float64)
+        if photons is None:
+            wmu = 2.0 * math.pi * wmu
+        den = 1.0 + transport_symbol(b * mu, h)
+        i0, i1 = np.sum(wmu / den), np.sum(wmu * mu / den)
     kap = math.sqrt(2.0 / math.pi) * kn / 2.0 * np.linalg.inv(p.A) @ np.diag([5.0, p.d_r, p.d_v])
     kR = knp / 3.0
     mu = math.sqrt(2.0 / math.pi) * kn
@@ -192,7 +201,7 @@ def gsis_matrices(p, Kn_theta, grid=None):
     for n in range(NM):
         e = np.zeros(NM)
         e[n] = 1.0
-        y0, y1, y2, yR = kinetic_response(p, e, th, xi)
+        y0, y1, y2, yR = kinetic_response(p, e, th, xi, h)
         col = np.zeros(NM, complex)
         # momentum: int [-i theta x (xi xi - xi^2/3 I) + mu (theta^2 xi + theta (theta . xi)/3)] y0
         for a in range(3):
@@ -215,8 +224,22 @@ def spectral_radius_cis(p, Kn_theta, grid=None, h=None, photons=None):
     return float(np.max(np.abs(np.linalg.eigvals(cis_matrix(p, Kn_theta, grid, h, photons)))))
 
 
-def spectral_radius_gsis(p, Kn_theta, grid=None):
-    L, R = gsis_matrices(p, Kn_theta, grid)
+def gsis_algorithm_matrix(p, Kn_theta, grid=None, h=None, photons=None):
+    """The GSIS step as the algorithm of Section 3 takes it (step 3, the synchronisation):
+    the synthetic equations (L alpha' = R alpha) give the next density, velocity,
+    temperatures and e_R, and the equilibria that the synchronisation adds carry no heat
+    flux, so the next heat fluxes are those of the kinetic half step, the q rows of the CIS
+    matrix.  (The eigen-equation of Section 4 takes them from the constitutive rows of L.)"""
+    L, R = gsis_matrices(p, Kn_theta, grid, h, photons)
+    G = np.linalg.solve(L, R)
+    G[QT:QV + 3] = cis_matrix(p, Kn_theta, grid, h, photons)[QT:QV + 3]
+    return G
+
+
+def spectral_radius_gsis(p, Kn_theta, grid=None, h=None, photons=None, algorithm=False):
+    if algorithm:
+        return float(np.max(np.abs(np.linalg.eigvals(gsis_algorithm_matrix(p, Kn_theta, grid, h, photons)))))
+    L, R = gsis_matrices(p, Kn_theta, grid, h, photons)
     return float(np.max(np.abs(np.linalg.eigvals(np.linalg.solve(L, R)))))
 
 

@@ -185,6 +185,7 @@ class Geometry:
                 self.cell_faces[nb].append((o, -n, S, xf.copy()))
         self.vol = mesh.cell_volume.astype(np.float64)
         self.xc = mesh.cell_centroid[:, :dim].astype(np.float64)
+        self.period = float(getattr(mesh, "period", 0.0))
         self.dx = self.vol ** (1.0 / dim)
         # Least squares: grad_i = sum_j C_ij (phi_j - phi_i) over the stencil of cell i,
         # C_ij = (sum_k d_k d_k^T)^-1 d_j, d_j = x_j - x_i.  The stencil is the face
@@ -203,13 +204,21 @@ class Geometry:
             if len(st) < dim:
                 self.lsq.append((st, np.zeros((len(st), dim))))
                 continue
-            D = self.xc[st] - self.xc[i]
+            D = self.delta(self.xc[st] - self.xc[i])
             G = D.T @ D
             scale = np.trace(G) / dim
             if np.linalg.det(G) <= 1e-10 * scale ** dim:
                 self.lsq.append((st, np.zeros((len(st), dim))))
                 continue
             self.lsq.append((st, D @ np.linalg.inv(G).T))
+
+    def delta(self, d):
+        """Difference vectors d [..., dim] between two positions of the mesh: as given, or on
+        a domain periodic in x (mesh.period > 0) the minimal image of their x component."""
+        if self.period > 0.0:
+            d = np.array(d, np.float64, copy=True)
+            d[..., 0] -= self.period * np.round(d[..., 0] / self.period)
+        return d
 
     def interior_neighbours(self, i):
         return self.face_nbrs[i]
@@ -243,8 +252,9 @@ def limited_slope(geo, i, q, K):
         if nb < 0:
             continue
         d2 = np.zeros(qi.shape)
+        dx = geo.delta(xf - geo.xc[i])
         for a in range(geo.dim):
-            d2 = d2 + grad[a] * (xf[a] - geo.xc[i, a])
+            d2 = d2 + grad[a] * dx[a]
         d1 = np.where(d2 > 0.0, dmax, dmin)
         with np.errstate(invalid="ignore", divide="ignore"):
             pf = np.where(d2 != 0.0, venkatakrishnan(d1, d2, eps2), 1.0)
@@ -364,8 +374,9 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
             cache[j] = limited_slope(geo, j, q, K)
         grad, phi = cache[j]
         d = np.zeros(q[j].shape)
+        dx = geo.delta(xf - geo.xc[j])
         for a in range(dim):
-            d = d + grad[a] * (xf[a] - geo.xc[j, a])
+            d = d + grad[a] * dx[a]
         return q[j] + phi * d
 
     V = xi.shape[0]

@@ -105,7 +105,7 @@ class Faces:
         self.bf_n = m.face_normal[~inner, :dim]
         self.bf_S = m.face_area[~inner]
         self.bf_patch = (-1 - m.face_nbr[~inner]).astype(np.int64)
-        d = geo.xc[self.j] - geo.xc[self.i]
+        d = geo.delta(geo.xc[self.j] - geo.xc[self.i])
         self.dist = np.linalg.norm(d, axis=1)
         self.t = d / self.dist[:, None]
         self.dn = np.abs(np.sum(self.n * d, axis=1))          # |n . (x_j - x_i)|
@@ -145,13 +145,13 @@ def limited_values(faces, q, g, K_venkat):
         for nb, _, _, xf in geo.cell_faces[c]:
             if nb < 0:
                 continue
-            d2 = g[c].T @ (xf - geo.xc[c])
+            d2 = g[c].T @ geo.delta(xf - geo.xc[c])
             d1 = np.where(d2 > 0.0, dmax, dmin)
             with np.errstate(invalid="ignore", divide="ignore"):
                 pf = np.where(d2 != 0.0, K.venkatakrishnan(d1, d2, eps2), 1.0)
             phi[c] = np.minimum(phi[c], pf)
-    dL = np.einsum("fdk,fd->fk", g[faces.i], faces.xf - geo.xc[faces.i])
-    dR = np.einsum("fdk,fd->fk", g[faces.j], faces.xf - geo.xc[faces.j])
+    dL = np.einsum("fdk,fd->fk", g[faces.i], geo.delta(faces.xf - geo.xc[faces.i]))
+    dR = np.einsum("fdk,fd->fk", g[faces.j], geo.delta(faces.xf - geo.xc[faces.j]))
     return q[faces.i] + phi[faces.i] * dL, q[faces.j] + phi[faces.j] * dR
 
 
@@ -299,7 +299,7 @@ def macro_boundary_flux(faces, prim, wl):
     out = np.zeros((nb, nvar(dim)))
     rho, u, T_t, T_r, T_v, e_R = (x[c] for x in prim)
     xf = geo.mesh.face_centroid[geo.mesh.face_nbr < 0, :dim]
-    dn = np.abs(np.sum(n * (xf - geo.xc[c]), axis=1))
+    dn = np.abs(np.sum(n * geo.delta(xf - geo.xc[c]), axis=1))
     for b in range(nb):
         patch = geo.mesh.patches[faces.bf_patch[b]]
         uw = np.asarray(patch.u, float)[:dim]
@@ -464,7 +464,7 @@ def boundary_gamma(faces, prim, wl):
     c, n = faces.bf_cell, faces.bf_n
     rho, u, T_t = prim[0][c], prim[1][c], prim[2][c]
     xf = geo.mesh.face_centroid[geo.mesh.face_nbr < 0, :dim]
-    db = np.abs(np.sum(n * (xf - geo.xc[c]), axis=1))
+    db = np.abs(np.sum(n * geo.delta(xf - geo.xc[c]), axis=1))
     base = np.abs(np.sum(u * n, axis=1)) + sound_speed(T_t) + 2.0 * viscosity(T_t, wl.model) / (rho * db)
     G = np.repeat(base[:, None], nvar(dim), axis=1)
     kR = 1.0 / (3.0 * mdl.absorption(rho, wl.model))

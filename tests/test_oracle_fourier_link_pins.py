@@ -149,3 +149,97 @@ def test_upwind_decay_factor_tends_to_the_continuous_one(kn_theta, ratio, sigma_
     assert 2.5 < errs[0] / errs[1] < 6.0 and 2.5 < errs[1] / errs[2] < 6.0   # first order: 4x per 4x cells
     # the discrete direction set agrees with the exact sphere integral of the paper's analysis
     assert abs(rho_c - FO.spectral_radius_cis(p, kn_theta, grid)) < 1e-6
+
+
+# ---------------------------------------------------------------------------- GSIS
+def _solve_synthetic(W0, faces, hot, wl, newton=3):
+    """W with R(W) = 0 (the synthetic equations with the high-order terms held fixed), by
+    Newton steps on a finite-difference Jacobian of the oracle's residual.  On a periodic
+    row the Jacobian is singular along the uniform states (total mass, momentum and energy
+    are not fixed by the steady equations); the least-squares step of least norm keeps
+    their totals, as the solver's point relaxation does for a single Fourier mode."""
+    from oracle import macro as MA
+    W = W0.copy()
+    n, m = W.shape
+    for _ in range(newton):
+        R0 = MA.residual(W, faces, hot, wl).ravel()
+        J = np.empty((n * m, n * m))
+        for k in range(n * m):
+            dW = np.zeros(n * m)
+            st = 1e-7 * max(1.0, abs(W.ravel()[k]))
+            dW[k] = st
+            J[:, k] = (MA.residual(W + dW.reshape(n, m), faces, hot, wl).ravel() - R0) / st
+        W = W + np.linalg.lstsq(J, -R0, rcond=1e-11)[0].reshape(n, m)
+    return W
+
+
+def _measured_gsis_map(wl, theta, eps=1e-6):
+    """One GSIS step of the oracle (Section 3) on the periodic row, with the transport and
+    the synthetic equations solved exactly: kinetic half step, moments and high-order terms
+    (macro.high_order_terms), synthetic solve, synchronisation f + f_eq(M^{k+1}) -
+    f_eq(M^{k+1/2}) (and likewise I), moments of the result."""
+    from oracle import macro as MA
+    geo = K.Geometry(wl.mesh)
+    faces = MA.Faces(geo)
+    x = wl.mesh.cell_centroid[:, 0]
+    M = _base_fields(wl.mesh.n_cells)
+    F0 = K.fields_from_record(M, wl.model.sigma_R)
+    f0 = K.equilibrium_planes(F0, wl.xi, 1, wl.model)
+    I0 = K.photon_equilibrium(F0["T_R"], wl.omega.shape[0], wl.model.sigma_R)
+    wave = np.cos(theta * x)
+    A = np.zeros((len(LONG), len(LONG)), complex)
+    nO = wl.omega.shape[0]
+    for n, comp in enumerate(LONG):
+        amps = []
+        for sgn in (1.0, -1.0):
+            F = _fields(M, wl, comp, sgn * eps * wave)
+            f, I = _exact_transport(F, wl, geo, f0, I0)
+            Fh = K.moments(f, I, wl.xi, wl.w, wl.omega, wl.wo, 1, wl.model)
+            hot = MA.high_order_terms(faces, Fh, MA.kinetic_boundary_flux(faces, f, I, wl), wl)
+            W = _solve_synthetic(MA.conservative(Fh, 1, wl.model), faces, hot, wl)
+            Fn = MA.fields_from_W(W, 1, wl.model)
+            fn = f + K.equilibrium_planes(Fn, wl.xi, 1, wl.model) - K.equilibrium_planes(Fh, wl.xi, 1, wl.model)
+            In = I + (K.photon_equilibrium(Fn["T_R"], nO, wl.model.sigma_R)
+                      - K.photon_equilibrium(Fh["T_R"], nO, wl.model.sigma_R))
+            G = K.moments(fn, In, wl.xi, wl.w, wl.omega, wl.wo, 1, wl.model)
+            amps.append(_amplitudes(G, theta, x))
+        A[:, n] = (amps[0] - amps[1]) / (2.0 * eps)
+    return A
+
+
+@pytest.mark.parametrize("kn_theta,ratio,sigma_R,sizes,max_rich", [
+    (1.0, 0.1, 0.1, (32, 64), 0.008),        # case B
+    (0.3, 1.0, 0.01, (24, 48), 0.045),       # case A
+])
+def test_gsis_iteration_tends_to_the_fourier_gsis_matrix(kn_theta, ratio, sigma_R, sizes, max_rich):
+    """The oracle's GSIS step on a periodic row (exact transport, exact synthetic solve)
+    against the Section-4 GSIS matrices (Eqs. eigenfunction_gsis, eigenfunction_gsis_S) with
+    the same velocities, directions and upwind symbol in the kinetic half step, and with the
+    heat fluxes that the algorithm's synchronisation keeps: those of the half step
+    (oracle/fourier.py, ``gsis_algorithm_matrix``).  The synthetic equations are finite
+    volume on the cells and continuous in the analysis; the Rusanov dissipation of their
+    convective flux is first order in the cell size, their central terms second order.  So
+    the difference falls at first order, and its Richardson extrapolation 2 E(2n) - E(n)
+    is small.  A 5 % slip of the viscosity or the conductivity, or the stress or a heat flux
+    dropped from the high-order terms, multiplies that extrapolated difference by 2 to 60."""
+    E, rho = {}, {}
+    for n_cells in sizes:
+        wl, p, grid, theta = _setup(kn_theta, ratio, sigma_R, n_cells)
+        h = 2.0 * math.pi / n_cells
+        ph = (wl.omega[:, 0], wl.wo)
+        A = _measured_gsis_map(wl, theta)
+        G = FO.gsis_algorithm_matrix(p, kn_theta, grid, h=h, photons=ph)[np.ix_(LONG, LONG)]
+        C = FO.cis_matrix(p, kn_theta, grid, h=h, photons=ph)[np.ix_(LONG, LONG)]
+        # the synchronisation adds equilibria only: the heat-flux rows are the CIS step's
+        assert np.abs(A[6:] - C[6:]).max() < 1e-7 * np.abs(C).max()
+        E[n_cells] = A - G
+        rho[n_cells] = (np.abs(np.linalg.eigvals(A)).max(), np.abs(np.linalg.eigvals(G)).max())
+    a, b = sizes
+    ea, eb = np.abs(E[a]).max(), np.abs(E[b]).max()
+    assert 1.5 < ea / eb < 2.4, "difference falls by %.2f per halving of the cells" % (ea / eb)
+    rich = np.abs(2.0 * E[b] - E[a]).max()
+    assert rich < max_rich, "extrapolated difference %.3e" % rich
+    # decay factors: the extrapolated discrete factor against the analysis
+    ext_A = 2.0 * rho[b][0] - rho[a][0]
+    ext_G = 2.0 * rho[b][1] - rho[a][1]
+    assert abs(ext_A - ext_G) < 2.0 * max_rich
