@@ -162,7 +162,7 @@ def create_ctx(wl, stream):
     m = wl.mesh
     return G.gsis_create(m.dim, m.face_owner, m.face_nbr, m.face_normal, m.face_area, m.face_centroid,
                          m.cell_volume, m.cell_centroid, m.patches, wl.xi, wl.w, wl.omega, wl.wo, wl.model,
-                         wl.solver, stream)
+                         wl.solver, stream, period=getattr(m, "period", 0.0))
 
 
 def initial_state(wl):

@@ -88,7 +88,14 @@ typedef struct {
  * 3-D meshes run CIS and GSIS (the synthetic equations with five conservative gas
  * variables, rho u in three components) in FP32 or FP64 with tc_moments = 0; the learned
  * closure's samples (gsis_mlp_samples, gsis_warm_start with use_mlp) and velocity shards
- * are built for 1-D and 2-D and return UNSUPPORTED on a 3-D context. */
+ * are built for 1-D and 2-D and return UNSUPPORTED on a 3-D context.
+ * Periodic domains: period[a] > 0 makes axis a periodic with that period (0: not
+ * periodic; period NULL: no axis is).  The mesh itself joins the cells across each seam
+ * by ordinary interior faces (face_nbr >= 0, one face centroid); every difference of
+ * centroids the library forms (least-squares stencils, face offsets, face distances) is
+ * then the minimal image along the periodic axes.  A periodic pair of patches is thus a
+ * seam of interior faces, and the Fourier analysis of Section 4 is posed on such a domain.
+ * Errors: INVALID_ARG (a negative or non-finite period). */
 typedef struct {
     int32_t dim;                      /* 1, 2 or 3                                      */
     int64_t n_cells, n_faces;
@@ -101,6 +108,7 @@ typedef struct {
     const double *cell_centroid;      /* [n_cells][dim]       */
     int32_t n_patches;
     const gsis_patch *patches;        /* [n_patches]          */
+    const double *period;             /* [dim] or NULL (see below) */
 } gsis_mesh;
 
 /* Discrete velocities xi [n][dim] and weights w [n]: sum_i w_i phi(xi_i) approximates

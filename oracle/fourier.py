@@ -16,7 +16,10 @@ with h = theta dx, which tends to i a xi_x as h -> 0 (``transport_symbol``).  Wi
 ``h`` given, ``cis_matrix`` uses that symbol for the gas and the photons; with the solver's
 own velocity nodes (``velocity_grid(x_nodes=...)``) and photon directions it is the
 iteration matrix of the discrete-velocity, finite-volume CIS step with exact transport
-(tests/test_oracle_fourier_link_pins.py).
+(tests/test_oracle_fourier_link_pins.py).  ``gsis_matrices`` takes the same options for
+its kinetic half step; ``gsis_algorithm_matrix`` is the GSIS step with the heat fluxes
+that the algorithm's synchronisation keeps, which the oracle's GSIS step on a periodic row
+approaches at first order in the cell size (the same test file).
 
 Velocity integrals: the kinetic responses are (polynomial x Gaussian) / (1 + i a xi_x)
 with a = sqrt(2/pi) Kn theta.  They are evaluated on a tensor grid (dense trapezoid in

@@ -86,7 +86,7 @@ struct gsis_ctx {
     int tc_wait = 1 << 22;       // polls of the first tensor-core completion wait (gsis_set_wait_limit)
     int *m_fi_i = nullptr, *m_fi_j = nullptr, *m_cface = nullptr, *m_pkind = nullptr;
     double *m_fi_n = nullptr, *m_fi_S = nullptr, *m_fi_dn = nullptr, *m_fi_dist = nullptr, *m_fi_t = nullptr,
-           *m_fi_xf = nullptr, *m_lsq = nullptr, *m_eps2 = nullptr, *m_xc = nullptr, *m_bf_n = nullptr,
+           *m_fi_dx = nullptr, *m_lsq = nullptr, *m_eps2 = nullptr, *m_bf_n = nullptr,
            *m_bf_S = nullptr, *m_bf_dn = nullptr, *m_pstate = nullptr;
     double *vqd_x = nullptr, *vqd_w = nullptr, *oqd_x = nullptr, *oqd_w = nullptr;
     double *W[2] = {nullptr, nullptr}, *mq = nullptr, *mgrad = nullptr, *mphi = nullptr, *Rg = nullptr,
@@ -620,6 +620,10 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
         !m->cell_centroid)
         return why = "null mesh array", GSIS_ERR_INVALID_ARG;
     if (m->n_patches < 0 || (m->n_patches > 0 && !m->patches)) return why = "bad patches", GSIS_ERR_INVALID_ARG;
+    if (m->period)
+        for (int a = 0; a < m->dim; ++a)
+            if (!(m->period[a] >= 0.0) || !std::isfinite(m->period[a]))
+                return why = "periods must be finite and non-negative", GSIS_ERR_INVALID_ARG;
     if (vq->n <= 0 || !vq->xi || !vq->w) return why = "bad velocity quadrature", GSIS_ERR_INVALID_ARG;
     if (pq->n <= 0 || !pq->omega || !pq->w) return why = "bad photon quadrature", GSIS_ERR_INVALID_ARG;
     if (sp->precision != GSIS_FP32 && sp->precision != GSIS_FP64) return why = "bad precision", GSIS_ERR_INVALID_ARG;
@@ -794,6 +798,12 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         std::memcpy(md.Mix, Mx, sizeof(Mx));
     }
 
+    // periodic axes: a centroid difference across a seam is the minimal image
+    double per[3] = {0.0, 0.0, 0.0};
+    if (m->period)
+        for (int a = 0; a < dim; ++a) per[a] = m->period[a];
+    auto wrap = [&](double d, int a) { return per[a] > 0.0 ? d - per[a] * std::nearbyint(d / per[a]) : d; };
+
     // ---- connectivity: per cell up to MAXF faces (outward normal, neighbour)
     const int64_t nc = m->n_cells, nfc = m->n_faces;
     std::vector<int> nf(nc, 0), nbr(nc * MAXF, 0), bf_cell, bf_patch;
@@ -818,7 +828,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             if (!(V > 0)) return bail(GSIS_ERR_BAD_MESH);
             for (int a = 0; a < dim; ++a) {
                 nrm[(cell * MAXF + k) * 3 + a] = sg * m->face_normal[f * dim + a];
-                dxf[(cell * MAXF + k) * 3 + a] = m->face_centroid[f * dim + a] - m->cell_centroid[cell * dim + a];
+                dxf[(cell * MAXF + k) * 3 + a] = wrap(m->face_centroid[f * dim + a] - m->cell_centroid[cell * dim + a], a);
             }
             sv[cell * MAXF + k] = S / V;
             face_of[cell * MAXF + k] = f;
@@ -826,7 +836,8 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
                 const int other = sides[1 - s];
                 nbr[cell * MAXF + k] = other;
                 for (int a = 0; a < dim; ++a)
-                    dxn[(cell * MAXF + k) * 3 + a] = m->face_centroid[f * dim + a] - m->cell_centroid[other * dim + a];
+                    dxn[(cell * MAXF + k) * 3 + a] =
+                        wrap(m->face_centroid[f * dim + a] - m->cell_centroid[other * dim + a], a);
             } else {
                 const int b = (int)bf_cell.size();
                 nbr[cell * MAXF + k] = -1 - b;
@@ -899,7 +910,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         double G[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
         for (int j : st) {
             double d[3] = {0, 0, 0};
-            for (int a = 0; a < dim; ++a) d[a] = m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a];
+            for (int a = 0; a < dim; ++a) d[a] = wrap(m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a], a);
             for (int a = 0; a < dim; ++a)
                 for (int b = 0; b < dim; ++b) G[a][b] += d[a] * d[b];
         }
@@ -936,7 +947,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         for (size_t k = 0; k < st.size(); ++k) {
             const int j = st[k];
             double d[3] = {0, 0, 0};
-            for (int a = 0; a < dim; ++a) d[a] = m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a];
+            for (int a = 0; a < dim; ++a) d[a] = wrap(m->cell_centroid[j * dim + a] - m->cell_centroid[i * dim + a], a);
             for (int a = 0; a < dim; ++a) {
                 double s = 0.0;
                 for (int b = 0; b < dim; ++b) s += Gi[a][b] * d[b];
@@ -984,7 +995,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
     // ---- synthetic-equation geometry: interior faces (owner -> neighbour), the cell -> face
     // map in the cell's face order, boundary faces, FP64 quadratures and patch states
     std::vector<int> fi_i, fi_j, cface(nc * MAXF, 0), mpk(std::max(m->n_patches, 1), 0);
-    std::vector<double> fi_n, fi_S, fi_dn, fi_dist, fi_t, fi_xf, mxc(nc * MGS, 0.0), mbn, mbS, mbdn,
+    std::vector<double> fi_n, fi_S, fi_dn, fi_dist, fi_t, fi_dx, mbn, mbS, mbdn,
         mps(8 * std::max(m->n_patches, 1), 0.0);
     {
         std::vector<int> id_of(nfc, -1);
@@ -996,7 +1007,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             fi_j.push_back(nb);
             double d[3] = {0, 0, 0}, dn = 0.0, dd = 0.0;
             for (int a = 0; a < dim; ++a) {
-                d[a] = m->cell_centroid[nb * dim + a] - m->cell_centroid[o * dim + a];
+                d[a] = wrap(m->cell_centroid[nb * dim + a] - m->cell_centroid[o * dim + a], a);
                 dn += m->face_normal[f * dim + a] * d[a];
                 dd += d[a] * d[a];
             }
@@ -1004,14 +1015,17 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
             for (int a = 0; a < MGS; ++a) {
                 fi_n.push_back(a < dim ? m->face_normal[f * dim + a] : 0.0);
                 fi_t.push_back(d[a] / dd);
-                fi_xf.push_back(a < dim ? m->face_centroid[f * dim + a] : 0.0);
             }
+            for (int s = 0; s < 2; ++s)
+                for (int a = 0; a < MGS; ++a)
+                    fi_dx.push_back(a < dim ? wrap(m->face_centroid[f * dim + a] -
+                                                   m->cell_centroid[(s == 0 ? o : nb) * dim + a], a)
+                                            : 0.0);
             fi_S.push_back(m->face_area[f]);
             fi_dn.push_back(std::fabs(dn));
             fi_dist.push_back(dd);
         }
         for (int64_t i = 0; i < nc; ++i) {
-            for (int a = 0; a < dim; ++a) mxc[i * MGS + a] = m->cell_centroid[i * dim + a];
             for (int k = 0; k < MAXF; ++k) {
                 if (k >= nf[i]) { cface[i * MAXF + k] = -1 - std::max(c->n_bf, 1); continue; }
                 const int j = nbr[i * MAXF + k];
@@ -1031,7 +1045,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
                 double dn = 0.0;
                 for (int a = 0; a < dim; ++a) {
                     mbn[b * MGS + a] = m->face_normal[f * dim + a];
-                    dn += m->face_normal[f * dim + a] * (m->face_centroid[f * dim + a] - m->cell_centroid[i * dim + a]);
+                    dn += m->face_normal[f * dim + a] * wrap(m->face_centroid[f * dim + a] - m->cell_centroid[i * dim + a], a);
                 }
                 mbS[b] = m->face_area[f];
                 mbdn[b] = std::fabs(dn);
@@ -1045,7 +1059,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         }
         if (fi_i.empty()) {   // keep every device array non-empty
             fi_i.push_back(0); fi_j.push_back(0); fi_S.push_back(0.0); fi_dn.push_back(1.0); fi_dist.push_back(1.0);
-            for (int a = 0; a < MGS; ++a) { fi_n.push_back(0.0); fi_t.push_back(0.0); fi_xf.push_back(0.0); }
+            for (int a = 0; a < MGS; ++a) { fi_n.push_back(0.0); fi_t.push_back(0.0); fi_dx.push_back(0.0); fi_dx.push_back(0.0); }
         }
     }
     const int n_fi = (int)std::count_if(fi_S.begin(), fi_S.end(), [](double x) { return x > 0.0; });
@@ -1106,10 +1120,9 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         A_(dalloc(c, &c->m_fi_dn, nfi1));
         A_(dalloc(c, &c->m_fi_dist, nfi1));
         A_(dalloc(c, &c->m_fi_t, nfi1 * MGS));
-        A_(dalloc(c, &c->m_fi_xf, nfi1 * MGS));
+        A_(dalloc(c, &c->m_fi_dx, nfi1 * 2 * MGS));
         A_(dalloc(c, &c->m_lsq, lsq.size()));
         A_(dalloc(c, &c->m_eps2, (size_t)nc));
-        A_(dalloc(c, &c->m_xc, (size_t)nc * MGS));
         A_(dalloc(c, &c->m_bf_n, nbf1 * MGS));
         A_(dalloc(c, &c->m_bf_S, nbf1));
         A_(dalloc(c, &c->m_bf_dn, nbf1));
@@ -1146,10 +1159,9 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         A_(upload(c, c->m_fi_dn, fi_dn));
         A_(upload(c, c->m_fi_dist, fi_dist));
         A_(upload(c, c->m_fi_t, fi_t));
-        A_(upload(c, c->m_fi_xf, fi_xf));
+        A_(upload(c, c->m_fi_dx, fi_dx));
         A_(upload(c, c->m_lsq, lsq));
         A_(upload(c, c->m_eps2, eps2));
-        A_(upload(c, c->m_xc, mxc));
         A_(upload(c, c->m_bf_n, mbn));
         A_(upload(c, c->m_bf_S, mbS));
         A_(upload(c, c->m_bf_dn, mbdn));
@@ -1170,7 +1182,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         G.fi_dn = c->m_fi_dn;
         G.fi_dist = c->m_fi_dist;
         G.fi_t = c->m_fi_t;
-        G.fi_xf = c->m_fi_xf;
+        G.fi_dx = c->m_fi_dx;
         G.cface = c->m_cface;
         G.info = c->g_info;
         G.stn = c->g_stn;
@@ -1178,7 +1190,6 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         G.eps2 = c->m_eps2;
         G.vol = c->vol;
         G.dx = c->cell_dx;
-        G.xc = c->m_xc;
         G.bf_cell = c->bf_cell;
         G.bf_patch = c->bf_patch;
         G.bf_n = c->m_bf_n;

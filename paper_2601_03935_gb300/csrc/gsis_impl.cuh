@@ -207,13 +207,14 @@ struct MacroGeom {
     const double *fi_dn;       // [n_fi] |n . (x_j - x_i)|
     const double *fi_dist;     // [n_fi] |x_j - x_i|
     const double *fi_t;        // [n_fi][MGS] (x_j - x_i) / |x_j - x_i|
-    const double *fi_xf;       // [n_fi][MGS] face centroid
+    const double *fi_dx;       // [n_fi][2][MGS] face centroid - owner centroid, - neighbour centroid
+                               // (on a periodic axis the minimal image)
     const int *cface;          // [nc][MAXF] interior face id, or -1 - boundary face id; -1 - n_bf.. unused
     const int4 *info;          // [nc] faces, stencil size, face neighbours leading the stencil
     const int *stn;            // [nc][Lay::MAXS]
     const double *lsq;         // [nc][Lay::MAXS][Lay::LW]
     const double *eps2;        // [nc] (K dx)^3
-    const double *vol, *dx, *xc;   // [nc], [nc], [nc][MGS]
+    const double *vol, *dx;    // [nc], [nc]
     const int *bf_cell, *bf_patch; // [n_bf]
     const double *bf_n;        // [n_bf][MGS] outward normal
     const double *bf_S;        // [n_bf]

@@ -288,7 +288,8 @@ __global__ void k_macro_grad(MacroGeom g, ModelDev m, const MacroState *__restri
         const int fid = g.cface[i * MAXF + k];
         if (fid < 0) continue;
         R d[DIM];
-        for (int a = 0; a < DIM; ++a) d[a] = R(g.fi_xf[fid * MGS + a] - g.xc[i * MGS + a]);
+        const double *dxf = g.fi_dx + ((size_t)fid * 2 + (g.fi_i[fid] == i ? 0 : 1)) * MGS;
+        for (int a = 0; a < DIM; ++a) d[a] = R(dxf[a]);
         for (int v = 0; v < NQ; ++v) {
             R d2 = R(0);
             for (int a = 0; a < DIM; ++a) d2 += gr[a][v] * d[a];
@@ -371,11 +372,11 @@ __device__ void interior_flux(const MacroGeom &g, const ModelDev &m, const R (&b
         qR[v] = R(q[(size_t)j * NVM + v]);
     }
     if (ORDER == 2) {
-        const double *xf = g.fi_xf + (size_t)fid * MGS;
+        const double *dxf = g.fi_dx + (size_t)fid * 2 * MGS;
         R di[DIM], dj[DIM];
         for (int a = 0; a < DIM; ++a) {
-            di[a] = R(xf[a] - g.xc[i * MGS + a]);
-            dj[a] = R(xf[a] - g.xc[j * MGS + a]);
+            di[a] = R(dxf[a]);
+            dj[a] = R(dxf[MGS + a]);
         }
         for (int v = 0; v < NV; ++v) {
             R dL = R(0), dR = R(0);

@@ -42,7 +42,7 @@ class gsis_mesh(C.Structure):
     _fields_ = [("dim", C.c_int32), ("n_cells", C.c_int64), ("n_faces", C.c_int64),
                 ("face_owner", _ip), ("face_nbr", _ip), ("face_normal", _dp), ("face_area", _dp),
                 ("face_centroid", _dp), ("cell_volume", _dp), ("cell_centroid", _dp),
-                ("n_patches", C.c_int32), ("patches", C.POINTER(gsis_patch))]
+                ("n_patches", C.c_int32), ("patches", C.POINTER(gsis_patch)), ("period", _dp)]
 
 
 class gsis_velocity_quad(C.Structure):
@@ -164,10 +164,11 @@ class _Keep:
 
 
 def gsis_create(dim, face_owner, face_nbr, face_normal, face_area, face_centroid, cell_volume, cell_centroid,
-                patches, xi, w, omega, wo, model, solver, stream=0):
+                patches, xi, w, omega, wo, model, solver, stream=0, period=None):
     """Create a context.  ``patches`` is a list of dicts/objects with kind, rho, u, T_t, T_r, T_v, T_R;
     ``model`` and ``solver`` are objects with the fields of gsis_model_params/gsis_solver_params
-    (precision as "fp32"/"fp64").  ``stream`` is a cudaStream_t as an int (0 = default)."""
+    (precision as "fp32"/"fp64").  ``stream`` is a cudaStream_t as an int (0 = default).
+    ``period``: None, a number (the period of x) or dim numbers (0: not periodic)."""
     lib = load()
     k = _Keep()
     k.owner = np.ascontiguousarray(face_owner, np.int32)
@@ -185,8 +186,14 @@ def gsis_create(dim, face_owner, face_nbr, face_normal, face_area, face_centroid
         pa[i].T_t, pa[i].T_r = float(g("T_t", 1.0)), float(g("T_r", 1.0))
         pa[i].T_v, pa[i].T_R = float(g("T_v", 1.0)), float(g("T_R", 1.0))
     k.pa = pa
+    k.per = None
+    if period is not None and np.any(np.asarray(period, np.float64) != 0.0):
+        k.per = np.zeros(dim)
+        p_ = np.atleast_1d(np.asarray(period, np.float64))
+        k.per[:p_.shape[0]] = p_[:dim]
     mesh = gsis_mesh(dim, cell_volume.shape[0], k.owner.shape[0], _ptr(k.owner, C.c_int32), _ptr(k.nbr, C.c_int32),
-                     _ptr(k.normal), _ptr(k.area), _ptr(k.fc), _ptr(k.vol), _ptr(k.cc), len(patches), pa)
+                     _ptr(k.normal), _ptr(k.area), _ptr(k.fc), _ptr(k.vol), _ptr(k.cc), len(patches), pa,
+                     None if k.per is None else _ptr(k.per))
     k.xi, k.w = _d(xi), _d(w)
     k.om, k.wo = _d(omega), _d(wo)
     vq = gsis_velocity_quad(k.w.shape[0], _ptr(k.xi), _ptr(k.w))

@@ -72,7 +72,8 @@ class VelocityShard:
         self.ctx = G.gsis_create(dim, mesh.face_owner, mesh.face_nbr, mesh.face_normal, mesh.face_area,
                                  mesh.face_centroid, mesh.cell_volume, mesh.cell_centroid, mesh.patches,
                                  xi[self.lo:self.hi], np.asarray(w)[self.lo:self.hi], np.asarray(omega)[self.olo:self.ohi],
-                                 np.asarray(wo)[self.olo:self.ohi], model, solver, stream)
+                                 np.asarray(wo)[self.olo:self.ohi], model, solver, stream,
+                                 period=getattr(mesh, "period", 0.0))
         try:
             G.gsis_shard_setup(self.ctx, xi, w, omega, wo)
             ptr, n = G.gsis_shard_buffer(self.ctx)

@@ -8,7 +8,7 @@ def create(wl, stream=0):
     m = wl.mesh
     return G.gsis_create(m.dim, m.face_owner, m.face_nbr, m.face_normal, m.face_area, m.face_centroid,
                          m.cell_volume, m.cell_centroid, m.patches, wl.xi[:, :m.dim], wl.w, wl.omega, wl.wo,
-                         wl.model, wl.solver, stream)
+                         wl.model, wl.solver, stream, period=getattr(m, "period", 0.0))
 
 
 def assert_planes_close(got, ref, rtol, what=""):

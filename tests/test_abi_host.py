@@ -134,6 +134,9 @@ def test_bad_meshes_and_parameters_are_refused_on_the_host(lib):
     empty_v = list(_args(wl))
     empty_v[9], empty_v[10] = wl.xi[:0, :1], wl.w[:0]
     assert _code(empty_v) == G.GSIS_ERR_INVALID_ARG
+    with pytest.raises(G.GsisError) as e:
+        G.gsis_create(*_args(wl), 0, period=-1.0)
+    assert e.value.code == G.GSIS_ERR_INVALID_ARG
     empty_o = list(_args(wl))
     empty_o[11], empty_o[12] = wl.omega[:0], wl.wo[:0]
     assert _code(empty_o) == G.GSIS_ERR_INVALID_ARG
