@@ -178,6 +178,32 @@ def cavity_triangles(n_side: int, seed: int = 0, jitter: float = 0.2, flip_p: fl
                 patches=list(patches))
 
 
+def channel_triangles(n_side: int, seed: int = 0, jitter: float = 0.2, flip_p: float = 0.5,
+                      patches=None) -> Mesh:
+    """The unit square of ``cavity_triangles`` made periodic in x (period 1): its left and
+    right boundary edges (whose vertices are not jittered, so they pair by height) become
+    interior faces from the cell at x = 1 to the cell at x = 0, with the right edge's
+    normal (+x) and centroid.  Patches: 0 bottom, 1 top."""
+    m = cavity_triangles(n_side, seed=seed, jitter=jitter, flip_p=flip_p,
+                         patches=[Patch(WALL), Patch(WALL), Patch(WALL), Patch(WALL)])
+    right = np.where(m.face_nbr == -1 - 1)[0]
+    left = np.where(m.face_nbr == -1 - 3)[0]
+    by_y = {round(float(m.face_centroid[f, 1]), 9): f for f in left}
+    owner, nbr = m.face_owner.copy(), m.face_nbr.copy()
+    keep = np.ones(m.n_faces, bool)
+    for f in right:
+        g = by_y[round(float(m.face_centroid[f, 1]), 9)]
+        nbr[f] = owner[g]               # right cell -> left cell across the seam
+        keep[g] = False
+    nbr[nbr == -1 - 2] = -1 - 1         # top wall becomes patch 1
+    if patches is None:
+        patches = [Patch(WALL, T_t=1.0), Patch(WALL, u=(0.2, 0.0, 0.0), T_t=1.0)]
+    return Mesh(dim=2, n_cells=m.n_cells, face_owner=owner[keep], face_nbr=nbr[keep],
+                face_normal=m.face_normal[keep], face_area=m.face_area[keep],
+                face_centroid=m.face_centroid[keep], cell_volume=m.cell_volume,
+                cell_centroid=m.cell_centroid, patches=list(patches), period=1.0)
+
+
 def cylinder_ogrid(n_theta: int, n_radial: int, seed: int = 1, r_body: float = 0.5,
                    r_outer: float = 3.0, stretch: float = 3.0, patches=None) -> Mesh:
     """Triangulated O-grid around a circular cylinder (diameter 1, outer diameter 6).

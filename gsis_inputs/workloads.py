@@ -106,6 +106,18 @@ def cavity(n_side: int = 100, n_v: int = 28, n_polar: int = 8, n_azim: int = 8, 
                     ModelParams(Kn=Kn, Kn_p=Kn_p, sigma_R=sigma_R))
 
 
+def couette(n_side: int = 8, n_v: int = 16, n_polar: int = 4, n_azim: int = 8, Kn: float = 0.1,
+            Kn_p: float = 1.0, sigma_R: float = 0.005, u_wall: float = 0.2, seed: int = 0) -> Workload:
+    """2-D planar Couette flow: the unit square periodic in x (``channel_triangles``)
+    between a wall at rest (bottom, T = 1) and a wall moving at u_wall along x (top, T = 1);
+    n_v x n_v trapezoid velocities on +-(|u_wall| + 5)."""
+    m = _mesh.channel_triangles(n_side, seed=seed, patches=[
+        _mesh.Patch(_mesh.WALL, T_t=1.0), _mesh.Patch(_mesh.WALL, u=(u_wall, 0.0, 0.0), T_t=1.0)])
+    xi, w = _q.trapezoid_nd(n_v, abs(u_wall) + 5.0, 2)
+    om, wo = _q.photon_product(n_polar, n_azim)
+    return Workload("couette%d" % m.n_cells, m, xi, w, om, wo, ModelParams(Kn=Kn, Kn_p=Kn_p, sigma_R=sigma_R))
+
+
 def cylinder(n_theta: int = 200, n_radial: int = 100, n_v: int = 48, n_polar: int = 8,
              n_azim: int = 12, Mach: float = 5.0, T_inf: float = 0.5, Kn: float = 0.01,
              Kn_p: float = 1000.0, sigma_R: float = 0.1, seed: int = 1) -> Workload:

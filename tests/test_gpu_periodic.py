@@ -113,3 +113,59 @@ def test_the_period_changes_the_second_order_path(mode):
         assert_fields_close(rec, Fo, 1e-10, wl.dim, "fields")
         out[periodic] = fg
     assert np.abs(out[True] - out[False]).max() > 1e-6 * np.abs(out[True]).max()
+
+
+def _couette(order, precision):
+    wl = gi.workloads.couette(n_side=6, n_v=12, Kn=0.1)
+    return gi.workloads.with_solver(wl, precision=precision, order=order, relax_block=16, max_inner=12,
+                                    tol_inner=0.0, macro_sweeps=4, cfl_macro=200.0)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("mode", ["cis", "gsis"])
+def test_periodic_channel_matches_oracle(mode, order):
+    """2-D: planar Couette flow in the unit square periodic in x (72 triangles, the seam
+    faces joining cells at x = 1 and x = 0), FP64, one iteration against the oracle."""
+    md = G.GSIS_MODE_GSIS if mode == "gsis" else G.GSIS_MODE_CIS
+    wl = _couette(order, "fp64")
+    M = gi.fields.uniform_fields(wl.mesh.n_cells)
+    y = wl.mesh.cell_centroid[:, 1]
+    x = wl.mesh.cell_centroid[:, 0]
+    M[:, 1] = 0.2 * y + 0.03 * np.sin(2 * math.pi * x)
+    M[:, 0] = 1.0 + 0.05 * np.cos(2 * math.pi * x) * np.sin(math.pi * y)
+    f, I = gi.fields.noisy_equilibrium(M, wl.xi, wl.omega, wl.dim, wl.model.d_r, wl.model.d_v,
+                                       wl.model.sigma_R, 9, noise=0.02)
+    fg, Ig, rec, eps = _gpu(wl, f, I, md)
+    fo, Io, eo, Fo = _oracle(wl, f, I, md)
+    assert_planes_close(fg, fo, 1e-10, "f")
+    assert_planes_close(Ig, Io, 1e-10, "I")
+    assert_fields_close(rec, Fo, 1e-10, wl.dim, "fields")
+    assert abs(eps - eo) <= 1e-10 * abs(eo)
+
+
+def test_steady_couette_flow_has_uniform_shear_stress():
+    """At the steady state of planar Couette flow the x-momentum flux through any plane
+    y = const is the same (the shear stress sigma_xy is uniform) and there is no mean flow
+    across the channel; GSIS in FP64 to eps < 1e-9 on the 12 x 12 channel (288 cells)."""
+    wl = gi.workloads.with_solver(gi.workloads.couette(n_side=12, n_v=16, Kn=0.1), precision="fp64", order=2,
+                                  relax_block=16, n_cis_precond=10, venkat_K=1.0)
+    ctx = create(wl)
+    try:
+        G.gsis_init_fields(ctx, gi.fields.uniform_fields(wl.mesh.n_cells))
+        it, hist = G.gsis_solve(ctx, G.GSIS_MODE_GSIS, 400, 1e-9)
+        rec = G.gsis_get_fields(ctx, wl.mesh.n_cells)
+    finally:
+        G.gsis_destroy(ctx)
+    assert hist[-1] < 1e-9, "eps %.2e after %d iterations" % (hist[-1], it)
+    y, vol = wl.mesh.cell_centroid[:, 1], wl.mesh.cell_volume
+    sxy = rec[:, 23]
+    mean = np.sum(sxy * vol) / vol.sum()
+    # the wall drags: sigma_xy = -mu du/dy < 0 for the lid moving along +x
+    assert mean < 0.0
+    # cells away from the walls, where the triangulation's face-flux errors are smallest
+    core = (y > 0.2) & (y < 0.8)
+    assert np.abs(sxy[core] - mean).max() < 0.05 * abs(mean)
+    # no net flow across the channel: per cell u_y is of the triangulation's discretization
+    # error (about 1e-4 of the wall speed on this mesh), the volume sum smaller still
+    assert abs(np.sum(rec[:, 0] * rec[:, 2] * vol)) < 1e-4 * 0.2
+    assert abs(np.sum(rec[:, 0] * vol) - 1.0) < 1e-9

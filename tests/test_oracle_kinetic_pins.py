@@ -64,7 +64,9 @@ def test_photon_product_sums():
 
 @pytest.mark.parametrize("mk", [lambda: gi.mesh.cavity_triangles(12, seed=5),
                                 lambda: gi.mesh.slab_1d(10),
-                                lambda: gi.mesh.cylinder_ogrid(24, 8)])
+                                lambda: gi.mesh.cylinder_ogrid(24, 8),
+                                lambda: gi.mesh.channel_triangles(8, seed=3),
+                                lambda: gi.mesh.ring_1d(12, 3.0)])
 def test_mesh_closure(mk):
     m = mk()
     acc = np.zeros((m.n_cells, m.dim))
@@ -73,6 +75,22 @@ def test_mesh_closure(mk):
     np.add.at(acc, m.face_nbr[inner], -m.face_normal[inner] * m.face_area[inner, None])
     assert np.abs(acc).max() < 1e-13
     assert np.allclose(np.linalg.norm(m.face_normal, axis=1), 1.0)
+
+
+def test_periodic_meshes_have_minimal_image_neighbours():
+    """On the periodic channel and ring every interior face's normal points from owner to
+    neighbour along the minimal-image centroid difference (the seam faces included), the
+    neighbours are a cell width apart, and the cells tile the domain."""
+    for m, h in ((gi.mesh.channel_triangles(8, seed=3), 1.0 / 8), (gi.mesh.ring_1d(12, 3.0), 3.0 / 12)):
+        geo = K.Geometry(m)
+        inner = m.face_nbr >= 0
+        d = geo.delta(m.cell_centroid[m.face_nbr[inner], :m.dim] - m.cell_centroid[m.face_owner[inner], :m.dim])
+        raw = m.cell_centroid[m.face_nbr[inner], 0] - m.cell_centroid[m.face_owner[inner], 0]
+        assert np.all(np.sum(d * m.face_normal[inner], axis=1) > 0.0)
+        assert np.linalg.norm(d, axis=1).max() < 1.5 * h
+        assert np.abs(raw).max() > 0.5 * m.period          # the seam faces are there
+        total = 1.0 if m.dim == 2 else m.period
+        assert abs(m.cell_volume.sum() - total) < 1e-12
 
 
 def test_cavity_volume():
