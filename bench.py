@@ -362,16 +362,18 @@ def time_to_steady(stream, n_side=32, kn=0.01, kn_p=10.0, tol=1e-6, max_outer=15
 
 def time_to_steady_full(stream, kn=0.01, kn_p=10.0, tol=1e-6, max_gsis=900, max_cis=3000, inner=100):
     """Time to eps < tol on the full 20 000-cell cavity at Kn = 0.01 (order 1, blocks of 16,
-    100 synthetic iterations per outer iteration): GSIS in plain FP64 and in FP32 with the
-    mixed synthetic schedule, and CIS in FP32 (stopped at max_cis) for context.  From
-    uniform rest; the timing excludes creation, as the paper's does."""
+    100 synthetic iterations of six relaxation sweeps per outer iteration, the paper's
+    settings): GSIS in plain FP64 and in FP32 with the mixed synthetic schedule, and CIS in
+    FP32 (stopped at max_cis) for context; then both GSIS forms with 200 inner iterations
+    of two sweeps, the fastest setting of a scan.  From uniform rest; the timing excludes
+    creation, as the paper's does."""
     import torch
     import gsis_inputs as gi
     from paper_2601_03935_gb300 import gsis as G
 
-    def run(prec, mode, mixed, n):
+    def run(prec, mode, mixed, n, max_inner=inner, sweeps=6):
         wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=100, Kn=kn, Kn_p=kn_p), precision=prec, order=1,
-                                      relax_block=16, max_inner=inner, n_cis_precond=10,
+                                      relax_block=16, max_inner=max_inner, macro_sweeps=sweeps, n_cis_precond=10,
                                       macro_fp32=2 if mixed else 0)
         ctx = create_ctx(wl, stream.cuda_stream)
         try:
@@ -393,6 +395,13 @@ def time_to_steady_full(stream, kn=0.01, kn_p=10.0, tol=1e-6, max_gsis=900, max_
     out["cis_fp32"] = run("fp32", G.GSIS_MODE_CIS, False, max_cis)
     if out["gsis_fp32_mixed"]["converged"] and out["gsis_fp64_plain"]["converged"]:
         out["speedup_fp32_mixed_vs_fp64_plain"] = out["gsis_fp64_plain"]["seconds"] / out["gsis_fp32_mixed"]["seconds"]
+    out["gsis_fp64_plain_200x2"] = run("fp64", G.GSIS_MODE_GSIS, False, max_gsis, 200, 2)
+    out["gsis_fp32_mixed_200x2"] = run("fp32", G.GSIS_MODE_GSIS, True, max_gsis, 200, 2)
+    a, b = out["gsis_fp64_plain_200x2"], out["gsis_fp32_mixed_200x2"]
+    if a["converged"] and b["converged"]:
+        out["speedup_fp32_mixed_vs_fp64_plain_200x2"] = a["seconds"] / b["seconds"]
+    if b["converged"] and out["gsis_fp64_plain"]["converged"]:
+        out["speedup_fp32_mixed_200x2_vs_fp64_plain_paper_settings"] = out["gsis_fp64_plain"]["seconds"] / b["seconds"]
     return out
 
 
