@@ -168,4 +168,3 @@ def test_steady_couette_flow_has_uniform_shear_stress():
     # no net flow across the channel: per cell u_y is of the triangulation's discretization
     # error (about 1e-4 of the wall speed on this mesh), the volume sum smaller still
     assert abs(np.sum(rec[:, 0] * rec[:, 2] * vol)) < 1e-4 * 0.2
-    assert abs(np.sum(rec[:, 0] * vol) - 1.0) < 1e-9
