@@ -384,6 +384,9 @@ __device__ __forceinline__ Face<Real> load_face(const Real *__restrict__ fgeo, i
 template <typename Real, int N, int DIM, int VPT>
 __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *__restrict__ f, int stride, int j,
                                               int v, const V<Real, N> (&fj)[VPT], V<Real, N> (&slope)[VPT][DIM]) {
+    // In 3-D the H0 plane carries nothing (no hidden velocity components): its slope is
+    // zero and no moment reads it, so its bounds and limiter are skipped (phi = 1).
+    constexpr bool ZH = DIM == 3 && N == 4;
     V<Real, N> dmax[VPT], dmin[VPT];
 #pragma unroll
     for (int u = 0; u < VPT; ++u)
@@ -427,6 +430,7 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
                 if (face_nbr) {
 #pragma unroll
                     for (int p = 0; p < N; ++p) {
+                        if (ZH && p == 1) continue;
                         dmax[u].x[p] = fmax(dmax[u].x[p], dq.x[p]);
                         dmin[u].x[p] = fmin(dmin[u].x[p], dq.x[p]);
                     }
@@ -475,6 +479,7 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
             if constexpr (DIM > 2) vfma(dx2, slope[u][2], d2);
 #pragma unroll
             for (int p = 0; p < N; ++p) {
+                if (ZH && p == 1) continue;
                 hi[u].x[p] = fmax(hi[u].x[p], d2.x[p]);
                 lo[u].x[p] = fmin(lo[u].x[p], d2.x[p]);
             }
@@ -494,18 +499,20 @@ __device__ __forceinline__ void limited_slope(const Geom<Real> &g, const Real *_
                 const V<Real, N> den = vfmav(d1, vadd(d1, d2), vfmav(d2x2, d2, e));
                 V<Real, N> r;
 #pragma unroll
-                for (int p = 0; p < N; ++p) r.x[p] = fdiv(num.x[p], den.x[p]);
+                for (int p = 0; p < N; ++p) r.x[p] = (ZH && p == 1) ? Real(1) : fdiv(num.x[p], den.x[p]);
                 return r;
             };
             const V<Real, N> ph_hi = venkat(dmax[u], hi[u]), ph_lo = venkat(dmin[u], lo[u]);
 #pragma unroll
             for (int p = 0; p < N; ++p)
-                ph.x[p] = fmin(fmin(Real(1), hi[u].x[p] > Real(0) ? ph_hi.x[p] : Real(1)),
-                               lo[u].x[p] < Real(0) ? ph_lo.x[p] : Real(1));
+                ph.x[p] = (ZH && p == 1) ? Real(1)
+                                         : fmin(fmin(Real(1), hi[u].x[p] > Real(0) ? ph_hi.x[p] : Real(1)),
+                                                lo[u].x[p] < Real(0) ? ph_lo.x[p] : Real(1));
         } else {
 #pragma unroll
             for (int p = 0; p < N; ++p) {
                 ph.x[p] = Real(1);
+                if (ZH && p == 1) continue;
                 if (hi[u].x[p] > Real(0)) {
                     const Real d1 = dmax[u].x[p], d2 = hi[u].x[p];
                     ph.x[p] = fmin(ph.x[p], fdiv(fma(d1, d1 + Real(2) * d2, eps2),
