@@ -405,6 +405,77 @@ def time_to_steady_full(stream, kn=0.01, kn_p=10.0, tol=1e-6, max_gsis=900, max_
     return out
 
 
+def time_to_steady_handover(args, kn=0.1, kn_p=10.0, w=0.7, tol=1e-6, switch=3e-6, nmax=3000):
+    """Time to eps < tol on the 20 000-cell cavity at Kn = 0.1 (order 1, blocks of 16, the
+    paper's inner settings, the synchronisation damped to w), where eps of FP32
+    distributions stops near 1.5e-6: plain FP64 GSIS, against FP32 distributions with the
+    mixed synthetic schedule until eps < switch, then the state handed to an FP64 context
+    through the C ABI (gsis_get_distributions / gsis_set_distributions, doubles at the
+    boundary) and FP64 GSIS to tol.  From uniform rest; the hand-over is timed."""
+    import torch
+    import gsis_inputs as gi
+    from paper_2601_03935_gb300 import build
+    from paper_2601_03935_gb300 import gsis as G
+    build.build()
+    G.load()
+    stream = torch.cuda.Stream()
+    base = gi.workloads.cavity(n_side=100, Kn=kn, Kn_p=kn_p)
+    nc, V, NO = base.mesh.n_cells, base.xi.shape[0], base.omega.shape[0]
+
+    def make(prec, mixed, cis_first):
+        wl = gi.workloads.with_solver(base, precision=prec, order=1, relax_block=16, n_cis_precond=cis_first,
+                                      macro_fp32=2 if mixed else 0, sync_relax=w)
+        return create_ctx(wl, stream.cuda_stream)
+
+    def solve(ctx, n, stop):
+        it, hist = G.gsis_solve(ctx, G.GSIS_MODE_GSIS, n, stop)
+        return int(it), (float(hist[-1]) if len(hist) else None)
+
+    out = {"workload": "cavity 2-D, 20000 triangles, 28x28 velocities, 64 directions, Kn=%g, Kn_p=%g, order 1, "
+                       "100 synthetic iterations of six sweeps, synchronisation weight %g" % (kn, kn_p, w),
+           "tol": tol, "switch": switch}
+    ctx = make("fp64", False, 10)
+    try:
+        G.gsis_init_fields(ctx, gi.fields.uniform_fields(nc))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, eps = solve(ctx, nmax, tol)
+        out["gsis_fp64_plain"] = {"iterations": it, "seconds": time.perf_counter() - t0, "final_eps": eps,
+                                  "converged": bool(eps is not None and eps < tol)}
+    finally:
+        G.gsis_destroy(ctx)
+    ctx = make("fp32", True, 10)
+    try:
+        G.gsis_init_fields(ctx, gi.fields.uniform_fields(nc))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it1, eps1 = solve(ctx, nmax, switch)
+        t1 = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        f, I = G.gsis_get_distributions(ctx, nc, V, NO)
+    finally:
+        G.gsis_destroy(ctx)
+    ctx = make("fp64", False, 0)
+    try:
+        G.gsis_set_distributions(ctx, f, I)
+        torch.cuda.synchronize()
+        th = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        it2, eps2 = solve(ctx, nmax, tol)
+        t2 = time.perf_counter() - t0
+    finally:
+        G.gsis_destroy(ctx)
+    out["gsis_fp32_mixed_then_fp64"] = {"fp32_iterations": it1, "fp32_seconds": t1, "fp32_final_eps": eps1,
+                                        "handover_seconds": th, "fp64_iterations": it2, "fp64_seconds": t2,
+                                        "final_eps": eps2, "seconds": t1 + th + t2,
+                                        "converged": bool(eps2 is not None and eps2 < tol)}
+    a, b = out["gsis_fp64_plain"], out["gsis_fp32_mixed_then_fp64"]
+    if a["converged"] and b["converged"]:
+        out["speedup"] = a["seconds"] / b["seconds"]
+    print(json.dumps({"handover": out}))
+    return 0
+
+
 def time_to_steady_capsule(stream, n=12, n_v=16, Mach=3.0, tol=1e-6, max_gsis=300, max_cis=3000):
     """Time to eps < tol on a reduced 3-D capsule (the config-4 geometry on 6 n^3 tetrahedra
     less the body, n_v^3 velocities, 8 x 16 directions, Kn = 0.01) at Mach 3, where 16^3
@@ -1070,6 +1141,8 @@ def main():
                     help="only run a small 3-D capsule case (N^3 hexahedra, NV^3 velocities) for profiling")
     ap.add_argument("--cylinder-probe", default=None, metavar="NT,NR",
                     help="only run a smaller Mach-5 cylinder (NT x NR O-grid, 2 NT NR triangles) for profiling")
+    ap.add_argument("--handover", action="store_true",
+                    help="only run the Kn = 0.1 cavity time to steady with the FP32 -> FP64 hand-over")
     ap.add_argument("--no-capsule", action="store_true",
                     help="skip the full-size 3-D capsule (tetrahedra) throughput leg")
     ap.add_argument("--no-full-cylinder", action="store_true",
@@ -1083,6 +1156,8 @@ def main():
         return capsule_probe(args)
     if args.cylinder_probe:
         return cylinder_probe(args)
+    if args.handover:
+        return time_to_steady_handover(args)
     return run_reference(args) if args.impl == "reference" else run_ours(args)
 
 
