@@ -316,10 +316,19 @@ int kinetic_step(gsis_ctx *c, int nxt) {
                                          (Real *)c->bcoef);
     }));
     // photon transport is independent of the gas planes: it runs on the side stream
-    if (!c->side_stream) {
-        CUDA_TRY(c, cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
-        CUDA_TRY(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
-        CUDA_TRY(c, cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    if (!c->side_stream) {   // the events first: a side stream implies both events exist
+        cudaEvent_t e = nullptr;
+        if (!c->fork_ev) {
+            CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            c->fork_ev = e;
+        }
+        if (!c->join_ev) {
+            CUDA_TRY(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            c->join_ev = e;
+        }
+        cudaStream_t st = nullptr;
+        CUDA_TRY(c, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        c->side_stream = st;
     }
     CUDA_TRY(c, cudaEventRecord(c->fork_ev, c->stream));
     CUDA_TRY(c, cudaStreamWaitEvent(c->side_stream, c->fork_ev, 0));
