@@ -50,6 +50,7 @@ class SolverParams:
     tc_moments: int = 1                  # library FP32 path: 0 CUDA cores, 1 tensor cores in the moment/sync
                                          # passes, 2 also in the sweep epilogue
     positivity: float = 0.0              # 0 <= theta < 1: the implicit update keeps f >= theta f_old (0: off)
+    defect_correction: int = 0           # 1: synthetic residual R(W) - R(W_h) + kinetic residual moments (0: off)
 
 
 @dataclass

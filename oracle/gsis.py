@@ -43,12 +43,36 @@ def cis_step(f, I, wl, geo):
     return f_new, I_new, epsilon(F_new, F_old, geo.vol, wl.model, wl.dim), F_new
 
 
+def kinetic_residual_rows(res, resR, wl):
+    """Velocity moments of the kinetic residual (Eq. dis_micro's right-hand side) in the
+    rows of the synthetic equations: mass, momentum (dim components), total energy (the
+    translational part 1/2 |xi|^2 F0 + 1/2 H0, f1, f2 and the radiative energy), e_r, e_v
+    and e_R."""
+    from . import macro as MA
+    dim, xi, w, wo = wl.dim, wl.xi, wl.w, wl.wo
+    x2 = np.sum(xi[:, :dim] ** 2, axis=1)
+    Rk = np.zeros((res.shape[0], MA.nvar(dim)))
+    Rk[:, 0] = res[:, :, 0] @ w
+    for a in range(dim):
+        Rk[:, 1 + a] = res[:, :, 0] @ (w * xi[:, a])
+    e_r, e_v, e_R = res[:, :, 2] @ w, res[:, :, 3] @ w, resR @ wo
+    Rk[:, 1 + dim] = res[:, :, 0] @ (0.5 * w * x2) + 0.5 * (res[:, :, 1] @ w) + e_r + e_v + e_R
+    Rk[:, 2 + dim], Rk[:, 3 + dim], Rk[:, 4 + dim] = e_r, e_v, e_R
+    return Rk
+
+
 def gsis_step(f, I, wl, geo, faces, F_old=None):
     """One GSIS iteration (Section 3): kinetic step, high-order terms, synthetic
     equations, then the synchronisation
         f^{k+1} = f^{k+1/2} + w [f^eq(M^{k+1}) - f^eq(M^{k+1/2})]
     with multi-temperature equilibria (photons: sigma_R T_R^4 / pi).  The paper's
     step has w = 1; w = wl.solver.sync_relax.
+
+    With wl.solver.defect_correction (an extension; off is the paper's step) the synthetic
+    equations solved are R(W) - R(W^{k+1/2}) + r^{k+1/2} = 0, r^{k+1/2} the moments of the
+    kinetic residual at f^{k+1/2} with the coefficients of M^{k+1/2}
+    (``kinetic_residual_rows``): at a kinetic steady state r = 0 and W^{k+1/2} solves them,
+    so GSIS keeps the kinetic steady state of the discretisation as its fixed point.
 
     In a closed domain (walls and mirror planes only) the total mass is not fixed by the
     steady equations, and a synthetic solve stopped after a finite number of
@@ -62,7 +86,13 @@ def gsis_step(f, I, wl, geo, faces, F_old=None):
     Fh = K.moments(fh, Ih, wl.xi, wl.w, wl.omega, wl.wo, dim, model)
     hot = MA.high_order_terms(faces, Fh, MA.kinetic_boundary_flux(faces, fh, Ih, wl), wl)
     Wh = MA.conservative(Fh, dim, model)
-    W = MA.macro_solve(Wh, faces, hot, wl)
+    offset = None
+    if getattr(wl.solver, "defect_correction", 0):
+        # an extension: R(W) - R(W_h) + (moments of the kinetic residual at f^{k+1/2}), so
+        # that the kinetic steady state is an exact fixed point of the synthetic solve
+        res, _, resR, _, _ = K.kinetic_residual(fh, Ih, wl, geo, np.arange(wl.mesh.n_cells), Fh)
+        offset = kinetic_residual_rows(res, resR, wl) - MA.residual(Wh, faces, hot, wl)
+    W = MA.macro_solve(Wh, faces, hot, wl, offset=offset)
     if all(p.kind in (K.WALL, K.SYMMETRY) for p in wl.mesh.patches):
         W = W * (np.sum(F_old["rho"] * geo.vol) / np.sum(W[:, 0] * geo.vol))
     Fn = MA.fields_from_W(W, dim, model)

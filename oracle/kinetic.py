@@ -324,35 +324,17 @@ def relaxation_source(Fc, f, I, wl):
 
 
 # --------------------------------------------------------------------------- sweep
-def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
-    """One implicit kinetic step (Eq. dis_micro) for the gas planes and photons.
-
-    For every cell i and discrete velocity (photon direction):
-      r_i = (g_i - f_i)/tau_i + s_i - (1/V_i) sum_faces S (xi_n^+ f_L + xi_n^- f_R)
-      d_i = 1/dt_i + 1/tau_i + (1/V_i) sum_faces S xi_n^+
-    with the photon relaxation rate k_eff in place of 1/tau, g_R = sigma_R T_v^4/pi,
-    and the radiative sink s = -(f0/rho) k_eff (4 sigma_R T_v^4 - int I dOmega) in
-    the f2 equation.  Point relaxation: relax_block = 1 is Jacobi (neighbours keep
-    their previous iterate); relax_block = B > 1 runs a forward and a backward
-    Gauss-Seidel sweep inside each block of B consecutive cells (B = n_cells is the
-    paper's natural-order symmetric sweep).
-
-    With wl.solver.positivity = theta > 0 every value of the result is at least theta times
-    its value in f (or I).
-
-    Returns (f_new, I_new) for ``cells`` (default: all cells, in order).
-    """
+def kinetic_residual(f, I, wl, geo, cells, F=None):
+    """The right-hand side of Eq. dis_micro at f, I for ``cells``: per cell and discrete
+    velocity (photon direction)
+      r_i = (g_i - f_i)/tau_i + s_i - (1/V_i) sum_faces S (xi_n^+ f_L + xi_n^- f_R),
+      d_i = 1/dt_i + 1/tau_i + (1/V_i) sum_faces S xi_n^+,
+    with the coefficients of the reference distributions from the fields F (default: the
+    moments of f, I).  Returns (res [n, V, 4], dg [n, V], resR [n, n_omega],
+    dR [n, n_omega], offdiag), offdiag[k] listing (neighbour, S xi_n^- / V, S Omega_n^- / V)
+    for every interior face of cells[k]."""
     mesh, model, solver = wl.mesh, wl.model, wl.solver
     dim, xi, w, om, wo = mesh.dim, wl.xi, wl.w, wl.omega, wl.wo
-    geo = geo or Geometry(mesh)
-    nc = mesh.n_cells
-    cells = np.arange(nc) if cells is None else np.asarray(cells)
-    if relax_block != 1:
-        blocks = sorted(set(int(c) // relax_block for c in cells))
-        want = np.concatenate([np.arange(b * relax_block, min((b + 1) * relax_block, nc)) for b in blocks])
-        if len(want) != len(cells) or np.any(np.sort(cells) != want):
-            raise ValueError("block relaxation needs whole blocks of consecutive cells")
-        cells = want
     order, K = solver.order, solver.venkat_K
 
     # cells whose moments are needed: targets and their neighbours (the neighbours'
@@ -416,6 +398,40 @@ def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
             dr_ += S * op / geo.vol[i]
         res[k], dg[k], resR[k], dR[k] = r, d, rR, dr_
         offdiag.append(od)
+
+    return res, dg, resR, dR, offdiag
+
+
+def kinetic_sweep(f, I, wl, geo=None, cells=None, relax_block=1, F=None):
+    """One implicit kinetic step (Eq. dis_micro) for the gas planes and photons.
+
+    For every cell i and discrete velocity (photon direction):
+      r_i = (g_i - f_i)/tau_i + s_i - (1/V_i) sum_faces S (xi_n^+ f_L + xi_n^- f_R)
+      d_i = 1/dt_i + 1/tau_i + (1/V_i) sum_faces S xi_n^+
+    with the photon relaxation rate k_eff in place of 1/tau, g_R = sigma_R T_v^4/pi,
+    and the radiative sink s = -(f0/rho) k_eff (4 sigma_R T_v^4 - int I dOmega) in
+    the f2 equation.  Point relaxation: relax_block = 1 is Jacobi (neighbours keep
+    their previous iterate); relax_block = B > 1 runs a forward and a backward
+    Gauss-Seidel sweep inside each block of B consecutive cells (B = n_cells is the
+    paper's natural-order symmetric sweep).
+
+    With wl.solver.positivity = theta > 0 every value of the result is at least theta times
+    its value in f (or I).
+
+    Returns (f_new, I_new) for ``cells`` (default: all cells, in order).
+    """
+    mesh, model, solver = wl.mesh, wl.model, wl.solver
+    dim, xi, w, om, wo = mesh.dim, wl.xi, wl.w, wl.omega, wl.wo
+    geo = geo or Geometry(mesh)
+    nc = mesh.n_cells
+    cells = np.arange(nc) if cells is None else np.asarray(cells)
+    if relax_block != 1:
+        blocks = sorted(set(int(c) // relax_block for c in cells))
+        want = np.concatenate([np.arange(b * relax_block, min((b + 1) * relax_block, nc)) for b in blocks])
+        if len(want) != len(cells) or np.any(np.sort(cells) != want):
+            raise ValueError("block relaxation needs whole blocks of consecutive cells")
+        cells = want
+    res, dg, resR, dR, offdiag = kinetic_residual(f, I, wl, geo, cells, F)
 
     if relax_block == 1:
         df = res / dg[..., None]

@@ -417,8 +417,10 @@ def kinetic_boundary_flux(faces, f, I, wl):
 
 
 # ----------------------------------------------------------------- residual and solve
-def residual(W, faces, hot, wl):
-    """R_i = -(1/V_i) sum_faces S (F_c + F_v).n + Q_i  (Eq. delta_macro, right-hand side)."""
+def residual(W, faces, hot, wl, offset=None):
+    """R_i = -(1/V_i) sum_faces S (F_c + F_v).n + Q_i  (Eq. delta_macro, right-hand side),
+    plus a fixed per-cell ``offset`` [nc, nvar] when given (the defect correction of
+    gsis.gsis_step)."""
     dim, model, geo = wl.dim, wl.model, faces.geo
     prim = primitive(W, dim, model)
     q = np.column_stack([prim[0], prim[1], prim[2], prim[3], prim[4], prim[5]])
@@ -437,7 +439,8 @@ def residual(W, faces, hot, wl):
     bflux = macro_boundary_flux(faces, prim, wl) + hot["boundary"]
     np.add.at(R, faces.bf_cell, -bflux * faces.bf_S[:, None])
     R /= geo.vol[:, None]
-    return R + source(prim, dim, model)
+    R = R + source(prim, dim, model)
+    return R if offset is None else R + offset
 
 
 def gamma_face(faces, prim, wl):
@@ -509,7 +512,7 @@ def source_jacobian_block(prim, dim, model):
     return J
 
 
-def macro_solve(W0, faces, hot, wl, history=None):
+def macro_solve(W0, faces, hot, wl, history=None, offset=None):
     """Pseudo-time iterations of Eq. (delta_macro) until ||R|| <= tol_inner ||R_0|| or
     max_inner.  Each iteration solves
         D_i dW_i + (1/(2 V_i)) sum_j (dF_j . n_ij - Gamma_ij dW_j) S_ij = R_i,
@@ -522,7 +525,7 @@ def macro_solve(W0, faces, hot, wl, history=None):
     r0 = None
     for it in range(s.max_inner):
         prim = primitive(W, dim, model)
-        R = residual(W, faces, hot, wl)
+        R = residual(W, faces, hot, wl, offset)
         rn = np.sqrt(np.sum(R * R))
         if history is not None:
             history.append(rn)
