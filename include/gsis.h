@@ -177,6 +177,19 @@ typedef struct {
                                    leaves every steady state unchanged; it lets the order-2
                                    defect correction start from impulsive hypersonic states).
                                    0: off, the paper's scheme.                               */
+    int32_t defect_correction;  /* 1: every GSIS synthetic solve (Section 3, step 2) solves
+                                   R(W) - R(W_h) + r_h = 0 instead of R(W) = 0, with W_h the
+                                   conservative variables of M^{k+1/2} and r_h the velocity
+                                   moments, in the rows of the synthetic equations, of the
+                                   kinetic residual (Eq. dis_micro's right-hand side) at
+                                   f^{k+1/2} with the coefficients of M^{k+1/2}.  At a kinetic
+                                   steady state r_h = 0 and W_h solves it, so GSIS keeps the
+                                   kinetic discretisation's steady state as its fixed point
+                                   (the paper's synthetic equations match it only to the
+                                   discretisation error, which leaves an eps floor).  Costs one
+                                   slope pass and one residual-only sweep per GSIS iteration.
+                                   An extension; 0 (default) is the paper's step.  Not with
+                                   velocity shards (UNSUPPORTED).                            */
 } gsis_solver_params;
 
 typedef struct gsis_ctx gsis_ctx;

@@ -55,6 +55,10 @@ struct gsis_ctx {
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool staged = false;
     void *coef = nullptr, *bcoef = nullptr, *partial = nullptr, *opartial = nullptr;
+    // defect correction (solver.defect_correction): coefficients of M^{k+1/2}, the moment
+    // rows of the kinetic residual at f^{k+1/2} and the synthetic residual's offset
+    void *coef_h = nullptr;
+    double *rrow = nullptr, *moff = nullptr;
     void *sync_kc = nullptr;                    // FP32: per-cell synchronisation constants [nc][SYNC_KC] floats
     void *fface = nullptr, *oface = nullptr;    // upwind face values [n_fi][Vp][4], [n_fi][Op] (order 2)
     double *fields = nullptr, *fields_old = nullptr, *eps_terms = nullptr, *eps_sums = nullptr;
@@ -207,6 +211,7 @@ Geom<Real> geom(const gsis_ctx *c) {
     g.bf_tab = c->bf_tab;
     g.refl_v = c->refl_v;
     g.refl_o = c->refl_o;
+    g.resid = 0;
     return g;
 }
 
@@ -532,6 +537,67 @@ int macro_solve(gsis_ctx *c, int *w_out) {
     return GSIS_OK;
 }
 
+// Defect correction (an extension): the offset r_h - R(W_h) that the synthetic solve adds
+// to its residual, so that it solves R(W) - R(W_h) + r_h = 0 with r_h the moments of the
+// kinetic residual (Eq. dis_micro's right-hand side) at f^{k+1/2}, coefficients of M^{k+1/2}:
+// the wall densities, slopes and residuals of f^{k+1/2} (into the buffers the next kinetic
+// step overwrites anyway), their moment rows, and R(W_h) in FP64 without the offset.
+template <typename Real>
+int defect_offset(gsis_ctx *c, int nxt) {
+    const Geom<Real> g = geom<Real>(c);
+    TRY(launch(c, K_COEF, [&] {
+        return launch_coefficients<Real>(c->stream, c->dim, g, c->model, c->fields_h, c->cell_dx, (Real *)c->coef_h);
+    }));
+    TRY(launch(c, K_WALL, [&] {
+        return launch_wall_density<Real>(c->stream, c->dim, g, vquad<Real>(c), c->patch_T, c->bf_inc, c->patch_kind,
+                                         (const Real *)c->f[nxt], nullptr, (Real *)c->bcoef);
+    }));
+    if (c->order == 2) {
+        TRY(launch(c, K_SLOPE_GAS, [&] {
+            return launch_slopes<Real>(c->stream, c->dim, 4, g, vquad<Real>(c), (const Real *)c->f[nxt],
+                                       (Real *)c->fface);
+        }));
+        TRY(launch(c, K_SLOPE_PHOTON, [&] {
+            return launch_slopes<Real>(c->stream, c->dim, 1, g, oquad<Real>(c), (const Real *)c->I[nxt],
+                                       (Real *)c->oface);
+        }));
+    }
+    Geom<Real> gr = g;
+    gr.resid = 1;
+    gr.tc = 0;
+    TRY(launch(c, K_SWEEP_GAS, [&] {   // residual moments only: f_out is not written
+        return launch_sweep_gas<Real>(c->stream, c->dim, c->order, gr, vquad<Real>(c), (const Real *)c->coef_h,
+                                      (const Real *)c->bcoef, (const Real *)c->f[nxt], (const Real *)c->fface,
+                                      (Real *)c->f[nxt], (Real *)c->partial);
+    }));
+    TRY(launch(c, K_SWEEP_PHOTON, [&] {
+        return launch_sweep_photon<Real>(c->stream, c->dim, c->order, gr, oquad<Real>(c), (const Real *)c->coef_h,
+                                         (const Real *)c->bcoef, (const Real *)c->I[nxt], (const Real *)c->oface,
+                                         (Real *)c->I[nxt], (Real *)c->opartial);
+    }));
+    TRY(launch(c, K_MCONV, [&] {
+        return launch_resid_rows<Real>(c->stream, c->dim, (int)c->nc, c->nch, c->och, (const Real *)c->coef_h,
+                                       (const Real *)c->partial, (const Real *)c->opartial, c->rrow);
+    }));
+    MacroGeom g0 = c->mg;
+    g0.moff = nullptr;
+    TRY(launch(c, K_MGRAD, [&] {
+        return launch_macro_grad(c->stream, g0, c->order, 0, c->model, nullptr, c->W[0], c->mq, c->mgrad, c->mphi);
+    }));
+    TRY(launch(c, K_MBFLUX, [&] {
+        return launch_macro_bflux(c->stream, g0, 0, c->model, vquad_d(c), oquad_d(c), nullptr, c->mq, c->mbf);
+    }));
+    TRY(launch(c, K_MRES, [&] {
+        return launch_macro_residual(c->stream, g0, c->order, 0, c->model, c->solver.cfl_macro, nullptr, c->W[0],
+                                     c->mq, c->mgrad, c->mphi, c->hot, c->mbf, c->hot_b, c->Rg, c->Dinv, c->gam,
+                                     c->rpart);
+    }));
+    TRY(launch(c, K_MCONV, [&] {
+        return launch_macro_offset(c->stream, c->dim, (int)c->nc, c->Rg, c->rrow, c->moff);
+    }));
+    return GSIS_OK;
+}
+
 // One GSIS iteration (Section 3): kinetic step, high-order terms from f^{k+1/2}, the
 // synthetic equations, f^{k+1} = f^{k+1/2} + w [f_eq(M^{k+1}) - f_eq(M^{k+1/2})].
 template <typename Real>
@@ -562,6 +628,7 @@ int gsis_iteration(gsis_ctx *c) {
         return launch_macro_hot(c->stream, g, c->mfp32 == 1, c->model, c->fields_h, c->mq, c->mgrad, c->kbf, c->mbf, c->hot,
                                 c->hot_b);
     }));
+    if (c->moff) TRY(defect_offset<Real>(c, nxt));
     int w = 0;
     TRY(macro_solve(c, &w));
     if (c->closed) {
@@ -650,6 +717,8 @@ int validate(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_photon
     if (!(sp->sync_relax > 0) || !(sp->sync_relax <= 1)) return why = "sync_relax must be in (0, 1]", GSIS_ERR_INVALID_ARG;
     if (sp->tc_moments < 0 || sp->tc_moments > 2) return why = "tc_moments must be 0, 1 or 2", GSIS_ERR_INVALID_ARG;
     if (!(sp->positivity >= 0.0) || !(sp->positivity < 1.0)) return why = "positivity must be in [0, 1)", GSIS_ERR_INVALID_ARG;
+    if (sp->defect_correction != 0 && sp->defect_correction != 1)
+        return why = "defect_correction must be 0 or 1", GSIS_ERR_INVALID_ARG;
     if (sp->macro_fp32 < 0 || sp->macro_fp32 > 2) return why = "macro_fp32 must be 0, 1 or 2", GSIS_ERR_INVALID_ARG;
     if (!(mp->Kn > 0) || !(mp->Kn_p > 0) || !(mp->sigma_R >= 0) || !(mp->Z_r > 0) || !(mp->Z_v > 0) ||
         !(mp->d_r >= 0) || !(mp->d_v > 0) || !(mp->d_r > 0))
@@ -1148,6 +1217,12 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         A_(dalloc(c, &c->mgrad, (size_t)nc * MGS * NVM));
         A_(dalloc(c, &c->mphi, (size_t)nc * NVM));
         A_(dalloc(c, &c->Rg, (size_t)nc * NVM));
+        if (sp->defect_correction) {
+            A_(dalloc_real(c, &c->coef_h, (size_t)nc * cf::NC));
+            A_(dalloc(c, &c->rrow, (size_t)nc * NVM));
+            A_(dalloc(c, &c->moff, (size_t)nc * NVM));
+            if (cudaMemset(c->moff, 0, (size_t)nc * NVM * sizeof(double)) != cudaSuccess) return bail(GSIS_ERR_CUDA);
+        }
         A_(dalloc(c, &c->Dinv, (size_t)nc * 24));
         A_(dalloc(c, &c->gam, (size_t)nc * MAXF * 2));
         A_(dalloc(c, &c->rpart, (size_t)macro_rpart_count((int)nc)));
@@ -1199,6 +1274,7 @@ int gsis_create(const gsis_mesh *m, const gsis_velocity_quad *vq, const gsis_pho
         G.eps2 = c->m_eps2;
         G.vol = c->vol;
         G.dx = c->cell_dx;
+        G.moff = c->moff;              // null unless the defect correction is on
         G.bf_cell = c->bf_cell;
         G.bf_patch = c->bf_patch;
         G.bf_n = c->m_bf_n;
@@ -1693,6 +1769,7 @@ int gsis_shard_setup(gsis_ctx *c, int32_t n_xi_all, const double *xi_all, const 
     if (c->mirrors)
         return fail(c, GSIS_ERR_UNSUPPORTED, "mirror planes pair velocities across shards; shard a mesh without them");
     if (c->dim == 3) return fail(c, GSIS_ERR_UNSUPPORTED, "velocity shards are built for 1-D and 2-D meshes");
+    if (c->moff) return fail(c, GSIS_ERR_UNSUPPORTED, "the defect correction is built for unsharded contexts");
     if (n_xi_all < c->V || n_omega_all < c->NO) return fail(c, GSIS_ERR_INVALID_ARG, "the full sets are smaller than the shard");
     const int dim = c->dim;
     // the incoming unit-density wall flux over every velocity of every shard
@@ -2140,6 +2217,8 @@ int warm_start(gsis_ctx *c, int n_presolve, bool use_mlp) {
             CUDA_TRY(c, cudaMemsetAsync(c->hot, 0, (size_t)std::max(g.n_fi, 1) * NHOT * sizeof(double), c->stream));
             CUDA_TRY(c, cudaMemsetAsync(c->hot_b, 0, (size_t)std::max(g.n_bf, 1) * NVM * sizeof(double), c->stream));
         }
+        if (c->moff)   // the pre-solve has no kinetic residual: no offset
+            CUDA_TRY(c, cudaMemsetAsync(c->moff, 0, (size_t)c->nc * NVM * sizeof(double), c->stream));
         int w = 0;
         TRY(macro_solve(c, &w));
         if (c->closed) {

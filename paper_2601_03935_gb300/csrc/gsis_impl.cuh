@@ -98,6 +98,7 @@ struct Geom {
     int tc_wait;               // polls of the first tensor-core completion wait (ERR_TIMEOUT bit on expiry)
     Real pos_theta;            // > 0: the sweep keeps every value >= pos_theta times its previous value
     int *err;                  // device error word: bit 0 divergence, bit 1 a completion wait ran out
+    int resid;                 // sweep: the moments of the residual only (no relaxation, no update)
 };
 
 template <typename Real>
@@ -223,6 +224,7 @@ struct MacroGeom {
     const double *patch_state; // [n_patches][8]: rho, u[3], T_t, T_r, T_v, T_R
     const int *bf_tab;         // [n_bf] mirror-reflection table of the face or -1 (as Geom)
     const int *refl_v, *refl_o;
+    const double *moff;        // [nc][NVM] added to the synthetic residual (defect correction), or null
 };
 
 // Double-precision quadratures for the macroscopic boundary fluxes.
@@ -340,6 +342,11 @@ template <typename Real>
 cudaError_t launch_slopes(cudaStream_t s, int dim, int planes, const Geom<Real> &g, const Quad<Real> &q,
                           const Real *f, Real *fface);
 size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size, bool tc);
+template <typename Real>
+cudaError_t launch_resid_rows(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const Real *coef,
+                              const Real *partial, const Real *opartial, double *rows);
+cudaError_t launch_macro_offset(cudaStream_t s, int dim, int n_cells, const double *Rg, const double *rows,
+                                double *moff);
 template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
                              const Real *coef, const Real *bcoef, const Real *f_in, const Real *fface,

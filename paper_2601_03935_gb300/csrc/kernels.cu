@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
     // the tensor-core epilogue's basis covers the 1-D and 2-D moments
     constexpr bool TCM = std::is_same<Real, float>::value && N == 4 && DIM < 3;
     constexpr int NMPD = Lay<DIM>::NMP;
-    const bool tc = TCM && g.tc;
+    const bool tc = TCM && g.tc && !g.resid;
     Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, DIM, sizeof(Real), tc));   // [DIM+1][SV]
     signed char *Lg = reinterpret_cast<signed char *>(sxi + (DIM + 1) * SV);   // [block][MAXF] in-block neighbour or -1
     tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(Lg + ((g.block * MAXF + 15) & ~15));
@@ -877,7 +877,9 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
     // the in-block face records of phase 0, used where a < 0 (in-block inflow):
     //   forward  delta*_l = (r_l - sum_{j<l} a delta*_j) / d_l
     //   backward delta_l  = delta*_l - (sum_{j>l} a delta_j) / d_l
-    if (ty == 0) {
+    // (g.resid: the residuals themselves are the result; phases 2 and 3 are skipped and
+    // phase 4 takes their moments)
+    if (ty == 0 && !g.resid) {
         for (int l = 0; l < nb; ++l) {
             Vec<Real, N> acc = R[l * SV + tx];
 #pragma unroll
@@ -981,7 +983,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
             return;
         }
     }
-    for (int l = ty; l < nb; l += SROWS) {
+    for (int l = ty; l < nb && !g.resid; l += SROWS) {
         const size_t idx = (size_t)(c0 + l) * stride + v;
         V<Real, N> fo = ldv<Real, N>(f_in, idx);
         Vec<Real, N> t = R[l * SV + tx];
@@ -1872,6 +1874,58 @@ cudaError_t launch_cell_sums(cudaStream_t s, int dim, int n_cells, int n_chunks,
     return cudaGetLastError();
 }
 
+// Per cell: the rows of the synthetic equations (mass, momentum, total energy, e_r, e_v,
+// e_R; stride NVM) of the moment partials of the kinetic residual that a sweep with
+// Geom::resid leaves in partial / opartial.  The gas partials are about the velocity u0 of
+// the cell's moment tile (coef of the tile's first cell, as the sweep took it):
+//   sum xi r0 = sum c r0 + u0 sum r0,  sum |xi|^2 r0 = sum |c|^2 r0 + 2 u0 . sum c r0 + |u0|^2 sum r0.
+template <typename Real, int DIM>
+__global__ void k_resid_rows(int n_cells, int n_chunks, int o_chunks, const Real *__restrict__ coef,
+                             const Real *__restrict__ partial, const Real *__restrict__ opartial,
+                             double *__restrict__ rows) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    constexpr int NM = n_gas_moments<DIM>(), NMPD = Lay<DIM>::NMP;
+    double S[NM];
+    for (int k = 0; k < NM; ++k) S[k] = 0.0;
+    for (int c = 0; c < n_chunks; ++c)
+        for (int k = 0; k < NM; ++k) S[k] += (double)partial[((size_t)i * n_chunks + c) * NMPD + k];
+    double eR = 0.0;
+    for (int c = 0; c < o_chunks; ++c) eR += (double)opartial[((size_t)i * o_chunks + c) * NMO];
+    const Real *u = coef + (size_t)(i / MT * MT) * cf::NC + cf::U;
+    double u0[DIM], uS = 0.0, u2 = 0.0, trc = 0.0;
+    for (int a = 0; a < DIM; ++a) {
+        u0[a] = (double)u[a];
+        uS += u0[a] * S[1 + a];
+        u2 += u0[a] * u0[a];
+    }
+    int m = 1 + DIM;
+    for (int a = 0; a < DIM; ++a)
+        for (int b = a; b < DIM; ++b, ++m)
+            if (b == a) trc += S[m];
+    m += DIM;                                  // past the c |c|^2 moments
+    double plane[4] = {S[0], 0.0, 0.0, 0.0};   // sum r_p over the velocities
+    for (int p = (DIM < 3 ? 1 : 2); p < 4; ++p) {
+        plane[p] = S[m];
+        m += 1 + DIM;
+    }
+    double *r = rows + (size_t)i * NVM;
+    r[0] = S[0];
+    for (int a = 0; a < DIM; ++a) r[1 + a] = S[1 + a] + u0[a] * S[0];
+    r[1 + DIM] = 0.5 * (trc + 2.0 * uS + u2 * S[0]) + 0.5 * plane[1] + plane[2] + plane[3] + eR;
+    r[2 + DIM] = plane[2];
+    r[3 + DIM] = plane[3];
+    r[4 + DIM] = eR;
+}
+
+template <typename Real>
+cudaError_t launch_resid_rows(cudaStream_t s, int dim, int n_cells, int n_chunks, int o_chunks, const Real *coef,
+                              const Real *partial, const Real *opartial, double *rows) {
+    GSIS_DISPATCH_DIM3(dim, (k_resid_rows<Real, DIM><<<(n_cells + 127) / 128, 128, 0, s>>>(
+                                n_cells, n_chunks, o_chunks, coef, partial, opartial, rows)));
+    return cudaGetLastError();
+}
+
 template <typename Real, int N, int DIM>
 static cudaError_t slopes_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *f,
                             Real *fface) {
@@ -2042,6 +2096,8 @@ cudaError_t launch_sync(cudaStream_t s, int dim, int n_cells, bool tc, const Qua
                                                    const int *, const Real *, double *);                           \
     template cudaError_t launch_cell_sums<Real>(cudaStream_t, int, int, int, int, const Real *, const Real *,      \
                                                 double *);                                                         \
+    template cudaError_t launch_resid_rows<Real>(cudaStream_t, int, int, int, int, const Real *, const Real *,     \
+                                                 const Real *, double *);                                          \
     template cudaError_t launch_slopes<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,      \
                                              const Real *, Real *);                                                \
     template cudaError_t launch_sweep_gas<Real>(cudaStream_t, int, int, const Geom<Real> &, const Quad<Real> &,    \

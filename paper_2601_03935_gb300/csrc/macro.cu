@@ -735,6 +735,7 @@ __global__ void __launch_bounds__(128) k_macro_residual(MacroGeom g, ModelDev m,
         source<R, DIM>(qi, m, Q);
         for (int v = 0; v < NV; ++v) {
             Rr[v] = Rr[v] / V + Q[v];
+            if (g.moff) Rr[v] += R(g.moff[(size_t)i * NVM + v]);
             r2 += (double)Rr[v] * (double)Rr[v];
         }
         double *rg = Rg + (size_t)i * NVM;
@@ -1024,6 +1025,26 @@ cudaError_t launch_macro_residual(cudaStream_t s, const MacroGeom &g, int order,
             k_macro_residual<R, DIM, 1><<<nb, 128, 0, s>>>(g, m, cfl_macro, st, q, grad, phi, hot, bflux, hot_b, Rg,
                                                               Dinv, gam, rpart);
     }));
+    return cudaGetLastError();
+}
+
+// Defect correction: moff = (kinetic residual rows) - R(W_h), from the relaxation form Rg of
+// R(W_h) (whose total-energy row holds the gas energy, R_E - R_eR).
+__global__ void k_macro_offset(int n_cells, int nv, const double *__restrict__ Rg, const double *__restrict__ rows,
+                               double *__restrict__ moff) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_cells) return;
+    const int E = nv - 4, ER = nv - 1;
+    const double *rg = Rg + (size_t)i * NVM;
+    for (int v = 0; v < nv; ++v) {
+        const double Rh = v == E ? rg[E] + rg[ER] : rg[v];
+        moff[(size_t)i * NVM + v] = rows[(size_t)i * NVM + v] - Rh;
+    }
+}
+
+cudaError_t launch_macro_offset(cudaStream_t s, int dim, int n_cells, const double *Rg, const double *rows,
+                                double *moff) {
+    k_macro_offset<<<(n_cells + 127) / 128, 128, 0, s>>>(n_cells, dim + 5, Rg, rows, moff);
     return cudaGetLastError();
 }
 

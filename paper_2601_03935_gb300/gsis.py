@@ -66,7 +66,7 @@ class gsis_solver_params(C.Structure):
                 ("n_cis_precond", C.c_int32), ("max_outer", C.c_int32), ("max_inner", C.c_int32),
                 ("macro_sweeps", C.c_int32), ("tol_outer", C.c_double), ("tol_inner", C.c_double),
                 ("sync_relax", C.c_double), ("macro_fp32", C.c_int32), ("tc_moments", C.c_int32),
-                ("positivity", C.c_double)]
+                ("positivity", C.c_double), ("defect_correction", C.c_int32)]
 
 
 _LIB = None
@@ -208,7 +208,8 @@ def gsis_create(dim, face_owner, face_nbr, face_normal, face_area, face_centroid
                             solver.cfl_macro, solver.venkat_K, solver.n_cis_precond, solver.max_outer,
                             solver.max_inner, solver.macro_sweeps, solver.tol_outer, solver.tol_inner,
                             getattr(solver, "sync_relax", 1.0), int(getattr(solver, "macro_fp32", 0)),
-                            int(getattr(solver, "tc_moments", 1)), float(getattr(solver, "positivity", 0.0)))
+                            int(getattr(solver, "tc_moments", 1)), float(getattr(solver, "positivity", 0.0)),
+                            int(getattr(solver, "defect_correction", 0)))
     out = C.c_void_p()
     rc = lib.gsis_create(C.byref(mesh), C.byref(vq), C.byref(pq), C.byref(mp), C.byref(sp), C.c_void_p(stream),
                          C.byref(out))

@@ -129,7 +129,7 @@ def test_bad_meshes_and_parameters_are_refused_on_the_host(lib):
                       face_nbr=lambda x: np.where(x >= 0, np.arange(1, x.shape[0] + 1) % 8, x))
     assert _code(many) in (G.GSIS_ERR_UNSUPPORTED, G.GSIS_ERR_BAD_MESH)
     for kw in (dict(positivity=1.0), dict(positivity=-0.1), dict(sync_relax=0.0), dict(macro_fp32=3),
-               dict(tc_moments=3), dict(max_inner=0), dict(venkat_K=0.0)):
+               dict(tc_moments=3), dict(max_inner=0), dict(venkat_K=0.0), dict(defect_correction=2)):
         assert _code(_args(gi.workloads.with_solver(wl, **kw))) == G.GSIS_ERR_INVALID_ARG, kw
     empty_v = list(_args(wl))
     empty_v[9], empty_v[10] = wl.xi[:0, :1], wl.w[:0]
