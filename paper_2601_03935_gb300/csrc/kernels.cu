@@ -694,7 +694,7 @@ __host__ __device__ constexpr size_t sweep_main_bytes(int block, int planes, int
 //     operator, one thread per velocity (row 0);
 //  3. f^{k+1/2} = f^k + delta, staged in shared memory;
 //  4. velocity moments per (cell, chunk), eight lanes per cell.
-template <typename Real, int N, int DIM, int ORDER>
+template <typename Real, int N, int DIM, int ORDER, bool RESID = false>
 __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 : 6) : 1) k_sweep(Geom<Real> g, Quad<Real> q, const Real *__restrict__ coef,
                                                       const Real *__restrict__ bcoef, const Real *__restrict__ f_in,
                                                       const Real *__restrict__ fface, Real *__restrict__ f_out,
@@ -712,7 +712,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
     // the tensor-core epilogue's basis covers the 1-D and 2-D moments
     constexpr bool TCM = std::is_same<Real, float>::value && N == 4 && DIM < 3;
     constexpr int NMPD = Lay<DIM>::NMP;
-    const bool tc = TCM && g.tc && !g.resid;
+    const bool tc = TCM && g.tc && !RESID;
     Real *sxi = reinterpret_cast<Real *>(smem_raw + sweep_main_bytes(g.block, N, DIM, sizeof(Real), tc));   // [DIM+1][SV]
     signed char *Lg = reinterpret_cast<signed char *>(sxi + (DIM + 1) * SV);   // [block][MAXF] in-block neighbour or -1
     tcm::Ctl *ctl = reinterpret_cast<tcm::Ctl *>(Lg + ((g.block * MAXF + 15) & ~15));
@@ -877,9 +877,9 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
     // the in-block face records of phase 0, used where a < 0 (in-block inflow):
     //   forward  delta*_l = (r_l - sum_{j<l} a delta*_j) / d_l
     //   backward delta_l  = delta*_l - (sum_{j>l} a delta_j) / d_l
-    // (g.resid: the residuals themselves are the result; phases 2 and 3 are skipped and
+    // (RESID: the residuals themselves are the result; phases 2 and 3 are skipped and
     // phase 4 takes their moments)
-    if (ty == 0 && !g.resid) {
+    if (ty == 0 && !RESID) {
         for (int l = 0; l < nb; ++l) {
             Vec<Real, N> acc = R[l * SV + tx];
 #pragma unroll
@@ -983,7 +983,7 @@ __global__ void __launch_bounds__(SV * SROWS, sizeof(Real) == 4 ? (DIM < 3 ? 8 :
             return;
         }
     }
-    for (int l = ty; l < nb && !g.resid; l += SROWS) {
+    for (int l = ty; l < nb && !RESID; l += SROWS) {
         const size_t idx = (size_t)(c0 + l) * stride + v;
         V<Real, N> fo = ldv<Real, N>(f_in, idx);
         Vec<Real, N> t = R[l * SV + tx];
@@ -1951,13 +1951,13 @@ size_t sweep_smem_bytes(int block, int planes, int dim, size_t real_size, bool t
            (size_t)((block * MAXF + 15) & ~15) + (tc ? sizeof(tcm::Ctl) : 0);
 }
 
-template <typename Real, int N, int DIM, int ORDER>
+template <typename Real, int N, int DIM, int ORDER, bool RESID>
 static cudaError_t sweep_t(cudaStream_t s, const Geom<Real> &g, const Quad<Real> &q, const Real *coef,
                            const Real *bcoef, const Real *f_in, const Real *fface, Real *f_out, Real *partial) {
-    const bool tc = N == 4 && sizeof(Real) == 4 && DIM < 3 && g.tc;
+    const bool tc = N == 4 && sizeof(Real) == 4 && DIM < 3 && g.tc && !RESID;
     if (g.tc && (DIM == 3 || MT % g.block != 0)) return cudaErrorInvalidValue;
     const size_t smem = sweep_smem_bytes(g.block, N, DIM, sizeof(Real), tc);
-    auto kern = k_sweep<Real, N, DIM, ORDER>;
+    auto kern = k_sweep<Real, N, DIM, ORDER, RESID>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.n_cells + g.block - 1) / g.block, q.n_pad / SV), block(SV, SROWS);
@@ -1969,10 +1969,15 @@ template <typename Real>
 cudaError_t launch_sweep_gas(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &vq,
                              const Real *coef, const Real *bcoef, const Real *f_in, const Real *fface, Real *f_out,
                              Real *partial) {
-    if (order == 1) {
-        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 1>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
+    // g.resid selects the residual-only instantiation (the moments of the residual)
+    if (order == 1 && g.resid) {
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 1, true>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
+    } else if (order == 1) {
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 1, false>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
+    } else if (g.resid) {
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 2, true>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 2>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 4, DIM, 2, false>(s, g, vq, coef, bcoef, f_in, fface, f_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
@@ -1981,10 +1986,14 @@ template <typename Real>
 cudaError_t launch_sweep_photon(cudaStream_t s, int dim, int order, const Geom<Real> &g, const Quad<Real> &oq,
                                 const Real *coef, const Real *bcoef, const Real *I_in, const Real *fface,
                                 Real *I_out, Real *partial) {
-    if (order == 1) {
-        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 1>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
+    if (order == 1 && g.resid) {
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 1, true>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
+    } else if (order == 1) {
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 1, false>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
+    } else if (g.resid) {
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 2, true>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
     } else {
-        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 2>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
+        GSIS_DISPATCH_DIM3(dim, return (sweep_t<Real, 1, DIM, 2, false>(s, g, oq, coef, bcoef, I_in, fface, I_out, partial)));
     }
     return cudaErrorInvalidValue;
 }
