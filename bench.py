@@ -516,7 +516,8 @@ def time_to_steady_capsule(stream, n=12, n_v=16, Mach=3.0, tol=1e-6, max_gsis=30
 def normal_shock(max_gsis=300):
     """The paper's Mach-5 normal shock (FP64, order 2): CIS and GSIS outer iterations to
     eps < 2e-6 for (Z_r, Z_v) = (2.6, 26) on 200 L0 and (8, 100) on 350 L0, with the
-    paper's iteration counts beside them.  GSIS stops at max_gsis iterations."""
+    paper's iteration counts beside them; and GSIS with the defect-corrected synthetic
+    equations and 400 inner iterations.  GSIS stops at max_gsis iterations."""
     import torch
     import gsis_inputs as gi
     from paper_2601_03935_gb300 import gsis as G
@@ -530,8 +531,10 @@ def normal_shock(max_gsis=300):
                                            0, noise=0.0)
         res = {"cells": wl.mesh.n_cells, "n_xi": wl.xi.shape[0], "n_omega": wl.omega.shape[0],
                "paper_iterations": paper[Zv]}
-        for mode, name, mx in ((G.GSIS_MODE_CIS, "cis", 6000), (G.GSIS_MODE_GSIS, "gsis", max_gsis)):
-            ctx = create_ctx(wl, 0)
+        wl_dc = gi.workloads.with_solver(wl, defect_correction=1, max_inner=400)
+        for mode, name, mx, w_ in ((G.GSIS_MODE_CIS, "cis", 6000, wl), (G.GSIS_MODE_GSIS, "gsis", max_gsis, wl),
+                                   (G.GSIS_MODE_GSIS, "gsis_defect_corrected_400_inner", max_gsis, wl_dc)):
+            ctx = create_ctx(w_, 0)
             G.gsis_set_distributions(ctx, f, I)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -550,8 +553,9 @@ def slab_time_to_steady(oracle_seconds=40.0):
     thickness 1, 32 Gauss-Hermite velocities, 16 Gauss-Legendre directions, order 2, FP64)
     from the uniform rest state at T = 1.25: outer iterations and seconds to eps < 1e-8
     on the GPU for CIS and for GSIS (3 CIS iterations first), at the config's Kn = 0.1 and
-    at Kn = 0.01; and the FP64 oracle's time to the same tolerance on one host core
-    (stopped after about `oracle_seconds`)."""
+    at Kn = 0.01, at Kn = 0.1 also GSIS with the defect correction and the synchronisation
+    weight 0.8; and the FP64 oracle's time to the same tolerance on one host core (stopped
+    after about `oracle_seconds`)."""
     import torch
     import gsis_inputs as gi
     from oracle import gsis as OG
@@ -567,8 +571,12 @@ def slab_time_to_steady(oracle_seconds=40.0):
                                            noise=0.0)
         res = {"workload": "slab 1-D, 64 cells, 32 velocities, 16 directions, Kn %g, Kn_p 1, FP64, order 2, "
                            "%d inner iterations, eps < 1e-8" % (kn, inner)}
-        for mode, name, mx in ((G.GSIS_MODE_GSIS, "gsis", 200), (G.GSIS_MODE_CIS, "cis", 20000)):
-            ctx = create_ctx(wl, 0)
+        runs = [(G.GSIS_MODE_GSIS, "gsis", 200, wl), (G.GSIS_MODE_CIS, "cis", 20000, wl)]
+        if kn == 0.1:
+            runs.append((G.GSIS_MODE_GSIS, "gsis_defect_corrected_w0.8", 600,
+                         gi.workloads.with_solver(wl, defect_correction=1, sync_relax=0.8)))
+        for mode, name, mx, w_ in runs:
+            ctx = create_ctx(w_, 0)
             G.gsis_set_distributions(ctx, f, I)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
