@@ -188,6 +188,9 @@ typedef struct {
                                    (the paper's synthetic equations match it only to the
                                    discretisation error, which leaves an eps floor).  Costs one
                                    slope pass and one residual-only sweep per GSIS iteration.
+                                   With GSIS_FP32 storage the residual moments are FP32 sums
+                                   whose rounding the offset carries into every solve (eps then
+                                   stops near 1e-6 to 1e-5): meant for GSIS_FP64.
                                    An extension; 0 (default) is the paper's step.  Not with
                                    velocity shards (UNSUPPORTED).                            */
 } gsis_solver_params;
