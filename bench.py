@@ -477,7 +477,7 @@ def time_to_steady_handover(args, kn=0.1, kn_p=10.0, w=0.7, tol=1e-6, switch=3e-
 
 
 def time_to_steady_capsule(stream, n=12, n_v=16, Mach=3.0, tol=1e-6, max_gsis=300, max_cis=3000):
-    """Time to eps < tol on a reduced 3-D capsule (the config-4 geometry on 6 n^3 tetrahedra
+    """Time to eps < tol on a reduced 3-D capsule (the sphere-cone capsule geometry on 6 n^3 tetrahedra
     less the body, n_v^3 velocities, 8 x 16 directions, Kn = 0.01) at Mach 3, where 16^3
     velocities resolve the free stream, order 1, from the uniform free stream: GSIS in
     plain FP64 and with FP32 distributions and the mixed synthetic schedule, and CIS in FP32."""
@@ -549,7 +549,7 @@ def normal_shock(max_gsis=300):
 
 
 def slab_time_to_steady(oracle_seconds=40.0):
-    """The 1-D planar slab of config 1 (64 cells between walls at T = 1 and 1.5, optical
+    """The 1-D planar slab (64 cells between walls at T = 1 and 1.5, optical
     thickness 1, 32 Gauss-Hermite velocities, 16 Gauss-Legendre directions, order 2, FP64)
     from the uniform rest state at T = 1.25: outer iterations and seconds to eps < 1e-8
     on the GPU for CIS and for GSIS (3 CIS iterations first), at the config's Kn = 0.1 and
