@@ -118,3 +118,40 @@ def test_side_stream_photon_transport_gives_identical_results(stream_kind):
         assert got[0] == ref[0]
         for a, b in zip(got[1:], ref[1:]):
             assert np.array_equal(a, b)
+
+
+def test_distributions_replaced_between_steps_give_the_results_of_a_fresh_context():
+    """A call that replaces the distributions between two steps (upload, set, state
+    import) leaves the second step bit-identical to the same step of a fresh context: no
+    state of the first step (face values, coefficients, side-stream work) leaks into it."""
+    wl = gi.workloads.with_solver(gi.workloads.cavity(n_side=13), precision="fp32", order=2, relax_block=16)
+    nc, V, NO = wl.mesh.n_cells, wl.xi.shape[0], wl.omega.shape[0]
+    (f1, I1), (f2, I2) = _states(wl, 2)
+    stream = torch.cuda.Stream()
+
+    def second_step(replace):
+        ctx = create(wl, stream.cuda_stream)
+        try:
+            G.gsis_upload_distributions(ctx, f1.data_ptr(), I1.data_ptr())
+            G.gsis_step(ctx, G.GSIS_MODE_CIS)
+            replace(ctx)
+            eps = G.gsis_step(ctx, G.GSIS_MODE_CIS)
+            return eps, G.gsis_get_distributions(ctx, nc, V, NO)
+        finally:
+            G.gsis_destroy(ctx)
+
+    ref_ctx = create(wl, stream.cuda_stream)
+    try:
+        G.gsis_upload_distributions(ref_ctx, f2.data_ptr(), I2.data_ptr())
+        state = G.gsis_export_state(ref_ctx)
+        eps_ref = G.gsis_step(ref_ctx, G.GSIS_MODE_CIS)
+        ref = G.gsis_get_distributions(ref_ctx, nc, V, NO)
+    finally:
+        G.gsis_destroy(ref_ctx)
+    f2d, I2d = f2.numpy().astype(np.float64), I2.numpy().astype(np.float64)
+    for name, replace in (("upload", lambda c: G.gsis_upload_distributions(c, f2.data_ptr(), I2.data_ptr())),
+                          ("set", lambda c: G.gsis_set_distributions(c, f2d, I2d)),
+                          ("import", lambda c: G.gsis_import_state(c, state))):
+        eps, got = second_step(replace)
+        assert eps == eps_ref, name
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1]), name
